@@ -1,0 +1,173 @@
+/*
+ * xm.h - C ABI of libxm: the data-parallel hot path of XM (scaled bundle adjustment solved
+ * as an SDP by Burer-Monteiro factorisation, a Riemannian trust-region method and a dual
+ * certificate), for NVIDIA B300 (sm_103a).
+ *
+ * Notation follows the paper: N cameras, M landmarks, E observations (i, k, u_ik, w_ik),
+ * n = 3N.  The BM factor U = [Rbar_1 ... Rbar_N] (r x 3N, Prop. 4) is exchanged as
+ * Y = U^T, an n x r row-major array of doubles (camera i owns rows 3i..3i+2, the "world"
+ * dimension r is fastest).  Camera 0 is the anchor (the paper's camera 1: R = I, s = 1).
+ *
+ * Conventions for every entry point
+ *   - Array arguments are DEVICE pointers owned by the caller unless the name ends in
+ *     _host; the library never frees them and never keeps them after the call returns.
+ *   - Work is issued on the stream given to xm_create.  Calls that must read scalars
+ *     back (solve, certify, build, the pipeline) synchronise that stream before returning;
+ *     xm_qy is asynchronous.
+ *   - Errors are returned as xm_status; xm_last_error() gives a message for the calling
+ *     thread.  No call traps or aborts the device: device-side checks raise an error word
+ *     that the host turns into a status.  On error, output arrays are unspecified.
+ *   - Not thread-safe per context; distinct contexts may be used from distinct threads.
+ */
+#ifndef XM_H_
+#define XM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define XM_ABI_VERSION 1
+#define XM_MAX_RANK 8   /* largest BM rank r the kernels handle (Alg. 1 stops there) */
+
+typedef struct xm_ctx xm_ctx;   /* opaque: device, stream, workspaces */
+typedef struct xm_qmat xm_qmat; /* opaque: the reduced data matrix Q on the device */
+
+typedef enum xm_status {
+  XM_OK = 0,
+  XM_EINVAL = 1,        /* bad argument or observation (index range, w <= 0, NaN) */
+  XM_EDISCONNECTED = 2, /* view graph not connected: Q_tp rank < N+M-1 (App. A lemma) */
+  XM_ECUDA = 3,         /* CUDA runtime / library error */
+  XM_ENOMEM = 4,        /* device allocation failed */
+  XM_ENOCONV = 5,       /* iteration or time limit reached; best iterate returned */
+  XM_ENUMERIC = 6,      /* NaN/Inf in the objective or gradient */
+  XM_ETIMEOUT = 7,      /* a bounded device-side wait gave up (kernel pipeline stall) */
+  XM_ENOTCERT = 8       /* lambda_min(Z) < -tau at r_max: results filled, not certified */
+} xm_status;
+
+/* Precision modes (arithmetic of the Q.Y sweeps).
+ * XM_FP64:        every sweep, vector and scalar in FP64 (Q stored FP64).
+ * XM_FP32_BULK:   RTR-tCG in FP32 (Q stored FP32), then an FP64 polish (FP64 gradient and
+ *                 objective, FP32 Hessian-vector products) and the FP64 certificate.
+ * XM_BF16Q_BULK:  as XM_FP32_BULK but the tCG Hessian-vector products read Q stored in
+ *                 BF16 (FP32 accumulation); gradients and objectives use FP32/FP64 Q. */
+typedef enum xm_prec { XM_FP64 = 0, XM_FP32_BULK = 1, XM_BF16Q_BULK = 2 } xm_prec;
+
+/* Storage copies of Q that xm_build_Q keeps (bit mask). */
+#define XM_STORE_FP64 1u   /* FP64 packed upper-triangle tiles (needed by XM_FP64, polish) */
+#define XM_STORE_FP32 2u   /* FP32 packed tiles */
+#define XM_STORE_BF16 4u   /* BF16 packed tiles */
+#define XM_STORE_ALL  7u
+
+typedef struct xm_opts {
+  int r0;                  /* initial BM rank, 1 <= r0 <= XM_MAX_RANK (Alg. 1 uses 3)      */
+  int r_max;               /* staircase cap, r0 <= r_max <= XM_MAX_RANK                    */
+  int prec;                /* xm_prec                                                       */
+  double grad_tol_rel;     /* final stop: ||rgrad|| <= grad_tol_rel * ||rgrad(Y0)||         */
+  double bulk_tol_rel;     /* mixed modes: hand over to the FP64 polish at this tolerance   */
+  double cert_tau_rel;     /* certified iff lambda_min(Z) >= -cert_tau_rel * lambda_max     */
+  int max_outer;           /* RTR iterations per rank (per phase)                          */
+  int max_tcg;             /* tCG iterations per RTR step                                  */
+  int max_polish;          /* FP64 polish RTR iterations (mixed modes)                     */
+  int lanczos_max;         /* Krylov dimension cap of the certificate                      */
+  double lanczos_tol;      /* Ritz residual / |theta_max| stop for lambda_min              */
+  double time_limit_s;     /* wall-clock cap of xm_solve (<= 0: none)                      */
+  uint64_t seed;           /* Lanczos start vector                                         */
+  int verbose;             /* 0 silent, 1 per rank, 2 per RTR iteration (stderr)           */
+} xm_opts;
+
+typedef struct xm_info {
+  double f;                /* tr(Q Y^T Y) at the returned Y, FP64 (Eq. 17 objective)        */
+  double grad_norm;        /* ||rgrad|| at the returned Y, FP64                              */
+  double lambda_min;       /* lambda_min(Z), Z = Q - blockdiag(Lambda) (Thm. 1), FP64 Ritz  */
+  double lambda_min_deflated; /* smallest Ritz value of Z on range(Y)^perp                  */
+  double lambda_max;       /* largest Ritz value of Z (scale of the tolerance tau)           */
+  double dual;             /* sum b_i y_i = tr(Lambda_0)                                     */
+  double rho_hat;          /* objective of the rounded SO(3) solution (Eq. 5)                */
+  double eta;              /* Eq. 18 relative suboptimality                                   */
+  double eta_robust;       /* App. E bound with min(0, lambda_min) tr(X)                      */
+  int rank;                /* BM rank r of the returned Y                                    */
+  int certified;           /* 1 iff lambda_min >= -tau                                       */
+  int n_sweeps;            /* Q.Y sweeps of every precision                                  */
+  int n_sweeps_fp64;       /* of which FP64                                                  */
+  int n_outer, n_tcg, n_lanczos, n_escapes;
+  double t_solve_s, t_cert_s, t_build_s;
+  double qy_ms_fp32, qy_ms_fp64; /* mean device time of one r-column sweep, when measured   */
+} xm_info;
+
+/* ---- context ---------------------------------------------------------------------- */
+int         xm_abi_version(void);
+void        xm_default_opts(xm_opts* opts);
+/* device: CUDA ordinal; stream: a cudaStream_t (NULL = legacy default stream). */
+xm_status   xm_create(xm_ctx** out, int device, void* stream);
+void        xm_destroy(xm_ctx* ctx);
+const char* xm_last_error(void);
+xm_status   xm_sync(xm_ctx* ctx);
+
+/* ---- Q construction (Prop. 1, App. A) ------------------------------------------------
+ * Q = P - Bbar Sbar^{-1} Bbar^T with P = Q1 - V2 Q3^{-1} V2^T, B = V1 - V2 Q3^{-1} V3^T,
+ * S = Q2 - V3 Q3^{-1} V3^T (landmarks eliminated, then translations with t_0 = 0); equal to
+ * the printed A^T Q_tp A + V_tp A + A^T V_tp^T + Q1.  FP64 arithmetic throughout.
+ * cam, lmk: int32[E]; ukp: double[E][3] (u_ik, camera frame); w: double[E] (> 0).
+ * Observations may come in any order; landmarks with one observation contribute zero.
+ * Fails with XM_EINVAL on out-of-range indices, w <= 0 or non-finite values, and with
+ * XM_EDISCONNECTED when the view graph is not connected.  store_mask: XM_STORE_*.
+ * The returned handle owns its device memory until xm_free_Q. */
+xm_status xm_build_Q(xm_ctx* ctx, int N, int M, int64_t E, const int32_t* cam,
+                     const int32_t* lmk, const double* ukp, const double* w,
+                     unsigned store_mask, xm_qmat** out);
+/* Q from a dense symmetric n x n FP64 array (device, row-major); for tests. */
+xm_status xm_qmat_from_dense(xm_ctx* ctx, int N, const double* Q, unsigned store_mask,
+                             xm_qmat** out);
+/* Copy Q back as a dense symmetric n x n FP64 row-major array (device); needs the FP64
+ * copy. */
+xm_status xm_qmat_to_dense(xm_ctx* ctx, const xm_qmat* q, double* Q_out);
+xm_status xm_qmat_dims(const xm_qmat* q, int* N, int* n, unsigned* store_mask);
+xm_status xm_free_Q(xm_ctx* ctx, xm_qmat* q);
+
+/* ---- one sweep (Sec. 3.2, Euclidean Hessian-vector product) ---------------------------
+ * W = Q Y for an n x r row-major Y, r in [1, XM_MAX_RANK].  prec picks the stored copy:
+ * XM_FP64 reads FP64 Q with double Y/W; XM_FP32_BULK reads FP32 Q, XM_BF16Q_BULK BF16 Q,
+ * both with float Y/W.  Asynchronous on the context stream. */
+xm_status xm_qy(xm_ctx* ctx, const xm_qmat* q, int prec, int r, const void* Y, void* W);
+
+/* Device time of one sweep, measured with CUDA events on the context stream after three
+ * warm-up sweeps (Y filled with a fixed pattern, W zeroed before each sweep outside the timed
+ * interval).  ms_mean / ms_min may be NULL.  Synchronous. */
+xm_status xm_bench_qy(xm_ctx* ctx, const xm_qmat* q, int prec, int r, int iters, double* ms_mean,
+                      double* ms_min);
+/* Kernel launches issued by the most recent xm_solve / xm_certify call of this process. */
+long xm_last_launch_count(void);
+
+/* ---- solve (Alg. 1 + RTR-tCG, Sec. 3) -------------------------------------------------
+ * Y0: NULL for Alg. 1's [I_3, ..., I_3] start padded with zero columns to rank r0, else an
+ * n x r_in row-major start (made feasible by the retraction).  Outputs (device, may be NULL):
+ * Y_out n x XM_MAX_RANK (columns >= rank are zero), R_out N x 3 x 3 and s_out N of the
+ * rounded solution (Sec. 2.2).  Synchronous.  Returns XM_ENOTCERT if the staircase stops
+ * at r_max without a certificate, XM_ENOCONV on the time limit. */
+xm_status xm_solve(xm_ctx* ctx, const xm_qmat* q, const xm_opts* opts, int r_in,
+                   const double* Y0, double* Y_out, double* R_out, double* s_out,
+                   xm_info* info);
+
+/* ---- certificate (Thm. 1) ---------------------------------------------------------------
+ * For a rank-r Y (n x r row-major): Lambda_i = P_i(sym((QY)_i Y_i^T)) / alpha_i, Z = Q -
+ * blockdiag(Lambda), lambda_min(Z) by Lanczos with full reorthogonalisation on range(Y)^perp
+ * (FP64 vectors and Ritz values).  Lambda_out: N x 3 x 3 (may be NULL); v_out: n (the Ritz
+ * vector of lambda_min, may be NULL).  Synchronous. */
+xm_status xm_certify(xm_ctx* ctx, const xm_qmat* q, const xm_opts* opts, int r,
+                     const double* Y, double* Lambda_out, double* v_out, xm_info* info);
+
+/* ---- end-to-end from host arrays --------------------------------------------------------
+ * Copies the observations to the device, builds Q, solves, certifies and rounds, and
+ * copies R (N x 3 x 3) and s (N) back.  Every pointer here is a HOST pointer. */
+xm_status xm_pipeline_host(xm_ctx* ctx, int N, int M, int64_t E, const int32_t* cam_host,
+                           const int32_t* lmk_host, const double* ukp_host,
+                           const double* w_host, const xm_opts* opts, double* R_host,
+                           double* s_host, xm_info* info);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* XM_H_ */

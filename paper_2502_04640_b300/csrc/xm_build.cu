@@ -1,0 +1,411 @@
+// Construction of the reduced data matrix Q (Prop. 1, App. A) on the device, in FP64.
+//
+//   1. validate observations, accumulate per camera Q1 blocks (sum w u u^T), V1 (sum w u) and
+//      Q2 (sum w), per landmark Q3 (d_k = sum w);
+//   2. landmark elimination: for every landmark the camera pairs (a, b) of its observers get
+//      P_ab -= w_a w_b u_a u_b^T / d_k, B_ab -= w_a w_b u_a / d_k, S_ab -= w_a w_b / d_k
+//      (P = Q1 - V2 D^-1 V2^T, B = V1 - V2 D^-1 V3^T, S = Q2 - V3 D^-1 V3^T with D = Q3);
+//   3. translation elimination with the anchor t_0 = 0: Sbar = L L^T (Cholesky), C = L^-1 Bbar^T,
+//      Q = P - C^T C (dense FP64 factor / triangular solve / rank-k update from cuSOLVER and
+//      cuBLAS: the paper's "large dense matrix multiplications");
+//   4. pack the upper triangle into the tile layout of the sweep kernel (FP64 / FP32 / BF16).
+// Connectivity of the view graph (rank N+M-1 of the Laplacian Q_tp, App. A lemma) is checked
+// with a union-find over the camera-landmark edges before any elimination.
+#include <cublas_v2.h>
+#include <cusolverDn.h>
+
+#include <chrono>
+
+#include "xm_internal.cuh"
+
+namespace xm {
+
+// ------------------------------------------------------------------ validation / sums
+__global__ void k_validate(int64_t E, int N, int M, const int32_t* cam, const int32_t* lmk,
+                           const double* ukp, const double* w, int* err) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = cam[e], k = lmk[e];
+    if (i < 0 || i >= N || k < 0 || k >= M) atomicOr(err, DEV_BAD_INDEX);
+    const double ww = w[e];
+    const double u0 = ukp[3 * e], u1 = ukp[3 * e + 1], u2 = ukp[3 * e + 2];
+    if (!(ww > 0.0) || !isfinite(ww) || !isfinite(u0) || !isfinite(u1) || !isfinite(u2))
+      atomicOr(err, DEV_BAD_VALUE);
+  }
+}
+
+// union-find over vertices 0..N-1 (cameras) and N..N+M-1 (landmarks).  Links always point from
+// a larger to a smaller index, so every parent chain strictly decreases and find() terminates.
+__device__ int uf_find(int* parent, int x) {
+  while (true) {
+    const int p = parent[x];
+    if (p == x) return x;
+    const int gp = parent[p];
+    if (gp != p) atomicCAS(&parent[x], p, gp);   // path halving (benign race)
+    x = p;
+  }
+}
+__global__ void k_uf_init(int* parent, int nv) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += gridDim.x * blockDim.x)
+    parent[v] = v;
+}
+__global__ void k_uf_union(int64_t E, int N, const int32_t* cam, const int32_t* lmk, int* parent) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int a = cam[e], b = N + lmk[e];
+    for (int guard = 0; guard < (1 << 20); ++guard) {
+      int ra = uf_find(parent, a), rb = uf_find(parent, b);
+      if (ra == rb) break;
+      if (ra < rb) { const int t = ra; ra = rb; rb = t; }
+      if (atomicCAS(&parent[ra], ra, rb) == ra) break;   // link the larger root under the smaller
+    }
+  }
+}
+// every camera and every observed landmark must share camera 0's root
+__global__ void k_uf_check(int64_t E, int N, const int32_t* cam, const int32_t* lmk, int* parent,
+                           int* disconnected) {
+  const int r0 = uf_find(parent, 0);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E + N;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int v = e < E ? N + lmk[e] : (int)(e - E);
+    if (uf_find(parent, v) != r0) *disconnected = 1;
+  }
+}
+
+// per-observation terms on the camera diagonal: Q1 block (upper entries), V1 column, Q2;
+// and the landmark weight sums d_k and counts.
+__global__ void k_camera_terms(int64_t E, int n, int N, const int32_t* cam, const int32_t* lmk,
+                               const double* ukp, const double* w, double* P, double* B,
+                               double* S, double* d, int* cnt) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = cam[e], k = lmk[e];
+    const double ww = w[e];
+    const double u[3] = {ukp[3 * e], ukp[3 * e + 1], ukp[3 * e + 2]};
+    for (int p = 0; p < 3; ++p) {
+      for (int q = p; q < 3; ++q) atomicAdd(&P[(size_t)(3 * i + p) * n + 3 * i + q], ww * u[p] * u[q]);
+      atomicAdd(&B[(size_t)(3 * i + p) * N + i], ww * u[p]);
+    }
+    atomicAdd(&S[(size_t)i * N + i], ww);
+    atomicAdd(&d[k], ww);
+    atomicAdd(&cnt[k], 1);
+  }
+}
+
+// ------------------------------------------------------------------ landmark CSR
+// exclusive scan of cnt[0..M) into off[0..M] (blocks of 1024, two levels)
+__global__ void k_scan_blocks(const int* in, int64_t* out, int64_t* bsum, int M) {
+  __shared__ int64_t sh[1024];
+  const int i = blockIdx.x * 1024 + threadIdx.x;
+  int64_t v = i < M ? in[i] : 0;
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    int64_t t = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
+    __syncthreads();
+    sh[threadIdx.x] += t;
+    __syncthreads();
+  }
+  if (i < M) out[i] = sh[threadIdx.x] - v;
+  if (threadIdx.x == 1023) bsum[blockIdx.x] = sh[1023];
+}
+__global__ void k_scan_sums(int64_t* bsum, int nb) {   // one thread: nb is small (M / 1024)
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    int64_t run = 0;
+    for (int b = 0; b < nb; ++b) { const int64_t t = bsum[b]; bsum[b] = run; run += t; }
+    bsum[nb] = run;
+  }
+}
+__global__ void k_scan_add(int64_t* out, const int64_t* bsum, int M) {
+  const int i = blockIdx.x * 1024 + threadIdx.x;
+  if (i < M) out[i] += bsum[blockIdx.x];
+  if (i == 0) out[M] = bsum[(M + 1023) / 1024];
+}
+__global__ void k_csr_fill(int64_t E, const int32_t* lmk, const int64_t* off, int* cursor,
+                           int64_t* idx) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int k = lmk[e];
+    const int pos = atomicAdd(&cursor[k], 1);
+    idx[off[k] + pos] = e;
+  }
+}
+// Deterministic order within each landmark: sort its observation indices (short segments).
+__global__ void k_csr_sort(int M, const int64_t* off, int64_t* idx) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < M; k += gridDim.x * blockDim.x) {
+    const int64_t a = off[k], b = off[k + 1];
+    for (int64_t x = a + 1; x < b; ++x) {
+      const int64_t v = idx[x];
+      int64_t y = x - 1;
+      while (y >= a && idx[y] > v) { idx[y + 1] = idx[y]; --y; }
+      idx[y + 1] = v;
+    }
+  }
+}
+
+// landmark elimination: one thread per landmark, all ordered observer pairs
+__global__ void k_landmark_schur(int M, int n, int N, const int64_t* off, const int64_t* idx,
+                                 const int32_t* cam, const double* ukp, const double* w,
+                                 const double* d, double* P, double* B, double* S) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < M; k += gridDim.x * blockDim.x) {
+    const int64_t a0 = off[k], a1 = off[k + 1];
+    if (a1 - a0 < 1 || !(d[k] > 0.0)) continue;
+    const double dinv = 1.0 / d[k];
+    for (int64_t x = a0; x < a1; ++x) {
+      const int64_t ea = idx[x];
+      const int i = cam[ea];
+      const double wa = w[ea] * dinv;
+      const double ua[3] = {ukp[3 * ea], ukp[3 * ea + 1], ukp[3 * ea + 2]};
+      for (int64_t y = a0; y < a1; ++y) {
+        const int64_t eb = idx[y];
+        const int j = cam[eb];
+        const double c = wa * w[eb];
+        const double ub[3] = {ukp[3 * eb], ukp[3 * eb + 1], ukp[3 * eb + 2]};
+        for (int p = 0; p < 3; ++p) atomicAdd(&B[(size_t)(3 * i + p) * N + j], -c * ua[p]);
+        if (i < j) {
+          for (int p = 0; p < 3; ++p)
+            for (int q = 0; q < 3; ++q)
+              atomicAdd(&P[(size_t)(3 * i + p) * n + 3 * j + q], -c * ua[p] * ub[q]);
+          atomicAdd(&S[(size_t)i * N + j], -c);
+        } else if (i == j) {
+          for (int p = 0; p < 3; ++p)
+            for (int q = p; q < 3; ++q)
+              atomicAdd(&P[(size_t)(3 * i + p) * n + 3 * i + q], -c * ua[p] * ub[q]);
+          atomicAdd(&S[(size_t)i * N + i], -c);
+        }
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ tile packing
+// Reads the upper triangle (row <= col) of a row-major n x n FP64 matrix; one block per tile.
+__global__ void k_pack_tiles(const double* __restrict__ Qd, int n, int nt, int64_t ntiles,
+                             double* q64, float* q32, __nv_bfloat16* q16) {
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    // tile coordinates from the linear index (row-major upper triangle)
+    int I = (int)(((2.0f * nt + 1.0f) -
+                   sqrtf((2.0f * nt + 1.0f) * (2.0f * nt + 1.0f) - 8.0f * (float)t)) * 0.5f);
+    if (I < 0) I = 0;
+    if (I > nt - 1) I = nt - 1;
+    while (I > 0 && tile_index(nt, I, I) > t) --I;
+    while (I + 1 < nt && tile_index(nt, I + 1, I + 1) <= t) ++I;
+    const int J = I + (int)(t - tile_index(nt, I, I));
+    const int64_t g0 = t * TILE * TILE;
+    for (int e = threadIdx.x; e < TILE * TILE; e += blockDim.x) {
+      const int a = e / TILE, b = e % TILE;
+      const int row = I * TILE + a, col = J * TILE + b;
+      double v = 0.0;
+      if (row < n && col < n) {
+        if (I < J || a < b) v = Qd[(size_t)row * n + col];
+        else if (a == b) v = 0.5 * Qd[(size_t)row * n + col];
+      }
+      if (q64) q64[g0 + e] = v;
+      if (q32) q32[g0 + e] = (float)v;
+      if (q16) q16[g0 + e] = __double2bfloat16(v);
+    }
+  }
+}
+
+// dense symmetric n x n from FP64 tiles
+__global__ void k_unpack_tiles(const double* __restrict__ q64, int n, int nt, double* Qd) {
+  const int64_t total = (int64_t)n * n;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    int row = (int)(g / n), col = (int)(g % n);
+    if (row > col) { const int t = row; row = col; col = t; }
+    const int I = row / TILE, J = col / TILE, a = row % TILE, b = col % TILE;
+    double v = q64[tile_index(nt, I, J) * TILE * TILE + (int64_t)a * TILE + b];
+    if (I == J && a == b) v *= 2.0;
+    Qd[g] = v;
+  }
+}
+
+static int grid_for(int64_t work, int threads, int num_sms) {
+  int64_t g = (work + threads - 1) / threads;
+  const int64_t cap = (int64_t)num_sms * 32;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+xm_status alloc_tiles(xm_ctx* ctx, DeviceQ& q, int N, unsigned mask) {
+  (void)ctx;
+  q.N = N;
+  q.n = 3 * N;
+  q.nt = (q.n + TILE - 1) / TILE;
+  q.n_pad = q.nt * TILE;
+  q.ntiles = tile_count(q.nt);
+  q.mask = mask;
+  const size_t elems = (size_t)q.ntiles * TILE * TILE;
+  if (mask & XM_STORE_FP64) XM_CUDA_TRY(cudaMalloc(&q.q64, elems * sizeof(double)));
+  if (mask & XM_STORE_FP32) XM_CUDA_TRY(cudaMalloc(&q.q32, elems * sizeof(float)));
+  if (mask & XM_STORE_BF16) XM_CUDA_TRY(cudaMalloc(&q.q16, elems * sizeof(__nv_bfloat16)));
+  return XM_OK;
+}
+
+void free_tiles(DeviceQ& q) {
+  if (q.q64) cudaFree(q.q64);
+  if (q.q32) cudaFree(q.q32);
+  if (q.q16) cudaFree(q.q16);
+  q.q64 = nullptr; q.q32 = nullptr; q.q16 = nullptr;
+}
+
+xm_status pack_dense(xm_ctx* ctx, DeviceQ& q, const double* Qd) {
+  const int grid = (int)(q.ntiles < (int64_t)ctx->num_sms * 16 ? q.ntiles : (int64_t)ctx->num_sms * 16);
+  k_pack_tiles<<<grid, 256, 0, ctx->stream>>>(Qd, q.n, q.nt, q.ntiles, q.q64, q.q32, q.q16);
+  XM_CUDA_TRY(cudaGetLastError());
+  return XM_OK;
+}
+
+xm_status unpack_dense(xm_ctx* ctx, const DeviceQ& q, double* Qd) {
+  if (!q.q64) return set_error(XM_EINVAL, "Q has no FP64 copy to unpack");
+  const int64_t total = (int64_t)q.n * q.n;
+  k_unpack_tiles<<<grid_for(total, 256, ctx->num_sms), 256, 0, ctx->stream>>>(q.q64, q.n, q.nt, Qd);
+  XM_CUDA_TRY(cudaGetLastError());
+  return XM_OK;
+}
+
+#define XM_CUBLAS_TRY(expr)                                                                \
+  do {                                                                                     \
+    cublasStatus_t s_ = (expr);                                                            \
+    if (s_ != CUBLAS_STATUS_SUCCESS)                                                       \
+      return set_error(XM_ECUDA, "%s failed: cublas status %d", #expr, (int)s_);           \
+  } while (0)
+#define XM_CUSOLVER_TRY(expr)                                                              \
+  do {                                                                                     \
+    cusolverStatus_t s_ = (expr);                                                          \
+    if (s_ != CUSOLVER_STATUS_SUCCESS)                                                     \
+      return set_error(XM_ECUDA, "%s failed: cusolver status %d", #expr, (int)s_);         \
+  } while (0)
+
+namespace {
+struct DevBuf {
+  void* p = nullptr;
+  ~DevBuf() { if (p) cudaFree(p); }
+  template <typename T> T* as() { return static_cast<T*>(p); }
+};
+}  // namespace
+
+xm_status build_Q(xm_ctx* ctx, int N, int M, int64_t E, const int32_t* cam, const int32_t* lmk,
+                  const double* ukp, const double* w, unsigned mask, DeviceQ& out,
+                  double* t_build) {
+  auto tic = std::chrono::steady_clock::now();
+  cudaStream_t st = ctx->stream;
+  const int n = 3 * N;
+  const int threads = 256;
+  XM_CUDA_TRY(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), st));
+  if (E > 0) {
+    k_validate<<<grid_for(E, threads, ctx->num_sms), threads, 0, st>>>(E, N, M, cam, lmk, ukp, w,
+                                                                       ctx->d_err);
+    XM_CUDA_TRY(cudaGetLastError());
+  }
+  XM_TRY(check_device_error(ctx, "observation validation"));
+
+  // ---- connectivity (App. A lemma: rank N + M - 1 iff the view graph is connected)
+  {
+    DevBuf parent, flag;
+    XM_CUDA_TRY(cudaMalloc(&parent.p, sizeof(int) * (size_t)(N + M)));
+    XM_CUDA_TRY(cudaMalloc(&flag.p, sizeof(int)));
+    XM_CUDA_TRY(cudaMemsetAsync(flag.p, 0, sizeof(int), st));
+    k_uf_init<<<grid_for(N + M, threads, ctx->num_sms), threads, 0, st>>>(parent.as<int>(), N + M);
+    if (E > 0)
+      k_uf_union<<<grid_for(E, threads, ctx->num_sms), threads, 0, st>>>(E, N, cam, lmk,
+                                                                          parent.as<int>());
+    k_uf_check<<<grid_for(E + N, threads, ctx->num_sms), threads, 0, st>>>(
+        E, N, cam, lmk, parent.as<int>(), flag.as<int>());
+    XM_CUDA_TRY(cudaGetLastError());
+    int h = 0;
+    XM_CUDA_TRY(cudaMemcpyAsync(&h, flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    XM_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h) return set_error(XM_EDISCONNECTED, "view graph is not connected (N=%d, M=%d)", N, M);
+  }
+
+  DevBuf P, B, S, d, cnt, off, bsum, cursor, idx;
+  XM_CUDA_TRY(cudaMalloc(&P.p, sizeof(double) * (size_t)n * n));
+  XM_CUDA_TRY(cudaMalloc(&B.p, sizeof(double) * (size_t)n * N));
+  XM_CUDA_TRY(cudaMalloc(&S.p, sizeof(double) * (size_t)N * N));
+  XM_CUDA_TRY(cudaMalloc(&d.p, sizeof(double) * (size_t)(M > 0 ? M : 1)));
+  XM_CUDA_TRY(cudaMalloc(&cnt.p, sizeof(int) * (size_t)(M > 0 ? M : 1)));
+  XM_CUDA_TRY(cudaMemsetAsync(P.p, 0, sizeof(double) * (size_t)n * n, st));
+  XM_CUDA_TRY(cudaMemsetAsync(B.p, 0, sizeof(double) * (size_t)n * N, st));
+  XM_CUDA_TRY(cudaMemsetAsync(S.p, 0, sizeof(double) * (size_t)N * N, st));
+  XM_CUDA_TRY(cudaMemsetAsync(d.p, 0, sizeof(double) * (size_t)(M > 0 ? M : 1), st));
+  XM_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, sizeof(int) * (size_t)(M > 0 ? M : 1), st));
+  if (E > 0) {
+    k_camera_terms<<<grid_for(E, threads, ctx->num_sms), threads, 0, st>>>(
+        E, n, N, cam, lmk, ukp, w, P.as<double>(), B.as<double>(), S.as<double>(), d.as<double>(),
+        cnt.as<int>());
+    XM_CUDA_TRY(cudaGetLastError());
+  }
+  if (M > 0 && E > 0) {
+    const int nb = (M + 1023) / 1024;
+    XM_CUDA_TRY(cudaMalloc(&off.p, sizeof(int64_t) * (size_t)(M + 1)));
+    XM_CUDA_TRY(cudaMalloc(&bsum.p, sizeof(int64_t) * (size_t)(nb + 1)));
+    XM_CUDA_TRY(cudaMalloc(&cursor.p, sizeof(int) * (size_t)M));
+    XM_CUDA_TRY(cudaMalloc(&idx.p, sizeof(int64_t) * (size_t)E));
+    XM_CUDA_TRY(cudaMemsetAsync(cursor.p, 0, sizeof(int) * (size_t)M, st));
+    k_scan_blocks<<<nb, 1024, 0, st>>>(cnt.as<int>(), off.as<int64_t>(), bsum.as<int64_t>(), M);
+    k_scan_sums<<<1, 32, 0, st>>>(bsum.as<int64_t>(), nb);
+    k_scan_add<<<nb, 1024, 0, st>>>(off.as<int64_t>(), bsum.as<int64_t>(), M);
+    k_csr_fill<<<grid_for(E, threads, ctx->num_sms), threads, 0, st>>>(
+        E, lmk, off.as<int64_t>(), cursor.as<int>(), idx.as<int64_t>());
+    k_csr_sort<<<grid_for(M, threads, ctx->num_sms), threads, 0, st>>>(M, off.as<int64_t>(),
+                                                                      idx.as<int64_t>());
+    k_landmark_schur<<<grid_for(M, 128, ctx->num_sms), 128, 0, st>>>(
+        M, n, N, off.as<int64_t>(), idx.as<int64_t>(), cam, ukp, w, d.as<double>(),
+        P.as<double>(), B.as<double>(), S.as<double>());
+    XM_CUDA_TRY(cudaGetLastError());
+  }
+
+  // ---- translation elimination (dense FP64)
+  if (N > 1) {
+    if (!ctx->cublas) {
+      cublasHandle_t h;
+      XM_CUBLAS_TRY(cublasCreate(&h));
+      ctx->cublas = h;
+    }
+    if (!ctx->cusolver) {
+      cusolverDnHandle_t h;
+      XM_CUSOLVER_TRY(cusolverDnCreate(&h));
+      ctx->cusolver = h;
+    }
+    cublasHandle_t cb = static_cast<cublasHandle_t>(ctx->cublas);
+    cusolverDnHandle_t cs = static_cast<cusolverDnHandle_t>(ctx->cusolver);
+    XM_CUBLAS_TRY(cublasSetStream(cb, st));
+    XM_CUSOLVER_TRY(cusolverDnSetStream(cs, st));
+    XM_CUBLAS_TRY(cublasSetMathMode(cb, CUBLAS_DEFAULT_MATH));
+    const int m = N - 1;
+    // rows/cols 1..N-1 of S, ld N: the row-major upper triangle is the column-major lower one
+    double* Sbar = S.as<double>() + N + 1;
+    double* BbarT = B.as<double>() + 1;          // column-major (N-1) x n, ld N
+    int lwork = 0;
+    XM_CUSOLVER_TRY(cusolverDnDpotrf_bufferSize(cs, CUBLAS_FILL_MODE_LOWER, m, Sbar, N, &lwork));
+    DevBuf work, info;
+    XM_CUDA_TRY(cudaMalloc(&work.p, sizeof(double) * (size_t)(lwork > 0 ? lwork : 1)));
+    XM_CUDA_TRY(cudaMalloc(&info.p, sizeof(int)));
+    XM_CUSOLVER_TRY(cusolverDnDpotrf(cs, CUBLAS_FILL_MODE_LOWER, m, Sbar, N, work.as<double>(),
+                                     lwork, info.as<int>()));
+    int hinfo = 0;
+    XM_CUDA_TRY(cudaMemcpyAsync(&hinfo, info.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    XM_CUDA_TRY(cudaStreamSynchronize(st));
+    if (hinfo != 0)
+      return set_error(XM_EDISCONNECTED,
+                       "translation Schur block not positive definite (potrf info %d)", hinfo);
+    const double one = 1.0, minus_one = -1.0;
+    XM_CUBLAS_TRY(cublasDtrsm(cb, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N,
+                              CUBLAS_DIAG_NON_UNIT, m, n, &one, Sbar, N, BbarT, N));
+    XM_CUBLAS_TRY(cublasDsyrk(cb, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T, n, m, &minus_one, BbarT, N,
+                              &one, P.as<double>(), n));
+  }
+
+  XM_TRY(alloc_tiles(ctx, out, N, mask));
+  XM_TRY(pack_dense(ctx, out, P.as<double>()));
+  XM_CUDA_TRY(cudaStreamSynchronize(st));
+  XM_TRY(check_device_error(ctx, "Q construction"));
+  if (t_build)
+    *t_build = std::chrono::duration<double>(std::chrono::steady_clock::now() - tic).count();
+  return XM_OK;
+}
+
+}  // namespace xm

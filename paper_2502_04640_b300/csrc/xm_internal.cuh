@@ -1,0 +1,159 @@
+// Internal declarations shared by the libxm translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/xm.h"
+
+namespace xm {
+
+// ------------------------------------------------------------------ errors (host side)
+xm_status set_error(xm_status st, const char* fmt, ...);
+#define XM_CUDA_TRY(...)                                                                   \
+  do {                                                                                     \
+    cudaError_t e_ = (__VA_ARGS__);                                                        \
+    if (e_ != cudaSuccess)                                                                 \
+      return ::xm::set_error(e_ == cudaErrorMemoryAllocation ? XM_ENOMEM : XM_ECUDA,       \
+                             "%s failed: %s (%s:%d)", #__VA_ARGS__, cudaGetErrorString(e_), \
+                             __FILE__, __LINE__);                                          \
+  } while (0)
+#define XM_TRY(...)                                                                        \
+  do {                                                                                     \
+    xm_status s_ = (__VA_ARGS__);                                                          \
+    if (s_ != XM_OK) return s_;                                                            \
+  } while (0)
+
+// Device error word values (ctx->d_err); host maps them to xm_status.
+enum DevErr : int {
+  DEV_OK = 0,
+  DEV_TIMEOUT = 1,        // bounded mbarrier / flag wait gave up
+  DEV_BAD_INDEX = 2,      // observation index out of range
+  DEV_BAD_VALUE = 4,      // w <= 0 or non-finite input
+  DEV_NUMERIC = 8,        // NaN / Inf produced
+};
+
+// ------------------------------------------------------------------ Q storage
+// Packed symmetric layout: n is padded to n_pad = nt * TILE; the upper-triangle tiles (I <= J)
+// are stored one after another in row-major tile order, each tile a contiguous TILE x TILE
+// row-major block.  Off-diagonal tile (I, J) holds Q[I*T + a][J*T + b]; a diagonal tile holds
+// the upper triangle of its block with the diagonal halved and zeros below, so that every
+// tile T contributes T Y_J to W_I and T^T Y_I to W_J (the diagonal block is T + T^T).
+constexpr int TILE = 128;
+constexpr int SLAB_BYTES = 16384;   // unit of one bulk async copy
+
+__host__ __device__ inline int64_t tile_count(int nt) { return (int64_t)nt * (nt + 1) / 2; }
+__host__ __device__ inline int64_t tile_index(int nt, int I, int J) {
+  return (int64_t)I * nt - (int64_t)I * (I - 1) / 2 + (J - I);
+}
+
+struct DeviceQ {
+  int N = 0, n = 0, n_pad = 0, nt = 0;
+  int64_t ntiles = 0;
+  unsigned mask = 0;
+  double* q64 = nullptr;            // packed FP64 tiles
+  float* q32 = nullptr;             // packed FP32 tiles
+  __nv_bfloat16* q16 = nullptr;     // packed BF16 tiles
+};
+
+}  // namespace xm
+
+struct xm_qmat {
+  xm::DeviceQ d;
+  double t_build_s = 0.0;
+};
+
+struct xm_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int num_sms = 0;
+  size_t smem_optin = 0;
+  int* d_err = nullptr;           // device error word
+  int* h_err = nullptr;           // pinned mirror
+  // reduction scratch: per-block partials and a completion counter
+  double* d_partials = nullptr;
+  size_t partials_cap = 0;        // doubles
+  unsigned* d_counter = nullptr;
+  // cuBLAS / cuSOLVER handles for the dense FP64 translation Schur complement (lazy)
+  void* cublas = nullptr;
+  void* cusolver = nullptr;
+};
+
+namespace xm {
+
+xm_status check_device_error(xm_ctx* ctx, const char* where);
+extern long g_last_launches;   // kernel launches of the last solve / certify call
+extern long g_last_sweeps;
+xm_status ensure_partials(xm_ctx* ctx, size_t ndoubles);
+
+// ------------------------------------------------------------------ sweep (xm_qy.cu)
+// W = Q Y (n_pad x R, row-major, zero-initialised by the caller: the kernel accumulates).
+// skip: optional device flag; when non-zero the launch does nothing (early-exit of loops).
+xm_status qy_launch(xm_ctx* ctx, const DeviceQ& q, int prec, int R, const void* Y, void* W,
+                    const int* skip, cudaStream_t st);
+
+// ------------------------------------------------------------------ device helpers
+#ifdef __CUDACC__
+constexpr long long WAIT_LIMIT = 1ll << 24;   // try_wait polls before a wait gives up
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// Bounded wait for the completion of the phase with the given parity.  Returns false after
+// WAIT_LIMIT polls (the caller records DEV_TIMEOUT and stops waiting).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  for (long long it = 0; it < WAIT_LIMIT; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(
+                   smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// 1-D bulk async copy global -> shared, completion signalled on an mbarrier (TMA engine).
+// Both addresses 16-byte aligned, size a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src_gmem, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst_smem)),
+      "l"(src_gmem), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void named_bar_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+#endif
+
+}  // namespace xm

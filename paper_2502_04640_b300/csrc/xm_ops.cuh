@@ -1,0 +1,670 @@
+// Per-camera and vector kernels of the solver (Sec. 3.2): gradient / Hessian epilogues with
+// the closed-form dual blocks, tangent projection, polar retraction, truncated-CG updates with
+// device-resident scalars, Lanczos helpers and rounding.  Layout: every n x r quantity is an
+// n_pad x R row-major array (R = 4 or 8, unused columns zero), camera i owns rows 3i..3i+2.
+#pragma once
+#include "xm_internal.cuh"
+
+namespace xm {
+
+// Scalars of one RTR step, resident on the device (the tCG loop never waits for the host).
+struct Scal {
+  double f, g2, y2;          // objective, ||rgrad||^2, ||Y||^2 at the current point
+  double fc, gc2, yc2;       // the same at the candidate point
+  double Delta;              // trust-region radius
+  double rr, r0;             // <r, r>, ||r_0||
+  double ee, ed, dd;         // <eta,eta>, <eta,delta>, <delta,delta>
+  double kappa, alpha, beta; // curvature, step, CG coefficient
+  double theta, kappa_tol;   // residual-based stop: ||r|| <= r0 min(r0^theta, kappa_tol)
+  double g_eta, eta_Heta, eta2;  // model terms of the step
+  double dot;                // generic reduction result
+  int done, stop_after, iters, max_iters, reason, pad_;
+};
+
+constexpr int CAM_THREADS = 128;
+
+// ------------------------------------------------------------------ reductions
+// Deterministic grid reduction of K per-thread values: block sums -> partials[b*K+k]; the last
+// block to finish adds the partials in block order and thread 0 calls fin(total).
+template <int K, typename Fin>
+__device__ __forceinline__ void grid_reduce(double (&v)[K], double* partials, unsigned* counter,
+                                            Fin fin) {
+  __shared__ double sh[K][CAM_THREADS / 32];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double x = warp_sum(v[k]);
+    if (lane == 0) sh[k][wid] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      double s = 0.0;
+      for (int w = 0; w < CAM_THREADS / 32; ++w) s += sh[k][w];
+      partials[(size_t)blockIdx.x * K + k] = s;
+    }
+    __threadfence();
+    const unsigned prev = atomicAdd(counter, 1u);
+    last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (threadIdx.x == 0) {
+    double tot[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) tot[k] = 0.0;
+    for (unsigned b = 0; b < gridDim.x; ++b)
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        tot[k] += static_cast<volatile double*>(partials)[(size_t)b * K + k];
+    fin(tot);
+    *counter = 0u;
+    __threadfence();
+  }
+}
+
+// ------------------------------------------------------------------ small dense algebra
+// Cyclic Jacobi eigen-decomposition of a symmetric 3x3 matrix (Golub & Van Loan, Sec. 8.5):
+// A = V diag(d) V^T, V orthogonal (columns = eigenvectors).
+template <typename C>
+__device__ __forceinline__ void jacobi3(C (&A)[3][3], C (&V)[3][3], C (&d)[3]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) V[i][j] = (i == j) ? C(1) : C(0);
+  for (int sweep = 0; sweep < 12; ++sweep) {
+    const C off = fabs(A[0][1]) + fabs(A[0][2]) + fabs(A[1][2]);
+    const C diag = fabs(A[0][0]) + fabs(A[1][1]) + fabs(A[2][2]);
+    if (off <= C(1e-30) + diag * (sizeof(C) == 8 ? C(1e-17) : C(1e-8))) break;
+#pragma unroll
+    for (int pq = 0; pq < 3; ++pq) {
+      const int p = pq == 2 ? 1 : 0;
+      const int q = pq == 0 ? 1 : 2;
+      const C apq = A[p][q];
+      if (fabs(apq) <= C(1e-300)) continue;
+      const C tau = (A[q][q] - A[p][p]) / (C(2) * apq);
+      const C t = (tau >= C(0) ? C(1) : C(-1)) / (fabs(tau) + sqrt(C(1) + tau * tau));
+      const C c = C(1) / sqrt(C(1) + t * t), s = t * c;
+      // A <- J^T A J with J = rotation in the (p, q) plane
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const C akp = A[k][p], akq = A[k][q];
+        A[k][p] = c * akp - s * akq;
+        A[k][q] = s * akp + c * akq;
+      }
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const C apk = A[p][k], aqk = A[q][k];
+        A[p][k] = c * apk - s * aqk;
+        A[q][k] = s * apk + c * aqk;
+      }
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const C vkp = V[k][p], vkq = V[k][q];
+        V[k][p] = c * vkp - s * vkq;
+        V[k][q] = s * vkp + c * vkq;
+      }
+    }
+  }
+  d[0] = A[0][0]; d[1] = A[1][1]; d[2] = A[2][2];
+}
+
+template <typename C>
+__device__ __forceinline__ C det3(const C (&A)[3][3]) {
+  return A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) -
+         A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
+         A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+}
+
+// Closed-form dual block (Thm. 1 / App. C): Lambda = P_i(sym(X Y^T)) / alpha with
+// alpha = ||Y||_F^2 / 3; P_i removes the trace except on the anchor (i = 0).
+template <typename C, int R>
+__device__ __forceinline__ void dual_block(const C (&X)[3][R], const C (&Y)[3][R], bool anchor,
+                                          C (&L)[3][3], C& alpha) {
+  C y2 = C(0);
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int j = 0; j < R; ++j) y2 += Y[a][j] * Y[a][j];
+  alpha = y2 / C(3);
+  C M[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      C s = C(0);
+#pragma unroll
+      for (int j = 0; j < R; ++j) s += X[a][j] * Y[b][j];
+      M[a][b] = s;
+    }
+  const C tr3 = anchor ? C(0) : (M[0][0] + M[1][1] + M[2][2]) / C(3);
+  const C inv = alpha > C(0) ? C(1) / alpha : C(0);
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+      L[a][b] = (C(0.5) * (M[a][b] + M[b][a]) - (a == b ? tr3 : C(0))) * inv;
+}
+
+template <typename T, typename C, int R>
+__device__ __forceinline__ void load_block(const T* p, int i, C (&X)[3][R]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int j = 0; j < R; ++j) X[a][j] = C(p[(size_t)(3 * i + a) * R + j]);
+}
+template <typename T, typename C, int R>
+__device__ __forceinline__ void store_block(T* p, int i, const C (&X)[3][R]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int j = 0; j < R; ++j) p[(size_t)(3 * i + a) * R + j] = T(X[a][j]);
+}
+template <typename T, int R>
+__device__ __forceinline__ void zero_block(T* p, int i) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int j = 0; j < R; ++j) p[(size_t)(3 * i + a) * R + j] = T(0);
+}
+
+// ------------------------------------------------------------------ gradient epilogue
+// From W = Q Y: Lambda_i, rgrad_i = 2 (W_i - Lambda_i Y_i), f = <Y, W>, ||rgrad||^2, ||Y||^2.
+// W is reset to zero for the next accumulating sweep.  Results go to (sc->f, g2, y2) or, with
+// cand = 1, to (sc->fc, gc2, yc2).
+template <typename T, int R>
+__global__ void __launch_bounds__(CAM_THREADS)
+k_grad_epi(int N, const T* __restrict__ Y, T* __restrict__ W, T* __restrict__ G,
+           double* __restrict__ Lam, Scal* sc, int cand, double* partials, unsigned* counter,
+           int* err) {
+  using C = T;
+  double v[3] = {0.0, 0.0, 0.0};
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) {
+    C y[3][R], w[3][R], L[3][3], alpha;
+    load_block<T, C, R>(Y, i, y);
+    load_block<T, C, R>(W, i, w);
+    zero_block<T, R>(W, i);
+    dual_block<C, R>(w, y, i == 0, L, alpha);
+    C g[3][R];
+    double fi = 0.0, gi = 0.0, yi = 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        C ly = L[a][0] * y[0][j] + L[a][1] * y[1][j] + L[a][2] * y[2][j];
+        g[a][j] = C(2) * (w[a][j] - ly);
+        fi += double(y[a][j]) * double(w[a][j]);
+        gi += double(g[a][j]) * double(g[a][j]);
+        yi += double(y[a][j]) * double(y[a][j]);
+      }
+    store_block<T, C, R>(G, i, g);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) Lam[(size_t)9 * i + 3 * a + b] = double(L[a][b]);
+    v[0] = fi; v[1] = gi; v[2] = yi;
+  }
+  grid_reduce<3>(v, partials, counter, [&](double* t) {
+    if (!isfinite(t[0]) || !isfinite(t[1])) atomicOr(err, DEV_NUMERIC);
+    if (cand) { sc->fc = t[0]; sc->gc2 = t[1]; sc->yc2 = t[2]; }
+    else { sc->f = t[0]; sc->g2 = t[1]; sc->y2 = t[2]; }
+  });
+}
+
+// ------------------------------------------------------------------ truncated CG
+// Steihaug-Toint tCG (Absil et al. 2008, Alg. 11) on the model with Hessian 2 P_Y(Q d - Lambda d).
+template <typename To, typename Ti, int R>
+__global__ void __launch_bounds__(CAM_THREADS)
+k_tcg_init(int n_rows, const To* __restrict__ G, Ti* eta, Ti* Heta, Ti* r, Ti* delta, Scal* sc,
+           double Delta, int max_iters, double theta, double kappa_tol) {
+  const size_t total = (size_t)n_rows * R;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const Ti g = Ti(G[e]);
+    eta[e] = Ti(0); Heta[e] = Ti(0); r[e] = g; delta[e] = -g;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    sc->Delta = Delta;
+    sc->rr = sc->g2;
+    sc->r0 = sqrt(sc->g2);
+    sc->ee = 0.0; sc->ed = 0.0; sc->dd = sc->g2;
+    sc->done = sc->g2 > 0.0 ? 0 : 1;
+    sc->stop_after = 0; sc->iters = 0; sc->max_iters = max_iters; sc->reason = 0;
+    sc->theta = theta; sc->kappa_tol = kappa_tol;
+  }
+}
+
+// Hd = 2 P_Y(Wd - Lambda d); kappa = <d, Hd>; then decide the step (alpha, or tau to the
+// trust-region boundary on negative curvature / when the CG step leaves the region).
+template <typename T, int R>
+__global__ void __launch_bounds__(CAM_THREADS)
+k_hvp_epi(int N, const T* __restrict__ Y, T* __restrict__ Wd, const T* __restrict__ delta,
+          T* __restrict__ Hd, const double* __restrict__ Lam, Scal* sc, double* partials,
+          unsigned* counter) {
+  if (sc->done) return;
+  using C = T;
+  double v[1] = {0.0};
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) {
+    C y[3][R], w[3][R], d[3][R], L[3][3];
+    load_block<T, C, R>(Y, i, y);
+    load_block<T, C, R>(Wd, i, w);
+    zero_block<T, R>(Wd, i);
+    load_block<T, C, R>(delta, i, d);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) L[a][b] = C(Lam[(size_t)9 * i + 3 * a + b]);
+    C A[3][R];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int j = 0; j < R; ++j)
+        A[a][j] = C(2) * (w[a][j] - (L[a][0] * d[0][j] + L[a][1] * d[1][j] + L[a][2] * d[2][j]));
+    C S[3][3], alpha;
+    dual_block<C, R>(A, y, i == 0, S, alpha);
+    double kap = 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        A[a][j] -= S[a][0] * y[0][j] + S[a][1] * y[1][j] + S[a][2] * y[2][j];
+        kap += double(d[a][j]) * double(A[a][j]);
+      }
+    store_block<T, C, R>(Hd, i, A);
+    v[0] = kap;
+  }
+  grid_reduce<1>(v, partials, counter, [&](double* t) {
+    const double kap = t[0];
+    sc->kappa = kap;
+    const double D2 = sc->Delta * sc->Delta;
+    const double a = kap > 0.0 ? sc->rr / kap : 0.0;
+    if (!(kap > 0.0) || sc->ee + 2.0 * a * sc->ed + a * a * sc->dd >= D2) {
+      const double disc = sc->ed * sc->ed + sc->dd * (D2 - sc->ee);
+      sc->alpha = (-sc->ed + sqrt(disc > 0.0 ? disc : 0.0)) / sc->dd;
+      sc->stop_after = 1;
+      sc->reason = kap > 0.0 ? 2 : 1;
+    } else {
+      sc->alpha = a;
+    }
+  });
+}
+
+// eta += alpha d, Heta += alpha Hd, r += alpha Hd (re-projected); residual test, beta.
+template <typename T, int R>
+__global__ void __launch_bounds__(CAM_THREADS)
+k_tcg_update(int N, const T* __restrict__ Y, T* eta, T* Heta, T* r, const T* __restrict__ delta,
+             const T* __restrict__ Hd, Scal* sc, double* partials, unsigned* counter) {
+  if (sc->done) return;
+  using C = T;
+  const C alpha = C(sc->alpha);
+  const bool stop = sc->stop_after != 0;
+  double v[1] = {0.0};
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) {
+    C e[3][R], he[3][R], d[3][R], hd[3][R];
+    load_block<T, C, R>(eta, i, e);
+    load_block<T, C, R>(Heta, i, he);
+    load_block<T, C, R>(delta, i, d);
+    load_block<T, C, R>(Hd, i, hd);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        e[a][j] += alpha * d[a][j];
+        he[a][j] += alpha * hd[a][j];
+      }
+    store_block<T, C, R>(eta, i, e);
+    store_block<T, C, R>(Heta, i, he);
+    if (!stop) {
+      C rr[3][R], y[3][R];
+      load_block<T, C, R>(r, i, rr);
+      load_block<T, C, R>(Y, i, y);
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int j = 0; j < R; ++j) rr[a][j] += alpha * hd[a][j];
+      C S[3][3], al;
+      dual_block<C, R>(rr, y, i == 0, S, al);   // re-project r onto the tangent space
+      double s = 0.0;
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+          rr[a][j] -= S[a][0] * y[0][j] + S[a][1] * y[1][j] + S[a][2] * y[2][j];
+          s += double(rr[a][j]) * double(rr[a][j]);
+        }
+      store_block<T, C, R>(r, i, rr);
+      v[0] = s;
+    }
+  }
+  grid_reduce<1>(v, partials, counter, [&](double* t) {
+    sc->iters += 1;
+    if (stop) { sc->done = 1; return; }
+    const double rr_new = t[0];
+    const double rn = sqrt(rr_new);
+    const double thr = sc->r0 * fmin(pow(sc->r0, sc->theta), sc->kappa_tol);
+    if (rn <= thr) { sc->done = 1; sc->reason = 3; return; }
+    if (sc->iters >= sc->max_iters) { sc->done = 1; sc->reason = 4; return; }
+    sc->beta = rr_new / sc->rr;
+    sc->rr = rr_new;
+  });
+}
+
+// d = -r + beta d; recompute <eta,eta>, <eta,d>, <d,d>.
+template <typename T, int R>
+__global__ void __launch_bounds__(CAM_THREADS)
+k_tcg_dir(int N, const T* __restrict__ eta, const T* __restrict__ r, T* delta, Scal* sc,
+          double* partials, unsigned* counter) {
+  if (sc->done) return;
+  using C = T;
+  const C beta = C(sc->beta);
+  double v[3] = {0.0, 0.0, 0.0};
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) {
+    C e[3][R], rr[3][R], d[3][R];
+    load_block<T, C, R>(eta, i, e);
+    load_block<T, C, R>(r, i, rr);
+    load_block<T, C, R>(delta, i, d);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        d[a][j] = -rr[a][j] + beta * d[a][j];
+        v[0] += double(e[a][j]) * double(e[a][j]);
+        v[1] += double(e[a][j]) * double(d[a][j]);
+        v[2] += double(d[a][j]) * double(d[a][j]);
+      }
+    store_block<T, C, R>(delta, i, d);
+  }
+  grid_reduce<3>(v, partials, counter, [&](double* t) {
+    sc->ee = t[0]; sc->ed = t[1]; sc->dd = t[2];
+  });
+}
+
+// model terms <grad, eta>, <eta, Heta>, ||eta||^2 after tCG
+template <typename To, typename Ti, int R>
+__global__ void __launch_bounds__(CAM_THREADS)
+k_model_terms(int n_rows, const To* __restrict__ G, const Ti* __restrict__ eta,
+              const Ti* __restrict__ Heta, Scal* sc, double* partials, unsigned* counter) {
+  double v[3] = {0.0, 0.0, 0.0};
+  const size_t total = (size_t)n_rows * R;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const double g = double(G[e]), x = double(eta[e]), h = double(Heta[e]);
+    v[0] += g * x; v[1] += x * h; v[2] += x * x;
+  }
+  grid_reduce<3>(v, partials, counter, [&](double* t) {
+    sc->g_eta = t[0]; sc->eta_Heta = t[1]; sc->eta2 = t[2];
+  });
+}
+
+// ------------------------------------------------------------------ retraction
+// Metric projection onto {sqrt(a) * (3 x r with orthonormal rows)}: A = Y_i + s Xi_i,
+// polar(A) = (A A^T)^{-1/2} A, scale = (sum of singular values) / 3 (anchor: 1).
+template <typename To, typename Ti, int R>
+__global__ void __launch_bounds__(CAM_THREADS)
+k_retract(int N, const To* __restrict__ Y, const Ti* __restrict__ Xi, double s, To* __restrict__ Yo) {
+  using C = To;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  C A[3][R];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int j = 0; j < R; ++j)
+      A[a][j] = C(Y[(size_t)(3 * i + a) * R + j]) + C(s) * C(Xi[(size_t)(3 * i + a) * R + j]);
+  C M[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      C t = C(0);
+#pragma unroll
+      for (int j = 0; j < R; ++j) t += A[a][j] * A[b][j];
+      M[a][b] = t;
+    }
+  C V[3][3], d[3];
+  jacobi3<C>(M, V, d);
+  C sq[3], isq[3];
+  C ssum = C(0);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const C dk = d[k] > C(1e-300) ? d[k] : C(1e-300);
+    sq[k] = sqrt(dk);
+    isq[k] = C(1) / sq[k];
+    ssum += sq[k];
+  }
+  const C scale = i == 0 ? C(1) : ssum / C(3);
+  C P[3][3];   // scale * V diag(1/sqrt d) V^T
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+      P[a][b] = scale * (V[a][0] * isq[0] * V[b][0] + V[a][1] * isq[1] * V[b][1] +
+                         V[a][2] * isq[2] * V[b][2]);
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int j = 0; j < R; ++j)
+      Yo[(size_t)(3 * i + a) * R + j] = To(P[a][0] * A[0][j] + P[a][1] * A[1][j] + P[a][2] * A[2][j]);
+}
+
+// ------------------------------------------------------------------ element-wise helpers
+template <typename Ts, typename Td>
+__global__ void k_cast(size_t total, const Ts* __restrict__ s, Td* __restrict__ d) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x)
+    d[e] = Td(s[e]);
+}
+
+// copy an n x rs row-major array into an n_rows x Rd padded one (zero fill), any types
+template <typename Ts, typename Td>
+__global__ void k_repad(int n, int n_rows, const Ts* __restrict__ s, int rs, Td* __restrict__ d,
+                        int Rd) {
+  const size_t total = (size_t)n_rows * Rd;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int row = (int)(e / Rd), col = (int)(e % Rd);
+    d[e] = (row < n && col < rs) ? Td(s[(size_t)row * rs + col]) : Td(0);
+  }
+}
+
+// Y <- Y Rot (R x R matrix in device memory), rows independent
+template <int R>
+__global__ void k_rotate(int n_rows, double* Y, const double* __restrict__ Rot) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= n_rows) return;
+  double y[R], o[R];
+#pragma unroll
+  for (int j = 0; j < R; ++j) y[j] = Y[(size_t)row * R + j];
+#pragma unroll
+  for (int j = 0; j < R; ++j) {
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < R; ++k) s += y[k] * Rot[k * R + j];
+    o[j] = s;
+  }
+#pragma unroll
+  for (int j = 0; j < R; ++j) Y[(size_t)row * R + j] = o[j];
+}
+
+// G = Y^T Y (R x R), deterministic
+template <typename T, int R>
+__global__ void __launch_bounds__(CAM_THREADS)
+k_gram(int n_rows, const T* __restrict__ Y, double* out, double* partials, unsigned* counter) {
+  double v[R * R];
+#pragma unroll
+  for (int k = 0; k < R * R; ++k) v[k] = 0.0;
+  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < n_rows;
+       row += gridDim.x * blockDim.x) {
+    double y[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) y[j] = double(Y[(size_t)row * R + j]);
+#pragma unroll
+    for (int a = 0; a < R; ++a)
+#pragma unroll
+      for (int b = 0; b < R; ++b) v[a * R + b] += y[a] * y[b];
+  }
+  grid_reduce<R * R>(v, partials, counter, [&](double* t) {
+    for (int k = 0; k < R * R; ++k) out[k] = t[k];
+  });
+}
+
+// <a, b> over total elements (mixed types) -> *out
+template <typename Ta, typename Tb>
+__global__ void __launch_bounds__(CAM_THREADS)
+k_dot(size_t total, const Ta* __restrict__ a, const Tb* __restrict__ b, double* out,
+      double* partials, unsigned* counter) {
+  double v[1] = {0.0};
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x)
+    v[0] += double(a[e]) * double(b[e]);
+  grid_reduce<1>(v, partials, counter, [&](double* t) { *out = t[0]; });
+}
+
+// ------------------------------------------------------------------ Lanczos (FP64 vectors)
+// w_i = Wz_i - Lambda_i v_i (Z v with Z = Q - blockdiag(Lambda)); Wz reset to zero.
+template <typename Tw>
+__global__ void k_zv_epi(int N, Tw* __restrict__ Wz, const double* __restrict__ v,
+                         const double* __restrict__ Lam, double* __restrict__ w) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double x[3] = {v[3 * i], v[3 * i + 1], v[3 * i + 2]};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const double lx = Lam[9 * i + 3 * a] * x[0] + Lam[9 * i + 3 * a + 1] * x[1] +
+                      Lam[9 * i + 3 * a + 2] * x[2];
+    w[3 * i + a] = double(Wz[3 * i + a]) - lx;
+    Wz[3 * i + a] = Tw(0);
+  }
+}
+
+// c[j] = <V_j, w> for the m columns of V (column-major, stride ld); one block per column
+__global__ void k_gemv_t(int n, int m, const double* __restrict__ V, size_t ld,
+                         const double* __restrict__ w, double* __restrict__ c) {
+  __shared__ double sh[8];
+  for (int j = blockIdx.x; j < m; j += gridDim.x) {
+    double s = 0.0;
+    const double* col = V + (size_t)j * ld;
+    for (int e = threadIdx.x; e < n; e += blockDim.x) s += col[e] * w[e];
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += sh[k];
+      c[j] = t;
+    }
+    __syncthreads();
+  }
+}
+
+// w -= V c (m columns)
+__global__ void k_gemv_n_sub(int n, int m, const double* __restrict__ V, size_t ld,
+                             const double* __restrict__ c, double* __restrict__ w) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int j = 0; j < m; ++j) s += V[(size_t)j * ld + e] * c[j];
+    w[e] -= s;
+  }
+}
+
+// w -= a[k] v_k + b[k-1] v_{k-1}  (coefficients read on the device)
+__global__ void k_lanczos_3term(int n, double* __restrict__ w, const double* __restrict__ vk,
+                                const double* __restrict__ vkm1, const double* alpha,
+                                const double* beta, int k) {
+  const double a = alpha[k];
+  const double b = (k > 0 && vkm1) ? beta[k - 1] : 0.0;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x)
+    w[e] -= a * vk[e] + (b != 0.0 ? b * vkm1[e] : 0.0);
+}
+
+// dst = w / sqrt(*nrm2); *beta_out = sqrt(*nrm2)
+__global__ void k_normalize(int n, const double* __restrict__ w, const double* nrm2,
+                            double* __restrict__ dst, double* beta_out) {
+  const double b = sqrt(*nrm2);
+  const double inv = b > 0.0 ? 1.0 / b : 0.0;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x)
+    dst[e] = w[e] * inv;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && beta_out) *beta_out = b;
+}
+
+// deterministic pseudo-random start vector (splitmix64 of (seed, index)), uniform in [-1, 1)
+__global__ void k_random_vec(int n, uint64_t seed, double* v) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    uint64_t z = seed + 0x9E3779B97F4A7C15ull * (uint64_t)(e + 1);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    v[e] = (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+  }
+}
+
+// ------------------------------------------------------------------ rounding (Sec. 2.2)
+// Per camera: Ubar_i = Yh_i^T (3 x 3), G_i = O0^T Ubar_i, s_i = ||G_i||_F / sqrt(3),
+// R_i = SO(3) projection of G_i (SVD with determinant fix, Prop. 2); the anchor is (I, 1).
+// Writes R (N x 9, row-major), s (N) and Yhat = [s_i R_i]^T (n_rows x 4, last column zero).
+__global__ void k_round(int N, const double* __restrict__ Yh, const double* __restrict__ O0,
+                        double* __restrict__ Rout, double* __restrict__ sout,
+                        double* __restrict__ Yhat) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double Rm[3][3], s;
+  if (i == 0) {
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) Rm[a][b] = a == b ? 1.0 : 0.0;
+    s = 1.0;
+  } else {
+    double Ub[3][3], G[3][3];
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) Ub[a][b] = Yh[(size_t)(3 * i + b) * 4 + a];   // Yh_i^T
+    double fro = 0.0;
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        double t = 0.0;
+        for (int k = 0; k < 3; ++k) t += O0[3 * k + a] * Ub[k][b];
+        G[a][b] = t;
+        fro += t * t;
+      }
+    s = sqrt(fro / 3.0);
+    // SVD via the eigen-decomposition of G^T G = V diag(sig^2) V^T, U = G V diag(1/sig)
+    double M[3][3], V[3][3], d[3];
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        double t = 0.0;
+        for (int k = 0; k < 3; ++k) t += G[k][a] * G[k][b];
+        M[a][b] = t;
+      }
+    jacobi3<double>(M, V, d);
+    double U[3][3];
+    for (int k = 0; k < 3; ++k) {
+      const double sig = sqrt(d[k] > 1e-300 ? d[k] : 1e-300);
+      for (int a = 0; a < 3; ++a)
+        U[a][k] = (G[a][0] * V[0][k] + G[a][1] * V[1][k] + G[a][2] * V[2][k]) / sig;
+    }
+    // the smallest singular direction takes the sign that makes det(R) = +1
+    int kmin = 0;
+    for (int k = 1; k < 3; ++k) if (d[k] < d[kmin]) kmin = k;
+    const double sgn = det3<double>(U) * det3<double>(V) < 0.0 ? -1.0 : 1.0;
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        double t = 0.0;
+        for (int k = 0; k < 3; ++k) t += U[a][k] * (k == kmin ? sgn : 1.0) * V[b][k];
+        Rm[a][b] = t;
+      }
+  }
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      Rout[(size_t)9 * i + 3 * a + b] = Rm[a][b];
+      Yhat[(size_t)(3 * i + b) * 4 + a] = s * Rm[a][b];
+    }
+  for (int b = 0; b < 3; ++b) Yhat[(size_t)(3 * i + b) * 4 + 3] = 0.0;
+  sout[i] = s;
+}
+
+}  // namespace xm

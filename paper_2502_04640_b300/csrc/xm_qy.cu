@@ -1,0 +1,330 @@
+// Q.Y sweep on the packed symmetric tile layout (the Euclidean Hessian-vector product of
+// Sec. 3.2: "matrix-vector multiplication"; one sweep also gives the gradient 2QY and the
+// objective tr(Y^T Q Y) of Eq. 17).
+//
+// B300 design: Q is dense (a Schur complement through the inverse of a connected Laplacian,
+// App. A), so each unique entry must be read once per sweep and the kernel is HBM-bound for
+// FP32/BF16 storage.  Storing only the upper-triangle tiles halves the bytes; every tile is
+// then used twice, T Y_J -> W_I (row contribution) and T^T Y_I -> W_J (column contribution).
+//   * persistent grid, one CTA per SM, contiguous ranges of the tile list per CTA;
+//   * one producer thread streams 16 KB slabs with cp.async.bulk (TMA engine) into a ring of
+//     mbarrier-guarded stages (bounded waits: a stall sets DEV_TIMEOUT, no wait is endless);
+//   * NW consumer warps: lane l owns columns 4l..4l+3 of the tile, keeps Y_J for them in
+//     registers and accumulates the column contribution; the row contribution of each slab
+//     row is reduced across lanes with a transpose-reduce butterfly and accumulated per
+//     tile row in registers;
+//   * column partials are combined across warps in shared memory and added to W_J with one
+//     atomic per output; row partials are added to W_I when the tile row changes.
+#include "xm_internal.cuh"
+
+namespace xm {
+
+template <typename TQ> struct QT;
+template <> struct QT<float> {
+  using A = float;
+  static constexpr int ROWS = SLAB_BYTES / (TILE * 4);   // 32 rows per slab
+};
+template <> struct QT<__nv_bfloat16> {
+  using A = float;
+  static constexpr int ROWS = SLAB_BYTES / (TILE * 2);   // 64
+};
+template <> struct QT<double> {
+  using A = double;
+  static constexpr int ROWS = SLAB_BYTES / (TILE * 8);   // 16
+};
+
+// four consecutive stored Q values of a slab row -> accumulation type
+__device__ __forceinline__ void load4(const float* p, float (&q)[4]) {
+  float4 v = *reinterpret_cast<const float4*>(p);
+  q[0] = v.x; q[1] = v.y; q[2] = v.z; q[3] = v.w;
+}
+__device__ __forceinline__ void load4(const __nv_bfloat16* p, float (&q)[4]) {
+  uint2 v = *reinterpret_cast<const uint2*>(p);
+  q[0] = __uint_as_float(v.x << 16);
+  q[1] = __uint_as_float(v.x & 0xffff0000u);
+  q[2] = __uint_as_float(v.y << 16);
+  q[3] = __uint_as_float(v.y & 0xffff0000u);
+}
+__device__ __forceinline__ void load4(const double* p, double (&q)[4]) {
+  double2 a = *reinterpret_cast<const double2*>(p);
+  double2 b = *reinterpret_cast<const double2*>(p + 2);
+  q[0] = a.x; q[1] = a.y; q[2] = b.x; q[3] = b.y;
+}
+
+// Butterfly transpose-reduce of V <= 32 per-lane values: afterwards lane l holds the
+// warp-wide sum of value index l * V / 32 (lanes sharing that index hold the same sum).
+template <int V, typename T>
+__device__ __forceinline__ T transpose_reduce(T (&v)[V], int lane) {
+  static_assert(V >= 1 && V <= 32 && (V & (V - 1)) == 0, "V must be a power of two <= 32");
+  int o = 16;
+#pragma unroll
+  for (int h = V / 2; h >= 1; h >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      const T send = up ? v[i] : v[i + h];
+      const T keep = up ? v[i + h] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+    o >>= 1;
+  }
+  T x = v[0];
+#pragma unroll
+  for (; o >= 1; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+template <typename TQ, int R, int NW>
+struct SweepCfg {
+  using A = typename QT<TQ>::A;
+  static constexpr int ROWS = QT<TQ>::ROWS;           // rows per slab
+  static constexpr int SLABS = TILE / ROWS;           // slabs per tile
+  static constexpr int RPW = ROWS / NW;               // slab rows per consumer warp
+  static_assert(RPW >= 1 && RPW * NW == ROWS, "slab rows must split evenly over warps");
+  static constexpr int CHUNK = (RPW * R <= 32) ? RPW : (32 / R);   // rows per butterfly
+  static constexpr int NCHUNK = RPW / CHUNK;
+  static constexpr int V = CHUNK * R;
+  static constexpr int THREADS = 32 * (NW + 1);
+  static constexpr size_t YSM_BYTES = sizeof(A) * TILE * R;
+  static constexpr size_t RED_BYTES = sizeof(A) * NW * TILE * R;
+  static size_t smem_bytes(int nstage) {
+    return 128 + (size_t)nstage * SLAB_BYTES + YSM_BYTES + RED_BYTES + 16 * (size_t)nstage;
+  }
+};
+
+template <typename TQ, int R, int NW>
+__global__ void __launch_bounds__(SweepCfg<TQ, R, NW>::THREADS, 1)
+qy_packed_kernel(const TQ* __restrict__ tiles, int nt, int64_t ntiles, int nstage,
+                 const typename QT<TQ>::A* __restrict__ Y, typename QT<TQ>::A* __restrict__ W,
+                 int* err, const int* skip) {
+  using C = SweepCfg<TQ, R, NW>;
+  using A = typename C::A;
+  if (skip != nullptr && *skip != 0) return;
+
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  unsigned char* stages = base;
+  A* ysm = reinterpret_cast<A*>(stages + (size_t)nstage * SLAB_BYTES);
+  A* red = reinterpret_cast<A*>(reinterpret_cast<unsigned char*>(ysm) + C::YSM_BYTES);
+  uint64_t* full = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(red) + C::RED_BYTES);
+  uint64_t* empty = full + nstage;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t t0 = ntiles * blockIdx.x / gridDim.x;
+  const int64_t t1 = ntiles * (blockIdx.x + 1) / gridDim.x;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < nstage; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], NW);
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (t0 >= t1) return;
+
+  // first tile coordinates of this CTA's range
+  int I0 = 0;
+  {
+    int64_t rem = t0;
+    while (rem >= nt - I0) { rem -= nt - I0; ++I0; }
+  }
+  const int J0 = I0 + (int)(t0 - tile_index(nt, I0, I0));
+
+  if (warp == NW) {
+    // ---------------- producer: one thread streams the slabs of [t0, t1)
+    if (lane == 0) {
+      const unsigned char* src = reinterpret_cast<const unsigned char*>(tiles) +
+                                 (size_t)t0 * C::SLABS * SLAB_BYTES;
+      const int64_t nslab = (t1 - t0) * C::SLABS;
+      int stage = 0;
+      uint32_t phase = 0;
+      int64_t issued = 0;
+      for (; issued < nslab; ++issued) {
+        if (!mbar_wait(&empty[stage], phase ^ 1u)) { atomicOr(err, DEV_TIMEOUT); break; }
+        mbar_arrive_expect_tx(&full[stage], SLAB_BYTES);
+        bulk_g2s(stages + (size_t)stage * SLAB_BYTES, src + (size_t)issued * SLAB_BYTES,
+                 SLAB_BYTES, &full[stage]);
+        if (++stage == nstage) { stage = 0; phase ^= 1u; }
+      }
+      // Drain: do not leave while copies into this CTA's shared memory are in flight.
+      const int64_t first = issued > nstage ? issued - nstage : 0;
+      for (int64_t k = first; k < issued; ++k) {
+        const int s = (int)(k % nstage);
+        const uint32_t ph = (uint32_t)((k / nstage) & 1);
+        if (!mbar_wait(&full[s], ph)) { atomicOr(err, DEV_TIMEOUT); break; }
+      }
+    }
+    return;
+  }
+
+  // ---------------- consumers
+  const int ctid = threadIdx.x;            // 0 .. 32*NW-1
+  constexpr int NCT = 32 * NW;
+  A yj[4][R];
+  A colacc[4][R];
+  A rowacc[C::SLABS][C::NCHUNK];
+  int curI = -1;
+  int I = I0, J = J0;
+  int stage = 0;
+  uint32_t phase = 0;
+  bool ok = true;
+
+  auto flush_rows = [&](int Irow) {
+    constexpr int DUP = 32 / C::V;         // lanes sharing one butterfly result
+    if ((lane & (DUP - 1)) == 0) {
+      const int idx = lane / DUP;           // value index within a chunk
+      const int k = idx / R, j = idx % R;
+#pragma unroll
+      for (int s = 0; s < C::SLABS; ++s)
+#pragma unroll
+        for (int c = 0; c < C::NCHUNK; ++c) {
+          const int row = s * C::ROWS + warp * C::RPW + c * C::CHUNK + k;
+          atomicAdd(&W[((size_t)Irow * TILE + row) * R + j], rowacc[s][c]);
+        }
+    }
+  };
+
+  // Every consumer warp runs the same sequence of named barriers whatever happens: a wait that
+  // gives up only marks the warp as failed (no further waits, no work), so no barrier can hang.
+  for (int64_t t = t0; t < t1; ++t) {
+    if (I != curI) {
+      if (curI >= 0) flush_rows(curI);
+      named_bar_sync(1, NCT);
+      for (int e = ctid; e < TILE * R; e += NCT) ysm[e] = Y[(size_t)I * TILE * R + e];
+      named_bar_sync(1, NCT);
+#pragma unroll
+      for (int s = 0; s < C::SLABS; ++s)
+#pragma unroll
+        for (int c = 0; c < C::NCHUNK; ++c) rowacc[s][c] = A(0);
+      curI = I;
+    }
+    {
+      const A* yp = Y + ((size_t)J * TILE + 4 * lane) * R;
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int j = 0; j < R; ++j) { yj[c][j] = yp[c * R + j]; colacc[c][j] = A(0); }
+    }
+#pragma unroll
+    for (int s = 0; s < C::SLABS; ++s) {
+      if (ok && !mbar_wait(&full[stage], phase)) { atomicOr(err, DEV_TIMEOUT); ok = false; }
+      const TQ* slab = reinterpret_cast<const TQ*>(stages + (size_t)stage * SLAB_BYTES);
+      A q[C::RPW][4];
+#pragma unroll
+      for (int k = 0; k < C::RPW; ++k) {
+        if (ok) load4(slab + (size_t)(warp * C::RPW + k) * TILE + 4 * lane, q[k]);
+        else q[k][0] = q[k][1] = q[k][2] = q[k][3] = A(0);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[stage]);
+      if (++stage == nstage) { stage = 0; phase ^= 1u; }
+      const int rbase = s * C::ROWS + warp * C::RPW;
+#pragma unroll
+      for (int k = 0; k < C::RPW; ++k) {
+        A yi[R];
+#pragma unroll
+        for (int j = 0; j < R; ++j) yi[j] = ysm[(rbase + k) * R + j];
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+          for (int j = 0; j < R; ++j) colacc[c][j] = fma(q[k][c], yi[j], colacc[c][j]);
+      }
+#pragma unroll
+      for (int ch = 0; ch < C::NCHUNK; ++ch) {
+        A v[C::V];
+#pragma unroll
+        for (int kk = 0; kk < C::CHUNK; ++kk) {
+          const int k = ch * C::CHUNK + kk;
+#pragma unroll
+          for (int j = 0; j < R; ++j) {
+            A acc = q[k][0] * yj[0][j];
+            acc = fma(q[k][1], yj[1][j], acc);
+            acc = fma(q[k][2], yj[2][j], acc);
+            acc = fma(q[k][3], yj[3][j], acc);
+            v[kk * R + j] = acc;
+          }
+        }
+        rowacc[s][ch] += transpose_reduce<C::V>(v, lane);
+      }
+    }
+    // column contribution: combine the NW warps' partials, then one atomic per output
+    {
+      A* mine = red + (size_t)warp * TILE * R;
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int j = 0; j < R; ++j) mine[(4 * lane + c) * R + j] = colacc[c][j];
+      named_bar_sync(1, NCT);
+      for (int o = ctid; o < TILE * R; o += NCT) {
+        A sum = A(0);
+#pragma unroll
+        for (int w = 0; w < NW; ++w) sum += red[(size_t)w * TILE * R + o];
+        atomicAdd(&W[(size_t)J * TILE * R + o], sum);
+      }
+      named_bar_sync(1, NCT);
+    }
+    if (++J == nt) { ++I; J = I; }
+  }
+  if (curI >= 0) flush_rows(curI);
+}
+
+// ------------------------------------------------------------------ host launcher
+template <typename TQ, int R, int NW>
+static xm_status launch_t(xm_ctx* ctx, const TQ* tiles, const DeviceQ& q, const void* Y, void* W,
+                          const int* skip, cudaStream_t st) {
+  using C = SweepCfg<TQ, R, NW>;
+  using A = typename C::A;
+  static int configured_dev = -1;
+  static int nstage_cfg = 0;
+  if (configured_dev != ctx->device) {
+    const size_t fixed = C::smem_bytes(0);
+    int ns = (int)((ctx->smem_optin - fixed) / (SLAB_BYTES + 16));
+    if (ns > 12) ns = 12;
+    if (ns < 2) return set_error(XM_ECUDA, "sweep: not enough shared memory (%zu)", ctx->smem_optin);
+    XM_CUDA_TRY(cudaFuncSetAttribute(qy_packed_kernel<TQ, R, NW>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)C::smem_bytes(ns)));
+    nstage_cfg = ns;
+    configured_dev = ctx->device;
+  }
+  int grid = ctx->num_sms;
+  if ((int64_t)grid > q.ntiles) grid = (int)q.ntiles;
+  qy_packed_kernel<TQ, R, NW><<<grid, C::THREADS, C::smem_bytes(nstage_cfg), st>>>(
+      tiles, q.nt, q.ntiles, nstage_cfg, static_cast<const A*>(Y), static_cast<A*>(W),
+      ctx->d_err, skip);
+  XM_CUDA_TRY(cudaGetLastError());
+  return XM_OK;
+}
+
+template <typename TQ, int NW>
+static xm_status dispatch_r(xm_ctx* ctx, const TQ* tiles, const DeviceQ& q, int R, const void* Y,
+                            void* W, const int* skip, cudaStream_t st) {
+  switch (R) {
+    case 1: return launch_t<TQ, 1, NW>(ctx, tiles, q, Y, W, skip, st);
+    case 4: return launch_t<TQ, 4, NW>(ctx, tiles, q, Y, W, skip, st);
+    case 8: return launch_t<TQ, 8, NW>(ctx, tiles, q, Y, W, skip, st);
+    default: return set_error(XM_EINVAL, "sweep: padded width %d not in {1,4,8}", R);
+  }
+}
+
+xm_status qy_launch(xm_ctx* ctx, const DeviceQ& q, int prec, int R, const void* Y, void* W,
+                    const int* skip, cudaStream_t st) {
+  if (q.ntiles == 0) return XM_OK;
+  switch (prec) {
+    case XM_FP64:
+      if (!q.q64) return set_error(XM_EINVAL, "sweep: Q has no FP64 copy");
+      return dispatch_r<double, 8>(ctx, q.q64, q, R, Y, W, skip, st);
+    case XM_FP32_BULK:
+      if (!q.q32) return set_error(XM_EINVAL, "sweep: Q has no FP32 copy");
+      return dispatch_r<float, 8>(ctx, q.q32, q, R, Y, W, skip, st);
+    case XM_BF16Q_BULK:
+      if (!q.q16) return set_error(XM_EINVAL, "sweep: Q has no BF16 copy");
+      return dispatch_r<__nv_bfloat16, 8>(ctx, q.q16, q, R, Y, W, skip, st);
+    default:
+      return set_error(XM_EINVAL, "sweep: unknown precision %d", prec);
+  }
+}
+
+}  // namespace xm

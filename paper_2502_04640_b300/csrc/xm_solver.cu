@@ -1,0 +1,1003 @@
+// Solver driver: Alg. 1 (Riemannian staircase) around RTR-tCG (Sec. 3.2), the dual certificate
+// of Thm. 1 with a Lanczos lambda_min, the escape of Thm. 2 and the rounding of Sec. 2.2.
+// The host only takes per-step trust-region decisions; inside truncated CG the control flow
+// (step length, boundary, negative curvature, residual test) runs on the device, so the host
+// checks a done flag once per chunk of iterations.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <type_traits>
+#include <vector>
+
+#include "xm_ops.cuh"
+
+namespace xm {
+
+// ------------------------------------------------------------------ host linear algebra
+// Cyclic Jacobi eigen-decomposition of a small symmetric matrix (Golub & Van Loan, Sec. 8.5),
+// eigenvalues sorted in descending order, eigenvectors as the columns of V (row-major m x m).
+static void sym_eig_desc(int m, std::vector<double> A, std::vector<double>& w,
+                         std::vector<double>& V) {
+  V.assign((size_t)m * m, 0.0);
+  for (int i = 0; i < m; ++i) V[(size_t)i * m + i] = 1.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int p = 0; p < m; ++p)
+      for (int q = 0; q < m; ++q) {
+        const double a = A[(size_t)p * m + q];
+        tot += a * a;
+        if (p != q) off += a * a;
+      }
+    if (off <= 1e-30 * tot || off == 0.0) break;
+    for (int p = 0; p < m - 1; ++p)
+      for (int q = p + 1; q < m; ++q) {
+        const double apq = A[(size_t)p * m + q];
+        if (std::fabs(apq) < 1e-300) continue;
+        const double tau = (A[(size_t)q * m + q] - A[(size_t)p * m + p]) / (2.0 * apq);
+        const double t = (tau >= 0 ? 1.0 : -1.0) / (std::fabs(tau) + std::sqrt(1.0 + tau * tau));
+        const double c = 1.0 / std::sqrt(1.0 + t * t), s = t * c;
+        for (int k = 0; k < m; ++k) {
+          const double akp = A[(size_t)k * m + p], akq = A[(size_t)k * m + q];
+          A[(size_t)k * m + p] = c * akp - s * akq;
+          A[(size_t)k * m + q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < m; ++k) {
+          const double apk = A[(size_t)p * m + k], aqk = A[(size_t)q * m + k];
+          A[(size_t)p * m + k] = c * apk - s * aqk;
+          A[(size_t)q * m + k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < m; ++k) {
+          const double vkp = V[(size_t)k * m + p], vkq = V[(size_t)k * m + q];
+          V[(size_t)k * m + p] = c * vkp - s * vkq;
+          V[(size_t)k * m + q] = s * vkp + c * vkq;
+        }
+      }
+  }
+  std::vector<int> idx(m);
+  for (int i = 0; i < m; ++i) idx[i] = i;
+  std::sort(idx.begin(), idx.end(),
+            [&](int a, int b) { return A[(size_t)a * m + a] > A[(size_t)b * m + b]; });
+  std::vector<double> V2((size_t)m * m);
+  w.resize(m);
+  for (int j = 0; j < m; ++j) {
+    w[j] = A[(size_t)idx[j] * m + idx[j]];
+    for (int k = 0; k < m; ++k) V2[(size_t)k * m + j] = V[(size_t)k * m + idx[j]];
+  }
+  V.swap(V2);
+}
+
+// Number of eigenvalues of the symmetric tridiagonal (a[0..k), b[0..k-1)) below x (Sturm).
+static int sturm_count(int k, const double* a, const double* b, double x) {
+  int c = 0;
+  double q = a[0] - x;
+  if (q < 0) ++c;
+  for (int i = 1; i < k; ++i) {
+    const double qq = (q == 0.0) ? 1e-300 : q;
+    q = a[i] - x - b[i - 1] * b[i - 1] / qq;
+    if (q < 0) ++c;
+  }
+  return c;
+}
+
+// j-th smallest eigenvalue (0-based) of the tridiagonal by bisection
+static double tri_eig_bisect(int k, const double* a, const double* b, int j) {
+  double lo = a[0], hi = a[0];
+  for (int i = 0; i < k; ++i) {
+    const double r = (i > 0 ? std::fabs(b[i - 1]) : 0.0) + (i + 1 < k ? std::fabs(b[i]) : 0.0);
+    lo = std::min(lo, a[i] - r);
+    hi = std::max(hi, a[i] + r);
+  }
+  const double span = std::max(std::fabs(lo), std::fabs(hi)) + 1e-300;
+  for (int it = 0; it < 200 && hi - lo > 1e-16 * span; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (sturm_count(k, a, b, mid) > j) hi = mid; else lo = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+// Eigenvector of the tridiagonal for eigenvalue th by inverse iteration with a tridiagonal
+// LU factorisation with partial pivoting.
+static void tri_eigvec(int k, const double* a, const double* b, double th, std::vector<double>& s) {
+  s.assign(k, 0.0);
+  if (k == 1) { s[0] = 1.0; return; }
+  double scale = 0.0;
+  for (int i = 0; i < k; ++i) scale = std::max(scale, std::fabs(a[i]) + (i < k - 1 ? std::fabs(b[i]) : 0.0));
+  const double sigma = th - 1e-13 * (scale + 1e-300);
+  // factor (T - sigma I) = P L U with U upper triangular (bandwidth 2)
+  std::vector<double> d(k), du(k), du2(k), l(k), dl(k);
+  std::vector<char> piv(k, 0);
+  for (int i = 0; i < k; ++i) { d[i] = a[i] - sigma; du[i] = i < k - 1 ? b[i] : 0.0; du2[i] = 0.0; }
+  for (int i = 0; i < k - 1; ++i) dl[i] = b[i];
+  for (int i = 0; i < k - 1; ++i) {
+    if (std::fabs(d[i]) >= std::fabs(dl[i])) {
+      const double f = d[i] != 0.0 ? dl[i] / d[i] : 0.0;
+      l[i] = f;
+      d[i + 1] -= f * du[i];
+    } else {
+      const double f = d[i] / dl[i];
+      l[i] = f;
+      piv[i] = 1;
+      const double t = du[i];
+      d[i] = dl[i];
+      du[i] = d[i + 1];
+      d[i + 1] = t - f * d[i + 1];
+      if (i < k - 2) {
+        du2[i] = du[i + 1];
+        du[i + 1] = -f * du[i + 1];
+      }
+    }
+  }
+  for (int i = 0; i < k; ++i) if (d[i] == 0.0) d[i] = 1e-300;
+  for (int i = 0; i < k; ++i) s[i] = 1.0 / std::sqrt((double)k) * ((i % 3) ? 1.0 : -0.7);
+  for (int it = 0; it < 4; ++it) {
+    for (int i = 0; i < k - 1; ++i) {
+      if (piv[i]) { const double t = s[i]; s[i] = s[i + 1]; s[i + 1] = t - l[i] * s[i + 1]; }
+      else s[i + 1] -= l[i] * s[i];
+    }
+    s[k - 1] /= d[k - 1];
+    if (k > 1) s[k - 2] = (s[k - 2] - du[k - 2] * s[k - 1]) / d[k - 2];
+    for (int i = k - 3; i >= 0; --i) s[i] = (s[i] - du[i] * s[i + 1] - du2[i] * s[i + 2]) / d[i];
+    double nrm = 0.0;
+    for (int i = 0; i < k; ++i) nrm += s[i] * s[i];
+    nrm = std::sqrt(nrm);
+    for (int i = 0; i < k; ++i) s[i] /= nrm;
+  }
+}
+
+// ------------------------------------------------------------------ the solver
+struct Solver {
+  xm_ctx* ctx;
+  const DeviceQ& q;
+  xm_opts o;
+  cudaStream_t st;
+  int N, n, n_pad, nb_cam;
+  size_t vec_bytes;
+  // vectors (n_pad x 8 elements of up to 8 bytes each)
+  void *bY = nullptr, *bYc = nullptr, *bW = nullptr, *bWc = nullptr, *bG = nullptr,
+       *bGc = nullptr, *bYin = nullptr, *bEta = nullptr, *bHeta = nullptr, *bR = nullptr,
+       *bD = nullptr, *bHd = nullptr, *bWd = nullptr, *bY64 = nullptr, *bXi = nullptr,
+       *bYh = nullptr;
+  double *Lam = nullptr, *Lamc = nullptr;
+  Scal* d_sc = nullptr;
+  Scal* h_sc = nullptr;
+  double* d_small = nullptr;   // gram / rotation / O0 / scalar scratch (256 doubles)
+  // Lanczos
+  int kmax = 0;
+  double *V = nullptr, *lw = nullptr, *lz = nullptr, *lalpha = nullptr, *lbeta = nullptr,
+         *lc = nullptr, *lnrm = nullptr, *lritz = nullptr;
+  float *lv32 = nullptr, *lW32 = nullptr;
+  // stats
+  xm_info info{};
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  double ms32 = 0, ms64 = 0;
+  int n32 = 0, n64 = 0;
+  long launches = 0;
+  std::chrono::steady_clock::time_point t_start;
+  bool timed_out = false;
+  double ref_g = -1.0;   // ||rgrad|| at the start point of the solve (tolerance reference)
+  double cur_g2 = 0.0;
+
+  Solver(xm_ctx* c, const DeviceQ& qq, const xm_opts& oo) : ctx(c), q(qq), o(oo), st(c->stream) {
+    N = q.N; n = q.n; n_pad = q.n_pad;
+    nb_cam = (N + CAM_THREADS - 1) / CAM_THREADS;
+    vec_bytes = (size_t)n_pad * XM_MAX_RANK * sizeof(double);
+  }
+  ~Solver() {
+    void* bufs[] = {bY, bYc, bW, bWc, bG, bGc, bYin, bEta, bHeta, bR, bD, bHd, bWd, bY64, bXi, bYh,
+                    Lam, Lamc, d_sc, d_small, V, lw, lz, lalpha, lbeta, lc, lnrm, lritz, lv32, lW32};
+    for (void* p : bufs) if (p) cudaFree(p);
+    if (h_sc) cudaFreeHost(h_sc);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+  }
+
+  xm_status alloc() {
+    void** vecs[] = {&bY, &bYc, &bW, &bWc, &bG, &bGc, &bYin, &bEta, &bHeta, &bR, &bD, &bHd, &bWd,
+                     &bY64, &bXi, &bYh};
+    for (void** p : vecs) {
+      XM_CUDA_TRY(cudaMalloc(p, vec_bytes));
+      XM_CUDA_TRY(cudaMemsetAsync(*p, 0, vec_bytes, st));
+    }
+    XM_CUDA_TRY(cudaMalloc(&Lam, sizeof(double) * 9 * (size_t)N));
+    XM_CUDA_TRY(cudaMalloc(&Lamc, sizeof(double) * 9 * (size_t)N));
+    XM_CUDA_TRY(cudaMemsetAsync(Lam, 0, sizeof(double) * 9 * (size_t)N, st));
+    XM_CUDA_TRY(cudaMemsetAsync(Lamc, 0, sizeof(double) * 9 * (size_t)N, st));
+    XM_CUDA_TRY(cudaMalloc(&d_sc, sizeof(Scal)));
+    XM_CUDA_TRY(cudaMemsetAsync(d_sc, 0, sizeof(Scal), st));
+    XM_CUDA_TRY(cudaMallocHost(&h_sc, sizeof(Scal)));
+    XM_CUDA_TRY(cudaMalloc(&d_small, 256 * sizeof(double)));
+    XM_CUDA_TRY(cudaMemsetAsync(d_small, 0, 256 * sizeof(double), st));
+    XM_CUDA_TRY(cudaEventCreate(&ev0));
+    XM_CUDA_TRY(cudaEventCreate(&ev1));
+    XM_TRY(ensure_partials(ctx, (size_t)std::max(nb_cam, 1024) * 64));
+    return XM_OK;
+  }
+
+  // Zero every work vector except the FP64 master iterate.  Called whenever the precision or
+  // the padded width changes, so that no buffer is ever read through a stale reinterpretation.
+  xm_status clear_vecs() {
+    void* vecs[] = {bY, bYc, bW, bWc, bG, bGc, bYin, bEta, bHeta, bR, bD, bHd, bWd, bXi, bYh};
+    for (void* p : vecs) XM_CUDA_TRY(cudaMemsetAsync(p, 0, vec_bytes, st));
+    return XM_OK;
+  }
+
+  int grid_elems(size_t total) const {
+    size_t g = (total + CAM_THREADS - 1) / CAM_THREADS;
+    const size_t cap = (size_t)ctx->num_sms * 8;
+    if (g > cap) g = cap;
+    return (int)std::max<size_t>(g, 1);
+  }
+  int grid_gram() const { return std::max(1, std::min(nb_cam * 3, ctx->num_sms * 4)); }
+  double* d_slot() { return d_small + 200; }
+
+  bool over_time() {
+    if (o.time_limit_s <= 0) return false;
+    const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    if (el > o.time_limit_s) timed_out = true;
+    return timed_out;
+  }
+
+  xm_status pull_scalars() {
+    XM_CUDA_TRY(cudaMemcpyAsync(h_sc, d_sc, sizeof(Scal), cudaMemcpyDeviceToHost, st));
+    XM_CUDA_TRY(cudaStreamSynchronize(st));
+    return check_device_error(ctx, "solver");
+  }
+
+  // one sweep; timed = bracket it with events (only for sweeps that always run)
+  xm_status sweep(int prec, int R, const void* Yp, void* Wp, const int* skip, bool timed) {
+    if (timed) XM_CUDA_TRY(cudaEventRecord(ev0, st));
+    XM_TRY(qy_launch(ctx, q, prec, R, Yp, Wp, skip, st));
+    ++launches;
+    ++info.n_sweeps;
+    if (prec == XM_FP64) ++info.n_sweeps_fp64;
+    if (timed) {
+      XM_CUDA_TRY(cudaEventRecord(ev1, st));
+      XM_CUDA_TRY(cudaEventSynchronize(ev1));
+      float ms = 0.f;
+      XM_CUDA_TRY(cudaEventElapsedTime(&ms, ev0, ev1));
+      if (prec == XM_FP64) { ms64 += ms; ++n64; }
+      else if (prec == XM_FP32_BULK && R == 4) { ms32 += ms; ++n32; }
+    }
+    return XM_OK;
+  }
+
+  // ---------------- gradient / objective at a point (W zero on entry, zero on exit)
+  template <typename To, int R>
+  xm_status grad_at(int prec, void* Yp, void* Wp, void* Gp, double* L, int cand, bool timed) {
+    XM_TRY(sweep(prec, R, Yp, Wp, nullptr, timed));
+    k_grad_epi<To, R><<<nb_cam, CAM_THREADS, 0, st>>>(N, (const To*)Yp, (To*)Wp, (To*)Gp, L, d_sc,
+                                                      cand, ctx->d_partials, ctx->d_counter,
+                                                      ctx->d_err);
+    ++launches;
+    XM_CUDA_TRY(cudaGetLastError());
+    return XM_OK;
+  }
+
+  // ---------------- RTR (Absil et al. 2008, Alg. 10) at fixed rank
+  template <typename To, typename Ti, int R>
+  xm_status rtr(int prec_grad, int prec_hvp, double tol_rel, int max_outer, bool bulk) {
+    const size_t rows = (size_t)n_pad;
+    XM_TRY(grad_at<To, R>(prec_grad, bY, bW, bG, Lam, 0, true));
+    XM_TRY(pull_scalars());
+    double f = h_sc->f, g2 = h_sc->g2;
+    if (!std::isfinite(f) || !std::isfinite(g2)) return set_error(XM_ENUMERIC, "rtr: non-finite f");
+    if (ref_g <= 0) ref_g = std::sqrt(g2);
+    const double tol_abs = tol_rel * ref_g;
+    const double Delta_bar = std::sqrt(std::max(h_sc->y2, 1e-300));
+    double Delta = Delta_bar / 8.0;
+    const double eps_reg = std::is_same<To, float>::value ? 1e2 * 1.1920929e-07
+                                                          : 1e3 * 2.220446049250313e-16;
+    int rejects = 0;
+    for (int k = 0; k < max_outer; ++k) {
+      if (std::sqrt(g2) <= tol_abs) break;
+      if (over_time()) break;
+      const Ti* Yin;
+      if (!std::is_same<To, Ti>::value) {
+        k_cast<To, Ti><<<grid_elems(rows * R), CAM_THREADS, 0, st>>>(rows * R, (const To*)bY, (Ti*)bYin);
+        ++launches;
+        Yin = (const Ti*)bYin;
+      } else {
+        Yin = (const Ti*)bY;
+      }
+      k_tcg_init<To, Ti, R><<<grid_elems(rows * R), CAM_THREADS, 0, st>>>(
+          (int)rows, (const To*)bG, (Ti*)bEta, (Ti*)bHeta, (Ti*)bR, (Ti*)bD, d_sc, Delta, o.max_tcg,
+          1.0, 0.1);
+      ++launches;
+      XM_CUDA_TRY(cudaGetLastError());
+      const int CH = 4;
+      int done = 0;
+      for (int j = 0; j < o.max_tcg && !done; j += CH) {
+        for (int c = 0; c < CH; ++c) {
+          XM_TRY(sweep(prec_hvp, R, bD, bWd, &d_sc->done, false));
+          k_hvp_epi<Ti, R><<<nb_cam, CAM_THREADS, 0, st>>>(N, Yin, (Ti*)bWd, (const Ti*)bD, (Ti*)bHd,
+                                                           Lam, d_sc, ctx->d_partials, ctx->d_counter);
+          k_tcg_update<Ti, R><<<nb_cam, CAM_THREADS, 0, st>>>(N, Yin, (Ti*)bEta, (Ti*)bHeta, (Ti*)bR,
+                                                              (const Ti*)bD, (const Ti*)bHd, d_sc,
+                                                              ctx->d_partials, ctx->d_counter);
+          k_tcg_dir<Ti, R><<<nb_cam, CAM_THREADS, 0, st>>>(N, (const Ti*)bEta, (const Ti*)bR, (Ti*)bD,
+                                                           d_sc, ctx->d_partials, ctx->d_counter);
+          launches += 3;
+        }
+        XM_CUDA_TRY(cudaGetLastError());
+        XM_CUDA_TRY(cudaMemcpyAsync(&h_sc->done, &d_sc->done, sizeof(int), cudaMemcpyDeviceToHost, st));
+        XM_CUDA_TRY(cudaStreamSynchronize(st));
+        done = h_sc->done;
+      }
+      k_model_terms<To, Ti, R><<<grid_elems(rows * R), CAM_THREADS, 0, st>>>(
+          (int)rows, (const To*)bG, (const Ti*)bEta, (const Ti*)bHeta, d_sc, ctx->d_partials,
+          ctx->d_counter);
+      k_retract<To, Ti, R><<<nb_cam, CAM_THREADS, 0, st>>>(N, (const To*)bY, (const Ti*)bEta, 1.0,
+                                                           (To*)bYc);
+      launches += 2;
+      XM_CUDA_TRY(cudaGetLastError());
+      XM_TRY(grad_at<To, R>(prec_grad, bYc, bWc, bGc, Lamc, 1, true));
+      XM_TRY(pull_scalars());
+      ++info.n_outer;
+      info.n_tcg += h_sc->iters;
+      const double fc = h_sc->fc;
+      const double model_dec = -(h_sc->g_eta + 0.5 * h_sc->eta_Heta);
+      const double reg = std::max(1.0, std::fabs(f)) * eps_reg;
+      const double rho = (f - fc + reg) / (model_dec + reg);
+      const double en = std::sqrt(h_sc->eta2);
+      if (!std::isfinite(fc) || rho < 0.25) {
+        Delta *= 0.25;
+      } else if (rho > 0.75 && en >= Delta * (1.0 - 1e-6)) {
+        Delta = std::min(2.0 * Delta, Delta_bar);
+      }
+      const bool accept = std::isfinite(fc) && rho > 0.1 && fc <= f + reg;
+      if (o.verbose >= 2)
+        fprintf(stderr, "[xm] %s k=%d f=%.12e |g|=%.3e rho=%.3f Delta=%.3e tcg=%d(%d) %s\n",
+                bulk ? "bulk" : "fp64", k, f, std::sqrt(g2), rho, Delta, h_sc->iters, h_sc->reason,
+                accept ? "acc" : "rej");
+      if (accept) {
+        std::swap(bY, bYc); std::swap(bW, bWc); std::swap(bG, bGc); std::swap(Lam, Lamc);
+        f = fc;
+        g2 = h_sc->gc2;
+        rejects = 0;
+      } else {
+        ++rejects;
+      }
+      if (Delta < 1e-12 * Delta_bar) break;
+      if (bulk && (rejects >= 6 || Delta < 1e-7 * Delta_bar)) break;
+    }
+    info.f = f;
+    cur_g2 = g2;
+    return XM_OK;
+  }
+
+  // w = Z v (v, w: FP64 n_pad vectors), Z = Q - blockdiag(Lam)
+  xm_status zmul(int prec, const double* v, double* w) {
+    const int nn = n_pad;
+    if (prec == XM_FP64) {
+      XM_TRY(sweep(XM_FP64, 1, v, lz, nullptr, false));
+      k_zv_epi<double><<<nb_cam, CAM_THREADS, 0, st>>>(N, lz, v, Lam, w);
+    } else {
+      k_cast<double, float><<<grid_elems(nn), CAM_THREADS, 0, st>>>((size_t)nn, v, lv32);
+      XM_TRY(sweep(XM_FP32_BULK, 1, lv32, lW32, nullptr, false));
+      k_zv_epi<float><<<nb_cam, CAM_THREADS, 0, st>>>(N, lW32, v, Lam, w);
+      ++launches;
+    }
+    ++launches;
+    XM_CUDA_TRY(cudaGetLastError());
+    return XM_OK;
+  }
+
+  // classical Gram-Schmidt pass of w against the first m columns of V
+  xm_status reorth(double* w, int m) {
+    if (m <= 0) return XM_OK;
+    const int nn = n_pad;
+    k_gemv_t<<<std::min(m, ctx->num_sms * 8), 256, 0, st>>>(nn, m, V, nn, w, lc);
+    k_gemv_n_sub<<<grid_elems(nn), CAM_THREADS, 0, st>>>(nn, m, V, nn, lc, w);
+    launches += 2;
+    XM_CUDA_TRY(cudaGetLastError());
+    return XM_OK;
+  }
+
+  // ---------------- Lanczos on Z restricted to range(Y)^perp (Thm. 1 certificate)
+  template <int R>
+  xm_status certify(int r, int prec_z, double* lam_def, double* lam_max, double* lam_range) {
+    auto tic = std::chrono::steady_clock::now();
+    const int nn = n_pad;
+    const int nd_max = XM_MAX_RANK;
+    if (!V) {
+      kmax = std::max(10, std::min(o.lanczos_max, n));
+      XM_CUDA_TRY(cudaMalloc(&V, sizeof(double) * (size_t)nn * (nd_max + kmax + 1)));
+      XM_CUDA_TRY(cudaMalloc(&lw, sizeof(double) * nn));
+      XM_CUDA_TRY(cudaMemsetAsync(lw, 0, sizeof(double) * nn, st));
+      XM_CUDA_TRY(cudaMalloc(&lz, sizeof(double) * nn));
+      XM_CUDA_TRY(cudaMalloc(&lritz, sizeof(double) * nn));
+      XM_CUDA_TRY(cudaMalloc(&lalpha, sizeof(double) * (kmax + 1)));
+      XM_CUDA_TRY(cudaMalloc(&lbeta, sizeof(double) * (kmax + 1)));
+      XM_CUDA_TRY(cudaMalloc(&lc, sizeof(double) * (nd_max + kmax + 2)));
+      XM_CUDA_TRY(cudaMalloc(&lnrm, sizeof(double) * 2));
+      XM_CUDA_TRY(cudaMalloc(&lv32, sizeof(float) * nn));
+      XM_CUDA_TRY(cudaMalloc(&lW32, sizeof(float) * nn));
+      XM_CUDA_TRY(cudaMemsetAsync(lz, 0, sizeof(double) * nn, st));
+      XM_CUDA_TRY(cudaMemsetAsync(lritz, 0, sizeof(double) * nn, st));
+      XM_CUDA_TRY(cudaMemsetAsync(lW32, 0, sizeof(float) * nn, st));
+    }
+    const int gv = grid_elems((size_t)nn);
+    // orthonormal basis of range(Y) from the Gram matrix (first r columns)
+    k_gram<double, R><<<grid_gram(), CAM_THREADS, 0, st>>>(nn, (const double*)bY64, d_small,
+                                                           ctx->d_partials, ctx->d_counter);
+    ++launches;
+    std::vector<double> gram(R * R);
+    XM_CUDA_TRY(cudaMemcpyAsync(gram.data(), d_small, sizeof(double) * R * R, cudaMemcpyDeviceToHost, st));
+    XM_CUDA_TRY(cudaStreamSynchronize(st));
+    std::vector<double> gr((size_t)r * r), ew, EV;
+    for (int a = 0; a < r; ++a) for (int b = 0; b < r; ++b) gr[(size_t)a * r + b] = gram[a * R + b];
+    sym_eig_desc(r, gr, ew, EV);
+    int nd = 0;
+    std::vector<double> rot((size_t)R * R, 0.0);   // R x R: column j = E_j / sqrt(w_j)
+    for (int j = 0; j < r; ++j)
+      if (ew[j] > 1e-10 * ew[0]) {
+        for (int a = 0; a < r; ++a) rot[(size_t)a * R + nd] = EV[(size_t)a * r + j] / std::sqrt(ew[j]);
+        ++nd;
+      }
+    // V[:, j] = Y rot[:, j] for j < nd, through a row-major staging copy in bXi
+    XM_CUDA_TRY(cudaMemcpyAsync(bXi, bY64, sizeof(double) * (size_t)nn * R, cudaMemcpyDeviceToDevice, st));
+    XM_CUDA_TRY(cudaMemcpyAsync(d_small + 64, rot.data(), sizeof(double) * R * R, cudaMemcpyHostToDevice, st));
+    k_rotate<R><<<(nn + 127) / 128, 128, 0, st>>>(nn, (double*)bXi, d_small + 64);
+    ++launches;
+    for (int j = 0; j < nd; ++j)
+      XM_CUDA_TRY(cudaMemcpy2DAsync(V + (size_t)j * nn, sizeof(double), (const double*)bXi + j,
+                                    sizeof(double) * R, sizeof(double), nn,
+                                    cudaMemcpyDeviceToDevice, st));
+    // Rayleigh quotients of Z on range(Y): Vd^T Z Vd (nd x nd)
+    std::vector<double> zr((size_t)nd * nd, 0.0);
+    for (int j = 0; j < nd; ++j) {
+      XM_TRY(zmul(prec_z, V + (size_t)j * nn, lw));
+      k_gemv_t<<<nd, 256, 0, st>>>(nn, nd, V, nn, lw, lc);
+      ++launches;
+      std::vector<double> cj(nd);
+      XM_CUDA_TRY(cudaMemcpyAsync(cj.data(), lc, sizeof(double) * nd, cudaMemcpyDeviceToHost, st));
+      XM_CUDA_TRY(cudaStreamSynchronize(st));
+      for (int l = 0; l < nd; ++l) zr[(size_t)j * nd + l] = cj[l];
+    }
+    if (nd > 0) {
+      for (int a = 0; a < nd; ++a) for (int b = a + 1; b < nd; ++b) {
+        const double m = 0.5 * (zr[(size_t)a * nd + b] + zr[(size_t)b * nd + a]);
+        zr[(size_t)a * nd + b] = zr[(size_t)b * nd + a] = m;
+      }
+      std::vector<double> zw, zv;
+      sym_eig_desc(nd, zr, zw, zv);
+      *lam_range = zw[nd - 1];
+    } else {
+      *lam_range = 0.0;
+    }
+    // start vector
+    double* v0 = V + (size_t)nd * nn;
+    k_random_vec<<<gv, CAM_THREADS, 0, st>>>(n, o.seed, v0);
+    XM_CUDA_TRY(cudaMemsetAsync(v0 + n, 0, sizeof(double) * (nn - n), st));
+    ++launches;
+    XM_TRY(reorth(v0, nd));
+    k_dot<double, double><<<gv, CAM_THREADS, 0, st>>>((size_t)nn, v0, v0, lnrm, ctx->d_partials, ctx->d_counter);
+    k_normalize<<<gv, CAM_THREADS, 0, st>>>(nn, v0, lnrm, v0, nullptr);
+    launches += 2;
+    std::vector<double> ha(kmax + 1), hb(kmax + 1), s;
+    int K = 0;
+    double th_min = 0, th_max = 0;
+    bool conv = false;
+    const int kcap = std::min(kmax, n - nd);
+    for (int k = 0; k < kcap; ++k) {
+      double* vk = V + (size_t)(nd + k) * nn;
+      double* vkm1 = k > 0 ? V + (size_t)(nd + k - 1) * nn : nullptr;
+      XM_TRY(zmul(prec_z, vk, lw));
+      k_dot<double, double><<<gv, CAM_THREADS, 0, st>>>((size_t)nn, vk, lw, lalpha + k, ctx->d_partials, ctx->d_counter);
+      k_lanczos_3term<<<gv, CAM_THREADS, 0, st>>>(nn, lw, vk, vkm1, lalpha, lbeta, k);
+      launches += 2;
+      XM_TRY(reorth(lw, nd + k + 1));
+      XM_TRY(reorth(lw, nd + k + 1));
+      k_dot<double, double><<<gv, CAM_THREADS, 0, st>>>((size_t)nn, lw, lw, lnrm, ctx->d_partials, ctx->d_counter);
+      k_normalize<<<gv, CAM_THREADS, 0, st>>>(nn, lw, lnrm, V + (size_t)(nd + k + 1) * nn, lbeta + k);
+      launches += 2;
+      XM_CUDA_TRY(cudaGetLastError());
+      ++info.n_lanczos;
+      K = k + 1;
+      if ((K % 10) == 0 || K == kcap) {
+        XM_CUDA_TRY(cudaMemcpyAsync(ha.data(), lalpha, sizeof(double) * K, cudaMemcpyDeviceToHost, st));
+        XM_CUDA_TRY(cudaMemcpyAsync(hb.data(), lbeta, sizeof(double) * K, cudaMemcpyDeviceToHost, st));
+        XM_CUDA_TRY(cudaStreamSynchronize(st));
+        th_min = tri_eig_bisect(K, ha.data(), hb.data(), 0);
+        th_max = tri_eig_bisect(K, ha.data(), hb.data(), K - 1);
+        tri_eigvec(K, ha.data(), hb.data(), th_min, s);
+        const double res = std::fabs(hb[K - 1] * s[K - 1]);
+        const double scale = std::max(std::fabs(th_max), std::fabs(th_min)) + 1e-300;
+        if (res <= o.lanczos_tol * scale || hb[K - 1] <= 1e-14 * scale || K == kcap) {
+          conv = true;
+          break;
+        }
+      }
+    }
+    if (!conv && K > 0) {
+      XM_CUDA_TRY(cudaMemcpyAsync(ha.data(), lalpha, sizeof(double) * K, cudaMemcpyDeviceToHost, st));
+      XM_CUDA_TRY(cudaMemcpyAsync(hb.data(), lbeta, sizeof(double) * K, cudaMemcpyDeviceToHost, st));
+      XM_CUDA_TRY(cudaStreamSynchronize(st));
+      th_min = tri_eig_bisect(K, ha.data(), hb.data(), 0);
+      th_max = tri_eig_bisect(K, ha.data(), hb.data(), K - 1);
+      tri_eigvec(K, ha.data(), hb.data(), th_min, s);
+    }
+    // Ritz vector of theta_min -> lritz (k_gemv_n_sub subtracts: lritz = -V s; the sign of an
+    // eigenvector is irrelevant)
+    if (K > 0) {
+      XM_CUDA_TRY(cudaMemcpyAsync(lc, s.data(), sizeof(double) * K, cudaMemcpyHostToDevice, st));
+      XM_CUDA_TRY(cudaMemsetAsync(lritz, 0, sizeof(double) * nn, st));
+      k_gemv_n_sub<<<gv, CAM_THREADS, 0, st>>>(nn, K, V + (size_t)nd * nn, nn, lc, lritz);
+      ++launches;
+    }
+    XM_CUDA_TRY(cudaStreamSynchronize(st));
+    *lam_def = th_min;
+    *lam_max = th_max;
+    info.t_cert_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - tic).count();
+    return XM_OK;
+  }
+
+  // ---------------- rounding (Sec. 2.2) and the Eq. 18 / App. E numbers
+  template <int R>
+  xm_status round_and_eval(int r, double* R_out, double* s_out) {
+    const int nn = n_pad;
+    k_gram<double, R><<<grid_gram(), CAM_THREADS, 0, st>>>(nn, (const double*)bY64, d_small,
+                                                           ctx->d_partials, ctx->d_counter);
+    ++launches;
+    std::vector<double> gram(R * R);
+    XM_CUDA_TRY(cudaMemcpyAsync(gram.data(), d_small, sizeof(double) * R * R, cudaMemcpyDeviceToHost, st));
+    XM_CUDA_TRY(cudaStreamSynchronize(st));
+    std::vector<double> gr((size_t)r * r), ew, EV;
+    for (int a = 0; a < r; ++a) for (int b = 0; b < r; ++b) gr[(size_t)a * r + b] = gram[a * R + b];
+    sym_eig_desc(r, gr, ew, EV);
+    // Yh = Y V3 (n_pad x 4, last column zero): a rotation padded to R x R then truncated
+    std::vector<double> rot((size_t)R * R, 0.0);
+    for (int a = 0; a < r; ++a) for (int j = 0; j < 3 && j < r; ++j) rot[(size_t)a * R + j] = EV[(size_t)a * r + j];
+    XM_CUDA_TRY(cudaMemcpyAsync(bXi, bY64, sizeof(double) * (size_t)nn * R, cudaMemcpyDeviceToDevice, st));
+    XM_CUDA_TRY(cudaMemcpyAsync(d_small + 64, rot.data(), sizeof(double) * R * R, cudaMemcpyHostToDevice, st));
+    k_rotate<R><<<(nn + 127) / 128, 128, 0, st>>>(nn, (double*)bXi, d_small + 64);
+    k_repad<double, double><<<grid_elems((size_t)nn * 4), CAM_THREADS, 0, st>>>(nn, nn, (const double*)bXi, R,
+                                                                          (double*)bYh, 4);
+    launches += 2;
+    // anchor block -> O0 = polar(Ubar_0), Ubar_0 = Yh_0^T
+    double yh0[12];
+    XM_CUDA_TRY(cudaMemcpyAsync(yh0, bYh, sizeof(double) * 12, cudaMemcpyDeviceToHost, st));
+    XM_CUDA_TRY(cudaStreamSynchronize(st));
+    std::vector<double> Ub(9), UtU(9), w3, V3;
+    for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) Ub[a * 3 + b] = yh0[b * 4 + a];
+    for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) {
+      double t = 0; for (int k = 0; k < 3; ++k) t += Ub[k * 3 + a] * Ub[k * 3 + b];
+      UtU[a * 3 + b] = t;
+    }
+    sym_eig_desc(3, UtU, w3, V3);
+    double O0[9];   // Ub V diag(1/sig) V^T
+    for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) {
+      double t = 0;
+      for (int k = 0; k < 3; ++k) {
+        const double sig = std::sqrt(std::max(w3[k], 1e-300));
+        double uk = 0; for (int m = 0; m < 3; ++m) uk += Ub[a * 3 + m] * V3[m * 3 + k];
+        t += uk / sig * V3[b * 3 + k];
+      }
+      O0[a * 3 + b] = t;
+    }
+    XM_CUDA_TRY(cudaMemcpyAsync(d_small + 128, O0, sizeof(O0), cudaMemcpyHostToDevice, st));
+    double* Rd = (double*)bXi;                  // N x 9 scratch (9N <= 8 n_pad doubles)
+    double* sd = Lamc;                          // N scratch
+    XM_CUDA_TRY(cudaMemsetAsync(bYc, 0, vec_bytes, st));
+    k_round<<<nb_cam, CAM_THREADS, 0, st>>>(N, (const double*)bYh, d_small + 128, Rd, sd, (double*)bYc);
+    ++launches;
+    XM_CUDA_TRY(cudaGetLastError());
+    if (R_out) XM_CUDA_TRY(cudaMemcpyAsync(R_out, Rd, sizeof(double) * 9 * N, cudaMemcpyDeviceToDevice, st));
+    if (s_out) XM_CUDA_TRY(cudaMemcpyAsync(s_out, sd, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+    // rho_hat = f(Yhat) in FP64
+    XM_CUDA_TRY(cudaMemsetAsync(bWc, 0, vec_bytes, st));
+    XM_TRY(sweep(XM_FP64, 4, bYc, bWc, nullptr, false));
+    k_dot<double, double><<<grid_elems((size_t)nn * 4), CAM_THREADS, 0, st>>>(
+        (size_t)nn * 4, (const double*)bYc, (const double*)bWc, d_slot(), ctx->d_partials,
+        ctx->d_counter);
+    ++launches;
+    double rho_hat = 0;
+    XM_CUDA_TRY(cudaMemcpyAsync(&rho_hat, d_slot(), sizeof(double), cudaMemcpyDeviceToHost, st));
+    XM_CUDA_TRY(cudaStreamSynchronize(st));
+    XM_CUDA_TRY(cudaMemsetAsync(bWc, 0, vec_bytes, st));
+    info.rho_hat = rho_hat;
+    return XM_OK;
+  }
+};
+
+// ------------------------------------------------------------------ staircase driver
+template <typename F4, typename F8>
+static xm_status with_R(int R, F4 f4, F8 f8) {
+  return R == 4 ? f4() : f8();
+}
+
+__global__ void k_init_identity(int N, int R, double* Y) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  for (int a = 0; a < 3; ++a)
+    for (int j = 0; j < R; ++j) Y[(size_t)(3 * i + a) * R + j] = (a == j) ? 1.0 : 0.0;
+}
+
+__global__ void k_set_col(int n, int n_rows, int R, int col, const double* v, double* Xi) {
+  const size_t total = (size_t)n_rows * R;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int row = (int)(e / R), c = (int)(e % R);
+    Xi[e] = (c == col && row < n) ? v[row] : 0.0;
+  }
+}
+
+static double suboptimality(double rho_hat, double rho) {
+  return (rho_hat - rho) / (1.0 + std::fabs(rho_hat) + std::fabs(rho));
+}
+
+xm_status solve_impl(xm_ctx* ctx, const DeviceQ& q, const xm_opts& o, int r_in, const double* Y0,
+                     double* Y_out, double* R_out, double* s_out, xm_info* out_info,
+                     bool certify_only, double* Lambda_out, double* v_out) {
+  Solver S(ctx, q, o);
+  S.t_start = std::chrono::steady_clock::now();
+  XM_TRY(S.alloc());
+  cudaStream_t st = ctx->stream;
+  const int N = q.N, n = q.n, nn = q.n_pad;
+  const bool fp64_mode = o.prec == XM_FP64;
+  const int prec_hvp = o.prec == XM_BF16Q_BULK ? XM_BF16Q_BULK : (fp64_mode ? XM_FP64 : XM_FP32_BULK);
+  const int prec_z = fp64_mode ? XM_FP64 : XM_FP32_BULK;
+
+  int r = Y0 ? r_in : o.r0;
+  int R = r <= 4 ? 4 : 8;
+  // initial point (FP64, n_pad x R)
+  if (Y0) {
+    k_repad<double, double><<<S.grid_elems((size_t)nn * R), CAM_THREADS, 0, st>>>(
+        n, nn, Y0, r_in, (double*)S.bY64, R);
+    XM_CUDA_TRY(cudaMemsetAsync(S.bXi, 0, S.vec_bytes, st));
+    // make it feasible: retract with a zero step
+    XM_TRY(with_R(R,
+        [&] { k_retract<double, double, 4><<<S.nb_cam, CAM_THREADS, 0, st>>>(N, (const double*)S.bY64, (const double*)S.bXi, 0.0, (double*)S.bYc); return XM_OK; },
+        [&] { k_retract<double, double, 8><<<S.nb_cam, CAM_THREADS, 0, st>>>(N, (const double*)S.bY64, (const double*)S.bXi, 0.0, (double*)S.bYc); return XM_OK; }));
+    XM_CUDA_TRY(cudaMemcpyAsync(S.bY64, S.bYc, sizeof(double) * (size_t)nn * R, cudaMemcpyDeviceToDevice, st));
+    S.launches += 2;
+  } else {
+    k_init_identity<<<S.nb_cam, CAM_THREADS, 0, st>>>(N, R, (double*)S.bY64);
+    ++S.launches;
+  }
+  XM_CUDA_TRY(cudaGetLastError());
+
+  double lam_def = 0, lam_max = 0, lam_range = 0;
+  bool certified = false;
+  xm_status result = XM_OK;
+  for (;;) {
+    const size_t elems = (size_t)nn * R;
+    XM_TRY(S.clear_vecs());
+    // ---- local optimisation at rank r
+    if (certify_only) {
+      XM_CUDA_TRY(cudaMemcpyAsync(S.bY, S.bY64, sizeof(double) * elems, cudaMemcpyDeviceToDevice, st));
+      XM_TRY(with_R(R, [&] { return S.grad_at<double, 4>(XM_FP64, S.bY, S.bW, S.bG, S.Lam, 0, false); },
+                       [&] { return S.grad_at<double, 8>(XM_FP64, S.bY, S.bW, S.bG, S.Lam, 0, false); }));
+      XM_TRY(S.pull_scalars());
+      S.info.f = S.h_sc->f;
+      S.cur_g2 = S.h_sc->g2;
+    } else if (fp64_mode) {
+      XM_CUDA_TRY(cudaMemcpyAsync(S.bY, S.bY64, sizeof(double) * elems, cudaMemcpyDeviceToDevice, st));
+      XM_TRY(with_R(R,
+          [&] { return S.rtr<double, double, 4>(XM_FP64, XM_FP64, o.grad_tol_rel, o.max_outer, false); },
+          [&] { return S.rtr<double, double, 8>(XM_FP64, XM_FP64, o.grad_tol_rel, o.max_outer, false); }));
+      XM_CUDA_TRY(cudaMemcpyAsync(S.bY64, S.bY, sizeof(double) * elems, cudaMemcpyDeviceToDevice, st));
+    } else {
+      // bulk FP32 phase
+      k_cast<double, float><<<S.grid_elems(elems), CAM_THREADS, 0, st>>>(elems, (const double*)S.bY64, (float*)S.bY);
+      ++S.launches;
+      XM_TRY(with_R(R,
+          [&] { return S.rtr<float, float, 4>(XM_FP32_BULK, prec_hvp, o.bulk_tol_rel, o.max_outer, true); },
+          [&] { return S.rtr<float, float, 8>(XM_FP32_BULK, prec_hvp, o.bulk_tol_rel, o.max_outer, true); }));
+      k_cast<float, double><<<S.grid_elems(elems), CAM_THREADS, 0, st>>>(elems, (const float*)S.bY, (double*)S.bY64);
+      ++S.launches;
+      XM_CUDA_TRY(cudaGetLastError());
+      // FP64 polish: FP64 gradient and objective, FP32 Hessian-vector products
+      XM_TRY(S.clear_vecs());
+      XM_CUDA_TRY(cudaMemcpyAsync(S.bY, S.bY64, sizeof(double) * elems, cudaMemcpyDeviceToDevice, st));
+      XM_TRY(with_R(R,
+          [&] { return S.rtr<double, float, 4>(XM_FP64, XM_FP32_BULK, o.grad_tol_rel, o.max_polish, false); },
+          [&] { return S.rtr<double, float, 8>(XM_FP64, XM_FP32_BULK, o.grad_tol_rel, o.max_polish, false); }));
+      XM_CUDA_TRY(cudaMemcpyAsync(S.bY64, S.bY, sizeof(double) * elems, cudaMemcpyDeviceToDevice, st));
+    }
+    // ---- certificate (FP64 Lambda from the last FP64 gradient)
+    XM_TRY(with_R(R, [&] { return S.certify<4>(r, prec_z, &lam_def, &lam_max, &lam_range); },
+                     [&] { return S.certify<8>(r, prec_z, &lam_def, &lam_max, &lam_range); }));
+    const double tau = o.cert_tau_rel * std::max(std::fabs(lam_max), 1e-300);
+    certified = lam_def >= -tau;
+    if (o.verbose >= 1)
+      fprintf(stderr, "[xm] rank %d: f=%.12e |g|=%.3e lam_def=%.6e lam_rng=%.3e lam_max=%.6e %s\n", r,
+              S.info.f, std::sqrt(S.cur_g2), lam_def, lam_range, lam_max, certified ? "CERTIFIED" : "escape");
+    if (certified || certify_only) break;
+    if (S.timed_out) { result = XM_ENOCONV; break; }
+    if (r >= o.r_max) { result = XM_ENOTCERT; break; }
+    // ---- escape (Thm. 2): into a null column of Y if one exists, else one rank up
+    std::vector<double> gram(R * R);
+    XM_TRY(with_R(R,
+        [&] { k_gram<double, 4><<<S.grid_gram(), CAM_THREADS, 0, st>>>(nn, (const double*)S.bY64, S.d_small, ctx->d_partials, ctx->d_counter); return XM_OK; },
+        [&] { k_gram<double, 8><<<S.grid_gram(), CAM_THREADS, 0, st>>>(nn, (const double*)S.bY64, S.d_small, ctx->d_partials, ctx->d_counter); return XM_OK; }));
+    XM_CUDA_TRY(cudaMemcpyAsync(gram.data(), S.d_small, sizeof(double) * R * R, cudaMemcpyDeviceToHost, st));
+    XM_CUDA_TRY(cudaStreamSynchronize(st));
+    std::vector<double> gr((size_t)r * r), ew, EV;
+    for (int a = 0; a < r; ++a) for (int b = 0; b < r; ++b) gr[(size_t)a * r + b] = gram[a * R + b];
+    sym_eig_desc(r, gr, ew, EV);
+    int col;
+    if (ew[r - 1] < 1e-12 * ew[0]) {
+      std::vector<double> rot((size_t)R * R, 0.0);
+      for (int a = 0; a < R; ++a) for (int b = 0; b < R; ++b)
+        rot[(size_t)a * R + b] = (a < r && b < r) ? EV[(size_t)a * r + b] : (a == b ? 1.0 : 0.0);
+      XM_CUDA_TRY(cudaMemcpyAsync(S.d_small + 64, rot.data(), sizeof(double) * R * R, cudaMemcpyHostToDevice, st));
+      XM_TRY(with_R(R, [&] { k_rotate<4><<<(nn + 127) / 128, 128, 0, st>>>(nn, (double*)S.bY64, S.d_small + 64); return XM_OK; },
+                       [&] { k_rotate<8><<<(nn + 127) / 128, 128, 0, st>>>(nn, (double*)S.bY64, S.d_small + 64); return XM_OK; }));
+      col = r - 1;
+    } else {
+      const int Rn = (r + 1) <= 4 ? 4 : 8;
+      if (Rn != R) {
+        k_repad<double, double><<<S.grid_elems((size_t)nn * Rn), CAM_THREADS, 0, st>>>(nn, nn, (const double*)S.bY64, R, (double*)S.bYc, Rn);
+        XM_CUDA_TRY(cudaMemcpyAsync(S.bY64, S.bYc, sizeof(double) * (size_t)nn * Rn, cudaMemcpyDeviceToDevice, st));
+        R = Rn;
+        XM_TRY(S.clear_vecs());
+      }
+      col = r;
+      r += 1;
+    }
+    S.launches += 2;
+    k_set_col<<<S.grid_elems((size_t)nn * R), CAM_THREADS, 0, st>>>(n, nn, R, col, S.lritz, (double*)S.bXi);
+    // line search on f, FP64
+    const double f0 = S.info.f;
+    bool moved = false;
+    double alpha = 1.0;
+    for (int h = 0; h <= 30; ++h, alpha *= 0.5) {
+      XM_CUDA_TRY(cudaMemsetAsync(S.bWc, 0, S.vec_bytes, st));
+      XM_TRY(with_R(R,
+          [&] { k_retract<double, double, 4><<<S.nb_cam, CAM_THREADS, 0, st>>>(N, (const double*)S.bY64, (const double*)S.bXi, alpha, (double*)S.bYc);
+                return S.grad_at<double, 4>(XM_FP64, S.bYc, S.bWc, S.bGc, S.Lamc, 1, false); },
+          [&] { k_retract<double, double, 8><<<S.nb_cam, CAM_THREADS, 0, st>>>(N, (const double*)S.bY64, (const double*)S.bXi, alpha, (double*)S.bYc);
+                return S.grad_at<double, 8>(XM_FP64, S.bYc, S.bWc, S.bGc, S.Lamc, 1, false); }));
+      ++S.launches;
+      XM_TRY(S.pull_scalars());
+      if (S.h_sc->fc < f0) {
+        XM_CUDA_TRY(cudaMemcpyAsync(S.bY64, S.bYc, sizeof(double) * (size_t)nn * R, cudaMemcpyDeviceToDevice, st));
+        moved = true;
+        break;
+      }
+    }
+    ++S.info.n_escapes;
+    if (!moved) { result = XM_ENOTCERT; break; }
+  }
+
+  // ---- rounding, suboptimality
+  XM_TRY(with_R(R, [&] { return S.round_and_eval<4>(r, R_out, s_out); },
+                   [&] { return S.round_and_eval<8>(r, R_out, s_out); }));
+  if (Lambda_out) XM_CUDA_TRY(cudaMemcpyAsync(Lambda_out, S.Lam, sizeof(double) * 9 * N, cudaMemcpyDeviceToDevice, st));
+  if (v_out && S.lritz) XM_CUDA_TRY(cudaMemcpyAsync(v_out, S.lritz, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  if (Y_out) {
+    k_repad<double, double><<<S.grid_elems((size_t)n * XM_MAX_RANK), CAM_THREADS, 0, st>>>(
+        n, n, (const double*)S.bY64, R, Y_out, XM_MAX_RANK);
+    ++S.launches;
+  }
+  XM_CUDA_TRY(cudaStreamSynchronize(st));
+  XM_TRY(check_device_error(ctx, "solve"));
+
+  xm_info& I = S.info;
+  I.rank = r;
+  I.grad_norm = std::sqrt(S.cur_g2);
+  I.lambda_min_deflated = lam_def;
+  I.lambda_min = std::min(lam_def, lam_range);
+  I.lambda_max = lam_max;
+  I.certified = certified ? 1 : 0;
+  // dual value tr(Lambda_0)
+  double L0[9];
+  XM_CUDA_TRY(cudaMemcpy(L0, S.Lam, sizeof(L0), cudaMemcpyDeviceToHost));
+  I.dual = L0[0] + L0[4] + L0[8];
+  double y2 = 0;
+  {
+    XM_TRY(with_R(R,
+        [&] { k_gram<double, 4><<<S.grid_gram(), CAM_THREADS, 0, st>>>(nn, (const double*)S.bY64, S.d_small, ctx->d_partials, ctx->d_counter); return XM_OK; },
+        [&] { k_gram<double, 8><<<S.grid_gram(), CAM_THREADS, 0, st>>>(nn, (const double*)S.bY64, S.d_small, ctx->d_partials, ctx->d_counter); return XM_OK; }));
+    std::vector<double> g(R * R);
+    XM_CUDA_TRY(cudaMemcpy(g.data(), S.d_small, sizeof(double) * R * R, cudaMemcpyDeviceToHost));
+    for (int j = 0; j < R; ++j) y2 += g[j * R + j];
+  }
+  I.eta = suboptimality(I.rho_hat, I.f);
+  const double lower = I.dual + std::min(0.0, I.lambda_min) * y2;
+  I.eta_robust = suboptimality(I.rho_hat, lower);
+  I.qy_ms_fp32 = S.n32 ? S.ms32 / S.n32 : 0.0;
+  I.qy_ms_fp64 = S.n64 ? S.ms64 / S.n64 : 0.0;
+  I.t_solve_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - S.t_start).count();
+  g_last_launches = S.launches;
+  g_last_sweeps = S.info.n_sweeps;
+  if (out_info) *out_info = I;
+  if (result == XM_ENOTCERT)
+    return set_error(XM_ENOTCERT, "staircase stopped at rank %d without a certificate (lambda_min %.3e)", r, lam_def);
+  if (result == XM_ENOCONV) return set_error(XM_ENOCONV, "time limit reached");
+  return XM_OK;
+}
+
+// ====================================================================================== ABI
+xm_status build_Q(xm_ctx* ctx, int N, int M, int64_t E, const int32_t* cam, const int32_t* lmk,
+                  const double* ukp, const double* w, unsigned mask, DeviceQ& out,
+                  double* t_build);
+
+static xm_status check_opts(const DeviceQ& q, const xm_opts& o) {
+  if (o.r0 < 1 || o.r0 > XM_MAX_RANK || o.r_max < o.r0 || o.r_max > XM_MAX_RANK)
+    return set_error(XM_EINVAL, "opts: need 1 <= r0 <= r_max <= %d (r0=%d, r_max=%d)", XM_MAX_RANK,
+                     o.r0, o.r_max);
+  if (o.prec < XM_FP64 || o.prec > XM_BF16Q_BULK) return set_error(XM_EINVAL, "opts: bad prec %d", o.prec);
+  if (!q.q64) return set_error(XM_EINVAL, "solve: Q needs its FP64 copy (XM_STORE_FP64)");
+  if (o.prec != XM_FP64 && !q.q32) return set_error(XM_EINVAL, "solve: mixed precision needs XM_STORE_FP32");
+  if (o.prec == XM_BF16Q_BULK && !q.q16) return set_error(XM_EINVAL, "solve: XM_BF16Q_BULK needs XM_STORE_BF16");
+  if (o.max_outer < 1 || o.max_tcg < 1 || o.lanczos_max < 1)
+    return set_error(XM_EINVAL, "opts: iteration caps must be positive");
+  return XM_OK;
+}
+
+template <typename T>
+static xm_status qy_generic(xm_ctx* c, const DeviceQ& q, int prec, int r, const T* Y, T* W) {
+  const int R = r == 1 ? 1 : (r <= 4 ? 4 : 8);
+  cudaStream_t st = c->stream;
+  T *Yp = nullptr, *Wp = nullptr;
+  const size_t bytes = sizeof(T) * (size_t)q.n_pad * R;
+  XM_CUDA_TRY(cudaMallocAsync(&Yp, bytes, st));
+  XM_CUDA_TRY(cudaMallocAsync(&Wp, bytes, st));
+  const int g = (int)std::min<size_t>(((size_t)q.n_pad * R + 255) / 256, (size_t)c->num_sms * 8);
+  k_repad<T, T><<<g, 256, 0, st>>>(q.n, q.n_pad, Y, r, Yp, R);
+  XM_CUDA_TRY(cudaMemsetAsync(Wp, 0, bytes, st));
+  xm_status s = qy_launch(c, q, prec, R, Yp, Wp, nullptr, st);
+  if (s == XM_OK) {
+    const int g2 = (int)std::min<size_t>(((size_t)q.n * r + 255) / 256, (size_t)c->num_sms * 8);
+    k_repad<T, T><<<std::max(g2, 1), 256, 0, st>>>(q.n, q.n, Wp, R, W, r);
+  }
+  cudaFreeAsync(Yp, st);
+  cudaFreeAsync(Wp, st);
+  XM_CUDA_TRY(cudaGetLastError());
+  return s;
+}
+
+template <typename T>
+static xm_status bench_generic(xm_ctx* c, const DeviceQ& q, int prec, int r, int iters, double* ms_mean,
+                               double* ms_min) {
+  const int R = r == 1 ? 1 : (r <= 4 ? 4 : 8);
+  cudaStream_t st = c->stream;
+  T *Yp = nullptr, *Wp = nullptr;
+  const size_t bytes = sizeof(T) * (size_t)q.n_pad * R;
+  XM_CUDA_TRY(cudaMalloc(&Yp, bytes));
+  XM_CUDA_TRY(cudaMalloc(&Wp, bytes));
+  std::vector<T> hy((size_t)q.n_pad * R, T(0));
+  for (int i = 0; i < q.n; ++i)
+    for (int j = 0; j < r; ++j) hy[(size_t)i * R + j] = T(((i * 7 + j * 13) % 17) - 8) / T(8);
+  xm_status s = XM_OK;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double tot = 0.0, mn = 1e30;
+  if (cudaMemcpyAsync(Yp, hy.data(), bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    s = set_error(XM_ECUDA, "bench: copy failed");
+  for (int it = -3; it < iters && s == XM_OK; ++it) {
+    cudaMemsetAsync(Wp, 0, bytes, st);
+    cudaEventRecord(e0, st);
+    s = qy_launch(c, q, prec, R, Yp, Wp, nullptr, st);
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (it >= 0) { tot += ms; mn = std::min(mn, (double)ms); }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamSynchronize(st);
+  cudaFree(Yp);
+  cudaFree(Wp);
+  if (s != XM_OK) return s;
+  XM_TRY(check_device_error(c, "sweep benchmark"));
+  if (ms_mean) *ms_mean = iters > 0 ? tot / iters : 0.0;
+  if (ms_min) *ms_min = mn;
+  return XM_OK;
+}
+}  // namespace xm
+
+using namespace xm;
+extern "C" {
+
+xm_status xm_qy(xm_ctx* c, const xm_qmat* q, int prec, int r, const void* Y, void* W) {
+  if (!c || !q || !Y || !W) return set_error(XM_EINVAL, "xm_qy: NULL argument");
+  if (r < 1 || r > XM_MAX_RANK) return set_error(XM_EINVAL, "xm_qy: r=%d not in [1, %d]", r, XM_MAX_RANK);
+  XM_CUDA_TRY(cudaSetDevice(c->device));
+  if (prec == XM_FP64) return qy_generic<double>(c, q->d, prec, r, (const double*)Y, (double*)W);
+  return qy_generic<float>(c, q->d, prec, r, (const float*)Y, (float*)W);
+}
+
+xm_status xm_bench_qy(xm_ctx* c, const xm_qmat* q, int prec, int r, int iters, double* ms_mean,
+                      double* ms_min) {
+  if (!c || !q || iters < 0) return set_error(XM_EINVAL, "xm_bench_qy: bad argument");
+  if (r < 1 || r > XM_MAX_RANK) return set_error(XM_EINVAL, "xm_bench_qy: r=%d", r);
+  XM_CUDA_TRY(cudaSetDevice(c->device));
+  if (prec == XM_FP64) return bench_generic<double>(c, q->d, prec, r, iters, ms_mean, ms_min);
+  return bench_generic<float>(c, q->d, prec, r, iters, ms_mean, ms_min);
+}
+
+long xm_last_launch_count(void) { return g_last_launches; }
+
+xm_status xm_solve(xm_ctx* c, const xm_qmat* q, const xm_opts* opts, int r_in, const double* Y0,
+                   double* Y_out, double* R_out, double* s_out, xm_info* info) {
+  if (!c || !q) return set_error(XM_EINVAL, "xm_solve: NULL context or Q");
+  xm_opts o;
+  if (opts) o = *opts; else xm_default_opts(&o);
+  if (Y0 && (r_in < 1 || r_in > XM_MAX_RANK)) return set_error(XM_EINVAL, "xm_solve: r_in=%d", r_in);
+  if (Y0 && r_in > o.r_max) o.r_max = r_in;
+  XM_TRY(check_opts(q->d, o));
+  XM_CUDA_TRY(cudaSetDevice(c->device));
+  return solve_impl(c, q->d, o, r_in, Y0, Y_out, R_out, s_out, info, false, nullptr, nullptr);
+}
+
+xm_status xm_certify(xm_ctx* c, const xm_qmat* q, const xm_opts* opts, int r, const double* Y,
+                     double* Lambda_out, double* v_out, xm_info* info) {
+  if (!c || !q || !Y) return set_error(XM_EINVAL, "xm_certify: NULL argument");
+  if (r < 1 || r > XM_MAX_RANK) return set_error(XM_EINVAL, "xm_certify: r=%d", r);
+  xm_opts o;
+  if (opts) o = *opts; else xm_default_opts(&o);
+  o.r0 = r;
+  o.r_max = r;
+  XM_TRY(check_opts(q->d, o));
+  XM_CUDA_TRY(cudaSetDevice(c->device));
+  return solve_impl(c, q->d, o, r, Y, nullptr, nullptr, nullptr, info, true, Lambda_out, v_out);
+}
+
+xm_status xm_pipeline_host(xm_ctx* c, int N, int M, int64_t E, const int32_t* cam_h,
+                           const int32_t* lmk_h, const double* ukp_h, const double* w_h,
+                           const xm_opts* opts, double* R_h, double* s_h, xm_info* info) {
+  if (!c || !cam_h || !lmk_h || !ukp_h || !w_h || !R_h || !s_h || E < 0 || N < 1)
+    return set_error(XM_EINVAL, "xm_pipeline_host: bad argument");
+  xm_opts o;
+  if (opts) o = *opts; else xm_default_opts(&o);
+  XM_CUDA_TRY(cudaSetDevice(c->device));
+  cudaStream_t st = c->stream;
+  unsigned mask = XM_STORE_FP64;
+  if (o.prec != XM_FP64) mask |= XM_STORE_FP32;
+  if (o.prec == XM_BF16Q_BULK) mask |= XM_STORE_BF16;
+  int32_t *cam = nullptr, *lmk = nullptr;
+  double *ukp = nullptr, *w = nullptr, *R = nullptr, *s = nullptr;
+  auto cleanup = [&]() {
+    if (cam) cudaFree(cam);
+    if (lmk) cudaFree(lmk);
+    if (ukp) cudaFree(ukp);
+    if (w) cudaFree(w);
+    if (R) cudaFree(R);
+    if (s) cudaFree(s);
+  };
+  auto t0 = std::chrono::steady_clock::now();
+  cudaError_t e = cudaSuccess;
+  const size_t Ez = (size_t)(E > 0 ? E : 1);
+  e = cudaMalloc(&cam, sizeof(int32_t) * Ez);
+  if (e == cudaSuccess) e = cudaMalloc(&lmk, sizeof(int32_t) * Ez);
+  if (e == cudaSuccess) e = cudaMalloc(&ukp, sizeof(double) * 3 * Ez);
+  if (e == cudaSuccess) e = cudaMalloc(&w, sizeof(double) * Ez);
+  if (e == cudaSuccess) e = cudaMalloc(&R, sizeof(double) * 9 * (size_t)N);
+  if (e == cudaSuccess) e = cudaMalloc(&s, sizeof(double) * (size_t)N);
+  if (e == cudaSuccess && E > 0) e = cudaMemcpyAsync(cam, cam_h, sizeof(int32_t) * E, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && E > 0) e = cudaMemcpyAsync(lmk, lmk_h, sizeof(int32_t) * E, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && E > 0) e = cudaMemcpyAsync(ukp, ukp_h, sizeof(double) * 3 * E, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && E > 0) e = cudaMemcpyAsync(w, w_h, sizeof(double) * E, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) {
+    cleanup();
+    return set_error(e == cudaErrorMemoryAllocation ? XM_ENOMEM : XM_ECUDA, "xm_pipeline_host: %s",
+                     cudaGetErrorString(e));
+  }
+  xm_qmat* q = nullptr;
+  xm_status stt = xm_build_Q(c, N, M, E, cam, lmk, ukp, w, mask, &q);
+  xm_info inf{};
+  if (stt == XM_OK) {
+    stt = xm_solve(c, q, &o, 0, nullptr, nullptr, R, s, &inf);
+    inf.t_build_s = q->t_build_s;
+    if (stt == XM_OK || stt == XM_ENOTCERT) {
+      cudaError_t e2 = cudaMemcpyAsync(R_h, R, sizeof(double) * 9 * N, cudaMemcpyDeviceToHost, st);
+      if (e2 == cudaSuccess) e2 = cudaMemcpyAsync(s_h, s, sizeof(double) * N, cudaMemcpyDeviceToHost, st);
+      if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(st);
+      if (e2 != cudaSuccess) stt = set_error(XM_ECUDA, "xm_pipeline_host: %s", cudaGetErrorString(e2));
+    }
+    xm_free_Q(c, q);
+  }
+  cleanup();
+  inf.t_solve_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (info) *info = inf;
+  return stt;
+}
+
+}  // extern "C"

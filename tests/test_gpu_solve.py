@@ -1,0 +1,126 @@
+"""End-to-end parity of the CUDA solver (Alg. 1 + RTR-tCG + certificate + rounding) with the
+FP64 oracle, in every precision mode.  Compared quantities are gauge invariant: the objective,
+the certificate decision and gap, and the rounded rotations / scales in the anchored gauge.
+Tolerances: relative objective 1e-6 (1 + |f| denominator) for the FP64 path and the mixed
+modes (both end with an FP64 polish and an FP64 certificate)."""
+import numpy as np
+import pytest
+
+import scenes
+from oracle import xm_oracle as O
+from tests.gpu_util import ctx, torch
+
+pytestmark = pytest.mark.gpu
+
+PRECS = {"fp64": 0, "fp32": 1, "bf16": 2}
+
+
+@pytest.fixture(scope="module")
+def C():
+    c = ctx()
+    yield c
+    c.close()
+
+
+def _solve(C, sc, prec, **kw):
+    from paper_2502_04640_b300 import xm
+    q = xm.xm_build_Q(C, sc.N, sc.M, *xm.scene_tensors(sc))
+    opts = xm.xm_default_opts(prec=prec, **kw)
+    out = xm.xm_solve(q, opts)
+    out["R"] = out["R"].cpu().numpy(); out["s"] = out["s"].cpu().numpy(); out["Y"] = out["Y"].cpu().numpy()
+    return q, out
+
+
+def _rel(a, b):
+    return abs(a - b) / (1.0 + abs(b))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
+def test_config1_matches_oracle(C, prec):
+    sc = scenes.config1()
+    Qo = O.build_Q_schur(sc.N, sc.M, sc.cam, sc.lmk, sc.ukp, sc.w)
+    ref = O.solve(Qo, r0=4)
+    q, out = _solve(C, sc, PRECS[prec])
+    info = out["info"]
+    assert out["status"] == 0 and info["certified"] == 1 and ref.certified
+    assert _rel(info["f"], ref.f) <= 1e-6
+    assert _rel(info["rho_hat"], ref.rho_hat) <= 1e-6
+    assert abs(info["dual"] - ref.cert.dual) <= 1e-6 * (1 + abs(ref.f))
+    assert abs(info["lambda_min_deflated"] - ref.cert.lam_min_deflated) <= 1e-4 * ref.cert.lam_max_Q
+    assert np.abs(out["R"] - ref.R).max() <= 1e-5
+    assert np.abs(out["s"] - ref.s).max() <= 1e-5 * ref.s.max()
+    assert info["n_escapes"] >= 1     # the [I..I] start needs the escape of Thm. 2
+    q.free()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_noise_free_recovery(C, prec):
+    sc = scenes.circle_scene(40, 600, 4, 0.0, seed=11)
+    q, out = _solve(C, sc, PRECS[prec])
+    R, s, _, _ = sc.anchored_gt()
+    info = out["info"]
+    assert info["certified"] == 1
+    assert abs(info["f"]) <= 1e-8 * np.sum(sc.w * np.sum(sc.ukp ** 2, 1))
+    assert np.abs(out["R"] - R).max() <= 1e-6 and np.abs(out["s"] - s).max() <= 1e-6
+    q.free()
+
+
+def test_two_views_umeyama(C):
+    sc = scenes.circle_scene(2, 60, 2, 0.05, seed=17, w_range=(0.5, 1.5))
+    q, out = _solve(C, sc, 0)
+    x = np.zeros((sc.M, 3)); y = np.zeros((sc.M, 3)); w1 = np.zeros(sc.M); w2 = np.zeros(sc.M)
+    for e in range(sc.E):
+        if sc.cam[e] == 0:
+            y[sc.lmk[e]] = sc.ukp[e]; w1[sc.lmk[e]] = sc.w[e]
+        else:
+            x[sc.lmk[e]] = sc.ukp[e]; w2[sc.lmk[e]] = sc.w[e]
+    s, R, t, c = O.umeyama_weighted(x, y, w1 * w2 / (w1 + w2))
+    assert out["info"]["certified"] == 1
+    assert _rel(out["info"]["rho_hat"], c) <= 1e-8
+    assert np.abs(out["R"][1] - R).max() <= 1e-6 and abs(out["s"][1] - s) <= 1e-6
+    q.free()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_outliers_and_tiles_match_oracle(C, prec):
+    sc = scenes.random_scene(90, 4000, noise=0.03, outlier_frac=0.05, seed=21)
+    Qo = O.build_Q_schur(sc.N, sc.M, sc.cam, sc.lmk, sc.ukp, sc.w)
+    ref = O.solve(Qo, r0=4)
+    q, out = _solve(C, sc, PRECS[prec])
+    info = out["info"]
+    assert info["certified"] == int(ref.certified)
+    assert _rel(info["f"], ref.f) <= 1e-6
+    if ref.certified:
+        assert _rel(info["rho_hat"], ref.rho_hat) <= 1e-6
+    q.free()
+
+
+def test_certify_entry_point_matches_oracle(C):
+    from paper_2502_04640_b300 import xm
+    sc = scenes.config1()
+    Qo = O.build_Q_schur(sc.N, sc.M, sc.cam, sc.lmk, sc.ukp, sc.w)
+    ref = O.solve(Qo, r0=4)
+    q = xm.xm_build_Q(C, sc.N, sc.M, *xm.scene_tensors(sc))
+    out = xm.xm_certify(q, torch.tensor(ref.Y, device="cuda"), xm.xm_default_opts(prec=0))
+    Lam = out["Lambda"].cpu().numpy()
+    cert = O.certify(Qo, ref.Y)
+    assert np.abs(Lam - cert.Lambda).max() <= 1e-8 * np.abs(cert.Lambda).max()
+    assert abs(out["info"]["lambda_min_deflated"] - cert.lam_min_deflated) <= 1e-5 * cert.lam_max_Q
+    assert out["info"]["certified"] == 1
+    # at the rank-3 local optimum of the [I..I] start the certificate fails (Thm. 2)
+    r3 = O.rtr(Qo, O.initial_point(sc.N, 3))
+    bad = xm.xm_certify(q, torch.tensor(r3.Y, device="cuda"), xm.xm_default_opts(prec=0))
+    c3 = O.certify(Qo, r3.Y)
+    assert bad["info"]["certified"] == 0
+    assert abs(bad["info"]["lambda_min_deflated"] - c3.lam_min_deflated) <= 1e-5 * c3.lam_max_Q
+    q.free()
+
+
+def test_pipeline_from_host_arrays(C):
+    from paper_2502_04640_b300 import xm
+    sc = scenes.config1()
+    ref = O.solve(O.build_Q_schur(sc.N, sc.M, sc.cam, sc.lmk, sc.ukp, sc.w), r0=4)
+    R, s, info, st = xm.xm_pipeline_host(C, sc.N, sc.M, sc.cam, sc.lmk, sc.ukp, sc.w,
+                                         xm.xm_default_opts(prec=1))
+    assert st == 0 and info["certified"] == 1
+    assert np.abs(R - ref.R).max() <= 1e-5 and np.abs(s - ref.s).max() <= 1e-5 * ref.s.max()
