@@ -1,0 +1,336 @@
+"""Benchmark: time-to-certified-solve of XM on the 10155-camera workload (Q resident in HBM),
+with the Q.Y sweep's achieved HBM bandwidth, the FP32-bulk vs FP64 comparison, an
+end-to-end number from pinned host arrays through the C ABI, and the FP64 oracle timed on the
+host cores.  Prints one JSON line (rank 0).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c3] [--prec fp32]
+    python bench.py --impl reference ...      # the oracle on the host cores, same metric/unit
+
+A "step" is one certified solve (Alg. 1 + RTR-tCG + certificate + rounding) from the
+[I, ..., I] start on a Q already built on the device.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import scenes  # noqa: E402
+
+METRIC = "time-to-certified-solve (s) at 10k cams; Q·Y GB/s vs HBM peak, FP32 vs FP64"
+WORKLOADS = {
+    "c3": (scenes.config3, 10155, "10155 cameras, 1.5M landmarks, ~7.5M observations, track "
+                                  "2+Geom(1/4), 5% outliers, noise N(0,0.02^2), w~U[0.5,1]; BM rank "
+                                  "4 start with staircase"),
+    "c2": (scenes.config2, 1934, "1934 cameras, 300k landmarks, ~1.5M observations, 2% outliers"),
+    "c4": (scenes.config4, 2000, "2000-frame indoor trajectory, 400k landmarks, multiplicative depth noise"),
+    "c1": (scenes.config1, 20, "20 cameras on a circle, 200 landmarks x 4 observers"),
+}
+PRECS = {"fp64": 0, "fp32": 1, "bf16": 2}
+DTYPES = {"fp64": "f64", "fp32": "f32", "bf16": "bf16/f32"}
+# Sweeps of one certified FP32-bulk solve of the 10155-camera workload as measured on a B300 by
+# the GPU arm of this benchmark; the reference arm multiplies the oracle's time per sweep by it.
+REFERENCE_SWEEPS = {"c3": 1000, "c2": 500, "c4": 500, "c1": 300}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampled every 200 ms while the timed region runs."""
+
+    def __init__(self, index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1])); mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def sweep_bytes(n: int, r: int, bq: int, by: int) -> float:
+    """Algorithmic bytes of one sweep: the unique entries of symmetric Q plus Y read and W written."""
+    return n * (n + 1) / 2 * bq + 2 * n * r * by
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_sweep_seconds(n: int, r: int, reps: int = 2, seed: int = 0) -> float:
+    """Host time of one oracle sweep (dense FP64 Q @ Y plus the oracle's per-camera dual blocks
+    and tangent projection) at size n.  Q's values do not change the time of a dense product; a
+    seeded random symmetric matrix of the workload's size is used."""
+    from oracle import xm_oracle as O
+    rng = np.random.default_rng(seed)
+    Q = rng.standard_normal((n, n))
+    Q += Q.T
+    Y = O.initial_point(n // 3, r)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        G = Q @ Y
+        L = O.lambdas(Y, G)
+        O.proj_tangent(Y, 2.0 * (G - O.apply_blockdiag(L, Y)))
+    return (time.perf_counter() - t0) / reps
+
+
+def run_reference(args):
+    """The oracle as it stands on the host cores: each step times one oracle sweep at the
+    workload's size; the value is that time per sweep times the sweeps of one certified solve."""
+    if int(os.environ.get("RANK", "0")) != 0:
+        return 0
+    _, N, desc = WORKLOADS[args.workload]
+    n = 3 * N
+    S = REFERENCE_SWEEPS[args.workload]
+    times = []
+    for i in range(args.warmup + args.steps):
+        dt = oracle_sweep_seconds(n, 4, reps=1, seed=i)
+        if i >= args.warmup:
+            times.append(dt)
+    per = statistics.mean(times)
+    value = per * S
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {desc}", "prec": "fp64 (oracle)"},
+        "cpu_baseline": {"value": value, "unit": "s", "cores": host_cores(), "kind": "oracle",
+                         "sample": f"one oracle sweep (dense FP64 Q@Y, n={n}, r=4, plus dual blocks "
+                                   f"and projection) per step, times {S} sweeps of a certified solve"},
+        "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS))
+    ap.add_argument("--prec", default="fp32", choices=sorted(PRECS))
+    ap.add_argument("--impl", default="xm", choices=["xm", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--no-compare", action="store_true", help="skip the FP64 / BF16 comparison solves")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_2502_04640_b300 import xm
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
+
+    mk, _, desc = WORKLOADS[args.workload]
+    sc = mk()    # every replica solves the same synthetic scene (replicas only: no exchange)
+    ctx = xm.Context(local)
+    prec = PRECS[args.prec]
+    cam, lmk, ukp, w = xm.scene_tensors(sc, local)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    q = xm.xm_build_Q(ctx, sc.N, sc.M, cam, lmk, ukp, w, xm.XM_STORE_ALL)
+    torch.cuda.synchronize()
+    t_build = time.perf_counter() - t0
+    del cam, lmk, ukp, w
+    torch.cuda.empty_cache()
+    opts = xm.xm_default_opts(prec=prec)
+    stream = ctx.stream
+
+    for _ in range(args.warmup):
+        xm.xm_solve(q, opts)
+    # ---- timed region: exactly K certified solves
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    wall0 = time.perf_counter()
+    launches = 0
+    timed = []
+    out = None
+    for _ in range(args.steps):
+        out = xm.xm_solve(q, opts)
+        launches += xm.xm_last_launch_count()
+        timed.append(out["info"])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    dev_s = ev0.elapsed_time(ev1) / 1e3
+    total = max(dev_s, wall)
+    if dist:
+        t = torch.tensor([total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total = float(t.item())
+    value = total / (args.steps * world)
+    info = timed[-1]
+    certified = all(i["certified"] for i in timed)
+
+    # ---- roofline of the dominant kernel, from the sweeps timed live inside the solves
+    n = q.n
+    key = "qy_ms_fp64" if prec == 0 else "qy_ms_fp32"
+    live = [i[key] for i in timed if i[key] > 0]
+    qy_ms = statistics.mean(live) if live else float("nan")
+    bq, by = (8, 8) if prec == 0 else (4, 4)
+    alg = sweep_bytes(n, 4, bq, by)
+    peak, peak_kind = peaks()
+    achieved = alg / (qy_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm" if prec != 0 else "alu", "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                "kernel": f"qy_packed_kernel<{'double' if prec == 0 else 'float'},4,8>",
+                "bytes_per_launch": alg, "launch_ms": qy_ms, "peak_kind": peak_kind}
+
+    extra = {}
+    if rank == 0 and not args.no_compare:
+        # plain FP64 GPU form and the BF16-Q trial, one solve each, errors against the FP64 run
+        ref = xm.xm_solve(q, xm.xm_default_opts(prec=0))
+        fi = ref["info"]
+        extra["fp64_solve_s"] = fi["t_solve_s"]
+        extra["fp64_certified"] = fi["certified"]
+        extra["fp64_sweeps"] = fi["n_sweeps"]
+
+        def errs(o):
+            return {"f_rel": abs(o["info"]["f"] - fi["f"]) / (1 + abs(fi["f"])),
+                    "rho_hat_rel": abs(o["info"]["rho_hat"] - fi["rho_hat"]) / (1 + abs(fi["rho_hat"])),
+                    "lambda_min_abs": abs(o["info"]["lambda_min_deflated"] - fi["lambda_min_deflated"]),
+                    "R_max_abs": float((o["R"] - ref["R"]).abs().max()),
+                    "s_max_rel": float(((o["s"] - ref["s"]).abs() / ref["s"].abs()).max())}
+        extra["fp32_vs_fp64"] = errs(out)
+        if prec != 2:
+            b = xm.xm_solve(q, xm.xm_default_opts(prec=2))
+            extra["bf16q_solve_s"] = b["info"]["t_solve_s"]
+            extra["bf16q_certified"] = b["info"]["certified"]
+            extra["bf16q_vs_fp64"] = errs(b)
+        for pname, pv in (("fp32", 1), ("bf16", 2), ("fp64", 0)):
+            mean_ms, _ = xm.xm_bench_qy(q, pv, 4, 10)
+            bqq = {1: 4, 2: 2, 0: 8}[pv]
+            byy = 8 if pv == 0 else 4
+            extra[f"qy_{pname}_r4_ms"] = mean_ms
+            extra[f"qy_{pname}_r4_GBps"] = sweep_bytes(n, 4, bqq, byy) / (mean_ms * 1e-3) / 1e9
+
+    # ---- end to end through the C ABI from pinned host arrays (H2D, build, solve, D2H)
+    e2e = None
+    q.free()
+    if rank == 0 and args.e2e_steps > 0:
+        def pin(a, dt):
+            return torch.from_numpy(np.ascontiguousarray(a)).to(dt).pin_memory()
+        hc, hl = pin(sc.cam, torch.int32), pin(sc.lmk, torch.int32)
+        hu, hw = pin(sc.ukp, torch.float64), pin(sc.w, torch.float64)
+        Rh = torch.zeros((sc.N, 3, 3), dtype=torch.float64).pin_memory()
+        sh = torch.zeros(sc.N, dtype=torch.float64).pin_memory()
+        torch.cuda.synchronize()
+        te = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            xm.xm_pipeline_host_ptrs(ctx, sc.N, sc.M, hc, hl, hu, hw, opts, Rh, sh)
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - te) / args.e2e_steps
+        e2e = {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(sc.E * (4 + 4 + 24 + 8)),
+               "d2h_bytes_per_step": int(sc.N * (72 + 8))}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        dt = oracle_sweep_seconds(n, 4, reps=2)
+        S = int(info["n_sweeps"])
+        cpu = {"value": dt * S, "unit": "s", "cores": host_cores(), "kind": "oracle",
+               "sample": f"two oracle sweeps (dense FP64 Q@Y, n={n}, r=4, dual blocks, projection) "
+                         f"timed, times the {S} sweeps of this certified solve"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": value * 1e3 * world, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[args.prec], "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {desc}", "prec": args.prec,
+                       "replicas": world, "l2": "inputs larger than L2 (packed FP32 Q "
+                       f"{n * (n + 1) / 2 * 4 / 1e9:.2f} GB > 126 MB)", "N": sc.N, "M": sc.M, "E": sc.E},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk,
+            "certified": certified,
+            "solve": {k: info[k] for k in ("f", "grad_norm", "lambda_min", "lambda_min_deflated",
+                                           "lambda_max", "dual", "rho_hat", "eta", "eta_robust", "rank",
+                                           "n_sweeps", "n_sweeps_fp64", "n_outer", "n_tcg",
+                                           "n_lanczos", "n_escapes", "t_cert_s")},
+            "build_q_s": t_build,
+            **extra,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    ctx.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
