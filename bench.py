@@ -126,6 +126,18 @@ def oracle_sweep_seconds(n: int, r: int, reps: int = 2, seed: int = 0) -> float:
     return (time.perf_counter() - t0) / reps
 
 
+def whole_job_seconds(local_total: float, steps: int, world: int, dist=None, device=None) -> float:
+    """Replicas only: every rank solves its own copy; the job's time is the slowest rank's timed
+    region (max over ranks) and the value is that time over all solves of all ranks."""
+    total = float(local_total)
+    if dist is not None and world > 1:
+        import torch
+        t = torch.tensor([total], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total = float(t.item())
+    return total / (steps * world)
+
+
 def run_reference(args):
     """The oracle as it stands on the host cores: each step times one oracle sweep at the
     workload's size; the value is that time per sweep times the sweeps of one certified solve."""
@@ -225,12 +237,7 @@ def main():
         dist.barrier()
     clk = clocks.stop()
     dev_s = ev0.elapsed_time(ev1) / 1e3
-    total = max(dev_s, wall)
-    if dist:
-        t = torch.tensor([total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total = float(t.item())
-    value = total / (args.steps * world)
+    value = whole_job_seconds(max(dev_s, wall), args.steps, world, dist, dev)
     info = timed[-1]
     certified = all(i["certified"] for i in timed)
 
