@@ -220,7 +220,7 @@ k_grad_epi(int N, const T* __restrict__ Y, T* __restrict__ W, T* __restrict__ G,
 template <typename To, typename Ti, int R>
 __global__ void __launch_bounds__(CAM_THREADS)
 k_tcg_init(int n_rows, const To* __restrict__ G, Ti* eta, Ti* Heta, Ti* r, Ti* delta, Scal* sc,
-           double Delta, int max_iters, double theta, double kappa_tol) {
+           double g2, double Delta, int max_iters, double theta, double kappa_tol) {
   const size_t total = (size_t)n_rows * R;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
        e += (size_t)gridDim.x * blockDim.x) {
@@ -228,11 +228,13 @@ k_tcg_init(int n_rows, const To* __restrict__ G, Ti* eta, Ti* Heta, Ti* r, Ti* d
     eta[e] = Ti(0); Heta[e] = Ti(0); r[e] = g; delta[e] = -g;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
+    // g2 = ||grad||^2 of the current point, passed by the host (after an accepted step the
+    // device holds it in the candidate slot, not in sc->g2)
     sc->Delta = Delta;
-    sc->rr = sc->g2;
-    sc->r0 = sqrt(sc->g2);
-    sc->ee = 0.0; sc->ed = 0.0; sc->dd = sc->g2;
-    sc->done = sc->g2 > 0.0 ? 0 : 1;
+    sc->rr = g2;
+    sc->r0 = sqrt(g2);
+    sc->ee = 0.0; sc->ed = 0.0; sc->dd = g2;
+    sc->done = g2 > 0.0 ? 0 : 1;
     sc->stop_after = 0; sc->iters = 0; sc->max_iters = max_iters; sc->reason = 0;
     sc->theta = theta; sc->kappa_tol = kappa_tol;
   }

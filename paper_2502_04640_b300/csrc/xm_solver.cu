@@ -302,8 +302,8 @@ struct Solver {
         Yin = (const Ti*)bY;
       }
       k_tcg_init<To, Ti, R><<<grid_elems(rows * R), CAM_THREADS, 0, st>>>(
-          (int)rows, (const To*)bG, (Ti*)bEta, (Ti*)bHeta, (Ti*)bR, (Ti*)bD, d_sc, Delta, o.max_tcg,
-          1.0, 0.1);
+          (int)rows, (const To*)bG, (Ti*)bEta, (Ti*)bHeta, (Ti*)bR, (Ti*)bD, d_sc, g2, Delta,
+          o.max_tcg, 1.0, 0.1);
       ++launches;
       XM_CUDA_TRY(cudaGetLastError());
       const int CH = 4;
@@ -701,12 +701,19 @@ xm_status solve_impl(xm_ctx* ctx, const DeviceQ& q, const xm_opts& o, int r_in, 
     XM_TRY(with_R(R, [&] { return S.certify<4>(r, prec_z, &lam_def, &lam_max, &lam_range); },
                      [&] { return S.certify<8>(r, prec_z, &lam_def, &lam_max, &lam_range); }));
     const double tau = o.cert_tau_rel * std::max(std::fabs(lam_max), 1e-300);
-    certified = lam_def >= -tau;
+    // Thm. 1 needs a first-order critical point: with Lambda in closed form the duality gap
+    // f - tr(Lambda_0) = <Y, Z Y> vanishes exactly there, so it is checked beside lambda_min.
+    double L0g[9];
+    XM_CUDA_TRY(cudaMemcpy(L0g, S.Lam, sizeof(L0g), cudaMemcpyDeviceToHost));
+    const double gap = S.info.f - (L0g[0] + L0g[4] + L0g[8]);
+    const bool stationary = std::fabs(gap) <= 1e-6 * (1.0 + std::fabs(S.info.f));
+    certified = lam_def >= -tau && stationary;
     if (o.verbose >= 1)
-      fprintf(stderr, "[xm] rank %d: f=%.12e |g|=%.3e lam_def=%.6e lam_rng=%.3e lam_max=%.6e %s\n", r,
-              S.info.f, std::sqrt(S.cur_g2), lam_def, lam_range, lam_max, certified ? "CERTIFIED" : "escape");
+      fprintf(stderr, "[xm] rank %d: f=%.12e |g|=%.3e gap=%.3e lam_def=%.6e lam_rng=%.3e lam_max=%.6e %s\n",
+              r, S.info.f, std::sqrt(S.cur_g2), gap, lam_def, lam_range, lam_max,
+              certified ? "CERTIFIED" : "escape");
     if (certified || certify_only) break;
-    if (S.timed_out) { result = XM_ENOCONV; break; }
+    if (S.timed_out || (lam_def >= -tau && !stationary)) { result = XM_ENOCONV; break; }
     if (r >= o.r_max) { result = XM_ENOTCERT; break; }
     // ---- escape (Thm. 2): into a null column of Y if one exists, else one rank up
     std::vector<double> gram(R * R);
@@ -807,7 +814,8 @@ xm_status solve_impl(xm_ctx* ctx, const DeviceQ& q, const xm_opts& o, int r_in, 
   if (out_info) *out_info = I;
   if (result == XM_ENOTCERT)
     return set_error(XM_ENOTCERT, "staircase stopped at rank %d without a certificate (lambda_min %.3e)", r, lam_def);
-  if (result == XM_ENOCONV) return set_error(XM_ENOCONV, "time limit reached");
+  if (result == XM_ENOCONV)
+    return set_error(XM_ENOCONV, "not converged: time limit, or iteration caps hit before a stationary point");
   return XM_OK;
 }
 

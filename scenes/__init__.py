@@ -93,13 +93,17 @@ def _distinct_observers(rng, N: int, L: np.ndarray):
     cams, lmks = [], []
     for Lv in np.unique(L):
         idx = np.nonzero(L == Lv)[0]
-        rows = rng.integers(0, N, size=(idx.size, Lv))
-        while Lv > 1:
-            srt = np.sort(rows, axis=1)
-            bad = np.nonzero((srt[:, 1:] == srt[:, :-1]).any(axis=1))[0]
-            if bad.size == 0:
-                break
-            rows[bad] = rng.integers(0, N, size=(bad.size, Lv))
+        if Lv * Lv > N:
+            # long tracks relative to N: the first Lv entries of a random permutation per row
+            rows = np.argsort(rng.random((idx.size, N)), axis=1)[:, :Lv]
+        else:
+            rows = rng.integers(0, N, size=(idx.size, Lv))
+            while Lv > 1:
+                srt = np.sort(rows, axis=1)
+                bad = np.nonzero((srt[:, 1:] == srt[:, :-1]).any(axis=1))[0]
+                if bad.size == 0:
+                    break
+                rows[bad] = rng.integers(0, N, size=(bad.size, Lv))
         cams.append(rows.ravel())
         lmks.append(np.repeat(idx, Lv))
     if not cams:
