@@ -51,6 +51,22 @@ __device__ __forceinline__ void load4(const double* p, double (&q)[4]) {
   q[0] = a.x; q[1] = a.y; q[2] = b.x; q[3] = b.y;
 }
 
+// Packed FP32 pair arithmetic (fma.rn.f32x2, sm_100 and later): two FMAs per instruction.
+__device__ __forceinline__ unsigned long long pk(float x, float y) {
+  unsigned long long u;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(u) : "f"(x), "f"(y));
+  return u;
+}
+__device__ __forceinline__ void upk(unsigned long long u, float& x, float& y) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(u));
+}
+__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b,
+                                                    unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
 // Butterfly transpose-reduce of V <= 32 per-lane values: afterwards lane l holds the
 // warp-wide sum of value index l * V / 32 (lanes sharing that index hold the same sum).
 template <int V, typename T>
@@ -85,7 +101,11 @@ struct SweepCfg {
   static constexpr int NCHUNK = RPW / CHUNK;
   static constexpr int V = CHUNK * R;
   static constexpr int THREADS = 32 * (NW + 1);
-  static constexpr size_t YSM_BYTES = sizeof(A) * TILE * R;
+  // FP32 accumulation with R >= 2 uses packed pairs; Y_I is then staged as duplicated pairs
+  static constexpr bool PAIR = sizeof(A) == 4 && R >= 2;
+  // row partials kept per tile row (reduced across lanes once per tile row) when they fit
+  static constexpr bool DEFER = PAIR && SLABS * RPW * R <= 64;
+  static constexpr size_t YSM_BYTES = sizeof(A) * TILE * R * (PAIR ? 2 : 1);
   static constexpr size_t RED_BYTES = sizeof(A) * NW * TILE * R;
   static size_t smem_bytes(int nstage) {
     return 128 + (size_t)nstage * SLAB_BYTES + YSM_BYTES + RED_BYTES + 16 * (size_t)nstage;
@@ -162,27 +182,64 @@ qy_packed_kernel(const TQ* __restrict__ tiles, int nt, int64_t ntiles, int nstag
   // ---------------- consumers
   const int ctid = threadIdx.x;            // 0 .. 32*NW-1
   constexpr int NCT = 32 * NW;
-  A yj[4][R];
-  A colacc[4][R];
-  A rowacc[C::SLABS][C::NCHUNK];
+  constexpr int RH = C::PAIR ? R / 2 : 1;  // j-pairs per row
   int curI = -1;
   int I = I0, J = J0;
   int stage = 0;
   uint32_t phase = 0;
   bool ok = true;
 
+  // scalar-path state
+  A yj[4][R];
+  A colacc[4][R];
+  A rowacc[C::SLABS][C::NCHUNK];
+  // pair-path state: column pairs over c, Y_J pairs over j, row pairs over j
+  unsigned long long colp[2][R];
+  unsigned long long yjp[4][RH];
+  unsigned long long rowp[C::DEFER ? C::SLABS : 1][C::DEFER ? C::RPW : 1][RH];
+
+  // Reduce this lane's row partials of slab s across the warp and add them to W_I.
+  auto reduce_add_rows = [&](int Irow, int s, A (&vals)[C::RPW * R]) {
+#pragma unroll
+    for (int ch = 0; ch < C::NCHUNK; ++ch) {
+      A v[C::V];
+#pragma unroll
+      for (int e = 0; e < C::V; ++e) v[e] = vals[ch * C::V + e];
+      const A x = transpose_reduce<C::V>(v, lane);
+      constexpr int DUP = 32 / C::V;
+      if ((lane & (DUP - 1)) == 0) {
+        const int idx = lane / DUP;
+        const int k = idx / R, j = idx % R;
+        const int row = s * C::ROWS + warp * C::RPW + ch * C::CHUNK + k;
+        atomicAdd(&W[((size_t)Irow * TILE + row) * R + j], x);
+      }
+    }
+  };
+
   auto flush_rows = [&](int Irow) {
-    constexpr int DUP = 32 / C::V;         // lanes sharing one butterfly result
-    if ((lane & (DUP - 1)) == 0) {
-      const int idx = lane / DUP;           // value index within a chunk
-      const int k = idx / R, j = idx % R;
+    if constexpr (C::DEFER) {
 #pragma unroll
-      for (int s = 0; s < C::SLABS; ++s)
+      for (int s = 0; s < C::SLABS; ++s) {
+        A vals[C::RPW * R];
 #pragma unroll
-        for (int c = 0; c < C::NCHUNK; ++c) {
-          const int row = s * C::ROWS + warp * C::RPW + c * C::CHUNK + k;
-          atomicAdd(&W[((size_t)Irow * TILE + row) * R + j], rowacc[s][c]);
-        }
+        for (int k = 0; k < C::RPW; ++k)
+#pragma unroll
+          for (int jp = 0; jp < RH; ++jp) upk(rowp[s][k][jp], vals[k * R + 2 * jp], vals[k * R + 2 * jp + 1]);
+        reduce_add_rows(Irow, s, vals);
+      }
+    } else {
+      constexpr int DUP = 32 / C::V;         // lanes sharing one butterfly result
+      if ((lane & (DUP - 1)) == 0) {
+        const int idx = lane / DUP;           // value index within a chunk
+        const int k = idx / R, j = idx % R;
+#pragma unroll
+        for (int s = 0; s < C::SLABS; ++s)
+#pragma unroll
+          for (int c = 0; c < C::NCHUNK; ++c) {
+            const int row = s * C::ROWS + warp * C::RPW + c * C::CHUNK + k;
+            atomicAdd(&W[((size_t)Irow * TILE + row) * R + j], rowacc[s][c]);
+          }
+      }
     }
   };
 
@@ -192,20 +249,48 @@ qy_packed_kernel(const TQ* __restrict__ tiles, int nt, int64_t ntiles, int nstag
     if (I != curI) {
       if (curI >= 0) flush_rows(curI);
       named_bar_sync(1, NCT);
-      for (int e = ctid; e < TILE * R; e += NCT) ysm[e] = Y[(size_t)I * TILE * R + e];
+      if constexpr (C::PAIR) {
+        unsigned long long* ys2 = reinterpret_cast<unsigned long long*>(ysm);
+        for (int e = ctid; e < TILE * R; e += NCT) {
+          const float y = Y[(size_t)I * TILE * R + e];
+          ys2[e] = pk(y, y);
+        }
+      } else {
+        for (int e = ctid; e < TILE * R; e += NCT) ysm[e] = Y[(size_t)I * TILE * R + e];
+      }
       named_bar_sync(1, NCT);
+      if constexpr (C::DEFER) {
 #pragma unroll
-      for (int s = 0; s < C::SLABS; ++s)
+        for (int s = 0; s < C::SLABS; ++s)
 #pragma unroll
-        for (int c = 0; c < C::NCHUNK; ++c) rowacc[s][c] = A(0);
+          for (int k = 0; k < C::RPW; ++k)
+#pragma unroll
+            for (int jp = 0; jp < RH; ++jp) rowp[s][k][jp] = 0ull;
+      } else {
+#pragma unroll
+        for (int s = 0; s < C::SLABS; ++s)
+#pragma unroll
+          for (int c = 0; c < C::NCHUNK; ++c) rowacc[s][c] = A(0);
+      }
       curI = I;
     }
     {
       const A* yp = Y + ((size_t)J * TILE + 4 * lane) * R;
+      if constexpr (C::PAIR) {
 #pragma unroll
-      for (int c = 0; c < 4; ++c)
+        for (int c = 0; c < 4; ++c)
 #pragma unroll
-        for (int j = 0; j < R; ++j) { yj[c][j] = yp[c * R + j]; colacc[c][j] = A(0); }
+          for (int jp = 0; jp < RH; ++jp) yjp[c][jp] = pk(yp[c * R + 2 * jp], yp[c * R + 2 * jp + 1]);
+#pragma unroll
+        for (int cp = 0; cp < 2; ++cp)
+#pragma unroll
+          for (int j = 0; j < R; ++j) colp[cp][j] = 0ull;
+      } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+          for (int j = 0; j < R; ++j) { yj[c][j] = yp[c * R + j]; colacc[c][j] = A(0); }
+      }
     }
 #pragma unroll
     for (int s = 0; s < C::SLABS; ++s) {
@@ -221,41 +306,100 @@ qy_packed_kernel(const TQ* __restrict__ tiles, int nt, int64_t ntiles, int nstag
       if (lane == 0) mbar_arrive(&empty[stage]);
       if (++stage == nstage) { stage = 0; phase ^= 1u; }
       const int rbase = s * C::ROWS + warp * C::RPW;
+      if constexpr (C::PAIR) {
+        const unsigned long long* ys2 = reinterpret_cast<const unsigned long long*>(ysm);
+        unsigned long long rloc[C::DEFER ? 1 : C::RPW][RH];
+        if constexpr (!C::DEFER) {
 #pragma unroll
-      for (int k = 0; k < C::RPW; ++k) {
-        A yi[R];
+          for (int k = 0; k < C::RPW; ++k)
 #pragma unroll
-        for (int j = 0; j < R; ++j) yi[j] = ysm[(rbase + k) * R + j];
+            for (int jp = 0; jp < RH; ++jp) rloc[k][jp] = 0ull;
+        }
 #pragma unroll
-        for (int c = 0; c < 4; ++c)
-#pragma unroll
-          for (int j = 0; j < R; ++j) colacc[c][j] = fma(q[k][c], yi[j], colacc[c][j]);
-      }
-#pragma unroll
-      for (int ch = 0; ch < C::NCHUNK; ++ch) {
-        A v[C::V];
-#pragma unroll
-        for (int kk = 0; kk < C::CHUNK; ++kk) {
-          const int k = ch * C::CHUNK + kk;
+        for (int k = 0; k < C::RPW; ++k) {
+          const unsigned long long q01 = pk(q[k][0], q[k][1]);
+          const unsigned long long q23 = pk(q[k][2], q[k][3]);
+          // column contribution: (colacc[c][j], colacc[c+1][j]) += (q_c, q_c+1) * (y_j, y_j)
 #pragma unroll
           for (int j = 0; j < R; ++j) {
-            A acc = q[k][0] * yj[0][j];
-            acc = fma(q[k][1], yj[1][j], acc);
-            acc = fma(q[k][2], yj[2][j], acc);
-            acc = fma(q[k][3], yj[3][j], acc);
-            v[kk * R + j] = acc;
+            const unsigned long long yy = ys2[(rbase + k) * R + j];
+            colp[0][j] = ffma2(q01, yy, colp[0][j]);
+            colp[1][j] = ffma2(q23, yy, colp[1][j]);
+          }
+          // row contribution: (v_j, v_j+1) += (q_c, q_c) * (Y_J[c][j], Y_J[c][j+1])
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const unsigned long long qq = pk(q[k][c], q[k][c]);
+#pragma unroll
+            for (int jp = 0; jp < RH; ++jp) {
+              if constexpr (C::DEFER) rowp[s][k][jp] = ffma2(qq, yjp[c][jp], rowp[s][k][jp]);
+              else rloc[k][jp] = ffma2(qq, yjp[c][jp], rloc[k][jp]);
+            }
           }
         }
-        rowacc[s][ch] += transpose_reduce<C::V>(v, lane);
+        if constexpr (!C::DEFER) {
+          A vals[C::RPW * R];
+#pragma unroll
+          for (int k = 0; k < C::RPW; ++k)
+#pragma unroll
+            for (int jp = 0; jp < RH; ++jp) upk(rloc[k][jp], vals[k * R + 2 * jp], vals[k * R + 2 * jp + 1]);
+#pragma unroll
+          for (int ch = 0; ch < C::NCHUNK; ++ch) {
+            A v[C::V];
+#pragma unroll
+            for (int e = 0; e < C::V; ++e) v[e] = vals[ch * C::V + e];
+            rowacc[s][ch] += transpose_reduce<C::V>(v, lane);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < C::RPW; ++k) {
+          A yi[R];
+#pragma unroll
+          for (int j = 0; j < R; ++j) yi[j] = ysm[(rbase + k) * R + j];
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int j = 0; j < R; ++j) colacc[c][j] = fma(q[k][c], yi[j], colacc[c][j]);
+        }
+#pragma unroll
+        for (int ch = 0; ch < C::NCHUNK; ++ch) {
+          A v[C::V];
+#pragma unroll
+          for (int kk = 0; kk < C::CHUNK; ++kk) {
+            const int k = ch * C::CHUNK + kk;
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+              A acc = q[k][0] * yj[0][j];
+              acc = fma(q[k][1], yj[1][j], acc);
+              acc = fma(q[k][2], yj[2][j], acc);
+              acc = fma(q[k][3], yj[3][j], acc);
+              v[kk * R + j] = acc;
+            }
+          }
+          rowacc[s][ch] += transpose_reduce<C::V>(v, lane);
+        }
       }
     }
     // column contribution: combine the NW warps' partials, then one atomic per output
     {
       A* mine = red + (size_t)warp * TILE * R;
+      if constexpr (C::PAIR) {
 #pragma unroll
-      for (int c = 0; c < 4; ++c)
+        for (int cp = 0; cp < 2; ++cp)
 #pragma unroll
-        for (int j = 0; j < R; ++j) mine[(4 * lane + c) * R + j] = colacc[c][j];
+          for (int j = 0; j < R; ++j) {
+            float lo, hi;
+            upk(colp[cp][j], lo, hi);
+            mine[(4 * lane + 2 * cp) * R + j] = lo;
+            mine[(4 * lane + 2 * cp + 1) * R + j] = hi;
+          }
+      } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+          for (int j = 0; j < R; ++j) mine[(4 * lane + c) * R + j] = colacc[c][j];
+      }
       named_bar_sync(1, NCT);
       for (int o = ctid; o < TILE * R; o += NCT) {
         A sum = A(0);

@@ -691,7 +691,12 @@ xm_status solve_impl(xm_ctx* ctx, const DeviceQ& q, const xm_opts& o, int r_in, 
       XM_CUDA_TRY(cudaGetLastError());
       // FP64 polish: FP64 gradient and objective, FP32 Hessian-vector products
       XM_TRY(S.clear_vecs());
-      XM_CUDA_TRY(cudaMemcpyAsync(S.bY, S.bY64, sizeof(double) * elems, cudaMemcpyDeviceToDevice, st));
+      // The widened FP32 iterate is feasible only to FP32 precision; project it back onto the
+      // manifold in FP64 (retraction with a zero step) so the polish compares feasible points.
+      XM_TRY(with_R(R,
+          [&] { k_retract<double, double, 4><<<S.nb_cam, CAM_THREADS, 0, st>>>(N, (const double*)S.bY64, (const double*)S.bXi, 0.0, (double*)S.bY); return XM_OK; },
+          [&] { k_retract<double, double, 8><<<S.nb_cam, CAM_THREADS, 0, st>>>(N, (const double*)S.bY64, (const double*)S.bXi, 0.0, (double*)S.bY); return XM_OK; }));
+      ++S.launches;
       XM_TRY(with_R(R,
           [&] { return S.rtr<double, float, 4>(XM_FP64, XM_FP32_BULK, o.grad_tol_rel, o.max_polish, false); },
           [&] { return S.rtr<double, float, 8>(XM_FP64, XM_FP32_BULK, o.grad_tol_rel, o.max_polish, false); }));
