@@ -13,8 +13,10 @@
 //     registers and accumulates the column contribution; the row contribution of each slab
 //     row is reduced across lanes with a transpose-reduce butterfly and accumulated per
 //     tile row in registers;
-//   * column partials are combined across warps in shared memory and added to W_J with one
-//     atomic per output; row partials are added to W_I when the tile row changes.
+//   * the producer also bulk-copies Y_J of every tile into a 4-slot ring, so no consumer waits
+//     on a global load; each warp adds its column partials to W_J with vector reductions (no
+//     barrier between warps inside a tile row); row partials are kept per tile row in registers
+//     (FP32/BF16, R = 4) and reduced across lanes once per tile row.
 #include "xm_internal.cuh"
 
 namespace xm {
@@ -67,6 +69,14 @@ __device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsign
   return d;
 }
 
+// W[0..3] += (a, b, c, d) with one vector reduction (16-byte aligned address)
+__device__ __forceinline__ void red_add4(float* w, float a, float b, float c, float d) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(w), "f"(a), "f"(b), "f"(c),
+               "f"(d)
+               : "memory");
+}
+__device__ __forceinline__ void red_add4(double*, double, double, double, double) {}
+
 // Butterfly transpose-reduce of V <= 32 per-lane values: afterwards lane l holds the
 // warp-wide sum of value index l * V / 32 (lanes sharing that index hold the same sum).
 template <int V, typename T>
@@ -106,9 +116,11 @@ struct SweepCfg {
   // row partials kept per tile row (reduced across lanes once per tile row) when they fit
   static constexpr bool DEFER = PAIR && SLABS * RPW * R <= 64;
   static constexpr size_t YSM_BYTES = sizeof(A) * TILE * R * (PAIR ? 2 : 1);
-  static constexpr size_t RED_BYTES = sizeof(A) * NW * TILE * R;
+  static constexpr int YJ_SLOTS = 4;                       // ring of Y_J tiles
+  static constexpr uint32_t YJ_BYTES = sizeof(A) * TILE * R;
   static size_t smem_bytes(int nstage) {
-    return 128 + (size_t)nstage * SLAB_BYTES + YSM_BYTES + RED_BYTES + 16 * (size_t)nstage;
+    return 128 + (size_t)nstage * SLAB_BYTES + YSM_BYTES + (size_t)YJ_SLOTS * YJ_BYTES +
+           16 * (size_t)(nstage + YJ_SLOTS);
   }
 };
 
@@ -126,9 +138,12 @@ qy_packed_kernel(const TQ* __restrict__ tiles, int nt, int64_t ntiles, int nstag
       (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   unsigned char* stages = base;
   A* ysm = reinterpret_cast<A*>(stages + (size_t)nstage * SLAB_BYTES);
-  A* red = reinterpret_cast<A*>(reinterpret_cast<unsigned char*>(ysm) + C::YSM_BYTES);
-  uint64_t* full = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(red) + C::RED_BYTES);
+  A* yjs = reinterpret_cast<A*>(reinterpret_cast<unsigned char*>(ysm) + C::YSM_BYTES);
+  uint64_t* full = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(yjs) +
+                                               (size_t)C::YJ_SLOTS * C::YJ_BYTES);
   uint64_t* empty = full + nstage;
+  uint64_t* fully = empty + nstage;
+  uint64_t* emptyy = fully + C::YJ_SLOTS;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t t0 = ntiles * blockIdx.x / gridDim.x;
@@ -138,6 +153,10 @@ qy_packed_kernel(const TQ* __restrict__ tiles, int nt, int64_t ntiles, int nstag
     for (int s = 0; s < nstage; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], NW);
+    }
+    for (int s = 0; s < C::YJ_SLOTS; ++s) {
+      mbar_init(&fully[s], 1);
+      mbar_init(&emptyy[s], NW);
     }
     fence_mbar_init();
   }
@@ -153,27 +172,38 @@ qy_packed_kernel(const TQ* __restrict__ tiles, int nt, int64_t ntiles, int nstag
   const int J0 = I0 + (int)(t0 - tile_index(nt, I0, I0));
 
   if (warp == NW) {
-    // ---------------- producer: one thread streams the slabs of [t0, t1)
+    // ---------------- producer: one thread streams, per tile, Y_J then the tile's slabs
     if (lane == 0) {
       const unsigned char* src = reinterpret_cast<const unsigned char*>(tiles) +
                                  (size_t)t0 * C::SLABS * SLAB_BYTES;
-      const int64_t nslab = (t1 - t0) * C::SLABS;
-      int stage = 0;
-      uint32_t phase = 0;
-      int64_t issued = 0;
-      for (; issued < nslab; ++issued) {
-        if (!mbar_wait(&empty[stage], phase ^ 1u)) { atomicOr(err, DEV_TIMEOUT); break; }
-        mbar_arrive_expect_tx(&full[stage], SLAB_BYTES);
-        bulk_g2s(stages + (size_t)stage * SLAB_BYTES, src + (size_t)issued * SLAB_BYTES,
-                 SLAB_BYTES, &full[stage]);
-        if (++stage == nstage) { stage = 0; phase ^= 1u; }
+      const unsigned char* ysrc = reinterpret_cast<const unsigned char*>(Y);
+      int stage = 0, ys = 0;
+      uint32_t phase = 0, yphase = 0;
+      int64_t issued = 0, yissued = 0;
+      int Jp = J0, Ip = I0;
+      bool good = true;
+      for (int64_t t = t0; t < t1 && good; ++t) {
+        if (!mbar_wait(&emptyy[ys], yphase ^ 1u)) { atomicOr(err, DEV_TIMEOUT); break; }
+        mbar_arrive_expect_tx(&fully[ys], C::YJ_BYTES);
+        bulk_g2s(reinterpret_cast<unsigned char*>(yjs) + (size_t)ys * C::YJ_BYTES,
+                 ysrc + (size_t)Jp * C::YJ_BYTES, C::YJ_BYTES, &fully[ys]);
+        ++yissued;
+        if (++ys == C::YJ_SLOTS) { ys = 0; yphase ^= 1u; }
+        for (int sl = 0; sl < C::SLABS; ++sl, ++issued) {
+          if (!mbar_wait(&empty[stage], phase ^ 1u)) { atomicOr(err, DEV_TIMEOUT); good = false; break; }
+          mbar_arrive_expect_tx(&full[stage], SLAB_BYTES);
+          bulk_g2s(stages + (size_t)stage * SLAB_BYTES, src + (size_t)issued * SLAB_BYTES,
+                   SLAB_BYTES, &full[stage]);
+          if (++stage == nstage) { stage = 0; phase ^= 1u; }
+        }
+        if (++Jp == nt) { ++Ip; Jp = Ip; }
       }
       // Drain: do not leave while copies into this CTA's shared memory are in flight.
-      const int64_t first = issued > nstage ? issued - nstage : 0;
-      for (int64_t k = first; k < issued; ++k) {
-        const int s = (int)(k % nstage);
-        const uint32_t ph = (uint32_t)((k / nstage) & 1);
-        if (!mbar_wait(&full[s], ph)) { atomicOr(err, DEV_TIMEOUT); break; }
+      for (int64_t k = issued > nstage ? issued - nstage : 0; k < issued; ++k) {
+        if (!mbar_wait(&full[k % nstage], (uint32_t)((k / nstage) & 1))) { atomicOr(err, DEV_TIMEOUT); break; }
+      }
+      for (int64_t k = yissued > C::YJ_SLOTS ? yissued - C::YJ_SLOTS : 0; k < yissued; ++k) {
+        if (!mbar_wait(&fully[k % C::YJ_SLOTS], (uint32_t)((k / C::YJ_SLOTS) & 1))) { atomicOr(err, DEV_TIMEOUT); break; }
       }
     }
     return;
@@ -185,8 +215,8 @@ qy_packed_kernel(const TQ* __restrict__ tiles, int nt, int64_t ntiles, int nstag
   constexpr int RH = C::PAIR ? R / 2 : 1;  // j-pairs per row
   int curI = -1;
   int I = I0, J = J0;
-  int stage = 0;
-  uint32_t phase = 0;
+  int stage = 0, ysl = 0;
+  uint32_t phase = 0, yphase = 0;
   bool ok = true;
 
   // scalar-path state
@@ -275,7 +305,8 @@ qy_packed_kernel(const TQ* __restrict__ tiles, int nt, int64_t ntiles, int nstag
       curI = I;
     }
     {
-      const A* yp = Y + ((size_t)J * TILE + 4 * lane) * R;
+      if (ok && !mbar_wait(&fully[ysl], yphase)) { atomicOr(err, DEV_TIMEOUT); ok = false; }
+      const A* yp = yjs + (size_t)ysl * (TILE * R) + (size_t)(4 * lane) * R;
       if constexpr (C::PAIR) {
 #pragma unroll
         for (int c = 0; c < 4; ++c)
@@ -291,6 +322,9 @@ qy_packed_kernel(const TQ* __restrict__ tiles, int nt, int64_t ntiles, int nstag
 #pragma unroll
           for (int j = 0; j < R; ++j) { yj[c][j] = yp[c * R + j]; colacc[c][j] = A(0); }
       }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&emptyy[ysl]);
+      if (++ysl == C::YJ_SLOTS) { ysl = 0; yphase ^= 1u; }
     }
 #pragma unroll
     for (int s = 0; s < C::SLABS; ++s) {
@@ -381,33 +415,30 @@ qy_packed_kernel(const TQ* __restrict__ tiles, int nt, int64_t ntiles, int nstag
         }
       }
     }
-    // column contribution: combine the NW warps' partials, then one atomic per output
+    // column contribution: each warp adds its partials for columns 4l..4l+3 of Y_J directly
+    // (vector reductions in L2; no barrier between warps)
     {
-      A* mine = red + (size_t)warp * TILE * R;
+      A* wj = W + ((size_t)J * TILE + 4 * lane) * R;
       if constexpr (C::PAIR) {
 #pragma unroll
-        for (int cp = 0; cp < 2; ++cp)
+        for (int cp = 0; cp < 2; ++cp) {
+          float lo[R], hi[R];
 #pragma unroll
-          for (int j = 0; j < R; ++j) {
-            float lo, hi;
-            upk(colp[cp][j], lo, hi);
-            mine[(4 * lane + 2 * cp) * R + j] = lo;
-            mine[(4 * lane + 2 * cp + 1) * R + j] = hi;
+          for (int j = 0; j < R; ++j) upk(colp[cp][j], lo[j], hi[j]);
+#pragma unroll
+          for (int j = 0; j < R; j += 4) {
+            red_add4(wj + (2 * cp) * R + j, lo[j], lo[j + 1], lo[j + 2], lo[j + 3]);
+            red_add4(wj + (2 * cp + 1) * R + j, hi[j], hi[j + 1], hi[j + 2], hi[j + 3]);
           }
+        }
+      } else if constexpr (sizeof(A) == 4 && R == 1) {
+        red_add4(wj, colacc[0][0], colacc[1][0], colacc[2][0], colacc[3][0]);
       } else {
 #pragma unroll
         for (int c = 0; c < 4; ++c)
 #pragma unroll
-          for (int j = 0; j < R; ++j) mine[(4 * lane + c) * R + j] = colacc[c][j];
+          for (int j = 0; j < R; ++j) atomicAdd(&wj[c * R + j], colacc[c][j]);
       }
-      named_bar_sync(1, NCT);
-      for (int o = ctid; o < TILE * R; o += NCT) {
-        A sum = A(0);
-#pragma unroll
-        for (int w = 0; w < NW; ++w) sum += red[(size_t)w * TILE * R + o];
-        atomicAdd(&W[(size_t)J * TILE * R + o], sum);
-      }
-      named_bar_sync(1, NCT);
     }
     if (++J == nt) { ++I; J = I; }
   }
