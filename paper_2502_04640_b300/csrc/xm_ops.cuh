@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(CAM_THREADS)
 k_grad_epi(int N, const T* __restrict__ Y, T* __restrict__ W, T* __restrict__ G,
            double* __restrict__ Lam, Scal* sc, int cand, double* partials, unsigned* counter,
            int* err) {
-  using C = T;
+  using C = double;   // per-camera arithmetic in FP64 whatever the storage type
   double v[3] = {0.0, 0.0, 0.0};
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < N) {
@@ -248,7 +248,7 @@ k_hvp_epi(int N, const T* __restrict__ Y, T* __restrict__ Wd, const T* __restric
           T* __restrict__ Hd, const double* __restrict__ Lam, Scal* sc, double* partials,
           unsigned* counter) {
   if (sc->done) return;
-  using C = T;
+  using C = double;   // per-camera arithmetic in FP64 whatever the storage type
   double v[1] = {0.0};
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < N) {
@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(CAM_THREADS)
 k_tcg_update(int N, const T* __restrict__ Y, T* eta, T* Heta, T* r, const T* __restrict__ delta,
              const T* __restrict__ Hd, Scal* sc, double* partials, unsigned* counter) {
   if (sc->done) return;
-  using C = T;
+  using C = double;   // per-camera arithmetic in FP64 whatever the storage type
   const C alpha = C(sc->alpha);
   const bool stop = sc->stop_after != 0;
   double v[1] = {0.0};
@@ -363,7 +363,7 @@ __global__ void __launch_bounds__(CAM_THREADS)
 k_tcg_dir(int N, const T* __restrict__ eta, const T* __restrict__ r, T* delta, Scal* sc,
           double* partials, unsigned* counter) {
   if (sc->done) return;
-  using C = T;
+  using C = double;   // per-camera arithmetic in FP64 whatever the storage type
   const C beta = C(sc->beta);
   double v[3] = {0.0, 0.0, 0.0};
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -411,7 +411,7 @@ k_model_terms(int n_rows, const To* __restrict__ G, const Ti* __restrict__ eta,
 template <typename To, typename Ti, int R>
 __global__ void __launch_bounds__(CAM_THREADS)
 k_retract(int N, const To* __restrict__ Y, const Ti* __restrict__ Xi, double s, To* __restrict__ Yo) {
-  using C = To;
+  using C = double;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   C A[3][R];
@@ -420,6 +420,15 @@ k_retract(int N, const To* __restrict__ Y, const Ti* __restrict__ Xi, double s, 
 #pragma unroll
     for (int j = 0; j < R; ++j)
       A[a][j] = C(Y[(size_t)(3 * i + a) * R + j]) + C(s) * C(Xi[(size_t)(3 * i + a) * R + j]);
+  // work with A / ||A||_F so that the 3x3 eigenproblem is scale free (blocks can shrink far
+  // towards zero on the way to a scale-collapsed stationary point)
+  C fro = C(0);
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int j = 0; j < R; ++j) fro += A[a][j] * A[a][j];
+  fro = sqrt(fro);
+  const C ifro = fro > C(0) ? C(1) / fro : C(0);
   C M[3][3];
 #pragma unroll
   for (int a = 0; a < 3; ++a)
@@ -427,7 +436,7 @@ k_retract(int N, const To* __restrict__ Y, const Ti* __restrict__ Xi, double s, 
     for (int b = 0; b < 3; ++b) {
       C t = C(0);
 #pragma unroll
-      for (int j = 0; j < R; ++j) t += A[a][j] * A[b][j];
+      for (int j = 0; j < R; ++j) t += (A[a][j] * ifro) * (A[b][j] * ifro);
       M[a][b] = t;
     }
   C V[3][3], d[3];
@@ -436,12 +445,12 @@ k_retract(int N, const To* __restrict__ Y, const Ti* __restrict__ Xi, double s, 
   C ssum = C(0);
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    const C dk = d[k] > C(1e-300) ? d[k] : C(1e-300);
+    const C dk = d[k] > C(1e-30) ? d[k] : C(1e-30);   // eigenvalues of the unit-norm problem
     sq[k] = sqrt(dk);
-    isq[k] = C(1) / sq[k];
+    isq[k] = ifro / sq[k];                             // (A A^T)^{-1/2} = V diag(1/(|A| sqrt d)) V^T
     ssum += sq[k];
   }
-  const C scale = i == 0 ? C(1) : ssum / C(3);
+  const C scale = i == 0 ? C(1) : fro * ssum / C(3);
   C P[3][3];   // scale * V diag(1/sqrt d) V^T
 #pragma unroll
   for (int a = 0; a < 3; ++a)
