@@ -666,6 +666,7 @@ xm_status solve_impl(xm_ctx* ctx, const DeviceQ& q, const xm_opts& o, int r_in, 
     const size_t elems = (size_t)nn * R;
     XM_TRY(S.clear_vecs());
     // ---- local optimisation at rank r
+    bool quick_escape = false;
     if (certify_only) {
       XM_CUDA_TRY(cudaMemcpyAsync(S.bY, S.bY64, sizeof(double) * elems, cudaMemcpyDeviceToDevice, st));
       XM_TRY(with_R(R, [&] { return S.grad_at<double, 4>(XM_FP64, S.bY, S.bW, S.bG, S.Lam, 0, false); },
@@ -689,36 +690,54 @@ xm_status solve_impl(xm_ctx* ctx, const DeviceQ& q, const xm_opts& o, int r_in, 
       k_cast<float, double><<<S.grid_elems(elems), CAM_THREADS, 0, st>>>(elems, (const float*)S.bY, (double*)S.bY64);
       ++S.launches;
       XM_CUDA_TRY(cudaGetLastError());
-      // FP64 polish: FP64 gradient and objective, FP32 Hessian-vector products
-      XM_TRY(S.clear_vecs());
-      // The widened FP32 iterate is feasible only to FP32 precision; project it back onto the
-      // manifold in FP64 (retraction with a zero step) so the polish compares feasible points.
-      XM_TRY(with_R(R,
-          [&] { k_retract<double, double, 4><<<S.nb_cam, CAM_THREADS, 0, st>>>(N, (const double*)S.bY64, (const double*)S.bXi, 0.0, (double*)S.bY); return XM_OK; },
-          [&] { k_retract<double, double, 8><<<S.nb_cam, CAM_THREADS, 0, st>>>(N, (const double*)S.bY64, (const double*)S.bXi, 0.0, (double*)S.bY); return XM_OK; }));
-      ++S.launches;
-      XM_TRY(with_R(R,
-          [&] { return S.rtr<double, float, 4>(XM_FP64, XM_FP32_BULK, o.grad_tol_rel, o.max_polish, false); },
-          [&] { return S.rtr<double, float, 8>(XM_FP64, XM_FP32_BULK, o.grad_tol_rel, o.max_polish, false); }));
-      XM_CUDA_TRY(cudaMemcpyAsync(S.bY64, S.bY, sizeof(double) * elems, cudaMemcpyDeviceToDevice, st));
+      // Quick certificate with the bulk-phase dual blocks: clearly negative curvature means the
+      // rank-r point is a saddle of the SDP (Thm. 2) and an FP64 polish would be wasted.
+      if (r < o.r_max) {
+        XM_TRY(with_R(R, [&] { return S.certify<4>(r, XM_FP32_BULK, &lam_def, &lam_max, &lam_range); },
+                         [&] { return S.certify<8>(r, XM_FP32_BULK, &lam_def, &lam_max, &lam_range); }));
+        if (lam_def < -1e-4 * std::fabs(lam_max)) {
+          if (o.verbose >= 1)
+            fprintf(stderr, "[xm] rank %d: bulk f=%.12e lam_def=%.6e lam_max=%.6e escape without polish\n",
+                    r, S.info.f, lam_def, lam_max);
+          quick_escape = true;
+        }
+      }
+      if (!quick_escape) {
+        // FP64 polish: FP64 gradient and objective, FP32 Hessian-vector products
+        XM_TRY(S.clear_vecs());
+        // The widened FP32 iterate is feasible only to FP32 precision; project it back onto the
+        // manifold in FP64 (retraction with a zero step) so the polish compares feasible points.
+        XM_TRY(with_R(R,
+            [&] { k_retract<double, double, 4><<<S.nb_cam, CAM_THREADS, 0, st>>>(N, (const double*)S.bY64, (const double*)S.bXi, 0.0, (double*)S.bY); return XM_OK; },
+            [&] { k_retract<double, double, 8><<<S.nb_cam, CAM_THREADS, 0, st>>>(N, (const double*)S.bY64, (const double*)S.bXi, 0.0, (double*)S.bY); return XM_OK; }));
+        ++S.launches;
+        XM_TRY(with_R(R,
+            [&] { return S.rtr<double, float, 4>(XM_FP64, XM_FP32_BULK, o.grad_tol_rel, o.max_polish, false); },
+            [&] { return S.rtr<double, float, 8>(XM_FP64, XM_FP32_BULK, o.grad_tol_rel, o.max_polish, false); }));
+        XM_CUDA_TRY(cudaMemcpyAsync(S.bY64, S.bY, sizeof(double) * elems, cudaMemcpyDeviceToDevice, st));
+      }
     }
     // ---- certificate (FP64 Lambda from the last FP64 gradient)
-    XM_TRY(with_R(R, [&] { return S.certify<4>(r, prec_z, &lam_def, &lam_max, &lam_range); },
-                     [&] { return S.certify<8>(r, prec_z, &lam_def, &lam_max, &lam_range); }));
+    double gap = 0.0;
+    bool stationary = false;
+    if (!quick_escape) {
+      XM_TRY(with_R(R, [&] { return S.certify<4>(r, prec_z, &lam_def, &lam_max, &lam_range); },
+                       [&] { return S.certify<8>(r, prec_z, &lam_def, &lam_max, &lam_range); }));
+      // Thm. 1 needs a first-order critical point: with Lambda in closed form the duality gap
+      // f - tr(Lambda_0) = <Y, Z Y> vanishes exactly there, so it is checked beside lambda_min.
+      double L0g[9];
+      XM_CUDA_TRY(cudaMemcpy(L0g, S.Lam, sizeof(L0g), cudaMemcpyDeviceToHost));
+      gap = S.info.f - (L0g[0] + L0g[4] + L0g[8]);
+      stationary = std::fabs(gap) <= 1e-6 * (1.0 + std::fabs(S.info.f));
+    }
     const double tau = o.cert_tau_rel * std::max(std::fabs(lam_max), 1e-300);
-    // Thm. 1 needs a first-order critical point: with Lambda in closed form the duality gap
-    // f - tr(Lambda_0) = <Y, Z Y> vanishes exactly there, so it is checked beside lambda_min.
-    double L0g[9];
-    XM_CUDA_TRY(cudaMemcpy(L0g, S.Lam, sizeof(L0g), cudaMemcpyDeviceToHost));
-    const double gap = S.info.f - (L0g[0] + L0g[4] + L0g[8]);
-    const bool stationary = std::fabs(gap) <= 1e-6 * (1.0 + std::fabs(S.info.f));
-    certified = lam_def >= -tau && stationary;
-    if (o.verbose >= 1)
+    certified = !quick_escape && lam_def >= -tau && stationary;
+    if (o.verbose >= 1 && !quick_escape)
       fprintf(stderr, "[xm] rank %d: f=%.12e |g|=%.3e gap=%.3e lam_def=%.6e lam_rng=%.3e lam_max=%.6e %s\n",
               r, S.info.f, std::sqrt(S.cur_g2), gap, lam_def, lam_range, lam_max,
               certified ? "CERTIFIED" : "escape");
     if (certified || certify_only) break;
-    if (S.timed_out || (lam_def >= -tau && !stationary)) { result = XM_ENOCONV; break; }
+    if (S.timed_out || (!quick_escape && lam_def >= -tau && !stationary)) { result = XM_ENOCONV; break; }
     if (r >= o.r_max) { result = XM_ENOTCERT; break; }
     // ---- escape (Thm. 2): into a null column of Y if one exists, else one rank up
     std::vector<double> gram(R * R);
@@ -752,21 +771,39 @@ xm_status solve_impl(xm_ctx* ctx, const DeviceQ& q, const xm_opts& o, int r_in, 
     }
     S.launches += 2;
     k_set_col<<<S.grid_elems((size_t)nn * R), CAM_THREADS, 0, st>>>(n, nn, R, col, S.lritz, (double*)S.bXi);
-    // line search on f, FP64
-    const double f0 = S.info.f;
+    // line search on f in the working precision (FP64 mode: FP64; mixed modes: FP32 sweeps of
+    // the FP64-retracted points), against f at alpha = 0 in the same precision
+    const bool ls64 = fp64_mode;
+    const size_t ls_elems = (size_t)nn * R;
+    auto f_at = [&](double a, double* fout) -> xm_status {
+      XM_CUDA_TRY(cudaMemsetAsync(S.bWc, 0, S.vec_bytes, st));
+      XM_TRY(with_R(R,
+          [&] { k_retract<double, double, 4><<<S.nb_cam, CAM_THREADS, 0, st>>>(N, (const double*)S.bY64, (const double*)S.bXi, a, (double*)S.bYh); return XM_OK; },
+          [&] { k_retract<double, double, 8><<<S.nb_cam, CAM_THREADS, 0, st>>>(N, (const double*)S.bY64, (const double*)S.bXi, a, (double*)S.bYh); return XM_OK; }));
+      ++S.launches;
+      if (ls64) {
+        XM_TRY(with_R(R, [&] { return S.grad_at<double, 4>(XM_FP64, S.bYh, S.bWc, S.bGc, S.Lamc, 1, false); },
+                         [&] { return S.grad_at<double, 8>(XM_FP64, S.bYh, S.bWc, S.bGc, S.Lamc, 1, false); }));
+      } else {
+        XM_CUDA_TRY(cudaMemsetAsync(S.bYc, 0, S.vec_bytes, st));
+        k_cast<double, float><<<S.grid_elems(ls_elems), CAM_THREADS, 0, st>>>(ls_elems, (const double*)S.bYh, (float*)S.bYc);
+        ++S.launches;
+        XM_TRY(with_R(R, [&] { return S.grad_at<float, 4>(XM_FP32_BULK, S.bYc, S.bWc, S.bGc, S.Lamc, 1, false); },
+                         [&] { return S.grad_at<float, 8>(XM_FP32_BULK, S.bYc, S.bWc, S.bGc, S.Lamc, 1, false); }));
+      }
+      XM_TRY(S.pull_scalars());
+      *fout = S.h_sc->fc;
+      return XM_OK;
+    };
+    double f0 = 0.0;
+    XM_TRY(f_at(0.0, &f0));
     bool moved = false;
     double alpha = 1.0;
     for (int h = 0; h <= 30; ++h, alpha *= 0.5) {
-      XM_CUDA_TRY(cudaMemsetAsync(S.bWc, 0, S.vec_bytes, st));
-      XM_TRY(with_R(R,
-          [&] { k_retract<double, double, 4><<<S.nb_cam, CAM_THREADS, 0, st>>>(N, (const double*)S.bY64, (const double*)S.bXi, alpha, (double*)S.bYc);
-                return S.grad_at<double, 4>(XM_FP64, S.bYc, S.bWc, S.bGc, S.Lamc, 1, false); },
-          [&] { k_retract<double, double, 8><<<S.nb_cam, CAM_THREADS, 0, st>>>(N, (const double*)S.bY64, (const double*)S.bXi, alpha, (double*)S.bYc);
-                return S.grad_at<double, 8>(XM_FP64, S.bYc, S.bWc, S.bGc, S.Lamc, 1, false); }));
-      ++S.launches;
-      XM_TRY(S.pull_scalars());
-      if (S.h_sc->fc < f0) {
-        XM_CUDA_TRY(cudaMemcpyAsync(S.bY64, S.bYc, sizeof(double) * (size_t)nn * R, cudaMemcpyDeviceToDevice, st));
+      double fa = 0.0;
+      XM_TRY(f_at(alpha, &fa));
+      if (fa < f0) {
+        XM_CUDA_TRY(cudaMemcpyAsync(S.bY64, S.bYh, sizeof(double) * (size_t)nn * R, cudaMemcpyDeviceToDevice, st));
         moved = true;
         break;
       }
