@@ -76,6 +76,10 @@ typedef struct xm_opts {
   double time_limit_s;     /* wall-clock cap of xm_solve (<= 0: none)                      */
   uint64_t seed;           /* Lanczos start vector                                         */
   int verbose;             /* 0 silent, 1 per rank, 2 per RTR iteration (stderr)           */
+  double init_jitter;      /* start = Alg. 1's [I_3, ..., I_3] padded to rank r0, plus this
+                              amplitude times a seeded uniform(-1, 1) fill of the extra
+                              columns (0: the padded start exactly; a zero column confines
+                              rank-r0 RTR to the rank-3 subspace)                           */
 } xm_opts;
 
 typedef struct xm_info {

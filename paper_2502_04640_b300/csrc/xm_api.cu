@@ -71,7 +71,7 @@ void xm_default_opts(xm_opts* o) {
   o->r_max = XM_MAX_RANK;
   o->prec = XM_FP32_BULK;
   o->grad_tol_rel = 1e-9;
-  o->bulk_tol_rel = 1e-5;
+  o->bulk_tol_rel = 1e-9;
   o->cert_tau_rel = 1e-6;
   o->max_outer = 300;
   o->max_tcg = 200;
@@ -81,6 +81,7 @@ void xm_default_opts(xm_opts* o) {
   o->time_limit_s = 0.0;
   o->seed = 12345;
   o->verbose = 0;
+  o->init_jitter = 0.1;
 }
 
 xm_status xm_create(xm_ctx** out, int device, void* stream) {

@@ -608,11 +608,23 @@ static xm_status with_R(int R, F4 f4, F8 f8) {
   return R == 4 ? f4() : f8();
 }
 
-__global__ void k_init_identity(int N, int R, double* Y) {
+// Alg. 1's start [I_3, ..., I_3] padded to rank r with zero columns, plus jitter * u in columns
+// 3..r-1, u uniform in [-1, 1) from splitmix64 of (seed, element index).
+__global__ void k_init_identity(int N, int R, int r, double jitter, uint64_t seed, double* Y) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   for (int a = 0; a < 3; ++a)
-    for (int j = 0; j < R; ++j) Y[(size_t)(3 * i + a) * R + j] = (a == j) ? 1.0 : 0.0;
+    for (int j = 0; j < R; ++j) {
+      double v = (a == j) ? 1.0 : 0.0;
+      if (j >= 3 && j < r && jitter != 0.0) {
+        uint64_t z = seed + 0x9E3779B97F4A7C15ull * (uint64_t)((3 * i + a) * R + j + 1);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        v = jitter * ((double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0);
+      }
+      Y[(size_t)(3 * i + a) * R + j] = v;
+    }
 }
 
 __global__ void k_set_col(int n, int n_rows, int R, int col, const double* v, double* Xi) {
@@ -654,8 +666,17 @@ xm_status solve_impl(xm_ctx* ctx, const DeviceQ& q, const xm_opts& o, int r_in, 
     XM_CUDA_TRY(cudaMemcpyAsync(S.bY64, S.bYc, sizeof(double) * (size_t)nn * R, cudaMemcpyDeviceToDevice, st));
     S.launches += 2;
   } else {
-    k_init_identity<<<S.nb_cam, CAM_THREADS, 0, st>>>(N, R, (double*)S.bY64);
+    k_init_identity<<<S.nb_cam, CAM_THREADS, 0, st>>>(N, R, r, o.init_jitter, o.seed, (double*)S.bY64);
     ++S.launches;
+    if (o.init_jitter != 0.0 && r > 3) {
+      // make the jittered start feasible: retraction with a zero step
+      XM_CUDA_TRY(cudaMemsetAsync(S.bXi, 0, S.vec_bytes, st));
+      XM_TRY(with_R(R,
+          [&] { k_retract<double, double, 4><<<S.nb_cam, CAM_THREADS, 0, st>>>(N, (const double*)S.bY64, (const double*)S.bXi, 0.0, (double*)S.bYc); return XM_OK; },
+          [&] { k_retract<double, double, 8><<<S.nb_cam, CAM_THREADS, 0, st>>>(N, (const double*)S.bY64, (const double*)S.bXi, 0.0, (double*)S.bYc); return XM_OK; }));
+      XM_CUDA_TRY(cudaMemcpyAsync(S.bY64, S.bYc, sizeof(double) * (size_t)nn * R, cudaMemcpyDeviceToDevice, st));
+      ++S.launches;
+    }
   }
   XM_CUDA_TRY(cudaGetLastError());
 

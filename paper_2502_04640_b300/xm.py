@@ -30,7 +30,7 @@ class XmOpts(ctypes.Structure):
                 ("max_tcg", ctypes.c_int), ("max_polish", ctypes.c_int),
                 ("lanczos_max", ctypes.c_int), ("lanczos_tol", ctypes.c_double),
                 ("time_limit_s", ctypes.c_double), ("seed", ctypes.c_uint64),
-                ("verbose", ctypes.c_int)]
+                ("verbose", ctypes.c_int), ("init_jitter", ctypes.c_double)]
 
 
 class XmInfo(ctypes.Structure):
