@@ -137,6 +137,19 @@ xm_status xm_free_Q(xm_ctx* ctx, xm_qmat* q);
  * both with float Y/W.  Asynchronous on the context stream. */
 xm_status xm_qy(xm_ctx* ctx, const xm_qmat* q, int prec, int r, const void* Y, void* W);
 
+/* The same sweep as xm_qy without any device allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot let a library allocate device memory, such as
+ * applications whose device memory is owned by their own pool allocator, or latency-bound
+ * loops that cannot afford an allocation's implicit synchronisation.  The padded copies of Y
+ * and W live in one fixed 4 MiB device array inside the library (held on every GPU that loads
+ * it until the process exits); 2 * n_pad * R * sizeof(element) must fit, n_pad = n rounded up
+ * to a multiple of 128 and R = 1, 4 or 8 the padded width of r (for example every precision and
+ * r <= 8 at 10155 cameras).  Larger sizes are rejected with XM_EINVAL (use xm_qy).  The first
+ * call on a device looks up the array's device address; make it before any stream capture.
+ * All calls share the array: calls whose work overlaps on the GPU race.  Asynchronous on the
+ * context stream. */
+xm_status xm_qy_noalloc(xm_ctx* ctx, const xm_qmat* q, int prec, int r, const void* Y, void* W);
+
 /* Device time of one sweep, measured with CUDA events on the context stream after three
  * warm-up sweeps (Y filled with a fixed pattern, W zeroed before each sweep outside the timed
  * interval).  ms_mean / ms_min may be NULL.  Synchronous. */

@@ -83,6 +83,7 @@ def lib() -> ctypes.CDLL:
                                         ctypes.POINTER(ctypes.c_uint)]),
         "xm_free_Q": (ctypes.c_int, [_P, _P]),
         "xm_qy": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, _P, _P]),
+        "xm_qy_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, _P, _P]),
         "xm_bench_qy": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
         "xm_last_launch_count": (ctypes.c_long, []),
