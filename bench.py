@@ -168,6 +168,31 @@ def run_reference(args):
     return 0
 
 
+def run_sweep_only(args):
+    """Q.Y sweep alone (FP32 storage, r = 4, the solver's dominant launch configuration) on a
+    seeded random symmetric Q of the given number of cameras; prints one JSON line."""
+    import torch
+    from paper_2502_04640_b300 import xm
+    N = args.sweep_only
+    n = 3 * N
+    ctx = xm.Context(0)
+    g = torch.Generator(device="cuda").manual_seed(1)
+    Q = torch.randn((n, n), dtype=torch.float64, device="cuda", generator=g)
+    Q = (Q + Q.T) * 0.5
+    q = xm.xm_qmat_from_dense(ctx, Q, xm.XM_STORE_FP32)
+    del Q
+    torch.cuda.empty_cache()
+    ms, ms_min = xm.xm_bench_qy(q, xm.XM_FP32_BULK, 4, max(args.steps, 1))
+    alg = sweep_bytes(n, 4, 4, 4)
+    peak, kind = peaks()
+    print(json.dumps({"sweep_only": True, "N": N, "n": n, "ms": ms, "ms_min": ms_min,
+                      "GBps": alg / (ms * 1e-3) / 1e9, "frac": alg / (ms * 1e-3) / 1e9 / peak,
+                      "peak": peak, "peak_kind": kind}), flush=True)
+    q.free()
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -179,11 +204,16 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 / BF16 comparison solves")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--sweep-only", type=int, default=0, metavar="N",
+                    help="time only the Q.Y sweep on a seeded random symmetric Q of N cameras "
+                         "(the small case used for profiler captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.sweep_only:
+        return run_sweep_only(args)
 
     import torch
     from paper_2502_04640_b300 import xm
@@ -221,6 +251,7 @@ def main():
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
     ev0.record(stream)
     wall0 = time.perf_counter()
     launches = 0
@@ -231,6 +262,7 @@ def main():
         launches += xm.xm_last_launch_count()
         timed.append(out["info"])
     ev1.record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     if dist:
