@@ -204,11 +204,14 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 / BF16 comparison solves")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--profile-solve", action="store_true",
+                    help="build Q and run exactly one solve inside the NVTX range 'timed' (profiler "
+                         "launch lists); prints the solve's info")
     ap.add_argument("--sweep-only", type=int, default=0, metavar="N",
                     help="time only the Q.Y sweep on a seeded random symmetric Q of N cameras "
                          "(the small case used for profiler captures)")
     args = ap.parse_args()
-    if args.warmup < 3:
+    if args.warmup < 3 and not args.profile_solve:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
@@ -243,6 +246,16 @@ def main():
     opts = xm.xm_default_opts(prec=prec)
     stream = ctx.stream
 
+    if args.profile_solve:
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("timed")
+        o = xm.xm_solve(q, opts)
+        torch.cuda.nvtx.range_pop()
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_solve": True, "launches": xm.xm_last_launch_count(), **o["info"]}))
+        q.free()
+        ctx.close()
+        return 0
     for _ in range(args.warmup):
         xm.xm_solve(q, opts)
     # ---- timed region: exactly K certified solves
