@@ -207,6 +207,8 @@ def main():
     ap.add_argument("--profile-solve", action="store_true",
                     help="build Q and run exactly one solve inside the NVTX range 'timed' (profiler "
                          "launch lists); prints the solve's info")
+    ap.add_argument("--time-limit", type=float, default=0.0,
+                    help="wall-clock cap of each solve in seconds (0: none)")
     ap.add_argument("--sweep-only", type=int, default=0, metavar="N",
                     help="time only the Q.Y sweep on a seeded random symmetric Q of N cameras "
                          "(the small case used for profiler captures)")
@@ -243,7 +245,7 @@ def main():
     t_build = time.perf_counter() - t0
     del cam, lmk, ukp, w
     torch.cuda.empty_cache()
-    opts = xm.xm_default_opts(prec=prec)
+    opts = xm.xm_default_opts(prec=prec, time_limit_s=args.time_limit)
     stream = ctx.stream
 
     if args.profile_solve:
