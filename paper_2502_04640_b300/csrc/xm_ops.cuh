@@ -21,7 +21,7 @@ struct Scal {
   int done, stop_after, iters, max_iters, reason, pad_;
 };
 
-constexpr int CAM_THREADS = 128;
+constexpr int CAM_THREADS = 64;   // per-camera kernels: 10155 cameras -> 159 blocks
 
 // ------------------------------------------------------------------ reductions
 // Deterministic grid reduction of K per-thread values: block sums -> partials[b*K+k]; the last
@@ -52,14 +52,26 @@ __device__ __forceinline__ void grid_reduce(double (&v)[K], double* partials, un
   __syncthreads();
   if (!last) return;
   __threadfence();
+  // every thread of the last block adds a fixed stride of the partials, then a fixed tree
+  double acc[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) acc[k] = 0.0;
+  for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x)
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] += static_cast<volatile double*>(partials)[(size_t)b * K + k];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double x = warp_sum(acc[k]);
+    if (lane == 0) sh[k][wid] = x;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
     double tot[K];
 #pragma unroll
-    for (int k = 0; k < K; ++k) tot[k] = 0.0;
-    for (unsigned b = 0; b < gridDim.x; ++b)
-#pragma unroll
-      for (int k = 0; k < K; ++k)
-        tot[k] += static_cast<volatile double*>(partials)[(size_t)b * K + k];
+    for (int k = 0; k < K; ++k) {
+      tot[k] = 0.0;
+      for (int w = 0; w < CAM_THREADS / 32; ++w) tot[k] += sh[k][w];
+    }
     fin(tot);
     *counter = 0u;
     __threadfence();

@@ -397,7 +397,8 @@ struct Solver {
 
   // ---------------- Lanczos on Z restricted to range(Y)^perp (Thm. 1 certificate)
   template <int R>
-  xm_status certify(int r, int prec_z, double* lam_def, double* lam_max, double* lam_range) {
+  xm_status certify(int r, int prec_z, double* lam_def, double* lam_max, double* lam_range,
+                    int kcap_steps = 0) {
     auto tic = std::chrono::steady_clock::now();
     const int nn = n_pad;
     const int nd_max = XM_MAX_RANK;
@@ -480,7 +481,7 @@ struct Solver {
     int K = 0;
     double th_min = 0, th_max = 0;
     bool conv = false;
-    const int kcap = std::min(kmax, n - nd);
+    const int kcap = std::min(kcap_steps > 0 ? std::min(kcap_steps, kmax) : kmax, n - nd);
     for (int k = 0; k < kcap; ++k) {
       double* vk = V + (size_t)(nd + k) * nn;
       double* vkm1 = k > 0 ? V + (size_t)(nd + k - 1) * nn : nullptr;
@@ -714,8 +715,9 @@ xm_status solve_impl(xm_ctx* ctx, const DeviceQ& q, const xm_opts& o, int r_in, 
       // Quick certificate with the bulk-phase dual blocks: clearly negative curvature means the
       // rank-r point is a saddle of the SDP (Thm. 2) and an FP64 polish would be wasted.
       if (r < o.r_max) {
-        XM_TRY(with_R(R, [&] { return S.certify<4>(r, XM_FP32_BULK, &lam_def, &lam_max, &lam_range); },
-                         [&] { return S.certify<8>(r, XM_FP32_BULK, &lam_def, &lam_max, &lam_range); }));
+        // a short Krylov run suffices: strong negative curvature is an extreme eigenvalue
+        XM_TRY(with_R(R, [&] { return S.certify<4>(r, XM_FP32_BULK, &lam_def, &lam_max, &lam_range, 60); },
+                         [&] { return S.certify<8>(r, XM_FP32_BULK, &lam_def, &lam_max, &lam_range, 60); }));
         if (lam_def < -1e-4 * std::fabs(lam_max)) {
           if (o.verbose >= 1)
             fprintf(stderr, "[xm] rank %d: bulk f=%.12e lam_def=%.6e lam_max=%.6e escape without polish\n",
