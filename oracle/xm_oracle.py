@@ -349,8 +349,12 @@ def rtr(Q, Y0, grad_tol_rel=1e-10, grad_tol_abs=0.0, max_outer=500, max_inner=10
     hist = [(f, gn)]
     k = 0
     eps_reg = 1e3 * np.finfo(np.float64).eps
+    # Rounding floor of the Riemannian gradient: FP64 products Q Y carry errors of order
+    # eps * ||Q Y||; below ~1e4 eps * ||2 Q Y0|| a first-order point is reached for all purposes.
+    floor = 1e4 * np.finfo(np.float64).eps * float(np.linalg.norm(2.0 * G))
+    best = (gn, Y, f)
     for k in range(1, max_outer + 1):
-        if gn <= max(grad_tol_abs, grad_tol_rel * g0):
+        if gn <= max(grad_tol_abs, grad_tol_rel * g0, floor):
             break
         eta, Heta, nin, _ = tcg(Q, Y, grad, L, Delta, max_inner=max_inner)
         inner_total += nin
@@ -373,10 +377,15 @@ def rtr(Q, Y0, grad_tol_rel=1e-10, grad_tol_abs=0.0, max_outer=500, max_inner=10
             grad = 2.0 * (G - apply_blockdiag(L, Y))
             gn = math.sqrt(inner(grad, grad))
         hist.append((f, gn))
+        if gn < best[0]:
+            best = (gn, Y, f)
         if verbose:
             print(f"rtr {k:3d} f={f:.12e} |g|={gn:.3e} rho={rho:.3f} D={Delta:.3e} inner={nin}")
         if Delta < 1e-15 * Delta_bar:
             break
+    # near the rounding floor accepted steps along flat directions can raise ||grad||; return the
+    # most stationary iterate seen
+    gn, Y, f = best
     return RTRResult(Y, f, gn, k, inner_total, sweeps, hist)
 
 
@@ -619,3 +628,77 @@ def umeyama_weighted(x, y, omega):
     t = my - s * R @ mx
     res = s * x @ R.T + t - y
     return s, R, t, float((omega * (res * res).sum(1)).sum())
+
+
+# ======================================================================================
+# Adjoint of the certified optimum (implicit differentiation of the stationarity condition)
+# ======================================================================================
+
+def anchored_blocks_grad(Y, dL_dG):
+    """Euclidean gradient in Y of L(G) with G_i = Y_0 Y_i^T (i >= 1): the anchored scaled
+    rotations s_i R_i of a tight (rank-3) optimum are exactly the blocks X_0i of X = Y Y^T."""
+    Yb = blocks(Y)
+    dY = np.zeros_like(Yb)
+    for i in range(1, Yb.shape[0]):
+        dY[i] = dL_dG[i].T @ Yb[0]
+        dY[0] += dL_dG[i] @ Yb[i]
+    return dY.reshape(Y.shape)
+
+
+def conjugate_gradient(apply, b, tol=1e-14, maxit=10000):
+    """Plain CG for a symmetric positive semi-definite operator and a consistent right side."""
+    x = np.zeros_like(b)
+    r = b.copy()
+    p = r.copy()
+    rr = inner(r, r)
+    r0 = math.sqrt(rr)
+    for _ in range(maxit):
+        if math.sqrt(rr) <= tol * r0:
+            break
+        Ap = apply(p)
+        pAp = inner(p, Ap)
+        if pAp <= 0:
+            break
+        a = rr / pAp
+        x = x + a * p
+        r = r - a * Ap
+        rr_new = inner(r, r)
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+    return x
+
+
+def optimal_residuals(N, M, cam, lmk, ukp, w, U):
+    """Residuals e_e = U_i^T u_e + t_i - p_k at the least-squares t (t_0 = 0) and p for every
+    column of U (n x c), by the sparse normal equations (the elimination of App. A)."""
+    cam, lmk, ukp, w = _validated(N, M, cam, lmk, ukp, w)
+    E = cam.size
+    a = np.einsum("eab,ea->eb", blocks(U)[cam], ukp)              # E x c
+    rows = np.concatenate([np.arange(E)[cam > 0], np.arange(E)])
+    cols = np.concatenate([cam[cam > 0] - 1, N - 1 + lmk])
+    vals = np.concatenate([np.ones(int((cam > 0).sum())), -np.ones(E)])
+    Gm = sp.csr_matrix((vals, (rows, cols)), shape=(E, N - 1 + M))
+    Hm = (Gm.T @ sp.diags(w) @ Gm).tocsc()
+    sol = spla.splu(Hm).solve(-(Gm.T @ (w[:, None] * a)))
+    return a + Gm @ sol
+
+
+def adjoint(N, M, cam, lmk, ukp, w, Y, dL_dG, Q=None, tol=1e-14):
+    """Gradient of L(G(theta)) w.r.t. the lifted keypoints u (E x 3) and weights w (E) at a
+    certified optimum Y of rank 3 (G_i = s_i R_i).  Implicit differentiation: the Riemannian
+    gradient 2 P_Y(Q Y) vanishes, so Hess[Ydot] = -P_Y(2 Qdot Y); with Hess[lam] = P_Y(dL/dY),
+    dL/dQ = -(lam Y^T + Y lam^T).  The bilinear form a^T Q b equals sum_e w_e e_a e_b at the
+    optimal residuals (Prop. 1), whose derivatives follow from the envelope theorem:
+        d(a^T Q b)/du_e = w_e (e_a b_i + e_b a_i),   d(a^T Q b)/dw_e = e_a e_b."""
+    cam, lmk, ukp, w = _validated(N, M, cam, lmk, ukp, w)
+    Q = build_Q_schur(N, M, cam, lmk, ukp, w) if Q is None else Q
+    L = lambdas(Y, Q @ Y)
+    gL = proj_tangent(Y, anchored_blocks_grad(Y, dL_dG))
+    lam = conjugate_gradient(lambda v: hess(Q, Y, v, L), gL, tol=tol)
+    r = Y.shape[1]
+    e = optimal_residuals(N, M, cam, lmk, ukp, w, np.hstack([Y, lam]))
+    eY, eL = e[:, :r], e[:, r:]
+    Yb, Lb = blocks(Y)[cam], blocks(lam)[cam]                     # E x 3 x r
+    d_u = -2.0 * w[:, None] * (np.einsum("ear,er->ea", Yb, eL) + np.einsum("ear,er->ea", Lb, eY))
+    d_w = -2.0 * np.sum(eL * eY, axis=1)
+    return d_u, d_w, lam
