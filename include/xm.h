@@ -184,6 +184,46 @@ xm_status xm_pipeline_host(xm_ctx* ctx, int N, int M, int64_t E, const int32_t* 
                            const double* w_host, const xm_opts* opts, double* R_host,
                            double* s_host, xm_info* info);
 
+/* ---- adjoint of the certified optimum (implicit differentiation of Sec. 3's first-order
+ * condition through the Q of App. A) ---------------------------------------------------------
+ * Loss L(G) of the anchored blocks G_i = Y_0 Y_i^T (i >= 1; equal to s_i R_i of Sec. 2.2 at a
+ * tight optimum with R_0 = I, s_0 = 1).  Given dL/dG, returns dL/du_e (E x 3) and dL/dw_e (E)
+ * for the lifted keypoints u_e = d_e * bearing_e and the weights of Eq. 1 (dL/dd_e follows as
+ * <dL/du_e, bearing_e>).  Steps: lambda with Hess[lambda] = P_Y(dL/dY) (CG on the Riemannian
+ * Hessian of Sec. 3; the operator is positive semi-definite at a certified optimum), then
+ * dL/dQ = -(lambda Y^T + Y lambda^T) pulled back to the observations by the envelope theorem
+ * at the optimal translations and landmarks of Prop. 1:
+ *   dL/du_e = -2 w_e (Y_i e_lambda + lambda_i e_Y),   dL/dw_e = -2 <e_lambda, e_Y>,
+ * e_a = U_i^T u_e + t_i - p_k the least-squares residual of column set a (t_0 = 0).
+ * Arguments (device pointers unless stated): q from xm_build_Q on the same observations, with
+ * an FP64 copy (and an FP32 copy unless opts->prec == XM_FP64); Y n x ldy row-major, the
+ * first r columns used (the Y_out of xm_solve, r = info.rank); cam, lmk, ukp, w as for
+ * xm_build_Q; dL_dG N x 3 x 3 row-major (entry 0 ignored).  Outputs dL_dukp (E x 3), dL_dw (E)
+ * and, if not NULL, lam (n x r).  opts: prec XM_FP64 runs the CG on the FP64 operator; any
+ * other value runs FP32 inner CG (at most max_tcg iterations per pass) inside FP64 residual
+ * refinement (at most max_polish passes) until ||res|| <= grad_tol_rel ||P_Y(dL/dY)||.
+ * Allocates an N x N FP64 work matrix (the Cholesky factor of the anchored camera block) and
+ * O(E + n) more, freed before return.  Synchronous.  Returns XM_ENOCONV (outputs written,
+ * info->res_rel says how far) when the refinement cap is reached, XM_EDISCONNECTED if the
+ * camera block is singular, XM_EINVAL on bad arguments. */
+typedef struct xm_adj_info {
+  double res_rel;          /* ||P_Y(dL/dY) - Hess[lambda]|| / ||P_Y(dL/dY)||, FP64 operator  */
+  double g_norm;           /* ||P_Y(dL/dY)||                                                   */
+  double grad_norm_Y;      /* ||rgrad|| at Y (the solve's stationarity, FP64)                  */
+  int n_refine;            /* FP64 residual passes after the first                            */
+  int n_cg;                /* inner CG iterations over all passes                             */
+  int n_sweeps_fp32, n_sweeps_fp64;
+  double t_lambda_s;       /* wall time of the adjoint solve                                   */
+  double t_resid_s;        /* wall time of the residual pull-back (incl. the Cholesky)         */
+  double t_total_s;
+  long launches;           /* kernel launches of this call (library calls not counted)        */
+} xm_adj_info;
+
+xm_status xm_backward(xm_ctx* ctx, const xm_qmat* q, const xm_opts* opts, int r, const double* Y,
+                      int ldy, int M, int64_t E, const int32_t* cam, const int32_t* lmk,
+                      const double* ukp, const double* w, const double* dL_dG, double* dL_dukp,
+                      double* dL_dw, double* lam, xm_adj_info* info);
+
 #ifdef __cplusplus
 }
 #endif

@@ -14,6 +14,7 @@
 #include <cublas_v2.h>
 #include <cusolverDn.h>
 
+#include <algorithm>
 #include <chrono>
 
 #include "xm_internal.cuh"
@@ -405,6 +406,159 @@ xm_status build_Q(xm_ctx* ctx, int N, int M, int64_t E, const int32_t* cam, cons
   XM_TRY(check_device_error(ctx, "Q construction"));
   if (t_build)
     *t_build = std::chrono::duration<double>(std::chrono::steady_clock::now() - tic).count();
+  return XM_OK;
+}
+
+}  // namespace xm
+
+// ------------------------------------------------------------------ adjoint support
+namespace xm {
+
+// Index and value checks of the observation arrays (DEV_BAD_INDEX / DEV_BAD_VALUE).
+xm_status validate_obs(xm_ctx* ctx, int N, int M, int64_t E, const int32_t* cam, const int32_t* lmk,
+                       const double* ukp, const double* w) {
+  cudaStream_t st = ctx->stream;
+  XM_CUDA_TRY(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), st));
+  if (E > 0) {
+    k_validate<<<grid_for(E, 256, ctx->num_sms), 256, 0, st>>>(E, N, M, cam, lmk, ukp, w, ctx->d_err);
+    XM_CUDA_TRY(cudaGetLastError());
+  }
+  return check_device_error(ctx, "observation validation");
+}
+
+__global__ void k_count_keys(int64_t E, const int32_t* key, int* cnt) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E;
+       e += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&cnt[key[e]], 1);
+}
+
+// Observations grouped by key (landmark or camera): off (K+1) and idx (E), both allocated by the
+// caller; within a group the observation indices are ascending, so that every per-group sum
+// taken in idx order is deterministic.
+xm_status obs_csr(xm_ctx* ctx, int64_t E, const int32_t* key, int K, int64_t* off, int64_t* idx) {
+  cudaStream_t st = ctx->stream;
+  const int threads = 256;
+  if (K <= 0) return XM_OK;
+  if (E <= 0) {
+    XM_CUDA_TRY(cudaMemsetAsync(off, 0, sizeof(int64_t) * (size_t)(K + 1), st));
+    return XM_OK;
+  }
+  DevBuf cnt, bsum, cursor;
+  const int nb = (K + 1023) / 1024;
+  XM_CUDA_TRY(cudaMalloc(&cnt.p, sizeof(int) * (size_t)K));
+  XM_CUDA_TRY(cudaMalloc(&bsum.p, sizeof(int64_t) * (size_t)(nb + 1)));
+  XM_CUDA_TRY(cudaMalloc(&cursor.p, sizeof(int) * (size_t)K));
+  XM_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, sizeof(int) * (size_t)K, st));
+  XM_CUDA_TRY(cudaMemsetAsync(cursor.p, 0, sizeof(int) * (size_t)K, st));
+  k_count_keys<<<grid_for(E, threads, ctx->num_sms), threads, 0, st>>>(E, key, cnt.as<int>());
+  k_scan_blocks<<<nb, 1024, 0, st>>>(cnt.as<int>(), off, bsum.as<int64_t>(), K);
+  k_scan_sums<<<1, 32, 0, st>>>(bsum.as<int64_t>(), nb);
+  k_scan_add<<<nb, 1024, 0, st>>>(off, bsum.as<int64_t>(), K);
+  k_csr_fill<<<grid_for(E, threads, ctx->num_sms), threads, 0, st>>>(E, key, off, cursor.as<int>(), idx);
+  k_csr_sort<<<grid_for(K, threads, ctx->num_sms), threads, 0, st>>>(K, off, idx);
+  XM_CUDA_TRY(cudaGetLastError());
+  XM_CUDA_TRY(cudaStreamSynchronize(st));   // the scratch above is freed on return
+  return XM_OK;
+}
+
+// d_k = sum of the weights of landmark k; S (row-major upper triangle) gets the camera
+// diagonal sum_e w_e, one thread per camera group so that the sums are deterministic
+__global__ void k_S_diag(int N, int M, const int64_t* coff, const int64_t* cidx,
+                         const int64_t* loff, const int64_t* lidx, const double* w, double* S,
+                         double* d) {
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t j = tid; j < N; j += stride) {
+    double s = 0.0;
+    for (int64_t x = coff[j]; x < coff[j + 1]; ++x) s += w[cidx[x]];
+    S[(size_t)j * N + j] = s;
+  }
+  for (int64_t k = tid; k < M; k += stride) {
+    double s = 0.0;
+    for (int64_t x = loff[k]; x < loff[k + 1]; ++x) s += w[lidx[x]];
+    d[k] = s;
+  }
+}
+
+// S_ij -= w_a w_b / d_k over the ordered observer pairs (a, b) of every landmark k with
+// cam_a <= cam_b (row-major upper triangle == column-major lower triangle)
+__global__ void k_landmark_S(int M, int N, const int64_t* off, const int64_t* idx,
+                             const int32_t* cam, const double* w, const double* d, double* S) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < M; k += gridDim.x * blockDim.x) {
+    const int64_t a0 = off[k], a1 = off[k + 1];
+    if (a1 <= a0 || !(d[k] > 0.0)) continue;
+    const double dinv = 1.0 / d[k];
+    for (int64_t x = a0; x < a1; ++x) {
+      const int i = cam[idx[x]];
+      const double wa = w[idx[x]] * dinv;
+      for (int64_t y = a0; y < a1; ++y) {
+        const int j = cam[idx[y]];
+        if (i <= j) atomicAdd(&S[(size_t)i * N + j], -wa * w[idx[y]]);
+      }
+    }
+  }
+}
+
+// The camera block S = diag(sum w) - sum_k (w w^T)/d_k that remains after the landmarks are
+// eliminated (App. A), and the Cholesky factor of Sbar (camera 0 anchored, t_0 = 0).  S (N x N)
+// and d (M) are allocated by the caller; on return the column-major lower triangle of rows and
+// columns 1..N-1 of S (leading dimension N) holds the factor.
+xm_status schur_S_factor(xm_ctx* ctx, int N, int M, const int32_t* cam, const double* w,
+                         const int64_t* coff, const int64_t* cidx, const int64_t* loff,
+                         const int64_t* lidx, double* S, double* d) {
+  cudaStream_t st = ctx->stream;
+  XM_CUDA_TRY(cudaMemsetAsync(S, 0, sizeof(double) * (size_t)N * N, st));
+  const int g = grid_for(std::max(N, M), 128, ctx->num_sms);
+  k_S_diag<<<g, 128, 0, st>>>(N, M, coff, cidx, loff, lidx, w, S, d);
+  if (M > 0)
+    k_landmark_S<<<grid_for(M, 128, ctx->num_sms), 128, 0, st>>>(M, N, loff, lidx, cam, w, d, S);
+  XM_CUDA_TRY(cudaGetLastError());
+  if (N > 1) {
+    if (!ctx->cusolver) {
+      cusolverDnHandle_t h;
+      XM_CUSOLVER_TRY(cusolverDnCreate(&h));
+      ctx->cusolver = h;
+    }
+    cusolverDnHandle_t cs = static_cast<cusolverDnHandle_t>(ctx->cusolver);
+    XM_CUSOLVER_TRY(cusolverDnSetStream(cs, st));
+    const int m = N - 1;
+    double* Sbar = S + N + 1;
+    int lwork = 0;
+    XM_CUSOLVER_TRY(cusolverDnDpotrf_bufferSize(cs, CUBLAS_FILL_MODE_LOWER, m, Sbar, N, &lwork));
+    DevBuf work, info;
+    XM_CUDA_TRY(cudaMalloc(&work.p, sizeof(double) * (size_t)(lwork > 0 ? lwork : 1)));
+    XM_CUDA_TRY(cudaMalloc(&info.p, sizeof(int)));
+    XM_CUSOLVER_TRY(cusolverDnDpotrf(cs, CUBLAS_FILL_MODE_LOWER, m, Sbar, N, work.as<double>(), lwork,
+                                     info.as<int>()));
+    int hinfo = 0;
+    XM_CUDA_TRY(cudaMemcpyAsync(&hinfo, info.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    XM_CUDA_TRY(cudaStreamSynchronize(st));
+    if (hinfo != 0)
+      return set_error(XM_EDISCONNECTED, "translation Schur block not positive definite (minor %d)", hinfo);
+  }
+  return XM_OK;
+}
+
+// b (N x c, column-major, leading dimension N) <- t with Sbar tbar = -bbar and t_0 = 0, using
+// the factor left in S by schur_S_factor.
+xm_status schur_S_solve(xm_ctx* ctx, int N, const double* S, double* b, int c) {
+  cudaStream_t st = ctx->stream;
+  if (N > 1 && c > 0) {
+    if (!ctx->cublas) {
+      cublasHandle_t h;
+      XM_CUBLAS_TRY(cublasCreate(&h));
+      ctx->cublas = h;
+    }
+    cublasHandle_t cb = static_cast<cublasHandle_t>(ctx->cublas);
+    XM_CUBLAS_TRY(cublasSetStream(cb, st));
+    const double minus_one = -1.0, one = 1.0;
+    const double* Sbar = S + N + 1;
+    XM_CUBLAS_TRY(cublasDtrsm(cb, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N,
+                              CUBLAS_DIAG_NON_UNIT, N - 1, c, &minus_one, Sbar, N, b + 1, N));
+    XM_CUBLAS_TRY(cublasDtrsm(cb, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T,
+                              CUBLAS_DIAG_NON_UNIT, N - 1, c, &one, Sbar, N, b + 1, N));
+  }
+  if (c > 0) XM_CUDA_TRY(cudaMemset2DAsync(b, sizeof(double) * N, 0, sizeof(double), c, st));
   return XM_OK;
 }
 

@@ -95,6 +95,21 @@ xm_status ensure_partials(xm_ctx* ctx, size_t ndoubles);
 xm_status qy_launch(xm_ctx* ctx, const DeviceQ& q, int prec, int R, const void* Y, void* W,
                     const int* skip, cudaStream_t st);
 
+// ------------------------------------------------------------------ adjoint support (xm_build.cu)
+// Index and value checks of the observation arrays (synchronous; XM_EINVAL on a bad entry).
+xm_status validate_obs(xm_ctx* ctx, int N, int M, int64_t E, const int32_t* cam, const int32_t* lmk,
+                       const double* ukp, const double* w);
+// Observations grouped by key (ascending observation index within a group); off (K+1), idx (E)
+// are allocated by the caller.
+xm_status obs_csr(xm_ctx* ctx, int64_t E, const int32_t* key, int K, int64_t* off, int64_t* idx);
+// Camera block S left after landmark elimination and the Cholesky factor of Sbar (camera 0
+// anchored); S (N x N) and d (M, landmark weight sums) are allocated by the caller.
+xm_status schur_S_factor(xm_ctx* ctx, int N, int M, const int32_t* cam, const double* w,
+                         const int64_t* coff, const int64_t* cidx, const int64_t* loff,
+                         const int64_t* lidx, double* S, double* d);
+// b (N x c column-major) <- t with Sbar tbar = -bbar, t_0 = 0.
+xm_status schur_S_solve(xm_ctx* ctx, int N, const double* S, double* b, int c);
+
 // ------------------------------------------------------------------ device helpers
 #ifdef __CUDACC__
 constexpr long long WAIT_LIMIT = 1ll << 24;   // try_wait polls before a wait gives up

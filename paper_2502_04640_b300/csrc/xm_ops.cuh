@@ -252,6 +252,42 @@ k_tcg_init(int n_rows, const To* __restrict__ G, Ti* eta, Ti* Heta, Ti* r, Ti* d
   }
 }
 
+// Hd_i = 2 P_{Y_i}(Wd_i - Lambda_i d_i) for camera i (Wd_i is reset to zero for the next
+// accumulating sweep); returns <d_i, Hd_i>.
+template <typename T, int R>
+__device__ __forceinline__ double hvp_block(int i, const T* __restrict__ Y, T* __restrict__ Wd,
+                                            const T* __restrict__ delta, T* __restrict__ Hd,
+                                            const double* __restrict__ Lam) {
+  using C = double;   // per-camera arithmetic in FP64 whatever the storage type
+  C y[3][R], w[3][R], d[3][R], L[3][3];
+  load_block<T, C, R>(Y, i, y);
+  load_block<T, C, R>(Wd, i, w);
+  zero_block<T, R>(Wd, i);
+  load_block<T, C, R>(delta, i, d);
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) L[a][b] = C(Lam[(size_t)9 * i + 3 * a + b]);
+  C A[3][R];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int j = 0; j < R; ++j)
+      A[a][j] = C(2) * (w[a][j] - (L[a][0] * d[0][j] + L[a][1] * d[1][j] + L[a][2] * d[2][j]));
+  C S[3][3], alpha;
+  dual_block<C, R>(A, y, i == 0, S, alpha);
+  double kap = 0.0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      A[a][j] -= S[a][0] * y[0][j] + S[a][1] * y[1][j] + S[a][2] * y[2][j];
+      kap += double(d[a][j]) * double(A[a][j]);
+    }
+  store_block<T, C, R>(Hd, i, A);
+  return kap;
+}
+
 // Hd = 2 P_Y(Wd - Lambda d); kappa = <d, Hd>; then decide the step (alpha, or tau to the
 // trust-region boundary on negative curvature / when the CG step leaves the region).
 template <typename T, int R>
@@ -260,38 +296,9 @@ k_hvp_epi(int N, const T* __restrict__ Y, T* __restrict__ Wd, const T* __restric
           T* __restrict__ Hd, const double* __restrict__ Lam, Scal* sc, double* partials,
           unsigned* counter) {
   if (sc->done) return;
-  using C = double;   // per-camera arithmetic in FP64 whatever the storage type
   double v[1] = {0.0};
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < N) {
-    C y[3][R], w[3][R], d[3][R], L[3][3];
-    load_block<T, C, R>(Y, i, y);
-    load_block<T, C, R>(Wd, i, w);
-    zero_block<T, R>(Wd, i);
-    load_block<T, C, R>(delta, i, d);
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int b = 0; b < 3; ++b) L[a][b] = C(Lam[(size_t)9 * i + 3 * a + b]);
-    C A[3][R];
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int j = 0; j < R; ++j)
-        A[a][j] = C(2) * (w[a][j] - (L[a][0] * d[0][j] + L[a][1] * d[1][j] + L[a][2] * d[2][j]));
-    C S[3][3], alpha;
-    dual_block<C, R>(A, y, i == 0, S, alpha);
-    double kap = 0.0;
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int j = 0; j < R; ++j) {
-        A[a][j] -= S[a][0] * y[0][j] + S[a][1] * y[1][j] + S[a][2] * y[2][j];
-        kap += double(d[a][j]) * double(A[a][j]);
-      }
-    store_block<T, C, R>(Hd, i, A);
-    v[0] = kap;
-  }
+  if (i < N) v[0] = hvp_block<T, R>(i, Y, Wd, delta, Hd, Lam);
   grid_reduce<1>(v, partials, counter, [&](double* t) {
     const double kap = t[0];
     sc->kappa = kap;
@@ -568,7 +575,7 @@ __global__ void k_zv_epi(int N, Tw* __restrict__ Wz, const double* __restrict__ 
 }
 
 // c[j] = <V_j, w> for the m columns of V (column-major, stride ld); one block per column
-__global__ void k_gemv_t(int n, int m, const double* __restrict__ V, size_t ld,
+static __global__ void k_gemv_t(int n, int m, const double* __restrict__ V, size_t ld,
                          const double* __restrict__ w, double* __restrict__ c) {
   __shared__ double sh[8];
   for (int j = blockIdx.x; j < m; j += gridDim.x) {
@@ -588,7 +595,7 @@ __global__ void k_gemv_t(int n, int m, const double* __restrict__ V, size_t ld,
 }
 
 // w -= V c (m columns)
-__global__ void k_gemv_n_sub(int n, int m, const double* __restrict__ V, size_t ld,
+static __global__ void k_gemv_n_sub(int n, int m, const double* __restrict__ V, size_t ld,
                              const double* __restrict__ c, double* __restrict__ w) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
     double s = 0.0;
@@ -598,7 +605,7 @@ __global__ void k_gemv_n_sub(int n, int m, const double* __restrict__ V, size_t 
 }
 
 // w -= a[k] v_k + b[k-1] v_{k-1}  (coefficients read on the device)
-__global__ void k_lanczos_3term(int n, double* __restrict__ w, const double* __restrict__ vk,
+static __global__ void k_lanczos_3term(int n, double* __restrict__ w, const double* __restrict__ vk,
                                 const double* __restrict__ vkm1, const double* alpha,
                                 const double* beta, int k) {
   const double a = alpha[k];
@@ -608,7 +615,7 @@ __global__ void k_lanczos_3term(int n, double* __restrict__ w, const double* __r
 }
 
 // dst = w / sqrt(*nrm2); *beta_out = sqrt(*nrm2)
-__global__ void k_normalize(int n, const double* __restrict__ w, const double* nrm2,
+static __global__ void k_normalize(int n, const double* __restrict__ w, const double* nrm2,
                             double* __restrict__ dst, double* beta_out) {
   const double b = sqrt(*nrm2);
   const double inv = b > 0.0 ? 1.0 / b : 0.0;
@@ -618,7 +625,7 @@ __global__ void k_normalize(int n, const double* __restrict__ w, const double* n
 }
 
 // deterministic pseudo-random start vector (splitmix64 of (seed, index)), uniform in [-1, 1)
-__global__ void k_random_vec(int n, uint64_t seed, double* v) {
+static __global__ void k_random_vec(int n, uint64_t seed, double* v) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
     uint64_t z = seed + 0x9E3779B97F4A7C15ull * (uint64_t)(e + 1);
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -632,7 +639,7 @@ __global__ void k_random_vec(int n, uint64_t seed, double* v) {
 // Per camera: Ubar_i = Yh_i^T (3 x 3), G_i = O0^T Ubar_i, s_i = ||G_i||_F / sqrt(3),
 // R_i = SO(3) projection of G_i (SVD with determinant fix, Prop. 2); the anchor is (I, 1).
 // Writes R (N x 9, row-major), s (N) and Yhat = [s_i R_i]^T (n_rows x 4, last column zero).
-__global__ void k_round(int N, const double* __restrict__ Yh, const double* __restrict__ O0,
+static __global__ void k_round(int N, const double* __restrict__ Yh, const double* __restrict__ O0,
                         double* __restrict__ Rout, double* __restrict__ sout,
                         double* __restrict__ Yhat) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;

@@ -50,6 +50,18 @@ class XmInfo(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class XmAdjInfo(ctypes.Structure):
+    _fields_ = [("res_rel", ctypes.c_double), ("g_norm", ctypes.c_double),
+                ("grad_norm_Y", ctypes.c_double), ("n_refine", ctypes.c_int),
+                ("n_cg", ctypes.c_int), ("n_sweeps_fp32", ctypes.c_int),
+                ("n_sweeps_fp64", ctypes.c_int), ("t_lambda_s", ctypes.c_double),
+                ("t_resid_s", ctypes.c_double), ("t_total_s", ctypes.c_double),
+                ("launches", ctypes.c_long)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class XmError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -93,6 +105,9 @@ def lib() -> ctypes.CDLL:
                                       ctypes.POINTER(XmInfo)]),
         "xm_pipeline_host": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int64, _P, _P, _P,
                                             _P, ctypes.POINTER(XmOpts), _P, _P, ctypes.POINTER(XmInfo)]),
+        "xm_backward": (ctypes.c_int, [_P, _P, ctypes.POINTER(XmOpts), ctypes.c_int, _P, ctypes.c_int,
+                                       ctypes.c_int, ctypes.c_int64, _P, _P, _P, _P, _P, _P, _P, _P,
+                                       ctypes.POINTER(XmAdjInfo)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -265,6 +280,32 @@ def xm_certify(q: QMat, Y, opts: XmOpts | None = None):
     _check(lib().xm_certify(q.ctx.h, q.h, ctypes.byref(opts), Y.shape[1], _ptr(Y), _ptr(Lam), _ptr(v),
                             ctypes.byref(info)))
     return dict(Lambda=Lam, v=v, info=info.as_dict())
+
+
+def xm_backward(q: QMat, Y, rank: int, M: int, cam, lmk, ukp, w, dL_dG, opts: XmOpts | None = None,
+                want_lambda: bool = False, allow_noconv: bool = False):
+    """Adjoint of the certified optimum: (dL/du (E x 3), dL/dw (E), lambda or None, info, status)
+    for a loss of G_i = Y_0 Y_i^T.  Y: n x ldy float64 CUDA tensor (xm_solve's Y), rank its
+    used columns; dL_dG: N x 3 x 3 float64 CUDA tensor; observations as for xm_build_Q."""
+    import torch
+    dev = f"cuda:{q.ctx.device}"
+    opts = opts or xm_default_opts()
+    E = int(cam.shape[0])
+    if Y.dtype != torch.float64 or Y.dim() != 2 or Y.shape[0] != q.n:
+        raise ValueError(f"Y must be float64 of shape (n={q.n}, ldy)")
+    if dL_dG.dtype != torch.float64 or tuple(dL_dG.shape) != (q.N, 3, 3):
+        raise ValueError(f"dL_dG must be float64 of shape ({q.N}, 3, 3)")
+    Y = Y.contiguous()
+    dL_dG = dL_dG.contiguous()
+    d_u = torch.empty((E, 3), dtype=torch.float64, device=dev)
+    d_w = torch.empty((E,), dtype=torch.float64, device=dev)
+    lam = torch.empty((q.n, rank), dtype=torch.float64, device=dev) if want_lambda else None
+    info = XmAdjInfo()
+    allow = (XM_OK, XM_ENOCONV) if allow_noconv else (XM_OK,)
+    st = _check(lib().xm_backward(q.ctx.h, q.h, ctypes.byref(opts), rank, _ptr(Y), Y.shape[1], M, E,
+                                  _ptr(cam), _ptr(lmk), _ptr(ukp), _ptr(w), _ptr(dL_dG), _ptr(d_u),
+                                  _ptr(d_w), _ptr(lam), ctypes.byref(info)), allow)
+    return d_u, d_w, lam, info.as_dict(), st
 
 
 def xm_pipeline_host(ctx: Context, N: int, M: int, cam, lmk, ukp, w, opts: XmOpts | None = None):

@@ -1,0 +1,185 @@
+"""Parity of the CUDA adjoint (xm_backward) with the FP64 oracle's adjoint, and finite
+differences of complete GPU re-solves on the 50-camera trajectory sub-instance.
+
+The outputs dL/du and dL/dw are gauge invariant (the loss reads G_i = Y_0 Y_i^T and a gauge
+component of lambda cancels in lambda Y^T + Y lambda^T), so they are compared element by
+element.  Tolerances:
+  * same Y on both sides: the two adjoint solves stop at relative residuals 1e-12 (CUDA,
+    grad_tol_rel) and 1e-14 (oracle); the solution error is that times the condition number of
+    the Hessian on the tangent space (below 1e4 on these scenes), so 1e-6 relative to the
+    largest entry leaves a wide margin over the expected 1e-8;
+  * against the oracle's own solve: both optima agree to the solve tolerance, so 1e-5;
+  * finite differences: central differences with step h along a random direction over all
+    observations, truncation O(h^2) and solve noise O(tol / h), so 1e-5 relative."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import scenes
+from oracle import xm_oracle as O
+from tests.gpu_util import ctx, torch
+
+pytestmark = pytest.mark.gpu
+
+PRECS = {"fp64": 0, "fp32": 1}
+
+
+@pytest.fixture(scope="module")
+def C():
+    c = ctx()
+    yield c
+    c.close()
+
+
+def _scenes():
+    return {
+        "circle": scenes.circle_scene(12, 150, 4, 0.03, seed=41, w_range=(0.5, 1.5)),
+        "random": scenes.random_scene(9, 120, noise=0.02, seed=42, center_sigma=2.0),
+        "traj50": scenes.sub_scene(scenes.trajectory_scene(200, 20000, seed=43), 50),
+    }
+
+
+def _solve(C, sc, opts, Y0=None):
+    from paper_2502_04640_b300 import xm
+    t = xm.scene_tensors(sc)
+    q = xm.xm_build_Q(C, sc.N, sc.M, *t)
+    out = xm.xm_solve(q, opts, Y0=Y0)
+    return q, t, out
+
+
+def _dG(sc, seed):
+    D = np.random.default_rng(seed).standard_normal((sc.N, 3, 3))
+    D[0] = 0.0
+    return D
+
+
+def _max_rel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+@pytest.mark.parametrize("name", ["circle", "random", "traj50"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_backward_matches_oracle_adjoint(C, name, prec):
+    from paper_2502_04640_b300 import xm
+    sc = _scenes()[name]
+    opts = xm.xm_default_opts(prec=0, grad_tol_rel=1e-12)
+    q, t, out = _solve(C, sc, opts)
+    assert out["status"] == 0 and out["info"]["certified"] == 1
+    r = out["info"]["rank"]
+    D = _dG(sc, 7)
+    bopts = xm.xm_default_opts(prec=PRECS[prec], grad_tol_rel=1e-12)
+    d_u, d_w, lam, info, st = xm.xm_backward(q, out["Y"], r, sc.M, *t,
+                                             torch.as_tensor(D, device="cuda:0"), bopts,
+                                             want_lambda=True)
+    assert st == 0 and info["res_rel"] <= 1e-12
+    Y = out["Y"].cpu().numpy()[:, :r]
+    ref_u, ref_w, ref_lam = O.adjoint(sc.N, sc.M, sc.cam, sc.lmk, sc.ukp, sc.w, Y, D)
+    assert _max_rel(d_u.cpu().numpy(), ref_u) <= 1e-6
+    assert _max_rel(d_w.cpu().numpy(), ref_w) <= 1e-6
+    # lambda itself is fixed only up to the kernel of the Hessian: compare Hess[lambda]
+    Qo = O.build_Q_schur(sc.N, sc.M, sc.cam, sc.lmk, sc.ukp, sc.w)
+    L = O.lambdas(Y, Qo @ Y)
+    lam_g = lam.cpu().numpy()
+    gL = O.proj_tangent(Y, O.anchored_blocks_grad(Y, D))
+    assert np.linalg.norm(O.hess(Qo, Y, lam_g, L) - gL) <= 1e-9 * np.linalg.norm(gL)
+    if prec == "fp32":
+        assert info["n_sweeps_fp32"] > info["n_sweeps_fp64"]
+    q.free()
+
+
+def test_backward_matches_oracle_solution(C):
+    """Both pipelines end to end (own solve, own adjoint) on the same observations."""
+    from paper_2502_04640_b300 import xm
+    sc = _scenes()["circle"]
+    q, t, out = _solve(C, sc, xm.xm_default_opts(grad_tol_rel=1e-12))
+    r = out["info"]["rank"]
+    D = _dG(sc, 8)
+    d_u, d_w, _, info, _ = xm.xm_backward(q, out["Y"], r, sc.M, *t, torch.as_tensor(D, device="cuda:0"),
+                                          xm.xm_default_opts(grad_tol_rel=1e-12))
+    Qo = O.build_Q_schur(sc.N, sc.M, sc.cam, sc.lmk, sc.ukp, sc.w)
+    ref = O.solve(Qo, r0=4, grad_tol_rel=1e-13)
+    assert ref.certified
+    ref_u, ref_w, _ = O.adjoint(sc.N, sc.M, sc.cam, sc.lmk, sc.ukp, sc.w, ref.Y, D, Q=Qo)
+    assert _max_rel(d_u.cpu().numpy(), ref_u) <= 1e-5
+    assert _max_rel(d_w.cpu().numpy(), ref_w) <= 1e-5
+    q.free()
+
+
+def test_finite_differences_trajectory_50(C):
+    """Directional derivatives of L = <D, G> along random directions in u and in w, by central
+    differences of warm-started FP64 GPU re-solves, against the adjoint's dL/du and dL/dw."""
+    from paper_2502_04640_b300 import xm
+    sc = scenes.sub_scene(scenes.config4(), 50)
+    opts = xm.xm_default_opts(prec=0, grad_tol_rel=1e-13)
+    q, t, out = _solve(C, sc, opts)
+    assert out["status"] == 0 and out["info"]["certified"] == 1
+    r = out["info"]["rank"]
+    Y0 = out["Y"][:, :r].contiguous()
+    D = _dG(sc, 9)
+    d_u, d_w, _, info, st = xm.xm_backward(q, out["Y"], r, sc.M, *t, torch.as_tensor(D, device="cuda:0"),
+                                           xm.xm_default_opts(prec=1, grad_tol_rel=1e-12))
+    assert st == 0
+    q.free()
+    rng = np.random.default_rng(10)
+
+    def loss(ukp, w):
+        s2 = dataclasses.replace(sc, ukp=ukp, w=w)
+        qq, _, o2 = _solve(C, s2, opts, Y0=Y0)
+        assert o2["info"]["certified"] == 1
+        G = (o2["s"][:, None, None] * o2["R"]).cpu().numpy()
+        qq.free()
+        return float(np.sum(D * G))
+
+    du_dir = rng.standard_normal(sc.ukp.shape)
+    h = 1e-5 * float(np.abs(sc.ukp).max())
+    fd = (loss(sc.ukp + h * du_dir, sc.w) - loss(sc.ukp - h * du_dir, sc.w)) / (2 * h)
+    pred = float(np.sum(d_u.cpu().numpy() * du_dir))
+    assert abs(fd - pred) <= 1e-5 * max(abs(pred), 1.0), (fd, pred)
+    dw_dir = rng.uniform(-1.0, 1.0, sc.w.shape) * sc.w
+    hw = 1e-5
+    fd = (loss(sc.ukp, sc.w + hw * dw_dir) - loss(sc.ukp, sc.w - hw * dw_dir)) / (2 * hw)
+    pred = float(np.sum(d_w.cpu().numpy() * dw_dir))
+    assert abs(fd - pred) <= 1e-5 * max(abs(pred), 1.0), (fd, pred)
+
+
+def test_autograd_function(C):
+    from paper_2502_04640_b300 import xm
+    from paper_2502_04640_b300.autograd import xm_solve_G
+    sc = _scenes()["random"]
+    cam, lmk, ukp, w = xm.scene_tensors(sc)
+    ukp = ukp.clone().requires_grad_(True)
+    w = w.clone().requires_grad_(True)
+    opts = xm.xm_default_opts(grad_tol_rel=1e-12)
+    G = xm_solve_G(ukp, w, cam, lmk, sc.N, sc.M, C, opts)
+    D = torch.as_tensor(_dG(sc, 11), device="cuda:0")
+    (D * G).sum().backward()
+    Gn = G.detach().cpu().numpy()
+    Qo = O.build_Q_schur(sc.N, sc.M, sc.cam, sc.lmk, sc.ukp, sc.w)
+    ref = O.solve(Qo, r0=4, grad_tol_rel=1e-13)
+    assert np.abs(Gn - ref.s[:, None, None] * ref.R).max() <= 1e-6 * ref.s.max()
+    ref_u, ref_w, _ = O.adjoint(sc.N, sc.M, sc.cam, sc.lmk, sc.ukp, sc.w, ref.Y, D.cpu().numpy(), Q=Qo)
+    assert _max_rel(ukp.grad.cpu().numpy(), ref_u) <= 1e-5
+    assert _max_rel(w.grad.cpu().numpy(), ref_w) <= 1e-5
+
+
+def test_backward_edge_cases(C):
+    from paper_2502_04640_b300 import xm
+    sc = _scenes()["circle"]
+    q, t, out = _solve(C, sc, xm.xm_default_opts())
+    r = out["info"]["rank"]
+    zero = torch.zeros((sc.N, 3, 3), dtype=torch.float64, device="cuda:0")
+    d_u, d_w, lam, info, st = xm.xm_backward(q, out["Y"], r, sc.M, *t, zero, want_lambda=True)
+    assert st == 0 and info["g_norm"] == 0.0
+    assert float(d_u.abs().max()) == 0.0 and float(d_w.abs().max()) == 0.0
+    assert float(lam.abs().max()) == 0.0
+    # a loss of the anchor entry alone is ignored (G_0 = I is fixed by the gauge)
+    D0 = zero.clone()
+    D0[0] = 1.0
+    d_u, d_w, _, info, st = xm.xm_backward(q, out["Y"], r, sc.M, *t, D0)
+    assert st == 0 and info["g_norm"] == 0.0
+    with pytest.raises(xm.XmError, match="XM_EINVAL"):
+        xm.xm_backward(q, out["Y"], 2, sc.M, *t, zero)
+    with pytest.raises(xm.XmError, match="XM_EINVAL"):
+        xm.xm_backward(q, out["Y"][:, :3].contiguous(), 4, sc.M, *t, zero)
+    q.free()
