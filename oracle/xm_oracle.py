@@ -234,26 +234,69 @@ def proj_tangent(Y, Xi):
     return Xi - apply_blockdiag(S, Y)
 
 
-def cost(Q, Y):
-    return float(np.sum(Y * (Q @ Y)))
+# App. D scale regularisation: F(X) = mu * sum_{i >= 2} (X_{3i,3i} - 1)^2 in the paper's 1-based
+# indexing, i.e. the third diagonal entry of every non-anchor block; here row 3i + 2 of camera
+# i >= 1 (0-based), with X_{3i+2,3i+2} = ||Y_{3i+2,:}||^2.  mu = 0 is the plain problem of Eq. 17.
+
+def scale_reg_x(Y):
+    """x_i = X_{3i+2,3i+2} for every camera (the regularised diagonal entries)."""
+    return np.sum(Y[2::3] * Y[2::3], axis=1)
 
 
-def egrad(Q, Y):
-    return 2.0 * (Q @ Y)
+def scale_reg_F(Y, mu):
+    """F(X) = mu sum_{i >= 1} (x_i - 1)^2."""
+    if mu == 0.0:
+        return 0.0
+    x = scale_reg_x(Y)[1:]
+    return float(mu * np.sum((x - 1.0) ** 2))
 
 
-def rgrad(Q, Y, G=None):
-    """Riemannian gradient 2 (Q - blockdiag(Lambda)) Y = 2 Z Y."""
-    G = Q @ Y if G is None else G
+def scale_reg_diag(Y, mu):
+    """grad_X F as the n-vector of its diagonal: 2 mu (x_i - 1) on row 3i + 2, i >= 1."""
+    d = np.zeros(Y.shape[0])
+    if mu != 0.0:
+        d[2::3] = 2.0 * mu * (scale_reg_x(Y) - 1.0)
+        d[2] = 0.0
+    return d
+
+
+def qeff(Q, Y, mu=0.0):
+    """(Q + grad_X F) Y: half the Euclidean gradient of f(Y) = tr(Y^T Q Y) + F(Y Y^T)."""
+    G = Q @ Y
+    if mu != 0.0:
+        G = G + scale_reg_diag(Y, mu)[:, None] * Y
+    return G
+
+
+def cost(Q, Y, mu=0.0):
+    return float(np.sum(Y * (Q @ Y))) + scale_reg_F(Y, mu)
+
+
+def egrad(Q, Y, mu=0.0):
+    return 2.0 * qeff(Q, Y, mu)
+
+
+def rgrad(Q, Y, G=None, mu=0.0):
+    """Riemannian gradient 2 (Q + grad F - blockdiag(Lambda)) Y = 2 Z Y (App. D's Z)."""
+    G = qeff(Q, Y, mu) if G is None else G
     L = lambdas(Y, G)
     return 2.0 * (G - apply_blockdiag(L, Y))
 
 
-def hess(Q, Y, Xi, L=None):
-    """Riemannian Hessian of f on the embedded manifold: P_Y(2 (Q Xi - blockdiag(Lambda) Xi))."""
+def hess(Q, Y, Xi, L=None, mu=0.0):
+    """Riemannian Hessian of f on the embedded manifold: P_Y(Euclidean Hessian - 2 Lambda Xi)
+    with the Euclidean Hessian 2 Q Xi + 2 D Xi + 2 Ddot Y of f(Y) = tr(Y^T Q Y) + F(Y Y^T):
+    D = grad_X F (diagonal), Ddot = 2 mu dX_{jj} = 4 mu <y_j, xi_j> on the regularised rows j."""
     if L is None:
-        L = lambdas(Y, Q @ Y)
-    return proj_tangent(Y, 2.0 * (Q @ Xi - apply_blockdiag(L, Xi)))
+        L = lambdas(Y, qeff(Q, Y, mu))
+    E = Q @ Xi - apply_blockdiag(L, Xi)
+    if mu != 0.0:
+        d = scale_reg_diag(Y, mu)
+        dd = np.zeros(Y.shape[0])
+        dd[2::3] = 4.0 * mu * np.sum(Y[2::3] * Xi[2::3], axis=1)
+        dd[2] = 0.0
+        E = E + d[:, None] * Xi + dd[:, None] * Y
+    return proj_tangent(Y, 2.0 * E)
 
 
 def retract(Y, Xi):
@@ -302,7 +345,7 @@ class RTRResult:
     history: list = field(default_factory=list)
 
 
-def tcg(Q, Y, grad, L, Delta, theta=1.0, kappa=0.1, max_inner=1000):
+def tcg(Q, Y, grad, L, Delta, theta=1.0, kappa=0.1, max_inner=1000, mu=0.0):
     """Steihaug-Toint truncated CG on the model m(eta) = <grad, eta> + 1/2 <Hess eta, eta>,
     ||eta|| <= Delta.  Returns (eta, Heta, inner iterations, hit-boundary flag)."""
     eta = np.zeros_like(Y)
@@ -312,7 +355,7 @@ def tcg(Q, Y, grad, L, Delta, theta=1.0, kappa=0.1, max_inner=1000):
     rr = r0 * r0
     delta = -r
     for j in range(max_inner):
-        Hd = hess(Q, Y, delta, L)
+        Hd = hess(Q, Y, delta, L, mu)
         kap = inner(delta, Hd)
         ee, ed, dd = inner(eta, eta), inner(eta, delta), inner(delta, delta)
         alpha = rr / kap if kap > 0 else 0.0
@@ -333,12 +376,12 @@ def tcg(Q, Y, grad, L, Delta, theta=1.0, kappa=0.1, max_inner=1000):
 
 
 def rtr(Q, Y0, grad_tol_rel=1e-10, grad_tol_abs=0.0, max_outer=500, max_inner=1000,
-        Delta_bar=None, rho_prime=0.1, verbose=False) -> RTRResult:
+        Delta_bar=None, rho_prime=0.1, verbose=False, mu=0.0) -> RTRResult:
     """Riemannian trust-region method (Absil et al. 2008, Alg. 10): tCG model step,
     retraction, ratio test rho, radius update, until ||rgrad|| <= tol."""
     Y = Y0.copy()
-    G = Q @ Y
-    f = float(np.sum(Y * G))
+    G = qeff(Q, Y, mu)
+    f = cost(Q, Y, mu)
     L = lambdas(Y, G)
     grad = 2.0 * (G - apply_blockdiag(L, Y))
     gn = math.sqrt(inner(grad, grad))
@@ -356,13 +399,13 @@ def rtr(Q, Y0, grad_tol_rel=1e-10, grad_tol_abs=0.0, max_outer=500, max_inner=10
     for k in range(1, max_outer + 1):
         if gn <= max(grad_tol_abs, grad_tol_rel * g0, floor):
             break
-        eta, Heta, nin, _ = tcg(Q, Y, grad, L, Delta, max_inner=max_inner)
+        eta, Heta, nin, _ = tcg(Q, Y, grad, L, Delta, max_inner=max_inner, mu=mu)
         inner_total += nin
         sweeps += nin
         Yp = retract(Y, eta)
-        Gp = Q @ Yp
+        Gp = qeff(Q, Yp, mu)
         sweeps += 1
-        fp = float(np.sum(Yp * Gp))
+        fp = cost(Q, Yp, mu)
         model_dec = -(inner(grad, eta) + 0.5 * inner(eta, Heta))
         reg = max(1.0, abs(f)) * eps_reg
         rho = (f - fp + reg) / (model_dec + reg)
@@ -397,7 +440,7 @@ def rtr(Q, Y0, grad_tol_rel=1e-10, grad_tol_abs=0.0, max_outer=500, max_inner=10
 class Certificate:
     Lambda: np.ndarray
     f: float
-    dual: float           # tr(Lambda_0) = sum_i b_i y_i
+    dual: float           # tr(Lambda_0) = sum_i b_i y_i (+ F - <grad F, X> with App. D's term)
     lam_min: float        # lambda_min(Z)
     lam_min_deflated: float
     v: np.ndarray         # eigenvector of lambda_min(Z)
@@ -411,17 +454,21 @@ def _deflation_basis(Y):
     return Uu[:, keep]
 
 
-def certify(Q, Y, dense_limit=4000, tol=1e-12):
-    """Z = Q - blockdiag(Lambda) with the closed-form Lambda; lambda_min(Z) (raw, for the
-    escape direction) and lambda_min of Z restricted to range(Y)^perp (the gap)."""
+def certify(Q, Y, dense_limit=4000, tol=1e-12, mu=0.0):
+    """Z = Q - blockdiag(Lambda) with the closed-form Lambda (App. D: Z = Q + grad F(X) -
+    blockdiag(Lambda)); lambda_min(Z) (raw, for the escape direction) and lambda_min of Z
+    restricted to range(Y)^perp (the gap).  The dual value is tr(Lambda_0), plus
+    F(X) - <grad F(X), X> with the regulariser (App. E)."""
     n = Q.shape[0]
-    G = Q @ Y
+    d = scale_reg_diag(Y, mu)
+    G = qeff(Q, Y, mu)
     L = lambdas(Y, G)
-    f = float(np.sum(Y * G))
+    f = cost(Q, Y, mu)
+    dual = float(np.trace(L[0])) + scale_reg_F(Y, mu) - float(np.sum(d * np.sum(Y * Y, axis=1)))
     ZY = G - apply_blockdiag(L, Y)
     Vd = _deflation_basis(Y)
     if n <= dense_limit:
-        Z = Q.copy()
+        Z = Q.copy() + np.diag(d)
         for i in range(n // 3):
             Z[3 * i:3 * i + 3, 3 * i:3 * i + 3] -= L[i]
         Z = 0.5 * (Z + Z.T)
@@ -436,8 +483,7 @@ def certify(Q, Y, dense_limit=4000, tol=1e-12):
     else:
         def zmul(x):
             x = x.reshape(n, -1)
-            return (Q @ x - apply_blockdiag(L, x)).reshape(-1) if x.shape[1] == 1 else \
-                Q @ x - apply_blockdiag(L, x)
+            return Q @ x + d[:, None] * x - apply_blockdiag(L, x)
         Zop = spla.LinearOperator((n, n), matvec=lambda x: zmul(x[:, None]).ravel(), dtype=np.float64)
         lmQ = float(spla.eigsh(spla.aslinearoperator(Q), k=1, which="LA", tol=1e-8,
                                return_eigenvectors=False)[0])
@@ -454,11 +500,10 @@ def certify(Q, Y, dense_limit=4000, tol=1e-12):
                                  dtype=np.float64)
         lam_def = float(spla.eigsh(Zd, k=1, which="SA", tol=tol, maxiter=20 * n,
                                    return_eigenvectors=False)[0])
-    return Certificate(L, f, float(np.trace(L[0])), lam_min, lam_def, v, lmQ,
-                       float(np.linalg.norm(ZY)))
+    return Certificate(L, f, dual, lam_min, lam_def, v, lmQ, float(np.linalg.norm(ZY)))
 
 
-def escape(Q, Y, v, f, max_halvings=30):
+def escape(Q, Y, v, f, max_halvings=30, mu=0.0):
     """Thm. 2 / Alg. 1 escape: step along the tangent direction [0, v] at [Y, 0] with
     step alpha = 1, 1/2, 1/4, ... until the retracted point strictly decreases f."""
     n, r = Y.shape
@@ -467,14 +512,14 @@ def escape(Q, Y, v, f, max_halvings=30):
     alpha = 1.0
     for _ in range(max_halvings + 1):
         Yp = retract(Y0, alpha * D)
-        fp = cost(Q, Yp)
+        fp = cost(Q, Yp, mu)
         if fp < f:
             return Yp, fp, alpha
         alpha *= 0.5
     return None, f, 0.0
 
 
-def round_solution(Q, Y):
+def round_solution(Q, Y, mu=0.0):
     """Rounding (Sec. 2.2): top-3 eigenvectors of X = Y Y^T (via the r x r Gram Y^T Y),
     gauge by the anchor's orthogonal factor (Prop. 3), per-camera scale ||.||_F / sqrt(3)
     and projection onto SO(3) (det fix, Prop. 2).  Returns (R, s, Yhat (n x 3), rho_hat)."""
@@ -495,7 +540,7 @@ def round_solution(Q, Y):
     R[0] = np.eye(3); s[0] = 1.0
     Uhat = np.concatenate([s[i] * R[i] for i in range(N)], axis=1)   # 3 x 3N
     Yhat = Uhat.T
-    return R, s, Yhat, cost(Q, Yhat)
+    return R, s, Yhat, cost(Q, Yhat, mu)
 
 
 @dataclass
@@ -521,8 +566,9 @@ def suboptimality(rho_hat, rho_sdp):
 
 
 def solve(Q, r0=4, r_max=None, cert_tau_rel=1e-6, Y0=None, grad_tol_rel=1e-10,
-          max_outer=500, verbose=False) -> SolveResult:
-    """Alg. 1 (Riemannian staircase): RTR at rank r, certificate, escape to rank r+1."""
+          max_outer=500, verbose=False, mu=0.0) -> SolveResult:
+    """Alg. 1 (Riemannian staircase): RTR at rank r, certificate, escape to rank r+1.
+    mu > 0 solves App. D's scale-regularised problem."""
     n = Q.shape[0]
     N = n // 3
     r_max = n if r_max is None else r_max
@@ -532,19 +578,19 @@ def solve(Q, r0=4, r_max=None, cert_tau_rel=1e-6, Y0=None, grad_tol_rel=1e-10,
     while True:
         r = Y.shape[1]
         visited.append(r)
-        res = rtr(Q, Y, grad_tol_rel=grad_tol_rel, max_outer=max_outer, verbose=verbose)
+        res = rtr(Q, Y, grad_tol_rel=grad_tol_rel, max_outer=max_outer, verbose=verbose, mu=mu)
         sweeps += res.sweeps
         Y = res.Y
-        cert = certify(Q, Y)
+        cert = certify(Q, Y, mu=mu)
         tau = cert_tau_rel * max(cert.lam_max_Q, 1e-300)
         ok = cert.lam_min >= -tau
         if ok or r >= r_max:
             break
-        Yn, fn, alpha = escape(Q, Y, cert.v, res.f)
+        Yn, fn, alpha = escape(Q, Y, cert.v, res.f, mu=mu)
         if Yn is None:
             break
         Y = Yn
-    R, s, Yhat, rho_hat = round_solution(Q, Y)
+    R, s, Yhat, rho_hat = round_solution(Q, Y, mu)
     trX = float(np.sum(Y * Y))
     lower = cert.dual + min(0.0, cert.lam_min) * trX
     return SolveResult(Y, Y.shape[1], res.f, res.grad_norm, cert, bool(ok), R, s, rho_hat,
@@ -683,18 +729,19 @@ def optimal_residuals(N, M, cam, lmk, ukp, w, U):
     return a + Gm @ sol
 
 
-def adjoint(N, M, cam, lmk, ukp, w, Y, dL_dG, Q=None, tol=1e-14):
+def adjoint(N, M, cam, lmk, ukp, w, Y, dL_dG, Q=None, tol=1e-14, mu=0.0):
     """Gradient of L(G(theta)) w.r.t. the lifted keypoints u (E x 3) and weights w (E) at a
     certified optimum Y of rank 3 (G_i = s_i R_i).  Implicit differentiation: the Riemannian
     gradient 2 P_Y(Q Y) vanishes, so Hess[Ydot] = -P_Y(2 Qdot Y); with Hess[lam] = P_Y(dL/dY),
     dL/dQ = -(lam Y^T + Y lam^T).  The bilinear form a^T Q b equals sum_e w_e e_a e_b at the
-    optimal residuals (Prop. 1), whose derivatives follow from the envelope theorem:
+    optimal residuals (Prop. 1), whose derivatives follow from the envelope theorem (App. D's
+    regulariser F(X) does not depend on the observations and enters only the Hessian):
         d(a^T Q b)/du_e = w_e (e_a b_i + e_b a_i),   d(a^T Q b)/dw_e = e_a e_b."""
     cam, lmk, ukp, w = _validated(N, M, cam, lmk, ukp, w)
     Q = build_Q_schur(N, M, cam, lmk, ukp, w) if Q is None else Q
-    L = lambdas(Y, Q @ Y)
+    L = lambdas(Y, qeff(Q, Y, mu))
     gL = proj_tangent(Y, anchored_blocks_grad(Y, dL_dG))
-    lam = conjugate_gradient(lambda v: hess(Q, Y, v, L), gL, tol=tol)
+    lam = conjugate_gradient(lambda v: hess(Q, Y, v, L, mu), gL, tol=tol)
     r = Y.shape[1]
     e = optimal_residuals(N, M, cam, lmk, ukp, w, np.hstack([Y, lam]))
     eY, eL = e[:, :r], e[:, r:]
