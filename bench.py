@@ -33,9 +33,13 @@ WORKLOADS = {
                                   "2+Geom(1/4), 5% outliers, noise N(0,0.02^2), w~U[0.5,1]; BM rank "
                                   "4 start with staircase"),
     "c2": (scenes.config2, 1934, "1934 cameras, 300k landmarks, ~1.5M observations, 2% outliers"),
-    "c4": (scenes.config4, 2000, "2000-frame indoor trajectory, 400k landmarks, multiplicative depth noise"),
+    "c4": (scenes.config4, 2000, "2000-frame indoor trajectory, 400k landmarks, multiplicative depth "
+                                 "noise; App. D scale regularisation weight 10"),
     "c1": (scenes.config1, 20, "20 cameras on a circle, 200 landmarks x 4 observers"),
 }
+# objective options per workload: the trajectory's unregularised optimum collapses the scales of
+# later frames towards zero (App. D), so it is solved with the scale regulariser
+WORKLOAD_OPTS = {"c4": {"scale_reg": 10.0}}
 PRECS = {"fp64": 0, "fp32": 1, "bf16": 2}
 DTYPES = {"fp64": "f64", "fp32": "f32", "bf16": "bf16/f32"}
 # Sweeps of one certified FP32-bulk solve of the 10155-camera workload as measured on a B300 by
@@ -193,6 +197,46 @@ def run_sweep_only(args):
     return 0
 
 
+def run_adjoint(args):
+    """Adjoint of the certified optimum on a workload (default: the 2000-frame trajectory):
+    one certified FP32-bulk solve, then W untimed and K timed xm_backward calls per inner
+    precision for L = <D, G> with a seeded D; prints one JSON line."""
+    import torch
+    from paper_2502_04640_b300 import xm
+    mk, _, desc = WORKLOADS[args.workload]
+    sc = mk()
+    ctx = xm.Context(0)
+    t = xm.scene_tensors(sc)
+    q = xm.xm_build_Q(ctx, sc.N, sc.M, *t, xm.XM_STORE_ALL)
+    wopts = WORKLOAD_OPTS.get(args.workload, {})
+    out = xm.xm_solve(q, xm.xm_default_opts(prec=1, **wopts))
+    r = out["info"]["rank"]
+    D = torch.as_tensor(np.random.default_rng(5).standard_normal((sc.N, 3, 3)), device="cuda:0")
+    res = {}
+    for name, pv in (("fp32_refined", 1), ("fp64", 0)):
+        opts = xm.xm_default_opts(prec=pv, **wopts)
+        for _ in range(args.warmup):
+            xm.xm_backward(q, out["Y"], r, sc.M, *t, D, opts)
+        infos = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            infos.append(xm.xm_backward(q, out["Y"], r, sc.M, *t, D, opts)[3])
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / args.steps
+        last = infos[-1]
+        res[name] = {"s_per_backward": dt, "grads_per_s": sc.E * 4 / dt,
+                     **{k: last[k] for k in ("res_rel", "n_refine", "n_cg", "n_sweeps_fp32",
+                                             "n_sweeps_fp64", "t_lambda_s", "t_resid_s", "launches")}}
+    print(json.dumps({"adjoint": True, "workload": f"{args.workload}: {desc}", "opts": wopts, "N": sc.N, "M": sc.M,
+                      "E": sc.E, "rank": r, "forward_solve_s": out["info"]["t_solve_s"],
+                      "certified": out["info"]["certified"], "steps": args.steps,
+                      "warmup": args.warmup, **res}), flush=True)
+    q.free()
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -212,7 +256,11 @@ def main():
     ap.add_argument("--sweep-only", type=int, default=0, metavar="N",
                     help="time only the Q.Y sweep on a seeded random symmetric Q of N cameras "
                          "(the small case used for profiler captures)")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="time xm_backward (the adjoint of the certified optimum) on --workload")
     args = ap.parse_args()
+    if args.adjoint:
+        return run_adjoint(args)
     if args.warmup < 3 and not args.profile_solve:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
@@ -245,7 +293,8 @@ def main():
     t_build = time.perf_counter() - t0
     del cam, lmk, ukp, w
     torch.cuda.empty_cache()
-    opts = xm.xm_default_opts(prec=prec, time_limit_s=args.time_limit)
+    wopts = WORKLOAD_OPTS.get(args.workload, {})
+    opts = xm.xm_default_opts(prec=prec, time_limit_s=args.time_limit, **wopts)
     stream = ctx.stream
 
     if args.profile_solve:
@@ -305,7 +354,7 @@ def main():
     extra = {}
     if rank == 0 and not args.no_compare:
         # plain FP64 GPU form and the BF16-Q trial, one solve each, errors against the FP64 run
-        ref = xm.xm_solve(q, xm.xm_default_opts(prec=0))
+        ref = xm.xm_solve(q, xm.xm_default_opts(prec=0, **wopts))
         fi = ref["info"]
         extra["fp64_solve_s"] = fi["t_solve_s"]
         extra["fp64_certified"] = fi["certified"]
@@ -319,7 +368,7 @@ def main():
                     "s_max_rel": float(((o["s"] - ref["s"]).abs() / ref["s"].abs()).max())}
         extra["fp32_vs_fp64"] = errs(out)
         if prec != 2:
-            b = xm.xm_solve(q, xm.xm_default_opts(prec=2))
+            b = xm.xm_solve(q, xm.xm_default_opts(prec=2, **wopts))
             extra["bf16q_solve_s"] = b["info"]["t_solve_s"]
             extra["bf16q_certified"] = b["info"]["certified"]
             extra["bf16q_vs_fp64"] = errs(b)

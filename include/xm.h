@@ -80,6 +80,11 @@ typedef struct xm_opts {
                               amplitude times a seeded uniform(-1, 1) fill of the extra
                               columns (0: the padded start exactly; a zero column confines
                               rank-r0 RTR to the rank-3 subspace)                           */
+  double scale_reg;        /* App. D scale regularisation: objective tr(QX) + scale_reg *
+                              sum_{i>=2} (X_{3i,3i} - 1)^2 (the third diagonal entry of every
+                              non-anchor block, paper's 1-based indexing); Z, the dual value
+                              and the suboptimality bounds follow App. D / App. E.  0 (the
+                              default): the plain objective of Eq. 17.  Must be >= 0.        */
 } xm_opts;
 
 typedef struct xm_info {
@@ -201,7 +206,10 @@ xm_status xm_pipeline_host(xm_ctx* ctx, int N, int M, int64_t E, const int32_t* 
  * xm_build_Q; dL_dG N x 3 x 3 row-major (entry 0 ignored).  Outputs dL_dukp (E x 3), dL_dw (E)
  * and, if not NULL, lam (n x r).  opts: prec XM_FP64 runs the CG on the FP64 operator; any
  * other value runs FP32 inner CG (at most max_tcg iterations per pass) inside FP64 residual
- * refinement (at most max_polish passes) until ||res|| <= grad_tol_rel ||P_Y(dL/dY)||.
+ * refinement (at most max_polish passes) until ||res|| <= grad_tol_rel ||P_Y(dL/dY)||, or
+ * until a pass no longer halves ||res|| (the floor set by the stationarity of Y; XM_OK if
+ * ||res|| <= 1e-6 ||P_Y(dL/dY)|| then, else XM_ENOCONV);
+ * scale_reg must be the value the solve used (App. D's term enters the Hessian).
  * Allocates an N x N FP64 work matrix (the Cholesky factor of the anchored camera block) and
  * O(E + n) more, freed before return.  Synchronous.  Returns XM_ENOCONV (outputs written,
  * info->res_rel says how far) when the refinement cap is reached, XM_EDISCONNECTED if the
@@ -217,6 +225,9 @@ typedef struct xm_adj_info {
   double t_resid_s;        /* wall time of the residual pull-back (incl. the Cholesky)         */
   double t_total_s;
   long launches;           /* kernel launches of this call (library calls not counted)        */
+  int dense_precond;       /* 1: CG preconditioned by the dense factor of Z + gamma Pi_Y
+                              (n <= 40000); 0: by Z's 3 x 3 diagonal blocks                   */
+  double gamma;            /* curvature given to range(Y) by the dense preconditioner          */
 } xm_adj_info;
 
 xm_status xm_backward(xm_ctx* ctx, const xm_qmat* q, const xm_opts* opts, int r, const double* Y,

@@ -82,6 +82,7 @@ void xm_default_opts(xm_opts* o) {
   o->seed = 12345;
   o->verbose = 0;
   o->init_jitter = 0.1;
+  o->scale_reg = 0.0;
 }
 
 xm_status xm_create(xm_ctx** out, int device, void* stream) {

@@ -13,14 +13,21 @@
 //
 // Device path:
 //   1. FP64 gradient at Y (dual blocks Lambda of Sec. 3), dL/dY from dL/dG, tangent projection.
-//   2. Hess[lambda] = g_L by conjugate gradients on the Q sweep: FP64 operator for prec FP64;
-//      otherwise FP32 inner CG with FP64 residual refinement (mixed-precision iterative
-//      refinement: each refinement step solves Hess[delta] = g_L - Hess64[lambda] in FP32).
+//   2. Hess[lambda] = g_L by conjugate gradients on the Q sweep, preconditioned by the
+//      per-camera 3 x 3 diagonal blocks of the certificate matrix Z (block Jacobi, projected
+//      onto the tangent space): FP64 operator for prec FP64; otherwise FP32 inner CG with FP64
+//      residual refinement (mixed-precision iterative refinement: each refinement step solves
+//      Hess[delta] = g_L - Hess64[lambda] in FP32).
 //   3. The optimal residuals of the 2R columns [Y, lambda]: landmark means, camera sums, the
 //      anchored translation solve with the Cholesky factor of Sbar, then the outputs.
+#include <cublas_v2.h>
+#include <cusolverDn.h>
+
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <vector>
 
 #include "xm_internal.cuh"
 #include "xm_ops.cuh"
@@ -86,7 +93,7 @@ k_adj_proj(int N, const double* __restrict__ Y, double* __restrict__ X, Scal* sc
 }
 
 // res = g_L - Hess[lambda] from the FP64 sweep Wd = Q lambda (Wd is reset to zero); the inner
-// CG's right side Gin = -res in its storage type; sc->dot = ||res||^2
+// CG's right side Gin = res in its storage type; sc->dot = ||res||^2
 template <typename Ti, int R>
 __global__ void __launch_bounds__(CAM_THREADS)
 k_adj_resid(int N, const double* __restrict__ Y, double* __restrict__ Wd,
@@ -96,7 +103,7 @@ k_adj_resid(int N, const double* __restrict__ Y, double* __restrict__ Wd,
   double v[1] = {0.0};
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < N) {
-    hvp_block<double, R>(i, Y, Wd, lam, res, Lam);
+    hvp_block<double, R>(i, N, Y, Wd, lam, res, Lam, sc->mu);
     double h[3][R], g[3][R];
     load_block<double, double, R>(res, i, h);
     load_block<double, double, R>(gL, i, g);
@@ -107,7 +114,7 @@ k_adj_resid(int N, const double* __restrict__ Y, double* __restrict__ Wd,
       for (int j = 0; j < R; ++j) {
         h[a][j] = g[a][j] - h[a][j];
         s += h[a][j] * h[a][j];
-        Gin[(size_t)(3 * i + a) * R + j] = Ti(-h[a][j]);
+        Gin[(size_t)(3 * i + a) * R + j] = Ti(h[a][j]);
       }
     store_block<double, double, R>(res, i, h);
     v[0] = s;
@@ -115,9 +122,9 @@ k_adj_resid(int N, const double* __restrict__ Y, double* __restrict__ Wd,
   grid_reduce<1>(v, partials, counter, [&](double* t) { sc->dot = t[0]; });
 }
 
-// plain CG step length: alpha = <r,r> / <d, Hess d>; a non-positive curvature ends the solve
-// (the operator is positive semi-definite at a certified optimum and the right side lies in
-// its range)
+// CG step length alpha = <r, z> / <p, Hess p> (z = M^-1 r); a non-positive curvature ends the
+// solve (the operator is positive semi-definite at a certified optimum and the right side lies
+// in its range)
 template <typename T, int R>
 __global__ void __launch_bounds__(CAM_THREADS)
 k_cg_epi(int N, const T* __restrict__ Y, T* __restrict__ Wd, const T* __restrict__ delta,
@@ -126,12 +133,353 @@ k_cg_epi(int N, const T* __restrict__ Y, T* __restrict__ Wd, const T* __restrict
   if (sc->done) return;
   double v[1] = {0.0};
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < N) v[0] = hvp_block<T, R>(i, Y, Wd, delta, Hd, Lam);
+  if (i < N) v[0] = hvp_block<T, R>(i, N, Y, Wd, delta, Hd, Lam, sc->mu);
   grid_reduce<1>(v, partials, counter, [&](double* t) {
     sc->kappa = t[0];
     if (!(t[0] > 0.0)) { sc->done = 1; sc->reason = 1; return; }
-    sc->alpha = sc->rr / t[0];
+    sc->alpha = sc->rz / t[0];
   });
+}
+
+// ---- block-Jacobi preconditioner of the Riemannian Hessian
+// Entry (r, c) of Q from the packed FP64 tiles (upper-triangle tiles, halved diagonal).
+__device__ __forceinline__ double q_entry(const double* __restrict__ q64, int nt, int r, int c) {
+  if (r > c) { const int t = r; r = c; c = t; }
+  const int I = r / TILE, J = c / TILE, a = r % TILE, b = c % TILE;
+  const double v = q64[tile_index(nt, I, J) * TILE * TILE + (int64_t)a * TILE + b];
+  return (I == J && a == b) ? 2.0 * v : v;
+}
+
+// Per camera, Minv_i = (2 Z_ii)^-1 with Z_ii = Q_ii + diag(0, 0, dreg_i) - Lambda_i, the 3 x 3
+// diagonal block of the certificate matrix (positive semi-definite at a certified optimum),
+// eigenvalues clamped below at 1e-8 of the largest; the preconditioner is the tangent
+// projection of the block-diagonal left multiplication, z_i = P_{Y_i}(Minv_i r_i).
+__global__ void k_adj_precond(int N, const double* __restrict__ q64, int nt,
+                              const double* __restrict__ Lam, double* __restrict__ Minv) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double Z[3][3], V[3][3], d[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+      Z[a][b] = q_entry(q64, nt, 3 * i + a, 3 * i + b) - Lam[(size_t)9 * i + 3 * a + b];
+  Z[2][2] += Lam[(size_t)9 * N + i];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = a + 1; b < 3; ++b) { const double m = 0.5 * (Z[a][b] + Z[b][a]); Z[a][b] = m; Z[b][a] = m; }
+  jacobi3<double>(Z, V, d);
+  const double dmax = fmax(d[0], fmax(d[1], d[2]));
+  double inv[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) inv[k] = dmax > 0.0 ? 0.5 / fmax(d[k], 1e-8 * dmax) : 1.0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+      Minv[(size_t)9 * i + 3 * a + b] =
+          V[a][0] * inv[0] * V[b][0] + V[a][1] * inv[1] * V[b][1] + V[a][2] * inv[2] * V[b][2];
+}
+
+// z_i = P_{Y_i}(Minv_i r_i)
+template <int R>
+__device__ __forceinline__ void precond_block(int i, const double (&y)[3][R], const double (&r)[3][R],
+                                              const double* __restrict__ Minv, double (&z)[3][R]) {
+  double M[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) M[a][b] = Minv[(size_t)9 * i + 3 * a + b];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int j = 0; j < R; ++j) z[a][j] = M[a][0] * r[0][j] + M[a][1] * r[1][j] + M[a][2] * r[2][j];
+  double S[3][3], al;
+  dual_block<double, R>(z, y, i == 0, S, al);
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int j = 0; j < R; ++j) z[a][j] -= S[a][0] * y[0][j] + S[a][1] * y[1][j] + S[a][2] * y[2][j];
+}
+
+// ---- gauge deflation
+// The Hessian of the rank-r problem vanishes on the orbit directions N = {Y Omega : Omega skew}
+// (f(Y O) = f(Y) for orthogonal O); the right side and Hess's range are orthogonal to N, so the
+// CG residual and the preconditioned residual are kept orthogonal to N.  The projection of v
+// onto N is Y Omega with skew(Y^T v) = (G Omega + Omega G) / 2, G = Y^T Y: in the eigenbasis W
+// of G (eigenvalues g), Omega~_ab = 2 (W^T skew(Y^T v) W)_ab / (g_a + g_b).
+// defl = [W (R x R row-major), g (R), threshold]; C = Y^T v (R x R, C[a R + b]).
+template <int R>
+__device__ __forceinline__ void omega_from_C(const double* C, const double* __restrict__ defl,
+                                             double* __restrict__ Om) {
+  const double* W = defl;
+  const double* g = defl + R * R;
+  const double thr = defl[R * R + R];
+  double B[R][R], T[R][R];
+  for (int a = 0; a < R; ++a)
+    for (int b = 0; b < R; ++b) B[a][b] = 0.5 * (C[a * R + b] - C[b * R + a]);
+  for (int a = 0; a < R; ++a)        // T = W^T B
+    for (int b = 0; b < R; ++b) {
+      double t = 0.0;
+      for (int k = 0; k < R; ++k) t += W[k * R + a] * B[k][b];
+      T[a][b] = t;
+    }
+  for (int a = 0; a < R; ++a)        // B~ = T W, then divide
+    for (int b = 0; b < R; ++b) {
+      double t = 0.0;
+      for (int k = 0; k < R; ++k) t += T[a][k] * W[k * R + b];
+      const double den = g[a] + g[b];
+      B[a][b] = den > thr ? 2.0 * t / den : 0.0;
+    }
+  for (int a = 0; a < R; ++a)        // Omega = W B~ W^T
+    for (int b = 0; b < R; ++b) {
+      double t = 0.0;
+      for (int k = 0; k < R; ++k)
+        for (int l = 0; l < R; ++l) t += W[a * R + k] * B[k][l] * W[b * R + l];
+      Om[a * R + b] = t;
+    }
+}
+
+// per-camera share of C = Y^T v
+template <int R>
+__device__ __forceinline__ void yt_v(const double (&y)[3][R], const double (&v)[3][R], double (&c)[R * R]) {
+#pragma unroll
+  for (int a = 0; a < R; ++a)
+#pragma unroll
+    for (int b = 0; b < R; ++b) c[a * R + b] = y[0][a] * v[0][b] + y[1][a] * v[1][b] + y[2][a] * v[2][b];
+}
+
+// x = 0, r = b (tangent), C = Y^T r -> Om; resets the CG scalars
+template <typename T, int R>
+__global__ void __launch_bounds__(CAM_THREADS)
+k_pcg_begin(int N, const T* __restrict__ Y, const T* __restrict__ b, T* __restrict__ x,
+            T* __restrict__ r, const double* __restrict__ defl, double* __restrict__ Om, Scal* sc,
+            int max_iters, double tol, double* partials, unsigned* counter) {
+  double v[R * R];
+#pragma unroll
+  for (int k = 0; k < R * R; ++k) v[k] = 0.0;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) {
+    double y[3][R], rr[3][R];
+    load_block<T, double, R>(Y, i, y);
+    load_block<T, double, R>(b, i, rr);
+    yt_v<R>(y, rr, v);
+    zero_block<T, R>(x, i);
+    store_block<T, double, R>(r, i, rr);
+  }
+  grid_reduce<R * R>(v, partials, counter, [&](double* t) {
+    omega_from_C<R>(t, defl, Om);
+    sc->done = 0; sc->iters = 0; sc->max_iters = max_iters; sc->reason = 0; sc->kappa_tol = tol;
+  });
+}
+
+// x += alpha p, r -= alpha Hp (re-projected onto the tangent space), C = Y^T r -> Om
+template <typename T, int R>
+__global__ void __launch_bounds__(CAM_THREADS)
+k_pcg_update(int N, const T* __restrict__ Y, T* __restrict__ x, T* __restrict__ r,
+             const T* __restrict__ p, const T* __restrict__ Hp, const double* __restrict__ defl,
+             double* __restrict__ Om, Scal* sc, double* partials, unsigned* counter) {
+  if (sc->done) return;
+  const double alpha = sc->alpha;
+  double v[R * R];
+#pragma unroll
+  for (int k = 0; k < R * R; ++k) v[k] = 0.0;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) {
+    double y[3][R], xx[3][R], rr[3][R], pp[3][R], hp[3][R];
+    load_block<T, double, R>(Y, i, y);
+    load_block<T, double, R>(x, i, xx);
+    load_block<T, double, R>(r, i, rr);
+    load_block<T, double, R>(p, i, pp);
+    load_block<T, double, R>(Hp, i, hp);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int j = 0; j < R; ++j) { xx[a][j] += alpha * pp[a][j]; rr[a][j] -= alpha * hp[a][j]; }
+    double S[3][3], al;
+    dual_block<double, R>(rr, y, i == 0, S, al);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int j = 0; j < R; ++j) rr[a][j] -= S[a][0] * y[0][j] + S[a][1] * y[1][j] + S[a][2] * y[2][j];
+    yt_v<R>(y, rr, v);
+    store_block<T, double, R>(x, i, xx);
+    store_block<T, double, R>(r, i, rr);
+  }
+  grid_reduce<R * R>(v, partials, counter, [&](double* t) { omega_from_C<R>(t, defl, Om); });
+}
+
+// v -= Y Om (deflation); optionally also writes v column-major in FP32 (n x R, ld n) for the
+// dense preconditioner's triangular solves
+template <typename T, int R>
+__global__ void __launch_bounds__(CAM_THREADS)
+k_deflate(int N, const T* __restrict__ Y, T* __restrict__ v, const double* __restrict__ Om,
+          float* __restrict__ col, const Scal* sc) {
+  if (sc->done) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double y[3][R], vv[3][R], O[R][R];
+  load_block<T, double, R>(Y, i, y);
+  load_block<T, double, R>(v, i, vv);
+#pragma unroll
+  for (int a = 0; a < R; ++a)
+#pragma unroll
+    for (int b = 0; b < R; ++b) O[a][b] = Om[a * R + b];
+  const size_t n = (size_t)3 * N;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      double t = 0.0;
+#pragma unroll
+      for (int k = 0; k < R; ++k) t += y[a][k] * O[k][j];
+      vv[a][j] -= t;
+      if (col) col[(size_t)j * n + 3 * i + a] = float(vv[a][j]);
+    }
+  store_block<T, double, R>(v, i, vv);
+}
+
+// block-Jacobi preconditioner: z = P_Y(Minv r), C = Y^T z -> Om
+template <typename T, int R>
+__global__ void __launch_bounds__(CAM_THREADS)
+k_precond_bj(int N, const T* __restrict__ Y, const T* __restrict__ r, T* __restrict__ z,
+             const double* __restrict__ Minv, const double* __restrict__ defl, double* __restrict__ Om,
+             Scal* sc, double* partials, unsigned* counter) {
+  if (sc->done) return;
+  double v[R * R];
+#pragma unroll
+  for (int k = 0; k < R * R; ++k) v[k] = 0.0;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) {
+    double y[3][R], rr[3][R], zz[3][R];
+    load_block<T, double, R>(Y, i, y);
+    load_block<T, double, R>(r, i, rr);
+    precond_block<R>(i, y, rr, Minv, zz);
+    yt_v<R>(y, zz, v);
+    store_block<T, double, R>(z, i, zz);
+  }
+  grid_reduce<R * R>(v, partials, counter, [&](double* t) { omega_from_C<R>(t, defl, Om); });
+}
+
+// dense preconditioner, after the two triangular solves: z = P_Y(col / 2), C = Y^T z -> Om
+template <typename T, int R>
+__global__ void __launch_bounds__(CAM_THREADS)
+k_precond_from_col(int N, const T* __restrict__ Y, const float* __restrict__ col, T* __restrict__ z,
+                   const double* __restrict__ defl, double* __restrict__ Om, Scal* sc,
+                   double* partials, unsigned* counter) {
+  if (sc->done) return;
+  double v[R * R];
+#pragma unroll
+  for (int k = 0; k < R * R; ++k) v[k] = 0.0;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) {
+    double y[3][R], zz[3][R];
+    load_block<T, double, R>(Y, i, y);
+    const size_t n = (size_t)3 * N;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int j = 0; j < R; ++j) zz[a][j] = 0.5 * double(col[(size_t)j * n + 3 * i + a]);
+    double S[3][3], al;
+    dual_block<double, R>(zz, y, i == 0, S, al);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int j = 0; j < R; ++j) zz[a][j] -= S[a][0] * y[0][j] + S[a][1] * y[1][j] + S[a][2] * y[2][j];
+    yt_v<R>(y, zz, v);
+    store_block<T, double, R>(z, i, zz);
+  }
+  grid_reduce<R * R>(v, partials, counter, [&](double* t) { omega_from_C<R>(t, defl, Om); });
+}
+
+// z -= Y Om (deflation); <r, r>, <r, z>; first call (init): p = z, r0; later: residual test and
+// beta = <r, z>' / <r, z>
+template <typename T, int R>
+__global__ void __launch_bounds__(CAM_THREADS)
+k_pcg_rz(int N, const T* __restrict__ Y, const T* __restrict__ r, T* __restrict__ z,
+         T* __restrict__ p, const double* __restrict__ Om, int init, Scal* sc, double* partials,
+         unsigned* counter) {
+  if (sc->done) return;
+  double v[2] = {0.0, 0.0};
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) {
+    double y[3][R], rr[3][R], zz[3][R], O[R][R];
+    load_block<T, double, R>(Y, i, y);
+    load_block<T, double, R>(r, i, rr);
+    load_block<T, double, R>(z, i, zz);
+#pragma unroll
+    for (int a = 0; a < R; ++a)
+#pragma unroll
+      for (int b = 0; b < R; ++b) O[a][b] = Om[a * R + b];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        double t = 0.0;
+#pragma unroll
+        for (int k = 0; k < R; ++k) t += y[a][k] * O[k][j];
+        zz[a][j] -= t;
+        v[0] += rr[a][j] * rr[a][j];
+        v[1] += rr[a][j] * zz[a][j];
+      }
+    store_block<T, double, R>(z, i, zz);
+    if (init) store_block<T, double, R>(p, i, zz);
+  }
+  grid_reduce<2>(v, partials, counter, [&](double* t) {
+    sc->rr = t[0];
+    if (init) {
+      sc->r0 = sqrt(t[0]); sc->rz = t[1];
+      if (!(t[0] > 0.0) || !(t[1] > 0.0)) { sc->done = 1; sc->reason = 3; }
+      return;
+    }
+    sc->iters += 1;
+    if (sqrt(t[0]) <= sc->r0 * sc->kappa_tol) { sc->done = 1; sc->reason = 3; }
+    else if (sc->iters >= sc->max_iters) { sc->done = 1; sc->reason = 4; }
+    else if (!(t[1] > 0.0)) { sc->done = 1; sc->reason = 5; }
+    else { sc->beta = t[1] / sc->rz; sc->rz = t[1]; }
+  });
+}
+
+// dense Z + gamma Pi_Y (FP32, column-major n x n): Q + diag(dreg) - blockdiag(Lambda) +
+// gamma Y G^+ Y^T, the preconditioner's matrix (Pi_Y = Y G^+ Y^T projects onto range(Y), the
+// null space of Z at a certified optimum)
+template <int R>
+__global__ void k_dense_Z(int N, const double* __restrict__ q64, int nt, const double* __restrict__ Lam,
+                          const double* __restrict__ Y, const double* __restrict__ Gp, double gamma,
+                          float* __restrict__ Z) {
+  const int n = 3 * N;
+  const int64_t total = (int64_t)n * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e / n), rr = (int)(e % n);
+    double v = q_entry(q64, nt, rr, c);
+    if (rr / 3 == c / 3) {
+      const int i = rr / 3;
+      v -= Lam[(size_t)9 * i + 3 * (rr % 3) + (c % 3)];
+      if (rr == c && rr % 3 == 2) v += Lam[(size_t)9 * N + i];
+    }
+    double t = 0.0;
+#pragma unroll
+    for (int a = 0; a < R; ++a) {
+      double u = 0.0;
+#pragma unroll
+      for (int b = 0; b < R; ++b) u += Gp[a * R + b] * Y[(size_t)c * R + b];
+      t += Y[(size_t)rr * R + a] * u;
+    }
+    Z[e] = float(v + gamma * t);
+  }
+}
+
+// p = z + beta p
+template <typename T, int R>
+__global__ void __launch_bounds__(CAM_THREADS)
+k_pcg_dir(int N, const T* __restrict__ z, T* __restrict__ p, const Scal* sc) {
+  if (sc->done) return;
+  const double beta = sc->beta;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  for (int e = 3 * i * R; e < 3 * (i + 1) * R; ++e) p[e] = T(double(z[e]) + beta * double(p[e]));
 }
 
 template <typename Ti>
@@ -268,6 +616,51 @@ int grid_cap(size_t work, int threads, int num_sms) {
 
 }  // namespace
 
+// cyclic Jacobi eigen-decomposition of a small symmetric m x m matrix (row-major):
+// A = V diag(w) V^T, V's columns the eigenvectors
+static void small_sym_eig(int m, std::vector<double> A, std::vector<double>& w, std::vector<double>& V) {
+  V.assign((size_t)m * m, 0.0);
+  for (int i = 0; i < m; ++i) V[(size_t)i * m + i] = 1.0;
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) {
+        tot += A[(size_t)i * m + j] * A[(size_t)i * m + j];
+        if (i != j) off += A[(size_t)i * m + j] * A[(size_t)i * m + j];
+      }
+    if (off <= 1e-30 * tot || off == 0.0) break;
+    for (int p = 0; p < m; ++p)
+      for (int q = p + 1; q < m; ++q) {
+        const double apq = A[(size_t)p * m + q];
+        if (apq == 0.0) continue;
+        const double th = 0.5 * (A[(size_t)q * m + q] - A[(size_t)p * m + p]) / apq;
+        const double t = (th >= 0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(th * th + 1.0));
+        const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < m; ++k) {   // A <- J^T A J
+          const double akp = A[(size_t)k * m + p], akq = A[(size_t)k * m + q];
+          A[(size_t)k * m + p] = c * akp - s * akq;
+          A[(size_t)k * m + q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < m; ++k) {
+          const double apk = A[(size_t)p * m + k], aqk = A[(size_t)q * m + k];
+          A[(size_t)p * m + k] = c * apk - s * aqk;
+          A[(size_t)q * m + k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < m; ++k) {
+          const double vkp = V[(size_t)k * m + p], vkq = V[(size_t)k * m + q];
+          V[(size_t)k * m + p] = c * vkp - s * vkq;
+          V[(size_t)k * m + q] = s * vkp + c * vkq;
+        }
+      }
+  }
+  w.resize(m);
+  for (int i = 0; i < m; ++i) w[i] = A[(size_t)i * m + i];
+}
+
+// Largest n for which the dense preconditioner is factored (n x n FP32: 6.4 GB at the limit);
+// above it the block-Jacobi preconditioner is used.
+constexpr int DENSE_PRECOND_MAX_N = 40000;
+
 template <int R>
 static xm_status backward_impl(xm_ctx* ctx, const DeviceQ& q, const xm_opts& o, int r,
                                const double* Yin, int ldy, int M, int64_t E, const int32_t* cam,
@@ -282,20 +675,28 @@ static xm_status backward_impl(xm_ctx* ctx, const DeviceQ& q, const xm_opts& o, 
   const bool fp64 = o.prec == XM_FP64;
   const size_t rows = (size_t)n_pad, vec64 = rows * R * sizeof(double);
   XM_TRY(validate_obs(ctx, N, M, E, cam, lmk, ukp, w));
-  XM_TRY(ensure_partials(ctx, (size_t)std::max(nb_cam, 1) * 3 * R + 64));
+  XM_TRY(ensure_partials(ctx, (size_t)std::max(3 * nb_cam, ctx->num_sms * 4) * R * R + 64));
   long launches = 0;
   xm_adj_info inf{};
 
   // ---- vectors (FP64: Y, G, Lam, g_L, lambda, res, Wd; inner: Y, G, eta, Heta, r, d, Hd, Wd)
-  Buf bY, bG, bLam, bgL, blam, bres, bWd, bsc, bYi, bGi, beta, bHeta, br, bd, bHd, bWi;
+  Buf bY, bG, bLam, bMinv, bgL, blam, bres, bWd, bsc, bYi, bGi, beta, bHeta, br, bd, bHd, bWi;
+  Buf bsmall, bZ, bcol, bwork, binfo;
   for (Buf* b : {&bY, &bG, &bgL, &blam, &bres, &bWd}) {
     XM_CUDA_TRY(cudaMalloc(&b->p, vec64));
     XM_CUDA_TRY(cudaMemsetAsync(b->p, 0, vec64, st));
   }
-  XM_CUDA_TRY(cudaMalloc(&bLam.p, sizeof(double) * 9 * (size_t)N));
+  XM_CUDA_TRY(cudaMalloc(&bLam.p, sizeof(double) * lam_doubles(N)));
+  XM_CUDA_TRY(cudaMalloc(&bMinv.p, sizeof(double) * 9 * (size_t)N));
+  // small: G = Y^T Y | defl = [W, g, thr] | G^+ | Omega
+  const int SM_G = 0, SM_DEFL = R * R, SM_GP = 2 * R * R + R + 1, SM_OM = 3 * R * R + R + 1;
+  XM_CUDA_TRY(cudaMalloc(&bsmall.p, sizeof(double) * (4 * R * R + R + 1)));
+  XM_CUDA_TRY(cudaMemsetAsync(bsmall.p, 0, sizeof(double) * (4 * R * R + R + 1), st));
+  double* dsm = bsmall.as<double>();
   XM_CUDA_TRY(cudaMalloc(&bsc.p, sizeof(Scal)));
   XM_CUDA_TRY(cudaMemsetAsync(bsc.p, 0, sizeof(Scal), st));
   Scal* sc = bsc.as<Scal>();
+  XM_CUDA_TRY(cudaMemcpyAsync(&sc->mu, &o.scale_reg, sizeof(double), cudaMemcpyHostToDevice, st));
   Scal hs{};
   auto pull = [&]() -> xm_status {
     XM_CUDA_TRY(cudaMemcpyAsync(&hs, sc, sizeof(Scal), cudaMemcpyDeviceToHost, st));
@@ -334,12 +735,105 @@ static xm_status backward_impl(xm_ctx* ctx, const DeviceQ& q, const xm_opts& o, 
                                               ctx->d_partials, ctx->d_counter);
   k_adj_proj<R><<<nb_cam, CAM_THREADS, 0, st>>>(N, bY.as<double>(), bgL.as<double>(), sc,
                                                 ctx->d_partials, ctx->d_counter);
-  launches += 4;
+  k_gram<double, R><<<std::max(1, std::min(nb_cam * 3, ctx->num_sms * 4)), CAM_THREADS, 0, st>>>(
+      n_pad, bY.as<double>(), dsm + SM_G, ctx->d_partials, ctx->d_counter);
+  launches += 5;
   XM_CUDA_TRY(cudaGetLastError());
   XM_TRY(pull());
   const double gnorm = std::sqrt(hs.dot);
   inf.g_norm = gnorm;
   inf.grad_norm_Y = std::sqrt(hs.g2);
+
+  // ---- preconditioner data: deflation basis of the gauge directions, Pi_Y, gamma, Z's factor
+  {
+    std::vector<double> G(R * R), gw, W, host(4 * R * R + R + 1, 0.0);
+    XM_CUDA_TRY(cudaMemcpy(G.data(), dsm + SM_G, sizeof(double) * R * R, cudaMemcpyDeviceToHost));
+    small_sym_eig(R, G, gw, W);
+    double gmax = 0.0;
+    for (double x : gw) gmax = std::max(gmax, x);
+    for (int k = 0; k < R * R; ++k) host[SM_DEFL + k] = W[k];
+    for (int k = 0; k < R; ++k) host[SM_DEFL + R * R + k] = gw[k];
+    host[SM_DEFL + R * R + R] = 1e-12 * gmax;
+    for (int a = 0; a < R; ++a)
+      for (int b = 0; b < R; ++b) {
+        double t = 0.0;
+        for (int k = 0; k < R; ++k)
+          if (gw[k] > 1e-10 * gmax) t += W[a * R + k] * W[b * R + k] / gw[k];
+        host[SM_GP + a * R + b] = t;
+      }
+    XM_CUDA_TRY(cudaMemcpy(dsm + SM_DEFL, host.data() + SM_DEFL, sizeof(double) * (2 * R * R + R + 1),
+                           cudaMemcpyHostToDevice));
+    // gamma: the mean Frobenius norm of the dual blocks over sqrt(3), the curvature scale the
+    // dense preconditioner gives to range(Y)
+    std::vector<double> Lh((size_t)9 * N);
+    XM_CUDA_TRY(cudaMemcpy(Lh.data(), bLam.p, sizeof(double) * 9 * N, cudaMemcpyDeviceToHost));
+    double gsum = 0.0;
+    for (int i = 0; i < N; ++i) {
+      double f2 = 0.0;
+      for (int k = 0; k < 9; ++k) f2 += Lh[(size_t)9 * i + k] * Lh[(size_t)9 * i + k];
+      gsum += std::sqrt(f2);
+    }
+    const double gamma = gsum / (std::sqrt(3.0) * N) + 1e-300;
+    inf.dense_precond = 0;
+    if (n <= DENSE_PRECOND_MAX_N && gnorm > 0.0) {
+      XM_CUDA_TRY(cudaMalloc(&bZ.p, sizeof(float) * (size_t)n * n));
+      XM_CUDA_TRY(cudaMalloc(&bcol.p, sizeof(float) * (size_t)n * R));
+      k_dense_Z<R><<<grid_cap((size_t)n * n, 256, ctx->num_sms * 4), 256, 0, st>>>(
+          N, q.q64, q.nt, bLam.as<double>(), bY.as<double>(), dsm + SM_GP, gamma, bZ.as<float>());
+      ++launches;
+      XM_CUDA_TRY(cudaGetLastError());
+      if (!ctx->cusolver) {
+        cusolverDnHandle_t h;
+        if (cusolverDnCreate(&h) != CUSOLVER_STATUS_SUCCESS)
+          return set_error(XM_ECUDA, "xm_backward: cusolverDnCreate failed");
+        ctx->cusolver = h;
+      }
+      cusolverDnHandle_t cs = static_cast<cusolverDnHandle_t>(ctx->cusolver);
+      int lwork = 0, hinfo = 1;
+      bool ok = cusolverDnSetStream(cs, st) == CUSOLVER_STATUS_SUCCESS &&
+                cusolverDnSpotrf_bufferSize(cs, CUBLAS_FILL_MODE_LOWER, n, bZ.as<float>(), n, &lwork) ==
+                    CUSOLVER_STATUS_SUCCESS;
+      if (ok) {
+        XM_CUDA_TRY(cudaMalloc(&bwork.p, sizeof(float) * (size_t)std::max(lwork, 1)));
+        XM_CUDA_TRY(cudaMalloc(&binfo.p, sizeof(int)));
+        ok = cusolverDnSpotrf(cs, CUBLAS_FILL_MODE_LOWER, n, bZ.as<float>(), n, bwork.as<float>(), lwork,
+                              binfo.as<int>()) == CUSOLVER_STATUS_SUCCESS;
+        XM_CUDA_TRY(cudaMemcpyAsync(&hinfo, binfo.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        XM_CUDA_TRY(cudaStreamSynchronize(st));
+      }
+      if (ok && hinfo == 0) {
+        inf.dense_precond = 1;
+        if (!ctx->cublas) {
+          cublasHandle_t h;
+          if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS)
+            return set_error(XM_ECUDA, "xm_backward: cublasCreate failed");
+          ctx->cublas = h;
+        }
+        if (cublasSetStream(static_cast<cublasHandle_t>(ctx->cublas), st) != CUBLAS_STATUS_SUCCESS)
+          return set_error(XM_ECUDA, "xm_backward: cublasSetStream failed");
+      } else {
+        cudaFree(bZ.p); bZ.p = nullptr;
+      }
+    }
+    if (!inf.dense_precond) {
+      k_adj_precond<<<nb_cam, CAM_THREADS, 0, st>>>(N, q.q64, q.nt, bLam.as<double>(), bMinv.as<double>());
+      ++launches;
+      XM_CUDA_TRY(cudaGetLastError());
+    }
+    inf.gamma = gamma;
+  }
+  const bool dense = inf.dense_precond != 0;
+  // z = M^-1 r for the dense preconditioner: two triangular solves on the FP32 column copy
+  auto trsm_pair = [&]() -> xm_status {
+    cublasHandle_t cb = static_cast<cublasHandle_t>(ctx->cublas);
+    const float one = 1.0f;
+    if (cublasStrsm(cb, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N, CUBLAS_DIAG_NON_UNIT, n, R,
+                    &one, bZ.as<float>(), n, bcol.as<float>(), n) != CUBLAS_STATUS_SUCCESS ||
+        cublasStrsm(cb, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T, CUBLAS_DIAG_NON_UNIT, n, R,
+                    &one, bZ.as<float>(), n, bcol.as<float>(), n) != CUBLAS_STATUS_SUCCESS)
+      return set_error(XM_ECUDA, "xm_backward: cublasStrsm failed");
+    return XM_OK;
+  };
 
   // ---- 2. Hess[lambda] = g_L: CG, FP64 residual refinement around an FP32 inner solve
   const double target = o.grad_tol_rel * gnorm;
@@ -373,10 +867,18 @@ static xm_status backward_impl(xm_ctx* ctx, const DeviceQ& q, const xm_opts& o, 
       ++launches;
       XM_CUDA_TRY(cudaGetLastError());
       XM_TRY(pull());
+      const double res_prev = res;
       res = std::sqrt(hs.dot);
       inf.n_refine = it;
       if (!std::isfinite(res)) { result = set_error(XM_ENUMERIC, "xm_backward: non-finite residual"); break; }
       if (res <= target) break;
+      // a pass that no longer halves the residual has reached the floor set by how stationary
+      // Y is (Hess is singular along the gauge directions only at an exact critical point)
+      if (it >= 2 && res > 0.5 * res_prev) {
+        if (res > 1e-6 * gnorm)
+          result = set_error(XM_ENOCONV, "xm_backward: adjoint residual stalled at %.3e of %.3e", res, gnorm);
+        break;
+      }
       if (it >= std::max(1, o.max_polish)) {
         result = set_error(XM_ENOCONV, "xm_backward: adjoint residual %.3e of %.3e after %d refinements",
                            res, gnorm, it);
@@ -387,25 +889,51 @@ static xm_status backward_impl(xm_ctx* ctx, const DeviceQ& q, const xm_opts& o, 
       const int prec_in = fp64 ? XM_FP64 : XM_FP32_BULK;
       auto inner = [&](auto tag) -> xm_status {
         using Ti = decltype(tag);
-        k_tcg_init<Ti, Ti, R><<<grid_cap(rows * R, CAM_THREADS, ctx->num_sms), CAM_THREADS, 0, st>>>(
-            (int)rows, bGi.as<Ti>(), beta.as<Ti>(), bHeta.as<Ti>(), br.as<Ti>(), bd.as<Ti>(), sc,
-            res * res, 0.0, o.max_tcg, 0.0, tol_in);
-        ++launches;
+        const Ti* Yi = (const Ti*)Yinner;
+        double* Om = dsm + SM_OM;
+        const double* defl = dsm + SM_DEFL;
+        // z = deflated, projected M^-1 r (r already deflated)
+        auto precond = [&]() -> xm_status {
+          if (dense) {
+            XM_TRY(trsm_pair());
+            k_precond_from_col<Ti, R><<<nb_cam, CAM_THREADS, 0, st>>>(
+                N, Yi, bcol.as<float>(), bHeta.as<Ti>(), defl, Om, sc, ctx->d_partials, ctx->d_counter);
+          } else {
+            k_precond_bj<Ti, R><<<nb_cam, CAM_THREADS, 0, st>>>(
+                N, Yi, br.as<Ti>(), bHeta.as<Ti>(), bMinv.as<double>(), defl, Om, sc, ctx->d_partials,
+                ctx->d_counter);
+          }
+          ++launches;
+          return XM_OK;
+        };
+        float* col = dense ? bcol.as<float>() : nullptr;
+        k_pcg_begin<Ti, R><<<nb_cam, CAM_THREADS, 0, st>>>(N, Yi, bGi.as<Ti>(), beta.as<Ti>(), br.as<Ti>(),
+                                                          defl, Om, sc, o.max_tcg, tol_in,
+                                                          ctx->d_partials, ctx->d_counter);
+        k_deflate<Ti, R><<<nb_cam, CAM_THREADS, 0, st>>>(N, Yi, br.as<Ti>(), Om, col, sc);
+        XM_TRY(precond());
+        k_pcg_rz<Ti, R><<<nb_cam, CAM_THREADS, 0, st>>>(N, Yi, br.as<Ti>(), bHeta.as<Ti>(), bd.as<Ti>(), Om,
+                                                        1, sc, ctx->d_partials, ctx->d_counter);
+        launches += 3;
+        XM_CUDA_TRY(cudaGetLastError());
         const int CH = 4;
         int done = 0;
         for (int j = 0; j < o.max_tcg && !done; j += CH) {
           for (int c = 0; c < CH; ++c) {
             XM_TRY(qy_launch(ctx, q, prec_in, R, bd.p, bWi.p, &sc->done, st));
             if (fp64) ++inf.n_sweeps_fp64; else ++inf.n_sweeps_fp32;
-            k_cg_epi<Ti, R><<<nb_cam, CAM_THREADS, 0, st>>>(N, (const Ti*)Yinner, bWi.as<Ti>(), bd.as<Ti>(),
-                                                            bHd.as<Ti>(), bLam.as<double>(), sc,
-                                                            ctx->d_partials, ctx->d_counter);
-            k_tcg_update<Ti, R><<<nb_cam, CAM_THREADS, 0, st>>>(
-                N, (const Ti*)Yinner, beta.as<Ti>(), bHeta.as<Ti>(), br.as<Ti>(), bd.as<Ti>(),
-                bHd.as<Ti>(), sc, ctx->d_partials, ctx->d_counter);
-            k_tcg_dir<Ti, R><<<nb_cam, CAM_THREADS, 0, st>>>(N, beta.as<Ti>(), br.as<Ti>(), bd.as<Ti>(),
-                                                             sc, ctx->d_partials, ctx->d_counter);
-            launches += 4;
+            k_cg_epi<Ti, R><<<nb_cam, CAM_THREADS, 0, st>>>(N, Yi, bWi.as<Ti>(), bd.as<Ti>(), bHd.as<Ti>(),
+                                                            bLam.as<double>(), sc, ctx->d_partials,
+                                                            ctx->d_counter);
+            k_pcg_update<Ti, R><<<nb_cam, CAM_THREADS, 0, st>>>(N, Yi, beta.as<Ti>(), br.as<Ti>(), bd.as<Ti>(),
+                                                               bHd.as<Ti>(), defl, Om, sc, ctx->d_partials,
+                                                               ctx->d_counter);
+            k_deflate<Ti, R><<<nb_cam, CAM_THREADS, 0, st>>>(N, Yi, br.as<Ti>(), Om, col, sc);
+            XM_TRY(precond());
+            k_pcg_rz<Ti, R><<<nb_cam, CAM_THREADS, 0, st>>>(N, Yi, br.as<Ti>(), bHeta.as<Ti>(), bd.as<Ti>(),
+                                                            Om, 0, sc, ctx->d_partials, ctx->d_counter);
+            k_pcg_dir<Ti, R><<<nb_cam, CAM_THREADS, 0, st>>>(N, bHeta.as<Ti>(), bd.as<Ti>(), sc);
+            launches += 6;
           }
           XM_CUDA_TRY(cudaGetLastError());
           XM_CUDA_TRY(cudaMemcpyAsync(&hs.done, &sc->done, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -414,9 +942,16 @@ static xm_status backward_impl(xm_ctx* ctx, const DeviceQ& q, const xm_opts& o, 
         }
         XM_TRY(pull());
         inf.n_cg += hs.iters;
+        if (o.verbose >= 1)
+          fprintf(stderr, "[xm] adjoint pass %d: |res| %.3e (target %.3e) inner CG %d its, stop %d, "
+                  "last curvature %.3e, inner |r| %.3e\n", it, res, target, hs.iters, hs.reason,
+                  hs.kappa, std::sqrt(hs.rr));
         k_axpy_to64<Ti><<<grid_cap(rows * R, 256, ctx->num_sms), 256, 0, st>>>(
             rows * R, beta.as<Ti>(), blam.as<double>());
-        ++launches;
+        // an FP32 correction is tangent at the FP32-rounded Y: keep lambda tangent at Y in FP64
+        k_adj_proj<R><<<nb_cam, CAM_THREADS, 0, st>>>(N, bY.as<double>(), blam.as<double>(), sc,
+                                                      ctx->d_partials, ctx->d_counter);
+        launches += 2;
         XM_CUDA_TRY(cudaGetLastError());
         return XM_OK;
       };
@@ -488,6 +1023,8 @@ extern "C" xm_status xm_backward(xm_ctx* c, const xm_qmat* q, const xm_opts* opt
   if (r < 3 || r > XM_MAX_RANK) return set_error(XM_EINVAL, "xm_backward: r=%d not in [3, %d]", r, XM_MAX_RANK);
   if (ldy < r) return set_error(XM_EINVAL, "xm_backward: ldy=%d < r=%d", ldy, r);
   if (M < 0 || E < 0) return set_error(XM_EINVAL, "xm_backward: negative size");
+  if (!(opts->scale_reg >= 0.0) || !std::isfinite(opts->scale_reg))
+    return set_error(XM_EINVAL, "xm_backward: scale_reg must be finite and >= 0");
   const DeviceQ& d = q->d;
   if (!d.q64) return set_error(XM_EINVAL, "xm_backward: Q has no FP64 copy (residual refinement needs it)");
   if (opts->prec != XM_FP64 && !d.q32)

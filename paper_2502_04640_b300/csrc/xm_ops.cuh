@@ -12,14 +12,21 @@ struct Scal {
   double f, g2, y2;          // objective, ||rgrad||^2, ||Y||^2 at the current point
   double fc, gc2, yc2;       // the same at the candidate point
   double Delta;              // trust-region radius
-  double rr, r0;             // <r, r>, ||r_0||
+  double rr, r0, rz;         // <r, r>, ||r_0||, <r, M^-1 r> (preconditioned CG)
   double ee, ed, dd;         // <eta,eta>, <eta,delta>, <delta,delta>
   double kappa, alpha, beta; // curvature, step, CG coefficient
   double theta, kappa_tol;   // residual-based stop: ||r|| <= r0 min(r0^theta, kappa_tol)
   double g_eta, eta_Heta, eta2;  // model terms of the step
   double dot;                // generic reduction result
+  double mu;                 // App. D scale-regularisation weight (0: plain Eq. 17 objective)
   int done, stop_after, iters, max_iters, reason, pad_;
 };
+
+// The dual-block arrays hold N row-major 3 x 3 blocks Lambda_i followed by N values
+// dreg_i = 2 mu (x_i - 1), x_i = X_{3i+2,3i+2} = ||row 2 of Y_i||^2 (0 for the anchor): the
+// diagonal of grad_X F of App. D's regulariser F(X) = mu sum_{i>=1} (x_i - 1)^2, which acts on
+// the third row of every non-anchor block.  Z = Q + diag(dreg) - blockdiag(Lambda).
+__host__ __device__ inline size_t lam_doubles(int N) { return (size_t)10 * N; }
 
 constexpr int CAM_THREADS = 64;   // per-camera kernels: 10155 cameras -> 159 blocks
 
@@ -184,7 +191,8 @@ __device__ __forceinline__ void zero_block(T* p, int i) {
 }
 
 // ------------------------------------------------------------------ gradient epilogue
-// From W = Q Y: Lambda_i, rgrad_i = 2 (W_i - Lambda_i Y_i), f = <Y, W>, ||rgrad||^2, ||Y||^2.
+// From W = Q Y: Lambda_i, rgrad_i = 2 (W_i - Lambda_i Y_i), f = <Y, W>, ||rgrad||^2, ||Y||^2
+// (with App. D's regulariser: W_i + dreg_i e_3 e_3^T Y_i in place of W_i, f + F(X)).
 // W is reset to zero for the next accumulating sweep.  Results go to (sc->f, g2, y2) or, with
 // cand = 1, to (sc->fc, gc2, yc2).
 template <typename T, int R>
@@ -200,16 +208,31 @@ k_grad_epi(int N, const T* __restrict__ Y, T* __restrict__ W, T* __restrict__ G,
     load_block<T, C, R>(Y, i, y);
     load_block<T, C, R>(W, i, w);
     zero_block<T, R>(W, i);
+    double fi = 0.0, gi = 0.0, yi = 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int j = 0; j < R; ++j) fi += double(y[a][j]) * double(w[a][j]);   // tr(Y^T Q Y)
+    // App. D regulariser: f += mu (x_i - 1)^2, (Q + grad F) Y adds dreg_i * row 2 of Y_i
+    const double mu = sc->mu;
+    C dreg = C(0);
+    if (mu != 0.0 && i > 0) {
+      C x2 = C(0);
+#pragma unroll
+      for (int j = 0; j < R; ++j) x2 += y[2][j] * y[2][j];
+      dreg = C(2) * C(mu) * (x2 - C(1));
+      fi += mu * double((x2 - C(1)) * (x2 - C(1)));
+#pragma unroll
+      for (int j = 0; j < R; ++j) w[2][j] += dreg * y[2][j];
+    }
     dual_block<C, R>(w, y, i == 0, L, alpha);
     C g[3][R];
-    double fi = 0.0, gi = 0.0, yi = 0.0;
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
       for (int j = 0; j < R; ++j) {
         C ly = L[a][0] * y[0][j] + L[a][1] * y[1][j] + L[a][2] * y[2][j];
         g[a][j] = C(2) * (w[a][j] - ly);
-        fi += double(y[a][j]) * double(w[a][j]);
         gi += double(g[a][j]) * double(g[a][j]);
         yi += double(y[a][j]) * double(y[a][j]);
       }
@@ -218,6 +241,7 @@ k_grad_epi(int N, const T* __restrict__ Y, T* __restrict__ W, T* __restrict__ G,
     for (int a = 0; a < 3; ++a)
 #pragma unroll
       for (int b = 0; b < 3; ++b) Lam[(size_t)9 * i + 3 * a + b] = double(L[a][b]);
+    Lam[(size_t)9 * N + i] = double(dreg);
     v[0] = fi; v[1] = gi; v[2] = yi;
   }
   grid_reduce<3>(v, partials, counter, [&](double* t) {
@@ -254,16 +278,26 @@ k_tcg_init(int n_rows, const To* __restrict__ G, Ti* eta, Ti* Heta, Ti* r, Ti* d
 
 // Hd_i = 2 P_{Y_i}(Wd_i - Lambda_i d_i) for camera i (Wd_i is reset to zero for the next
 // accumulating sweep); returns <d_i, Hd_i>.
+// With App. D's regulariser the Euclidean Hessian adds, on row 2 of every non-anchor block,
+// dreg_i d_i + 4 mu <y_i, d_i> y_i (row-2 vectors): the derivative of dreg_i y_i along d.
 template <typename T, int R>
-__device__ __forceinline__ double hvp_block(int i, const T* __restrict__ Y, T* __restrict__ Wd,
+__device__ __forceinline__ double hvp_block(int i, int N, const T* __restrict__ Y, T* __restrict__ Wd,
                                             const T* __restrict__ delta, T* __restrict__ Hd,
-                                            const double* __restrict__ Lam) {
+                                            const double* __restrict__ Lam, double mu) {
   using C = double;   // per-camera arithmetic in FP64 whatever the storage type
   C y[3][R], w[3][R], d[3][R], L[3][3];
   load_block<T, C, R>(Y, i, y);
   load_block<T, C, R>(Wd, i, w);
   zero_block<T, R>(Wd, i);
   load_block<T, C, R>(delta, i, d);
+  if (mu != 0.0 && i > 0) {
+    const C dreg = C(Lam[(size_t)9 * N + i]);
+    C yd = C(0);
+#pragma unroll
+    for (int j = 0; j < R; ++j) yd += y[2][j] * d[2][j];
+#pragma unroll
+    for (int j = 0; j < R; ++j) w[2][j] += dreg * d[2][j] + C(4) * C(mu) * yd * y[2][j];
+  }
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
@@ -298,7 +332,7 @@ k_hvp_epi(int N, const T* __restrict__ Y, T* __restrict__ Wd, const T* __restric
   if (sc->done) return;
   double v[1] = {0.0};
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < N) v[0] = hvp_block<T, R>(i, Y, Wd, delta, Hd, Lam);
+  if (i < N) v[0] = hvp_block<T, R>(i, N, Y, Wd, delta, Hd, Lam, sc->mu);
   grid_reduce<1>(v, partials, counter, [&](double* t) {
     const double kap = t[0];
     sc->kappa = kap;
@@ -558,20 +592,42 @@ k_dot(size_t total, const Ta* __restrict__ a, const Tb* __restrict__ b, double* 
 }
 
 // ------------------------------------------------------------------ Lanczos (FP64 vectors)
-// w_i = Wz_i - Lambda_i v_i (Z v with Z = Q - blockdiag(Lambda)); Wz reset to zero.
+// w_i = Wz_i + dreg_i e_3 e_3^T v_i - Lambda_i v_i (Z v with Z = Q + diag(dreg) -
+// blockdiag(Lambda), App. D; dreg = 0 without the regulariser); Wz reset to zero.
 template <typename Tw>
 __global__ void k_zv_epi(int N, Tw* __restrict__ Wz, const double* __restrict__ v,
                          const double* __restrict__ Lam, double* __restrict__ w) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   double x[3] = {v[3 * i], v[3 * i + 1], v[3 * i + 2]};
+  const double dreg = Lam[(size_t)9 * N + i];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const double lx = Lam[9 * i + 3 * a] * x[0] + Lam[9 * i + 3 * a + 1] * x[1] +
                       Lam[9 * i + 3 * a + 2] * x[2];
-    w[3 * i + a] = double(Wz[3 * i + a]) - lx;
+    w[3 * i + a] = double(Wz[3 * i + a]) - lx + (a == 2 ? dreg * x[2] : 0.0);
     Wz[3 * i + a] = Tw(0);
   }
+}
+
+// F(X) = mu sum_{i>=1} (x_i - 1)^2 and <grad F(X), X> = sum_i dreg_i x_i for the dual value of
+// App. E (sc->dot, sc->kappa)
+template <int R>
+__global__ void __launch_bounds__(CAM_THREADS)
+k_reg_terms(int N, const double* __restrict__ Y, Scal* sc, double* partials, unsigned* counter) {
+  double v[2] = {0.0, 0.0};
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > 0 && i < N) {
+    double x2 = 0.0;
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const double t = Y[(size_t)(3 * i + 2) * R + j];
+      x2 += t * t;
+    }
+    v[0] = sc->mu * (x2 - 1.0) * (x2 - 1.0);
+    v[1] = 2.0 * sc->mu * (x2 - 1.0) * x2;
+  }
+  grid_reduce<2>(v, partials, counter, [&](double* t) { sc->dot = t[0]; sc->kappa = t[1]; });
 }
 
 // c[j] = <V_j, w> for the m columns of V (column-major, stride ld); one block per column

@@ -200,12 +200,13 @@ struct Solver {
       XM_CUDA_TRY(cudaMalloc(p, vec_bytes));
       XM_CUDA_TRY(cudaMemsetAsync(*p, 0, vec_bytes, st));
     }
-    XM_CUDA_TRY(cudaMalloc(&Lam, sizeof(double) * 9 * (size_t)N));
-    XM_CUDA_TRY(cudaMalloc(&Lamc, sizeof(double) * 9 * (size_t)N));
-    XM_CUDA_TRY(cudaMemsetAsync(Lam, 0, sizeof(double) * 9 * (size_t)N, st));
-    XM_CUDA_TRY(cudaMemsetAsync(Lamc, 0, sizeof(double) * 9 * (size_t)N, st));
+    XM_CUDA_TRY(cudaMalloc(&Lam, sizeof(double) * lam_doubles(N)));
+    XM_CUDA_TRY(cudaMalloc(&Lamc, sizeof(double) * lam_doubles(N)));
+    XM_CUDA_TRY(cudaMemsetAsync(Lam, 0, sizeof(double) * lam_doubles(N), st));
+    XM_CUDA_TRY(cudaMemsetAsync(Lamc, 0, sizeof(double) * lam_doubles(N), st));
     XM_CUDA_TRY(cudaMalloc(&d_sc, sizeof(Scal)));
     XM_CUDA_TRY(cudaMemsetAsync(d_sc, 0, sizeof(Scal), st));
+    XM_CUDA_TRY(cudaMemcpyAsync(&d_sc->mu, &o.scale_reg, sizeof(double), cudaMemcpyHostToDevice, st));
     XM_CUDA_TRY(cudaMallocHost(&h_sc, sizeof(Scal)));
     XM_CUDA_TRY(cudaMalloc(&d_small, 256 * sizeof(double)));
     XM_CUDA_TRY(cudaMemsetAsync(d_small, 0, 256 * sizeof(double), st));
@@ -243,6 +244,19 @@ struct Solver {
     XM_CUDA_TRY(cudaMemcpyAsync(h_sc, d_sc, sizeof(Scal), cudaMemcpyDeviceToHost, st));
     XM_CUDA_TRY(cudaStreamSynchronize(st));
     return check_device_error(ctx, "solver");
+  }
+
+  // F(X) - <grad F(X), X> at the FP64 point Y64 (App. E dual value; 0 without regulariser)
+  template <int R>
+  xm_status reg_dual_terms(const double* Y64, double* out) {
+    *out = 0.0;
+    if (o.scale_reg == 0.0) return XM_OK;
+    k_reg_terms<R><<<nb_cam, CAM_THREADS, 0, st>>>(N, Y64, d_sc, ctx->d_partials, ctx->d_counter);
+    ++launches;
+    XM_CUDA_TRY(cudaGetLastError());
+    XM_TRY(pull_scalars());
+    *out = h_sc->dot - h_sc->kappa;
+    return XM_OK;
   }
 
   // one sweep; timed = bracket it with events (only for sweeps that always run)
@@ -598,6 +612,14 @@ struct Solver {
     XM_CUDA_TRY(cudaMemcpyAsync(&rho_hat, d_slot(), sizeof(double), cudaMemcpyDeviceToHost, st));
     XM_CUDA_TRY(cudaStreamSynchronize(st));
     XM_CUDA_TRY(cudaMemsetAsync(bWc, 0, vec_bytes, st));
+    if (o.scale_reg != 0.0) {   // + F(Xhat) = mu sum (s_i^2 - 1)^2 (App. D)
+      k_reg_terms<4><<<nb_cam, CAM_THREADS, 0, st>>>(N, (const double*)bYc, d_sc, ctx->d_partials,
+                                                     ctx->d_counter);
+      ++launches;
+      XM_CUDA_TRY(cudaGetLastError());
+      XM_TRY(pull_scalars());
+      rho_hat += h_sc->dot;
+    }
     info.rho_hat = rho_hat;
     return XM_OK;
   }
@@ -748,9 +770,11 @@ xm_status solve_impl(xm_ctx* ctx, const DeviceQ& q, const xm_opts& o, int r_in, 
                        [&] { return S.certify<8>(r, prec_z, &lam_def, &lam_max, &lam_range); }));
       // Thm. 1 needs a first-order critical point: with Lambda in closed form the duality gap
       // f - tr(Lambda_0) = <Y, Z Y> vanishes exactly there, so it is checked beside lambda_min.
-      double L0g[9];
+      double L0g[9], regd = 0.0;
       XM_CUDA_TRY(cudaMemcpy(L0g, S.Lam, sizeof(L0g), cudaMemcpyDeviceToHost));
-      gap = S.info.f - (L0g[0] + L0g[4] + L0g[8]);
+      XM_TRY(with_R(R, [&] { return S.reg_dual_terms<4>((const double*)S.bY64, &regd); },
+                       [&] { return S.reg_dual_terms<8>((const double*)S.bY64, &regd); }));
+      gap = S.info.f - (L0g[0] + L0g[4] + L0g[8] + regd);
       stationary = std::fabs(gap) <= 1e-6 * (1.0 + std::fabs(S.info.f));
     }
     const double tau = o.cert_tau_rel * std::max(std::fabs(lam_max), 1e-300);
@@ -855,10 +879,12 @@ xm_status solve_impl(xm_ctx* ctx, const DeviceQ& q, const xm_opts& o, int r_in, 
   I.lambda_min = std::min(lam_def, lam_range);
   I.lambda_max = lam_max;
   I.certified = certified ? 1 : 0;
-  // dual value tr(Lambda_0)
-  double L0[9];
+  // dual value tr(Lambda_0) (+ F(X) - <grad F(X), X> with App. D's regulariser, App. E)
+  double L0[9], regd = 0.0;
   XM_CUDA_TRY(cudaMemcpy(L0, S.Lam, sizeof(L0), cudaMemcpyDeviceToHost));
-  I.dual = L0[0] + L0[4] + L0[8];
+  XM_TRY(with_R(R, [&] { return S.reg_dual_terms<4>((const double*)S.bY64, &regd); },
+                   [&] { return S.reg_dual_terms<8>((const double*)S.bY64, &regd); }));
+  I.dual = L0[0] + L0[4] + L0[8] + regd;
   double y2 = 0;
   {
     XM_TRY(with_R(R,
@@ -899,6 +925,8 @@ static xm_status check_opts(const DeviceQ& q, const xm_opts& o) {
   if (o.prec == XM_BF16Q_BULK && !q.q16) return set_error(XM_EINVAL, "solve: XM_BF16Q_BULK needs XM_STORE_BF16");
   if (o.max_outer < 1 || o.max_tcg < 1 || o.lanczos_max < 1)
     return set_error(XM_EINVAL, "opts: iteration caps must be positive");
+  if (!(o.scale_reg >= 0.0) || !std::isfinite(o.scale_reg))
+    return set_error(XM_EINVAL, "opts: scale_reg must be finite and >= 0 (got %g)", o.scale_reg);
   return XM_OK;
 }
 

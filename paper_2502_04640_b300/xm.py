@@ -30,7 +30,8 @@ class XmOpts(ctypes.Structure):
                 ("max_tcg", ctypes.c_int), ("max_polish", ctypes.c_int),
                 ("lanczos_max", ctypes.c_int), ("lanczos_tol", ctypes.c_double),
                 ("time_limit_s", ctypes.c_double), ("seed", ctypes.c_uint64),
-                ("verbose", ctypes.c_int), ("init_jitter", ctypes.c_double)]
+                ("verbose", ctypes.c_int), ("init_jitter", ctypes.c_double),
+                ("scale_reg", ctypes.c_double)]
 
 
 class XmInfo(ctypes.Structure):
@@ -56,7 +57,8 @@ class XmAdjInfo(ctypes.Structure):
                 ("n_cg", ctypes.c_int), ("n_sweeps_fp32", ctypes.c_int),
                 ("n_sweeps_fp64", ctypes.c_int), ("t_lambda_s", ctypes.c_double),
                 ("t_resid_s", ctypes.c_double), ("t_total_s", ctypes.c_double),
-                ("launches", ctypes.c_long)]
+                ("launches", ctypes.c_long), ("dense_precond", ctypes.c_int),
+                ("gamma", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
