@@ -235,6 +235,45 @@ xm_status xm_backward(xm_ctx* ctx, const xm_qmat* q, const xm_opts* opts, int r,
                       const double* ukp, const double* w, const double* dL_dG, double* dL_dukp,
                       double* dL_dw, double* lam, xm_adj_info* info);
 
+/* ---- batched solve of many independent scenes (serving-style batches) ------------------
+ * Alg. 1 / Sec. 3.2 / Thm. 1 / Sec. 2.2 for every scene of a batch in one persistent launch:
+ * each CTA takes the next scene of a work queue (descending size) and runs its whole
+ * staircase with xm_solve's FP32-bulk schedule (FP32 RTR-tCG, quick certificate, FP64-gradient
+ * polish, Lanczos certificate with FP64 vectors, FP64 stationarity check, rounding).  A scene
+ * that needs rank > 4 is finished by a second (rank-8) persistent kernel in the same graph.
+ *
+ * xm_batch_create copies every scene's Q (each from xm_build_Q with an FP64 copy) into dense
+ * full FP32 and FP64 row-major copies (rows padded to a multiple of 4 columns) owned by the
+ * batch; the xm_qmat handles stay the caller's.  Scene size is limited by shared memory:
+ * 2 * 8 * ldq_max * 8 bytes of sweep staging plus the Krylov work must fit the 227 KB of a CTA
+ * (about 3N <= 1300; checked, XM_EINVAL otherwise). */
+typedef struct xm_batch xm_batch;
+
+typedef struct xm_batch_info {
+  double f, grad_norm, lambda_min, lambda_min_deflated, lambda_max, dual, rho_hat, eta, eta_robust;
+  unsigned long long t_begin_ns, t_end_ns; /* device clock when the scene started / finished  */
+  int N;                   /* cameras                                                          */
+  int status;              /* xm_status of this scene (XM_OK, XM_ENOTCERT, XM_ENOCONV)         */
+  int rank, certified, n_sweeps, n_sweeps_fp64, n_outer, n_tcg, n_lanczos, n_escapes;
+} xm_batch_info;
+
+xm_status xm_batch_create(xm_ctx* ctx, int S, const xm_qmat* const* qs, xm_batch** out);
+xm_status xm_batch_free(xm_ctx* ctx, xm_batch* b);
+/* Autotuner of the block-row tiling: times `reps` FP32 sweeps of every scene for each
+ * rows-per-warp candidate (1, 2, 4) and keeps, per scene-size class (3N <= 150, <= 450,
+ * <= 900, larger), the fastest; rpw_out (4 ints, may be NULL) receives the choice.  Run by
+ * xm_solve_batched on first use if not called before. */
+xm_status xm_batch_autotune(xm_ctx* ctx, xm_batch* b, int reps, int* rpw_out);
+/* Solves every scene.  opts: as xm_solve (r0 <= 4, r_max <= 8; prec is ignored: the FP32-bulk
+ * schedule is used; time_limit_s applies per scene).  R_out (sum N x 3 x 3) and s_out (sum N),
+ * device pointers, receive the rounded solutions scene after scene in the order of
+ * xm_batch_create; info (host, S entries, may be NULL) the per-scene results.  The two
+ * persistent launches are captured once in a CUDA graph (re-captured when opts or the output
+ * pointers change) and replayed.  Synchronous.  Returns XM_ENOTCERT / XM_ENOCONV if any scene
+ * ended so (see info[s].status). */
+xm_status xm_solve_batched(xm_ctx* ctx, xm_batch* b, const xm_opts* opts, double* R_out,
+                           double* s_out, xm_batch_info* info);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,1362 @@
+// Batched persistent solve of many independent scenes (serving-style batches of uneven size).
+//
+// One persistent launch walks a work queue of scenes in descending size order; each CTA takes
+// the next scene and runs the whole Riemannian staircase for it on the chip (Alg. 1 with
+// RTR-tCG of Sec. 3.2, the Thm. 1 certificate, the Thm. 2 escape, the Sec. 2.2 rounding) with
+// block-level reductions instead of grid-wide ones: no host round trip and no inter-CTA
+// synchronisation.  Per-scene Q (n_s <= a few thousand) is kept dense and full in FP32 (all the
+// bulk sweeps, HVPs and certificate products) and FP64 (polish gradients, objective, rounding),
+// row-major with the row length padded to a multiple of 4.  The sweep is a block-row product:
+// each warp owns RPW consecutive rows per step, lanes stride over 16-byte column chunks, Y is
+// staged in shared memory.  RPW is chosen per scene-size class by an autotuner that times the
+// candidates on the batch itself (xm_batch_autotune).
+//
+// The mixed-precision schedule matches xm_solve's XM_FP32_BULK mode: FP32 RTR-tCG to the bulk
+// tolerance, a 60-step quick certificate, an FP64-gradient polish with FP32 HVPs, then the
+// Lanczos certificate with FP64 vectors and Ritz values and the FP64 stationarity check.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <numeric>
+#include <vector>
+
+#include "xm_internal.cuh"
+#include "xm_ops.cuh"
+
+namespace xm {
+namespace bat {
+
+constexpr int NT = 256;            // threads per CTA
+constexpr int NW = NT / 32;
+constexpr int KQUICK = 60;         // Krylov steps of the quick certificate
+constexpr int NVEC = 17;           // per-slot vectors of NM x 8 doubles
+constexpr int NCLASS = 4;          // scene-size classes of the tiling table
+constexpr int XM_BATCH_HANDOVER = 100;   // internal status: continued by the rank-8 kernel
+
+__host__ __device__ inline int size_class(int n) { return n <= 150 ? 0 : (n <= 450 ? 1 : (n <= 900 ? 2 : 3)); }
+
+struct Desc {                      // one scene (device table, in queue order)
+  int N, n, ldq, scene;            // cameras, 3N, padded row length, index in the caller's order
+  int64_t q32, q64;                // element offsets of the dense Q copies
+  int64_t cam0;                    // first camera of the scene in the per-camera outputs
+  int64_t spill;                   // offset of the scene's hand-over area (n x 8 + n doubles)
+};
+
+struct Params {
+  const Desc* desc;
+  int S;
+  const float* Q32;
+  const double* Q64;
+  double* slots;                   // per-CTA scratch
+  int64_t slot_doubles;
+  int NM;                          // max ldq over the batch
+  int kmax;                        // Krylov cap of the final certificate
+  double* spill;                   // per-scene hand-over from the rank-4 to the rank-8 kernel
+  double* R_out;                   // sum N x 9
+  double* s_out;                   // sum N
+  xm_batch_info* out;              // S entries, indexed by the caller's scene order
+  unsigned* queue;                 // work-queue counter
+  int rpw[NCLASS];                 // rows per warp of the sweep, per size class
+  xm_opts o;
+  double mu;                       // App. D weight
+  unsigned long long time_limit_ns;  // per-scene wall-clock cap (0: none)
+};
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// ------------------------------------------------------------------ CTA reductions
+// Deterministic CTA sum of K values: warp butterflies, then the warp partials in warp order;
+// every thread returns the totals.  red: NW * K doubles of shared memory.
+template <int K>
+__device__ __forceinline__ void bsum(double (&v)[K], double* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const double x = warp_sum(v[k]);
+    if (lane == 0) red[wid * K + k] = x;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double t = 0.0;
+    for (int w = 0; w < NW; ++w) t += red[w * K + k];
+    v[k] = t;
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------------ block-row sweeps
+// ws (n x R) = Q xs with Q dense row-major (ld ldq, rows padded with zeros) and xs (ldq x R)
+// in shared memory, zero beyond row n.  Warp w takes rows [w RPW, w RPW + RPW), then strides
+// by NW RPW; lane l reads 16-byte chunks l, l + 32, ... of each row.
+template <int R, int RPW>
+__device__ __forceinline__ void sweep32_t(const float* __restrict__ Q, int n, int ldq,
+                                          const float* __restrict__ xs, float* __restrict__ ws) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nc = ldq >> 2;
+  for (int rb = wid * RPW; rb < n; rb += NW * RPW) {
+    float acc[RPW][R];
+#pragma unroll
+    for (int q = 0; q < RPW; ++q)
+#pragma unroll
+      for (int j = 0; j < R; ++j) acc[q][j] = 0.f;
+    for (int c = lane; c < nc; c += 32) {
+      float y[4][R];
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int j = 0; j < R; ++j) y[k][j] = xs[(4 * c + k) * R + j];
+#pragma unroll
+      for (int q = 0; q < RPW; ++q) {
+        if (rb + q < n) {
+          const float4 a = __ldg(reinterpret_cast<const float4*>(Q + (size_t)(rb + q) * ldq) + c);
+#pragma unroll
+          for (int j = 0; j < R; ++j)
+            acc[q][j] = fmaf(a.x, y[0][j], fmaf(a.y, y[1][j], fmaf(a.z, y[2][j], fmaf(a.w, y[3][j], acc[q][j]))));
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < RPW; ++q)
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        float x = acc[q][j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        acc[q][j] = x;
+      }
+    if (lane == 0) {
+#pragma unroll
+      for (int q = 0; q < RPW; ++q)
+        if (rb + q < n)
+#pragma unroll
+          for (int j = 0; j < R; ++j) ws[(rb + q) * R + j] = acc[q][j];
+    }
+  }
+}
+
+template <int R, int RPW>
+__device__ __forceinline__ void sweep64_t(const double* __restrict__ Q, int n, int ldq,
+                                          const double* __restrict__ xs, double* __restrict__ ws) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nc = ldq >> 1;
+  for (int rb = wid * RPW; rb < n; rb += NW * RPW) {
+    double acc[RPW][R];
+#pragma unroll
+    for (int q = 0; q < RPW; ++q)
+#pragma unroll
+      for (int j = 0; j < R; ++j) acc[q][j] = 0.0;
+    for (int c = lane; c < nc; c += 32) {
+      double y[2][R];
+#pragma unroll
+      for (int k = 0; k < 2; ++k)
+#pragma unroll
+        for (int j = 0; j < R; ++j) y[k][j] = xs[(2 * c + k) * R + j];
+#pragma unroll
+      for (int q = 0; q < RPW; ++q) {
+        if (rb + q < n) {
+          const double2 a = __ldg(reinterpret_cast<const double2*>(Q + (size_t)(rb + q) * ldq) + c);
+#pragma unroll
+          for (int j = 0; j < R; ++j) acc[q][j] = fma(a.x, y[0][j], fma(a.y, y[1][j], acc[q][j]));
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < RPW; ++q)
+#pragma unroll
+      for (int j = 0; j < R; ++j) acc[q][j] = warp_sum(acc[q][j]);
+    if (lane == 0) {
+#pragma unroll
+      for (int q = 0; q < RPW; ++q)
+        if (rb + q < n)
+#pragma unroll
+          for (int j = 0; j < R; ++j) ws[(rb + q) * R + j] = acc[q][j];
+    }
+  }
+}
+
+template <int R>
+__device__ __forceinline__ void sweep32(int rpw, const float* Q, int n, int ldq, const float* xs, float* ws) {
+  if (rpw == 1) sweep32_t<R, 1>(Q, n, ldq, xs, ws);
+  else if (rpw == 2) sweep32_t<R, 2>(Q, n, ldq, xs, ws);
+  else sweep32_t<R, 4>(Q, n, ldq, xs, ws);
+  __syncthreads();
+}
+
+template <int R>
+__device__ __forceinline__ void sweep64(const double* Q, int n, int ldq, const double* xs, double* ws) {
+  sweep64_t<R, 2>(Q, n, ldq, xs, ws);
+  __syncthreads();
+}
+
+// xs (ldq x R, type Td) <- v (n x R, type Ts), zero below row n
+template <typename Ts, typename Td, int R>
+__device__ __forceinline__ void stage(const Ts* __restrict__ v, int n, int ldq, Td* __restrict__ xs) {
+  for (int e = threadIdx.x; e < ldq * R; e += NT) xs[e] = e < n * R ? Td(v[e]) : Td(0);
+  __syncthreads();
+}
+
+// ------------------------------------------------------------------ serial small algebra
+// (run by one thread; m <= 8, Krylov dimension <= a few hundred)
+
+// cyclic Jacobi, eigenvalues in descending order, eigenvectors as columns of V (m x m row-major)
+__device__ void dev_sym_eig_desc(int m, double* A, double* w, double* V) {
+  for (int i = 0; i < m * m; ++i) V[i] = 0.0;
+  for (int i = 0; i < m; ++i) V[i * m + i] = 1.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int p = 0; p < m; ++p)
+      for (int q = 0; q < m; ++q) {
+        const double a = A[p * m + q];
+        tot += a * a;
+        if (p != q) off += a * a;
+      }
+    if (off <= 1e-30 * tot || off == 0.0) break;
+    for (int p = 0; p < m - 1; ++p)
+      for (int q = p + 1; q < m; ++q) {
+        const double apq = A[p * m + q];
+        if (fabs(apq) < 1e-300) continue;
+        const double tau = (A[q * m + q] - A[p * m + p]) / (2.0 * apq);
+        const double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+        const double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+        for (int k = 0; k < m; ++k) {
+          const double akp = A[k * m + p], akq = A[k * m + q];
+          A[k * m + p] = c * akp - s * akq;
+          A[k * m + q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < m; ++k) {
+          const double apk = A[p * m + k], aqk = A[q * m + k];
+          A[p * m + k] = c * apk - s * aqk;
+          A[q * m + k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < m; ++k) {
+          const double vkp = V[k * m + p], vkq = V[k * m + q];
+          V[k * m + p] = c * vkp - s * vkq;
+          V[k * m + q] = s * vkp + c * vkq;
+        }
+      }
+  }
+  for (int i = 0; i < m; ++i) w[i] = A[i * m + i];
+  // selection sort, descending, carrying the columns of V
+  for (int i = 0; i < m; ++i) {
+    int b = i;
+    for (int j = i + 1; j < m; ++j) if (w[j] > w[b]) b = j;
+    if (b != i) {
+      const double t = w[i]; w[i] = w[b]; w[b] = t;
+      for (int k = 0; k < m; ++k) { const double u = V[k * m + i]; V[k * m + i] = V[k * m + b]; V[k * m + b] = u; }
+    }
+  }
+}
+
+__device__ int dev_sturm(int k, const double* a, const double* b, double x) {
+  int c = 0;
+  double q = a[0] - x;
+  if (q < 0) ++c;
+  for (int i = 1; i < k; ++i) {
+    const double qq = (q == 0.0) ? 1e-300 : q;
+    q = a[i] - x - b[i - 1] * b[i - 1] / qq;
+    if (q < 0) ++c;
+  }
+  return c;
+}
+
+// j-th smallest eigenvalue of the tridiagonal (a[0..k), b[0..k-1)) by bisection
+__device__ double dev_tri_eig(int k, const double* a, const double* b, int j) {
+  double lo = a[0], hi = a[0];
+  for (int i = 0; i < k; ++i) {
+    const double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i + 1 < k ? fabs(b[i]) : 0.0);
+    lo = fmin(lo, a[i] - r);
+    hi = fmax(hi, a[i] + r);
+  }
+  const double span = fmax(fabs(lo), fabs(hi)) + 1e-300;
+  for (int it = 0; it < 200 && hi - lo > 1e-16 * span; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (dev_sturm(k, a, b, mid) > j) hi = mid; else lo = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+// eigenvector of the tridiagonal for th by inverse iteration on T - sigma I with a pivoted LU;
+// work: 5 k doubles + k chars
+__device__ void dev_tri_eigvec(int k, const double* a, const double* b, double th, double* s,
+                               double* work, char* piv) {
+  if (k == 1) { s[0] = 1.0; return; }
+  double* d = work;
+  double* du = work + k;
+  double* du2 = work + 2 * k;
+  double* l = work + 3 * k;
+  double* dl = work + 4 * k;
+  double scale = 0.0;
+  for (int i = 0; i < k; ++i) scale = fmax(scale, fabs(a[i]) + (i < k - 1 ? fabs(b[i]) : 0.0));
+  const double sigma = th - 1e-13 * (scale + 1e-300);
+  for (int i = 0; i < k; ++i) { d[i] = a[i] - sigma; du[i] = i < k - 1 ? b[i] : 0.0; du2[i] = 0.0; piv[i] = 0; }
+  for (int i = 0; i < k - 1; ++i) dl[i] = b[i];
+  for (int i = 0; i < k - 1; ++i) {
+    if (fabs(d[i]) >= fabs(dl[i])) {
+      const double f = d[i] != 0.0 ? dl[i] / d[i] : 0.0;
+      l[i] = f;
+      d[i + 1] -= f * du[i];
+    } else {
+      const double f = d[i] / dl[i];
+      l[i] = f;
+      piv[i] = 1;
+      const double t = du[i];
+      d[i] = dl[i];
+      du[i] = d[i + 1];
+      d[i + 1] = t - f * d[i + 1];
+      if (i < k - 2) { du2[i] = du[i + 1]; du[i + 1] = -f * du[i + 1]; }
+    }
+  }
+  for (int i = 0; i < k; ++i) if (d[i] == 0.0) d[i] = 1e-300;
+  for (int i = 0; i < k; ++i) s[i] = 1.0 / sqrt((double)k) * ((i % 3) ? 1.0 : -0.7);
+  for (int it = 0; it < 4; ++it) {
+    for (int i = 0; i < k - 1; ++i) {
+      if (piv[i]) { const double t = s[i]; s[i] = s[i + 1]; s[i + 1] = t - l[i] * s[i + 1]; }
+      else s[i + 1] -= l[i] * s[i];
+    }
+    s[k - 1] /= d[k - 1];
+    if (k > 1) s[k - 2] = (s[k - 2] - du[k - 2] * s[k - 1]) / d[k - 2];
+    for (int i = k - 3; i >= 0; --i) s[i] = (s[i] - du[i] * s[i + 1] - du2[i] * s[i + 2]) / d[i];
+    double nrm = 0.0;
+    for (int i = 0; i < k; ++i) nrm += s[i] * s[i];
+    nrm = sqrt(nrm);
+    for (int i = 0; i < k; ++i) s[i] /= nrm;
+  }
+}
+
+// ------------------------------------------------------------------ the per-CTA solver
+struct Smem {
+  void* xs;                        // sweep input staging, ldq x R (float or double)
+  void* ws;                        // sweep output, n x R
+  double* red;                     // NW x 64
+  double* small;                   // 320 doubles: Gram, eigenvectors, rotation, O0, scalars
+  double* ha;                      // Krylov alpha (kmax + 1)
+  double* hb;                      // Krylov beta (kmax + 1)
+  double* hs;                      // Ritz coefficients (kmax + 1)
+  double* cv;                      // reorthogonalisation coefficients (kmax + 16)
+  double* work;                    // 5 (kmax + 1)
+  char* piv;                       // kmax + 1
+};
+
+__host__ __device__ inline size_t smem_bytes(int NM, int R, int kmax) {
+  const size_t k1 = (size_t)kmax + 1;
+  return 2 * (size_t)NM * R * sizeof(double) + (size_t)NW * 64 * sizeof(double) + 320 * sizeof(double) +
+         (3 * k1 + (kmax + 16) + 5 * k1) * sizeof(double) + ((k1 + 15) / 16) * 16;
+}
+
+__device__ inline Smem carve(char* base, int NM, int R, int kmax) {
+  Smem s;
+  const size_t k1 = (size_t)kmax + 1;
+  double* p = reinterpret_cast<double*>(base);
+  s.xs = p; p += (size_t)NM * R;
+  s.ws = p; p += (size_t)NM * R;
+  s.red = p; p += NW * 64;
+  s.small = p; p += 320;
+  s.ha = p; p += k1;
+  s.hb = p; p += k1;
+  s.hs = p; p += k1;
+  s.cv = p; p += kmax + 16;
+  s.work = p; p += 5 * k1;
+  s.piv = reinterpret_cast<char*>(p);
+  return s;
+}
+
+template <int R>
+struct Cta {
+  const Params* P;
+  Desc d;
+  int N, n, ldq, rpw;
+  const float* Q32;
+  const double* Q64;
+  Smem sm;
+  double* slot;
+  // vectors (each NM x 8 doubles of the slot); the pointers move when RTR accepts a step
+  double *y64, *yc64, *g64, *gc64, *yh, *xi, *lam, *lamc;
+  float *yf, *ycf, *gf, *gcf;
+  double *t0, *t1, *t2, *t3, *t4;   // tCG vectors, used as float or double
+  double *V, *lw, *lritz;
+  xm_batch_info info;
+  double ref_g, cur_g2, f_cur;
+  bool timed_out;
+
+  __device__ void setup(const Params* p, const Desc& dd, char* smem_base) {
+    P = p; d = dd; N = dd.N; n = dd.n; ldq = dd.ldq;
+    rpw = p->rpw[size_class(n)];
+    Q32 = p->Q32 + dd.q32;
+    Q64 = p->Q64 + dd.q64;
+    sm = carve(smem_base, p->NM, R, p->kmax);
+    slot = p->slots + (size_t)blockIdx.x * p->slot_doubles;
+    const size_t VS = (size_t)p->NM * 8;
+    double* v[NVEC];
+    for (int k = 0; k < NVEC; ++k) v[k] = slot + k * VS;
+    y64 = v[0]; yc64 = v[1]; g64 = v[2]; gc64 = v[3]; yh = v[4]; xi = v[5];
+    yf = (float*)v[6]; ycf = (float*)v[7]; gf = (float*)v[8]; gcf = (float*)v[9];
+    t0 = v[10]; t1 = v[11]; t2 = v[12]; t3 = v[13]; t4 = v[14]; lam = v[15]; lamc = v[16];
+    V = slot + NVEC * VS;
+    lw = V + (size_t)p->NM * (XM_MAX_RANK + p->kmax + 1);
+    lritz = lw + p->NM;
+    ref_g = -1.0; cur_g2 = 0.0; f_cur = 0.0; timed_out = false;
+  }
+
+  // CTA-uniform: thread 0 reads the clock and broadcasts, so every thread takes the same branch
+  __device__ bool over_time() {
+    if (!P->time_limit_ns) return timed_out;
+    __shared__ int s_late;
+    if (threadIdx.x == 0) s_late = gtimer() > info.t_begin_ns + P->time_limit_ns ? 1 : 0;
+    __syncthreads();
+    if (s_late) timed_out = true;
+    __syncthreads();
+    return timed_out;
+  }
+
+  // W = Q Y in the sweep precision of To, then the gradient epilogue
+  template <typename To>
+  __device__ void grad_at(const To* Y, To* G, double* Lam, double& f, double& g2, double& y2) {
+    if (sizeof(To) == 4) {
+      stage<To, float, R>(Y, n, ldq, (float*)sm.xs);
+      sweep32<R>(rpw, Q32, n, ldq, (const float*)sm.xs, (float*)sm.ws);
+    } else {
+      stage<To, double, R>(Y, n, ldq, (double*)sm.xs);
+      sweep64<R>(Q64, n, ldq, (const double*)sm.xs, (double*)sm.ws);
+      ++info.n_sweeps_fp64;
+    }
+    ++info.n_sweeps;
+    double v[3] = {0.0, 0.0, 0.0};
+    for (int i = threadIdx.x; i < N; i += NT) {
+      double vi[3];
+      grad_block<To, R>(i, N, Y, (To*)sm.ws, G, Lam, P->mu, vi);
+      v[0] += vi[0]; v[1] += vi[1]; v[2] += vi[2];
+    }
+    bsum<3>(v, sm.red);
+    f = v[0]; g2 = v[1]; y2 = v[2];
+  }
+
+  // Hd = Hess[d] at Yin (Ti precision sweep); returns <d, Hd>
+  template <typename Ti>
+  __device__ double hvp(const Ti* Yin, const Ti* dv, Ti* Hd, const double* Lam) {
+    if (sizeof(Ti) == 4) {
+      stage<Ti, float, R>(dv, n, ldq, (float*)sm.xs);
+      sweep32<R>(rpw, Q32, n, ldq, (const float*)sm.xs, (float*)sm.ws);
+    } else {
+      stage<Ti, double, R>(dv, n, ldq, (double*)sm.xs);
+      sweep64<R>(Q64, n, ldq, (const double*)sm.xs, (double*)sm.ws);
+      ++info.n_sweeps_fp64;
+    }
+    ++info.n_sweeps;
+    double v[1] = {0.0};
+    for (int i = threadIdx.x; i < N; i += NT)
+      v[0] += hvp_block<Ti, R>(i, N, Yin, (Ti*)sm.ws, dv, Hd, Lam, P->mu);
+    bsum<1>(v, sm.red);
+    return v[0];
+  }
+
+  // w = Z v (FP64 vectors, FP32 product), Z = Q + diag(dreg) - blockdiag(Lambda)
+  __device__ void zmul(const double* v, double* w) {
+    stage<double, float, 1>(v, n, ldq, (float*)sm.xs);
+    sweep32<1>(rpw, Q32, n, ldq, (const float*)sm.xs, (float*)sm.ws);
+    ++info.n_sweeps;
+    const float* ws = (const float*)sm.ws;
+    for (int i = threadIdx.x; i < N; i += NT) {
+      const double x0 = v[3 * i], x1 = v[3 * i + 1], x2 = v[3 * i + 2];
+      const double* L = lam + 9 * (size_t)i;
+      const double dreg = lam[(size_t)9 * N + i];
+      w[3 * i] = double(ws[3 * i]) - (L[0] * x0 + L[1] * x1 + L[2] * x2);
+      w[3 * i + 1] = double(ws[3 * i + 1]) - (L[3] * x0 + L[4] * x1 + L[5] * x2);
+      w[3 * i + 2] = double(ws[3 * i + 2]) - (L[6] * x0 + L[7] * x1 + L[8] * x2) + dreg * x2;
+    }
+    __syncthreads();
+  }
+
+  __device__ double dot(const double* a, const double* b, int len) {
+    double v[1] = {0.0};
+    for (int e = threadIdx.x; e < len; e += NT) v[0] += a[e] * b[e];
+    bsum<1>(v, sm.red);
+    return v[0];
+  }
+
+  // Riemannian trust region (Absil et al. 2008, Alg. 10) with Steihaug-Toint tCG (Alg. 11);
+  // constants as in xm_solve.  To: iterate / gradient type, Ti: tCG type.  Y, G, Lam and their
+  // candidates are the member pointers of that precision (swapped on acceptance).
+  template <typename To, typename Ti>
+  __device__ void rtr(double tol_rel, int max_outer, bool bulk) {
+    To*& Y = *reinterpret_cast<To**>(sizeof(To) == 4 ? (void*)&yf : (void*)&y64);
+    To*& Yc = *reinterpret_cast<To**>(sizeof(To) == 4 ? (void*)&ycf : (void*)&yc64);
+    To*& G = *reinterpret_cast<To**>(sizeof(To) == 4 ? (void*)&gf : (void*)&g64);
+    To*& Gc = *reinterpret_cast<To**>(sizeof(To) == 4 ? (void*)&gcf : (void*)&gc64);
+    Ti* eta = (Ti*)t0;
+    Ti* Heta = (Ti*)t1;
+    Ti* rv = (Ti*)t2;
+    Ti* dv = (Ti*)t3;
+    Ti* Hd = (Ti*)t4;
+    const int nR = n * R;
+    double f, g2, y2;
+    grad_at<To>(Y, G, lam, f, g2, y2);
+    if (ref_g <= 0) ref_g = sqrt(g2);
+    const double tol_abs = tol_rel * ref_g;
+    const double Delta_bar = sqrt(fmax(y2, 1e-300));
+    double Delta = Delta_bar / 8.0;
+    const double eps_reg = sizeof(To) == 4 ? 1e2 * 1.1920929e-07 : 1e3 * 2.220446049250313e-16;
+    // the tCG's copy of Y when its precision differs (FP64 polish with FP32 HVPs)
+    const Ti* Yin;
+    int rejects = 0;
+    for (int k = 0; k < max_outer; ++k) {
+      if (!(sqrt(g2) > tol_abs) || over_time()) break;
+      if (sizeof(To) != sizeof(Ti)) {
+        for (int e = threadIdx.x; e < nR; e += NT) ((Ti*)yf)[e] = Ti(Y[e]);
+        Yin = (const Ti*)yf;
+      } else {
+        Yin = (const Ti*)Y;
+      }
+      // ---- tCG
+      for (int e = threadIdx.x; e < nR; e += NT) {
+        const Ti g = Ti(G[e]);
+        eta[e] = Ti(0); Heta[e] = Ti(0); rv[e] = g; dv[e] = -g;
+      }
+      __syncthreads();
+      double rr = g2, ee = 0.0, ed = 0.0, dd = g2;
+      const double r0 = sqrt(g2);
+      int iters = 0;
+      for (int j = 0; j < P->o.max_tcg; ++j) {
+        const double kap = hvp<Ti>(Yin, dv, Hd, lam);
+        ++iters;
+        const double D2 = Delta * Delta;
+        const double a = kap > 0.0 ? rr / kap : 0.0;
+        if (!(kap > 0.0) || ee + 2.0 * a * ed + a * a * dd >= D2) {
+          const double disc = ed * ed + dd * (D2 - ee);
+          const double tau = (-ed + sqrt(disc > 0.0 ? disc : 0.0)) / dd;
+          for (int e = threadIdx.x; e < nR; e += NT) {
+            eta[e] = Ti(double(eta[e]) + tau * double(dv[e]));
+            Heta[e] = Ti(double(Heta[e]) + tau * double(Hd[e]));
+          }
+          __syncthreads();
+          break;
+        }
+        // eta += a d, Heta += a Hd, r += a Hd re-projected onto the tangent space
+        double v[1] = {0.0};
+        for (int i = threadIdx.x; i < N; i += NT) {
+          double y[3][R], r3[3][R];
+          load_block<Ti, double, R>(Yin, i, y);
+#pragma unroll
+          for (int aa = 0; aa < 3; ++aa)
+#pragma unroll
+            for (int jj = 0; jj < R; ++jj) {
+              const size_t e = (size_t)(3 * i + aa) * R + jj;
+              const double hd = double(Hd[e]);
+              eta[e] = Ti(double(eta[e]) + a * double(dv[e]));
+              Heta[e] = Ti(double(Heta[e]) + a * hd);
+              r3[aa][jj] = double(rv[e]) + a * hd;
+            }
+          double S[3][3], al;
+          dual_block<double, R>(r3, y, i == 0, S, al);
+#pragma unroll
+          for (int aa = 0; aa < 3; ++aa)
+#pragma unroll
+            for (int jj = 0; jj < R; ++jj) {
+              r3[aa][jj] -= S[aa][0] * y[0][jj] + S[aa][1] * y[1][jj] + S[aa][2] * y[2][jj];
+              v[0] += r3[aa][jj] * r3[aa][jj];
+            }
+          store_block<Ti, double, R>(rv, i, r3);
+        }
+        bsum<1>(v, sm.red);
+        const double rr_new = v[0];
+        if (sqrt(rr_new) <= r0 * fmin(pow(r0, 1.0), 0.1)) break;
+        const double beta = rr_new / rr;
+        rr = rr_new;
+        double w3[3] = {0.0, 0.0, 0.0};
+        for (int e = threadIdx.x; e < nR; e += NT) {
+          const double de = -double(rv[e]) + beta * double(dv[e]);
+          dv[e] = Ti(de);
+          const double et = double(eta[e]);
+          w3[0] += et * et; w3[1] += et * de; w3[2] += de * de;
+        }
+        bsum<3>(w3, sm.red);
+        ee = w3[0]; ed = w3[1]; dd = w3[2];
+      }
+      info.n_tcg += iters;
+      // ---- model decrease, candidate, ratio test
+      double m3[3] = {0.0, 0.0, 0.0};
+      for (int e = threadIdx.x; e < nR; e += NT) {
+        const double g = double(G[e]), x = double(eta[e]), h = double(Heta[e]);
+        m3[0] += g * x; m3[1] += x * h; m3[2] += x * x;
+      }
+      bsum<3>(m3, sm.red);
+      for (int i = threadIdx.x; i < N; i += NT) retract_block<To, Ti, R>(i, Y, eta, 1.0, Yc);
+      __syncthreads();
+      double fc, gc2, yc2;
+      grad_at<To>(Yc, Gc, lamc, fc, gc2, yc2);
+      ++info.n_outer;
+      const double model_dec = -(m3[0] + 0.5 * m3[1]);
+      const double reg = fmax(1.0, fabs(f)) * eps_reg;
+      const double rho = (f - fc + reg) / (model_dec + reg);
+      const double en = sqrt(m3[2]);
+      if (!isfinite(fc) || rho < 0.25) Delta *= 0.25;
+      else if (rho > 0.75 && en >= Delta * (1.0 - 1e-6)) Delta = fmin(2.0 * Delta, Delta_bar);
+      const bool accept = isfinite(fc) && rho > 0.1 && fc <= f + reg;
+      if (accept) {
+        To* t = Y; Y = Yc; Yc = t;
+        t = G; G = Gc; Gc = t;
+        double* u = lam; lam = lamc; lamc = u;
+        f = fc; g2 = gc2;
+        rejects = 0;
+      } else {
+        ++rejects;
+      }
+      if (Delta < 1e-12 * Delta_bar) break;
+      if (bulk && (rejects >= 6 || Delta < 1e-7 * Delta_bar)) break;
+    }
+    f_cur = f;
+    cur_g2 = g2;
+  }
+
+  // Gram Y^T Y (R x R) of the FP64 iterate, then thread 0: eigen-decomposition of its leading
+  // m x m block, eigenvalues (descending) into small[0..m), eigenvectors (columns, m x m
+  // row-major) into small[64..)
+  __device__ void gram_eig(int m) {
+    double v[R * R];
+#pragma unroll
+    for (int k = 0; k < R * R; ++k) v[k] = 0.0;
+    for (int e = threadIdx.x; e < n; e += NT) {
+      double y[R];
+#pragma unroll
+      for (int a = 0; a < R; ++a) y[a] = y64[(size_t)e * R + a];
+#pragma unroll
+      for (int a = 0; a < R; ++a)
+#pragma unroll
+        for (int b = 0; b < R; ++b) v[a * R + b] += y[a] * y[b];
+    }
+    bsum<R * R>(v, sm.red);
+    if (threadIdx.x == 0) {
+      double A[R * R];
+      for (int a = 0; a < m; ++a)
+        for (int b = 0; b < m; ++b) A[a * m + b] = v[a * R + b];
+      dev_sym_eig_desc(m, A, sm.small, sm.small + 64);
+    }
+    __syncthreads();
+  }
+
+  // w -= V c over the first m columns of V (c = V^T w), one pass of classical Gram-Schmidt
+  __device__ void reorth(double* w, int m) {
+    if (m <= 0) return;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int NMc = P->NM;
+    for (int j = wid; j < m; j += NW) {
+      double s = 0.0;
+      const double* col = V + (size_t)j * NMc;
+      for (int e = lane; e < n; e += 32) s += col[e] * w[e];
+      s = warp_sum(s);
+      if (lane == 0) sm.cv[j] = s;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n; e += NT) {
+      double t = 0.0;
+      for (int j = 0; j < m; ++j) t += V[(size_t)j * NMc + e] * sm.cv[j];
+      w[e] -= t;
+    }
+    __syncthreads();
+  }
+
+  // Lanczos on Z restricted to range(Y)^perp (Thm. 1), as Solver::certify: deflation basis from
+  // the Gram matrix, Rayleigh quotients of Z on range(Y), full reorthogonalisation (twice), Ritz
+  // values by bisection every 10 steps, Ritz vector of the smallest into lritz.
+  __device__ void certify(int r, int kcap_steps, double& lam_def, double& lam_max, double& lam_range) {
+    const int NMc = P->NM;
+    const int kmax = P->kmax;
+    gram_eig(r);
+    // rotation: column j = E_j / sqrt(w_j) for the retained directions
+    __shared__ int s_nd;
+    if (threadIdx.x == 0) {
+      const double* w = sm.small;
+      const double* E = sm.small + 64;
+      double* rot = sm.small + 128;
+      int nd = 0;
+      for (int k = 0; k < R * R; ++k) rot[k] = 0.0;
+      for (int j = 0; j < r; ++j)
+        if (w[j] > 1e-10 * w[0]) {
+          for (int a = 0; a < r; ++a) rot[a * R + nd] = E[a * r + j] / sqrt(w[j]);
+          ++nd;
+        }
+      s_nd = nd;
+    }
+    __syncthreads();
+    const int nd = s_nd;
+    const double* rot = sm.small + 128;
+    for (int e = threadIdx.x; e < n; e += NT)
+      for (int j = 0; j < nd; ++j) {
+        double t = 0.0;
+        for (int a = 0; a < R; ++a) t += y64[(size_t)e * R + a] * rot[a * R + j];
+        V[(size_t)j * NMc + e] = t;
+      }
+    __syncthreads();
+    // Rayleigh quotients V_d^T Z V_d (nd x nd) -> smallest eigenvalue lam_range
+    __shared__ double zr[XM_MAX_RANK * XM_MAX_RANK];
+    for (int j = 0; j < nd; ++j) {
+      zmul(V + (size_t)j * NMc, lw);
+      for (int l = 0; l < nd; ++l) {
+        const double c = dot(V + (size_t)l * NMc, lw, n);
+        if (threadIdx.x == 0) zr[j * nd + l] = c;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (nd > 0) {
+        double A[XM_MAX_RANK * XM_MAX_RANK], w[XM_MAX_RANK], E[XM_MAX_RANK * XM_MAX_RANK];
+        for (int a = 0; a < nd; ++a)
+          for (int b = 0; b < nd; ++b) A[a * nd + b] = 0.5 * (zr[a * nd + b] + zr[b * nd + a]);
+        dev_sym_eig_desc(nd, A, w, E);
+        sm.small[300] = w[nd - 1];
+      } else {
+        sm.small[300] = 0.0;
+      }
+    }
+    __syncthreads();
+    lam_range = sm.small[300];
+    // start vector: splitmix64 uniform(-1, 1) keyed by (seed, index), as xm_solve
+    double* v0 = V + (size_t)nd * NMc;
+    for (int e = threadIdx.x; e < n; e += NT) {
+      uint64_t z = P->o.seed + 0x9E3779B97F4A7C15ull * (uint64_t)(e + 1);
+      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+      z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+      z ^= z >> 31;
+      v0[e] = (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+    }
+    __syncthreads();
+    reorth(v0, nd);
+    {
+      const double nrm = sqrt(dot(v0, v0, n));
+      const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+      for (int e = threadIdx.x; e < n; e += NT) v0[e] *= inv;
+      __syncthreads();
+    }
+    int K = 0;
+    double th_min = 0.0, th_max = 0.0;
+    const int kcap = min(kcap_steps > 0 ? min(kcap_steps, kmax) : kmax, n - nd);
+    __shared__ int s_conv;
+    for (int k = 0; k < kcap; ++k) {
+      double* vk = V + (size_t)(nd + k) * NMc;
+      const double* vkm1 = k > 0 ? V + (size_t)(nd + k - 1) * NMc : nullptr;
+      zmul(vk, lw);
+      const double a = dot(vk, lw, n);
+      const double b = k > 0 ? sm.hb[k - 1] : 0.0;
+      for (int e = threadIdx.x; e < n; e += NT) lw[e] -= a * vk[e] + (vkm1 ? b * vkm1[e] : 0.0);
+      __syncthreads();
+      reorth(lw, nd + k + 1);
+      reorth(lw, nd + k + 1);
+      const double bn = sqrt(dot(lw, lw, n));
+      const double inv = bn > 0.0 ? 1.0 / bn : 0.0;
+      double* vk1 = V + (size_t)(nd + k + 1) * NMc;
+      for (int e = threadIdx.x; e < n; e += NT) vk1[e] = lw[e] * inv;
+      if (threadIdx.x == 0) { sm.ha[k] = a; sm.hb[k] = bn; }
+      __syncthreads();
+      ++info.n_lanczos;
+      K = k + 1;
+      if ((K % 10) == 0 || K == kcap) {
+        if (threadIdx.x == 0) {
+          const double tmin = dev_tri_eig(K, sm.ha, sm.hb, 0);
+          const double tmax = dev_tri_eig(K, sm.ha, sm.hb, K - 1);
+          dev_tri_eigvec(K, sm.ha, sm.hb, tmin, sm.hs, sm.work, sm.piv);
+          const double res = fabs(sm.hb[K - 1] * sm.hs[K - 1]);
+          const double scale = fmax(fabs(tmax), fabs(tmin)) + 1e-300;
+          sm.small[301] = tmin;
+          sm.small[302] = tmax;
+          s_conv = (res <= P->o.lanczos_tol * scale || sm.hb[K - 1] <= 1e-14 * scale || K == kcap) ? 1 : 0;
+        }
+        __syncthreads();
+        th_min = sm.small[301];
+        th_max = sm.small[302];
+        if (s_conv) break;
+      }
+    }
+    // Ritz vector of th_min
+    for (int e = threadIdx.x; e < n; e += NT) {
+      double t = 0.0;
+      for (int j = 0; j < K; ++j) t += V[(size_t)(nd + j) * NMc + e] * sm.hs[j];
+      lritz[e] = t;
+    }
+    __syncthreads();
+    lam_def = th_min;
+    lam_max = th_max;
+  }
+
+  // F(X) - <grad F(X), X> at the FP64 iterate (App. E dual value; 0 without regulariser)
+  __device__ double reg_dual() {
+    if (P->mu == 0.0) return 0.0;
+    double v[2] = {0.0, 0.0};
+    for (int i = threadIdx.x + 0; i < N; i += NT) {
+      if (i == 0) continue;
+      double x2 = 0.0;
+      for (int j = 0; j < R; ++j) { const double t = y64[(size_t)(3 * i + 2) * R + j]; x2 += t * t; }
+      v[0] += P->mu * (x2 - 1.0) * (x2 - 1.0);
+      v[1] += 2.0 * P->mu * (x2 - 1.0) * x2;
+    }
+    bsum<2>(v, sm.red);
+    return v[0] - v[1];
+  }
+
+  // rounding (Sec. 2.2) into the scene's R and s; returns rho_hat = f(Yhat) in FP64 (+ F)
+  __device__ double round_and_eval(int r) {
+    gram_eig(r);
+    const double* E = sm.small + 64;
+    for (int e = threadIdx.x; e < n; e += NT) {
+      for (int j = 0; j < 3; ++j) {
+        double t = 0.0;
+        for (int a = 0; a < r; ++a) t += y64[(size_t)e * R + a] * (j < r ? E[a * r + j] : 0.0);
+        yh[(size_t)e * 4 + j] = t;
+      }
+      yh[(size_t)e * 4 + 3] = 0.0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {   // O0 = polar factor of Ubar_0 = Yh_0^T
+      double Ub[9], UtU[9], w3[3], V3[9];
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) Ub[a * 3 + b] = yh[b * 4 + a];
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+          double t = 0.0;
+          for (int k = 0; k < 3; ++k) t += Ub[k * 3 + a] * Ub[k * 3 + b];
+          UtU[a * 3 + b] = t;
+        }
+      dev_sym_eig_desc(3, UtU, w3, V3);
+      double* O0 = sm.small + 200;
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+          double t = 0.0;
+          for (int k = 0; k < 3; ++k) {
+            const double sig = sqrt(fmax(w3[k], 1e-300));
+            double uk = 0.0;
+            for (int m = 0; m < 3; ++m) uk += Ub[a * 3 + m] * V3[m * 3 + k];
+            t += uk / sig * V3[b * 3 + k];
+          }
+          O0[a * 3 + b] = t;
+        }
+    }
+    __syncthreads();
+    double* Yhat = xi;   // n x 4
+    for (int i = threadIdx.x; i < N; i += NT)
+      round_block(i, yh, sm.small + 200, P->R_out + 9 * d.cam0, P->s_out + d.cam0, Yhat);
+    __syncthreads();
+    stage<double, double, 4>(Yhat, n, ldq, (double*)sm.xs);
+    sweep64<4>(Q64, n, ldq, (const double*)sm.xs, (double*)sm.ws);
+    ++info.n_sweeps; ++info.n_sweeps_fp64;
+    const double* ws = (const double*)sm.ws;
+    double v[1] = {0.0};
+    for (int e = threadIdx.x; e < n * 4; e += NT) v[0] += Yhat[e] * ws[e];
+    if (P->mu != 0.0)
+      for (int i = threadIdx.x; i < N; i += NT)
+        if (i > 0) {
+          double x2 = 0.0;
+          for (int j = 0; j < 4; ++j) { const double t = Yhat[(size_t)(3 * i + 2) * 4 + j]; x2 += t * t; }
+          v[0] += P->mu * (x2 - 1.0) * (x2 - 1.0);
+        }
+    bsum<1>(v, sm.red);
+    return v[0];
+  }
+
+  // f at the FP64-retracted point Y + a Xi, evaluated with FP32 sweeps (the mixed mode's line
+  // search); the retracted point is left in yh
+  __device__ double f_at(double a) {
+    for (int i = threadIdx.x; i < N; i += NT) retract_block<double, double, R>(i, y64, xi, a, yh);
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * R; e += NT) ycf[e] = float(yh[e]);
+    __syncthreads();
+    double f, g2, y2;
+    grad_at<float>(ycf, gcf, lamc, f, g2, y2);
+    return f;
+  }
+
+  __device__ void copy64(const double* s, double* t, int len) {
+    for (int e = threadIdx.x; e < len; e += NT) t[e] = s[e];
+    __syncthreads();
+  }
+
+  // The staircase for one scene (Alg. 1 with xm_solve's FP32-bulk schedule).  Returns false
+  // when the scene needs rank > R and was handed over (rank-4 kernel only).
+  __device__ bool run(bool resume) {
+    const xm_opts& o = P->o;
+    const size_t nR = (size_t)n * R;
+    int r = o.r0;
+    bool pending_escape = false;
+    double* spill = P->spill + d.spill;
+    if (!resume) {
+      for (int i = threadIdx.x; i < N; i += NT) init_block(i, R, r, o.init_jitter, o.seed, y64);
+      __syncthreads();
+      if (o.init_jitter != 0.0 && r > 3) {   // make the jittered start feasible
+        for (int e = threadIdx.x; e < (int)nR; e += NT) xi[e] = 0.0;
+        __syncthreads();
+        for (int i = threadIdx.x; i < N; i += NT) retract_block<double, double, R>(i, y64, xi, 0.0, yc64);
+        __syncthreads();
+        double* t = y64; y64 = yc64; yc64 = t;
+      }
+    } else {
+      // hand-over from the rank-4 kernel: [ref_g, r, Y (n x 4), Ritz vector (n)]
+      ref_g = spill[0];
+      const int r_old = (int)spill[1];
+      for (int e = threadIdx.x; e < n; e += NT)
+        for (int j = 0; j < R; ++j) {
+          y64[(size_t)e * R + j] = j < 4 ? spill[2 + (size_t)e * 4 + j] : 0.0;
+          xi[(size_t)e * R + j] = j == r_old ? spill[2 + (size_t)n * 4 + e] : 0.0;
+        }
+      __syncthreads();
+      r = r_old + 1;
+      pending_escape = true;
+    }
+    double lam_def = 0.0, lam_max = 0.0, lam_range = 0.0;
+    bool certified = false;
+    int status = XM_OK;
+    for (;;) {
+      if (!pending_escape) {
+        // ---- FP32 bulk
+        for (int e = threadIdx.x; e < (int)nR; e += NT) yf[e] = float(y64[e]);
+        __syncthreads();
+        rtr<float, float>(o.bulk_tol_rel, o.max_outer, true);
+        for (int e = threadIdx.x; e < (int)nR; e += NT) y64[e] = double(yf[e]);
+        __syncthreads();
+        bool quick_escape = false;
+        if (r < o.r_max) {
+          certify(r, KQUICK, lam_def, lam_max, lam_range);
+          quick_escape = lam_def < -1e-4 * fabs(lam_max);
+        }
+        double gap = 0.0;
+        bool stationary = false;
+        if (!quick_escape) {
+          // FP64 polish from the FP64-projected iterate
+          for (int e = threadIdx.x; e < (int)nR; e += NT) xi[e] = 0.0;
+          __syncthreads();
+          for (int i = threadIdx.x; i < N; i += NT) retract_block<double, double, R>(i, y64, xi, 0.0, yc64);
+          __syncthreads();
+          { double* t = y64; y64 = yc64; yc64 = t; }
+          rtr<double, float>(o.grad_tol_rel, o.max_polish, false);
+          certify(r, 0, lam_def, lam_max, lam_range);
+          const double regd = reg_dual();
+          gap = f_cur - (lam[0] + lam[4] + lam[8] + regd);
+          stationary = fabs(gap) <= 1e-6 * (1.0 + fabs(f_cur));
+        }
+        const double tau = o.cert_tau_rel * fmax(fabs(lam_max), 1e-300);
+        certified = !quick_escape && lam_def >= -tau && stationary;
+        if (certified) break;
+        if (timed_out || (!quick_escape && lam_def >= -tau && !stationary)) { status = XM_ENOCONV; break; }
+        if (r >= o.r_max) { status = XM_ENOTCERT; break; }
+        // ---- escape (Thm. 2): into a null column of Y if one exists, else one rank up
+        gram_eig(r);
+        int col;
+        if (sm.small[r - 1] < 1e-12 * sm.small[0]) {
+          const double* E = sm.small + 64;
+          for (int e = threadIdx.x; e < n; e += NT) {
+            double y[R], t[R];
+            for (int a = 0; a < R; ++a) y[a] = y64[(size_t)e * R + a];
+            for (int b = 0; b < R; ++b) {
+              double acc = 0.0;
+              for (int a = 0; a < R; ++a)
+                acc += y[a] * ((a < r && b < r) ? E[a * r + b] : (a == b ? 1.0 : 0.0));
+              t[b] = acc;
+            }
+            for (int b = 0; b < R; ++b) y64[(size_t)e * R + b] = t[b];
+          }
+          __syncthreads();
+          col = r - 1;
+        } else if (r + 1 > R) {
+          // hand the scene to the rank-8 kernel
+          if (threadIdx.x == 0) { spill[0] = ref_g; spill[1] = r; }
+          for (int e = threadIdx.x; e < n; e += NT) {
+            for (int j = 0; j < 4; ++j) spill[2 + (size_t)e * 4 + j] = y64[(size_t)e * R + j];
+            spill[2 + (size_t)n * 4 + e] = lritz[e];
+          }
+          __syncthreads();
+          return false;
+        } else {
+          col = r;
+          r += 1;
+        }
+        for (int e = threadIdx.x; e < n; e += NT)
+          for (int j = 0; j < R; ++j) xi[(size_t)e * R + j] = j == col ? lritz[e] : 0.0;
+        __syncthreads();
+      }
+      pending_escape = false;
+      // ---- line search along the escape direction
+      const double f0 = f_at(0.0);
+      bool moved = false;
+      double alpha = 1.0;
+      for (int h = 0; h <= 30; ++h, alpha *= 0.5) {
+        const double fa = f_at(alpha);
+        if (fa < f0) {
+          copy64(yh, y64, n * R);
+          moved = true;
+          break;
+        }
+      }
+      ++info.n_escapes;
+      if (!moved) { status = XM_ENOTCERT; break; }
+      // every escape strictly lowers f; the cap bounds the work of a pathological scene
+      if (info.n_escapes >= 4 * XM_MAX_RANK) { status = XM_ENOTCERT; break; }
+    }
+    // ---- rounding and the reported numbers
+    const double rho_hat = round_and_eval(r);
+    double yy[1] = {0.0};
+    for (int e = threadIdx.x; e < (int)nR; e += NT) yy[0] += y64[e] * y64[e];
+    bsum<1>(yy, sm.red);
+    const double regd = reg_dual();
+    const double dual = lam[0] + lam[4] + lam[8] + regd;
+    const double lmin = fmin(lam_def, lam_range);
+    info.f = f_cur;
+    info.grad_norm = sqrt(cur_g2);
+    info.lambda_min_deflated = lam_def;
+    info.lambda_min = lmin;
+    info.lambda_max = lam_max;
+    info.dual = dual;
+    info.rho_hat = rho_hat;
+    info.eta = (rho_hat - f_cur) / (1.0 + fabs(rho_hat) + fabs(f_cur));
+    const double lower = dual + fmin(0.0, lmin) * yy[0];
+    info.eta_robust = (rho_hat - lower) / (1.0 + fabs(rho_hat) + fabs(lower));
+    info.rank = r;
+    info.certified = certified ? 1 : 0;
+    info.status = status;
+    return true;
+  }
+};
+
+// ------------------------------------------------------------------ kernels
+// Persistent batched solve: CTA-per-scene work queue (scenes in descending size order).  The
+// rank-4 kernel runs every scene; a scene that needs rank > 4 is handed to the rank-8 kernel
+// (launched right after it, which only takes the handed-over scenes).
+template <int R>
+__global__ void __launch_bounds__(NT, 1) k_batched(Params p) {
+  extern __shared__ __align__(16) char smem_base[];
+  __shared__ int s_job;
+  for (;;) {
+    if (threadIdx.x == 0) s_job = (int)atomicAdd(p.queue, 1u);
+    __syncthreads();
+    const int job = s_job;
+    __syncthreads();
+    if (job >= p.S) break;
+    const Desc d = p.desc[job];
+    xm_batch_info* out = p.out + d.scene;
+    if (R == 8 && out->status != XM_BATCH_HANDOVER) continue;
+    Cta<R> c;
+    c.setup(&p, d, smem_base);
+    const bool resume = (R == 8);
+    if (resume) {
+      c.info = *out;
+    } else {
+      c.info = xm_batch_info{};
+      c.info.N = d.N;
+      c.info.t_begin_ns = gtimer();
+    }
+    __syncthreads();
+    const bool finished = c.run(resume);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (!finished) c.info.status = XM_BATCH_HANDOVER;
+      c.info.t_end_ns = gtimer();
+      *out = c.info;
+    }
+    __syncthreads();
+  }
+}
+
+// Autotuner probe: CTA j runs `reps` FP32 sweeps (r = 4) of scene j with rows-per-warp rpw and
+// records its clock cycles.
+template <int RPW>
+__global__ void __launch_bounds__(NT, 1) k_tune_sweep(const Desc* desc, const float* Q32, int S, int NM, int reps,
+                                                     long long* cycles) {
+  extern __shared__ __align__(16) char smem_base[];
+  const int j = blockIdx.x;
+  if (j >= S) return;
+  const Desc d = desc[j];
+  float* xs = reinterpret_cast<float*>(smem_base);
+  float* ws = xs + (size_t)NM * 4;
+  for (int e = threadIdx.x; e < d.ldq * 4; e += NT) xs[e] = e < d.n * 4 ? 1.0f / (1 + (e % 7)) : 0.0f;
+  __syncthreads();
+  const long long t0 = clock64();
+  for (int k = 0; k < reps; ++k) {
+    sweep32_t<4, RPW>(Q32 + d.q32, d.n, d.ldq, xs, ws);
+    __syncthreads();
+  }
+  const long long t1 = clock64();
+  if (threadIdx.x == 0) cycles[j] = t1 - t0;
+}
+
+}  // namespace bat
+}  // namespace xm
+
+// ====================================================================================== host
+namespace xm {
+xm_status unpack_dense(xm_ctx* ctx, const DeviceQ& q, double* Qd);
+
+// dense n x n FP64 -> row-padded (n x ldq) FP64 and FP32 copies, zero padding
+__global__ void k_pack_batch_scene(const double* __restrict__ Qd, int n, int ldq, double* __restrict__ q64,
+                                   float* __restrict__ q32) {
+  const int64_t total = (int64_t)n * ldq;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int row = (int)(e / ldq), col = (int)(e % ldq);
+    const double v = col < n ? Qd[(size_t)row * n + col] : 0.0;
+    q64[e] = v;
+    q32[e] = float(v);
+  }
+}
+}  // namespace xm
+
+struct xm_batch {
+  int S = 0, NM = 0, n_max = 0;
+  int64_t total_cams = 0;
+  std::vector<xm::bat::Desc> desc_h;       // queue order
+  xm::bat::Desc* desc = nullptr;
+  float* Q32 = nullptr;
+  double* Q64 = nullptr;
+  double* spill = nullptr;
+  xm_batch_info* out = nullptr;
+  unsigned* queue = nullptr;
+  int rpw[xm::bat::NCLASS] = {1, 2, 2, 4};
+  bool tuned = false;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev = nullptr;
+  double* slots = nullptr;
+  size_t slots_doubles = 0;
+  // graph cache
+  cudaGraphExec_t gexec = nullptr;
+  xm_opts gopts{};
+  double* gR = nullptr;
+  double* gs = nullptr;
+  int gkmax = 0;
+};
+
+using namespace xm;
+
+namespace {
+
+void batch_release(xm_batch* b) {
+  if (!b) return;
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  void* ps[] = {b->desc, b->Q32, b->Q64, b->spill, b->out, b->queue, b->slots};
+  for (void* p : ps) if (p) cudaFree(p);
+  if (b->ev) cudaEventDestroy(b->ev);
+  if (b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+}  // namespace
+
+extern "C" xm_status xm_batch_create(xm_ctx* c, int S, const xm_qmat* const* qs, xm_batch** out) {
+  if (!c || !qs || !out || S < 1) return set_error(XM_EINVAL, "xm_batch_create: bad arguments");
+  *out = nullptr;
+  XM_CUDA_TRY(cudaSetDevice(c->device));
+  std::vector<int> order(S);
+  for (int j = 0; j < S; ++j) {
+    if (!qs[j]) return set_error(XM_EINVAL, "xm_batch_create: scene %d has no Q", j);
+    if (!qs[j]->d.q64) return set_error(XM_EINVAL, "xm_batch_create: scene %d's Q has no FP64 copy", j);
+    order[j] = j;
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return qs[a]->d.n > qs[b]->d.n; });
+  xm_batch* b = new xm_batch();
+  b->S = S;
+  std::vector<int64_t> cam0(S);
+  int64_t cams = 0;
+  for (int j = 0; j < S; ++j) { cam0[j] = cams; cams += qs[j]->d.N; }
+  b->total_cams = cams;
+  int64_t o64 = 0, osp = 0;
+  for (int k = 0; k < S; ++k) {
+    const int j = order[k];
+    bat::Desc d{};
+    d.N = qs[j]->d.N;
+    d.n = qs[j]->d.n;
+    d.ldq = (d.n + 3) & ~3;
+    d.scene = j;
+    d.q32 = o64;
+    d.q64 = o64;
+    d.cam0 = cam0[j];
+    d.spill = osp;
+    o64 += (int64_t)d.n * d.ldq;
+    osp += 2 + 5 * (int64_t)d.n;
+    b->NM = std::max(b->NM, d.ldq);
+    b->n_max = std::max(b->n_max, d.n);
+    b->desc_h.push_back(d);
+  }
+  auto fail = [&](xm_status st) { batch_release(b); return st; };
+#define XB_TRY(...)                                                                        \
+  do {                                                                                     \
+    cudaError_t e_ = (__VA_ARGS__);                                                        \
+    if (e_ != cudaSuccess)                                                                 \
+      return fail(set_error(e_ == cudaErrorMemoryAllocation ? XM_ENOMEM : XM_ECUDA,        \
+                            "%s failed: %s", #__VA_ARGS__, cudaGetErrorString(e_)));       \
+  } while (0)
+  XB_TRY(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+  XB_TRY(cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming));
+  XB_TRY(cudaMalloc(&b->desc, sizeof(bat::Desc) * S));
+  XB_TRY(cudaMalloc(&b->Q32, sizeof(float) * (size_t)o64));
+  XB_TRY(cudaMalloc(&b->Q64, sizeof(double) * (size_t)o64));
+  XB_TRY(cudaMalloc(&b->spill, sizeof(double) * (size_t)osp));
+  XB_TRY(cudaMalloc(&b->out, sizeof(xm_batch_info) * S));
+  XB_TRY(cudaMalloc(&b->queue, sizeof(unsigned) * 2));
+  XB_TRY(cudaMemcpyAsync(b->desc, b->desc_h.data(), sizeof(bat::Desc) * S, cudaMemcpyHostToDevice, c->stream));
+  double* tmp = nullptr;
+  XB_TRY(cudaMalloc(&tmp, sizeof(double) * (size_t)b->n_max * b->n_max));
+  for (int k = 0; k < S; ++k) {
+    const bat::Desc& d = b->desc_h[k];
+    xm_status st = unpack_dense(c, qs[d.scene]->d, tmp);
+    if (st != XM_OK) { cudaFree(tmp); return fail(st); }
+    const int64_t total = (int64_t)d.n * d.ldq;
+    const int g = (int)std::min<int64_t>((total + 255) / 256, (int64_t)c->num_sms * 8);
+    k_pack_batch_scene<<<std::max(g, 1), 256, 0, c->stream>>>(tmp, d.n, d.ldq, b->Q64 + d.q64, b->Q32 + d.q32);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) { cudaFree(tmp); return fail(set_error(XM_ECUDA, "pack: %s", cudaGetErrorString(e))); }
+  }
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  cudaFree(tmp);
+  if (e != cudaSuccess) return fail(set_error(XM_ECUDA, "xm_batch_create: %s", cudaGetErrorString(e)));
+#undef XB_TRY
+  *out = b;
+  return XM_OK;
+}
+
+extern "C" xm_status xm_batch_free(xm_ctx* c, xm_batch* b) {
+  if (!b) return XM_OK;
+  if (c) cudaSetDevice(c->device);
+  batch_release(b);
+  return XM_OK;
+}
+
+extern "C" xm_status xm_batch_autotune(xm_ctx* c, xm_batch* b, int reps, int* rpw_out) {
+  if (!c || !b) return set_error(XM_EINVAL, "xm_batch_autotune: NULL argument");
+  if (reps < 1) reps = 1;
+  XM_CUDA_TRY(cudaSetDevice(c->device));
+  const int S = b->S;
+  long long* dcyc = nullptr;
+  XM_CUDA_TRY(cudaMalloc(&dcyc, sizeof(long long) * S));
+  const size_t smem = (size_t)b->NM * 4 * sizeof(float) * 2;
+  const int cand[3] = {1, 2, 4};
+  double tot[3][bat::NCLASS] = {};
+  std::vector<long long> cyc(S);
+  xm_status st = XM_OK;
+  for (int ci = 0; ci < 3 && st == XM_OK; ++ci) {
+    cudaError_t e;
+    if (cand[ci] == 1) {
+      cudaFuncSetAttribute(bat::k_tune_sweep<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      bat::k_tune_sweep<1><<<S, bat::NT, smem, b->stream>>>(b->desc, b->Q32, S, b->NM, reps, dcyc);
+    } else if (cand[ci] == 2) {
+      cudaFuncSetAttribute(bat::k_tune_sweep<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      bat::k_tune_sweep<2><<<S, bat::NT, smem, b->stream>>>(b->desc, b->Q32, S, b->NM, reps, dcyc);
+    } else {
+      cudaFuncSetAttribute(bat::k_tune_sweep<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      bat::k_tune_sweep<4><<<S, bat::NT, smem, b->stream>>>(b->desc, b->Q32, S, b->NM, reps, dcyc);
+    }
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(cyc.data(), dcyc, sizeof(long long) * S, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) { st = set_error(XM_ECUDA, "xm_batch_autotune: %s", cudaGetErrorString(e)); break; }
+    for (int k = 0; k < S; ++k) tot[ci][bat::size_class(b->desc_h[k].n)] += (double)cyc[k];
+  }
+  cudaFree(dcyc);
+  if (st != XM_OK) return st;
+  for (int cl = 0; cl < bat::NCLASS; ++cl) {
+    int best = -1;
+    for (int ci = 0; ci < 3; ++ci)
+      if (tot[ci][cl] > 0 && (best < 0 || tot[ci][cl] < tot[best][cl])) best = ci;
+    if (best >= 0) b->rpw[cl] = cand[best];
+  }
+  b->tuned = true;
+  if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+  if (rpw_out) for (int cl = 0; cl < bat::NCLASS; ++cl) rpw_out[cl] = b->rpw[cl];
+  return XM_OK;
+}
+
+extern "C" xm_status xm_solve_batched(xm_ctx* c, xm_batch* b, const xm_opts* opts, double* R_out,
+                                      double* s_out, xm_batch_info* info) {
+  if (!c || !b || !opts || !R_out || !s_out) return set_error(XM_EINVAL, "xm_solve_batched: NULL argument");
+  const xm_opts& o = *opts;
+  if (o.r0 < 3 || o.r0 > 4 || o.r_max < o.r0 || o.r_max > XM_MAX_RANK)
+    return set_error(XM_EINVAL, "xm_solve_batched: need 3 <= r0 <= 4 and r0 <= r_max <= %d", XM_MAX_RANK);
+  if (o.max_outer < 1 || o.max_tcg < 1 || o.lanczos_max < 1)
+    return set_error(XM_EINVAL, "xm_solve_batched: iteration caps must be positive");
+  if (!(o.scale_reg >= 0.0) || !std::isfinite(o.scale_reg))
+    return set_error(XM_EINVAL, "xm_solve_batched: scale_reg must be finite and >= 0");
+  XM_CUDA_TRY(cudaSetDevice(c->device));
+  const int kmax = std::max(10, std::min(o.lanczos_max, b->n_max));
+  const size_t smem4 = bat::smem_bytes(b->NM, 4, kmax);
+  const size_t smem8 = bat::smem_bytes(b->NM, 8, kmax);
+  if (smem8 > c->smem_optin)
+    return set_error(XM_EINVAL, "xm_solve_batched: largest scene (3N = %d) needs %zu bytes of shared "
+                     "memory, above %zu", b->n_max, smem8, c->smem_optin);
+  XM_CUDA_TRY(cudaFuncSetAttribute(bat::k_batched<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem4));
+  XM_CUDA_TRY(cudaFuncSetAttribute(bat::k_batched<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem8));
+  const int grid = std::min(c->num_sms, b->S);
+  const size_t slot_doubles = ((size_t)bat::NVEC * b->NM * 8 + (size_t)b->NM * (XM_MAX_RANK + kmax + 1) +
+                               2 * (size_t)b->NM + 31) & ~size_t(31);
+  if (!b->slots || b->slots_doubles < slot_doubles * grid) {
+    if (b->slots) cudaFree(b->slots);
+    b->slots = nullptr;
+    b->slots_doubles = 0;
+    XM_CUDA_TRY(cudaMalloc(&b->slots, sizeof(double) * slot_doubles * grid));
+    b->slots_doubles = slot_doubles * grid;
+    if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+  }
+  if (!b->tuned) XM_TRY(xm_batch_autotune(c, b, 8, nullptr));
+  // order after the caller's work on the context stream
+  XM_CUDA_TRY(cudaEventRecord(b->ev, c->stream));
+  XM_CUDA_TRY(cudaStreamWaitEvent(b->stream, b->ev, 0));
+  const bool same = b->gexec && b->gR == R_out && b->gs == s_out && b->gkmax == kmax &&
+                    std::memcmp(&b->gopts, &o, sizeof(xm_opts)) == 0;
+  if (!same) {
+    if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+    bat::Params p{};
+    p.desc = b->desc;
+    p.S = b->S;
+    p.Q32 = b->Q32;
+    p.Q64 = b->Q64;
+    p.slots = b->slots;
+    p.slot_doubles = (int64_t)slot_doubles;
+    p.NM = b->NM;
+    p.kmax = kmax;
+    p.spill = b->spill;
+    p.R_out = R_out;
+    p.s_out = s_out;
+    p.out = b->out;
+    for (int cl = 0; cl < bat::NCLASS; ++cl) p.rpw[cl] = b->rpw[cl];
+    p.o = o;
+    p.mu = o.scale_reg;
+    p.time_limit_ns = o.time_limit_s > 0 ? (unsigned long long)(o.time_limit_s * 1e9) : 0ull;
+    bat::Params p8 = p;
+    p.queue = b->queue;
+    p8.queue = b->queue + 1;
+    cudaGraph_t graph = nullptr;
+    XM_CUDA_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    cudaMemsetAsync(b->queue, 0, sizeof(unsigned) * 2, b->stream);
+    bat::k_batched<4><<<grid, bat::NT, smem4, b->stream>>>(p);
+    if (o.r_max > 4) bat::k_batched<8><<<grid, bat::NT, smem8, b->stream>>>(p8);
+    const cudaError_t ec = cudaStreamEndCapture(b->stream, &graph);
+    if (ec != cudaSuccess) return set_error(XM_ECUDA, "xm_solve_batched: capture failed: %s", cudaGetErrorString(ec));
+    const cudaError_t ei = cudaGraphInstantiate(&b->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+      b->gexec = nullptr;
+      return set_error(XM_ECUDA, "xm_solve_batched: graph instantiate failed: %s", cudaGetErrorString(ei));
+    }
+    b->gR = R_out;
+    b->gs = s_out;
+    b->gkmax = kmax;
+    b->gopts = o;
+  }
+  XM_CUDA_TRY(cudaGraphLaunch(b->gexec, b->stream));
+  XM_CUDA_TRY(cudaStreamSynchronize(b->stream));
+  g_last_launches = o.r_max > 4 ? 2 : 1;
+  std::vector<xm_batch_info> h(b->S);
+  XM_CUDA_TRY(cudaMemcpy(h.data(), b->out, sizeof(xm_batch_info) * b->S, cudaMemcpyDeviceToHost));
+  long sweeps = 0;
+  int worst = XM_OK;
+  for (const auto& x : h) {
+    sweeps += x.n_sweeps;
+    if (x.status == XM_ENOCONV) worst = XM_ENOCONV;
+    else if (x.status != XM_OK && worst == XM_OK) worst = x.status;
+  }
+  g_last_sweeps = sweeps;
+  if (info) std::memcpy(info, h.data(), sizeof(xm_batch_info) * b->S);
+  if (worst == XM_ENOTCERT) return set_error(XM_ENOTCERT, "xm_solve_batched: some scenes stopped at r_max without a certificate");
+  if (worst == XM_ENOCONV) return set_error(XM_ENOCONV, "xm_solve_batched: some scenes hit the time limit or iteration caps");
+  if (worst != XM_OK) return set_error((xm_status)worst, "xm_solve_batched: scene status %d", worst);
+  return XM_OK;
+}

@@ -195,55 +195,61 @@ __device__ __forceinline__ void zero_block(T* p, int i) {
 // (with App. D's regulariser: W_i + dreg_i e_3 e_3^T Y_i in place of W_i, f + F(X)).
 // W is reset to zero for the next accumulating sweep.  Results go to (sc->f, g2, y2) or, with
 // cand = 1, to (sc->fc, gc2, yc2).
+// Camera i's share: Lambda_i (and dreg_i) into Lam, rgrad_i into G, W_i reset to zero;
+// returns (f_i, ||rgrad_i||^2, ||Y_i||^2) in v.
+template <typename T, int R>
+__device__ __forceinline__ void grad_block(int i, int N, const T* __restrict__ Y, T* __restrict__ W,
+                                           T* __restrict__ G, double* __restrict__ Lam, double mu,
+                                           double (&v)[3]) {
+  using C = double;   // per-camera arithmetic in FP64 whatever the storage type
+  C y[3][R], w[3][R], L[3][3], alpha;
+  load_block<T, C, R>(Y, i, y);
+  load_block<T, C, R>(W, i, w);
+  zero_block<T, R>(W, i);
+  double fi = 0.0, gi = 0.0, yi = 0.0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int j = 0; j < R; ++j) fi += double(y[a][j]) * double(w[a][j]);   // tr(Y^T Q Y)
+  // App. D regulariser: f += mu (x_i - 1)^2, (Q + grad F) Y adds dreg_i * row 2 of Y_i
+  C dreg = C(0);
+  if (mu != 0.0 && i > 0) {
+    C x2 = C(0);
+#pragma unroll
+    for (int j = 0; j < R; ++j) x2 += y[2][j] * y[2][j];
+    dreg = C(2) * C(mu) * (x2 - C(1));
+    fi += mu * double((x2 - C(1)) * (x2 - C(1)));
+#pragma unroll
+    for (int j = 0; j < R; ++j) w[2][j] += dreg * y[2][j];
+  }
+  dual_block<C, R>(w, y, i == 0, L, alpha);
+  C g[3][R];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      C ly = L[a][0] * y[0][j] + L[a][1] * y[1][j] + L[a][2] * y[2][j];
+      g[a][j] = C(2) * (w[a][j] - ly);
+      gi += double(g[a][j]) * double(g[a][j]);
+      yi += double(y[a][j]) * double(y[a][j]);
+    }
+  store_block<T, C, R>(G, i, g);
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) Lam[(size_t)9 * i + 3 * a + b] = double(L[a][b]);
+  Lam[(size_t)9 * N + i] = double(dreg);
+  v[0] = fi; v[1] = gi; v[2] = yi;
+}
+
 template <typename T, int R>
 __global__ void __launch_bounds__(CAM_THREADS)
 k_grad_epi(int N, const T* __restrict__ Y, T* __restrict__ W, T* __restrict__ G,
            double* __restrict__ Lam, Scal* sc, int cand, double* partials, unsigned* counter,
            int* err) {
-  using C = double;   // per-camera arithmetic in FP64 whatever the storage type
   double v[3] = {0.0, 0.0, 0.0};
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < N) {
-    C y[3][R], w[3][R], L[3][3], alpha;
-    load_block<T, C, R>(Y, i, y);
-    load_block<T, C, R>(W, i, w);
-    zero_block<T, R>(W, i);
-    double fi = 0.0, gi = 0.0, yi = 0.0;
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int j = 0; j < R; ++j) fi += double(y[a][j]) * double(w[a][j]);   // tr(Y^T Q Y)
-    // App. D regulariser: f += mu (x_i - 1)^2, (Q + grad F) Y adds dreg_i * row 2 of Y_i
-    const double mu = sc->mu;
-    C dreg = C(0);
-    if (mu != 0.0 && i > 0) {
-      C x2 = C(0);
-#pragma unroll
-      for (int j = 0; j < R; ++j) x2 += y[2][j] * y[2][j];
-      dreg = C(2) * C(mu) * (x2 - C(1));
-      fi += mu * double((x2 - C(1)) * (x2 - C(1)));
-#pragma unroll
-      for (int j = 0; j < R; ++j) w[2][j] += dreg * y[2][j];
-    }
-    dual_block<C, R>(w, y, i == 0, L, alpha);
-    C g[3][R];
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int j = 0; j < R; ++j) {
-        C ly = L[a][0] * y[0][j] + L[a][1] * y[1][j] + L[a][2] * y[2][j];
-        g[a][j] = C(2) * (w[a][j] - ly);
-        gi += double(g[a][j]) * double(g[a][j]);
-        yi += double(y[a][j]) * double(y[a][j]);
-      }
-    store_block<T, C, R>(G, i, g);
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int b = 0; b < 3; ++b) Lam[(size_t)9 * i + 3 * a + b] = double(L[a][b]);
-    Lam[(size_t)9 * N + i] = double(dreg);
-    v[0] = fi; v[1] = gi; v[2] = yi;
-  }
+  if (i < N) grad_block<T, R>(i, N, Y, W, G, Lam, sc->mu, v);
   grid_reduce<3>(v, partials, counter, [&](double* t) {
     if (!isfinite(t[0]) || !isfinite(t[1])) atomicOr(err, DEV_NUMERIC);
     if (cand) { sc->fc = t[0]; sc->gc2 = t[1]; sc->yc2 = t[2]; }
@@ -462,11 +468,9 @@ k_model_terms(int n_rows, const To* __restrict__ G, const Ti* __restrict__ eta,
 // Metric projection onto {sqrt(a) * (3 x r with orthonormal rows)}: A = Y_i + s Xi_i,
 // polar(A) = (A A^T)^{-1/2} A, scale = (sum of singular values) / 3 (anchor: 1).
 template <typename To, typename Ti, int R>
-__global__ void __launch_bounds__(CAM_THREADS)
-k_retract(int N, const To* __restrict__ Y, const Ti* __restrict__ Xi, double s, To* __restrict__ Yo) {
+__device__ __forceinline__ void retract_block(int i, const To* __restrict__ Y, const Ti* __restrict__ Xi,
+                                              double s, To* __restrict__ Yo) {
   using C = double;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
   C A[3][R];
 #pragma unroll
   for (int a = 0; a < 3; ++a)
@@ -516,6 +520,13 @@ k_retract(int N, const To* __restrict__ Y, const Ti* __restrict__ Xi, double s, 
 #pragma unroll
     for (int j = 0; j < R; ++j)
       Yo[(size_t)(3 * i + a) * R + j] = To(P[a][0] * A[0][j] + P[a][1] * A[1][j] + P[a][2] * A[2][j]);
+}
+
+template <typename To, typename Ti, int R>
+__global__ void __launch_bounds__(CAM_THREADS)
+k_retract(int N, const To* __restrict__ Y, const Ti* __restrict__ Xi, double s, To* __restrict__ Yo) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) retract_block<To, Ti, R>(i, Y, Xi, s, Yo);
 }
 
 // ------------------------------------------------------------------ element-wise helpers
@@ -691,15 +702,31 @@ static __global__ void k_random_vec(int n, uint64_t seed, double* v) {
   }
 }
 
+// ------------------------------------------------------------------ start point (Alg. 1)
+// Camera i's block of [I_3, ..., I_3] padded to rank r (R stored columns), plus jitter times a
+// splitmix64 uniform(-1, 1) fill of the columns 3..r-1 keyed by (seed, element index).
+__device__ __forceinline__ void init_block(int i, int R, int r, double jitter, uint64_t seed, double* Y) {
+  for (int a = 0; a < 3; ++a)
+    for (int j = 0; j < R; ++j) {
+      double v = (a == j) ? 1.0 : 0.0;
+      if (j >= 3 && j < r && jitter != 0.0) {
+        uint64_t z = seed + 0x9E3779B97F4A7C15ull * (uint64_t)((3 * i + a) * R + j + 1);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        v = jitter * ((double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0);
+      }
+      Y[(size_t)(3 * i + a) * R + j] = v;
+    }
+}
+
 // ------------------------------------------------------------------ rounding (Sec. 2.2)
 // Per camera: Ubar_i = Yh_i^T (3 x 3), G_i = O0^T Ubar_i, s_i = ||G_i||_F / sqrt(3),
 // R_i = SO(3) projection of G_i (SVD with determinant fix, Prop. 2); the anchor is (I, 1).
 // Writes R (N x 9, row-major), s (N) and Yhat = [s_i R_i]^T (n_rows x 4, last column zero).
-static __global__ void k_round(int N, const double* __restrict__ Yh, const double* __restrict__ O0,
-                        double* __restrict__ Rout, double* __restrict__ sout,
-                        double* __restrict__ Yhat) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
+__device__ __forceinline__ void round_block(int i, const double* __restrict__ Yh,
+                                            const double* __restrict__ O0, double* __restrict__ Rout,
+                                            double* __restrict__ sout, double* __restrict__ Yhat) {
   double Rm[3][3], s;
   if (i == 0) {
     for (int a = 0; a < 3; ++a)
@@ -751,6 +778,13 @@ static __global__ void k_round(int N, const double* __restrict__ Yh, const doubl
     }
   for (int b = 0; b < 3; ++b) Yhat[(size_t)(3 * i + b) * 4 + 3] = 0.0;
   sout[i] = s;
+}
+
+static __global__ void k_round(int N, const double* __restrict__ Yh, const double* __restrict__ O0,
+                               double* __restrict__ Rout, double* __restrict__ sout,
+                               double* __restrict__ Yhat) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) round_block(i, Yh, O0, Rout, sout, Yhat);
 }
 
 }  // namespace xm

@@ -635,19 +635,7 @@ static xm_status with_R(int R, F4 f4, F8 f8) {
 // 3..r-1, u uniform in [-1, 1) from splitmix64 of (seed, element index).
 __global__ void k_init_identity(int N, int R, int r, double jitter, uint64_t seed, double* Y) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  for (int a = 0; a < 3; ++a)
-    for (int j = 0; j < R; ++j) {
-      double v = (a == j) ? 1.0 : 0.0;
-      if (j >= 3 && j < r && jitter != 0.0) {
-        uint64_t z = seed + 0x9E3779B97F4A7C15ull * (uint64_t)((3 * i + a) * R + j + 1);
-        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-        z ^= z >> 31;
-        v = jitter * ((double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0);
-      }
-      Y[(size_t)(3 * i + a) * R + j] = v;
-    }
+  if (i < N) init_block(i, R, r, jitter, seed, Y);
 }
 
 __global__ void k_set_col(int n, int n_rows, int R, int col, const double* v, double* Xi) {

@@ -64,6 +64,21 @@ class XmAdjInfo(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class XmBatchInfo(ctypes.Structure):
+    _fields_ = [("f", ctypes.c_double), ("grad_norm", ctypes.c_double),
+                ("lambda_min", ctypes.c_double), ("lambda_min_deflated", ctypes.c_double),
+                ("lambda_max", ctypes.c_double), ("dual", ctypes.c_double),
+                ("rho_hat", ctypes.c_double), ("eta", ctypes.c_double),
+                ("eta_robust", ctypes.c_double), ("t_begin_ns", ctypes.c_ulonglong),
+                ("t_end_ns", ctypes.c_ulonglong), ("N", ctypes.c_int), ("status", ctypes.c_int),
+                ("rank", ctypes.c_int), ("certified", ctypes.c_int), ("n_sweeps", ctypes.c_int),
+                ("n_sweeps_fp64", ctypes.c_int), ("n_outer", ctypes.c_int), ("n_tcg", ctypes.c_int),
+                ("n_lanczos", ctypes.c_int), ("n_escapes", ctypes.c_int)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class XmError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -107,6 +122,11 @@ def lib() -> ctypes.CDLL:
                                       ctypes.POINTER(XmInfo)]),
         "xm_pipeline_host": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int64, _P, _P, _P,
                                             _P, ctypes.POINTER(XmOpts), _P, _P, ctypes.POINTER(XmInfo)]),
+        "xm_batch_create": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(_P)]),
+        "xm_batch_free": (ctypes.c_int, [_P, _P]),
+        "xm_batch_autotune": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+        "xm_solve_batched": (ctypes.c_int, [_P, _P, ctypes.POINTER(XmOpts), _P, _P,
+                                            ctypes.POINTER(XmBatchInfo)]),
         "xm_backward": (ctypes.c_int, [_P, _P, ctypes.POINTER(XmOpts), ctypes.c_int, _P, ctypes.c_int,
                                        ctypes.c_int, ctypes.c_int64, _P, _P, _P, _P, _P, _P, _P, _P,
                                        ctypes.POINTER(XmAdjInfo)]),
@@ -308,6 +328,56 @@ def xm_backward(q: QMat, Y, rank: int, M: int, cam, lmk, ukp, w, dL_dG, opts: Xm
                                   _ptr(cam), _ptr(lmk), _ptr(ukp), _ptr(w), _ptr(dL_dG), _ptr(d_u),
                                   _ptr(d_w), _ptr(lam), ctypes.byref(info)), allow)
     return d_u, d_w, lam, info.as_dict(), st
+
+
+class Batch:
+    """Owning handle of an xm_batch (dense per-scene copies of Q for the batched solve)."""
+
+    def __init__(self, ctx: Context, qmats):
+        self.ctx = ctx
+        self.S = len(qmats)
+        self.N = [q.N for q in qmats]
+        arr = (_P * self.S)(*[q.h for q in qmats])
+        h = _P()
+        _check(lib().xm_batch_create(ctx.h, self.S, arr, ctypes.byref(h)))
+        self.h = h
+
+    def free(self):
+        if getattr(self, "h", None):
+            lib().xm_batch_free(self.ctx.h, self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def xm_batch_create(ctx: Context, qmats) -> Batch:
+    return Batch(ctx, qmats)
+
+
+def xm_batch_autotune(b: Batch, reps: int = 8):
+    """Rows per warp chosen for the four scene-size classes."""
+    out = (ctypes.c_int * 4)()
+    _check(lib().xm_batch_autotune(b.ctx.h, b.h, reps, out))
+    return list(out)
+
+
+def xm_solve_batched(b: Batch, opts: XmOpts | None = None, R=None, s=None, allow_notcert: bool = True):
+    """Solves every scene; returns dict(R (sum N x 3 x 3), s (sum N), info (list of dicts), status).
+    R and s may be passed in (float64 CUDA tensors) to reuse the captured graph."""
+    import torch
+    dev = f"cuda:{b.ctx.device}"
+    opts = opts or xm_default_opts()
+    tot = sum(b.N)
+    R = torch.zeros((tot, 3, 3), dtype=torch.float64, device=dev) if R is None else R
+    s = torch.zeros((tot,), dtype=torch.float64, device=dev) if s is None else s
+    info = (XmBatchInfo * b.S)()
+    allow = (XM_OK, XM_ENOTCERT, XM_ENOCONV) if allow_notcert else (XM_OK,)
+    st = _check(lib().xm_solve_batched(b.ctx.h, b.h, ctypes.byref(opts), _ptr(R), _ptr(s), info), allow)
+    return dict(R=R, s=s, info=[x.as_dict() for x in info], status=st)
 
 
 def xm_pipeline_host(ctx: Context, N: int, M: int, cam, lmk, ukp, w, opts: XmOpts | None = None):

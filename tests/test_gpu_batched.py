@@ -1,0 +1,127 @@
+"""Parity of the batched persistent solve (xm_solve_batched) with the FP64 oracle and with the
+single-scene solver, scene by scene, on batches of uneven size.
+
+Tolerances are those of the single-scene solve tests (both paths end with an FP64 polish and an
+FP64 stationarity check): relative objective and rounded objective 1e-6, dual value 1e-6 of
+(1 + |f|), rotations 1e-5, scales 1e-5 relative.  The batched path is deterministic: every
+reduction has a fixed order and no scene's arithmetic depends on which CTA runs it, so two calls
+give bit-identical results."""
+import numpy as np
+import pytest
+
+import scenes
+from oracle import xm_oracle as O
+from tests.gpu_util import ctx, torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def C():
+    c = ctx()
+    yield c
+    c.close()
+
+
+def _rel(a, b):
+    return abs(a - b) / (1.0 + abs(b))
+
+
+def _batch(sizes, seed):
+    return [scenes.circle_scene(int(n), int(20 * n), 4, 0.01, seed=seed + j) for j, n in enumerate(sizes)]
+
+
+def _build(C, scs):
+    from paper_2502_04640_b300 import xm
+    qs = [xm.xm_build_Q(C, sc.N, sc.M, *xm.scene_tensors(sc)) for sc in scs]
+    return qs, xm.xm_batch_create(C, qs)
+
+
+def _split(out, scs):
+    R = out["R"].cpu().numpy()
+    s = out["s"].cpu().numpy()
+    off = np.cumsum([0] + [sc.N for sc in scs])
+    return [(R[off[j]:off[j + 1]], s[off[j]:off[j + 1]]) for j in range(len(scs))]
+
+
+def test_batched_matches_oracle_scene_by_scene(C):
+    from paper_2502_04640_b300 import xm
+    scs = _batch([12, 40, 7, 25, 60, 18, 33, 9], seed=700)
+    qs, b = _build(C, scs)
+    out = xm.xm_solve_batched(b, xm.xm_default_opts(time_limit_s=30.0), allow_notcert=False)
+    parts = _split(out, scs)
+    for j, sc in enumerate(scs):
+        info = out["info"][j]
+        Qo = O.build_Q_schur(sc.N, sc.M, sc.cam, sc.lmk, sc.ukp, sc.w)
+        ref = O.solve(Qo, r0=4)
+        assert ref.certified and info["certified"] == 1 and info["status"] == 0, (j, info)
+        assert info["N"] == sc.N
+        assert _rel(info["f"], ref.f) <= 1e-6, (j, info["f"], ref.f)
+        assert _rel(info["rho_hat"], ref.rho_hat) <= 1e-6
+        assert abs(info["dual"] - ref.cert.dual) <= 1e-6 * (1 + abs(ref.f))
+        R, s = parts[j]
+        assert np.abs(R - ref.R).max() <= 1e-5, j
+        assert np.abs(s - ref.s).max() <= 1e-5 * ref.s.max(), j
+        assert info["t_end_ns"] >= info["t_begin_ns"] > 0
+    for q in qs:
+        q.free()
+
+
+def test_batched_matches_single_scene_solver_and_is_deterministic(C):
+    from paper_2502_04640_b300 import xm
+    scs = _batch([30, 55, 14, 80], seed=800)
+    qs, b = _build(C, scs)
+    opts = xm.xm_default_opts(time_limit_s=30.0)
+    rpw = xm.xm_batch_autotune(b, reps=4)
+    assert all(x in (1, 2, 4) for x in rpw)
+    out = xm.xm_solve_batched(b, opts, allow_notcert=False)
+    out2 = xm.xm_solve_batched(b, opts, R=out["R"].clone(), s=out["s"].clone(), allow_notcert=False)
+    out3 = xm.xm_solve_batched(b, opts, R=out2["R"], s=out2["s"], allow_notcert=False)   # graph replay
+    assert torch.equal(out["R"], out2["R"]) and torch.equal(out["s"], out3["s"])
+    assert [i["f"] for i in out["info"]] == [i["f"] for i in out3["info"]]
+    parts = _split(out, scs)
+    for j, q in enumerate(qs):
+        single = xm.xm_solve(q, opts)
+        assert single["info"]["certified"] == 1
+        assert _rel(out["info"][j]["f"], single["info"]["f"]) <= 1e-6
+        assert np.abs(parts[j][0] - single["R"].cpu().numpy()).max() <= 1e-5
+        q.free()
+
+
+def test_batched_escapes_and_rank_handover(C):
+    """Alg. 1's exact start (no jitter) needs escapes; a scene whose staircase passes rank 4
+    continues in the rank-8 kernel."""
+    from paper_2502_04640_b300 import xm
+    scs = [scenes.config1(), scenes.circle_scene(12, 150, 4, 0.03, seed=41, w_range=(0.5, 1.5)),
+           scenes.circle_scene(16, 200, 4, 0.05, seed=61, w_range=(0.5, 1.5))]
+    qs, b = _build(C, scs)
+    out = xm.xm_solve_batched(b, xm.xm_default_opts(init_jitter=0.0, time_limit_s=30.0))
+    parts = _split(out, scs)
+    escapes = 0
+    for j, sc in enumerate(scs):
+        info = out["info"][j]
+        Qo = O.build_Q_schur(sc.N, sc.M, sc.cam, sc.lmk, sc.ukp, sc.w)
+        ref = O.solve(Qo, r0=4)
+        assert info["certified"] == 1, (j, info)
+        assert _rel(info["f"], ref.f) <= 1e-6
+        assert np.abs(parts[j][0] - ref.R).max() <= 1e-5
+        escapes += info["n_escapes"]
+    assert escapes >= 1
+    for q in qs:
+        q.free()
+
+
+def test_batched_regularised_and_errors(C):
+    from paper_2502_04640_b300 import xm
+    scs = _batch([20, 11], seed=900)
+    qs, b = _build(C, scs)
+    out = xm.xm_solve_batched(b, xm.xm_default_opts(scale_reg=2.0, time_limit_s=30.0), allow_notcert=False)
+    for j, sc in enumerate(scs):
+        Qo = O.build_Q_schur(sc.N, sc.M, sc.cam, sc.lmk, sc.ukp, sc.w)
+        ref = O.solve(Qo, r0=4, mu=2.0, grad_tol_rel=1e-12)
+        assert _rel(out["info"][j]["f"], ref.f) <= 1e-6
+        assert abs(out["info"][j]["dual"] - ref.cert.dual) <= 1e-6 * (1 + abs(ref.f))
+    with pytest.raises(xm.XmError, match="XM_EINVAL"):
+        xm.xm_solve_batched(b, xm.xm_default_opts(r0=5, r_max=8))
+    for q in qs:
+        q.free()
