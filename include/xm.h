@@ -252,6 +252,7 @@ typedef struct xm_batch xm_batch;
 typedef struct xm_batch_info {
   double f, grad_norm, lambda_min, lambda_min_deflated, lambda_max, dual, rho_hat, eta, eta_robust;
   unsigned long long t_begin_ns, t_end_ns; /* device clock when the scene started / finished  */
+  unsigned long long t_cert_ns, t_polish_ns; /* device time in the certificates / FP64 polish  */
   int N;                   /* cameras                                                          */
   int status;              /* xm_status of this scene (XM_OK, XM_ENOTCERT, XM_ENOCONV)         */
   int rank, certified, n_sweeps, n_sweeps_fp64, n_outer, n_tcg, n_lanczos, n_escapes;
@@ -259,11 +260,12 @@ typedef struct xm_batch_info {
 
 xm_status xm_batch_create(xm_ctx* ctx, int S, const xm_qmat* const* qs, xm_batch** out);
 xm_status xm_batch_free(xm_ctx* ctx, xm_batch* b);
-/* Autotuner of the block-row tiling: times `reps` FP32 sweeps of every scene for each
- * rows-per-warp candidate (1, 2, 4) and keeps, per scene-size class (3N <= 150, <= 450,
- * <= 900, larger), the fastest; rpw_out (4 ints, may be NULL) receives the choice.  Run by
- * xm_solve_batched on first use if not called before. */
-xm_status xm_batch_autotune(xm_ctx* ctx, xm_batch* b, int reps, int* rpw_out);
+/* Autotuner of the block-row tiling of the per-scene sweep: times `reps` FP32 sweeps of every
+ * scene for each candidate (rows per warp, 16-byte column chunks per lane and step) in
+ * {(2,4), (4,1), (4,2), (4,4), (8,1), (8,2)} and keeps, per scene-size class (3N <= 150, <= 450,
+ * <= 900, larger), the fastest; tile_out (8 ints: rows, chunks per class; may be NULL)
+ * receives the choice.  Run by xm_solve_batched on first use if not called before. */
+xm_status xm_batch_autotune(xm_ctx* ctx, xm_batch* b, int reps, int* tile_out);
 /* Solves every scene.  opts: as xm_solve (r0 <= 4, r_max <= 8; prec is ignored: the FP32-bulk
  * schedule is used; time_limit_s applies per scene).  R_out (sum N x 3 x 3) and s_out (sum N),
  * device pointers, receive the rounded solutions scene after scene in the order of

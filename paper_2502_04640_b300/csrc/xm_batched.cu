@@ -59,7 +59,7 @@ struct Params {
   double* s_out;                   // sum N
   xm_batch_info* out;              // S entries, indexed by the caller's scene order
   unsigned* queue;                 // work-queue counter
-  int rpw[NCLASS];                 // rows per warp of the sweep, per size class
+  int tile[NCLASS];                // sweep tiling variant per size class
   xm_opts o;
   double mu;                       // App. D weight
   unsigned long long time_limit_ns;  // per-scene wall-clock cap (0: none)
@@ -95,8 +95,10 @@ __device__ __forceinline__ void bsum(double (&v)[K], double* red) {
 // ------------------------------------------------------------------ block-row sweeps
 // ws (n x R) = Q xs with Q dense row-major (ld ldq, rows padded with zeros) and xs (ldq x R)
 // in shared memory, zero beyond row n.  Warp w takes rows [w RPW, w RPW + RPW), then strides
-// by NW RPW; lane l reads 16-byte chunks l, l + 32, ... of each row.
-template <int R, int RPW>
+// by NW RPW; lane l reads the 16-byte chunks l, l + 32, ... of each row, U chunks per step with
+// all RPW x U loads issued before the FMAs (memory-level parallelism: one CTA streams a whole
+// scene's Q).
+template <int R, int RPW, int U>
 __device__ __forceinline__ void sweep32_t(const float* __restrict__ Q, int n, int ldq,
                                           const float* __restrict__ xs, float* __restrict__ ws) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -107,19 +109,32 @@ __device__ __forceinline__ void sweep32_t(const float* __restrict__ Q, int n, in
     for (int q = 0; q < RPW; ++q)
 #pragma unroll
       for (int j = 0; j < R; ++j) acc[q][j] = 0.f;
-    for (int c = lane; c < nc; c += 32) {
-      float y[4][R];
+    for (int c0 = lane; c0 < nc; c0 += 32 * U) {
+      float4 a[RPW][U];
 #pragma unroll
-      for (int k = 0; k < 4; ++k)
+      for (int q = 0; q < RPW; ++q)
 #pragma unroll
-        for (int j = 0; j < R; ++j) y[k][j] = xs[(4 * c + k) * R + j];
+        for (int u = 0; u < U; ++u) {
+          const int c = c0 + 32 * u;
+          a[q][u] = (rb + q < n && c < nc)
+                        ? __ldg(reinterpret_cast<const float4*>(Q + (size_t)(rb + q) * ldq) + c)
+                        : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
 #pragma unroll
-      for (int q = 0; q < RPW; ++q) {
-        if (rb + q < n) {
-          const float4 a = __ldg(reinterpret_cast<const float4*>(Q + (size_t)(rb + q) * ldq) + c);
+      for (int u = 0; u < U; ++u) {
+        const int c = c0 + 32 * u;
+        if (c < nc) {
+          float y[4][R];
 #pragma unroll
-          for (int j = 0; j < R; ++j)
-            acc[q][j] = fmaf(a.x, y[0][j], fmaf(a.y, y[1][j], fmaf(a.z, y[2][j], fmaf(a.w, y[3][j], acc[q][j]))));
+          for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int j = 0; j < R; ++j) y[k][j] = xs[(4 * c + k) * R + j];
+#pragma unroll
+          for (int q = 0; q < RPW; ++q)
+#pragma unroll
+            for (int j = 0; j < R; ++j)
+              acc[q][j] = fmaf(a[q][u].x, y[0][j], fmaf(a[q][u].y, y[1][j],
+                          fmaf(a[q][u].z, y[2][j], fmaf(a[q][u].w, y[3][j], acc[q][j]))));
         }
       }
     }
@@ -141,6 +156,12 @@ __device__ __forceinline__ void sweep32_t(const float* __restrict__ Q, int n, in
     }
   }
 }
+
+// Tiling variants of the FP32 sweep (rows per warp, column chunks per step); the autotuner
+// picks one per scene-size class.
+constexpr int NTILE = 6;
+__host__ __device__ inline int tile_rpw(int v) { const int t[NTILE] = {2, 4, 4, 4, 8, 8}; return t[v]; }
+__host__ __device__ inline int tile_u(int v) { const int t[NTILE] = {4, 1, 2, 4, 1, 2}; return t[v]; }
 
 template <int R, int RPW>
 __device__ __forceinline__ void sweep64_t(const double* __restrict__ Q, int n, int ldq,
@@ -182,16 +203,23 @@ __device__ __forceinline__ void sweep64_t(const double* __restrict__ Q, int n, i
   }
 }
 
+// Out of line on purpose: one copy of the tiling variants per R instead of one per call site
+// keeps the solver kernel's instruction footprint small.
 template <int R>
-__device__ __forceinline__ void sweep32(int rpw, const float* Q, int n, int ldq, const float* xs, float* ws) {
-  if (rpw == 1) sweep32_t<R, 1>(Q, n, ldq, xs, ws);
-  else if (rpw == 2) sweep32_t<R, 2>(Q, n, ldq, xs, ws);
-  else sweep32_t<R, 4>(Q, n, ldq, xs, ws);
+__device__ __noinline__ void sweep32(int tile, const float* Q, int n, int ldq, const float* xs, float* ws) {
+  switch (tile) {
+    case 0: sweep32_t<R, 2, 4>(Q, n, ldq, xs, ws); break;
+    case 1: sweep32_t<R, 4, 1>(Q, n, ldq, xs, ws); break;
+    case 2: sweep32_t<R, 4, 2>(Q, n, ldq, xs, ws); break;
+    case 3: sweep32_t<R, 4, 4>(Q, n, ldq, xs, ws); break;
+    case 4: sweep32_t<R, 8, 1>(Q, n, ldq, xs, ws); break;
+    default: sweep32_t<R, 8, 2>(Q, n, ldq, xs, ws); break;
+  }
   __syncthreads();
 }
 
 template <int R>
-__device__ __forceinline__ void sweep64(const double* Q, int n, int ldq, const double* xs, double* ws) {
+__device__ __noinline__ void sweep64(const double* Q, int n, int ldq, const double* xs, double* ws) {
   sweep64_t<R, 2>(Q, n, ldq, xs, ws);
   __syncthreads();
 }
@@ -314,21 +342,96 @@ __device__ void dev_tri_eigvec(int k, const double* a, const double* b, double t
       if (i < k - 2) { du2[i] = du[i + 1]; du[i + 1] = -f * du[i + 1]; }
     }
   }
-  for (int i = 0; i < k; ++i) if (d[i] == 0.0) d[i] = 1e-300;
+  for (int i = 0; i < k; ++i) d[i] = 1.0 / (d[i] == 0.0 ? 1e-300 : d[i]);   // reciprocals
   for (int i = 0; i < k; ++i) s[i] = 1.0 / sqrt((double)k) * ((i % 3) ? 1.0 : -0.7);
   for (int it = 0; it < 4; ++it) {
     for (int i = 0; i < k - 1; ++i) {
       if (piv[i]) { const double t = s[i]; s[i] = s[i + 1]; s[i + 1] = t - l[i] * s[i + 1]; }
       else s[i + 1] -= l[i] * s[i];
     }
-    s[k - 1] /= d[k - 1];
-    if (k > 1) s[k - 2] = (s[k - 2] - du[k - 2] * s[k - 1]) / d[k - 2];
-    for (int i = k - 3; i >= 0; --i) s[i] = (s[i] - du[i] * s[i + 1] - du2[i] * s[i + 2]) / d[i];
+    s[k - 1] *= d[k - 1];
+    if (k > 1) s[k - 2] = (s[k - 2] - du[k - 2] * s[k - 1]) * d[k - 2];
+    for (int i = k - 3; i >= 0; --i) s[i] = (s[i] - du[i] * s[i + 1] - du2[i] * s[i + 2]) * d[i];
     double nrm = 0.0;
     for (int i = 0; i < k; ++i) nrm += s[i] * s[i];
-    nrm = sqrt(nrm);
-    for (int i = 0; i < k; ++i) s[i] /= nrm;
+    const double inv = 1.0 / sqrt(nrm);
+    for (int i = 0; i < k; ++i) s[i] *= inv;
   }
+}
+
+// Number of eigenvalues of the symmetric tridiagonal (a[0..k), b[0..k-1)) below x: sign
+// changes of the Sturm sequence p_0 = 1, p_i = (a_i - x) p_{i-1} - b_{i-1}^2 p_{i-2}, without
+// divisions (B300's FP64 division is slow); the pair (p_{i-1}, p_i) is rescaled by an exact
+// power of two when it leaves [2^-500, 2^500].  A zero p_i takes the sign opposite to p_{i-1}.
+__device__ __forceinline__ int sturm_nodiv(int k, const double* __restrict__ a, const double* __restrict__ b2,
+                                           double x) {
+  double pm = 1.0, p = a[0] - x;
+  int c = 0;
+  bool neg_prev = false;                       // sign of p_0 = +1
+  bool neg = p < 0.0 || (p == 0.0 && !neg_prev);
+  if (neg != neg_prev) ++c;
+  neg_prev = neg;
+  for (int i = 1; i < k; ++i) {
+    const double pn = (a[i] - x) * p - b2[i - 1] * pm;
+    pm = p;
+    p = pn;
+    const double ap = fabs(p);
+    if (ap > 0x1p500 || (ap < 0x1p-500 && fabs(pm) < 0x1p-500)) {
+      const double sc = ap > 0x1p500 ? 0x1p-500 : 0x1p500;
+      p *= sc;
+      pm *= sc;
+    }
+    neg = p < 0.0 || (p == 0.0 && !neg_prev);
+    if (neg != neg_prev) ++c;
+    neg_prev = neg;
+  }
+  return c;
+}
+
+// Smallest and largest eigenvalues of the tridiagonal by multisection: each round the 256
+// threads evaluate Sturm counts at 127 interior points of each bracket (threads 0..127 for
+// the smallest, 128..255 for the largest), shrinking both brackets by 128x; 8 rounds reach
+// FP64 resolution.  a, b2 (= b^2) and the scratch `cnt` (256 ints) in shared memory.
+__device__ void tri_extremes(int k, const double* a, const double* b, double* b2, int* cnt, double* brk,
+                             double& tmin, double& tmax) {
+  for (int i = threadIdx.x; i < k - 1; i += NT) b2[i] = b[i] * b[i];
+  if (threadIdx.x == 0) {
+    double lo = a[0], hi = a[0];
+    for (int i = 0; i < k; ++i) {
+      const double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i + 1 < k ? fabs(b[i]) : 0.0);
+      lo = fmin(lo, a[i] - r);
+      hi = fmax(hi, a[i] + r);
+    }
+    const double pad = 1e-12 * (fabs(lo) + fabs(hi)) + 1e-300;
+    brk[0] = lo - pad; brk[1] = hi + pad;   // bracket of the smallest
+    brk[2] = lo - pad; brk[3] = hi + pad;   // bracket of the largest
+  }
+  __syncthreads();
+  const int half = NT / 2;
+  const int t = threadIdx.x % half;
+  const bool upper = threadIdx.x >= half;
+  for (int round = 0; round < 8; ++round) {
+    const double lo = brk[upper ? 2 : 0], hi = brk[upper ? 3 : 1];
+    const double x = lo + (hi - lo) * (double)(t + 1) / (double)half;   // t = half-1 -> hi
+    cnt[threadIdx.x] = sturm_nodiv(k, a, b2, x);
+    __syncthreads();
+    if (threadIdx.x == 0 || threadIdx.x == half) {
+      // first point whose count reaches the target: the eigenvalue lies in (x_{t-1}, x_t]
+      const int target = upper ? k : 1;
+      const int base = upper ? half : 0;
+      int first = half - 1;
+      for (int u = 0; u < half; ++u)
+        if (cnt[base + u] >= target) { first = u; break; }
+      const double nlo = first == 0 ? lo : lo + (hi - lo) * (double)first / (double)half;
+      const double nhi = lo + (hi - lo) * (double)(first + 1) / (double)half;
+      brk[upper ? 2 : 0] = nlo;
+      brk[upper ? 3 : 1] = nhi;
+    }
+    __syncthreads();
+  }
+  tmin = 0.5 * (brk[0] + brk[1]);
+  tmax = 0.5 * (brk[2] + brk[3]);
+  __syncthreads();
 }
 
 // ------------------------------------------------------------------ the per-CTA solver
@@ -342,13 +445,16 @@ struct Smem {
   double* hs;                      // Ritz coefficients (kmax + 1)
   double* cv;                      // reorthogonalisation coefficients (kmax + 16)
   double* work;                    // 5 (kmax + 1)
+  double* b2;                      // squared Krylov beta (kmax + 1)
+  double* brk;                     // multisection brackets (4)
+  int* cnt;                        // Sturm counts (NT)
   char* piv;                       // kmax + 1
 };
 
 __host__ __device__ inline size_t smem_bytes(int NM, int R, int kmax) {
   const size_t k1 = (size_t)kmax + 1;
   return 2 * (size_t)NM * R * sizeof(double) + (size_t)NW * 64 * sizeof(double) + 320 * sizeof(double) +
-         (3 * k1 + (kmax + 16) + 5 * k1) * sizeof(double) + ((k1 + 15) / 16) * 16;
+         (3 * k1 + (kmax + 16) + 5 * k1 + k1 + 4) * sizeof(double) + NT * sizeof(int) + ((k1 + 15) / 16) * 16;
 }
 
 __device__ inline Smem carve(char* base, int NM, int R, int kmax) {
@@ -364,7 +470,10 @@ __device__ inline Smem carve(char* base, int NM, int R, int kmax) {
   s.hs = p; p += k1;
   s.cv = p; p += kmax + 16;
   s.work = p; p += 5 * k1;
-  s.piv = reinterpret_cast<char*>(p);
+  s.b2 = p; p += k1;
+  s.brk = p; p += 4;
+  s.cnt = reinterpret_cast<int*>(p);
+  s.piv = reinterpret_cast<char*>(s.cnt + NT);
   return s;
 }
 
@@ -372,7 +481,7 @@ template <int R>
 struct Cta {
   const Params* P;
   Desc d;
-  int N, n, ldq, rpw;
+  int N, n, ldq, tile;
   const float* Q32;
   const double* Q64;
   Smem sm;
@@ -388,7 +497,7 @@ struct Cta {
 
   __device__ void setup(const Params* p, const Desc& dd, char* smem_base) {
     P = p; d = dd; N = dd.N; n = dd.n; ldq = dd.ldq;
-    rpw = p->rpw[size_class(n)];
+    tile = p->tile[size_class(n)];
     Q32 = p->Q32 + dd.q32;
     Q64 = p->Q64 + dd.q64;
     sm = carve(smem_base, p->NM, R, p->kmax);
@@ -421,7 +530,7 @@ struct Cta {
   __device__ void grad_at(const To* Y, To* G, double* Lam, double& f, double& g2, double& y2) {
     if (sizeof(To) == 4) {
       stage<To, float, R>(Y, n, ldq, (float*)sm.xs);
-      sweep32<R>(rpw, Q32, n, ldq, (const float*)sm.xs, (float*)sm.ws);
+      sweep32<R>(tile, Q32, n, ldq, (const float*)sm.xs, (float*)sm.ws);
     } else {
       stage<To, double, R>(Y, n, ldq, (double*)sm.xs);
       sweep64<R>(Q64, n, ldq, (const double*)sm.xs, (double*)sm.ws);
@@ -431,7 +540,7 @@ struct Cta {
     double v[3] = {0.0, 0.0, 0.0};
     for (int i = threadIdx.x; i < N; i += NT) {
       double vi[3];
-      grad_block<To, R>(i, N, Y, (To*)sm.ws, G, Lam, P->mu, vi);
+      grad_block<To, R, To>(i, N, Y, (To*)sm.ws, G, Lam, P->mu, vi);
       v[0] += vi[0]; v[1] += vi[1]; v[2] += vi[2];
     }
     bsum<3>(v, sm.red);
@@ -443,7 +552,7 @@ struct Cta {
   __device__ double hvp(const Ti* Yin, const Ti* dv, Ti* Hd, const double* Lam) {
     if (sizeof(Ti) == 4) {
       stage<Ti, float, R>(dv, n, ldq, (float*)sm.xs);
-      sweep32<R>(rpw, Q32, n, ldq, (const float*)sm.xs, (float*)sm.ws);
+      sweep32<R>(tile, Q32, n, ldq, (const float*)sm.xs, (float*)sm.ws);
     } else {
       stage<Ti, double, R>(dv, n, ldq, (double*)sm.xs);
       sweep64<R>(Q64, n, ldq, (const double*)sm.xs, (double*)sm.ws);
@@ -452,26 +561,9 @@ struct Cta {
     ++info.n_sweeps;
     double v[1] = {0.0};
     for (int i = threadIdx.x; i < N; i += NT)
-      v[0] += hvp_block<Ti, R>(i, N, Yin, (Ti*)sm.ws, dv, Hd, Lam, P->mu);
+      v[0] += hvp_block<Ti, R, Ti>(i, N, Yin, (Ti*)sm.ws, dv, Hd, Lam, P->mu);
     bsum<1>(v, sm.red);
     return v[0];
-  }
-
-  // w = Z v (FP64 vectors, FP32 product), Z = Q + diag(dreg) - blockdiag(Lambda)
-  __device__ void zmul(const double* v, double* w) {
-    stage<double, float, 1>(v, n, ldq, (float*)sm.xs);
-    sweep32<1>(rpw, Q32, n, ldq, (const float*)sm.xs, (float*)sm.ws);
-    ++info.n_sweeps;
-    const float* ws = (const float*)sm.ws;
-    for (int i = threadIdx.x; i < N; i += NT) {
-      const double x0 = v[3 * i], x1 = v[3 * i + 1], x2 = v[3 * i + 2];
-      const double* L = lam + 9 * (size_t)i;
-      const double dreg = lam[(size_t)9 * N + i];
-      w[3 * i] = double(ws[3 * i]) - (L[0] * x0 + L[1] * x1 + L[2] * x2);
-      w[3 * i + 1] = double(ws[3 * i + 1]) - (L[3] * x0 + L[4] * x1 + L[5] * x2);
-      w[3 * i + 2] = double(ws[3 * i + 2]) - (L[6] * x0 + L[7] * x1 + L[8] * x2) + dreg * x2;
-    }
-    __syncthreads();
   }
 
   __device__ double dot(const double* a, const double* b, int len) {
@@ -506,6 +598,9 @@ struct Cta {
     // the tCG's copy of Y when its precision differs (FP64 polish with FP32 HVPs)
     const Ti* Yin;
     int rejects = 0;
+    constexpr int STALL_W = 5;   // bulk-phase stagnation window (as xm_solve)
+    double f_hist[STALL_W + 1];
+    int n_hist = 0;
     for (int k = 0; k < max_outer; ++k) {
       if (!(sqrt(g2) > tol_abs) || over_time()) break;
       if (sizeof(To) != sizeof(Ti)) {
@@ -538,44 +633,49 @@ struct Cta {
           __syncthreads();
           break;
         }
-        // eta += a d, Heta += a Hd, r += a Hd re-projected onto the tangent space
-        double v[1] = {0.0};
+        // eta += a d, Heta += a Hd, r += a Hd re-projected onto the tangent space (tCG
+        // arithmetic in the tCG's precision; per-thread partial sums, CTA sum in FP64)
+        Ti part = Ti(0);
+        const Ti at = Ti(a);
         for (int i = threadIdx.x; i < N; i += NT) {
-          double y[3][R], r3[3][R];
-          load_block<Ti, double, R>(Yin, i, y);
+          Ti y[3][R], r3[3][R];
+          load_block<Ti, Ti, R>(Yin, i, y);
 #pragma unroll
           for (int aa = 0; aa < 3; ++aa)
 #pragma unroll
             for (int jj = 0; jj < R; ++jj) {
               const size_t e = (size_t)(3 * i + aa) * R + jj;
-              const double hd = double(Hd[e]);
-              eta[e] = Ti(double(eta[e]) + a * double(dv[e]));
-              Heta[e] = Ti(double(Heta[e]) + a * hd);
-              r3[aa][jj] = double(rv[e]) + a * hd;
+              const Ti hd = Hd[e];
+              eta[e] = eta[e] + at * dv[e];
+              Heta[e] = Heta[e] + at * hd;
+              r3[aa][jj] = rv[e] + at * hd;
             }
-          double S[3][3], al;
-          dual_block<double, R>(r3, y, i == 0, S, al);
+          Ti S[3][3], al;
+          dual_block<Ti, R>(r3, y, i == 0, S, al);
 #pragma unroll
           for (int aa = 0; aa < 3; ++aa)
 #pragma unroll
             for (int jj = 0; jj < R; ++jj) {
               r3[aa][jj] -= S[aa][0] * y[0][jj] + S[aa][1] * y[1][jj] + S[aa][2] * y[2][jj];
-              v[0] += r3[aa][jj] * r3[aa][jj];
+              part += r3[aa][jj] * r3[aa][jj];
             }
-          store_block<Ti, double, R>(rv, i, r3);
+          store_block<Ti, Ti, R>(rv, i, r3);
         }
+        double v[1] = {double(part)};
         bsum<1>(v, sm.red);
         const double rr_new = v[0];
         if (sqrt(rr_new) <= r0 * fmin(pow(r0, 1.0), 0.1)) break;
         const double beta = rr_new / rr;
         rr = rr_new;
-        double w3[3] = {0.0, 0.0, 0.0};
+        Ti p3[3] = {Ti(0), Ti(0), Ti(0)};
+        const Ti bt = Ti(beta);
         for (int e = threadIdx.x; e < nR; e += NT) {
-          const double de = -double(rv[e]) + beta * double(dv[e]);
-          dv[e] = Ti(de);
-          const double et = double(eta[e]);
-          w3[0] += et * et; w3[1] += et * de; w3[2] += de * de;
+          const Ti de = -rv[e] + bt * dv[e];
+          dv[e] = de;
+          const Ti et = eta[e];
+          p3[0] += et * et; p3[1] += et * de; p3[2] += de * de;
         }
+        double w3[3] = {double(p3[0]), double(p3[1]), double(p3[2])};
         bsum<3>(w3, sm.red);
         ee = w3[0]; ed = w3[1]; dd = w3[2];
       }
@@ -587,7 +687,7 @@ struct Cta {
         m3[0] += g * x; m3[1] += x * h; m3[2] += x * x;
       }
       bsum<3>(m3, sm.red);
-      for (int i = threadIdx.x; i < N; i += NT) retract_block<To, Ti, R>(i, Y, eta, 1.0, Yc);
+      for (int i = threadIdx.x; i < N; i += NT) retract_block<To, Ti, R, To>(i, Y, eta, 1.0, Yc);
       __syncthreads();
       double fc, gc2, yc2;
       grad_at<To>(Yc, Gc, lamc, fc, gc2, yc2);
@@ -610,6 +710,17 @@ struct Cta {
       }
       if (Delta < 1e-12 * Delta_bar) break;
       if (bulk && (rejects >= 6 || Delta < 1e-7 * Delta_bar)) break;
+      if (bulk) {
+        // near the FP32 floor (||rgrad|| <= 1e-6 of the start) and f no longer improving beyond
+        // its own noise (reg) over STALL_W steps: hand over to the FP64-gradient polish.  This
+        // bounds the bulk work of the many small scenes of a batch; xm_solve keeps iterating
+        // to the bulk tolerance (its large scenes lean on the longer FP32 phase).
+        f_hist[n_hist % (STALL_W + 1)] = f;
+        ++n_hist;
+        if (n_hist > STALL_W && f_hist[(n_hist - 1 - STALL_W) % (STALL_W + 1)] - f < reg &&
+            sqrt(g2) <= 1e-6 * ref_g)
+          break;
+      }
     }
     f_cur = f;
     cur_g2 = g2;
@@ -641,33 +752,66 @@ struct Cta {
     __syncthreads();
   }
 
-  // w -= V c over the first m columns of V (c = V^T w), one pass of classical Gram-Schmidt
+  // The Lanczos basis is kept in FP32 (column stride NM): the Z products are FP32 sweeps, so
+  // FP32 orthogonality (~1e-7) matches their accuracy; the working vector lw, the recurrence
+  // coefficients, the Ritz values and the decision stay FP64.
+  __device__ float* Vf() const { return reinterpret_cast<float*>(V); }
+
+  // w -= V c over the first m columns of V (c = V^T w), one pass of classical Gram-Schmidt in
+  // FP32 arithmetic (FP64 w)
   __device__ void reorth(double* w, int m) {
     if (m <= 0) return;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int NMc = P->NM;
+    const float* Vb = Vf();
     for (int j = wid; j < m; j += NW) {
-      double s = 0.0;
-      const double* col = V + (size_t)j * NMc;
-      for (int e = lane; e < n; e += 32) s += col[e] * w[e];
-      s = warp_sum(s);
-      if (lane == 0) sm.cv[j] = s;
+      float sacc = 0.f;
+      const float* col = Vb + (size_t)j * NMc;
+      for (int e = lane; e < n; e += 32) sacc = fmaf(col[e], float(w[e]), sacc);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+      if (lane == 0) sm.cv[j] = double(sacc);
     }
     __syncthreads();
     for (int e = threadIdx.x; e < n; e += NT) {
-      double t = 0.0;
-      for (int j = 0; j < m; ++j) t += V[(size_t)j * NMc + e] * sm.cv[j];
-      w[e] -= t;
+      float t = 0.f;
+      for (int j = 0; j < m; ++j) t = fmaf(Vb[(size_t)j * NMc + e], float(sm.cv[j]), t);
+      w[e] -= double(t);
     }
     __syncthreads();
   }
 
+  // w = Z v for an FP32 basis vector v
+  __device__ void zmul_f(const float* v, double* w) {
+    stage<float, float, 1>(v, n, ldq, (float*)sm.xs);
+    sweep32<1>(tile, Q32, n, ldq, (const float*)sm.xs, (float*)sm.ws);
+    ++info.n_sweeps;
+    const float* ws = (const float*)sm.ws;
+    for (int i = threadIdx.x; i < N; i += NT) {
+      const double x0 = v[3 * i], x1 = v[3 * i + 1], x2 = v[3 * i + 2];
+      const double* L = lam + 9 * (size_t)i;
+      const double dreg = lam[(size_t)9 * N + i];
+      w[3 * i] = double(ws[3 * i]) - (L[0] * x0 + L[1] * x1 + L[2] * x2);
+      w[3 * i + 1] = double(ws[3 * i + 1]) - (L[3] * x0 + L[4] * x1 + L[5] * x2);
+      w[3 * i + 2] = double(ws[3 * i + 2]) - (L[6] * x0 + L[7] * x1 + L[8] * x2) + dreg * x2;
+    }
+    __syncthreads();
+  }
+
+  __device__ void certify(int r, int kcap_steps, double& lam_def, double& lam_max, double& lam_range) {
+    const unsigned long long tc0 = threadIdx.x == 0 ? gtimer() : 0ull;
+    certify_body(r, kcap_steps, lam_def, lam_max, lam_range);
+    if (threadIdx.x == 0) info.t_cert_ns += gtimer() - tc0;
+  }
+
   // Lanczos on Z restricted to range(Y)^perp (Thm. 1), as Solver::certify: deflation basis from
   // the Gram matrix, Rayleigh quotients of Z on range(Y), full reorthogonalisation (twice), Ritz
-  // values by bisection every 10 steps, Ritz vector of the smallest into lritz.
-  __device__ void certify(int r, int kcap_steps, double& lam_def, double& lam_max, double& lam_range) {
+  // values by multisection at K = 10, 20, 30, 45, 65, ... (about x1.45), Ritz vector of the
+  // smallest into lritz.
+  __device__ void certify_body(int r, int kcap_steps, double& lam_def, double& lam_max, double& lam_range) {
     const int NMc = P->NM;
     const int kmax = P->kmax;
+    float* Vb = Vf();
     gram_eig(r);
     // rotation: column j = E_j / sqrt(w_j) for the retained directions
     __shared__ int s_nd;
@@ -691,16 +835,18 @@ struct Cta {
       for (int j = 0; j < nd; ++j) {
         double t = 0.0;
         for (int a = 0; a < R; ++a) t += y64[(size_t)e * R + a] * rot[a * R + j];
-        V[(size_t)j * NMc + e] = t;
+        Vb[(size_t)j * NMc + e] = float(t);
       }
     __syncthreads();
     // Rayleigh quotients V_d^T Z V_d (nd x nd) -> smallest eigenvalue lam_range
     __shared__ double zr[XM_MAX_RANK * XM_MAX_RANK];
     for (int j = 0; j < nd; ++j) {
-      zmul(V + (size_t)j * NMc, lw);
+      zmul_f(Vb + (size_t)j * NMc, lw);
       for (int l = 0; l < nd; ++l) {
-        const double c = dot(V + (size_t)l * NMc, lw, n);
-        if (threadIdx.x == 0) zr[j * nd + l] = c;
+        double v[1] = {0.0};
+        for (int e = threadIdx.x; e < n; e += NT) v[0] += double(Vb[(size_t)l * NMc + e]) * lw[e];
+        bsum<1>(v, sm.red);
+        if (threadIdx.x == 0) zr[j * nd + l] = v[0];
       }
     }
     __syncthreads();
@@ -718,65 +864,65 @@ struct Cta {
     __syncthreads();
     lam_range = sm.small[300];
     // start vector: splitmix64 uniform(-1, 1) keyed by (seed, index), as xm_solve
-    double* v0 = V + (size_t)nd * NMc;
     for (int e = threadIdx.x; e < n; e += NT) {
       uint64_t z = P->o.seed + 0x9E3779B97F4A7C15ull * (uint64_t)(e + 1);
       z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
       z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
       z ^= z >> 31;
-      v0[e] = (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+      lw[e] = (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
     }
     __syncthreads();
-    reorth(v0, nd);
+    reorth(lw, nd);
     {
-      const double nrm = sqrt(dot(v0, v0, n));
+      const double nrm = sqrt(dot(lw, lw, n));
       const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
-      for (int e = threadIdx.x; e < n; e += NT) v0[e] *= inv;
+      float* v0 = Vb + (size_t)nd * NMc;
+      for (int e = threadIdx.x; e < n; e += NT) v0[e] = float(lw[e] * inv);
       __syncthreads();
     }
     int K = 0;
     double th_min = 0.0, th_max = 0.0;
     const int kcap = min(kcap_steps > 0 ? min(kcap_steps, kmax) : kmax, n - nd);
     __shared__ int s_conv;
+    int next_check = 10;
     for (int k = 0; k < kcap; ++k) {
-      double* vk = V + (size_t)(nd + k) * NMc;
-      const double* vkm1 = k > 0 ? V + (size_t)(nd + k - 1) * NMc : nullptr;
-      zmul(vk, lw);
-      const double a = dot(vk, lw, n);
+      const float* vk = Vb + (size_t)(nd + k) * NMc;
+      const float* vkm1 = k > 0 ? Vb + (size_t)(nd + k - 1) * NMc : nullptr;
+      zmul_f(vk, lw);
+      double av[1] = {0.0};
+      for (int e = threadIdx.x; e < n; e += NT) av[0] += double(vk[e]) * lw[e];
+      bsum<1>(av, sm.red);
+      const double a = av[0];
       const double b = k > 0 ? sm.hb[k - 1] : 0.0;
-      for (int e = threadIdx.x; e < n; e += NT) lw[e] -= a * vk[e] + (vkm1 ? b * vkm1[e] : 0.0);
+      for (int e = threadIdx.x; e < n; e += NT) lw[e] -= a * double(vk[e]) + (vkm1 ? b * double(vkm1[e]) : 0.0);
       __syncthreads();
       reorth(lw, nd + k + 1);
       reorth(lw, nd + k + 1);
       const double bn = sqrt(dot(lw, lw, n));
       const double inv = bn > 0.0 ? 1.0 / bn : 0.0;
-      double* vk1 = V + (size_t)(nd + k + 1) * NMc;
-      for (int e = threadIdx.x; e < n; e += NT) vk1[e] = lw[e] * inv;
+      float* vk1 = Vb + (size_t)(nd + k + 1) * NMc;
+      for (int e = threadIdx.x; e < n; e += NT) vk1[e] = float(lw[e] * inv);
       if (threadIdx.x == 0) { sm.ha[k] = a; sm.hb[k] = bn; }
       __syncthreads();
       ++info.n_lanczos;
       K = k + 1;
-      if ((K % 10) == 0 || K == kcap) {
+      if (K == next_check || K == kcap) {
+        next_check = max(next_check + 10, (next_check * 29) / 20);
+        tri_extremes(K, sm.ha, sm.hb, sm.b2, sm.cnt, sm.brk, th_min, th_max);
         if (threadIdx.x == 0) {
-          const double tmin = dev_tri_eig(K, sm.ha, sm.hb, 0);
-          const double tmax = dev_tri_eig(K, sm.ha, sm.hb, K - 1);
-          dev_tri_eigvec(K, sm.ha, sm.hb, tmin, sm.hs, sm.work, sm.piv);
+          dev_tri_eigvec(K, sm.ha, sm.hb, th_min, sm.hs, sm.work, sm.piv);
           const double res = fabs(sm.hb[K - 1] * sm.hs[K - 1]);
-          const double scale = fmax(fabs(tmax), fabs(tmin)) + 1e-300;
-          sm.small[301] = tmin;
-          sm.small[302] = tmax;
+          const double scale = fmax(fabs(th_max), fabs(th_min)) + 1e-300;
           s_conv = (res <= P->o.lanczos_tol * scale || sm.hb[K - 1] <= 1e-14 * scale || K == kcap) ? 1 : 0;
         }
         __syncthreads();
-        th_min = sm.small[301];
-        th_max = sm.small[302];
         if (s_conv) break;
       }
     }
     // Ritz vector of th_min
     for (int e = threadIdx.x; e < n; e += NT) {
       double t = 0.0;
-      for (int j = 0; j < K; ++j) t += V[(size_t)(nd + j) * NMc + e] * sm.hs[j];
+      for (int j = 0; j < K; ++j) t += double(Vb[(size_t)(nd + j) * NMc + e]) * sm.hs[j];
       lritz[e] = t;
     }
     __syncthreads();
@@ -931,7 +1077,9 @@ struct Cta {
           for (int i = threadIdx.x; i < N; i += NT) retract_block<double, double, R>(i, y64, xi, 0.0, yc64);
           __syncthreads();
           { double* t = y64; y64 = yc64; yc64 = t; }
+          const unsigned long long tp0 = threadIdx.x == 0 ? gtimer() : 0ull;
           rtr<double, float>(o.grad_tol_rel, o.max_polish, false);
+          if (threadIdx.x == 0) info.t_polish_ns += gtimer() - tp0;
           certify(r, 0, lam_def, lam_max, lam_range);
           const double regd = reg_dual();
           gap = f_cur - (lam[0] + lam[4] + lam[8] + regd);
@@ -1059,26 +1207,27 @@ __global__ void __launch_bounds__(NT, 1) k_batched(Params p) {
   }
 }
 
-// Autotuner probe: CTA j runs `reps` FP32 sweeps (r = 4) of scene j with rows-per-warp rpw and
-// records its clock cycles.
-template <int RPW>
+// Autotuner probe: persistent CTAs (one per SM, as the solver) each run `reps` FP32 sweeps
+// (r = 4) of their scenes with one tiling variant and record the clock cycles per scene.
+template <int RPW, int U>
 __global__ void __launch_bounds__(NT, 1) k_tune_sweep(const Desc* desc, const float* Q32, int S, int NM, int reps,
                                                      long long* cycles) {
   extern __shared__ __align__(16) char smem_base[];
-  const int j = blockIdx.x;
-  if (j >= S) return;
-  const Desc d = desc[j];
-  float* xs = reinterpret_cast<float*>(smem_base);
-  float* ws = xs + (size_t)NM * 4;
-  for (int e = threadIdx.x; e < d.ldq * 4; e += NT) xs[e] = e < d.n * 4 ? 1.0f / (1 + (e % 7)) : 0.0f;
-  __syncthreads();
-  const long long t0 = clock64();
-  for (int k = 0; k < reps; ++k) {
-    sweep32_t<4, RPW>(Q32 + d.q32, d.n, d.ldq, xs, ws);
+  for (int j = blockIdx.x; j < S; j += gridDim.x) {
+    const Desc d = desc[j];
+    float* xs = reinterpret_cast<float*>(smem_base);
+    float* ws = xs + (size_t)NM * 4;
+    for (int e = threadIdx.x; e < d.ldq * 4; e += NT) xs[e] = e < d.n * 4 ? 1.0f / (1 + (e % 7)) : 0.0f;
+    __syncthreads();
+    const long long t0 = clock64();
+    for (int k = 0; k < reps; ++k) {
+      sweep32_t<4, RPW, U>(Q32 + d.q32, d.n, d.ldq, xs, ws);
+      __syncthreads();
+    }
+    const long long t1 = clock64();
+    if (threadIdx.x == 0) cycles[j] = t1 - t0;
     __syncthreads();
   }
-  const long long t1 = clock64();
-  if (threadIdx.x == 0) cycles[j] = t1 - t0;
 }
 
 }  // namespace bat
@@ -1112,7 +1261,7 @@ struct xm_batch {
   double* spill = nullptr;
   xm_batch_info* out = nullptr;
   unsigned* queue = nullptr;
-  int rpw[xm::bat::NCLASS] = {1, 2, 2, 4};
+  int tile[xm::bat::NCLASS] = {1, 2, 2, 3};
   bool tuned = false;
   cudaStream_t stream = nullptr;
   cudaEvent_t ev = nullptr;
@@ -1221,47 +1370,55 @@ extern "C" xm_status xm_batch_free(xm_ctx* c, xm_batch* b) {
   return XM_OK;
 }
 
-extern "C" xm_status xm_batch_autotune(xm_ctx* c, xm_batch* b, int reps, int* rpw_out) {
+extern "C" xm_status xm_batch_autotune(xm_ctx* c, xm_batch* b, int reps, int* tile_out) {
   if (!c || !b) return set_error(XM_EINVAL, "xm_batch_autotune: NULL argument");
   if (reps < 1) reps = 1;
   XM_CUDA_TRY(cudaSetDevice(c->device));
   const int S = b->S;
   long long* dcyc = nullptr;
   XM_CUDA_TRY(cudaMalloc(&dcyc, sizeof(long long) * S));
-  const size_t smem = (size_t)b->NM * 4 * sizeof(float) * 2;
-  const int cand[3] = {1, 2, 4};
-  double tot[3][bat::NCLASS] = {};
+  // the solver's own shared-memory footprint, so that one CTA per SM runs, as in the solve
+  const size_t smem = std::max((size_t)b->NM * 4 * sizeof(float) * 2,
+                               bat::smem_bytes(b->NM, 4, std::max(10, std::min(400, b->n_max))));
+  const int grid = std::min(c->num_sms, S);
+  double tot[bat::NTILE][bat::NCLASS] = {};
   std::vector<long long> cyc(S);
   xm_status st = XM_OK;
-  for (int ci = 0; ci < 3 && st == XM_OK; ++ci) {
-    cudaError_t e;
-    if (cand[ci] == 1) {
-      cudaFuncSetAttribute(bat::k_tune_sweep<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      bat::k_tune_sweep<1><<<S, bat::NT, smem, b->stream>>>(b->desc, b->Q32, S, b->NM, reps, dcyc);
-    } else if (cand[ci] == 2) {
-      cudaFuncSetAttribute(bat::k_tune_sweep<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      bat::k_tune_sweep<2><<<S, bat::NT, smem, b->stream>>>(b->desc, b->Q32, S, b->NM, reps, dcyc);
-    } else {
-      cudaFuncSetAttribute(bat::k_tune_sweep<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      bat::k_tune_sweep<4><<<S, bat::NT, smem, b->stream>>>(b->desc, b->Q32, S, b->NM, reps, dcyc);
+  for (int v = 0; v < bat::NTILE && st == XM_OK; ++v) {
+    cudaError_t e = cudaSuccess;
+#define XB_TUNE(RP, UU)                                                                           \
+  e = cudaFuncSetAttribute(bat::k_tune_sweep<RP, UU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+  if (e == cudaSuccess) bat::k_tune_sweep<RP, UU><<<grid, bat::NT, smem, b->stream>>>(b->desc, b->Q32, S, b->NM, reps, dcyc);
+    switch (v) {
+      case 0: XB_TUNE(2, 4) break;
+      case 1: XB_TUNE(4, 1) break;
+      case 2: XB_TUNE(4, 2) break;
+      case 3: XB_TUNE(4, 4) break;
+      case 4: XB_TUNE(8, 1) break;
+      default: XB_TUNE(8, 2) break;
     }
-    e = cudaGetLastError();
+#undef XB_TUNE
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(cyc.data(), dcyc, sizeof(long long) * S, cudaMemcpyDeviceToHost, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) { st = set_error(XM_ECUDA, "xm_batch_autotune: %s", cudaGetErrorString(e)); break; }
-    for (int k = 0; k < S; ++k) tot[ci][bat::size_class(b->desc_h[k].n)] += (double)cyc[k];
+    for (int k = 0; k < S; ++k) tot[v][bat::size_class(b->desc_h[k].n)] += (double)cyc[k];
   }
   cudaFree(dcyc);
   if (st != XM_OK) return st;
   for (int cl = 0; cl < bat::NCLASS; ++cl) {
     int best = -1;
-    for (int ci = 0; ci < 3; ++ci)
-      if (tot[ci][cl] > 0 && (best < 0 || tot[ci][cl] < tot[best][cl])) best = ci;
-    if (best >= 0) b->rpw[cl] = cand[best];
+    for (int v = 0; v < bat::NTILE; ++v)
+      if (tot[v][cl] > 0 && (best < 0 || tot[v][cl] < tot[best][cl])) best = v;
+    if (best >= 0) b->tile[cl] = best;
   }
   b->tuned = true;
   if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
-  if (rpw_out) for (int cl = 0; cl < bat::NCLASS; ++cl) rpw_out[cl] = b->rpw[cl];
+  if (tile_out)
+    for (int cl = 0; cl < bat::NCLASS; ++cl) {
+      tile_out[2 * cl] = bat::tile_rpw(b->tile[cl]);
+      tile_out[2 * cl + 1] = bat::tile_u(b->tile[cl]);
+    }
   return XM_OK;
 }
 
@@ -1316,7 +1473,7 @@ extern "C" xm_status xm_solve_batched(xm_ctx* c, xm_batch* b, const xm_opts* opt
     p.R_out = R_out;
     p.s_out = s_out;
     p.out = b->out;
-    for (int cl = 0; cl < bat::NCLASS; ++cl) p.rpw[cl] = b->rpw[cl];
+    for (int cl = 0; cl < bat::NCLASS; ++cl) p.tile[cl] = b->tile[cl];
     p.o = o;
     p.mu = o.scale_reg;
     p.time_limit_ns = o.time_limit_s > 0 ? (unsigned long long)(o.time_limit_s * 1e9) : 0ull;

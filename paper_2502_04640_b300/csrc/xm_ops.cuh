@@ -197,20 +197,21 @@ __device__ __forceinline__ void zero_block(T* p, int i) {
 // cand = 1, to (sc->fc, gc2, yc2).
 // Camera i's share: Lambda_i (and dreg_i) into Lam, rgrad_i into G, W_i reset to zero;
 // returns (f_i, ||rgrad_i||^2, ||Y_i||^2) in v.
-template <typename T, int R>
+// C: per-camera arithmetic type (FP64 in the grid-wide kernels whatever the storage type; the
+// batched solver's FP32 bulk phase uses FP32).
+template <typename T, int R, typename C = double>
 __device__ __forceinline__ void grad_block(int i, int N, const T* __restrict__ Y, T* __restrict__ W,
                                            T* __restrict__ G, double* __restrict__ Lam, double mu,
                                            double (&v)[3]) {
-  using C = double;   // per-camera arithmetic in FP64 whatever the storage type
   C y[3][R], w[3][R], L[3][3], alpha;
   load_block<T, C, R>(Y, i, y);
   load_block<T, C, R>(W, i, w);
   zero_block<T, R>(W, i);
-  double fi = 0.0, gi = 0.0, yi = 0.0;
+  C fi = C(0), gi = C(0), yi = C(0);
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
-    for (int j = 0; j < R; ++j) fi += double(y[a][j]) * double(w[a][j]);   // tr(Y^T Q Y)
+    for (int j = 0; j < R; ++j) fi += y[a][j] * w[a][j];   // tr(Y^T Q Y)
   // App. D regulariser: f += mu (x_i - 1)^2, (Q + grad F) Y adds dreg_i * row 2 of Y_i
   C dreg = C(0);
   if (mu != 0.0 && i > 0) {
@@ -218,7 +219,7 @@ __device__ __forceinline__ void grad_block(int i, int N, const T* __restrict__ Y
 #pragma unroll
     for (int j = 0; j < R; ++j) x2 += y[2][j] * y[2][j];
     dreg = C(2) * C(mu) * (x2 - C(1));
-    fi += mu * double((x2 - C(1)) * (x2 - C(1)));
+    fi += C(mu) * (x2 - C(1)) * (x2 - C(1));
 #pragma unroll
     for (int j = 0; j < R; ++j) w[2][j] += dreg * y[2][j];
   }
@@ -230,8 +231,8 @@ __device__ __forceinline__ void grad_block(int i, int N, const T* __restrict__ Y
     for (int j = 0; j < R; ++j) {
       C ly = L[a][0] * y[0][j] + L[a][1] * y[1][j] + L[a][2] * y[2][j];
       g[a][j] = C(2) * (w[a][j] - ly);
-      gi += double(g[a][j]) * double(g[a][j]);
-      yi += double(y[a][j]) * double(y[a][j]);
+      gi += g[a][j] * g[a][j];
+      yi += y[a][j] * y[a][j];
     }
   store_block<T, C, R>(G, i, g);
 #pragma unroll
@@ -239,7 +240,7 @@ __device__ __forceinline__ void grad_block(int i, int N, const T* __restrict__ Y
 #pragma unroll
     for (int b = 0; b < 3; ++b) Lam[(size_t)9 * i + 3 * a + b] = double(L[a][b]);
   Lam[(size_t)9 * N + i] = double(dreg);
-  v[0] = fi; v[1] = gi; v[2] = yi;
+  v[0] = double(fi); v[1] = double(gi); v[2] = double(yi);
 }
 
 template <typename T, int R>
@@ -286,11 +287,10 @@ k_tcg_init(int n_rows, const To* __restrict__ G, Ti* eta, Ti* Heta, Ti* r, Ti* d
 // accumulating sweep); returns <d_i, Hd_i>.
 // With App. D's regulariser the Euclidean Hessian adds, on row 2 of every non-anchor block,
 // dreg_i d_i + 4 mu <y_i, d_i> y_i (row-2 vectors): the derivative of dreg_i y_i along d.
-template <typename T, int R>
+template <typename T, int R, typename C = double>
 __device__ __forceinline__ double hvp_block(int i, int N, const T* __restrict__ Y, T* __restrict__ Wd,
                                             const T* __restrict__ delta, T* __restrict__ Hd,
                                             const double* __restrict__ Lam, double mu) {
-  using C = double;   // per-camera arithmetic in FP64 whatever the storage type
   C y[3][R], w[3][R], d[3][R], L[3][3];
   load_block<T, C, R>(Y, i, y);
   load_block<T, C, R>(Wd, i, w);
@@ -316,16 +316,16 @@ __device__ __forceinline__ double hvp_block(int i, int N, const T* __restrict__ 
       A[a][j] = C(2) * (w[a][j] - (L[a][0] * d[0][j] + L[a][1] * d[1][j] + L[a][2] * d[2][j]));
   C S[3][3], alpha;
   dual_block<C, R>(A, y, i == 0, S, alpha);
-  double kap = 0.0;
+  C kap = C(0);
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
     for (int j = 0; j < R; ++j) {
       A[a][j] -= S[a][0] * y[0][j] + S[a][1] * y[1][j] + S[a][2] * y[2][j];
-      kap += double(d[a][j]) * double(A[a][j]);
+      kap += d[a][j] * A[a][j];
     }
   store_block<T, C, R>(Hd, i, A);
-  return kap;
+  return double(kap);
 }
 
 // Hd = 2 P_Y(Wd - Lambda d); kappa = <d, Hd>; then decide the step (alpha, or tau to the
@@ -467,10 +467,9 @@ k_model_terms(int n_rows, const To* __restrict__ G, const Ti* __restrict__ eta,
 // ------------------------------------------------------------------ retraction
 // Metric projection onto {sqrt(a) * (3 x r with orthonormal rows)}: A = Y_i + s Xi_i,
 // polar(A) = (A A^T)^{-1/2} A, scale = (sum of singular values) / 3 (anchor: 1).
-template <typename To, typename Ti, int R>
+template <typename To, typename Ti, int R, typename C = double>
 __device__ __forceinline__ void retract_block(int i, const To* __restrict__ Y, const Ti* __restrict__ Xi,
                                               double s, To* __restrict__ Yo) {
-  using C = double;
   C A[3][R];
 #pragma unroll
   for (int a = 0; a < 3; ++a)

@@ -70,7 +70,8 @@ class XmBatchInfo(ctypes.Structure):
                 ("lambda_max", ctypes.c_double), ("dual", ctypes.c_double),
                 ("rho_hat", ctypes.c_double), ("eta", ctypes.c_double),
                 ("eta_robust", ctypes.c_double), ("t_begin_ns", ctypes.c_ulonglong),
-                ("t_end_ns", ctypes.c_ulonglong), ("N", ctypes.c_int), ("status", ctypes.c_int),
+                ("t_end_ns", ctypes.c_ulonglong), ("t_cert_ns", ctypes.c_ulonglong),
+                ("t_polish_ns", ctypes.c_ulonglong), ("N", ctypes.c_int), ("status", ctypes.c_int),
                 ("rank", ctypes.c_int), ("certified", ctypes.c_int), ("n_sweeps", ctypes.c_int),
                 ("n_sweeps_fp64", ctypes.c_int), ("n_outer", ctypes.c_int), ("n_tcg", ctypes.c_int),
                 ("n_lanczos", ctypes.c_int), ("n_escapes", ctypes.c_int)]
@@ -359,10 +360,10 @@ def xm_batch_create(ctx: Context, qmats) -> Batch:
 
 
 def xm_batch_autotune(b: Batch, reps: int = 8):
-    """Rows per warp chosen for the four scene-size classes."""
-    out = (ctypes.c_int * 4)()
+    """(rows per warp, column chunks per step) chosen for the four scene-size classes."""
+    out = (ctypes.c_int * 8)()
     _check(lib().xm_batch_autotune(b.ctx.h, b.h, reps, out))
-    return list(out)
+    return [(out[2 * k], out[2 * k + 1]) for k in range(4)]
 
 
 def xm_solve_batched(b: Batch, opts: XmOpts | None = None, R=None, s=None, allow_notcert: bool = True):

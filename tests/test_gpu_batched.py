@@ -72,8 +72,8 @@ def test_batched_matches_single_scene_solver_and_is_deterministic(C):
     scs = _batch([30, 55, 14, 80], seed=800)
     qs, b = _build(C, scs)
     opts = xm.xm_default_opts(time_limit_s=30.0)
-    rpw = xm.xm_batch_autotune(b, reps=4)
-    assert all(x in (1, 2, 4) for x in rpw)
+    tiles = xm.xm_batch_autotune(b, reps=4)
+    assert all(t in ((2, 4), (4, 1), (4, 2), (4, 4), (8, 1), (8, 2)) for t in tiles)
     out = xm.xm_solve_batched(b, opts, allow_notcert=False)
     out2 = xm.xm_solve_batched(b, opts, R=out["R"].clone(), s=out["s"].clone(), allow_notcert=False)
     out3 = xm.xm_solve_batched(b, opts, R=out2["R"], s=out2["s"], allow_notcert=False)   # graph replay
