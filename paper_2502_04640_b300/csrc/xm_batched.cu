@@ -758,24 +758,29 @@ struct Cta {
   __device__ float* Vf() const { return reinterpret_cast<float*>(V); }
 
   // w -= V c over the first m columns of V (c = V^T w), one pass of classical Gram-Schmidt in
-  // FP32 arithmetic (FP64 w)
+  // FP32 arithmetic (FP64 w).  w and c are converted once per pass (FP32 copies in shared
+  // memory): float <-> double conversions share B300's narrow FP64 pipe.
   __device__ void reorth(double* w, int m) {
     if (m <= 0) return;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int NMc = P->NM;
     const float* Vb = Vf();
+    float* wf = (float*)sm.ws;             // free during the certificate between Z products
+    float* cf = (float*)sm.cv;
+    for (int e = threadIdx.x; e < n; e += NT) wf[e] = float(w[e]);
+    __syncthreads();
     for (int j = wid; j < m; j += NW) {
       float sacc = 0.f;
       const float* col = Vb + (size_t)j * NMc;
-      for (int e = lane; e < n; e += 32) sacc = fmaf(col[e], float(w[e]), sacc);
+      for (int e = lane; e < n; e += 32) sacc = fmaf(col[e], wf[e], sacc);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
-      if (lane == 0) sm.cv[j] = double(sacc);
+      if (lane == 0) cf[j] = sacc;
     }
     __syncthreads();
     for (int e = threadIdx.x; e < n; e += NT) {
       float t = 0.f;
-      for (int j = 0; j < m; ++j) t = fmaf(Vb[(size_t)j * NMc + e], float(sm.cv[j]), t);
+      for (int j = 0; j < m; ++j) t = fmaf(Vb[(size_t)j * NMc + e], cf[j], t);
       w[e] -= double(t);
     }
     __syncthreads();
@@ -919,11 +924,14 @@ struct Cta {
         if (s_conv) break;
       }
     }
-    // Ritz vector of th_min
+    // Ritz vector of th_min (FP32 combination of the FP32 basis)
+    float* hsf = (float*)sm.cv;
+    for (int j = threadIdx.x; j < K; j += NT) hsf[j] = float(sm.hs[j]);
+    __syncthreads();
     for (int e = threadIdx.x; e < n; e += NT) {
-      double t = 0.0;
-      for (int j = 0; j < K; ++j) t += double(Vb[(size_t)(nd + j) * NMc + e]) * sm.hs[j];
-      lritz[e] = t;
+      float t = 0.f;
+      for (int j = 0; j < K; ++j) t = fmaf(Vb[(size_t)(nd + j) * NMc + e], hsf[j], t);
+      lritz[e] = double(t);
     }
     __syncthreads();
     lam_def = th_min;
