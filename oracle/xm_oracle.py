@@ -691,6 +691,23 @@ def anchored_blocks_grad(Y, dL_dG):
     return dY.reshape(Y.shape)
 
 
+def gauge_basis(Y):
+    """Orthonormal basis (columns, vectorised n*r) of the gauge directions {Y Omega : Omega skew}:
+    f(Y O) = f(Y) for every orthogonal O, so the Riemannian Hessian vanishes on them at a
+    critical point and the loss of G_i = Y_0 Y_i^T is constant along them."""
+    n, r = Y.shape
+    cols = []
+    for a in range(r):
+        for b in range(a + 1, r):
+            Om = np.zeros((r, r)); Om[a, b] = 1.0; Om[b, a] = -1.0
+            cols.append((Y @ Om).ravel())
+    if not cols:
+        return np.zeros((n * r, 0))
+    A = np.array(cols).T
+    U, sv, _ = np.linalg.svd(A, full_matrices=False)
+    return U[:, sv > 1e-10 * max(sv.max(), 1e-300)]
+
+
 def conjugate_gradient(apply, b, tol=1e-14, maxit=10000):
     """Plain CG for a symmetric positive semi-definite operator and a consistent right side."""
     x = np.zeros_like(b)
@@ -740,8 +757,17 @@ def adjoint(N, M, cam, lmk, ukp, w, Y, dL_dG, Q=None, tol=1e-14, mu=0.0):
     cam, lmk, ukp, w = _validated(N, M, cam, lmk, ukp, w)
     Q = build_Q_schur(N, M, cam, lmk, ukp, w) if Q is None else Q
     L = lambdas(Y, qeff(Q, Y, mu))
-    gL = proj_tangent(Y, anchored_blocks_grad(Y, dL_dG))
-    lam = conjugate_gradient(lambda v: hess(Q, Y, v, L, mu), gL, tol=tol)
+    # CG on the Hessian restricted to the complement of the gauge directions (its null space at a
+    # critical point; dL/dY is orthogonal to them, and a gauge part of lambda cancels in dL/dQ)
+    Ng = gauge_basis(Y)
+    shp = Y.shape
+
+    def deflate(v):
+        x = v.ravel()
+        return (x - Ng @ (Ng.T @ x)).reshape(shp)
+
+    gL = deflate(proj_tangent(Y, anchored_blocks_grad(Y, dL_dG)))
+    lam = conjugate_gradient(lambda v: deflate(hess(Q, Y, deflate(v), L, mu)), gL, tol=tol)
     r = Y.shape[1]
     e = optimal_residuals(N, M, cam, lmk, ukp, w, np.hstack([Y, lam]))
     eY, eL = e[:, :r], e[:, r:]

@@ -45,3 +45,22 @@ def test_optimal_residuals_reproduce_the_objective():
     U = np.random.default_rng(32).standard_normal((3 * sc.N, 5))
     e = O.optimal_residuals(sc.N, sc.M, sc.cam, sc.lmk, sc.ukp, sc.w, U)
     assert abs(np.sum(sc.w[:, None] * e * e) - O.cost(Q, U)) <= 1e-10 * O.cost(Q, U)
+
+
+def test_adjoint_ignores_gauge_directions():
+    """The loss of G_i = Y_0 Y_i^T is constant along Y -> Y O; the adjoint's lambda has no part
+    along the gauge directions Y Omega, and the outputs do not change when the point moves along
+    the orbit (Y -> Y O, a different representative of the same X)."""
+    sc = scenes.circle_scene(8, 80, 3, 0.03, seed=33, w_range=(0.5, 1.5))
+    Q = O.build_Q_schur(sc.N, sc.M, sc.cam, sc.lmk, sc.ukp, sc.w)
+    res = O.solve(Q, r0=4, grad_tol_rel=1e-13)
+    assert res.certified
+    C = np.random.default_rng(34).standard_normal((sc.N, 3, 3)); C[0] = 0.0
+    d_u, d_w, lam = O.adjoint(sc.N, sc.M, sc.cam, sc.lmk, sc.ukp, sc.w, res.Y, C, Q=Q)
+    Ng = O.gauge_basis(res.Y)
+    assert np.abs(Ng.T @ lam.ravel()).max() <= 1e-10 * np.abs(lam).max()
+    r = res.Y.shape[1]
+    Oq, _ = np.linalg.qr(np.random.default_rng(35).standard_normal((r, r)))
+    d_u2, d_w2, _ = O.adjoint(sc.N, sc.M, sc.cam, sc.lmk, sc.ukp, sc.w, res.Y @ Oq, C, Q=Q)
+    assert np.abs(d_u2 - d_u).max() <= 1e-8 * np.abs(d_u).max()
+    assert np.abs(d_w2 - d_w).max() <= 1e-8 * np.abs(d_w).max()
