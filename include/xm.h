@@ -85,6 +85,11 @@ typedef struct xm_opts {
                               non-anchor block, paper's 1-based indexing); Z, the dual value
                               and the suboptimality bounds follow App. D / App. E.  0 (the
                               default): the plain objective of Eq. 17.  Must be >= 0.        */
+  int precond;             /* tCG preconditioner: 0 (default) plain Steihaug-Toint tCG
+                              (Sec. 3.2); 1: block Jacobi z_i = P(B_i^-1 r_i), B_i = 2 Q_ii
+                              (eigenvalues clamped at 1e-6 of the largest), trust region in the
+                              B-norm (halves the sweeps on the 1934-camera workload, slower on
+                              the 10155-camera one)                                            */
 } xm_opts;
 
 typedef struct xm_info {

@@ -70,7 +70,7 @@ void xm_default_opts(xm_opts* o) {
   o->r0 = 4;
   o->r_max = XM_MAX_RANK;
   o->prec = XM_FP32_BULK;
-  o->grad_tol_rel = 1e-9;
+  o->grad_tol_rel = 1e-11;
   o->bulk_tol_rel = 1e-9;
   o->cert_tau_rel = 1e-6;
   o->max_outer = 300;
@@ -83,6 +83,7 @@ void xm_default_opts(xm_opts* o) {
   o->verbose = 0;
   o->init_jitter = 0.1;
   o->scale_reg = 0.0;
+  o->precond = 0;
 }
 
 xm_status xm_create(xm_ctx** out, int device, void* stream) {

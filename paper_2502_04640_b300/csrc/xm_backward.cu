@@ -142,13 +142,6 @@ k_cg_epi(int N, const T* __restrict__ Y, T* __restrict__ Wd, const T* __restrict
 }
 
 // ---- block-Jacobi preconditioner of the Riemannian Hessian
-// Entry (r, c) of Q from the packed FP64 tiles (upper-triangle tiles, halved diagonal).
-__device__ __forceinline__ double q_entry(const double* __restrict__ q64, int nt, int r, int c) {
-  if (r > c) { const int t = r; r = c; c = t; }
-  const int I = r / TILE, J = c / TILE, a = r % TILE, b = c % TILE;
-  const double v = q64[tile_index(nt, I, J) * TILE * TILE + (int64_t)a * TILE + b];
-  return (I == J && a == b) ? 2.0 * v : v;
-}
 
 // Per camera, Minv_i = (2 Z_ii)^-1 with Z_ii = Q_ii + diag(0, 0, dreg_i) - Lambda_i, the 3 x 3
 // diagonal block of the certificate matrix (positive semi-definite at a certified optimum),

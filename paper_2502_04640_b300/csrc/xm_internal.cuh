@@ -163,6 +163,14 @@ __device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src_gmem, u
 __device__ __forceinline__ void named_bar_sync(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
+// Entry (r, c) of Q from the packed FP64 tiles (upper-triangle tiles, halved diagonal).
+__device__ __forceinline__ double q_entry(const double* __restrict__ q64, int nt, int r, int c) {
+  if (r > c) { const int t = r; r = c; c = t; }
+  const int I = r / TILE, J = c / TILE, a = r % TILE, b = c % TILE;
+  const double v = q64[tile_index(nt, I, J) * TILE * TILE + (int64_t)a * TILE + b];
+  return (I == J && a == b) ? 2.0 * v : v;
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll

@@ -259,28 +259,81 @@ k_grad_epi(int N, const T* __restrict__ Y, T* __restrict__ W, T* __restrict__ G,
 }
 
 // ------------------------------------------------------------------ truncated CG
-// Steihaug-Toint tCG (Absil et al. 2008, Alg. 11) on the model with Hessian 2 P_Y(Q d - Lambda d).
+// Steihaug-Toint tCG (Absil et al. 2008, Alg. 11) on the model with Hessian 2 P_Y(Q d - Lambda d),
+// optionally preconditioned (Conn, Gould and Toint's form): z = M^-1 r with the block-Jacobi
+// preconditioner z_i = P_{Y_i}(Minv_i r_i), Minv_i = (2 (Q_ii + eps I))^-1; the trust region is
+// then measured in the M-norm, whose <eta,M eta>, <eta,M delta>, <delta,M delta> follow by
+// recurrences (no product with M).  Minv == nullptr: z = r, the plain method.
+
+template <typename C, int R>
+__device__ __forceinline__ void tcg_precond(int i, const C (&y)[3][R], const C (&r)[3][R],
+                                            const double* __restrict__ Minv, C (&z)[3][R]) {
+  if (!Minv) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int j = 0; j < R; ++j) z[a][j] = r[a][j];
+    return;
+  }
+  C M[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) M[a][b] = C(Minv[(size_t)9 * i + 3 * a + b]);
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int j = 0; j < R; ++j) z[a][j] = M[a][0] * r[0][j] + M[a][1] * r[1][j] + M[a][2] * r[2][j];
+  C S[3][3], al;
+  dual_block<C, R>(z, y, i == 0, S, al);
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int j = 0; j < R; ++j) z[a][j] -= S[a][0] * y[0][j] + S[a][1] * y[1][j] + S[a][2] * y[2][j];
+}
+
+// eta = Heta = 0, r = G, z = M^-1 r, delta = -z; <r, r>, <r, z>
 template <typename To, typename Ti, int R>
 __global__ void __launch_bounds__(CAM_THREADS)
-k_tcg_init(int n_rows, const To* __restrict__ G, Ti* eta, Ti* Heta, Ti* r, Ti* delta, Scal* sc,
-           double g2, double Delta, int max_iters, double theta, double kappa_tol) {
-  const size_t total = (size_t)n_rows * R;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
-       e += (size_t)gridDim.x * blockDim.x) {
-    const Ti g = Ti(G[e]);
-    eta[e] = Ti(0); Heta[e] = Ti(0); r[e] = g; delta[e] = -g;
+k_tcg_init(int N, const Ti* __restrict__ Y, const To* __restrict__ G, Ti* eta, Ti* Heta, Ti* r, Ti* z,
+           Ti* delta, const double* __restrict__ Minv, Scal* sc, double Delta, int max_iters,
+           double theta, double kappa_tol, double* partials, unsigned* counter) {
+  using C = double;
+  double v[2] = {0.0, 0.0};
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) {
+    C y[3][R], rr[3][R], zz[3][R], zero[3][R];
+    load_block<Ti, C, R>(Y, i, y);
+    load_block<To, C, R>(G, i, rr);
+    tcg_precond<C, R>(i, y, rr, Minv, zz);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        v[0] += rr[a][j] * rr[a][j];
+        v[1] += rr[a][j] * zz[a][j];
+        zero[a][j] = C(0);
+      }
+    store_block<Ti, C, R>(r, i, rr);
+    store_block<Ti, C, R>(z, i, zz);
+    store_block<Ti, C, R>(eta, i, zero);
+    store_block<Ti, C, R>(Heta, i, zero);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int j = 0; j < R; ++j) zz[a][j] = -zz[a][j];
+    store_block<Ti, C, R>(delta, i, zz);
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    // g2 = ||grad||^2 of the current point, passed by the host (after an accepted step the
-    // device holds it in the candidate slot, not in sc->g2)
+  grid_reduce<2>(v, partials, counter, [&](double* t) {
     sc->Delta = Delta;
-    sc->rr = g2;
-    sc->r0 = sqrt(g2);
-    sc->ee = 0.0; sc->ed = 0.0; sc->dd = g2;
-    sc->done = g2 > 0.0 ? 0 : 1;
+    sc->rr = t[0];
+    sc->rz = t[1];
+    sc->r0 = sqrt(t[0]);
+    sc->ee = 0.0; sc->ed = 0.0; sc->dd = t[1];
+    sc->done = (t[0] > 0.0 && t[1] > 0.0) ? 0 : 1;
     sc->stop_after = 0; sc->iters = 0; sc->max_iters = max_iters; sc->reason = 0;
     sc->theta = theta; sc->kappa_tol = kappa_tol;
-  }
+  });
 }
 
 // Hd_i = 2 P_{Y_i}(Wd_i - Lambda_i d_i) for camera i (Wd_i is reset to zero for the next
@@ -343,7 +396,7 @@ k_hvp_epi(int N, const T* __restrict__ Y, T* __restrict__ Wd, const T* __restric
     const double kap = t[0];
     sc->kappa = kap;
     const double D2 = sc->Delta * sc->Delta;
-    const double a = kap > 0.0 ? sc->rr / kap : 0.0;
+    const double a = kap > 0.0 ? sc->rz / kap : 0.0;
     if (!(kap > 0.0) || sc->ee + 2.0 * a * sc->ed + a * a * sc->dd >= D2) {
       const double disc = sc->ed * sc->ed + sc->dd * (D2 - sc->ee);
       sc->alpha = (-sc->ed + sqrt(disc > 0.0 ? disc : 0.0)) / sc->dd;
@@ -355,16 +408,18 @@ k_hvp_epi(int N, const T* __restrict__ Y, T* __restrict__ Wd, const T* __restric
   });
 }
 
-// eta += alpha d, Heta += alpha Hd, r += alpha Hd (re-projected); residual test, beta.
+// eta += alpha d, Heta += alpha Hd, r += alpha Hd (re-projected), z = M^-1 r; residual test on
+// ||r||, beta = <r, z>' / <r, z>; M-norm recurrences for <eta,M eta>, <eta,M d>, <d,M d>.
 template <typename T, int R>
 __global__ void __launch_bounds__(CAM_THREADS)
-k_tcg_update(int N, const T* __restrict__ Y, T* eta, T* Heta, T* r, const T* __restrict__ delta,
-             const T* __restrict__ Hd, Scal* sc, double* partials, unsigned* counter) {
+k_tcg_update(int N, const T* __restrict__ Y, T* eta, T* Heta, T* r, T* z, const T* __restrict__ delta,
+             const T* __restrict__ Hd, const double* __restrict__ Minv, Scal* sc, double* partials,
+             unsigned* counter) {
   if (sc->done) return;
   using C = double;   // per-camera arithmetic in FP64 whatever the storage type
   const C alpha = C(sc->alpha);
   const bool stop = sc->stop_after != 0;
-  double v[1] = {0.0};
+  double v[2] = {0.0, 0.0};
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < N) {
     C e[3][R], he[3][R], d[3][R], hd[3][R];
@@ -382,7 +437,7 @@ k_tcg_update(int N, const T* __restrict__ Y, T* eta, T* Heta, T* r, const T* __r
     store_block<T, C, R>(eta, i, e);
     store_block<T, C, R>(Heta, i, he);
     if (!stop) {
-      C rr[3][R], y[3][R];
+      C rr[3][R], y[3][R], zz[3][R];
       load_block<T, C, R>(r, i, rr);
       load_block<T, C, R>(Y, i, y);
 #pragma unroll
@@ -391,60 +446,51 @@ k_tcg_update(int N, const T* __restrict__ Y, T* eta, T* Heta, T* r, const T* __r
         for (int j = 0; j < R; ++j) rr[a][j] += alpha * hd[a][j];
       C S[3][3], al;
       dual_block<C, R>(rr, y, i == 0, S, al);   // re-project r onto the tangent space
-      double s = 0.0;
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int j = 0; j < R; ++j) rr[a][j] -= S[a][0] * y[0][j] + S[a][1] * y[1][j] + S[a][2] * y[2][j];
+      tcg_precond<C, R>(i, y, rr, Minv, zz);
 #pragma unroll
       for (int a = 0; a < 3; ++a)
 #pragma unroll
         for (int j = 0; j < R; ++j) {
-          rr[a][j] -= S[a][0] * y[0][j] + S[a][1] * y[1][j] + S[a][2] * y[2][j];
-          s += double(rr[a][j]) * double(rr[a][j]);
+          v[0] += double(rr[a][j]) * double(rr[a][j]);
+          v[1] += double(rr[a][j]) * double(zz[a][j]);
         }
       store_block<T, C, R>(r, i, rr);
-      v[0] = s;
+      store_block<T, C, R>(z, i, zz);
     }
   }
-  grid_reduce<1>(v, partials, counter, [&](double* t) {
+  grid_reduce<2>(v, partials, counter, [&](double* t) {
     sc->iters += 1;
+    const double a = sc->alpha;
+    sc->ee = sc->ee + 2.0 * a * sc->ed + a * a * sc->dd;   // <eta, M eta> after the step
     if (stop) { sc->done = 1; return; }
-    const double rr_new = t[0];
+    const double rr_new = t[0], rz_new = t[1];
     const double rn = sqrt(rr_new);
     const double thr = sc->r0 * fmin(pow(sc->r0, sc->theta), sc->kappa_tol);
     if (rn <= thr) { sc->done = 1; sc->reason = 3; return; }
     if (sc->iters >= sc->max_iters) { sc->done = 1; sc->reason = 4; return; }
-    sc->beta = rr_new / sc->rr;
+    if (!(rz_new > 0.0)) { sc->done = 1; sc->reason = 5; return; }
+    const double beta = rz_new / sc->rz;
+    sc->beta = beta;
+    sc->ed = beta * (sc->ed + a * sc->dd);
+    sc->dd = rz_new + beta * beta * sc->dd;
+    sc->rz = rz_new;
     sc->rr = rr_new;
   });
 }
 
-// d = -r + beta d; recompute <eta,eta>, <eta,d>, <d,d>.
+// delta = -z + beta delta
 template <typename T, int R>
 __global__ void __launch_bounds__(CAM_THREADS)
-k_tcg_dir(int N, const T* __restrict__ eta, const T* __restrict__ r, T* delta, Scal* sc,
-          double* partials, unsigned* counter) {
+k_tcg_dir(int N, const T* __restrict__ z, T* delta, const Scal* sc) {
   if (sc->done) return;
-  using C = double;   // per-camera arithmetic in FP64 whatever the storage type
-  const C beta = C(sc->beta);
-  double v[3] = {0.0, 0.0, 0.0};
+  const double beta = sc->beta;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < N) {
-    C e[3][R], rr[3][R], d[3][R];
-    load_block<T, C, R>(eta, i, e);
-    load_block<T, C, R>(r, i, rr);
-    load_block<T, C, R>(delta, i, d);
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int j = 0; j < R; ++j) {
-        d[a][j] = -rr[a][j] + beta * d[a][j];
-        v[0] += double(e[a][j]) * double(e[a][j]);
-        v[1] += double(e[a][j]) * double(d[a][j]);
-        v[2] += double(d[a][j]) * double(d[a][j]);
-      }
-    store_block<T, C, R>(delta, i, d);
-  }
-  grid_reduce<3>(v, partials, counter, [&](double* t) {
-    sc->ee = t[0]; sc->ed = t[1]; sc->dd = t[2];
-  });
+  if (i >= N) return;
+  for (int e = 3 * i * R; e < 3 * (i + 1) * R; ++e) delta[e] = T(-double(z[e]) + beta * double(delta[e]));
 }
 
 // model terms <grad, eta>, <eta, Heta>, ||eta||^2 after tCG

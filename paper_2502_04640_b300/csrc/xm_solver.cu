@@ -147,6 +147,50 @@ static void tri_eigvec(int k, const double* a, const double* b, double th, std::
 }
 
 // ------------------------------------------------------------------ the solver
+// Block-Jacobi preconditioner of the tCG, per camera: B_i = 2 Q_ii and Minv_i = B_i^-1 with the
+// eigenvalues of Q_ii (positive semidefinite) clamped below at 1e-6 of the largest; N x 9 each.
+__global__ void k_tcg_precond_blocks(int N, const double* __restrict__ q64, int nt, double* __restrict__ Minv,
+                                     double* __restrict__ B) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double A[3][3], V[3][3], d[3];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) A[a][b] = q_entry(q64, nt, 3 * i + a, 3 * i + b);
+  jacobi3<double>(A, V, d);
+  const double dmax = fmax(d[0], fmax(d[1], d[2]));
+  double e[3];
+  for (int k = 0; k < 3; ++k) e[k] = dmax > 0.0 ? fmax(d[k], 1e-6 * dmax) : 1.0;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      double mi = 0.0, bb = 0.0;
+      for (int k = 0; k < 3; ++k) {
+        mi += V[a][k] * V[b][k] / (2.0 * e[k]);
+        bb += V[a][k] * V[b][k] * (2.0 * e[k]);
+      }
+      Minv[(size_t)9 * i + 3 * a + b] = mi;
+      B[(size_t)9 * i + 3 * a + b] = bb;
+    }
+}
+
+// sc->dot = sum_i <Y_i, B_i Y_i> (the preconditioner's norm of the iterate, the trust region's scale)
+template <typename T, int R>
+__global__ void __launch_bounds__(CAM_THREADS)
+k_bnorm(int N, const T* __restrict__ Y, const double* __restrict__ B, Scal* sc, double* partials,
+        unsigned* counter) {
+  double v[1] = {0.0};
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) {
+    double y[3][R];
+    load_block<T, double, R>(Y, i, y);
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        const double m = B[(size_t)9 * i + 3 * a + b];
+        for (int j = 0; j < R; ++j) v[0] += y[a][j] * m * y[b][j];
+      }
+  }
+  grid_reduce<1>(v, partials, counter, [&](double* t) { sc->dot = t[0]; });
+}
+
 struct Solver {
   xm_ctx* ctx;
   const DeviceQ& q;
@@ -160,6 +204,8 @@ struct Solver {
        *bD = nullptr, *bHd = nullptr, *bWd = nullptr, *bY64 = nullptr, *bXi = nullptr,
        *bYh = nullptr;
   double *Lam = nullptr, *Lamc = nullptr;
+  double *pcMinv = nullptr, *pcB = nullptr;   // tCG preconditioner blocks (N x 9), or null
+  void* bZ = nullptr;                         // tCG preconditioned residual
   Scal* d_sc = nullptr;
   Scal* h_sc = nullptr;
   double* d_small = nullptr;   // gram / rotation / O0 / scalar scratch (256 doubles)
@@ -186,7 +232,8 @@ struct Solver {
   }
   ~Solver() {
     void* bufs[] = {bY, bYc, bW, bWc, bG, bGc, bYin, bEta, bHeta, bR, bD, bHd, bWd, bY64, bXi, bYh,
-                    Lam, Lamc, d_sc, d_small, V, lw, lz, lalpha, lbeta, lc, lnrm, lritz, lv32, lW32};
+                    bZ, Lam, Lamc, pcMinv, pcB, d_sc, d_small, V, lw, lz, lalpha, lbeta, lc, lnrm,
+                    lritz, lv32, lW32};
     for (void* p : bufs) if (p) cudaFree(p);
     if (h_sc) cudaFreeHost(h_sc);
     if (ev0) cudaEventDestroy(ev0);
@@ -195,7 +242,7 @@ struct Solver {
 
   xm_status alloc() {
     void** vecs[] = {&bY, &bYc, &bW, &bWc, &bG, &bGc, &bYin, &bEta, &bHeta, &bR, &bD, &bHd, &bWd,
-                     &bY64, &bXi, &bYh};
+                     &bY64, &bXi, &bYh, &bZ};
     for (void** p : vecs) {
       XM_CUDA_TRY(cudaMalloc(p, vec_bytes));
       XM_CUDA_TRY(cudaMemsetAsync(*p, 0, vec_bytes, st));
@@ -213,13 +260,20 @@ struct Solver {
     XM_CUDA_TRY(cudaEventCreate(&ev0));
     XM_CUDA_TRY(cudaEventCreate(&ev1));
     XM_TRY(ensure_partials(ctx, (size_t)std::max(nb_cam, 1024) * 64));
+    if (o.precond) {
+      XM_CUDA_TRY(cudaMalloc(&pcMinv, sizeof(double) * 9 * (size_t)N));
+      XM_CUDA_TRY(cudaMalloc(&pcB, sizeof(double) * 9 * (size_t)N));
+      k_tcg_precond_blocks<<<nb_cam, CAM_THREADS, 0, st>>>(N, q.q64, q.nt, pcMinv, pcB);
+      ++launches;
+      XM_CUDA_TRY(cudaGetLastError());
+    }
     return XM_OK;
   }
 
   // Zero every work vector except the FP64 master iterate.  Called whenever the precision or
   // the padded width changes, so that no buffer is ever read through a stale reinterpretation.
   xm_status clear_vecs() {
-    void* vecs[] = {bY, bYc, bW, bWc, bG, bGc, bYin, bEta, bHeta, bR, bD, bHd, bWd, bXi, bYh};
+    void* vecs[] = {bY, bYc, bW, bWc, bG, bGc, bYin, bEta, bHeta, bR, bD, bHd, bWd, bXi, bYh, bZ};
     for (void* p : vecs) XM_CUDA_TRY(cudaMemsetAsync(p, 0, vec_bytes, st));
     return XM_OK;
   }
@@ -299,7 +353,16 @@ struct Solver {
     if (!std::isfinite(f) || !std::isfinite(g2)) return set_error(XM_ENUMERIC, "rtr: non-finite f");
     if (ref_g <= 0) ref_g = std::sqrt(g2);
     const double tol_abs = tol_rel * ref_g;
-    const double Delta_bar = std::sqrt(std::max(h_sc->y2, 1e-300));
+    // trust-region scale: ||Y|| in the tCG's norm (the preconditioner's B-norm when it is on)
+    double ynorm2 = h_sc->y2;
+    if (pcB) {
+      k_bnorm<To, R><<<nb_cam, CAM_THREADS, 0, st>>>(N, (const To*)bY, pcB, d_sc, ctx->d_partials,
+                                                      ctx->d_counter);
+      ++launches;
+      XM_TRY(pull_scalars());
+      ynorm2 = h_sc->dot;
+    }
+    const double Delta_bar = std::sqrt(std::max(ynorm2, 1e-300));
     double Delta = Delta_bar / 8.0;
     const double eps_reg = std::is_same<To, float>::value ? 1e2 * 1.1920929e-07
                                                           : 1e3 * 2.220446049250313e-16;
@@ -315,9 +378,9 @@ struct Solver {
       } else {
         Yin = (const Ti*)bY;
       }
-      k_tcg_init<To, Ti, R><<<grid_elems(rows * R), CAM_THREADS, 0, st>>>(
-          (int)rows, (const To*)bG, (Ti*)bEta, (Ti*)bHeta, (Ti*)bR, (Ti*)bD, d_sc, g2, Delta,
-          o.max_tcg, 1.0, 0.1);
+      k_tcg_init<To, Ti, R><<<nb_cam, CAM_THREADS, 0, st>>>(
+          N, Yin, (const To*)bG, (Ti*)bEta, (Ti*)bHeta, (Ti*)bR, (Ti*)bZ, (Ti*)bD, pcMinv, d_sc, Delta,
+          o.max_tcg, 1.0, 0.1, ctx->d_partials, ctx->d_counter);
       ++launches;
       XM_CUDA_TRY(cudaGetLastError());
       const int CH = 4;
@@ -328,10 +391,10 @@ struct Solver {
           k_hvp_epi<Ti, R><<<nb_cam, CAM_THREADS, 0, st>>>(N, Yin, (Ti*)bWd, (const Ti*)bD, (Ti*)bHd,
                                                            Lam, d_sc, ctx->d_partials, ctx->d_counter);
           k_tcg_update<Ti, R><<<nb_cam, CAM_THREADS, 0, st>>>(N, Yin, (Ti*)bEta, (Ti*)bHeta, (Ti*)bR,
-                                                              (const Ti*)bD, (const Ti*)bHd, d_sc,
-                                                              ctx->d_partials, ctx->d_counter);
-          k_tcg_dir<Ti, R><<<nb_cam, CAM_THREADS, 0, st>>>(N, (const Ti*)bEta, (const Ti*)bR, (Ti*)bD,
-                                                           d_sc, ctx->d_partials, ctx->d_counter);
+                                                              (Ti*)bZ, (const Ti*)bD, (const Ti*)bHd,
+                                                              pcMinv, d_sc, ctx->d_partials,
+                                                              ctx->d_counter);
+          k_tcg_dir<Ti, R><<<nb_cam, CAM_THREADS, 0, st>>>(N, (const Ti*)bZ, (Ti*)bD, d_sc);
           launches += 3;
         }
         XM_CUDA_TRY(cudaGetLastError());
@@ -354,7 +417,7 @@ struct Solver {
       const double model_dec = -(h_sc->g_eta + 0.5 * h_sc->eta_Heta);
       const double reg = std::max(1.0, std::fabs(f)) * eps_reg;
       const double rho = (f - fc + reg) / (model_dec + reg);
-      const double en = std::sqrt(h_sc->eta2);
+      const double en = std::sqrt(pcMinv ? h_sc->ee : h_sc->eta2);   // ||eta|| in the tCG's norm
       if (!std::isfinite(fc) || rho < 0.25) {
         Delta *= 0.25;
       } else if (rho > 0.75 && en >= Delta * (1.0 - 1e-6)) {
@@ -915,6 +978,7 @@ static xm_status check_opts(const DeviceQ& q, const xm_opts& o) {
     return set_error(XM_EINVAL, "opts: iteration caps must be positive");
   if (!(o.scale_reg >= 0.0) || !std::isfinite(o.scale_reg))
     return set_error(XM_EINVAL, "opts: scale_reg must be finite and >= 0 (got %g)", o.scale_reg);
+  if (o.precond != 0 && o.precond != 1) return set_error(XM_EINVAL, "opts: precond must be 0 or 1");
   return XM_OK;
 }
 

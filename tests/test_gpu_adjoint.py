@@ -9,10 +9,8 @@ element.  Tolerances:
     the Hessian on the tangent space (below 1e4 on these scenes), so 1e-6 relative to the
     largest entry leaves a wide margin over the expected 1e-8;
   * against the oracle's own solve: both optima agree to the solve tolerance, so 1e-5;
-  * finite differences: central differences with step h along a random direction over all
-    observations, truncation O(h^2) and solve noise O(tol / h), so 1e-5 relative."""
-import dataclasses
-
+  * finite differences: central differences of deterministic FP64 re-solves with step h along a
+    random direction over all observations, truncation O(h^2) ~ 1e-8, so 1e-6 relative."""
 import numpy as np
 import pytest
 
@@ -108,39 +106,42 @@ def test_backward_matches_oracle_solution(C):
 
 def test_finite_differences_trajectory_50(C):
     """Directional derivatives of L = <D, G> along random directions in u and in w, by central
-    differences of warm-started FP64 GPU re-solves, against the adjoint's dL/du and dL/dw."""
+    differences of complete FP64 re-solves of the 50-camera trajectory instance, against the
+    CUDA adjoint's dL/du and dL/dw.  The re-solves are the oracle's (deterministic FP64, warm
+    started, ||rgrad|| <= 1e-13 of the start): the GPU's FP64 sweeps add column partials with
+    atomics, and on this ill-conditioned instance that rounding moves a re-solved G by ~3e-8,
+    i.e. ~3e-4 of a difference quotient with step 1e-5.  With h = 1e-6 (of max |u|) the
+    truncation error is ~1e-8 and the quotients agree with the adjoint to ~2e-8; tolerance 1e-6."""
     from paper_2502_04640_b300 import xm
     sc = scenes.sub_scene(scenes.config4(), 50)
-    opts = xm.xm_default_opts(prec=0, grad_tol_rel=1e-13)
-    q, t, out = _solve(C, sc, opts)
+    q, t, out = _solve(C, sc, xm.xm_default_opts(prec=0, grad_tol_rel=1e-13))
     assert out["status"] == 0 and out["info"]["certified"] == 1
     r = out["info"]["rank"]
-    Y0 = out["Y"][:, :r].contiguous()
     D = _dG(sc, 9)
     d_u, d_w, _, info, st = xm.xm_backward(q, out["Y"], r, sc.M, *t, torch.as_tensor(D, device="cuda:0"),
                                            xm.xm_default_opts(prec=1, grad_tol_rel=1e-12))
     assert st == 0
     q.free()
+    Qo = O.build_Q_schur(sc.N, sc.M, sc.cam, sc.lmk, sc.ukp, sc.w)
+    base = O.solve(Qo, r0=4, grad_tol_rel=1e-13)
+    assert base.certified
     rng = np.random.default_rng(10)
 
     def loss(ukp, w):
-        s2 = dataclasses.replace(sc, ukp=ukp, w=w)
-        qq, _, o2 = _solve(C, s2, opts, Y0=Y0)
-        assert o2["info"]["certified"] == 1
-        G = (o2["s"][:, None, None] * o2["R"]).cpu().numpy()
-        qq.free()
-        return float(np.sum(D * G))
+        Qp = O.build_Q_schur(sc.N, sc.M, sc.cam, sc.lmk, ukp, w)
+        res = O.solve(Qp, r0=base.Y.shape[1], Y0=base.Y, grad_tol_rel=1e-13)
+        return float(np.sum(D * (res.s[:, None, None] * res.R)))
 
     du_dir = rng.standard_normal(sc.ukp.shape)
-    h = 1e-5 * float(np.abs(sc.ukp).max())
+    h = 1e-6 * float(np.abs(sc.ukp).max())
     fd = (loss(sc.ukp + h * du_dir, sc.w) - loss(sc.ukp - h * du_dir, sc.w)) / (2 * h)
     pred = float(np.sum(d_u.cpu().numpy() * du_dir))
-    assert abs(fd - pred) <= 1e-5 * max(abs(pred), 1.0), (fd, pred)
+    assert abs(fd - pred) <= 1e-6 * max(abs(pred), 1.0), (fd, pred)
     dw_dir = rng.uniform(-1.0, 1.0, sc.w.shape) * sc.w
-    hw = 1e-5
+    hw = 1e-6
     fd = (loss(sc.ukp, sc.w + hw * dw_dir) - loss(sc.ukp, sc.w - hw * dw_dir)) / (2 * hw)
     pred = float(np.sum(d_w.cpu().numpy() * dw_dir))
-    assert abs(fd - pred) <= 1e-5 * max(abs(pred), 1.0), (fd, pred)
+    assert abs(fd - pred) <= 1e-6 * max(abs(pred), 1.0), (fd, pred)
 
 
 def test_autograd_function(C):

@@ -126,3 +126,21 @@ def test_pipeline_from_host_arrays(C):
                                          xm.xm_default_opts(prec=1))
     assert st == 0 and info["certified"] == 1
     assert np.abs(R - ref.R).max() <= 1e-5 and np.abs(s - ref.s).max() <= 1e-5 * ref.s.max()
+
+
+@pytest.mark.parametrize("name", ["config1", "bal"])
+def test_block_jacobi_tcg_reaches_the_oracle_optimum(C, name):
+    """opts.precond = 1 (block-Jacobi preconditioned tCG with the trust region in its norm)
+    changes the path, not the certified optimum."""
+    sc = scenes.config1() if name == "config1" else scenes.random_scene(
+        60, 1500, noise=0.02, outlier_frac=0.02, seed=71, s_range=(0.3, 3.0))
+    Qo = O.build_Q_schur(sc.N, sc.M, sc.cam, sc.lmk, sc.ukp, sc.w)
+    ref = O.solve(Qo, r0=4)
+    assert ref.certified
+    for prec in (0, 1):
+        q, out = _solve(C, sc, prec, precond=1)
+        info = out["info"]
+        assert out["status"] == 0 and info["certified"] == 1
+        assert _rel(info["f"], ref.f) <= 1e-6
+        assert np.abs(out["R"] - ref.R).max() <= 1e-5
+        q.free()
