@@ -1444,9 +1444,12 @@ extern "C" xm_status xm_solve_batched(xm_ctx* c, xm_batch* b, const xm_opts* opt
   const int kmax = std::max(10, std::min(o.lanczos_max, b->n_max));
   const size_t smem4 = bat::smem_bytes(b->NM, 4, kmax);
   const size_t smem8 = bat::smem_bytes(b->NM, 8, kmax);
-  if (smem8 > c->smem_optin)
+  cudaFuncAttributes fa4{}, fa8{};
+  XM_CUDA_TRY(cudaFuncGetAttributes(&fa4, bat::k_batched<4>));
+  XM_CUDA_TRY(cudaFuncGetAttributes(&fa8, bat::k_batched<8>));
+  if (smem4 + fa4.sharedSizeBytes > c->smem_optin || smem8 + fa8.sharedSizeBytes > c->smem_optin)
     return set_error(XM_EINVAL, "xm_solve_batched: largest scene (3N = %d) needs %zu bytes of shared "
-                     "memory, above %zu", b->n_max, smem8, c->smem_optin);
+                     "memory, above %zu", b->n_max, smem8 + fa8.sharedSizeBytes, c->smem_optin);
   XM_CUDA_TRY(cudaFuncSetAttribute(bat::k_batched<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem4));
   XM_CUDA_TRY(cudaFuncSetAttribute(bat::k_batched<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem8));
   const int grid = std::min(c->num_sms, b->S);

@@ -13,13 +13,17 @@ namespace xm {
 
 // ------------------------------------------------------------------ errors (host side)
 xm_status set_error(xm_status st, const char* fmt, ...);
+// On failure the runtime's last-error slot is read and cleared as well, so that a non-sticky
+// error reported here is not picked up again by the next, unrelated cudaGetLastError().
 #define XM_CUDA_TRY(...)                                                                   \
   do {                                                                                     \
     cudaError_t e_ = (__VA_ARGS__);                                                        \
-    if (e_ != cudaSuccess)                                                                 \
+    if (e_ != cudaSuccess) {                                                               \
+      (void)cudaGetLastError();                                                            \
       return ::xm::set_error(e_ == cudaErrorMemoryAllocation ? XM_ENOMEM : XM_ECUDA,       \
                              "%s failed: %s (%s:%d)", #__VA_ARGS__, cudaGetErrorString(e_), \
                              __FILE__, __LINE__);                                          \
+    }                                                                                      \
   } while (0)
 #define XM_TRY(...)                                                                        \
   do {                                                                                     \
