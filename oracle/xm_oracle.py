@@ -173,16 +173,23 @@ def recover_tp(N, M, cam, lmk, ukp, w, U3):
     Yb = np.asarray(U3).T.reshape(N, 3, 3)
     a = np.einsum("eab,ea->eb", Yb[cam], ukp)
     E = cam.size
+    # a landmark without observations leaves p_k free: it is left out and reported as 0
+    seen = np.bincount(lmk, minlength=M) > 0
+    idx = -np.ones(M, dtype=np.int64)
+    idx[seen] = np.arange(int(seen.sum()))
+    Ms = int(seen.sum())
     rows = np.concatenate([np.arange(E)[cam > 0], np.arange(E)])
-    cols = np.concatenate([cam[cam > 0] - 1, N - 1 + lmk])
+    cols = np.concatenate([cam[cam > 0] - 1, N - 1 + idx[lmk]])
     vals = np.concatenate([np.ones(int((cam > 0).sum())), -np.ones(E)])
-    G = sp.csr_matrix((vals, (rows, cols)), shape=(E, N - 1 + M))
+    G = sp.csr_matrix((vals, (rows, cols)), shape=(E, N - 1 + Ms))
     Wd = sp.diags(w)
     Hm = (G.T @ Wd @ G).tocsc()
     rhs = -(G.T @ (w[:, None] * a))
     sol = spla.splu(Hm).solve(rhs)
     t = np.vstack([np.zeros((1, 3)), sol[: N - 1]])
-    return t, sol[N - 1:]
+    p = np.zeros((M, 3))
+    p[seen] = sol[N - 1:]
+    return t, p
 
 
 # ======================================================================================
@@ -596,6 +603,40 @@ def solve(Q, r0=4, r_max=None, cert_tau_rel=1e-6, Y0=None, grad_tol_rel=1e-10,
     return SolveResult(Y, Y.shape[1], res.f, res.grad_norm, cert, bool(ok), R, s, rho_hat,
                        suboptimality(rho_hat, res.f), suboptimality(rho_hat, lower), sweeps,
                        visited)
+
+
+def observation_residuals(cam, lmk, ukp, w, R, s, t, p):
+    """Per-measurement terms of Eq. 3: w_e || R_i (s_i u_e) + t_i - p_k ||^2."""
+    res = np.einsum("eab,eb->ea", R[cam], s[cam][:, None] * ukp) + t[cam] - p[lmk]
+    return w * np.sum(res * res, axis=1)
+
+
+def xm2_keep(res2, drop_frac=0.1):
+    """XM^2's greedy outlier rule: drop the fraction drop_frac of measurements with the largest
+    residual terms (ties broken by index), keep the rest; returns a boolean mask."""
+    E = res2.size
+    k = int(math.floor(drop_frac * E))
+    keep = np.ones(E, dtype=bool)
+    if k > 0:
+        order = np.lexsort((np.arange(E), -res2))     # largest first, then lower index
+        keep[order[:k]] = False
+    return keep
+
+
+def solve_xm2(N, M, cam, lmk, ukp, w, drop_frac=0.1, mu=0.0, **kw):
+    """XM^2 (running twice): solve, recover t and p (Eq. 7), drop the drop_frac measurements with
+    the largest residual terms, solve again on the rest.  Returns (first, second, keep, t, p)."""
+    cam, lmk, ukp, w = _validated(N, M, cam, lmk, ukp, w)
+    Q = build_Q_schur(N, M, cam, lmk, ukp, w)
+    first = solve(Q, mu=mu, **kw)
+    U3 = np.concatenate([first.s[i] * first.R[i] for i in range(N)], axis=1)
+    t, p = recover_tp(N, M, cam, lmk, ukp, w, U3)
+    keep = xm2_keep(observation_residuals(cam, lmk, ukp, w, first.R, first.s, t, p), drop_frac)
+    Q2 = build_Q_schur(N, M, cam[keep], lmk[keep], ukp[keep], w[keep])
+    second = solve(Q2, mu=mu, **kw)
+    U3 = np.concatenate([second.s[i] * second.R[i] for i in range(N)], axis=1)
+    t2, p2 = recover_tp(N, M, cam[keep], lmk[keep], ukp[keep], w[keep], U3)
+    return first, second, keep, t2, p2
 
 
 # ======================================================================================
