@@ -240,6 +240,25 @@ xm_status xm_backward(xm_ctx* ctx, const xm_qmat* q, const xm_opts* opts, int r,
                       const double* ukp, const double* w, const double* dL_dG, double* dL_dukp,
                       double* dL_dw, double* lam, xm_adj_info* info);
 
+/* ---- translations and landmarks (Eq. 7), per-measurement residuals, XM^2 (Sec. 5) --------
+ * xm_recover_tp: for rotations R (N x 3 x 3 row-major) and scales s (N), the least-squares
+ * translations (t_0 = 0) and landmarks of Eq. 3, in FP64: t_out N x 3, p_out M x 3 (a landmark
+ * without observations gets 0), res2_out E (w_e ||s_i R_i u_e + t_i - p_k||^2); any output may
+ * be NULL.  Device pointers; synchronous.  XM_EDISCONNECTED if the anchored camera block is
+ * singular. */
+xm_status xm_recover_tp(xm_ctx* ctx, int N, int M, int64_t E, const int32_t* cam, const int32_t* lmk,
+                        const double* ukp, const double* w, const double* R, const double* s,
+                        double* t_out, double* p_out, double* res2_out);
+/* xm_solve_xm2: XM^2 (running twice): build Q, solve, recover (t, p), drop the floor(drop_frac E)
+ * measurements with the largest Eq. 3 terms (ties by the lower index), then build and solve
+ * again on the rest.  Outputs (device) of the second solve: R_out, s_out, t_out, p_out (may be
+ * NULL); keep_out (E bytes, may be NULL): 1 for a kept measurement.  info_first / info_second
+ * (host, may be NULL).  Returns the second solve's status. */
+xm_status xm_solve_xm2(xm_ctx* ctx, int N, int M, int64_t E, const int32_t* cam, const int32_t* lmk,
+                       const double* ukp, const double* w, const xm_opts* opts, double drop_frac,
+                       double* R_out, double* s_out, double* t_out, double* p_out,
+                       unsigned char* keep_out, xm_info* info_first, xm_info* info_second);
+
 /* ---- batched solve of many independent scenes (serving-style batches) ------------------
  * Alg. 1 / Sec. 3.2 / Thm. 1 / Sec. 2.2 for every scene of a batch in one persistent launch:
  * each CTA takes the next scene of a work queue (descending size) and runs its whole

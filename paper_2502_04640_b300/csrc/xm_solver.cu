@@ -966,7 +966,7 @@ xm_status build_Q(xm_ctx* ctx, int N, int M, int64_t E, const int32_t* cam, cons
                   const double* ukp, const double* w, unsigned mask, DeviceQ& out,
                   double* t_build);
 
-static xm_status check_opts(const DeviceQ& q, const xm_opts& o) {
+xm_status check_opts(const DeviceQ& q, const xm_opts& o) {
   if (o.r0 < 1 || o.r0 > XM_MAX_RANK || o.r_max < o.r0 || o.r_max > XM_MAX_RANK)
     return set_error(XM_EINVAL, "opts: need 1 <= r0 <= r_max <= %d (r0=%d, r_max=%d)", XM_MAX_RANK,
                      o.r0, o.r_max);

@@ -123,6 +123,11 @@ def lib() -> ctypes.CDLL:
                                       ctypes.POINTER(XmInfo)]),
         "xm_pipeline_host": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int64, _P, _P, _P,
                                             _P, ctypes.POINTER(XmOpts), _P, _P, ctypes.POINTER(XmInfo)]),
+        "xm_recover_tp": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int64, _P, _P, _P, _P, _P,
+                                         _P, _P, _P, _P]),
+        "xm_solve_xm2": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int64, _P, _P, _P, _P,
+                                        ctypes.POINTER(XmOpts), ctypes.c_double, _P, _P, _P, _P, _P,
+                                        ctypes.POINTER(XmInfo), ctypes.POINTER(XmInfo)]),
         "xm_batch_create": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(_P)]),
         "xm_batch_free": (ctypes.c_int, [_P, _P]),
         "xm_batch_autotune": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
@@ -329,6 +334,41 @@ def xm_backward(q: QMat, Y, rank: int, M: int, cam, lmk, ukp, w, dL_dG, opts: Xm
                                   _ptr(cam), _ptr(lmk), _ptr(ukp), _ptr(w), _ptr(dL_dG), _ptr(d_u),
                                   _ptr(d_w), _ptr(lam), ctypes.byref(info)), allow)
     return d_u, d_w, lam, info.as_dict(), st
+
+
+def xm_recover_tp(ctx: Context, N: int, M: int, cam, lmk, ukp, w, R, s, want_res2: bool = True):
+    """(t (N x 3), p (M x 3), res2 (E) or None) of Eq. 7 for the rounded (R, s); CUDA tensors."""
+    import torch
+    dev = f"cuda:{ctx.device}"
+    E = int(cam.shape[0])
+    t = torch.empty((N, 3), dtype=torch.float64, device=dev)
+    p = torch.empty((M, 3), dtype=torch.float64, device=dev)
+    r2 = torch.empty((E,), dtype=torch.float64, device=dev) if want_res2 else None
+    _check(lib().xm_recover_tp(ctx.h, N, M, E, _ptr(cam), _ptr(lmk), _ptr(ukp), _ptr(w),
+                               _ptr(R.contiguous()), _ptr(s.contiguous()), _ptr(t), _ptr(p), _ptr(r2)))
+    return t, p, r2
+
+
+def xm_solve_xm2(ctx: Context, N: int, M: int, cam, lmk, ukp, w, opts: XmOpts | None = None,
+                 drop_frac: float = 0.1, allow_notcert: bool = True):
+    """XM^2 from observation tensors: dict(R, s, t, p, keep (bool, E), info_first, info_second,
+    status)."""
+    import torch
+    dev = f"cuda:{ctx.device}"
+    opts = opts or xm_default_opts()
+    E = int(cam.shape[0])
+    R = torch.zeros((N, 3, 3), dtype=torch.float64, device=dev)
+    s = torch.zeros((N,), dtype=torch.float64, device=dev)
+    t = torch.zeros((N, 3), dtype=torch.float64, device=dev)
+    p = torch.zeros((M, 3), dtype=torch.float64, device=dev)
+    keep = torch.zeros((E,), dtype=torch.uint8, device=dev)
+    i1, i2 = XmInfo(), XmInfo()
+    allow = (XM_OK, XM_ENOTCERT, XM_ENOCONV) if allow_notcert else (XM_OK,)
+    st = _check(lib().xm_solve_xm2(ctx.h, N, M, E, _ptr(cam), _ptr(lmk), _ptr(ukp), _ptr(w), ctypes.byref(opts),
+                                   drop_frac, _ptr(R), _ptr(s), _ptr(t), _ptr(p), _ptr(keep),
+                                   ctypes.byref(i1), ctypes.byref(i2)), allow)
+    return dict(R=R, s=s, t=t, p=p, keep=keep.bool(), info_first=i1.as_dict(), info_second=i2.as_dict(),
+                status=st)
 
 
 class Batch:
