@@ -71,7 +71,7 @@ typedef struct xm_opts {
   int max_outer;           /* RTR iterations per rank (per phase)                          */
   int max_tcg;             /* tCG iterations per RTR step                                  */
   int max_polish;          /* FP64 polish RTR iterations (mixed modes)                     */
-  int lanczos_max;         /* Krylov dimension cap of the certificate                      */
+  int lanczos_max;         /* Krylov dimension cap of the certificate (default 800)        */
   double lanczos_tol;      /* Ritz residual / |theta_max| stop for lambda_min              */
   double time_limit_s;     /* wall-clock cap of xm_solve (<= 0: none)                      */
   uint64_t seed;           /* Lanczos start vector                                         */
@@ -109,6 +109,9 @@ typedef struct xm_info {
   int n_outer, n_tcg, n_lanczos, n_escapes;
   double t_solve_s, t_cert_s, t_build_s;
   double qy_ms_fp32, qy_ms_fp64; /* mean device time of one r-column sweep, when measured   */
+  int lanczos_converged;   /* 1 iff the last certificate's Ritz residual met lanczos_tol (0: it
+                              stopped at the Krylov cap lanczos_max; the decision then rests on an
+                              unconverged Ritz value)                                           */
 } xm_info;
 
 /* ---- context ---------------------------------------------------------------------- */
@@ -270,7 +273,8 @@ xm_status xm_solve_xm2(xm_ctx* ctx, int N, int M, int64_t E, const int32_t* cam,
  * full FP32 and FP64 row-major copies (rows padded to a multiple of 4 columns) owned by the
  * batch; the xm_qmat handles stay the caller's.  Scene size is limited by shared memory:
  * 2 * 8 * ldq_max * 8 bytes of sweep staging plus the Krylov work must fit the 227 KB of a CTA
- * (about 3N <= 1300; checked, XM_EINVAL otherwise). */
+ * (about 3N <= 1300; checked, XM_EINVAL otherwise).  The Krylov work is shared-memory resident,
+ * so the batched certificate uses min(lanczos_max, 400) steps at most. */
 typedef struct xm_batch xm_batch;
 
 typedef struct xm_batch_info {

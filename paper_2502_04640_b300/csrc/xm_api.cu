@@ -76,7 +76,7 @@ void xm_default_opts(xm_opts* o) {
   o->max_outer = 300;
   o->max_tcg = 200;
   o->max_polish = 20;
-  o->lanczos_max = 400;
+  o->lanczos_max = 800;
   o->lanczos_tol = 1e-8;
   o->time_limit_s = 0.0;
   o->seed = 12345;

@@ -34,6 +34,7 @@ constexpr int NW = NT / 32;
 constexpr int KQUICK = 60;         // Krylov steps of the quick certificate
 constexpr int NVEC = 17;           // per-slot vectors of NM x 8 doubles
 constexpr int NCLASS = 4;          // scene-size classes of the tiling table
+constexpr int XM_BATCH_KMAX = 400;       // Krylov cap of the batched certificate (shared memory)
 constexpr int XM_BATCH_HANDOVER = 100;   // internal status: continued by the rank-8 kernel
 
 __host__ __device__ inline int size_class(int n) { return n <= 150 ? 0 : (n <= 450 ? 1 : (n <= 900 ? 2 : 3)); }
@@ -1441,7 +1442,9 @@ extern "C" xm_status xm_solve_batched(xm_ctx* c, xm_batch* b, const xm_opts* opt
   if (!(o.scale_reg >= 0.0) || !std::isfinite(o.scale_reg))
     return set_error(XM_EINVAL, "xm_solve_batched: scale_reg must be finite and >= 0");
   XM_CUDA_TRY(cudaSetDevice(c->device));
-  const int kmax = std::max(10, std::min(o.lanczos_max, b->n_max));
+  // The Krylov recurrence lives in shared memory beside the scene's sweep buffers, so the batched
+  // certificate caps its dimension at XM_BATCH_KMAX whatever lanczos_max asks for.
+  const int kmax = std::max(10, std::min(std::min(o.lanczos_max, xm::bat::XM_BATCH_KMAX), b->n_max));
   const size_t smem4 = bat::smem_bytes(b->NM, 4, kmax);
   const size_t smem8 = bat::smem_bytes(b->NM, 8, kmax);
   cudaFuncAttributes fa4{}, fa8{};

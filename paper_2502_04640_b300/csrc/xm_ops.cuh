@@ -650,12 +650,12 @@ k_dot(size_t total, const Ta* __restrict__ a, const Tb* __restrict__ b, double* 
 // ------------------------------------------------------------------ Lanczos (FP64 vectors)
 // w_i = Wz_i + dreg_i e_3 e_3^T v_i - Lambda_i v_i (Z v with Z = Q + diag(dreg) -
 // blockdiag(Lambda), App. D; dreg = 0 without the regulariser); Wz reset to zero.
-template <typename Tw>
-__global__ void k_zv_epi(int N, Tw* __restrict__ Wz, const double* __restrict__ v,
+template <typename Tw, typename Tv = double>
+__global__ void k_zv_epi(int N, Tw* __restrict__ Wz, const Tv* __restrict__ v,
                          const double* __restrict__ Lam, double* __restrict__ w) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
-  double x[3] = {v[3 * i], v[3 * i + 1], v[3 * i + 2]};
+  double x[3] = {double(v[3 * i]), double(v[3 * i + 1]), double(v[3 * i + 2])};
   const double dreg = Lam[(size_t)9 * N + i];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
@@ -686,54 +686,75 @@ k_reg_terms(int N, const double* __restrict__ Y, Scal* sc, double* partials, uns
   grid_reduce<2>(v, partials, counter, [&](double* t) { sc->dot = t[0]; sc->kappa = t[1]; });
 }
 
-// c[j] = <V_j, w> for the m columns of V (column-major, stride ld); one block per column
-static __global__ void k_gemv_t(int n, int m, const double* __restrict__ V, size_t ld,
-                         const double* __restrict__ w, double* __restrict__ c) {
+// The Lanczos basis V (column-major, stride ld) is FP32 when the Z products are FP32 sweeps
+// (orthogonality to ~1e-7 matches their accuracy; the per-element work then runs on the FP32
+// pipes, B300's FP64 rate being ~2 FMA per clock per SM) and FP64 otherwise.  Working vectors
+// (w), recurrence coefficients and Ritz values are FP64 in both cases.
+
+// c[j] = <V_j, w> for the m columns of V; one block per column; also writes cf = float(c).
+// w is given in the basis type (an FP32 copy of the FP64 working vector for an FP32 basis).
+template <typename VT>
+__global__ void k_gemv_t(int n, int m, const VT* __restrict__ V, size_t ld, const VT* __restrict__ w,
+                         double* __restrict__ c, float* __restrict__ cf) {
   __shared__ double sh[8];
   for (int j = blockIdx.x; j < m; j += gridDim.x) {
-    double s = 0.0;
-    const double* col = V + (size_t)j * ld;
+    VT s = VT(0);
+    const VT* col = V + (size_t)j * ld;
     for (int e = threadIdx.x; e < n; e += blockDim.x) s += col[e] * w[e];
-    s = warp_sum(s);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    double sd = warp_sum(double(s));
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = sd;
     __syncthreads();
     if (threadIdx.x == 0) {
       double t = 0.0;
       for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += sh[k];
       c[j] = t;
+      if (cf) cf[j] = float(t);
     }
     __syncthreads();
   }
 }
 
-// w -= V c (m columns)
-static __global__ void k_gemv_n_sub(int n, int m, const double* __restrict__ V, size_t ld,
-                             const double* __restrict__ c, double* __restrict__ w) {
+// w -= V c (m columns); cf = float(c) for an FP32 basis, c itself for an FP64 one
+template <typename VT>
+__global__ void k_gemv_n_sub(int n, int m, const VT* __restrict__ V, size_t ld, const double* __restrict__ c,
+                             const float* __restrict__ cf, double* __restrict__ w) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int j = 0; j < m; ++j) s += V[(size_t)j * ld + e] * c[j];
-    w[e] -= s;
+    VT s = VT(0);
+    if (sizeof(VT) == 4) {
+      for (int j = 0; j < m; ++j) s += V[(size_t)j * ld + e] * VT(cf[j]);
+    } else {
+      for (int j = 0; j < m; ++j) s += V[(size_t)j * ld + e] * VT(c[j]);
+    }
+    w[e] -= double(s);
   }
 }
 
 // w -= a[k] v_k + b[k-1] v_{k-1}  (coefficients read on the device)
-static __global__ void k_lanczos_3term(int n, double* __restrict__ w, const double* __restrict__ vk,
-                                const double* __restrict__ vkm1, const double* alpha,
-                                const double* beta, int k) {
+template <typename VT>
+__global__ void k_lanczos_3term(int n, double* __restrict__ w, const VT* __restrict__ vk,
+                                const VT* __restrict__ vkm1, const double* alpha, const double* beta, int k) {
   const double a = alpha[k];
   const double b = (k > 0 && vkm1) ? beta[k - 1] : 0.0;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x)
-    w[e] -= a * vk[e] + (b != 0.0 ? b * vkm1[e] : 0.0);
+    w[e] -= a * double(vk[e]) + (b != 0.0 ? b * double(vkm1[e]) : 0.0);
 }
 
 // dst = w / sqrt(*nrm2); *beta_out = sqrt(*nrm2)
-static __global__ void k_normalize(int n, const double* __restrict__ w, const double* nrm2,
-                            double* __restrict__ dst, double* beta_out) {
+template <typename VT>
+__global__ void k_normalize(int n, const double* __restrict__ w, const double* nrm2, VT* __restrict__ dst,
+                            double* beta_out) {
   const double b = sqrt(*nrm2);
   const double inv = b > 0.0 ? 1.0 / b : 0.0;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x)
-    dst[e] = w[e] * inv;
+    dst[e] = VT(w[e] * inv);
   if (blockIdx.x == 0 && threadIdx.x == 0 && beta_out) *beta_out = b;
+}
+
+// column j of V (stride ld) from column j of a row-major n_rows x R array
+template <typename VT, int R>
+__global__ void k_col_from_rows(int n_rows, int j, const double* __restrict__ src, VT* __restrict__ col) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n_rows; e += gridDim.x * blockDim.x)
+    col[e] = VT(src[(size_t)e * R + j]);
 }
 
 // deterministic pseudo-random start vector (splitmix64 of (seed, index)), uniform in [-1, 1)

@@ -211,9 +211,10 @@ struct Solver {
   double* d_small = nullptr;   // gram / rotation / O0 / scalar scratch (256 doubles)
   // Lanczos
   int kmax = 0;
-  double *V = nullptr, *lw = nullptr, *lz = nullptr, *lalpha = nullptr, *lbeta = nullptr,
-         *lc = nullptr, *lnrm = nullptr, *lritz = nullptr;
-  float *lv32 = nullptr, *lW32 = nullptr;
+  void* V = nullptr;   // Lanczos basis: FP32 or FP64 columns of n_pad (room for FP64)
+  double *lw = nullptr, *lz = nullptr, *lalpha = nullptr, *lbeta = nullptr, *lc = nullptr,
+         *lnrm = nullptr, *lritz = nullptr;
+  float *lv32 = nullptr, *lW32 = nullptr, *lwf = nullptr, *lcf = nullptr;
   // stats
   xm_info info{};
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -233,7 +234,7 @@ struct Solver {
   ~Solver() {
     void* bufs[] = {bY, bYc, bW, bWc, bG, bGc, bYin, bEta, bHeta, bR, bD, bHd, bWd, bY64, bXi, bYh,
                     bZ, Lam, Lamc, pcMinv, pcB, d_sc, d_small, V, lw, lz, lalpha, lbeta, lc, lnrm,
-                    lritz, lv32, lW32};
+                    lritz, lv32, lW32, lwf, lcf};
     for (void* p : bufs) if (p) cudaFree(p);
     if (h_sc) cudaFreeHost(h_sc);
     if (ev0) cudaEventDestroy(ev0);
@@ -445,57 +446,91 @@ struct Solver {
   }
 
   // w = Z v (v, w: FP64 n_pad vectors), Z = Q - blockdiag(Lam)
-  xm_status zmul(int prec, const double* v, double* w) {
+  // w = Z v (Z = Q + diag(dreg) - blockdiag(Lam)) for a basis vector v of type VT (n_pad long)
+  template <typename VT>
+  xm_status zmul(int prec, const VT* v, double* w) {
     const int nn = n_pad;
     if (prec == XM_FP64) {
-      XM_TRY(sweep(XM_FP64, 1, v, lz, nullptr, false));
-      k_zv_epi<double><<<nb_cam, CAM_THREADS, 0, st>>>(N, lz, v, Lam, w);
+      const double* vd = reinterpret_cast<const double*>(v);
+      if (sizeof(VT) != 8) {
+        k_cast<VT, double><<<grid_elems(nn), CAM_THREADS, 0, st>>>((size_t)nn, v, lritz_tmp());
+        ++launches;
+        vd = lritz_tmp();
+      }
+      XM_TRY(sweep(XM_FP64, 1, vd, lz, nullptr, false));
+      k_zv_epi<double, double><<<nb_cam, CAM_THREADS, 0, st>>>(N, lz, vd, Lam, w);
     } else {
-      k_cast<double, float><<<grid_elems(nn), CAM_THREADS, 0, st>>>((size_t)nn, v, lv32);
-      XM_TRY(sweep(XM_FP32_BULK, 1, lv32, lW32, nullptr, false));
-      k_zv_epi<float><<<nb_cam, CAM_THREADS, 0, st>>>(N, lW32, v, Lam, w);
-      ++launches;
+      const float* vf = reinterpret_cast<const float*>(v);
+      if (sizeof(VT) != 4) {
+        k_cast<VT, float><<<grid_elems(nn), CAM_THREADS, 0, st>>>((size_t)nn, v, lv32);
+        ++launches;
+        vf = lv32;
+      }
+      XM_TRY(sweep(XM_FP32_BULK, 1, vf, lW32, nullptr, false));
+      k_zv_epi<float, float><<<nb_cam, CAM_THREADS, 0, st>>>(N, lW32, vf, Lam, w);
     }
     ++launches;
     XM_CUDA_TRY(cudaGetLastError());
     return XM_OK;
   }
+  double* lritz_tmp() { return lz + n_pad; }   // second half of the lz scratch
 
-  // classical Gram-Schmidt pass of w against the first m columns of V
+  // classical Gram-Schmidt pass of w against the first m columns of V (basis type VT)
+  template <typename VT>
   xm_status reorth(double* w, int m) {
     if (m <= 0) return XM_OK;
     const int nn = n_pad;
-    k_gemv_t<<<std::min(m, ctx->num_sms * 8), 256, 0, st>>>(nn, m, V, nn, w, lc);
-    k_gemv_n_sub<<<grid_elems(nn), CAM_THREADS, 0, st>>>(nn, m, V, nn, lc, w);
+    const VT* Vb = static_cast<const VT*>(V);
+    const VT* wv;
+    if (sizeof(VT) == 4) {
+      k_cast<double, float><<<grid_elems(nn), CAM_THREADS, 0, st>>>((size_t)nn, w, lwf);
+      ++launches;
+      wv = reinterpret_cast<const VT*>(lwf);
+    } else {
+      wv = reinterpret_cast<const VT*>(w);
+    }
+    k_gemv_t<VT><<<std::min(m, ctx->num_sms * 8), 256, 0, st>>>(nn, m, Vb, nn, wv, lc, lcf);
+    k_gemv_n_sub<VT><<<grid_elems(nn), CAM_THREADS, 0, st>>>(nn, m, Vb, nn, lc, lcf, w);
     launches += 2;
     XM_CUDA_TRY(cudaGetLastError());
     return XM_OK;
   }
 
   // ---------------- Lanczos on Z restricted to range(Y)^perp (Thm. 1 certificate)
+  // The basis is FP32 when the Z products are FP32 sweeps, FP64 otherwise.
   template <int R>
   xm_status certify(int r, int prec_z, double* lam_def, double* lam_max, double* lam_range,
                     int kcap_steps = 0) {
+    if (prec_z == XM_FP64) return certify_t<R, double>(r, prec_z, lam_def, lam_max, lam_range, kcap_steps);
+    return certify_t<R, float>(r, prec_z, lam_def, lam_max, lam_range, kcap_steps);
+  }
+
+  template <int R, typename VT>
+  xm_status certify_t(int r, int prec_z, double* lam_def, double* lam_max, double* lam_range,
+                      int kcap_steps) {
     auto tic = std::chrono::steady_clock::now();
     const int nn = n_pad;
     const int nd_max = XM_MAX_RANK;
     if (!V) {
       kmax = std::max(10, std::min(o.lanczos_max, n));
-      XM_CUDA_TRY(cudaMalloc(&V, sizeof(double) * (size_t)nn * (nd_max + kmax + 1)));
+      XM_CUDA_TRY(cudaMalloc(&V, sizeof(double) * (size_t)nn * (nd_max + kmax + 1)));   // room for FP64
       XM_CUDA_TRY(cudaMalloc(&lw, sizeof(double) * nn));
       XM_CUDA_TRY(cudaMemsetAsync(lw, 0, sizeof(double) * nn, st));
-      XM_CUDA_TRY(cudaMalloc(&lz, sizeof(double) * nn));
+      XM_CUDA_TRY(cudaMalloc(&lz, sizeof(double) * 2 * (size_t)nn));
       XM_CUDA_TRY(cudaMalloc(&lritz, sizeof(double) * nn));
       XM_CUDA_TRY(cudaMalloc(&lalpha, sizeof(double) * (kmax + 1)));
       XM_CUDA_TRY(cudaMalloc(&lbeta, sizeof(double) * (kmax + 1)));
       XM_CUDA_TRY(cudaMalloc(&lc, sizeof(double) * (nd_max + kmax + 2)));
+      XM_CUDA_TRY(cudaMalloc(&lcf, sizeof(float) * (nd_max + kmax + 2)));
       XM_CUDA_TRY(cudaMalloc(&lnrm, sizeof(double) * 2));
       XM_CUDA_TRY(cudaMalloc(&lv32, sizeof(float) * nn));
       XM_CUDA_TRY(cudaMalloc(&lW32, sizeof(float) * nn));
-      XM_CUDA_TRY(cudaMemsetAsync(lz, 0, sizeof(double) * nn, st));
+      XM_CUDA_TRY(cudaMalloc(&lwf, sizeof(float) * nn));
+      XM_CUDA_TRY(cudaMemsetAsync(lz, 0, sizeof(double) * 2 * (size_t)nn, st));
       XM_CUDA_TRY(cudaMemsetAsync(lritz, 0, sizeof(double) * nn, st));
       XM_CUDA_TRY(cudaMemsetAsync(lW32, 0, sizeof(float) * nn, st));
     }
+    VT* Vb = static_cast<VT*>(V);
     const int gv = grid_elems((size_t)nn);
     // orthonormal basis of range(Y) from the Gram matrix (first r columns)
     k_gram<double, R><<<grid_gram(), CAM_THREADS, 0, st>>>(nn, (const double*)bY64, d_small,
@@ -519,15 +554,21 @@ struct Solver {
     XM_CUDA_TRY(cudaMemcpyAsync(d_small + 64, rot.data(), sizeof(double) * R * R, cudaMemcpyHostToDevice, st));
     k_rotate<R><<<(nn + 127) / 128, 128, 0, st>>>(nn, (double*)bXi, d_small + 64);
     ++launches;
-    for (int j = 0; j < nd; ++j)
-      XM_CUDA_TRY(cudaMemcpy2DAsync(V + (size_t)j * nn, sizeof(double), (const double*)bXi + j,
-                                    sizeof(double) * R, sizeof(double), nn,
-                                    cudaMemcpyDeviceToDevice, st));
+    for (int j = 0; j < nd; ++j) {
+      k_col_from_rows<VT, R><<<gv, CAM_THREADS, 0, st>>>(nn, j, (const double*)bXi, Vb + (size_t)j * nn);
+      ++launches;
+    }
     // Rayleigh quotients of Z on range(Y): Vd^T Z Vd (nd x nd)
     std::vector<double> zr((size_t)nd * nd, 0.0);
     for (int j = 0; j < nd; ++j) {
-      XM_TRY(zmul(prec_z, V + (size_t)j * nn, lw));
-      k_gemv_t<<<nd, 256, 0, st>>>(nn, nd, V, nn, lw, lc);
+      XM_TRY(zmul<VT>(prec_z, Vb + (size_t)j * nn, lw));
+      const VT* wv = reinterpret_cast<const VT*>(lw);
+      if (sizeof(VT) == 4) {
+        k_cast<double, float><<<gv, CAM_THREADS, 0, st>>>((size_t)nn, lw, lwf);
+        ++launches;
+        wv = reinterpret_cast<const VT*>(lwf);
+      }
+      k_gemv_t<VT><<<nd, 256, 0, st>>>(nn, nd, Vb, nn, wv, lc, nullptr);
       ++launches;
       std::vector<double> cj(nd);
       XM_CUDA_TRY(cudaMemcpyAsync(cj.data(), lc, sizeof(double) * nd, cudaMemcpyDeviceToHost, st));
@@ -545,31 +586,30 @@ struct Solver {
     } else {
       *lam_range = 0.0;
     }
-    // start vector
-    double* v0 = V + (size_t)nd * nn;
-    k_random_vec<<<gv, CAM_THREADS, 0, st>>>(n, o.seed, v0);
-    XM_CUDA_TRY(cudaMemsetAsync(v0 + n, 0, sizeof(double) * (nn - n), st));
+    // start vector (FP64 working vector, then normalised into the basis)
+    k_random_vec<<<gv, CAM_THREADS, 0, st>>>(n, o.seed, lw);
+    XM_CUDA_TRY(cudaMemsetAsync(lw + n, 0, sizeof(double) * (nn - n), st));
     ++launches;
-    XM_TRY(reorth(v0, nd));
-    k_dot<double, double><<<gv, CAM_THREADS, 0, st>>>((size_t)nn, v0, v0, lnrm, ctx->d_partials, ctx->d_counter);
-    k_normalize<<<gv, CAM_THREADS, 0, st>>>(nn, v0, lnrm, v0, nullptr);
+    XM_TRY(reorth<VT>(lw, nd));
+    k_dot<double, double><<<gv, CAM_THREADS, 0, st>>>((size_t)nn, lw, lw, lnrm, ctx->d_partials, ctx->d_counter);
+    k_normalize<VT><<<gv, CAM_THREADS, 0, st>>>(nn, lw, lnrm, Vb + (size_t)nd * nn, nullptr);
     launches += 2;
     std::vector<double> ha(kmax + 1), hb(kmax + 1), s;
     int K = 0;
     double th_min = 0, th_max = 0;
-    bool conv = false;
+    bool conv = false, met = false;
     const int kcap = std::min(kcap_steps > 0 ? std::min(kcap_steps, kmax) : kmax, n - nd);
     for (int k = 0; k < kcap; ++k) {
-      double* vk = V + (size_t)(nd + k) * nn;
-      double* vkm1 = k > 0 ? V + (size_t)(nd + k - 1) * nn : nullptr;
-      XM_TRY(zmul(prec_z, vk, lw));
-      k_dot<double, double><<<gv, CAM_THREADS, 0, st>>>((size_t)nn, vk, lw, lalpha + k, ctx->d_partials, ctx->d_counter);
-      k_lanczos_3term<<<gv, CAM_THREADS, 0, st>>>(nn, lw, vk, vkm1, lalpha, lbeta, k);
+      const VT* vk = Vb + (size_t)(nd + k) * nn;
+      const VT* vkm1 = k > 0 ? Vb + (size_t)(nd + k - 1) * nn : nullptr;
+      XM_TRY(zmul<VT>(prec_z, vk, lw));
+      k_dot<VT, double><<<gv, CAM_THREADS, 0, st>>>((size_t)nn, vk, lw, lalpha + k, ctx->d_partials, ctx->d_counter);
+      k_lanczos_3term<VT><<<gv, CAM_THREADS, 0, st>>>(nn, lw, vk, vkm1, lalpha, lbeta, k);
       launches += 2;
-      XM_TRY(reorth(lw, nd + k + 1));
-      XM_TRY(reorth(lw, nd + k + 1));
+      XM_TRY(reorth<VT>(lw, nd + k + 1));
+      XM_TRY(reorth<VT>(lw, nd + k + 1));
       k_dot<double, double><<<gv, CAM_THREADS, 0, st>>>((size_t)nn, lw, lw, lnrm, ctx->d_partials, ctx->d_counter);
-      k_normalize<<<gv, CAM_THREADS, 0, st>>>(nn, lw, lnrm, V + (size_t)(nd + k + 1) * nn, lbeta + k);
+      k_normalize<VT><<<gv, CAM_THREADS, 0, st>>>(nn, lw, lnrm, Vb + (size_t)(nd + k + 1) * nn, lbeta + k);
       launches += 2;
       XM_CUDA_TRY(cudaGetLastError());
       ++info.n_lanczos;
@@ -583,7 +623,8 @@ struct Solver {
         tri_eigvec(K, ha.data(), hb.data(), th_min, s);
         const double res = std::fabs(hb[K - 1] * s[K - 1]);
         const double scale = std::max(std::fabs(th_max), std::fabs(th_min)) + 1e-300;
-        if (res <= o.lanczos_tol * scale || hb[K - 1] <= 1e-14 * scale || K == kcap) {
+        met = res <= o.lanczos_tol * scale || hb[K - 1] <= 1e-14 * scale || K == n - nd;
+        if (met || K == kcap) {
           conv = true;
           break;
         }
@@ -597,12 +638,16 @@ struct Solver {
       th_max = tri_eig_bisect(K, ha.data(), hb.data(), K - 1);
       tri_eigvec(K, ha.data(), hb.data(), th_min, s);
     }
+    info.lanczos_converged = (met || K == 0) ? 1 : 0;
     // Ritz vector of theta_min -> lritz (k_gemv_n_sub subtracts: lritz = -V s; the sign of an
     // eigenvector is irrelevant)
     if (K > 0) {
+      std::vector<float> sf(K);
+      for (int j = 0; j < K; ++j) sf[j] = float(s[j]);
       XM_CUDA_TRY(cudaMemcpyAsync(lc, s.data(), sizeof(double) * K, cudaMemcpyHostToDevice, st));
+      XM_CUDA_TRY(cudaMemcpyAsync(lcf, sf.data(), sizeof(float) * K, cudaMemcpyHostToDevice, st));
       XM_CUDA_TRY(cudaMemsetAsync(lritz, 0, sizeof(double) * nn, st));
-      k_gemv_n_sub<<<gv, CAM_THREADS, 0, st>>>(nn, K, V + (size_t)nd * nn, nn, lc, lritz);
+      k_gemv_n_sub<VT><<<gv, CAM_THREADS, 0, st>>>(nn, K, Vb + (size_t)nd * nn, nn, lc, lcf, lritz);
       ++launches;
     }
     XM_CUDA_TRY(cudaStreamSynchronize(st));

@@ -45,7 +45,7 @@ class XmInfo(ctypes.Structure):
                 ("n_tcg", ctypes.c_int), ("n_lanczos", ctypes.c_int), ("n_escapes", ctypes.c_int),
                 ("t_solve_s", ctypes.c_double), ("t_cert_s", ctypes.c_double),
                 ("t_build_s", ctypes.c_double), ("qy_ms_fp32", ctypes.c_double),
-                ("qy_ms_fp64", ctypes.c_double)]
+                ("qy_ms_fp64", ctypes.c_double), ("lanczos_converged", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -97,18 +97,24 @@ def test_outliers_and_tiles_match_oracle(C, prec):
     q.free()
 
 
-def test_certify_entry_point_matches_oracle(C):
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_certify_entry_point_matches_oracle(C, prec):
+    """The FP32 mode keeps its Krylov basis in FP32 (FP64 recurrence coefficients): the deflated
+    minimum agrees with the oracle's to 1e-5 of lambda_max in both modes."""
     from paper_2502_04640_b300 import xm
     sc = scenes.config1()
     Qo = O.build_Q_schur(sc.N, sc.M, sc.cam, sc.lmk, sc.ukp, sc.w)
     ref = O.solve(Qo, r0=4)
     q = xm.xm_build_Q(C, sc.N, sc.M, *xm.scene_tensors(sc))
-    out = xm.xm_certify(q, torch.tensor(ref.Y, device="cuda"), xm.xm_default_opts(prec=0))
+    out = xm.xm_certify(q, torch.tensor(ref.Y, device="cuda"), xm.xm_default_opts(prec=PRECS[prec]))
     Lam = out["Lambda"].cpu().numpy()
     cert = O.certify(Qo, ref.Y)
     assert np.abs(Lam - cert.Lambda).max() <= 1e-8 * np.abs(cert.Lambda).max()
     assert abs(out["info"]["lambda_min_deflated"] - cert.lam_min_deflated) <= 1e-5 * cert.lam_max_Q
-    assert out["info"]["certified"] == 1
+    assert out["info"]["certified"] == 1 and out["info"]["lanczos_converged"] == 1
+    if prec == "fp32":
+        q.free()
+        return
     # at the rank-3 local optimum of the [I..I] start the certificate fails (Thm. 2)
     r3 = O.rtr(Qo, O.initial_point(sc.N, 3))
     bad = xm.xm_certify(q, torch.tensor(r3.Y, device="cuda"), xm.xm_default_opts(prec=0))
