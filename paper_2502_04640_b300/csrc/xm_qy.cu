@@ -133,9 +133,10 @@ qy_packed_kernel(const TQ* __restrict__ tiles, int nt, int64_t ntiles, int nstag
   using A = typename C::A;
   if (skip != nullptr && *skip != 0) return;
 
-  extern __shared__ unsigned char smem_raw[];
-  unsigned char* base = reinterpret_cast<unsigned char*>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // 128-byte alignment as an offset into the shared array (an integer round trip of the
+  // pointer would hide its address space and turn every shared load into a generic load)
+  unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
   unsigned char* stages = base;
   A* ysm = reinterpret_cast<A*>(stages + (size_t)nstage * SLAB_BYTES);
   A* yjs = reinterpret_cast<A*>(reinterpret_cast<unsigned char*>(ysm) + C::YSM_BYTES);
