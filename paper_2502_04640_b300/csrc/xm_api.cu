@@ -193,6 +193,21 @@ xm_status xm_qmat_dims(const xm_qmat* q, int* N, int* n, unsigned* mask) {
   return XM_OK;
 }
 
+xm_status xm_set_build_mode(xm_ctx* c, int mode) {
+  if (!c) return set_error(XM_EINVAL, "xm_set_build_mode: NULL context");
+  if (mode != XM_BUILD_AUTO && mode != XM_BUILD_FP64 && mode != XM_BUILD_SPLIT_BF16)
+    return set_error(XM_EINVAL, "xm_set_build_mode: unknown mode %d", mode);
+  c->build_mode = mode;
+  return XM_OK;
+}
+
+xm_status xm_qmat_build_info(const xm_qmat* q, int* path, double* t_update_s) {
+  if (!q) return set_error(XM_EINVAL, "xm_qmat_build_info: NULL handle");
+  if (path) *path = q->d.build_path;
+  if (t_update_s) *t_update_s = q->d.t_update_s;
+  return XM_OK;
+}
+
 xm_status xm_free_Q(xm_ctx* c, xm_qmat* q) {
   if (!q) return XM_OK;
   if (c) {

@@ -5,10 +5,12 @@
 //   2. landmark elimination: for every landmark the camera pairs (a, b) of its observers get
 //      P_ab -= w_a w_b u_a u_b^T / d_k, B_ab -= w_a w_b u_a / d_k, S_ab -= w_a w_b / d_k
 //      (P = Q1 - V2 D^-1 V2^T, B = V1 - V2 D^-1 V3^T, S = Q2 - V3 D^-1 V3^T with D = Q3);
-//   3. translation elimination with the anchor t_0 = 0: Sbar = L L^T (Cholesky), C = L^-1 Bbar^T,
-//      Q = P - C^T C (dense FP64 factor / triangular solve / rank-k update from cuSOLVER and
-//      cuBLAS: the paper's "large dense matrix multiplications");
-//   4. pack the upper triangle into the tile layout of the sweep kernel (FP64 / FP32 / BF16).
+//   3. translation elimination with the anchor t_0 = 0: Sbar = L L^T (Cholesky), C = L^-1 Bbar^T
+//      (dense FP64 factor and triangular solve from cuSOLVER / cuBLAS: the paper's "large dense
+//      matrix multiplications"), then Q = P - C^T C either by cuBLAS DSYRK (FP64 units) or by the
+//      digit-split BF16 tensor-core update of xm_ozaki.cu (FP64-accurate, XM_BUILD_SPLIT_BF16);
+//   4. pack the upper triangle into the tile layout of the sweep kernel (FP64 / FP32 / BF16);
+//      the tensor-core update writes the packed tiles itself.
 // Connectivity of the view graph (rank N+M-1 of the Laplacian Q_tp, App. A lemma) is checked
 // with a union-find over the camera-landmark edges before any elimination.
 #include <cublas_v2.h>
@@ -396,12 +398,48 @@ xm_status build_Q(xm_ctx* ctx, int N, int M, int64_t E, const int32_t* cam, cons
     const double one = 1.0, minus_one = -1.0;
     XM_CUBLAS_TRY(cublasDtrsm(cb, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N,
                               CUBLAS_DIAG_NON_UNIT, m, n, &one, Sbar, N, BbarT, N));
-    XM_CUBLAS_TRY(cublasDsyrk(cb, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T, n, m, &minus_one, BbarT, N,
-                              &one, P.as<double>(), n));
+    bool split = false;
+    if (ctx->build_mode == XM_BUILD_SPLIT_BF16) {
+      if (!split_update_fits(m, n))
+        return set_error(XM_EINVAL, "split-BF16 build: N - 1 = %d outside its range", m);
+      split = true;
+    } else if (ctx->build_mode == XM_BUILD_AUTO) {
+      split = N >= XM_BUILD_SPLIT_MIN_N && split_update_fits(m, n);
+    }
+    if (split) {
+      // Q = P - C^T C on the tensor cores, written straight into the packed tiles
+      XM_TRY(alloc_tiles(ctx, out, N, mask));
+      DevBuf acc;
+      double* acc64 = out.q64;
+      if (!acc64) {
+        XM_CUDA_TRY(cudaMalloc(&acc.p, sizeof(double) * (size_t)out.ntiles * TILE * TILE));
+        acc64 = acc.as<double>();
+      }
+      XM_TRY(split_update_pack(ctx, BbarT, N, m, P.as<double>(), out, acc64, &out.t_update_s));
+      out.build_path = XM_BUILD_SPLIT_BF16;
+    } else {
+      cudaEvent_t e0, e1;
+      XM_CUDA_TRY(cudaEventCreate(&e0));
+      XM_CUDA_TRY(cudaEventCreate(&e1));
+      XM_CUDA_TRY(cudaEventRecord(e0, st));
+      XM_CUBLAS_TRY(cublasDsyrk(cb, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T, n, m, &minus_one, BbarT,
+                                N, &one, P.as<double>(), n));
+      XM_CUDA_TRY(cudaEventRecord(e1, st));
+      XM_CUDA_TRY(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      XM_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      XM_TRY(alloc_tiles(ctx, out, N, mask));
+      XM_TRY(pack_dense(ctx, out, P.as<double>()));
+      out.t_update_s = ms * 1e-3;
+      out.build_path = XM_BUILD_FP64;
+    }
+  } else {
+    XM_TRY(alloc_tiles(ctx, out, N, mask));
+    XM_TRY(pack_dense(ctx, out, P.as<double>()));
   }
 
-  XM_TRY(alloc_tiles(ctx, out, N, mask));
-  XM_TRY(pack_dense(ctx, out, P.as<double>()));
   XM_CUDA_TRY(cudaStreamSynchronize(st));
   XM_TRY(check_device_error(ctx, "Q construction"));
   if (t_build)

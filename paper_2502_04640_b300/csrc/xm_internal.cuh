@@ -47,6 +47,7 @@ enum DevErr : int {
 // the upper triangle of its block with the diagonal halved and zeros below, so that every
 // tile T contributes T Y_J to W_I and T^T Y_I to W_J (the diagonal block is T + T^T).
 constexpr int TILE = 128;
+constexpr int XM_BUILD_SPLIT_MIN_N = 512;   // XM_BUILD_AUTO: tensor-core update from this N
 constexpr int SLAB_BYTES = 16384;   // unit of one bulk async copy
 
 __host__ __device__ inline int64_t tile_count(int nt) { return (int64_t)nt * (nt + 1) / 2; }
@@ -61,6 +62,8 @@ struct DeviceQ {
   double* q64 = nullptr;            // packed FP64 tiles
   float* q32 = nullptr;             // packed FP32 tiles
   __nv_bfloat16* q16 = nullptr;     // packed BF16 tiles
+  int build_path = 0;               // XM_BUILD_* of the rank-(N-1) update that built it
+  double t_update_s = 0.0;          // device time of that update (digit split + tensor cores)
 };
 
 }  // namespace xm
@@ -84,6 +87,7 @@ struct xm_ctx {
   // cuBLAS / cuSOLVER handles for the dense FP64 translation Schur complement (lazy)
   void* cublas = nullptr;
   void* cusolver = nullptr;
+  int build_mode = 0;             // XM_BUILD_* for xm_build_Q's dense update
 };
 
 namespace xm {
@@ -98,6 +102,14 @@ xm_status ensure_partials(xm_ctx* ctx, size_t ndoubles);
 // skip: optional device flag; when non-zero the launch does nothing (early-exit of loops).
 xm_status qy_launch(xm_ctx* ctx, const DeviceQ& q, int prec, int R, const void* Y, void* W,
                     const int* skip, cudaStream_t st);
+
+// ------------------------------------------------------------------ split-BF16 update (xm_ozaki.cu)
+// Whether the tensor-core rank-K update handles K = N - 1 and n = 3N.
+bool split_update_fits(int K, int n);
+// Packed tiles of Q = P - C^T C (C column-major K x n, leading dimension ldc; P row-major n x n,
+// upper triangle) written into q's copies; acc64 is q.q64 or an FP64 tile scratch of that size.
+xm_status split_update_pack(xm_ctx* ctx, const double* C, int ldc, int K, const double* P,
+                            DeviceQ& q, double* acc64, double* t_update);
 
 // ------------------------------------------------------------------ adjoint support (xm_build.cu)
 // Index and value checks of the observation arrays (synchronous; XM_EINVAL on a bad entry).

@@ -19,6 +19,7 @@ XM_OK, XM_EINVAL, XM_EDISCONNECTED, XM_ECUDA, XM_ENOMEM, XM_ENOCONV, XM_ENUMERIC
 XM_FP64, XM_FP32_BULK, XM_BF16Q_BULK = 0, 1, 2
 XM_STORE_FP64, XM_STORE_FP32, XM_STORE_BF16, XM_STORE_ALL = 1, 2, 4, 7
 XM_MAX_RANK = 8
+XM_BUILD_AUTO, XM_BUILD_FP64, XM_BUILD_SPLIT_BF16 = 0, 1, 2
 STATUS_NAMES = {0: "XM_OK", 1: "XM_EINVAL", 2: "XM_EDISCONNECTED", 3: "XM_ECUDA", 4: "XM_ENOMEM",
                 5: "XM_ENOCONV", 6: "XM_ENUMERIC", 7: "XM_ETIMEOUT", 8: "XM_ENOTCERT"}
 
@@ -112,6 +113,9 @@ def lib() -> ctypes.CDLL:
         "xm_qmat_dims": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_uint)]),
         "xm_free_Q": (ctypes.c_int, [_P, _P]),
+        "xm_set_build_mode": (ctypes.c_int, [_P, ctypes.c_int]),
+        "xm_qmat_build_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int),
+                                              ctypes.POINTER(ctypes.c_double)]),
         "xm_qy": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, _P, _P]),
         "xm_qy_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, _P, _P]),
         "xm_bench_qy": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -238,6 +242,18 @@ def xm_build_Q(ctx: Context, N: int, M: int, cam, lmk, ukp, w, store_mask: int =
     _check(lib().xm_build_Q(ctx.h, N, M, E, _ptr(cam), _ptr(lmk), _ptr(ukp), _ptr(w), store_mask,
                             ctypes.byref(h)))
     return QMat(ctx, h)
+
+
+def xm_set_build_mode(ctx: Context, mode: int) -> None:
+    """XM_BUILD_AUTO / XM_BUILD_FP64 / XM_BUILD_SPLIT_BF16 for later xm_build_Q calls."""
+    _check(lib().xm_set_build_mode(ctx.h, mode))
+
+
+def xm_qmat_build_info(q: QMat) -> tuple[int, float]:
+    """(update path XM_BUILD_*, its device seconds) of a Q built by xm_build_Q."""
+    path, t = ctypes.c_int(), ctypes.c_double()
+    _check(lib().xm_qmat_build_info(q.h, ctypes.byref(path), ctypes.byref(t)))
+    return path.value, t.value
 
 
 def xm_qmat_from_dense(ctx: Context, Q, store_mask: int = XM_STORE_ALL) -> QMat:
