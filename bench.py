@@ -223,6 +223,78 @@ def run_sweep_only(args):
     return 0
 
 
+def update_tensor_flops(N: int) -> float:
+    """BF16 tensor FLOPs of the translation elimination on the tensor cores: 36 digit pairs
+    (levels 0..7) of (a) the rank-(N-1) product over the n(n+1)/2 entries of the upper triangle
+    and (b) the block updates of the blocked triangular solve (512-row diagonal blocks), n = 3N."""
+    n, K = 3 * N, N - 1
+    syrk = 36 * 2.0 * K * n * (n + 1) / 2
+    trsm = sum(36 * 2.0 * (K - i0 - min(512, K - i0)) * n * min(512, K - i0) for i0 in range(0, K, 512))
+    return syrk + trsm
+
+
+def update_report(N: int, path: int, t_update: float) -> dict:
+    """The build's translation elimination (triangular solve + rank-(N-1) update + packing): its
+    path, device time and, for the tensor-core path, its tensor-core roofline (BF16 peak,
+    measured burst) and FP64-equivalent rate ((n^2 K + K^2 n) / t)."""
+    n, K = 3 * N, N - 1
+    rep = {"path": {0: "none", 1: "fp64_dtrsm_dsyrk", 2: "split_bf16_tcgen05"}.get(path, str(path)),
+           "seconds": t_update,
+           "fp64_equivalent_tflops": (n * n * K + K * K * n) / t_update / 1e12 if t_update > 0 else None}
+    if path == 2 and t_update > 0:
+        pk = None
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                pk = json.load(f).get("bf16_tflops")
+        except (OSError, ValueError):
+            pk = None
+        kind = "measured" if pk else "fallback"
+        pk = pk or 1800.0
+        ach = update_tensor_flops(N) / t_update / 1e12
+        rep["roofline"] = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+                           "frac": ach / pk, "traffic": None,
+                           "kernel": "k_oz_mma<SYRK> + k_oz_mma<GEMM> block updates (+ digit splits, "
+                                     "FP64 DTRSM diagonal blocks, packing)",
+                           "flops": update_tensor_flops(N), "peak_kind": kind + " bf16 burst"}
+    return rep
+
+
+def run_build_only(args):
+    """xm_build_Q alone on a seeded random scene of N cameras (30 N landmarks, track 2+Geom(1/4),
+    5 % outliers): one warm-up, then --steps builds with the tensor-core update and one with the
+    FP64 update; prints one JSON line."""
+    import torch
+    from paper_2502_04640_b300 import xm
+    N = args.build_only
+    sc = scenes.random_scene(N, 30 * N, noise=0.02, outlier_frac=0.05, seed=1)
+    ctx = xm.Context(0)
+    tens = xm.scene_tensors(sc)
+    res = {}
+    for mode, reps in ((xm.XM_BUILD_SPLIT_BF16, max(args.steps, 1)), (xm.XM_BUILD_FP64, 1)):
+        xm.xm_set_build_mode(ctx, mode)
+        walls, upds = [], []
+        for i in range(reps + (1 if mode == xm.XM_BUILD_SPLIT_BF16 else 0)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            q = xm.xm_build_Q(ctx, sc.N, sc.M, *tens)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            path, tu = xm.xm_qmat_build_info(q)
+            q.free()
+            if mode == xm.XM_BUILD_SPLIT_BF16 and i == 0:
+                continue    # first call: library set-up
+            walls.append(wall)
+            upds.append(tu)
+        res[mode] = (statistics.median(walls), statistics.median(upds), path)
+    ws, us, ps = res[xm.XM_BUILD_SPLIT_BF16]
+    wf, uf, pf = res[xm.XM_BUILD_FP64]
+    print(json.dumps({"build_only": True, "N": N, "n": 3 * N, "E": sc.E,
+                      "split": {"build_s": ws, **update_report(N, ps, us)},
+                      "fp64": {"build_s": wf, **update_report(N, pf, uf)}}), flush=True)
+    ctx.close()
+    return 0
+
+
 def _pct(xs, q):
     return float(np.percentile(np.asarray(xs, dtype=np.float64), q)) if len(xs) else float("nan")
 
@@ -420,6 +492,9 @@ def main():
     ap.add_argument("--sweep-only", type=int, default=0, metavar="N",
                     help="time only the Q.Y sweep on a seeded random symmetric Q of N cameras "
                          "(the small case used for profiler captures)")
+    ap.add_argument("--build-only", type=int, default=0, metavar="N",
+                    help="time only xm_build_Q (tensor-core and FP64 rank-k update) on a seeded random "
+                         "scene of N cameras (also the small case for profiler captures)")
     ap.add_argument("--adjoint", action="store_true",
                     help="time xm_backward (the adjoint of the certified optimum) on --workload")
     args = ap.parse_args()
@@ -436,6 +511,8 @@ def main():
         return run_batched(args)
     if args.sweep_only:
         return run_sweep_only(args)
+    if args.build_only:
+        return run_build_only(args)
 
     import torch
     from paper_2502_04640_b300 import xm
@@ -460,6 +537,7 @@ def main():
     q = xm.xm_build_Q(ctx, sc.N, sc.M, cam, lmk, ukp, w, xm.XM_STORE_ALL)
     torch.cuda.synchronize()
     t_build = time.perf_counter() - t0
+    build_path, t_update = xm.xm_qmat_build_info(q)
     del cam, lmk, ukp, w
     torch.cuda.empty_cache()
     wopts = WORKLOAD_OPTS.get(args.workload, {})
@@ -597,6 +675,7 @@ def main():
                                            "n_sweeps", "n_sweeps_fp64", "n_outer", "n_tcg",
                                            "n_lanczos", "n_escapes", "t_cert_s")},
             "build_q_s": t_build,
+            "build_update": update_report(sc.N, build_path, t_update),
             **extra,
         }
         print(json.dumps(line), flush=True)

@@ -7,8 +7,9 @@
 //      (P = Q1 - V2 D^-1 V2^T, B = V1 - V2 D^-1 V3^T, S = Q2 - V3 D^-1 V3^T with D = Q3);
 //   3. translation elimination with the anchor t_0 = 0: Sbar = L L^T (Cholesky), C = L^-1 Bbar^T
 //      (dense FP64 factor and triangular solve from cuSOLVER / cuBLAS: the paper's "large dense
-//      matrix multiplications"), then Q = P - C^T C either by cuBLAS DSYRK (FP64 units) or by the
-//      digit-split BF16 tensor-core update of xm_ozaki.cu (FP64-accurate, XM_BUILD_SPLIT_BF16);
+//      matrix multiplications"), then Q = P - C^T C: either cuBLAS DTRSM + DSYRK (FP64 units) or,
+//      with XM_BUILD_SPLIT_BF16, the blocked triangular solve and the rank-k update of
+//      xm_ozaki.cu on the BF16 tensor cores (digit splitting, FP64-accurate);
 //   4. pack the upper triangle into the tile layout of the sweep kernel (FP64 / FP32 / BF16);
 //      the tensor-core update writes the packed tiles itself.
 // Connectivity of the view graph (rank N+M-1 of the Laplacian Q_tp, App. A lemma) is checked
@@ -396,8 +397,6 @@ xm_status build_Q(xm_ctx* ctx, int N, int M, int64_t E, const int32_t* cam, cons
       return set_error(XM_EDISCONNECTED,
                        "translation Schur block not positive definite (potrf info %d)", hinfo);
     const double one = 1.0, minus_one = -1.0;
-    XM_CUBLAS_TRY(cublasDtrsm(cb, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N,
-                              CUBLAS_DIAG_NON_UNIT, m, n, &one, Sbar, N, BbarT, N));
     bool split = false;
     if (ctx->build_mode == XM_BUILD_SPLIT_BF16) {
       if (!split_update_fits(m, n))
@@ -406,35 +405,44 @@ xm_status build_Q(xm_ctx* ctx, int N, int M, int64_t E, const int32_t* cam, cons
     } else if (ctx->build_mode == XM_BUILD_AUTO) {
       split = N >= XM_BUILD_SPLIT_MIN_N && split_update_fits(m, n);
     }
+    // C = L^{-1} Bbar^T and Q = P - C^T C, timed together (device events)
+    cudaEvent_t e0, e1;
+    XM_CUDA_TRY(cudaEventCreate(&e0));
+    XM_CUDA_TRY(cudaEventCreate(&e1));
+    XM_CUDA_TRY(cudaEventRecord(e0, st));
+    xm_status stu = XM_OK;
     if (split) {
-      // Q = P - C^T C on the tensor cores, written straight into the packed tiles
-      XM_TRY(alloc_tiles(ctx, out, N, mask));
+      // both on the tensor cores; the rank-k update writes the packed tiles itself
+      stu = split_trsm(ctx, cb, Sbar, N, BbarT, N, m, n);
+      if (stu == XM_OK) stu = alloc_tiles(ctx, out, N, mask);
       DevBuf acc;
       double* acc64 = out.q64;
-      if (!acc64) {
-        XM_CUDA_TRY(cudaMalloc(&acc.p, sizeof(double) * (size_t)out.ntiles * TILE * TILE));
+      if (stu == XM_OK && !acc64) {
+        if (cudaMalloc(&acc.p, sizeof(double) * (size_t)out.ntiles * TILE * TILE) != cudaSuccess) {
+          (void)cudaGetLastError();
+          stu = set_error(XM_ENOMEM, "split-BF16 build: FP64 tile scratch");
+        }
         acc64 = acc.as<double>();
       }
-      XM_TRY(split_update_pack(ctx, BbarT, N, m, P.as<double>(), out, acc64, &out.t_update_s));
+      if (stu == XM_OK) stu = split_update_pack(ctx, BbarT, N, m, P.as<double>(), out, acc64);
       out.build_path = XM_BUILD_SPLIT_BF16;
     } else {
-      cudaEvent_t e0, e1;
-      XM_CUDA_TRY(cudaEventCreate(&e0));
-      XM_CUDA_TRY(cudaEventCreate(&e1));
-      XM_CUDA_TRY(cudaEventRecord(e0, st));
-      XM_CUBLAS_TRY(cublasDsyrk(cb, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T, n, m, &minus_one, BbarT,
-                                N, &one, P.as<double>(), n));
-      XM_CUDA_TRY(cudaEventRecord(e1, st));
-      XM_CUDA_TRY(cudaEventSynchronize(e1));
-      float ms = 0.f;
-      XM_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
-      cudaEventDestroy(e0);
-      cudaEventDestroy(e1);
-      XM_TRY(alloc_tiles(ctx, out, N, mask));
-      XM_TRY(pack_dense(ctx, out, P.as<double>()));
-      out.t_update_s = ms * 1e-3;
+      if (cublasDtrsm(cb, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N,
+                      CUBLAS_DIAG_NON_UNIT, m, n, &one, Sbar, N, BbarT, N) != CUBLAS_STATUS_SUCCESS ||
+          cublasDsyrk(cb, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T, n, m, &minus_one, BbarT, N, &one,
+                      P.as<double>(), n) != CUBLAS_STATUS_SUCCESS)
+        stu = set_error(XM_ECUDA, "cublasDtrsm / cublasDsyrk failed");
+      if (stu == XM_OK) stu = alloc_tiles(ctx, out, N, mask);
+      if (stu == XM_OK) stu = pack_dense(ctx, out, P.as<double>());
       out.build_path = XM_BUILD_FP64;
     }
+    float ms = 0.f;
+    if (stu == XM_OK && cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess)
+      cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    XM_TRY(stu);
+    out.t_update_s = ms * 1e-3;
   } else {
     XM_TRY(alloc_tiles(ctx, out, N, mask));
     XM_TRY(pack_dense(ctx, out, P.as<double>()));

@@ -109,7 +109,11 @@ bool split_update_fits(int K, int n);
 // Packed tiles of Q = P - C^T C (C column-major K x n, leading dimension ldc; P row-major n x n,
 // upper triangle) written into q's copies; acc64 is q.q64 or an FP64 tile scratch of that size.
 xm_status split_update_pack(xm_ctx* ctx, const double* C, int ldc, int K, const double* P,
-                            DeviceQ& q, double* acc64, double* t_update);
+                            DeviceQ& q, double* acc64);
+// X <- L^{-1} X (L lower triangular m x m, X m x n, both column-major): blocked forward
+// substitution with FP64 diagonal blocks (cuBLAS handle) and tensor-core block updates.
+xm_status split_trsm(xm_ctx* ctx, void* cublas, const double* L, int ldl, double* X, int ldx,
+                     int m, int n);
 
 // ------------------------------------------------------------------ adjoint support (xm_build.cu)
 // Index and value checks of the observation arrays (synchronous; XM_EINVAL on a bad entry).

@@ -1,32 +1,39 @@
-// The dense rank-(N-1) update of the Q build on the BF16 tensor cores (tcgen05), FP64-accurate.
+// The dense FP64 contractions of the Q build on the BF16 tensor cores (tcgen05), FP64-accurate.
 //
-// Translation elimination (App. A, Prop. 1) ends with Q = P - C^T C, C = L^{-1} Bbar^T an
-// (N-1) x n matrix (L the Cholesky factor of the anchored translation block Sbar).  C^T C is
-// the one truly dense contraction of the method: n = 30465, K = N - 1 = 10154 at 10155 cameras,
-// 9.4 TFLOP in FP64, about 9 s at B300's FP64 rate.  It is computed here by the error-free
-// splitting of Ozaki, Ogita, Oishi and Rump (2012) on the BF16 tensor cores:
+// Translation elimination (App. A, Prop. 1) forms C = L^{-1} Bbar^T, an (N-1) x n matrix (L the
+// Cholesky factor of the anchored translation block Sbar), and Q = P - C^T C.  The triangular
+// solve (3 N^3 flops) and the symmetric rank-(N-1) product (9 N^3 flops: 9.4 TFLOP at 10155
+// cameras) are the method's dense contractions; at B300's FP64 rate (about 1 TFLOP/s) they take
+// 12 s.  Both run here as products on the BF16 tensor cores by the error-free splitting of
+// Ozaki, Ogita, Oishi and Rump (2012):
 //
-//   * every column c of C is written as 2^{e_c} sum_{s<8} d_{s,c} 2^{-7(s+1)} with integer
-//     digits |d| <= 127 (exact in BF16); the 8 digits hold every entry to within 2^{-56} of the
-//     largest entry of its column;
-//   * (C^T C)_{ij} = 2^{e_i+e_j} sum_{m<8} 2^{-7(m+2)} L_m(i,j), L_m = sum_{a+b=m} d_a,i . d_b,j,
-//     dropping digit products of order m >= 8 (below 2^{-56} K max|c_i| max|c_j|): normwise as
-//     accurate as an FP64 rank-k update;
-//   * each level L_m is a BF16 GEMM over the concatenated K' = (m+1) K.  Its FP32 accumulation
-//     in tensor memory is exact when at most 1024 products (each < 2^14) are summed, so the
-//     accumulation restarts every 16 k-blocks of 64 and the epilogue adds each chunk, as an
+//   * every operand vector v (a column of C or of a block of C, a row of a block of L) is written
+//     as 2^{e_v} sum_{s<8} d_s 2^{-7(s+1)} with integer digits |d_s| <= 127 (exact in BF16); the
+//     8 digits hold every entry to within 2^{-56} of the largest entry of its vector;
+//   * (u . v) = 2^{e_u+e_v} sum_{m<8} 2^{-7(m+2)} L_m, L_m = sum_{a+b=m} d_a(u) . d_b(v), dropping
+//     digit products of order m >= 8 (below 2^{-56} K max|u| max|v|): normwise as accurate as FP64;
+//   * each level L_m is a BF16 GEMM over the concatenated K' = (m+1) K whose FP32 accumulation
+//     in tensor memory is exact as long as at most 1024 products (each < 2^14) are summed: the
+//     accumulator restarts every 16 k-blocks of 64 and the epilogue adds each chunk, as an
 //     integer, to int32 registers (|L_m| < 2^31 for K <= 16640);
-//   * a finished level is scaled by an exact power of two and added in FP64 into the packed
-//     FP64 tile; after the last level the tile gets P added and is written in the sweep's
-//     packed layout (halved diagonal, zero lower triangle) in FP64, FP32 and BF16.
+//   * a finished level is scaled by an exact power of two and subtracted in FP64 from the output.
 //
-// Kernel: persistent, one CTA per SM, 128 x 128 output tiles of the upper triangle in a
-// block-row order that lets concurrent CTAs share operand k-blocks in L2.  Warp 0 streams the
-// two 128 x 64 BF16 operand boxes of each k-block with TMA (128-byte swizzle) into a 6-stage
-// mbarrier ring; one thread of warp 1 issues tcgen05.mma (M = 128, N = 128, K = 16) into one of
-// two TMEM accumulators; warps 2..9 read finished chunks with tcgen05.ld (two warps per TMEM lane
-// quarter, 64 columns each) while the next chunk accumulates in the other buffer.  Every wait is
+// Two uses of one kernel (template MODE):
+//   OZ_SYRK  Q = P - C^T C into the packed upper-triangle tiles of the sweep (FP64 accumulator
+//            tile, then P added, diagonal halved, lower triangle and padding zeroed, FP32 and
+//            BF16 copies written);
+//   OZ_GEMM  X_rest -= L_rest,i X_i, the block update of a right-looking blocked triangular
+//            solve (column-major FP64 output; the 512 x 512 diagonal blocks are solved by cuBLAS
+//            DTRSM in FP64).
+//
+// Kernel: persistent, one CTA per SM, 128 x 256 output tiles (MMA M = 128, N = 256) in an order
+// that lets concurrent CTAs share operand k-blocks in L2.  Warp 0 streams the 128 x 64 and
+// 256 x 64 BF16 operand boxes of each k-block with TMA (128-byte swizzle) into a 4-stage
+// mbarrier ring; one thread of warp 1 issues tcgen05.mma (K = 16) into one of two 256-column
+// TMEM accumulators (all 512 columns); warps 2..17 read finished chunks with tcgen05.ld (four
+// warps per TMEM lane quarter, 64 columns each) while the next chunk accumulates.  Every wait is
 // bounded; a stalled pipeline raises DEV_TIMEOUT, drains its copies and frees tensor memory.
+#include <cublas_v2.h>
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -39,25 +46,28 @@ namespace xm {
 namespace {
 
 constexpr int OZ_BM = 128;                 // tile rows (MMA M)
-constexpr int OZ_BN = 128;                 // tile columns (MMA N)
+constexpr int OZ_BN = 256;                 // tile columns (MMA N)
 constexpr int OZ_BK = 64;                  // k-block: one 128-byte swizzled row of BF16
 constexpr int OZ_BITS = 7;                 // digit magnitude bits
 constexpr int OZ_SLICES = 8;               // digits per entry = levels
 constexpr int OZ_CHUNK = 16;               // k-blocks per exact FP32 accumulation (1024 products)
-constexpr int OZ_STAGES = 6;
-constexpr int OZ_EPI_WARPS = 8;
+constexpr int OZ_STAGES = 4;
+constexpr int OZ_ACC = 2;                  // TMEM accumulators (2 x 256 columns = all 512)
+constexpr int OZ_EPI_WARPS = 16;
 constexpr int OZ_THREADS = 32 * (2 + OZ_EPI_WARPS);
-constexpr int OZ_EPI_COLS = OZ_BN / 2;     // columns per epilogue warp
+constexpr int OZ_EPI_COLS = 64;            // columns per epilogue warp
 constexpr uint32_t OZ_A_BYTES = OZ_BM * OZ_BK * 2;
 constexpr uint32_t OZ_B_BYTES = OZ_BN * OZ_BK * 2;
 constexpr uint32_t OZ_STAGE_BYTES = OZ_A_BYTES + OZ_B_BYTES;
-constexpr uint32_t OZ_TMEM_COLS = 2 * OZ_BN;   // two FP32 accumulators
-constexpr size_t OZ_SMEM = 1024 + (size_t)OZ_STAGES * OZ_STAGE_BYTES + 1024 +
-                           (size_t)OZ_EPI_WARPS * OZ_EPI_COLS * sizeof(double);
+constexpr uint32_t OZ_TMEM_COLS = OZ_ACC * OZ_BN;
+constexpr size_t OZ_SMEM = 1024 + (size_t)OZ_STAGES * OZ_STAGE_BYTES + 256;
 constexpr int64_t OZ_MAX_K = 16640;        // int32 level sums: 8 K 127^2 < 2^31
+constexpr int OZ_TRSM_BLOCK = 512;         // diagonal block of the blocked triangular solve
+
+enum { OZ_SYRK = 0, OZ_GEMM = 1 };
 
 // instruction descriptor of tcgen05.mma kind::f16: D FP32, A and B BF16, both K-major,
-// N = 128 (bits 17..22 hold N / 8), M = 128 (bits 24..28 hold M / 16)
+// N = 256 (bits 17..22 hold N / 8), M = 128 (bits 24..28 hold M / 16)
 constexpr uint32_t OZ_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BN >> 3) << 17) |
                               ((uint32_t)(OZ_BM >> 4) << 24);
 
@@ -117,19 +127,29 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
+// 8 digits of x (|x| < 1): d_s = trunc(2^7 r_s), r_{s+1} = 2^7 r_s - d_s (all steps exact)
+__device__ __forceinline__ void digits8(double x, double (&d)[OZ_SLICES]) {
+#pragma unroll
+  for (int s = 0; s < OZ_SLICES; ++s) {
+    const double t = x * (double)(1 << OZ_BITS);
+    d[s] = trunc(t);
+    x = t - d[s];
+  }
+}
+
 // ------------------------------------------------------------------ digit split
-// One warp per output index c (a column of C, K entries at C + c * ldc).  Writes the 8 digit
-// slices S[s][c][0..K_pad) (BF16, zero beyond K and for c >= n) and scale[c] = 2^{e_c} with
-// max_k |C[k][c]| < 2^{e_c}.
-__global__ void k_oz_split(const double* __restrict__ C, int ldc, int K, int n, int n_pad,
-                           int K_pad, __nv_bfloat16* __restrict__ S, size_t slice_stride,
-                           double* __restrict__ scale) {
+// Columns of a column-major matrix: one warp per vector c (K entries at V + c * ldv, c < nv).
+// Writes the digit slices S[s][c][0..K_pad) (BF16, zero beyond K and for nv <= c < rows) and
+// scale[c] = 2^{e_c} with max_k |V[k][c]| < 2^{e_c} (0 for a zero vector).
+__global__ void k_oz_split_cols(const double* __restrict__ V, int ldv, int K, int nv, int rows,
+                                int K_pad, __nv_bfloat16* __restrict__ S, size_t slice_stride,
+                                double* __restrict__ scale) {
   const int lane = threadIdx.x & 31;
   const int wpb = blockDim.x >> 5;
-  for (int c = blockIdx.x * wpb + (threadIdx.x >> 5); c < n_pad; c += gridDim.x * wpb) {
-    const double* col = C + (size_t)c * ldc;
+  for (int c = blockIdx.x * wpb + (threadIdx.x >> 5); c < rows; c += gridDim.x * wpb) {
+    const double* col = V + (size_t)c * ldv;
     double mx = 0.0;
-    if (c < n)
+    if (c < nv)
       for (int k = lane; k < K; k += 32) mx = fmax(mx, fabs(col[k]));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -138,45 +158,81 @@ __global__ void k_oz_split(const double* __restrict__ C, int ldc, int K, int n, 
     if (lane == 0) scale[c] = mx > 0.0 ? ldexp(1.0, e) : 0.0;
     __nv_bfloat16* dst = S + (size_t)c * K_pad;
     for (int k = lane; k < K_pad; k += 32) {
-      double x = (c < n && k < K && mx > 0.0) ? ldexp(col[k], -e) : 0.0;   // |x| < 1
+      double d[OZ_SLICES];
+      digits8((c < nv && k < K && mx > 0.0) ? ldexp(col[k], -e) : 0.0, d);
 #pragma unroll
-      for (int s = 0; s < OZ_SLICES; ++s) {
-        const double t = x * (double)(1 << OZ_BITS);
-        const double d = trunc(t);          // |d| <= 127, exact in BF16
-        x = t - d;                          // exact
-        dst[(size_t)s * slice_stride + k] = __double2bfloat16(d);
-      }
+      for (int s = 0; s < OZ_SLICES; ++s) dst[(size_t)s * slice_stride + k] = __double2bfloat16(d[s]);
     }
   }
 }
 
-// ------------------------------------------------------------------ rank-k update + pack
+// Rows of a column-major block: one thread per vector r (entries A[r + k * lda], k < K, r < nv);
+// same outputs as k_oz_split_cols, written 8 digits (16 bytes) at a time.
+__global__ void k_oz_split_rows(const double* __restrict__ A, int lda, int K, int nv, int rows,
+                                int K_pad, __nv_bfloat16* __restrict__ S, size_t slice_stride,
+                                double* __restrict__ scale) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x) {
+    double mx = 0.0;
+    if (r < nv)
+      for (int k = 0; k < K; ++k) mx = fmax(mx, fabs(A[r + (size_t)k * lda]));
+    int e = 0;
+    if (mx > 0.0) (void)frexp(mx, &e);
+    scale[r] = mx > 0.0 ? ldexp(1.0, e) : 0.0;
+    for (int k0 = 0; k0 < K_pad; k0 += 8) {
+      uint32_t w[OZ_SLICES][4];
+#pragma unroll
+      for (int j = 0; j < 8; j += 2) {
+        double d0[OZ_SLICES], d1[OZ_SLICES];
+        const int k = k0 + j;
+        digits8((r < nv && k < K && mx > 0.0) ? ldexp(A[r + (size_t)k * lda], -e) : 0.0, d0);
+        digits8((r < nv && k + 1 < K && mx > 0.0) ? ldexp(A[r + (size_t)(k + 1) * lda], -e) : 0.0, d1);
+#pragma unroll
+        for (int s = 0; s < OZ_SLICES; ++s) {
+          const __nv_bfloat162 p = __halves2bfloat162(__double2bfloat16(d0[s]), __double2bfloat16(d1[s]));
+          w[s][j / 2] = *reinterpret_cast<const uint32_t*>(&p);
+        }
+      }
+#pragma unroll
+      for (int s = 0; s < OZ_SLICES; ++s)
+        *reinterpret_cast<uint4*>(S + (size_t)s * slice_stride + (size_t)r * K_pad + k0) =
+            make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ digit-product kernel
 struct OzArgs {
-  const int2* tiles;        // (I, J) per work item, I <= J
+  const int2* tiles;        // (I, J) per work item: rows I*128.., columns J*256..
   int ntiles;
   int KB;                   // k-blocks per digit slice
-  int n, nt;
-  const double* scale;      // 2^{e_c}, n_pad entries
+  const double* scaleA;     // 2^{e} of the A vectors (rows of the output)
+  const double* scaleB;     // 2^{e} of the B vectors (columns of the output)
+  // OZ_SYRK
+  int n, nt;                // Q order, 128-tiles per side
   const double* P;          // row-major n x n, upper triangle valid
   double* acc64;            // packed FP64 tiles (accumulator, then result)
   float* q32;               // packed FP32 tiles or null
   __nv_bfloat16* q16;       // packed BF16 tiles or null
+  // OZ_GEMM
+  double* out;              // column-major, out[row + col * ldo] -= product
+  int ldo, M, ncols;
   int* err;
 };
 
+template <int MODE>
 __global__ void __launch_bounds__(OZ_THREADS, 1)
-k_oz_syrk(const __grid_constant__ CUtensorMap tmap, OzArgs args) {
+k_oz_mma(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+         OzArgs args) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   unsigned char* stages = base;                                   // 1024-byte aligned
   uint64_t* bars = reinterpret_cast<uint64_t*>(stages + (size_t)OZ_STAGES * OZ_STAGE_BYTES);
   uint64_t* full = bars;                       // [OZ_STAGES]
   uint64_t* empty = full + OZ_STAGES;          // [OZ_STAGES]
-  uint64_t* accfull = empty + OZ_STAGES;       // [2]
-  uint64_t* accempty = accfull + 2;            // [2]
-  uint64_t* done = accempty + 2;               // [1]
+  uint64_t* accfull = empty + OZ_STAGES;       // [OZ_ACC]
+  uint64_t* accempty = accfull + OZ_ACC;       // [OZ_ACC]
+  uint64_t* done = accempty + OZ_ACC;          // [1]
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
-  double* colscale = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(bars) + 1024);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -184,7 +240,7 @@ k_oz_syrk(const __grid_constant__ CUtensorMap tmap, OzArgs args) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < OZ_ACC; ++b) {
       mbar_init(&accfull[b], 1);
       mbar_init(&accempty[b], OZ_EPI_WARPS);
     }
@@ -219,8 +275,8 @@ k_oz_syrk(const __grid_constant__ CUtensorMap tmap, OzArgs args) {
               if (!mbar_wait(&empty[stage], phase ^ 1u)) { atomicOr(args.err, DEV_TIMEOUT); ok = false; break; }
               mbar_arrive_expect_tx(&full[stage], OZ_STAGE_BYTES);
               unsigned char* sa = stages + (size_t)stage * OZ_STAGE_BYTES;
-              tma_load_3d(sa, &tmap, kb * OZ_BK, tj.x * OZ_BM, a, &full[stage]);
-              tma_load_3d(sa + OZ_A_BYTES, &tmap, kb * OZ_BK, tj.y * OZ_BN, m - a, &full[stage]);
+              tma_load_3d(sa, &mapA, kb * OZ_BK, tj.x * OZ_BM, a, &full[stage]);
+              tma_load_3d(sa + OZ_A_BYTES, &mapB, kb * OZ_BK, tj.y * OZ_BN, m - a, &full[stage]);
               ++issued;
               if (++stage == OZ_STAGES) { stage = 0; phase ^= 1u; }
             }
@@ -241,9 +297,9 @@ k_oz_syrk(const __grid_constant__ CUtensorMap tmap, OzArgs args) {
         for (int m = 0; m < OZ_SLICES && ok; ++m) {
           const int total = (m + 1) * KB;
           for (int g = 0; g < total; ++g) {
-            const int buf = (int)(chunk & 1);
+            const int buf = (int)(chunk % OZ_ACC);
             if (g % OZ_CHUNK == 0) {
-              if (!mbar_wait(&accempty[buf], (uint32_t)(((chunk >> 1) & 1) ^ 1))) { atomicOr(args.err, DEV_TIMEOUT); ok = false; break; }
+              if (!mbar_wait(&accempty[buf], (uint32_t)(((chunk / OZ_ACC) & 1) ^ 1))) { atomicOr(args.err, DEV_TIMEOUT); ok = false; break; }
               tc_fence_after();
             }
             if (!mbar_wait(&full[stage], phase)) { atomicOr(args.err, DEV_TIMEOUT); ok = false; break; }
@@ -268,72 +324,92 @@ k_oz_syrk(const __grid_constant__ CUtensorMap tmap, OzArgs args) {
       if (!mbar_wait(done, 0)) atomicOr(args.err, DEV_TIMEOUT);
     }
   } else {
-    // ---------------- epilogue: warps 2..9
-    const int ew = warp - 2;
-    const int quarter = warp & 3;            // TMEM lanes 32q .. 32q+31
-    const int c0 = (ew >> 2) * OZ_EPI_COLS;  // first tile column of this warp
-    const int a_loc = 32 * quarter + lane;   // tile row of this thread
-    double* cs = colscale + (size_t)ew * OZ_EPI_COLS;
+    // ---------------- epilogue: warps 2..17
+    const int quarter = warp & 3;             // TMEM lanes 32q .. 32q+31
+    const int grp = (warp - 2) >> 2;          // 64-column group of the 256-column tile
+    const int a_loc = 32 * quarter + lane;    // tile row of this thread
     int64_t chunk = 0;
     bool ok = true;
     for (int w = blockIdx.x; w < args.ntiles && ok; w += gridDim.x) {
       const int2 tj = args.tiles[w];
-      const int I = tj.x, J = tj.y;
-      const int row = I * OZ_BM + a_loc;
-      const double rs = args.scale[row];
-      __syncwarp();
-      for (int c = lane; c < OZ_EPI_COLS; c += 32) cs[c] = args.scale[J * OZ_BN + c0 + c];
-      __syncwarp();
-      const int64_t t = tile_index(args.nt, I, J);
-      double* dst = args.acc64 + (size_t)t * TILE * TILE + (size_t)a_loc * TILE + c0;
+      const int row = tj.x * OZ_BM + a_loc;
+      const int col0 = tj.y * OZ_BN + grp * OZ_EPI_COLS;       // first output column
+      const double rs = args.scaleA[row];
+      const double* cs = args.scaleB + col0;                     // uniform across the warp
+      // OZ_SYRK: the packed 128 x 128 tile this warp's columns fall in
+      const int I = tj.x, J = 2 * tj.y + (grp >> 1);
+      const bool live = MODE == OZ_GEMM || (J >= I && J < args.nt);
+      const int64_t t = (MODE == OZ_SYRK && live) ? tile_index(args.nt, I, J) : 0;
+      double* dst = MODE == OZ_SYRK
+                        ? args.acc64 + (size_t)t * TILE * TILE + (size_t)a_loc * TILE + (grp & 1) * OZ_EPI_COLS
+                        : nullptr;
       for (int m = 0; m < OZ_SLICES && ok; ++m) {
         int acc[OZ_EPI_COLS];
 #pragma unroll
         for (int c = 0; c < OZ_EPI_COLS; ++c) acc[c] = 0;
         const int nchunk = ((m + 1) * KB + OZ_CHUNK - 1) / OZ_CHUNK;
         for (int q = 0; q < nchunk; ++q) {
-          const int buf = (int)(chunk & 1);
-          if (!mbar_wait(&accfull[buf], (uint32_t)((chunk >> 1) & 1))) { atomicOr(args.err, DEV_TIMEOUT); ok = false; break; }
+          const int buf = (int)(chunk % OZ_ACC);
+          if (!mbar_wait(&accfull[buf], (uint32_t)((chunk / OZ_ACC) & 1))) { atomicOr(args.err, DEV_TIMEOUT); ok = false; break; }
           tc_fence_after();
-          const uint32_t ta = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(buf * OZ_BN + c0);
+          if (live) {
+            const uint32_t ta = tmem + ((uint32_t)(32 * quarter) << 16) +
+                                (uint32_t)(buf * OZ_BN + grp * OZ_EPI_COLS);
 #pragma unroll
-          for (int p = 0; p < OZ_EPI_COLS / 16; ++p) {
-            float v[16];
-            tc_ld16(ta + 16 * p, v);
+            for (int p = 0; p < OZ_EPI_COLS / 16; ++p) {
+              float v[16];
+              tc_ld16(ta + 16 * p, v);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) acc[16 * p + i] += __float2int_rn(v[i]);
+              for (int i = 0; i < 16; ++i) acc[16 * p + i] += __float2int_rn(v[i]);
+            }
           }
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(&accempty[buf]);
           ++chunk;
         }
-        if (!ok) break;
-        // level m: tile -= 2^{e_row + e_col - 7(m+2)} L_m (exact scaling, FP64 sum)
+        if (!ok || !live) continue;
+        // level m: output -= 2^{e_row + e_col - 7(m+2)} L_m (exact scaling, FP64 subtraction)
         const double f = ldexp(rs, -OZ_BITS * (m + 2));
+        if constexpr (MODE == OZ_SYRK) {
 #pragma unroll
-        for (int c = 0; c < OZ_EPI_COLS; c += 2) {
-          double2 cur = m == 0 ? make_double2(0.0, 0.0) : *reinterpret_cast<const double2*>(dst + c);
-          cur.x -= (double)acc[c] * (f * cs[c]);
-          cur.y -= (double)acc[c + 1] * (f * cs[c + 1]);
-          *reinterpret_cast<double2*>(dst + c) = cur;
+          for (int c = 0; c < OZ_EPI_COLS; c += 2) {
+            double2 cur = m == 0 ? make_double2(0.0, 0.0) : *reinterpret_cast<const double2*>(dst + c);
+            cur.x -= (double)acc[c] * (f * cs[c]);
+            cur.y -= (double)acc[c + 1] * (f * cs[c + 1]);
+            *reinterpret_cast<double2*>(dst + c) = cur;
+          }
+        } else {
+          if (row < args.M) {
+#pragma unroll
+            for (int c = 0; c < OZ_EPI_COLS; ++c) {
+              const int col = col0 + c;
+              if (col < args.ncols) {
+                double* o = args.out + (size_t)col * args.ldo + row;   // coalesced along rows
+                *o -= (double)acc[c] * (f * cs[c]);
+              }
+            }
+          }
         }
       }
       if (!ok) break;
-      // Q = P - C^T C in the packed layout: upper triangle, halved diagonal, zero padding
-      const int n = args.n;
-      const size_t g0 = (size_t)t * TILE * TILE + (size_t)a_loc * TILE + c0;
-      for (int c = 0; c < OZ_EPI_COLS; ++c) {
-        const int b_loc = c0 + c;
-        const int col = J * OZ_BN + b_loc;
-        double v = 0.0;
-        if (row < n && col < n && (I < J || a_loc <= b_loc)) {
-          v = args.P[(size_t)row * n + col] + dst[c];
-          if (I == J && a_loc == b_loc) v *= 0.5;
+      if constexpr (MODE == OZ_SYRK) {
+        if (!live) continue;
+        // Q = P - C^T C in the packed layout: upper triangle, halved diagonal, zero padding
+        const int n = args.n;
+        const size_t g0 = (size_t)t * TILE * TILE + (size_t)a_loc * TILE + (grp & 1) * OZ_EPI_COLS;
+        for (int c = 0; c < OZ_EPI_COLS; ++c) {
+          const int b_loc = (grp & 1) * OZ_EPI_COLS + c;
+          const int col = J * TILE + b_loc;
+          double v = 0.0;
+          if (row < n && col < n && (I < J || a_loc <= b_loc)) {
+            v = args.P[(size_t)row * n + col] + dst[c];
+            if (I == J && a_loc == b_loc) v *= 0.5;
+          }
+          dst[c] = v;
+          if (args.q32) args.q32[g0 + c] = (float)v;
+          if (args.q16) args.q16[g0 + c] = __double2bfloat16(v);
         }
-        dst[c] = v;
-        if (args.q32) args.q32[g0 + c] = (float)v;
-        if (args.q16) args.q16[g0 + c] = __double2bfloat16(v);
       }
     }
   }
@@ -359,10 +435,58 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
+// 3-D map of digit slices S[8][rows][K_pad] (BF16), box of 64 k x box_rows rows x 1 slice
+xm_status slice_map(CUtensorMap* map, void* S, int K_pad, int rows, uint32_t box_rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  if (!enc) return set_error(XM_ECUDA, "cuTensorMapEncodeTiled unavailable");
+  const cuuint64_t gdim[3] = {(cuuint64_t)K_pad, (cuuint64_t)rows, (cuuint64_t)OZ_SLICES};
+  const cuuint64_t gstride[2] = {(cuuint64_t)K_pad * 2, (cuuint64_t)K_pad * 2 * (cuuint64_t)rows};
+  const cuuint32_t box[3] = {OZ_BK, box_rows, 1};
+  const cuuint32_t estride[3] = {1, 1, 1};
+  const CUresult cr = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, S, gdim, gstride, box, estride,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (cr != CUDA_SUCCESS) return set_error(XM_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)cr);
+  return XM_OK;
+}
+
+template <int MODE>
+xm_status launch_mma(xm_ctx* ctx, const CUtensorMap& ma, const CUtensorMap& mb, OzArgs a) {
+  static int configured_dev = -1;
+  if (configured_dev != ctx->device) {
+    XM_CUDA_TRY(cudaFuncSetAttribute(k_oz_mma<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)OZ_SMEM));
+    configured_dev = ctx->device;
+  }
+  const int grid = std::min(ctx->num_sms, a.ntiles);
+  if (grid < 1) return XM_OK;
+  k_oz_mma<MODE><<<grid, OZ_THREADS, OZ_SMEM, ctx->stream>>>(ma, mb, a);
+  XM_CUDA_TRY(cudaGetLastError());
+  return XM_OK;
+}
+
+// (I, J) work items: groups of 8 tile rows, column by column, so that the CTAs running at one
+// time share the operand k-blocks of a few tile rows and columns in L2.  keep(I, J) filters.
+template <typename F>
+std::vector<int2> tile_order(int nI, int nJ, F keep) {
+  std::vector<int2> order;
+  for (int I0 = 0; I0 < nI; I0 += 8)
+    for (int J = 0; J < nJ; ++J)
+      for (int I = I0; I < std::min(I0 + 8, nI); ++I)
+        if (keep(I, J)) order.push_back(make_int2(I, J));
+  return order;
+}
+
 struct DevMem {
   void* p = nullptr;
   ~DevMem() { if (p) cudaFree(p); }
+  template <typename T> T* as() { return static_cast<T*>(p); }
 };
+
+int split_grid(xm_ctx* ctx, int work, int per_block) {
+  int g = (work + per_block - 1) / per_block;
+  return std::max(1, std::min(g, ctx->num_sms * 16));
+}
 
 }  // namespace
 
@@ -372,88 +496,109 @@ bool split_update_fits(int K, int n) { return K >= 1 && K <= OZ_MAX_K && n >= 1;
 // row-major n x n (upper triangle valid).  q's tiles are allocated; acc64 is q.q64 or an FP64
 // tile scratch of the same size.
 xm_status split_update_pack(xm_ctx* ctx, const double* C, int ldc, int K, const double* P,
-                            DeviceQ& q, double* acc64, double* t_update) {
+                            DeviceQ& q, double* acc64) {
   if (!split_update_fits(K, q.n))
     return set_error(XM_EINVAL, "split-BF16 update: K = %d outside [1, %lld]", K, (long long)OZ_MAX_K);
   cudaStream_t st = ctx->stream;
   const int KB = (K + OZ_BK - 1) / OZ_BK;
   const int K_pad = KB * OZ_BK;
-  const int n_pad = q.n_pad;
-  const size_t slice_stride = (size_t)n_pad * K_pad;
+  const int nt = q.nt;
+  const int nt2 = (nt + 1) / 2;                   // 256-column tiles
+  const int rows = nt2 * OZ_BN;                   // slice rows: a multiple of 128 and 256
+  const size_t slice_stride = (size_t)rows * K_pad;
   DevMem S, scale, tl;
   XM_CUDA_TRY(cudaMalloc(&S.p, sizeof(__nv_bfloat16) * slice_stride * OZ_SLICES));
-  XM_CUDA_TRY(cudaMalloc(&scale.p, sizeof(double) * (size_t)n_pad));
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (t_update) {
-    XM_CUDA_TRY(cudaEventCreate(&e0));
-    XM_CUDA_TRY(cudaEventCreate(&e1));
-    XM_CUDA_TRY(cudaEventRecord(e0, st));
-  }
-  {
-    const int threads = 256;
-    int grid = (n_pad + threads / 32 - 1) / (threads / 32);
-    grid = std::min(grid, ctx->num_sms * 16);
-    k_oz_split<<<grid, threads, 0, st>>>(C, ldc, K, q.n, n_pad, K_pad,
-                                         static_cast<__nv_bfloat16*>(S.p), slice_stride,
-                                         static_cast<double*>(scale.p));
-    XM_CUDA_TRY(cudaGetLastError());
-  }
-  // work list: block rows of 8 tile rows, column by column, so that the CTAs running at one
-  // time share the operand k-blocks of a few tile rows and columns in L2
-  const int nt = q.nt;
-  std::vector<int2> order;
-  order.reserve((size_t)q.ntiles);
-  for (int I0 = 0; I0 < nt; I0 += 8)
-    for (int J = I0; J < nt; ++J)
-      for (int I = I0; I < std::min(I0 + 8, J + 1); ++I) order.push_back(make_int2(I, J));
+  XM_CUDA_TRY(cudaMalloc(&scale.p, sizeof(double) * (size_t)rows));
+  k_oz_split_cols<<<split_grid(ctx, rows, 8), 256, 0, st>>>(C, ldc, K, q.n, rows, K_pad,
+                                                            S.as<__nv_bfloat16>(), slice_stride,
+                                                            scale.as<double>());
+  XM_CUDA_TRY(cudaGetLastError());
+  // 128 x 256 tiles meeting the upper triangle: packed tile (I, 2J) or (I, 2J+1) with J >= I
+  std::vector<int2> order = tile_order(nt, nt2, [](int I, int J) { return 2 * J + 1 >= I; });
   XM_CUDA_TRY(cudaMalloc(&tl.p, sizeof(int2) * order.size()));
   XM_CUDA_TRY(cudaMemcpyAsync(tl.p, order.data(), sizeof(int2) * order.size(),
                               cudaMemcpyHostToDevice, st));
-
-  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
-  if (!enc) return set_error(XM_ECUDA, "cuTensorMapEncodeTiled unavailable");
-  CUtensorMap map;
-  const cuuint64_t gdim[3] = {(cuuint64_t)K_pad, (cuuint64_t)n_pad, (cuuint64_t)OZ_SLICES};
-  const cuuint64_t gstride[2] = {(cuuint64_t)K_pad * 2, (cuuint64_t)slice_stride * 2};
-  const cuuint32_t box[3] = {OZ_BK, OZ_BM, 1};
-  const cuuint32_t estride[3] = {1, 1, 1};
-  const CUresult cr = enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, S.p, gdim, gstride, box,
-                          estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (cr != CUDA_SUCCESS) return set_error(XM_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)cr);
-
-  static int configured_dev = -1;
-  if (configured_dev != ctx->device) {
-    XM_CUDA_TRY(cudaFuncSetAttribute(k_oz_syrk, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)OZ_SMEM));
-    configured_dev = ctx->device;
-  }
-  OzArgs a;
-  a.tiles = static_cast<const int2*>(tl.p);
+  CUtensorMap ma, mb;
+  XM_TRY(slice_map(&ma, S.p, K_pad, rows, OZ_BM));
+  XM_TRY(slice_map(&mb, S.p, K_pad, rows, OZ_BN));
+  OzArgs a{};
+  a.tiles = tl.as<int2>();
   a.ntiles = (int)order.size();
   a.KB = KB;
+  a.scaleA = scale.as<double>();
+  a.scaleB = scale.as<double>();
   a.n = q.n;
   a.nt = nt;
-  a.scale = static_cast<const double*>(scale.p);
   a.P = P;
   a.acc64 = acc64;
   a.q32 = q.q32;
   a.q16 = q.q16;
   a.err = ctx->d_err;
-  const int grid = std::min(ctx->num_sms, a.ntiles);
-  k_oz_syrk<<<grid, OZ_THREADS, OZ_SMEM, st>>>(map, a);
-  XM_CUDA_TRY(cudaGetLastError());
-  if (t_update) {
-    XM_CUDA_TRY(cudaEventRecord(e1, st));
-    XM_CUDA_TRY(cudaEventSynchronize(e1));
-    float ms = 0.f;
-    XM_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
-    *t_update = ms * 1e-3;
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-  }
-  XM_CUDA_TRY(cudaStreamSynchronize(st));
+  XM_TRY(launch_mma<OZ_SYRK>(ctx, ma, mb, a));
+  XM_CUDA_TRY(cudaStreamSynchronize(st));       // the order vector and buffers die here
   return check_device_error(ctx, "split-BF16 rank-k update");
+}
+
+// X <- L^{-1} X for L lower triangular m x m (column-major, leading dimension ldl) and X m x n
+// (column-major, leading dimension ldx): right-looking blocked forward substitution, the
+// diagonal blocks by cuBLAS DTRSM (FP64), the block updates X_rest -= L_rest,i X_i on the
+// tensor cores.
+xm_status split_trsm(xm_ctx* ctx, void* cublas, const double* L, int ldl, double* X, int ldx,
+                     int m, int n) {
+  cudaStream_t st = ctx->stream;
+  cublasHandle_t cb = static_cast<cublasHandle_t>(cublas);
+  const int b = OZ_TRSM_BLOCK;
+  const int K_pad = b;                                       // a multiple of OZ_BK
+  const int nJ = (n + OZ_BN - 1) / OZ_BN;
+  const int rowsB = nJ * OZ_BN;
+  const int rowsA_max = ((std::max(m - b, 1) + OZ_BM - 1) / OZ_BM) * OZ_BM;
+  DevMem SA, SB, scA, scB, tl;
+  XM_CUDA_TRY(cudaMalloc(&SA.p, sizeof(__nv_bfloat16) * (size_t)OZ_SLICES * rowsA_max * K_pad));
+  XM_CUDA_TRY(cudaMalloc(&SB.p, sizeof(__nv_bfloat16) * (size_t)OZ_SLICES * rowsB * K_pad));
+  XM_CUDA_TRY(cudaMalloc(&scA.p, sizeof(double) * (size_t)rowsA_max));
+  XM_CUDA_TRY(cudaMalloc(&scB.p, sizeof(double) * (size_t)rowsB));
+  const int nI_max = rowsA_max / OZ_BM;
+  XM_CUDA_TRY(cudaMalloc(&tl.p, sizeof(int2) * (size_t)nI_max * nJ));
+  const double one = 1.0;
+  for (int i0 = 0; i0 < m; i0 += b) {
+    const int bi = std::min(b, m - i0);
+    if (cublasDtrsm(cb, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N, CUBLAS_DIAG_NON_UNIT,
+                    bi, n, &one, L + i0 + (size_t)i0 * ldl, ldl, X + i0, ldx) != CUBLAS_STATUS_SUCCESS)
+      return set_error(XM_ECUDA, "cublasDtrsm (diagonal block %d) failed", i0 / b);
+    const int rest = m - i0 - bi;
+    if (rest == 0) break;
+    const int KB = (bi + OZ_BK - 1) / OZ_BK;
+    const int rowsA = ((rest + OZ_BM - 1) / OZ_BM) * OZ_BM;
+    const size_t strideA = (size_t)rowsA * K_pad, strideB = (size_t)rowsB * K_pad;
+    k_oz_split_rows<<<split_grid(ctx, rowsA, 128), 128, 0, st>>>(
+        L + (i0 + bi) + (size_t)i0 * ldl, ldl, bi, rest, rowsA, K_pad, SA.as<__nv_bfloat16>(),
+        strideA, scA.as<double>());
+    k_oz_split_cols<<<split_grid(ctx, rowsB, 8), 256, 0, st>>>(
+        X + i0, ldx, bi, n, rowsB, K_pad, SB.as<__nv_bfloat16>(), strideB, scB.as<double>());
+    XM_CUDA_TRY(cudaGetLastError());
+    const int nI = rowsA / OZ_BM;
+    std::vector<int2> order = tile_order(nI, nJ, [](int, int) { return true; });
+    XM_CUDA_TRY(cudaMemcpyAsync(tl.p, order.data(), sizeof(int2) * order.size(),
+                                cudaMemcpyHostToDevice, st));
+    CUtensorMap ma, mb;
+    XM_TRY(slice_map(&ma, SA.p, K_pad, rowsA, OZ_BM));
+    XM_TRY(slice_map(&mb, SB.p, K_pad, rowsB, OZ_BN));
+    OzArgs a{};
+    a.tiles = tl.as<int2>();
+    a.ntiles = (int)order.size();
+    a.KB = KB;
+    a.scaleA = scA.as<double>();
+    a.scaleB = scB.as<double>();
+    a.out = X + i0 + bi;
+    a.ldo = ldx;
+    a.M = rest;
+    a.ncols = n;
+    a.err = ctx->d_err;
+    XM_TRY(launch_mma<OZ_GEMM>(ctx, ma, mb, a));
+    // the host order vector is reused next step: the copy above must have been consumed
+    XM_CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  return check_device_error(ctx, "split-BF16 triangular solve");
 }
 
 }  // namespace xm

@@ -1,5 +1,6 @@
-"""Q built with the digit-split BF16 tensor-core update (XM_BUILD_SPLIT_BF16: the rank-(N-1)
-product C^T C of App. A's translation elimination by error-free splitting on tcgen05) against
+"""Q built on the tensor cores (XM_BUILD_SPLIT_BF16: the blocked triangular solve C = L^-1 Bbar^T
+and the rank-(N-1) product C^T C of App. A's translation elimination, by error-free digit
+splitting on tcgen05) against
 the oracle's FP64 Schur-form Q and against the FP64 DSYRK build; its packed FP32 / BF16 copies;
 the automatic choice; and a certified solve on it."""
 import numpy as np
@@ -38,6 +39,9 @@ CASES = [
     ("traj", lambda: scenes.sub_scene(scenes.trajectory_scene(300, 20000, seed=7), 120)),
     # 55 tiles; K = 399: levels of up to 56 k-blocks, several exact-accumulation chunks each
     ("chunks", lambda: scenes.random_scene(400, 8000, noise=0.02, outlier_frac=0.05, seed=8)),
+    # K = 699: a blocked triangular solve (diagonal blocks 512 + 187, one tensor-core block
+    # update with a ragged row tile); 17 tile rows, so the last 256-column tile is half outside
+    ("trsm-blocks", lambda: scenes.random_scene(700, 12000, noise=0.02, outlier_frac=0.02, seed=15)),
 ]
 
 
@@ -64,7 +68,8 @@ def test_split_build_matches_oracle(C, name, make):
 
 
 def test_split_build_large_against_fp64_build(C):
-    """K = 1499: a single digit pair spans two exact-accumulation chunks; 666 tiles."""
+    """K = 1499: a single digit pair spans two exact-accumulation chunks; three diagonal blocks
+    and two tensor-core block updates in the triangular solve."""
     from paper_2502_04640_b300 import xm
     sc = scenes.random_scene(1500, 40000, noise=0.02, outlier_frac=0.05, seed=9)
     qs = _build(C, sc, xm.XM_BUILD_SPLIT_BF16)
