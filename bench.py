@@ -49,10 +49,11 @@ DTYPES = {"fp64": "f64", "fp32": "f32", "bf16": "bf16/f32"}
 # the GPU arm of this benchmark; the reference arm multiplies the oracle's time per sweep by it.
 REFERENCE_SWEEPS = {"c3": 3076, "c2": 1500, "c4": 1500, "c1": 500}
 # DRAM bytes (read + write) over algorithmic bytes of qy_packed_kernel<float,4,8>, from one ncu
-# capture of a 12000-row case (296.8 MB / 288.2 MB per launch); the kernel streams every tile
-# once, so traffic grows in proportion to the tiles and a full launch is scaled by this ratio.
-# Must be re-measured (or set to None) whenever the sweep kernel changes.
-SWEEP_TRAFFIC_RATIO = (293.1 + 3.7) / 288.2
+# capture of a 12000-row case (296.7 MB / 288.2 MB per launch, re-measured on the kernel with
+# explicit shared-memory loads); the kernel streams every tile once, so traffic grows in
+# proportion to the tiles and a full launch is scaled by this ratio.  Must be re-measured (or
+# set to None) whenever the sweep kernel changes.
+SWEEP_TRAFFIC_RATIO = (293.1 + 3.6) / 288.2
 
 
 def peaks():
@@ -215,10 +216,28 @@ def run_sweep_only(args):
     ms, ms_min = xm.xm_bench_qy(q, xm.XM_FP32_BULK, 4, max(args.steps, 1))
     alg = sweep_bytes(n, 4, 4, 4)
     peak, kind = peaks()
-    print(json.dumps({"sweep_only": True, "N": N, "n": n, "ms": ms, "ms_min": ms_min,
-                      "GBps": alg / (ms * 1e-3) / 1e9, "frac": alg / (ms * 1e-3) / 1e9 / peak,
-                      "peak": peak, "peak_kind": kind}), flush=True)
+    line = {"sweep_only": True, "N": N, "n": n, "ms": ms, "ms_min": ms_min,
+            "GBps": alg / (ms * 1e-3) / 1e9, "frac": alg / (ms * 1e-3) / 1e9 / peak,
+            "peak": peak, "peak_kind": kind}
     q.free()
+    if args.sweep_table:
+        # every storage precision and padded width on the same Q (mean of 20 after warm-up)
+        Q = torch.randn((n, n), dtype=torch.float64, device="cuda",
+                        generator=torch.Generator(device="cuda").manual_seed(1))
+        Q = (Q + Q.T) * 0.5
+        table = {}
+        for name, store, pv, bq, by in (("fp32", xm.XM_STORE_FP32, xm.XM_FP32_BULK, 4, 4),
+                                        ("bf16", xm.XM_STORE_BF16, xm.XM_BF16Q_BULK, 2, 4),
+                                        ("fp64", xm.XM_STORE_FP64, xm.XM_FP64, 8, 8)):
+            qq = xm.xm_qmat_from_dense(ctx, Q, store)
+            for r in (1, 4, 8):
+                m_ms, _ = xm.xm_bench_qy(qq, pv, r, 20)
+                gbs = sweep_bytes(n, r, bq, by) / (m_ms * 1e-3) / 1e9
+                table[f"{name}_r{r}"] = {"us": m_ms * 1e3, "GBps": gbs, "frac": gbs / peak}
+            qq.free()
+        del Q
+        line["table"] = table
+    print(json.dumps(line), flush=True)
     ctx.close()
     return 0
 
@@ -492,6 +511,8 @@ def main():
     ap.add_argument("--sweep-only", type=int, default=0, metavar="N",
                     help="time only the Q.Y sweep on a seeded random symmetric Q of N cameras "
                          "(the small case used for profiler captures)")
+    ap.add_argument("--sweep-table", action="store_true",
+                    help="with --sweep-only: also time every storage precision at r = 1, 4, 8")
     ap.add_argument("--build-only", type=int, default=0, metavar="N",
                     help="time only xm_build_Q (tensor-core and FP64 rank-k update) on a seeded random "
                          "scene of N cameras (also the small case for profiler captures)")
