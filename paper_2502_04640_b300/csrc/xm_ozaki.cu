@@ -43,6 +43,11 @@
 #include "xm_internal.cuh"
 
 namespace xm {
+
+// cuTensorMapEncodeTiled from the driver (through the runtime's entry-point query: no libcuda
+// link); null when the driver lacks it
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
+
 namespace {
 
 constexpr int OZ_BM = 128;                 // tile rows (MMA M)
@@ -422,22 +427,9 @@ k_oz_mma(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUten
                  : "memory");
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult qr;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                         &qr) == cudaSuccess &&
-        qr == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }
-  return fn;
-}
-
 // 3-D map of digit slices S[8][rows][K_pad] (BF16), box of 64 k x box_rows rows x 1 slice
 xm_status slice_map(CUtensorMap* map, void* S, int K_pad, int rows, uint32_t box_rows) {
-  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return set_error(XM_ECUDA, "cuTensorMapEncodeTiled unavailable");
   const cuuint64_t gdim[3] = {(cuuint64_t)K_pad, (cuuint64_t)rows, (cuuint64_t)OZ_SLICES};
   const cuuint64_t gstride[2] = {(cuuint64_t)K_pad * 2, (cuuint64_t)K_pad * 2 * (cuuint64_t)rows};
@@ -491,6 +483,19 @@ int split_grid(xm_ctx* ctx, int work, int per_block) {
 }  // namespace
 
 bool split_update_fits(int K, int n) { return K >= 1 && K <= OZ_MAX_K && n >= 1; }
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult qr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &qr) == cudaSuccess &&
+        qr == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
 
 // Q tiles <- pack(P - C^T C); C column-major K x n with leading dimension ldc (device), P
 // row-major n x n (upper triangle valid).  q's tiles are allocated; acc64 is q.q64 or an FP64

@@ -17,6 +17,11 @@
 //     on a global load; each warp adds its column partials to W_J with vector reductions (no
 //     barrier between warps inside a tile row); row partials are kept per tile row in registers
 //     (FP32/BF16, R = 4) and reduced across lanes once per tile row.
+#include <cuda.h>
+#include <cstring>
+#include <mutex>
+#include <cudaTypedefs.h>
+
 #include "xm_internal.cuh"
 
 namespace xm {
@@ -69,6 +74,16 @@ __device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsign
   return d;
 }
 
+// 2-D tensor copy global -> shared (TMA), completion on an mbarrier; x must be 16-byte aligned
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
 // W[0..3] += (a, b, c, d) with one vector reduction (16-byte aligned address)
 __device__ __forceinline__ void red_add4(float* w, float a, float b, float c, float d) {
   asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(w), "f"(a), "f"(b), "f"(c),
@@ -100,7 +115,24 @@ __device__ __forceinline__ T transpose_reduce(T (&v)[V], int lane) {
   return x;
 }
 
-template <typename TQ, int R, int NW>
+// Traversal order of the tiles: tile rows 0, nt-1, 1, nt-2, ... (a long row, then the short row
+// that completes it to nt + 1 tiles), each row from its diagonal tile outwards.  Every CTA takes a
+// contiguous range of this order, so each crosses one to three row boundaries (a row change costs
+// a flush of the row partials and a Y_I reload), where row-major order left the CTA holding the
+// last, shortest rows with a dozen or more.
+__device__ __forceinline__ void pair_order_start(int nt, int64_t v, int& I, int& J) {
+  const int64_t P = (int64_t)nt + 1;
+  const int p = (int)(v / P), rem = (int)(v % P);
+  if (rem < nt - p) { I = p; J = p + rem; }
+  else { I = nt - 1 - p; J = I + (rem - (nt - p)); }
+}
+__device__ __forceinline__ void pair_order_next(int nt, int& I, int& J) {
+  if (++J < nt) return;
+  I = (2 * I < nt - 1) ? nt - 1 - I : nt - I;   // long row p -> short row nt-1-p -> long row p+1
+  J = I;
+}
+
+template <typename TQ, int R, int NW, bool SW>
 struct SweepCfg {
   using A = typename QT<TQ>::A;
   static constexpr int ROWS = QT<TQ>::ROWS;           // rows per slab
@@ -118,25 +150,32 @@ struct SweepCfg {
   static constexpr size_t YSM_BYTES = sizeof(A) * TILE * R * (PAIR ? 2 : 1);
   static constexpr int YJ_SLOTS = 4;                       // ring of Y_J tiles
   static constexpr uint32_t YJ_BYTES = sizeof(A) * TILE * R;
+  // SW: Y_J arrives by a 2-D tensor copy with the 128-byte swizzle (Y viewed as rows of 32
+  // floats); lane l then reads its 4 rows (R = 4: 64 bytes, R = 8: 128 bytes) with 16-byte loads
+  // that hit distinct banks.  A contiguous copy would put the lanes 64 (128) bytes apart: a
+  // 16-way bank conflict at the start of every tile, in all consumer warps at once.
+  static_assert(!SW || (sizeof(A) == 4 && (R == 4 || R == 8)), "swizzled Y_J: FP32, R = 4 or 8");
+  static constexpr int YV_ROWS = TILE * R / 32;            // 32-float rows of one Y_J tile
   static size_t smem_bytes(int nstage) {
-    return 128 + (size_t)nstage * SLAB_BYTES + YSM_BYTES + (size_t)YJ_SLOTS * YJ_BYTES +
+    return 1024 + (size_t)nstage * SLAB_BYTES + YSM_BYTES + (size_t)YJ_SLOTS * YJ_BYTES +
            16 * (size_t)(nstage + YJ_SLOTS);
   }
 };
 
-template <typename TQ, int R, int NW>
-__global__ void __launch_bounds__(SweepCfg<TQ, R, NW>::THREADS, 1)
+template <typename TQ, int R, int NW, bool SW>
+__global__ void __launch_bounds__(SweepCfg<TQ, R, NW, SW>::THREADS, 1)
 qy_packed_kernel(const TQ* __restrict__ tiles, int nt, int64_t ntiles, int nstage,
                  const typename QT<TQ>::A* __restrict__ Y, typename QT<TQ>::A* __restrict__ W,
-                 int* err, const int* skip) {
-  using C = SweepCfg<TQ, R, NW>;
+                 int* err, const int* skip, const __grid_constant__ CUtensorMap ymap) {
+  using C = SweepCfg<TQ, R, NW, SW>;
   using A = typename C::A;
   if (skip != nullptr && *skip != 0) return;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  // 128-byte alignment as an offset into the shared array (an integer round trip of the
-  // pointer would hide its address space and turn every shared load into a generic load)
-  unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+  // 1024-byte alignment (the swizzle pattern of a Y_J slot) as an offset into the shared array
+  // (an integer round trip of the pointer would hide its address space and turn every shared
+  // load into a generic load); slabs and Y_I staging are multiples of 1024 bytes
+  unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   unsigned char* stages = base;
   A* ysm = reinterpret_cast<A*>(stages + (size_t)nstage * SLAB_BYTES);
   A* yjs = reinterpret_cast<A*>(reinterpret_cast<unsigned char*>(ysm) + C::YSM_BYTES);
@@ -164,19 +203,14 @@ qy_packed_kernel(const TQ* __restrict__ tiles, int nt, int64_t ntiles, int nstag
   __syncthreads();
   if (t0 >= t1) return;
 
-  // first tile coordinates of this CTA's range
-  int I0 = 0;
-  {
-    int64_t rem = t0;
-    while (rem >= nt - I0) { rem -= nt - I0; ++I0; }
-  }
-  const int J0 = I0 + (int)(t0 - tile_index(nt, I0, I0));
+  // first tile coordinates of this CTA's range (in the paired row order)
+  int I0, J0;
+  pair_order_start(nt, t0, I0, J0);
 
   if (warp == NW) {
     // ---------------- producer: one thread streams, per tile, Y_J then the tile's slabs
     if (lane == 0) {
-      const unsigned char* src = reinterpret_cast<const unsigned char*>(tiles) +
-                                 (size_t)t0 * C::SLABS * SLAB_BYTES;
+      const unsigned char* qsrc = reinterpret_cast<const unsigned char*>(tiles);
       const unsigned char* ysrc = reinterpret_cast<const unsigned char*>(Y);
       int stage = 0, ys = 0;
       uint32_t phase = 0, yphase = 0;
@@ -186,18 +220,23 @@ qy_packed_kernel(const TQ* __restrict__ tiles, int nt, int64_t ntiles, int nstag
       for (int64_t t = t0; t < t1 && good; ++t) {
         if (!mbar_wait(&emptyy[ys], yphase ^ 1u)) { atomicOr(err, DEV_TIMEOUT); break; }
         mbar_arrive_expect_tx(&fully[ys], C::YJ_BYTES);
-        bulk_g2s(reinterpret_cast<unsigned char*>(yjs) + (size_t)ys * C::YJ_BYTES,
-                 ysrc + (size_t)Jp * C::YJ_BYTES, C::YJ_BYTES, &fully[ys]);
+        if constexpr (SW)
+          tma_load_2d(reinterpret_cast<unsigned char*>(yjs) + (size_t)ys * C::YJ_BYTES, &ymap, 0,
+                      Jp * C::YV_ROWS, &fully[ys]);
+        else
+          bulk_g2s(reinterpret_cast<unsigned char*>(yjs) + (size_t)ys * C::YJ_BYTES,
+                   ysrc + (size_t)Jp * C::YJ_BYTES, C::YJ_BYTES, &fully[ys]);
         ++yissued;
         if (++ys == C::YJ_SLOTS) { ys = 0; yphase ^= 1u; }
+        const unsigned char* src = qsrc + (size_t)tile_index(nt, Ip, Jp) * C::SLABS * SLAB_BYTES;
         for (int sl = 0; sl < C::SLABS; ++sl, ++issued) {
           if (!mbar_wait(&empty[stage], phase ^ 1u)) { atomicOr(err, DEV_TIMEOUT); good = false; break; }
           mbar_arrive_expect_tx(&full[stage], SLAB_BYTES);
-          bulk_g2s(stages + (size_t)stage * SLAB_BYTES, src + (size_t)issued * SLAB_BYTES,
-                   SLAB_BYTES, &full[stage]);
+          bulk_g2s(stages + (size_t)stage * SLAB_BYTES, src + (size_t)sl * SLAB_BYTES, SLAB_BYTES,
+                   &full[stage]);
           if (++stage == nstage) { stage = 0; phase ^= 1u; }
         }
-        if (++Jp == nt) { ++Ip; Jp = Ip; }
+        pair_order_next(nt, Ip, Jp);
       }
       // Drain: do not leave while copies into this CTA's shared memory are in flight.
       for (int64_t k = issued > nstage ? issued - nstage : 0; k < issued; ++k) {
@@ -308,7 +347,31 @@ qy_packed_kernel(const TQ* __restrict__ tiles, int nt, int64_t ntiles, int nstag
     {
       if (ok && !mbar_wait(&fully[ysl], yphase)) { atomicOr(err, DEV_TIMEOUT); ok = false; }
       const A* yp = yjs + (size_t)ysl * (TILE * R) + (size_t)(4 * lane) * R;
-      if constexpr (C::PAIR) {
+      if constexpr (SW) {
+        // swizzled slot: 16-byte chunk k of 32-float row v sits at chunk k ^ (v & 7)
+        const unsigned char* slot = reinterpret_cast<const unsigned char*>(yjs) + (size_t)ysl * C::YJ_BYTES;
+        if constexpr (R == 4) {
+          const int v = lane >> 1;                       // rows 4l..4l+3 = chunks 4(l&1)..+3 of row v
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const float4 t = *reinterpret_cast<const float4*>(
+                slot + v * 128 + 16 * ((4 * (lane & 1) + c) ^ (v & 7)));
+            yjp[c][0] = pk(t.x, t.y);
+            yjp[c][1] = pk(t.z, t.w);
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {                  // rows 4l..4l+3 = the 8 chunks of row l
+            const float4 t = *reinterpret_cast<const float4*>(slot + lane * 128 + 16 * (k ^ (lane & 7)));
+            yjp[k >> 1][2 * (k & 1)] = pk(t.x, t.y);
+            yjp[k >> 1][2 * (k & 1) + 1] = pk(t.z, t.w);
+          }
+        }
+#pragma unroll
+        for (int cp = 0; cp < 2; ++cp)
+#pragma unroll
+          for (int j = 0; j < R; ++j) colp[cp][j] = 0ull;
+      } else if constexpr (C::PAIR) {
 #pragma unroll
         for (int c = 0; c < 4; ++c)
 #pragma unroll
@@ -441,16 +504,48 @@ qy_packed_kernel(const TQ* __restrict__ tiles, int nt, int64_t ntiles, int nstag
           for (int j = 0; j < R; ++j) atomicAdd(&wj[c * R + j], colacc[c][j]);
       }
     }
-    if (++J == nt) { ++I; J = I; }
+    pair_order_next(nt, I, J);
   }
   if (curI >= 0) flush_rows(curI);
 }
 
 // ------------------------------------------------------------------ host launcher
-template <typename TQ, int R, int NW>
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
+
+// 2-D map of an FP32 n_pad x R row-major Y viewed as rows of 32 floats, box = one Y_J tile,
+// 128-byte swizzle.  Maps are cached by (address, rows, R) (the solver reuses a few buffers);
+// false when Y is not 16-byte aligned or the driver cannot encode one.
+static bool y_swizzle_map(const void* Y, int n_pad, int R, CUtensorMap* out) {
+  struct Entry { const void* y; int n_pad, R; CUtensorMap map; };
+  static Entry cache[16];
+  static int used = 0, next = 0;
+  static std::mutex mu;   // contexts may be driven from different host threads
+  if ((reinterpret_cast<uintptr_t>(Y) & 15u) != 0) return false;
+  std::lock_guard<std::mutex> lock(mu);
+  for (int i = 0; i < used; ++i)
+    if (cache[i].y == Y && cache[i].n_pad == n_pad && cache[i].R == R) { *out = cache[i].map; return true; }
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  const cuuint64_t gdim[2] = {32, (cuuint64_t)n_pad * R / 32};
+  const cuuint64_t gstride[1] = {128};
+  const cuuint32_t box[2] = {32, (cuuint32_t)(TILE * R / 32)};
+  const cuuint32_t estride[2] = {1, 1};
+  CUtensorMap m;
+  if (enc(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(Y), gdim, gstride, box, estride,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return false;
+  cache[next] = Entry{Y, n_pad, R, m};
+  next = (next + 1) % 16;
+  if (used < 16) ++used;
+  *out = m;
+  return true;
+}
+
+template <typename TQ, int R, int NW, bool SW>
 static xm_status launch_t(xm_ctx* ctx, const TQ* tiles, const DeviceQ& q, const void* Y, void* W,
-                          const int* skip, cudaStream_t st) {
-  using C = SweepCfg<TQ, R, NW>;
+                          const int* skip, cudaStream_t st, const CUtensorMap& ymap) {
+  using C = SweepCfg<TQ, R, NW, SW>;
   using A = typename C::A;
   static int configured_dev = -1;
   static int nstage_cfg = 0;
@@ -459,7 +554,7 @@ static xm_status launch_t(xm_ctx* ctx, const TQ* tiles, const DeviceQ& q, const 
     int ns = (int)((ctx->smem_optin - fixed) / (SLAB_BYTES + 16));
     if (ns > 12) ns = 12;
     if (ns < 2) return set_error(XM_ECUDA, "sweep: not enough shared memory (%zu)", ctx->smem_optin);
-    XM_CUDA_TRY(cudaFuncSetAttribute(qy_packed_kernel<TQ, R, NW>,
+    XM_CUDA_TRY(cudaFuncSetAttribute(qy_packed_kernel<TQ, R, NW, SW>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)C::smem_bytes(ns)));
     nstage_cfg = ns;
@@ -467,9 +562,9 @@ static xm_status launch_t(xm_ctx* ctx, const TQ* tiles, const DeviceQ& q, const 
   }
   int grid = ctx->num_sms;
   if ((int64_t)grid > q.ntiles) grid = (int)q.ntiles;
-  qy_packed_kernel<TQ, R, NW><<<grid, C::THREADS, C::smem_bytes(nstage_cfg), st>>>(
+  qy_packed_kernel<TQ, R, NW, SW><<<grid, C::THREADS, C::smem_bytes(nstage_cfg), st>>>(
       tiles, q.nt, q.ntiles, nstage_cfg, static_cast<const A*>(Y), static_cast<A*>(W),
-      ctx->d_err, skip);
+      ctx->d_err, skip, ymap);
   XM_CUDA_TRY(cudaGetLastError());
   return XM_OK;
 }
@@ -477,10 +572,20 @@ static xm_status launch_t(xm_ctx* ctx, const TQ* tiles, const DeviceQ& q, const 
 template <typename TQ, int NW>
 static xm_status dispatch_r(xm_ctx* ctx, const TQ* tiles, const DeviceQ& q, int R, const void* Y,
                             void* W, const int* skip, cudaStream_t st) {
+  CUtensorMap m;
+  std::memset(&m, 0, sizeof(m));
+  constexpr bool f32 = sizeof(typename QT<TQ>::A) == 4;
+  const bool sw = f32 && (R == 4 || R == 8) && y_swizzle_map(Y, q.n_pad, R, &m);
   switch (R) {
-    case 1: return launch_t<TQ, 1, NW>(ctx, tiles, q, Y, W, skip, st);
-    case 4: return launch_t<TQ, 4, NW>(ctx, tiles, q, Y, W, skip, st);
-    case 8: return launch_t<TQ, 8, NW>(ctx, tiles, q, Y, W, skip, st);
+    case 1: return launch_t<TQ, 1, NW, false>(ctx, tiles, q, Y, W, skip, st, m);
+    case 4:
+      if constexpr (f32)
+        if (sw) return launch_t<TQ, 4, NW, true>(ctx, tiles, q, Y, W, skip, st, m);
+      return launch_t<TQ, 4, NW, false>(ctx, tiles, q, Y, W, skip, st, m);
+    case 8:
+      if constexpr (f32)
+        if (sw) return launch_t<TQ, 8, NW, true>(ctx, tiles, q, Y, W, skip, st, m);
+      return launch_t<TQ, 8, NW, false>(ctx, tiles, q, Y, W, skip, st, m);
     default: return set_error(XM_EINVAL, "sweep: padded width %d not in {1,4,8}", R);
   }
 }

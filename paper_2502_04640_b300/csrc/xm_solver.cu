@@ -218,6 +218,8 @@ struct Solver {
   // stats
   xm_info info{};
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaEvent_t fev[2] = {nullptr, nullptr};   // tCG chunk flags: one chunk in flight ahead
+  int* h_flags = nullptr;                     // pinned, 2 slots
   double ms32 = 0, ms64 = 0;
   int n32 = 0, n64 = 0;
   long launches = 0;
@@ -239,6 +241,8 @@ struct Solver {
     if (h_sc) cudaFreeHost(h_sc);
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
+    for (cudaEvent_t e : fev) if (e) cudaEventDestroy(e);
+    if (h_flags) cudaFreeHost(h_flags);
   }
 
   xm_status alloc() {
@@ -260,6 +264,8 @@ struct Solver {
     XM_CUDA_TRY(cudaMemsetAsync(d_small, 0, 256 * sizeof(double), st));
     XM_CUDA_TRY(cudaEventCreate(&ev0));
     XM_CUDA_TRY(cudaEventCreate(&ev1));
+    for (cudaEvent_t& e : fev) XM_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    XM_CUDA_TRY(cudaMallocHost(&h_flags, 2 * sizeof(int)));
     XM_TRY(ensure_partials(ctx, (size_t)std::max(nb_cam, 1024) * 64));
     if (o.precond) {
       XM_CUDA_TRY(cudaMalloc(&pcMinv, sizeof(double) * 9 * (size_t)N));
@@ -384,8 +390,12 @@ struct Solver {
           o.max_tcg, 1.0, 0.1, ctx->d_partials, ctx->d_counter);
       ++launches;
       XM_CUDA_TRY(cudaGetLastError());
+      // Chunks of CH iterations; the host reads the done flag of chunk k-1 while chunk k is
+      // already queued, so the device never waits for the host.  A chunk queued after the
+      // device set done is a no-op (every kernel of the loop returns on done).
       const int CH = 4;
-      int done = 0;
+      int done = 0, slot = 0;
+      bool pending = false;
       for (int j = 0; j < o.max_tcg && !done; j += CH) {
         for (int c = 0; c < CH; ++c) {
           XM_TRY(sweep(prec_hvp, R, bD, bWd, &d_sc->done, false));
@@ -399,9 +409,14 @@ struct Solver {
           launches += 3;
         }
         XM_CUDA_TRY(cudaGetLastError());
-        XM_CUDA_TRY(cudaMemcpyAsync(&h_sc->done, &d_sc->done, sizeof(int), cudaMemcpyDeviceToHost, st));
-        XM_CUDA_TRY(cudaStreamSynchronize(st));
-        done = h_sc->done;
+        XM_CUDA_TRY(cudaMemcpyAsync(&h_flags[slot], &d_sc->done, sizeof(int), cudaMemcpyDeviceToHost, st));
+        XM_CUDA_TRY(cudaEventRecord(fev[slot], st));
+        if (pending) {
+          XM_CUDA_TRY(cudaEventSynchronize(fev[slot ^ 1]));
+          done = h_flags[slot ^ 1];
+        }
+        pending = true;
+        slot ^= 1;
       }
       k_model_terms<To, Ti, R><<<grid_elems(rows * R), CAM_THREADS, 0, st>>>(
           (int)rows, (const To*)bG, (const Ti*)bEta, (const Ti*)bHeta, d_sc, ctx->d_partials,
