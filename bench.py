@@ -48,12 +48,12 @@ DTYPES = {"fp64": "f64", "fp32": "f32", "bf16": "bf16/f32"}
 # Sweeps of one certified FP32-bulk solve of the 10155-camera workload as measured on a B300 by
 # the GPU arm of this benchmark; the reference arm multiplies the oracle's time per sweep by it.
 REFERENCE_SWEEPS = {"c3": 3076, "c2": 1500, "c4": 1500, "c1": 500}
-# DRAM bytes (read + write) over algorithmic bytes of qy_packed_kernel<float,4,8>, from one ncu
-# capture of a 12000-row case (296.7 MB / 288.2 MB per launch, re-measured on the kernel with
-# explicit shared-memory loads); the kernel streams every tile once, so traffic grows in
-# proportion to the tiles and a full launch is scaled by this ratio.  Must be re-measured (or
-# set to None) whenever the sweep kernel changes.
-SWEEP_TRAFFIC_RATIO = (293.1 + 3.6) / 288.2
+# DRAM bytes (read + write) over algorithmic bytes of qy_packed_kernel<float,4,8> from one ncu
+# capture at the 10155-camera size itself (n = 30465: 1.8832 GB read + 0.0040 GB written per
+# launch against 1.8573 GB algorithmic), on the kernel as it stands (swizzled Y_J, paired
+# tile-row order).  The kernel streams every tile once, so other sizes scale the same ratio by
+# the tiles.  Must be re-measured (or set to None) whenever the sweep kernel changes.
+SWEEP_TRAFFIC_RATIO = (1.883209 + 0.003997) / 1.857268
 
 
 def peaks():
@@ -617,8 +617,8 @@ def main():
     traffic = alg * SWEEP_TRAFFIC_RATIO if prec == 1 and SWEEP_TRAFFIC_RATIO else None
     roofline = {"bound": "hbm" if prec != 0 else "alu", "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                "traffic_note": "ncu DRAM read+write of a 12000-row capture, scaled per tile"
-                                if traffic else None,
+                "traffic_note": "ncu DRAM read+write of one launch at n = 30465 (the same sweep "
+                                "size), as a ratio to the algorithmic bytes" if traffic else None,
                 "kernel": f"qy_packed_kernel<{'double' if prec == 0 else 'float'},4,8>",
                 "bytes_per_launch": alg, "launch_ms": qy_ms, "peak_kind": peak_kind}
 

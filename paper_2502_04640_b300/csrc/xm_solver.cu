@@ -220,6 +220,8 @@ struct Solver {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   cudaEvent_t fev[2] = {nullptr, nullptr};   // tCG chunk flags: one chunk in flight ahead
   int* h_flags = nullptr;                     // pinned, 2 slots
+  cudaStream_t cap_st = nullptr;              // side stream on which tCG chunks are captured
+  bool use_graphs = true;                     // cleared if a capture ever fails
   double ms32 = 0, ms64 = 0;
   int n32 = 0, n64 = 0;
   long launches = 0;
@@ -243,6 +245,7 @@ struct Solver {
     if (ev1) cudaEventDestroy(ev1);
     for (cudaEvent_t e : fev) if (e) cudaEventDestroy(e);
     if (h_flags) cudaFreeHost(h_flags);
+    if (cap_st) cudaStreamDestroy(cap_st);
   }
 
   xm_status alloc() {
@@ -266,6 +269,7 @@ struct Solver {
     XM_CUDA_TRY(cudaEventCreate(&ev1));
     for (cudaEvent_t& e : fev) XM_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     XM_CUDA_TRY(cudaMallocHost(&h_flags, 2 * sizeof(int)));
+    XM_CUDA_TRY(cudaStreamCreateWithFlags(&cap_st, cudaStreamNonBlocking));
     XM_TRY(ensure_partials(ctx, (size_t)std::max(nb_cam, 1024) * 64));
     if (o.precond) {
       XM_CUDA_TRY(cudaMalloc(&pcMinv, sizeof(double) * 9 * (size_t)N));
@@ -374,6 +378,20 @@ struct Solver {
     const double eps_reg = std::is_same<To, float>::value ? 1e2 * 1.1920929e-07
                                                           : 1e3 * 2.220446049250313e-16;
     int rejects = 0;
+    // captured tCG chunks of this call, keyed by the (iterate, Lambda) buffers they read
+    struct ChunkGraph { const void* yin; const double* lam; cudaGraphExec_t exec; };
+    struct GraphCache {
+      ChunkGraph e[2] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+      int n = 0;
+      cudaStream_t s = nullptr;
+      ~GraphCache() {
+        if (n > 0) cudaStreamSynchronize(s);   // no launch of these graphs still in flight
+        for (int i = 0; i < n; ++i) cudaGraphExecDestroy(e[i].exec);
+      }
+    } gcache;
+    gcache.s = st;
+    ChunkGraph* cg = gcache.e;
+    int& ncg = gcache.n;
     for (int k = 0; k < max_outer; ++k) {
       if (std::sqrt(g2) <= tol_abs) break;
       if (over_time()) break;
@@ -392,23 +410,61 @@ struct Solver {
       XM_CUDA_TRY(cudaGetLastError());
       // Chunks of CH iterations; the host reads the done flag of chunk k-1 while chunk k is
       // already queued, so the device never waits for the host.  A chunk queued after the
-      // device set done is a no-op (every kernel of the loop returns on done).
+      // device set done is a no-op (every kernel of the loop returns on done).  From the second
+      // chunk on, a chunk is one CUDA graph (captured on a side stream, replayed on st): its
+      // 4 CH kernels then start back to back without a host launch each.  The iterate and Lam
+      // alternate between two buffers as steps are accepted, so at most two graphs per call.
       const int CH = 4;
       int done = 0, slot = 0;
       bool pending = false;
-      for (int j = 0; j < o.max_tcg && !done; j += CH) {
+      auto launch_chunk = [&](cudaStream_t cst) -> xm_status {
         for (int c = 0; c < CH; ++c) {
-          XM_TRY(sweep(prec_hvp, R, bD, bWd, &d_sc->done, false));
-          k_hvp_epi<Ti, R><<<nb_cam, CAM_THREADS, 0, st>>>(N, Yin, (Ti*)bWd, (const Ti*)bD, (Ti*)bHd,
+          XM_TRY(qy_launch(ctx, q, prec_hvp, R, bD, bWd, &d_sc->done, cst));
+          k_hvp_epi<Ti, R><<<nb_cam, CAM_THREADS, 0, cst>>>(N, Yin, (Ti*)bWd, (const Ti*)bD, (Ti*)bHd,
                                                            Lam, d_sc, ctx->d_partials, ctx->d_counter);
-          k_tcg_update<Ti, R><<<nb_cam, CAM_THREADS, 0, st>>>(N, Yin, (Ti*)bEta, (Ti*)bHeta, (Ti*)bR,
+          k_tcg_update<Ti, R><<<nb_cam, CAM_THREADS, 0, cst>>>(N, Yin, (Ti*)bEta, (Ti*)bHeta, (Ti*)bR,
                                                               (Ti*)bZ, (const Ti*)bD, (const Ti*)bHd,
                                                               pcMinv, d_sc, ctx->d_partials,
                                                               ctx->d_counter);
-          k_tcg_dir<Ti, R><<<nb_cam, CAM_THREADS, 0, st>>>(N, (const Ti*)bZ, (Ti*)bD, d_sc);
-          launches += 3;
+          k_tcg_dir<Ti, R><<<nb_cam, CAM_THREADS, 0, cst>>>(N, (const Ti*)bZ, (Ti*)bD, d_sc);
         }
         XM_CUDA_TRY(cudaGetLastError());
+        return XM_OK;
+      };
+      auto chunk_exec = [&]() -> cudaGraphExec_t {
+        for (int i = 0; i < ncg; ++i)
+          if (cg[i].yin == Yin && cg[i].lam == Lam) return cg[i].exec;
+        if (cudaStreamBeginCapture(cap_st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+          (void)cudaGetLastError();
+          return nullptr;
+        }
+        const xm_status sc_ = launch_chunk(cap_st);
+        cudaGraph_t g = nullptr;
+        const cudaError_t ee = cudaStreamEndCapture(cap_st, &g);
+        cudaGraphExec_t ex = nullptr;
+        if (sc_ != XM_OK || ee != cudaSuccess || !g || cudaGraphInstantiate(&ex, g, 0) != cudaSuccess)
+          ex = nullptr;
+        if (g) cudaGraphDestroy(g);
+        (void)cudaGetLastError();
+        if (!ex) return nullptr;
+        if (ncg == 2) { cudaGraphExecDestroy(cg[0].exec); cg[0] = cg[1]; ncg = 1; }
+        cg[ncg++] = ChunkGraph{Yin, Lam, ex};
+        return ex;
+      };
+      xm_status chunk_status = XM_OK;
+      for (int j = 0; j < o.max_tcg && !done; j += CH) {
+        cudaGraphExec_t ex = (j > 0 && use_graphs) ? chunk_exec() : nullptr;
+        if (j > 0 && use_graphs && !ex) use_graphs = false;
+        if (ex) {
+          if (cudaGraphLaunch(ex, st) != cudaSuccess) {
+            chunk_status = set_error(XM_ECUDA, "tCG chunk graph launch failed");
+            break;
+          }
+        } else {
+          chunk_status = launch_chunk(st);
+          if (chunk_status != XM_OK) break;
+        }
+        launches += 4 * CH;
         XM_CUDA_TRY(cudaMemcpyAsync(&h_flags[slot], &d_sc->done, sizeof(int), cudaMemcpyDeviceToHost, st));
         XM_CUDA_TRY(cudaEventRecord(fev[slot], st));
         if (pending) {
@@ -418,6 +474,7 @@ struct Solver {
         pending = true;
         slot ^= 1;
       }
+      XM_TRY(chunk_status);
       k_model_terms<To, Ti, R><<<grid_elems(rows * R), CAM_THREADS, 0, st>>>(
           (int)rows, (const To*)bG, (const Ti*)bEta, (const Ti*)bHeta, d_sc, ctx->d_partials,
           ctx->d_counter);
@@ -429,6 +486,10 @@ struct Solver {
       XM_TRY(pull_scalars());
       ++info.n_outer;
       info.n_tcg += h_sc->iters;
+      // one Hessian-vector sweep per tCG iteration (the sweeps of chunks queued after the
+      // device stopped returned at once and are not counted)
+      info.n_sweeps += h_sc->iters;
+      if (prec_hvp == XM_FP64) info.n_sweeps_fp64 += h_sc->iters;
       const double fc = h_sc->fc;
       const double model_dec = -(h_sc->g_eta + 0.5 * h_sc->eta_Heta);
       const double reg = std::max(1.0, std::fabs(f)) * eps_reg;
