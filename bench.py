@@ -589,8 +589,11 @@ def main():
     launches = 0
     timed = []
     out = None
+    per_step = []
     for _ in range(args.steps):
-        out = xm.xm_solve(q, opts)
+        ts = time.perf_counter()
+        out = xm.xm_solve(q, opts)     # synchronises before returning
+        per_step.append(time.perf_counter() - ts)
         launches += xm.xm_last_launch_count()
         timed.append(out["info"])
     ev1.record(stream)
@@ -695,6 +698,9 @@ def main():
                                            "lambda_max", "dual", "rho_hat", "eta", "eta_robust", "rank",
                                            "n_sweeps", "n_sweeps_fp64", "n_outer", "n_tcg",
                                            "n_lanczos", "n_escapes", "t_cert_s")},
+            "per_step": [{"s": round(t, 4), "n_tcg": i["n_tcg"], "n_outer": i["n_outer"],
+                          "n_sweeps": i["n_sweeps"], "t_cert_s": round(i["t_cert_s"], 4),
+                          "certified": i["certified"]} for t, i in zip(per_step, timed)],
             "build_q_s": t_build,
             "build_update": update_report(sc.N, build_path, t_update),
             **extra,

@@ -729,6 +729,34 @@ __global__ void k_gemv_n_sub(int n, int m, const VT* __restrict__ V, size_t ld, 
   }
 }
 
+// Partial sums of V c over column chunks: part[s][e] = sum_{j in chunk s} V[j][e] c_j (chunk s =
+// columns [s*chunk, min(m, (s+1)*chunk)), one grid row per chunk), so that the product streams V
+// with every SM busy; k_gemv_n_finish adds the chunks in a fixed order (deterministic).
+template <typename VT>
+__global__ void k_gemv_n_part(int n, int m, const VT* __restrict__ V, size_t ld,
+                              const double* __restrict__ c, const float* __restrict__ cf, int chunk,
+                              double* __restrict__ part) {
+  const int j0 = blockIdx.y * chunk;
+  const int j1 = min(m, j0 + chunk);
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    VT s = VT(0);
+    if (sizeof(VT) == 4) {
+      for (int j = j0; j < j1; ++j) s += V[(size_t)j * ld + e] * VT(cf[j]);
+    } else {
+      for (int j = j0; j < j1; ++j) s += V[(size_t)j * ld + e] * VT(c[j]);
+    }
+    part[(size_t)blockIdx.y * n + e] = double(s);
+  }
+}
+// w -= sum_s part[s] (chunks in order)
+static __global__ void k_gemv_n_finish(int n, int S, const double* __restrict__ part, double* __restrict__ w) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    double t = 0.0;
+    for (int s = 0; s < S; ++s) t += part[(size_t)s * n + e];
+    w[e] -= t;
+  }
+}
+
 // w -= a[k] v_k + b[k-1] v_{k-1}  (coefficients read on the device)
 template <typename VT>
 __global__ void k_lanczos_3term(int n, double* __restrict__ w, const VT* __restrict__ vk,

@@ -215,6 +215,8 @@ struct Solver {
   double *lw = nullptr, *lz = nullptr, *lalpha = nullptr, *lbeta = nullptr, *lc = nullptr,
          *lnrm = nullptr, *lritz = nullptr;
   float *lv32 = nullptr, *lW32 = nullptr, *lwf = nullptr, *lcf = nullptr;
+  static constexpr int LPART_MAX = 64;   // column chunks of the reorthogonalisation product
+  double* lpart = nullptr;               // LPART_MAX x n_pad partial sums
   // stats
   xm_info info{};
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -238,7 +240,7 @@ struct Solver {
   ~Solver() {
     void* bufs[] = {bY, bYc, bW, bWc, bG, bGc, bYin, bEta, bHeta, bR, bD, bHd, bWd, bY64, bXi, bYh,
                     bZ, Lam, Lamc, pcMinv, pcB, d_sc, d_small, V, lw, lz, lalpha, lbeta, lc, lnrm,
-                    lritz, lv32, lW32, lwf, lcf};
+                    lritz, lv32, lW32, lwf, lcf, lpart};
     for (void* p : bufs) if (p) cudaFree(p);
     if (h_sc) cudaFreeHost(h_sc);
     if (ev0) cudaEventDestroy(ev0);
@@ -566,8 +568,13 @@ struct Solver {
       wv = reinterpret_cast<const VT*>(w);
     }
     k_gemv_t<VT><<<std::min(m, ctx->num_sms * 8), 256, 0, st>>>(nn, m, Vb, nn, wv, lc, lcf);
-    k_gemv_n_sub<VT><<<grid_elems(nn), CAM_THREADS, 0, st>>>(nn, m, Vb, nn, lc, lcf, w);
-    launches += 2;
+    // w -= V c over a (row block, column chunk) grid of about 8 blocks per SM
+    const int xb = (nn + 255) / 256;
+    const int S = std::max(1, std::min({m, LPART_MAX, (ctx->num_sms * 8 + xb - 1) / xb}));
+    const int chunk = (m + S - 1) / S;
+    k_gemv_n_part<VT><<<dim3(xb, (m + chunk - 1) / chunk), 256, 0, st>>>(nn, m, Vb, nn, lc, lcf, chunk, lpart);
+    k_gemv_n_finish<<<grid_elems(nn), CAM_THREADS, 0, st>>>(nn, (m + chunk - 1) / chunk, lpart, w);
+    launches += 3;
     XM_CUDA_TRY(cudaGetLastError());
     return XM_OK;
   }
@@ -594,6 +601,7 @@ struct Solver {
       XM_CUDA_TRY(cudaMemsetAsync(lw, 0, sizeof(double) * nn, st));
       XM_CUDA_TRY(cudaMalloc(&lz, sizeof(double) * 2 * (size_t)nn));
       XM_CUDA_TRY(cudaMalloc(&lritz, sizeof(double) * nn));
+      XM_CUDA_TRY(cudaMalloc(&lpart, sizeof(double) * (size_t)LPART_MAX * nn));
       XM_CUDA_TRY(cudaMalloc(&lalpha, sizeof(double) * (kmax + 1)));
       XM_CUDA_TRY(cudaMalloc(&lbeta, sizeof(double) * (kmax + 1)));
       XM_CUDA_TRY(cudaMalloc(&lc, sizeof(double) * (nd_max + kmax + 2)));
