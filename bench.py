@@ -244,22 +244,25 @@ def run_sweep_only(args):
 
 def update_tensor_flops(N: int) -> float:
     """BF16 tensor FLOPs of the translation elimination on the tensor cores: 36 digit pairs
-    (levels 0..7) of (a) the rank-(N-1) product over the n(n+1)/2 entries of the upper triangle
-    and (b) the block updates of the blocked triangular solve (512-row diagonal blocks), n = 3N."""
+    (levels 0..7) of (a) the rank-(N-1) product over the n(n+1)/2 entries of the upper
+    triangle, (b) the block updates of the blocked triangular solve and (c) the trailing updates
+    of the blocked Cholesky factor (lower triangle), both with 512-row blocks; n = 3N."""
     n, K = 3 * N, N - 1
     syrk = 36 * 2.0 * K * n * (n + 1) / 2
     trsm = sum(36 * 2.0 * (K - i0 - min(512, K - i0)) * n * min(512, K - i0) for i0 in range(0, K, 512))
-    return syrk + trsm
+    chol = sum(36 * 2.0 * (K - i0 - min(512, K - i0)) ** 2 / 2 * min(512, K - i0) for i0 in range(0, K, 512))
+    return syrk + trsm + chol
 
 
 def update_report(N: int, path: int, t_update: float) -> dict:
     """The build's translation elimination (triangular solve + rank-(N-1) update + packing): its
     path, device time and, for the tensor-core path, its tensor-core roofline (BF16 peak,
-    measured burst) and FP64-equivalent rate ((n^2 K + K^2 n) / t)."""
+    measured burst) and FP64-equivalent rate ((n^2 K + K^2 n + K^3 / 3) / t)."""
     n, K = 3 * N, N - 1
-    rep = {"path": {0: "none", 1: "fp64_dtrsm_dsyrk", 2: "split_bf16_tcgen05"}.get(path, str(path)),
+    rep = {"path": {0: "none", 1: "fp64_dpotrf_dtrsm_dsyrk", 2: "split_bf16_tcgen05"}.get(path, str(path)),
            "seconds": t_update,
-           "fp64_equivalent_tflops": (n * n * K + K * K * n) / t_update / 1e12 if t_update > 0 else None}
+           "fp64_equivalent_tflops": (n * n * K + K * K * n + K ** 3 / 3) / t_update / 1e12
+           if t_update > 0 else None}
     if path == 2 and t_update > 0:
         pk = None
         try:
@@ -273,7 +276,7 @@ def update_report(N: int, path: int, t_update: float) -> dict:
         rep["roofline"] = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
                            "frac": ach / pk, "traffic": None,
                            "kernel": "k_oz_mma<SYRK> + k_oz_mma<GEMM> block updates (+ digit splits, "
-                                     "FP64 DTRSM diagonal blocks, packing)",
+                                     "FP64 diagonal blocks and panels, packing)",
                            "flops": update_tensor_flops(N), "peak_kind": kind + " bf16 burst"}
     return rep
 
@@ -307,9 +310,11 @@ def run_build_only(args):
         res[mode] = (statistics.median(walls), statistics.median(upds), path)
     ws, us, ps = res[xm.XM_BUILD_SPLIT_BF16]
     wf, uf, pf = res[xm.XM_BUILD_FP64]
+    cpu = None if args.no_cpu else oracle_build_sample(N)
     print(json.dumps({"build_only": True, "N": N, "n": 3 * N, "E": sc.E,
                       "split": {"build_s": ws, **update_report(N, ps, us)},
-                      "fp64": {"build_s": wf, **update_report(N, pf, uf)}}), flush=True)
+                      "fp64": {"build_s": wf, **update_report(N, pf, uf)},
+                      "cpu_baseline": cpu}), flush=True)
     ctx.close()
     return 0
 
@@ -452,6 +457,85 @@ def oracle_batch_sample(scs, budget_s=20.0):
                       f"{t_used:.1f} s of host time)"}
 
 
+def oracle_adjoint_sample(sc, mu: float, n_cams: int = 120) -> dict:
+    """The oracle's adjoint on a bounded prefix of the workload (its first n_cams cameras and
+    their landmarks): oracle build and solve untimed, one adjoint call timed."""
+    from oracle import xm_oracle as O
+    sub = scenes.sub_scene(sc, min(n_cams, sc.N))
+    Q = O.build_Q_schur(sub.N, sub.M, sub.cam, sub.lmk, sub.ukp, sub.w)
+    res = O.solve(Q, r0=4, mu=mu)
+    D = np.random.default_rng(5).standard_normal((sub.N, 3, 3))
+    t0 = time.perf_counter()
+    O.adjoint(sub.N, sub.M, sub.cam, sub.lmk, sub.ukp, sub.w, res.Y, D, Q=Q, mu=mu)
+    dt = time.perf_counter() - t0
+    return {"value": dt, "unit": "s per backward", "cores": host_cores(), "kind": "oracle",
+            "sample": f"oracle adjoint (dense FP64) on the first {sub.N} cameras ({sub.E} observations) "
+                      f"of the workload, one call after an untimed oracle build and solve"}
+
+
+def oracle_build_sample(N: int, n_cap: int = 1500) -> dict:
+    """The oracle's Q construction (Schur form, dense FP64) on the same scene generator at
+    min(N, n_cap) cameras."""
+    from oracle import xm_oracle as O
+    Ns = min(N, n_cap)
+    sc = scenes.random_scene(Ns, 30 * Ns, noise=0.02, outlier_frac=0.05, seed=1)
+    t0 = time.perf_counter()
+    O.build_Q_schur(sc.N, sc.M, sc.cam, sc.lmk, sc.ukp, sc.w)
+    dt = time.perf_counter() - t0
+    return {"value": dt, "unit": "s per build", "cores": host_cores(), "kind": "oracle",
+            "sample": f"oracle build_Q_schur on the seeded random scene of {Ns} cameras "
+                      f"({sc.E} observations)"}
+
+
+def run_recover(args):
+    """Translations and landmarks of the solution (Eq. 7) with per-observation residual terms,
+    and the XM^2 re-run (Sec. 5) on a workload: one certified solve, then W untimed and K timed
+    xm_recover_tp calls and one timed xm_solve_xm2; prints one JSON line."""
+    import torch
+    from paper_2502_04640_b300 import xm
+    mk, _, desc = WORKLOADS[args.workload]
+    sc = mk()
+    ctx = xm.Context(0)
+    t = xm.scene_tensors(sc)
+    wopts = WORKLOAD_OPTS.get(args.workload, {})
+    q = xm.xm_build_Q(ctx, sc.N, sc.M, *t, xm.XM_STORE_ALL)
+    out = xm.xm_solve(q, xm.xm_default_opts(prec=1, **wopts))
+    q.free()
+    for _ in range(args.warmup):
+        xm.xm_recover_tp(ctx, sc.N, sc.M, *t, out["R"], out["s"])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        tt, pp, res2 = xm.xm_recover_tp(ctx, sc.N, sc.M, *t, out["R"], out["s"])
+    torch.cuda.synchronize()
+    rec_s = (time.perf_counter() - t0) / args.steps
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    x2 = xm.xm_solve_xm2(ctx, sc.N, sc.M, *t, xm.xm_default_opts(prec=1, **wopts))
+    torch.cuda.synchronize()
+    xm2_s = time.perf_counter() - t0
+    cpu = None
+    if not args.no_cpu:
+        from oracle import xm_oracle as O
+        sub = scenes.sub_scene(sc, min(400, sc.N))
+        Q = O.build_Q_schur(sub.N, sub.M, sub.cam, sub.lmk, sub.ukp, sub.w)
+        res = O.solve(Q, r0=4, mu=wopts.get("scale_reg", 0.0))
+        U3 = np.concatenate([res.s[i] * res.R[i] for i in range(sub.N)], axis=1)
+        c0 = time.perf_counter()
+        O.recover_tp(sub.N, sub.M, sub.cam, sub.lmk, sub.ukp, sub.w, U3)
+        cpu = {"value": time.perf_counter() - c0, "unit": "s per recovery", "cores": host_cores(),
+               "kind": "oracle", "sample": f"oracle recover_tp on the first {sub.N} cameras "
+                                           f"({sub.E} observations) of the workload"}
+    print(json.dumps({"recover": True, "workload": f"{args.workload}: {desc}", "N": sc.N, "M": sc.M,
+                      "E": sc.E, "steps": args.steps, "warmup": args.warmup,
+                      "recover_tp_s": rec_s, "observations_per_s": sc.E / rec_s,
+                      "xm2_s": xm2_s, "xm2_first_certified": x2["info_first"]["certified"],
+                      "xm2_second_certified": x2["info_second"]["certified"],
+                      "xm2_kept": int(x2["keep"].sum().item()), "cpu_baseline": cpu}), flush=True)
+    ctx.close()
+    return 0
+
+
 def run_adjoint(args):
     """Adjoint of the certified optimum on a workload (default: the 2000-frame trajectory):
     one certified FP32-bulk solve, then W untimed and K timed xm_backward calls per inner
@@ -483,10 +567,13 @@ def run_adjoint(args):
         res[name] = {"s_per_backward": dt, "grads_per_s": sc.E * 4 / dt,
                      **{k: last[k] for k in ("res_rel", "n_refine", "n_cg", "n_sweeps_fp32",
                                              "n_sweeps_fp64", "t_lambda_s", "t_resid_s", "launches")}}
+    cpu = None
+    if not args.no_cpu:
+        cpu = oracle_adjoint_sample(sc, wopts.get("scale_reg", 0.0))
     print(json.dumps({"adjoint": True, "workload": f"{args.workload}: {desc}", "opts": wopts, "N": sc.N, "M": sc.M,
                       "E": sc.E, "rank": r, "forward_solve_s": out["info"]["t_solve_s"],
                       "certified": out["info"]["certified"], "steps": args.steps,
-                      "warmup": args.warmup, **res}), flush=True)
+                      "warmup": args.warmup, **res, "cpu_baseline": cpu}), flush=True)
     q.free()
     ctx.close()
     return 0
@@ -516,11 +603,15 @@ def main():
     ap.add_argument("--build-only", type=int, default=0, metavar="N",
                     help="time only xm_build_Q (tensor-core and FP64 rank-k update) on a seeded random "
                          "scene of N cameras (also the small case for profiler captures)")
+    ap.add_argument("--recover", action="store_true",
+                    help="time xm_recover_tp (Eq. 7) and xm_solve_xm2 (Sec. 5) on --workload")
     ap.add_argument("--adjoint", action="store_true",
                     help="time xm_backward (the adjoint of the certified optimum) on --workload")
     args = ap.parse_args()
     if args.adjoint:
         return run_adjoint(args)
+    if args.recover:
+        return run_recover(args)
 
     if args.warmup < 3 and not args.profile_solve:
         ap.error("--warmup must be >= 3")

@@ -135,28 +135,29 @@ xm_status   xm_sync(xm_ctx* ctx);
 xm_status xm_build_Q(xm_ctx* ctx, int N, int M, int64_t E, const int32_t* cam,
                      const int32_t* lmk, const double* ukp, const double* w,
                      unsigned store_mask, xm_qmat** out);
-/* Arithmetic of the translation elimination that ends xm_build_Q (App. A): C = L^{-1} Bbar^T
- * (L the Cholesky factor of the anchored translation block; 3 N^3 flops) and the symmetric
- * rank-(N-1) update Q = P - C^T C (9 N^3 flops; 9.4 TFLOP at N = 10155): the build's dense
- * contractions.
- * XM_BUILD_FP64:       cuBLAS DTRSM and DSYRK on the FP64 units.
- * XM_BUILD_SPLIT_BF16: both on the BF16 tensor cores by error-free digit splitting (Ozaki et al.
- *                      2012): each operand vector as 8 signed 7-bit digits scaled by a power of
- *                      two, exact FP32 accumulation of the digit products, int32 and FP64
- *                      recombination; normwise as accurate as FP64 products (error below
- *                      2^-56 sqrt(K) |u| |v| per dot product).  The triangular solve is blocked
- *                      (512-row diagonal blocks solved by cuBLAS DTRSM in FP64, the block updates
- *                      on the tensor cores).  Needs N - 1 <= 16640.
+/* Arithmetic of the translation elimination that ends xm_build_Q (App. A): the Cholesky factor
+ * L of the anchored translation block (N^3 / 3 flops), C = L^{-1} Bbar^T (3 N^3 flops) and the
+ * symmetric rank-(N-1) update Q = P - C^T C (9 N^3 flops; 9.4 TFLOP at N = 10155): the build's
+ * dense contractions.
+ * XM_BUILD_FP64:       cuSOLVER DPOTRF, cuBLAS DTRSM and DSYRK on the FP64 units.
+ * XM_BUILD_SPLIT_BF16: the dense products on the BF16 tensor cores by error-free digit splitting
+ *                      (Ozaki et al. 2012): each operand vector as 8 signed 7-bit digits scaled by
+ *                      a power of two, exact FP32 accumulation of the digit products, int32 and
+ *                      FP64 recombination; normwise as accurate as FP64 products (error below
+ *                      2^-56 sqrt(K) |u| |v| per dot product).  The factorisation and the
+ *                      triangular solve are blocked (512-row diagonal blocks and panels by
+ *                      cuSOLVER / cuBLAS in FP64, the trailing and block updates on the tensor
+ *                      cores).  Needs N - 1 <= 16640.
  * XM_BUILD_AUTO:       XM_BUILD_SPLIT_BF16 when 512 <= N <= 16641, else XM_BUILD_FP64 (default).
- * The landmark elimination and the Cholesky factor stay in FP64 either way. */
+ * The landmark elimination stays in FP64 either way. */
 #define XM_BUILD_AUTO 0
 #define XM_BUILD_FP64 1
 #define XM_BUILD_SPLIT_BF16 2
 /* Select the arithmetic for later xm_build_Q calls on ctx (XM_EINVAL for an unknown mode). */
 xm_status xm_set_build_mode(xm_ctx* ctx, int mode);
 /* Which arithmetic built q (XM_BUILD_FP64 or XM_BUILD_SPLIT_BF16; XM_BUILD_AUTO when N = 1 and
- * there was no translation elimination) and the device seconds of its triangular solve,
- * rank-(N-1) update and packing (either pointer may be NULL). */
+ * there was no translation elimination) and the device seconds of its Cholesky factor,
+ * triangular solve, rank-(N-1) update and packing (either pointer may be NULL). */
 xm_status xm_qmat_build_info(const xm_qmat* q, int* path, double* t_update_s);
 /* Q from a dense symmetric n x n FP64 array (device, row-major); for tests. */
 xm_status xm_qmat_from_dense(xm_ctx* ctx, int N, const double* Q, unsigned store_mask,

@@ -7,9 +7,10 @@
 //      (P = Q1 - V2 D^-1 V2^T, B = V1 - V2 D^-1 V3^T, S = Q2 - V3 D^-1 V3^T with D = Q3);
 //   3. translation elimination with the anchor t_0 = 0: Sbar = L L^T (Cholesky), C = L^-1 Bbar^T
 //      (dense FP64 factor and triangular solve from cuSOLVER / cuBLAS: the paper's "large dense
-//      matrix multiplications"), then Q = P - C^T C: either cuBLAS DTRSM + DSYRK (FP64 units) or,
-//      with XM_BUILD_SPLIT_BF16, the blocked triangular solve and the rank-k update of
-//      xm_ozaki.cu on the BF16 tensor cores (digit splitting, FP64-accurate);
+//      matrix multiplications"), then Q = P - C^T C: either cuSOLVER DPOTRF + cuBLAS DTRSM + DSYRK
+//      (FP64 units) or, with XM_BUILD_SPLIT_BF16, the blocked Cholesky factor, blocked triangular
+//      solve and rank-k update of xm_ozaki.cu with their dense products on the BF16 tensor
+//      cores (digit splitting, FP64-accurate);
 //   4. pack the upper triangle into the tile layout of the sweep kernel (FP64 / FP32 / BF16);
 //      the tensor-core update writes the packed tiles itself.
 // Connectivity of the view graph (rank N+M-1 of the Laplacian Q_tp, App. A lemma) is checked
@@ -383,20 +384,6 @@ xm_status build_Q(xm_ctx* ctx, int N, int M, int64_t E, const int32_t* cam, cons
     // rows/cols 1..N-1 of S, ld N: the row-major upper triangle is the column-major lower one
     double* Sbar = S.as<double>() + N + 1;
     double* BbarT = B.as<double>() + 1;          // column-major (N-1) x n, ld N
-    int lwork = 0;
-    XM_CUSOLVER_TRY(cusolverDnDpotrf_bufferSize(cs, CUBLAS_FILL_MODE_LOWER, m, Sbar, N, &lwork));
-    DevBuf work, info;
-    XM_CUDA_TRY(cudaMalloc(&work.p, sizeof(double) * (size_t)(lwork > 0 ? lwork : 1)));
-    XM_CUDA_TRY(cudaMalloc(&info.p, sizeof(int)));
-    XM_CUSOLVER_TRY(cusolverDnDpotrf(cs, CUBLAS_FILL_MODE_LOWER, m, Sbar, N, work.as<double>(),
-                                     lwork, info.as<int>()));
-    int hinfo = 0;
-    XM_CUDA_TRY(cudaMemcpyAsync(&hinfo, info.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-    XM_CUDA_TRY(cudaStreamSynchronize(st));
-    if (hinfo != 0)
-      return set_error(XM_EDISCONNECTED,
-                       "translation Schur block not positive definite (potrf info %d)", hinfo);
-    const double one = 1.0, minus_one = -1.0;
     bool split = false;
     if (ctx->build_mode == XM_BUILD_SPLIT_BF16) {
       if (!split_update_fits(m, n))
@@ -405,11 +392,32 @@ xm_status build_Q(xm_ctx* ctx, int N, int M, int64_t E, const int32_t* cam, cons
     } else if (ctx->build_mode == XM_BUILD_AUTO) {
       split = N >= XM_BUILD_SPLIT_MIN_N && split_update_fits(m, n);
     }
-    // C = L^{-1} Bbar^T and Q = P - C^T C, timed together (device events)
+    // Cholesky factor, C = L^{-1} Bbar^T and Q = P - C^T C, timed together (device events)
     cudaEvent_t e0, e1;
     XM_CUDA_TRY(cudaEventCreate(&e0));
     XM_CUDA_TRY(cudaEventCreate(&e1));
     XM_CUDA_TRY(cudaEventRecord(e0, st));
+    int hinfo = 0;
+    if (split) {
+      XM_TRY(split_potrf(ctx, cb, cs, Sbar, N, m, &hinfo));
+    } else {
+      int lwork = 0;
+      XM_CUSOLVER_TRY(cusolverDnDpotrf_bufferSize(cs, CUBLAS_FILL_MODE_LOWER, m, Sbar, N, &lwork));
+      DevBuf work, info;
+      XM_CUDA_TRY(cudaMalloc(&work.p, sizeof(double) * (size_t)(lwork > 0 ? lwork : 1)));
+      XM_CUDA_TRY(cudaMalloc(&info.p, sizeof(int)));
+      XM_CUSOLVER_TRY(cusolverDnDpotrf(cs, CUBLAS_FILL_MODE_LOWER, m, Sbar, N, work.as<double>(),
+                                       lwork, info.as<int>()));
+      XM_CUDA_TRY(cudaMemcpyAsync(&hinfo, info.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+      XM_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    if (hinfo != 0) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return set_error(XM_EDISCONNECTED,
+                       "translation Schur block not positive definite (potrf info %d)", hinfo);
+    }
+    const double one = 1.0, minus_one = -1.0;
     xm_status stu = XM_OK;
     if (split) {
       // both on the tensor cores; the rank-k update writes the packed tiles itself

@@ -114,6 +114,10 @@ xm_status split_update_pack(xm_ctx* ctx, const double* C, int ldc, int K, const 
 // substitution with FP64 diagonal blocks (cuBLAS handle) and tensor-core block updates.
 xm_status split_trsm(xm_ctx* ctx, void* cublas, const double* L, int ldl, double* X, int ldx,
                      int m, int n);
+// In-place Cholesky factor (lower) of the SPD m x m A (column-major): blocked, FP64 diagonal
+// blocks and panels, tensor-core trailing updates; *minor = first failing leading minor or 0.
+xm_status split_potrf(xm_ctx* ctx, void* cublas, void* cusolver, double* A, int lda, int m,
+                      int* minor);
 
 // ------------------------------------------------------------------ adjoint support (xm_build.cu)
 // Index and value checks of the observation arrays (synchronous; XM_EINVAL on a bad entry).

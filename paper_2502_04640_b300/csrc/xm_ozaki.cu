@@ -22,9 +22,11 @@
 //   OZ_SYRK  Q = P - C^T C into the packed upper-triangle tiles of the sweep (FP64 accumulator
 //            tile, then P added, diagonal halved, lower triangle and padding zeroed, FP32 and
 //            BF16 copies written);
-//   OZ_GEMM  X_rest -= L_rest,i X_i, the block update of a right-looking blocked triangular
-//            solve (column-major FP64 output; the 512 x 512 diagonal blocks are solved by cuBLAS
-//            DTRSM in FP64).
+//   OZ_GEMM  out -= A B^T into a column-major FP64 matrix: the block updates X_rest -= L_rest,i X_i
+//            of a right-looking blocked triangular solve (the 512 x 512 diagonal blocks solved by
+//            cuBLAS DTRSM in FP64), and the trailing updates S_rest -= L_k L_k^T of a right-looking
+//            blocked Cholesky factorisation (diagonal blocks by cuSOLVER, panels by DTRSM, FP64;
+//            only tiles meeting the lower triangle).
 //
 // Kernel: persistent, one CTA per SM, 128 x 256 output tiles (MMA M = 128, N = 256) in an order
 // that lets concurrent CTAs share operand k-blocks in L2.  Warp 0 streams the 128 x 64 and
@@ -35,6 +37,7 @@
 // bounded; a stalled pipeline raises DEV_TIMEOUT, drains its copies and frees tensor memory.
 #include <cublas_v2.h>
 #include <cuda.h>
+#include <cusolverDn.h>
 #include <cudaTypedefs.h>
 
 #include <algorithm>
@@ -457,6 +460,8 @@ xm_status launch_mma(xm_ctx* ctx, const CUtensorMap& ma, const CUtensorMap& mb, 
   return XM_OK;
 }
 
+int split_grid(xm_ctx* ctx, int work, int per_block);
+
 // (I, J) work items: groups of 8 tile rows, column by column, so that the CTAs running at one
 // time share the operand k-blocks of a few tile rows and columns in L2.  keep(I, J) filters.
 template <typename F>
@@ -476,7 +481,7 @@ struct DevMem {
 };
 
 int split_grid(xm_ctx* ctx, int work, int per_block) {
-  int g = (work + per_block - 1) / per_block;
+  int g = (work + per_block - 1) / per_block;  // grid-stride kernels: at most 16 blocks per SM
   return std::max(1, std::min(g, ctx->num_sms * 16));
 }
 
@@ -604,6 +609,83 @@ xm_status split_trsm(xm_ctx* ctx, void* cublas, const double* L, int ldl, double
     XM_CUDA_TRY(cudaStreamSynchronize(st));
   }
   return check_device_error(ctx, "split-BF16 triangular solve");
+}
+
+}  // namespace xm
+
+namespace xm {
+
+// In-place Cholesky factor of the m x m SPD matrix A (column-major, leading dimension lda, lower
+// triangle used and overwritten by L): right-looking, blocks of 512; the diagonal blocks by
+// cuSOLVER DPOTRF and the panels by cuBLAS DTRSM (FP64), the trailing updates
+// A_rest -= L_k L_k^T on the tensor cores (only the tiles that meet the lower triangle).
+// *minor = 0 on success, else the 1-based order of the first non-positive leading minor.
+xm_status split_potrf(xm_ctx* ctx, void* cublas, void* cusolver, double* A, int lda, int m,
+                      int* minor) {
+  cudaStream_t st = ctx->stream;
+  cublasHandle_t cb = static_cast<cublasHandle_t>(cublas);
+  cusolverDnHandle_t cs = static_cast<cusolverDnHandle_t>(cusolver);
+  const int b = OZ_TRSM_BLOCK;
+  const int K_pad = b;
+  *minor = 0;
+  int lwork = 0;
+  if (cusolverDnDpotrf_bufferSize(cs, CUBLAS_FILL_MODE_LOWER, std::min(b, m), A, lda, &lwork) !=
+      CUSOLVER_STATUS_SUCCESS)
+    return set_error(XM_ECUDA, "cusolverDnDpotrf_bufferSize failed");
+  const int rows_max = ((std::max(m - b, 1) + OZ_BN - 1) / OZ_BN) * OZ_BN;   // boxes of 128 and 256 rows
+  DevMem work, info, S, sc, tl;
+  XM_CUDA_TRY(cudaMalloc(&work.p, sizeof(double) * (size_t)std::max(lwork, 1)));
+  XM_CUDA_TRY(cudaMalloc(&info.p, sizeof(int)));
+  XM_CUDA_TRY(cudaMalloc(&S.p, sizeof(__nv_bfloat16) * (size_t)OZ_SLICES * rows_max * K_pad));
+  XM_CUDA_TRY(cudaMalloc(&sc.p, sizeof(double) * (size_t)rows_max));
+  XM_CUDA_TRY(cudaMalloc(&tl.p, sizeof(int2) * (size_t)(rows_max / OZ_BM) * (rows_max / OZ_BN)));
+  const double one = 1.0;
+  for (int k0 = 0; k0 < m; k0 += b) {
+    const int bk = std::min(b, m - k0);
+    double* Akk = A + k0 + (size_t)k0 * lda;
+    if (cusolverDnDpotrf(cs, CUBLAS_FILL_MODE_LOWER, bk, Akk, lda, work.as<double>(), lwork,
+                         info.as<int>()) != CUSOLVER_STATUS_SUCCESS)
+      return set_error(XM_ECUDA, "cusolverDnDpotrf (diagonal block %d) failed", k0 / b);
+    int h = 0;
+    XM_CUDA_TRY(cudaMemcpyAsync(&h, info.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    XM_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h != 0) { *minor = k0 + h; return XM_OK; }
+    const int rest = m - k0 - bk;
+    if (rest == 0) break;
+    double* P = A + (k0 + bk) + (size_t)k0 * lda;              // panel, rest x bk
+    if (cublasDtrsm(cb, CUBLAS_SIDE_RIGHT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T, CUBLAS_DIAG_NON_UNIT,
+                    rest, bk, &one, Akk, lda, P, lda) != CUBLAS_STATUS_SUCCESS)
+      return set_error(XM_ECUDA, "cublasDtrsm (panel %d) failed", k0 / b);
+    const int rows = ((rest + OZ_BN - 1) / OZ_BN) * OZ_BN;
+    const size_t stride = (size_t)rows * K_pad;
+    k_oz_split_rows<<<split_grid(ctx, rows, 128), 128, 0, st>>>(P, lda, bk, rest, rows, K_pad,
+                                                               S.as<__nv_bfloat16>(), stride,
+                                                               sc.as<double>());
+    XM_CUDA_TRY(cudaGetLastError());
+    const int nI = (rest + OZ_BM - 1) / OZ_BM, nJ = (rest + OZ_BN - 1) / OZ_BN;
+    // 128 x 256 tiles with some column <= some row (they meet the lower triangle)
+    std::vector<int2> order = tile_order(nI, nJ, [](int I, int J) { return J * OZ_BN <= I * OZ_BM + OZ_BM - 1; });
+    XM_CUDA_TRY(cudaMemcpyAsync(tl.p, order.data(), sizeof(int2) * order.size(),
+                                cudaMemcpyHostToDevice, st));
+    CUtensorMap ma, mb;
+    XM_TRY(slice_map(&ma, S.p, K_pad, rows, OZ_BM));
+    XM_TRY(slice_map(&mb, S.p, K_pad, rows, OZ_BN));
+    OzArgs a{};
+    a.tiles = tl.as<int2>();
+    a.ntiles = (int)order.size();
+    a.KB = (bk + OZ_BK - 1) / OZ_BK;
+    a.scaleA = sc.as<double>();
+    a.scaleB = sc.as<double>();
+    a.out = A + (k0 + bk) + (size_t)(k0 + bk) * lda;
+    a.ldo = lda;
+    a.M = rest;
+    a.ncols = rest;
+    a.err = ctx->d_err;
+    XM_TRY(launch_mma<OZ_GEMM>(ctx, ma, mb, a));
+    // the host order vector is reused next step
+    XM_CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  return check_device_error(ctx, "split-BF16 Cholesky factor");
 }
 
 }  // namespace xm
