@@ -598,6 +598,8 @@ def main():
     ap.add_argument("--profile-solve", action="store_true",
                     help="build Q and run exactly one solve inside the NVTX range 'timed' (profiler "
                          "launch lists); prints the solve's info")
+    ap.add_argument("--bulk-stall", action="store_true",
+                    help="opts.bulk_stall = 1: hand the FP32 bulk phase to the FP64 polish on stagnation")
     ap.add_argument("--time-limit", type=float, default=0.0,
                     help="wall-clock cap of each solve in seconds (0: none)")
     ap.add_argument("--sweep-only", type=int, default=0, metavar="N",
@@ -657,7 +659,9 @@ def main():
     build_path, t_update = xm.xm_qmat_build_info(q)
     del cam, lmk, ukp, w
     torch.cuda.empty_cache()
-    wopts = WORKLOAD_OPTS.get(args.workload, {})
+    wopts = dict(WORKLOAD_OPTS.get(args.workload, {}))
+    if args.bulk_stall:
+        wopts["bulk_stall"] = 1
     opts = xm.xm_default_opts(prec=prec, time_limit_s=args.time_limit, **wopts)
     stream = ctx.stream
 
@@ -781,7 +785,7 @@ def main():
             "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": value * 1e3 * world, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[args.prec], "data": "synthetic",
-            "config": {"workload": f"{args.workload}: {desc}", "prec": args.prec,
+            "config": {"workload": f"{args.workload}: {desc}", "prec": args.prec, "opts": wopts,
                        "replicas": world, "l2": "inputs larger than L2 (packed FP32 Q "
                        f"{n * (n + 1) / 2 * 4 / 1e9:.2f} GB > 126 MB)", "N": sc.N, "M": sc.M, "E": sc.E},
             "roofline": roofline,

@@ -84,6 +84,7 @@ void xm_default_opts(xm_opts* o) {
   o->init_jitter = 0.1;
   o->scale_reg = 0.0;
   o->precond = 0;
+  o->bulk_stall = 0;
 }
 
 xm_status xm_create(xm_ctx** out, int device, void* stream) {

@@ -231,6 +231,8 @@ struct Solver {
   bool timed_out = false;
   double ref_g = -1.0;   // ||rgrad|| at the start point of the solve (tolerance reference)
   double cur_g2 = 0.0;
+  double carry_delta = 0.0;   // trust radius handed from a stalled bulk phase to the polish
+  bool bulk_stalled = false;  // the last bulk phase stopped on stagnation (opts.bulk_stall)
 
   Solver(xm_ctx* c, const DeviceQ& qq, const xm_opts& oo) : ctx(c), q(qq), o(oo), st(c->stream) {
     N = q.N; n = q.n; n_pad = q.n_pad;
@@ -377,9 +379,14 @@ struct Solver {
     }
     const double Delta_bar = std::sqrt(std::max(ynorm2, 1e-300));
     double Delta = Delta_bar / 8.0;
+    if (!bulk && carry_delta > 0.0) Delta = std::min(carry_delta, Delta_bar);   // polish after a stall
+    carry_delta = 0.0;
+    if (bulk) bulk_stalled = false;
     const double eps_reg = std::is_same<To, float>::value ? 1e2 * 1.1920929e-07
                                                           : 1e3 * 2.220446049250313e-16;
     int rejects = 0;
+    double best_f = f;   // bulk stagnation test (opts.bulk_stall)
+    int stall = 0;
     // captured tCG chunks of this call, keyed by the (iterate, Lambda) buffers they read
     struct ChunkGraph { const void* yin; const double* lam; cudaGraphExec_t exec; };
     struct GraphCache {
@@ -517,6 +524,17 @@ struct Solver {
       }
       if (Delta < 1e-12 * Delta_bar) break;
       if (bulk && (rejects >= 6 || Delta < 1e-7 * Delta_bar)) break;
+      if (bulk && o.bulk_stall) {
+        // the FP32 objective has stopped improving beyond its own noise (the ratio test's
+        // allowance reg): further FP32 steps only chase rounding, the FP64 polish takes over
+        if (f < best_f - reg) { best_f = f; stall = 0; } else { ++stall; }
+        if (stall >= 5 && std::sqrt(g2) <= 1e-6 * ref_g) {
+          // the polish continues from here: keep the trust radius the bulk phase found
+          carry_delta = Delta;
+          bulk_stalled = true;
+          break;
+        }
+      }
     }
     info.f = f;
     cur_g2 = g2;
@@ -915,8 +933,10 @@ xm_status solve_impl(xm_ctx* ctx, const DeviceQ& q, const xm_opts& o, int r_in, 
       ++S.launches;
       XM_CUDA_TRY(cudaGetLastError());
       // Quick certificate with the bulk-phase dual blocks: clearly negative curvature means the
-      // rank-r point is a saddle of the SDP (Thm. 2) and an FP64 polish would be wasted.
-      if (r < o.r_max) {
+      // rank-r point is a saddle of the SDP (Thm. 2) and an FP64 polish would be wasted.  After
+      // a stagnation hand-over the gradient, hence the dual blocks, are too coarse for that
+      // test; the FP64 certificate after the polish decides instead.
+      if (r < o.r_max && !S.bulk_stalled) {
         // a short Krylov run suffices: strong negative curvature is an extreme eigenvalue
         XM_TRY(with_R(R, [&] { return S.certify<4>(r, XM_FP32_BULK, &lam_def, &lam_max, &lam_range, 60); },
                          [&] { return S.certify<8>(r, XM_FP32_BULK, &lam_def, &lam_max, &lam_range, 60); }));
@@ -1108,6 +1128,7 @@ xm_status check_opts(const DeviceQ& q, const xm_opts& o) {
   if (!(o.scale_reg >= 0.0) || !std::isfinite(o.scale_reg))
     return set_error(XM_EINVAL, "opts: scale_reg must be finite and >= 0 (got %g)", o.scale_reg);
   if (o.precond != 0 && o.precond != 1) return set_error(XM_EINVAL, "opts: precond must be 0 or 1");
+  if (o.bulk_stall != 0 && o.bulk_stall != 1) return set_error(XM_EINVAL, "opts: bulk_stall must be 0 or 1");
   return XM_OK;
 }
 

@@ -32,7 +32,8 @@ class XmOpts(ctypes.Structure):
                 ("lanczos_max", ctypes.c_int), ("lanczos_tol", ctypes.c_double),
                 ("time_limit_s", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("verbose", ctypes.c_int), ("init_jitter", ctypes.c_double),
-                ("scale_reg", ctypes.c_double), ("precond", ctypes.c_int)]
+                ("scale_reg", ctypes.c_double), ("precond", ctypes.c_int),
+                ("bulk_stall", ctypes.c_int)]
 
 
 class XmInfo(ctypes.Structure):
