@@ -19,6 +19,7 @@ struct Scal {
   double g_eta, eta_Heta, eta2;  // model terms of the step
   double dot;                // generic reduction result
   double mu;                 // App. D scale-regularisation weight (0: plain Eq. 17 objective)
+  double thr_min;            // floor of the residual stop: no tighter than the phase's tolerance
   int done, stop_after, iters, max_iters, reason, pad_;
 };
 
@@ -297,7 +298,7 @@ template <typename To, typename Ti, int R>
 __global__ void __launch_bounds__(CAM_THREADS)
 k_tcg_init(int N, const Ti* __restrict__ Y, const To* __restrict__ G, Ti* eta, Ti* Heta, Ti* r, Ti* z,
            Ti* delta, const double* __restrict__ Minv, Scal* sc, double Delta, int max_iters,
-           double theta, double kappa_tol, double* partials, unsigned* counter) {
+           double theta, double kappa_tol, double thr_min, double* partials, unsigned* counter) {
   using C = double;
   double v[2] = {0.0, 0.0};
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -332,7 +333,7 @@ k_tcg_init(int N, const Ti* __restrict__ Y, const To* __restrict__ G, Ti* eta, T
     sc->ee = 0.0; sc->ed = 0.0; sc->dd = t[1];
     sc->done = (t[0] > 0.0 && t[1] > 0.0) ? 0 : 1;
     sc->stop_after = 0; sc->iters = 0; sc->max_iters = max_iters; sc->reason = 0;
-    sc->theta = theta; sc->kappa_tol = kappa_tol;
+    sc->theta = theta; sc->kappa_tol = kappa_tol; sc->thr_min = thr_min;
   });
 }
 
@@ -469,7 +470,7 @@ k_tcg_update(int N, const T* __restrict__ Y, T* eta, T* Heta, T* r, T* z, const 
     if (stop) { sc->done = 1; return; }
     const double rr_new = t[0], rz_new = t[1];
     const double rn = sqrt(rr_new);
-    const double thr = sc->r0 * fmin(pow(sc->r0, sc->theta), sc->kappa_tol);
+    const double thr = fmax(sc->r0 * fmin(pow(sc->r0, sc->theta), sc->kappa_tol), sc->thr_min);
     if (rn <= thr) { sc->done = 1; sc->reason = 3; return; }
     if (sc->iters >= sc->max_iters) { sc->done = 1; sc->reason = 4; return; }
     if (!(rz_new > 0.0)) { sc->done = 1; sc->reason = 5; return; }

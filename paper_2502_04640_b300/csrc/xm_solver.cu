@@ -414,7 +414,7 @@ struct Solver {
       }
       k_tcg_init<To, Ti, R><<<nb_cam, CAM_THREADS, 0, st>>>(
           N, Yin, (const To*)bG, (Ti*)bEta, (Ti*)bHeta, (Ti*)bR, (Ti*)bZ, (Ti*)bD, pcMinv, d_sc, Delta,
-          o.max_tcg, 1.0, 0.1, ctx->d_partials, ctx->d_counter);
+          o.max_tcg, 1.0, 0.1, 0.5 * tol_abs, ctx->d_partials, ctx->d_counter);
       ++launches;
       XM_CUDA_TRY(cudaGetLastError());
       // Chunks of CH iterations; the host reads the done flag of chunk k-1 while chunk k is
