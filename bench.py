@@ -598,8 +598,9 @@ def main():
     ap.add_argument("--profile-solve", action="store_true",
                     help="build Q and run exactly one solve inside the NVTX range 'timed' (profiler "
                          "launch lists); prints the solve's info")
-    ap.add_argument("--bulk-stall", action="store_true",
-                    help="opts.bulk_stall = 1: hand the FP32 bulk phase to the FP64 polish on stagnation")
+    ap.add_argument("--bulk-stall", type=int, default=None, metavar="K",
+                    help="opts.bulk_stall = K: hand the FP32 bulk phase to the FP64 polish after K "
+                         "outer steps of stagnation (0: off)")
     ap.add_argument("--time-limit", type=float, default=0.0,
                     help="wall-clock cap of each solve in seconds (0: none)")
     ap.add_argument("--sweep-only", type=int, default=0, metavar="N",
@@ -660,8 +661,8 @@ def main():
     del cam, lmk, ukp, w
     torch.cuda.empty_cache()
     wopts = dict(WORKLOAD_OPTS.get(args.workload, {}))
-    if args.bulk_stall:
-        wopts["bulk_stall"] = 1
+    if args.bulk_stall is not None:
+        wopts["bulk_stall"] = args.bulk_stall
     opts = xm.xm_default_opts(prec=prec, time_limit_s=args.time_limit, **wopts)
     stream = ctx.stream
 

@@ -90,11 +90,12 @@ typedef struct xm_opts {
                               (eigenvalues clamped at 1e-6 of the largest), trust region in the
                               B-norm (halves the sweeps on the 1934-camera workload, slower on
                               the 10155-camera one)                                            */
-  int bulk_stall;          /* mixed modes: 1 hands the FP32 bulk phase over to the FP64 polish
-                              once ||rgrad|| <= 1e-6 ||rgrad(Y0)|| and the best objective has not
-                              improved by more than the ratio test's FP32 noise allowance over 5
-                              outer steps (the FP32 objective is noise there); 0 runs the bulk to
-                              bulk_tol_rel                                                      */
+  int bulk_stall;          /* mixed modes: k > 0 hands the FP32 bulk phase over to the FP64
+                              polish once ||rgrad|| <= 1e-6 ||rgrad(Y0)|| and the best objective
+                              has not improved by more than the ratio test's FP32 noise allowance
+                              over k outer steps (the FP32 objective is noise there); the polish
+                              starts from the bulk's trust radius.  0 runs the bulk to
+                              bulk_tol_rel or max_outer.  0 <= k <= max_outer               */
 } xm_opts;
 
 typedef struct xm_info {

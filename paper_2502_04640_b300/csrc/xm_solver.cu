@@ -528,7 +528,7 @@ struct Solver {
         // the FP32 objective has stopped improving beyond its own noise (the ratio test's
         // allowance reg): further FP32 steps only chase rounding, the FP64 polish takes over
         if (f < best_f - reg) { best_f = f; stall = 0; } else { ++stall; }
-        if (stall >= 5 && std::sqrt(g2) <= 1e-6 * ref_g) {
+        if (stall >= o.bulk_stall && std::sqrt(g2) <= 1e-6 * ref_g) {
           // the polish continues from here: keep the trust radius the bulk phase found
           carry_delta = Delta;
           bulk_stalled = true;
@@ -1128,7 +1128,8 @@ xm_status check_opts(const DeviceQ& q, const xm_opts& o) {
   if (!(o.scale_reg >= 0.0) || !std::isfinite(o.scale_reg))
     return set_error(XM_EINVAL, "opts: scale_reg must be finite and >= 0 (got %g)", o.scale_reg);
   if (o.precond != 0 && o.precond != 1) return set_error(XM_EINVAL, "opts: precond must be 0 or 1");
-  if (o.bulk_stall != 0 && o.bulk_stall != 1) return set_error(XM_EINVAL, "opts: bulk_stall must be 0 or 1");
+  if (o.bulk_stall < 0 || o.bulk_stall > o.max_outer)
+    return set_error(XM_EINVAL, "opts: bulk_stall must be in [0, max_outer] (got %d)", o.bulk_stall);
   return XM_OK;
 }
 
