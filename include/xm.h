@@ -96,6 +96,11 @@ typedef struct xm_opts {
                               over k outer steps (the FP32 objective is noise there); the polish
                               starts from the bulk's trust radius.  0 runs the bulk to
                               bulk_tol_rel or max_outer.  0 <= k <= max_outer               */
+  int cert_lobpcg;         /* certificates with FP32 Z products (mixed modes): 1 (default)
+                              finds lambda_min(Z) on range(Y)^perp by block-Jacobi preconditioned
+                              LOBPCG (blocks of 4, stop at a Ritz residual <= 1e-6 lambda_max,
+                              lambda_max from 40 Lanczos steps; Lanczos if it does not converge
+                              in 300 iterations); 0: Lanczos to lanczos_tol                     */
 } xm_opts;
 
 typedef struct xm_info {

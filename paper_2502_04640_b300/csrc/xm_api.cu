@@ -85,6 +85,7 @@ void xm_default_opts(xm_opts* o) {
   o->scale_reg = 0.0;
   o->precond = 0;
   o->bulk_stall = 0;
+  o->cert_lobpcg = 1;
 }
 
 xm_status xm_create(xm_ctx** out, int device, void* stream) {

@@ -191,6 +191,196 @@ k_bnorm(int N, const T* __restrict__ Y, const double* __restrict__ B, Scal* sc, 
   grid_reduce<1>(v, partials, counter, [&](double* t) { sc->dot = t[0]; });
 }
 
+// ------------------------------------------------------------------ LOBPCG certificate kernels
+// Blocks of 4 vectors are n_pad x 4 row-major FP32 arrays (the sweep's layout for R = 4).
+
+// Minv_i = inverse of the 3 x 3 diagonal block Z_ii = Q_ii - Lambda_i + dreg_i e3 e3^T of the
+// certificate matrix, eigenvalues clamped at 1e-6 of the largest (block-Jacobi preconditioner).
+__global__ void k_zblock_precond(int N, const double* __restrict__ q64, int nt,
+                                 const double* __restrict__ Lam, double* __restrict__ Minv) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double A[3][3], V[3][3], d[3];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b)
+      A[a][b] = q_entry(q64, nt, 3 * i + a, 3 * i + b) - 0.5 * (Lam[9 * i + 3 * a + b] + Lam[9 * i + 3 * b + a]);
+  A[2][2] += Lam[(size_t)9 * N + i];
+  jacobi3<double>(A, V, d);
+  const double dmax = fmax(fabs(d[0]), fmax(fabs(d[1]), fabs(d[2])));
+  double e[3];
+  for (int k = 0; k < 3; ++k) e[k] = dmax > 0.0 ? fmax(d[k], 1e-6 * dmax) : 1.0;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      double m = 0.0;
+      for (int k = 0; k < 3; ++k) m += V[a][k] * V[b][k] / e[k];
+      Minv[(size_t)9 * i + 3 * a + b] = m;
+    }
+}
+
+// ZV_i = Wz_i - Lambda_i V_i + dreg_i e3 e3^T V_i for a 4-column block (Z V after the sweep
+// Wz = Q V); Wz is reset to zero for the next accumulating sweep.
+__global__ void k_zv4(int N, float* __restrict__ Wz, const float* __restrict__ V,
+                      const double* __restrict__ Lam, float* __restrict__ ZV) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double x[3][4];
+  for (int a = 0; a < 3; ++a)
+    for (int j = 0; j < 4; ++j) x[a][j] = V[(size_t)(3 * i + a) * 4 + j];
+  const double dreg = Lam[(size_t)9 * N + i];
+  for (int a = 0; a < 3; ++a)
+    for (int j = 0; j < 4; ++j) {
+      const double lx = Lam[9 * i + 3 * a] * x[0][j] + Lam[9 * i + 3 * a + 1] * x[1][j] +
+                        Lam[9 * i + 3 * a + 2] * x[2][j];
+      const size_t e = (size_t)(3 * i + a) * 4 + j;
+      ZV[e] = float(double(Wz[e]) - lx + (a == 2 ? dreg * x[2][j] : 0.0));
+      Wz[e] = 0.f;
+    }
+}
+
+// R = ZX - X diag(theta); W = Minv R (per camera); out[j] = ||R_j||^2 (j = 0..3)
+__global__ void __launch_bounds__(CAM_THREADS)
+k_lob_resid(int N, const float* __restrict__ X, const float* __restrict__ ZX,
+            const double* __restrict__ theta, const double* __restrict__ Minv, float* __restrict__ W,
+            double* partials, unsigned* counter, double* out) {
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) {
+    double r[3][4];
+    for (int a = 0; a < 3; ++a)
+      for (int j = 0; j < 4; ++j) {
+        const size_t e = (size_t)(3 * i + a) * 4 + j;
+        r[a][j] = double(ZX[e]) - theta[j] * double(X[e]);
+        v[j] += r[a][j] * r[a][j];
+      }
+    for (int a = 0; a < 3; ++a)
+      for (int j = 0; j < 4; ++j) {
+        double w = 0.0;
+        for (int b = 0; b < 3; ++b) w += Minv[(size_t)9 * i + 3 * a + b] * r[b][j];
+        W[(size_t)(3 * i + a) * 4 + j] = float(w);
+      }
+  }
+  grid_reduce<4>(v, partials, counter, [&](double* t) {
+    for (int j = 0; j < 4; ++j) out[j] = t[j];
+  });
+}
+
+// c[d][j] = <Vd_d, B_j> for the nd deflation columns (column-major, stride ld) and the 4 columns
+// of block B (c: nd x 4 row-major, nd <= 8)
+template <typename VT>
+__global__ void __launch_bounds__(CAM_THREADS)
+k_lob_defl_coef(int nn, int nd, const VT* __restrict__ Vd, size_t ld, const float* __restrict__ B,
+                double* partials, unsigned* counter, double* c) {
+  double v[32];
+  for (int k = 0; k < 32; ++k) v[k] = 0.0;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nn; e += gridDim.x * blockDim.x) {
+    double b[4];
+    for (int j = 0; j < 4; ++j) b[j] = B[(size_t)e * 4 + j];
+    for (int d = 0; d < nd; ++d) {
+      const double x = double(Vd[(size_t)d * ld + e]);
+      for (int j = 0; j < 4; ++j) v[d * 4 + j] += x * b[j];
+    }
+  }
+  grid_reduce<32>(v, partials, counter, [&](double* t) {
+    for (int k = 0; k < 32; ++k) c[k] = t[k];
+  });
+}
+// B -= Vd c (projection onto range(Y)^perp)
+template <typename VT>
+__global__ void k_lob_defl_apply(int nn, int nd, const VT* __restrict__ Vd, size_t ld,
+                                 const double* __restrict__ c, float* __restrict__ B) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nn; e += gridDim.x * blockDim.x)
+    for (int j = 0; j < 4; ++j) {
+      double s = 0.0;
+      for (int d = 0; d < nd; ++d) s += double(Vd[(size_t)d * ld + e]) * c[d * 4 + j];
+      B[(size_t)e * 4 + j] -= float(s);
+    }
+}
+
+// Gram blocks of S = [S0 S1 S2] (n x 12) and ZS: pair p < 6 is S_a^T S_b (a <= b), pair p >= 6
+// is S_a^T ZS_b; blockIdx.y = p, partial sums per x-block (16 values), FP64 accumulation.
+__device__ __constant__ int c_lob_pa[15] = {0, 0, 0, 1, 1, 2, 0, 0, 0, 1, 1, 1, 2, 2, 2};
+__device__ __constant__ int c_lob_pb[15] = {0, 1, 2, 1, 2, 2, 0, 1, 2, 0, 1, 2, 0, 1, 2};
+struct LobBlocks { const float* s[3]; const float* zs[3]; };
+__global__ void __launch_bounds__(256)
+k_lob_gram(int nn, LobBlocks B, double* __restrict__ part) {
+  const int p = blockIdx.y;
+  const float* A = B.s[c_lob_pa[p]];
+  const float* C = p < 6 ? B.s[c_lob_pb[p]] : B.zs[c_lob_pb[p]];
+  double acc[16];
+  for (int k = 0; k < 16; ++k) acc[k] = 0.0;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nn; e += gridDim.x * blockDim.x) {
+    const float4 a = *reinterpret_cast<const float4*>(A + (size_t)e * 4);
+    const float4 c = *reinterpret_cast<const float4*>(C + (size_t)e * 4);
+    const double av[4] = {a.x, a.y, a.z, a.w}, cv[4] = {c.x, c.y, c.z, c.w};
+    for (int x = 0; x < 4; ++x)
+      for (int y = 0; y < 4; ++y) acc[x * 4 + y] += av[x] * cv[y];
+  }
+  __shared__ double sh[16][8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int k = 0; k < 16; ++k) {
+    const double t = warp_sum(acc[k]);
+    if (lane == 0) sh[k][wid] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x < 16) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += sh[threadIdx.x][w];
+    part[((size_t)p * gridDim.x + blockIdx.x) * 16 + threadIdx.x] = t;
+  }
+}
+// out[p][16] = sum over x-blocks of part (fixed order)
+__global__ void k_lob_gram_finish(int nxb, const double* __restrict__ part, double* __restrict__ out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 15 * 16) return;
+  const int p = t / 16, k = t % 16;
+  double s = 0.0;
+  for (int x = 0; x < nxb; ++x) s += part[((size_t)p * nxb + x) * 16 + k];
+  out[t] = s;
+}
+
+// Xo = S C, ZXo = ZS C, Po = S CP, ZPo = ZS CP (C, CP: 12 x 4 row-major, FP64)
+__global__ void k_lob_update(int nn, LobBlocks B, const double* __restrict__ C,
+                             const double* __restrict__ CP, float* __restrict__ Xo,
+                             float* __restrict__ ZXo, float* __restrict__ Po, float* __restrict__ ZPo) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nn; e += gridDim.x * blockDim.x) {
+    double s[12], z[12];
+    for (int b = 0; b < 3; ++b)
+      for (int j = 0; j < 4; ++j) {
+        s[b * 4 + j] = B.s[b][(size_t)e * 4 + j];
+        z[b * 4 + j] = B.zs[b][(size_t)e * 4 + j];
+      }
+    for (int j = 0; j < 4; ++j) {
+      double x = 0, zx = 0, pp = 0, zp = 0;
+      for (int k = 0; k < 12; ++k) {
+        x += s[k] * C[k * 4 + j];
+        zx += z[k] * C[k * 4 + j];
+        pp += s[k] * CP[k * 4 + j];
+        zp += z[k] * CP[k * 4 + j];
+      }
+      Xo[(size_t)e * 4 + j] = float(x);
+      ZXo[(size_t)e * 4 + j] = float(zx);
+      Po[(size_t)e * 4 + j] = float(pp);
+      ZPo[(size_t)e * 4 + j] = float(zp);
+    }
+  }
+}
+
+// 4-column block filled with the seeded uniform(-1, 1) sequence (rows >= n zero)
+__global__ void k_lob_random(int nn, int n, uint64_t seed, float* __restrict__ X) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nn * 4; e += gridDim.x * blockDim.x) {
+    uint64_t z = seed + 0x9E3779B97F4A7C15ull * (uint64_t)(e + 1);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    X[e] = (e / 4 < n) ? float((double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0) : 0.f;
+  }
+}
+// dst (n_pad FP64) = column j of the block
+__global__ void k_lob_col(int nn, int j, const float* __restrict__ X, double* __restrict__ dst) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nn; e += gridDim.x * blockDim.x)
+    dst[e] = double(X[(size_t)e * 4 + j]);
+}
+
 struct Solver {
   xm_ctx* ctx;
   const DeviceQ& q;
@@ -217,6 +407,11 @@ struct Solver {
   float *lv32 = nullptr, *lW32 = nullptr, *lwf = nullptr, *lcf = nullptr;
   static constexpr int LPART_MAX = 64;   // column chunks of the reorthogonalisation product
   double* lpart = nullptr;               // LPART_MAX x n_pad partial sums
+  int last_nd = 0;                       // deflation columns of the last certificate's basis
+  // LOBPCG certificate: 12 blocks of n_pad x 4 floats, preconditioner, Gram partials, scalars
+  float* lob = nullptr;
+  double *lob_minv = nullptr, *lob_part = nullptr, *lob_small = nullptr;
+  int lob_nxb = 0;
   // stats
   xm_info info{};
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -242,7 +437,7 @@ struct Solver {
   ~Solver() {
     void* bufs[] = {bY, bYc, bW, bWc, bG, bGc, bYin, bEta, bHeta, bR, bD, bHd, bWd, bY64, bXi, bYh,
                     bZ, Lam, Lamc, pcMinv, pcB, d_sc, d_small, V, lw, lz, lalpha, lbeta, lc, lnrm,
-                    lritz, lv32, lW32, lwf, lcf, lpart};
+                    lritz, lv32, lW32, lwf, lcf, lpart, lob, lob_minv, lob_part, lob_small};
     for (void* p : bufs) if (p) cudaFree(p);
     if (h_sc) cudaFreeHost(h_sc);
     if (ev0) cudaEventDestroy(ev0);
@@ -414,7 +609,7 @@ struct Solver {
       }
       k_tcg_init<To, Ti, R><<<nb_cam, CAM_THREADS, 0, st>>>(
           N, Yin, (const To*)bG, (Ti*)bEta, (Ti*)bHeta, (Ti*)bR, (Ti*)bZ, (Ti*)bD, pcMinv, d_sc, Delta,
-          o.max_tcg, 1.0, 0.1, 0.5 * tol_abs, ctx->d_partials, ctx->d_counter);
+          o.max_tcg, 1.0, 0.1, bulk ? 0.5 * tol_abs : 0.0, ctx->d_partials, ctx->d_counter);
       ++launches;
       XM_CUDA_TRY(cudaGetLastError());
       // Chunks of CH iterations; the host reads the done flag of chunk k-1 while chunk k is
@@ -603,7 +798,186 @@ struct Solver {
   xm_status certify(int r, int prec_z, double* lam_def, double* lam_max, double* lam_range,
                     int kcap_steps = 0) {
     if (prec_z == XM_FP64) return certify_t<R, double>(r, prec_z, lam_def, lam_max, lam_range, kcap_steps);
+    if (kcap_steps == 0 && o.cert_lobpcg) {
+      bool conv = false;
+      XM_TRY(certify_lobpcg<R>(r, lam_def, lam_max, lam_range, &conv));
+      if (conv) return XM_OK;
+      if (o.verbose >= 1) fprintf(stderr, "[xm] LOBPCG certificate did not converge: Lanczos\n");
+    }
     return certify_t<R, float>(r, prec_z, lam_def, lam_max, lam_range, kcap_steps);
+  }
+
+  // Rayleigh-Ritz on the active columns of S = [X W P] (nb blocks of 4) from the 15 Gram blocks
+  // (SVQB: columns scaled to unit norm, near-dependent directions of S^T S dropped); C, CP:
+  // 12 x 4 coefficients of the 4 smallest Ritz vectors and of their [W P] part; false when
+  // fewer than 4 independent directions remain.
+  static bool lob_rayleigh_ritz(const double* blk, int nb, double* C, double* CP, double* theta) {
+    const int m = 4 * nb;
+    auto gidx = [](int a, int b) { static const int t[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}}; return t[a][b]; };
+    std::vector<double> G((size_t)m * m), H((size_t)m * m);
+    for (int a = 0; a < nb; ++a)
+      for (int b = 0; b < nb; ++b)
+        for (int x = 0; x < 4; ++x)
+          for (int y = 0; y < 4; ++y) {
+            G[(size_t)(4 * a + x) * m + 4 * b + y] =
+                a <= b ? blk[gidx(a, b) * 16 + x * 4 + y] : blk[gidx(b, a) * 16 + y * 4 + x];
+            H[(size_t)(4 * a + x) * m + 4 * b + y] = blk[(6 + 3 * a + b) * 16 + x * 4 + y];
+          }
+    std::vector<double> Dn(m), Gn((size_t)m * m), Hn((size_t)m * m);
+    double gmax = 0.0;
+    for (int j = 0; j < m; ++j) gmax = std::max(gmax, G[(size_t)j * m + j]);
+    for (int j = 0; j < m; ++j) {
+      const double g = G[(size_t)j * m + j];
+      Dn[j] = (g > 1e-20 * gmax && g > 0.0) ? 1.0 / std::sqrt(g) : 0.0;
+    }
+    for (int a = 0; a < m; ++a)
+      for (int b = 0; b < m; ++b) {
+        Gn[(size_t)a * m + b] = 0.5 * (G[(size_t)a * m + b] + G[(size_t)b * m + a]) * Dn[a] * Dn[b];
+        Hn[(size_t)a * m + b] = 0.5 * (H[(size_t)a * m + b] + H[(size_t)b * m + a]) * Dn[a] * Dn[b];
+      }
+    std::vector<double> w, V;
+    sym_eig_desc(m, Gn, w, V);
+    std::vector<int> keep;
+    for (int j = 0; j < m; ++j)
+      if (w[j] > 1e-10 * w[0]) keep.push_back(j);
+    const int k = (int)keep.size();
+    if (k < 4) return false;
+    std::vector<double> Bm((size_t)m * k);   // m x k: kept eigenvectors / sqrt(eigenvalue)
+    for (int a = 0; a < m; ++a)
+      for (int c = 0; c < k; ++c) Bm[(size_t)a * k + c] = V[(size_t)a * m + keep[c]] / std::sqrt(w[keep[c]]);
+    std::vector<double> Hr((size_t)k * k, 0.0);
+    for (int c = 0; c < k; ++c)
+      for (int d = 0; d < k; ++d) {
+        double t = 0.0;
+        for (int a = 0; a < m; ++a)
+          for (int b = 0; b < m; ++b) t += Bm[(size_t)a * k + c] * Hn[(size_t)a * m + b] * Bm[(size_t)b * k + d];
+        Hr[(size_t)c * k + d] = t;
+      }
+    for (int c = 0; c < k; ++c)
+      for (int d = c + 1; d < k; ++d) Hr[(size_t)c * k + d] = Hr[(size_t)d * k + c] = 0.5 * (Hr[(size_t)c * k + d] + Hr[(size_t)d * k + c]);
+    std::vector<double> hw, HV;
+    sym_eig_desc(k, Hr, hw, HV);   // descending: the 4 smallest are the last
+    for (int i = 0; i < 48; ++i) { C[i] = 0.0; CP[i] = 0.0; }
+    for (int j = 0; j < 4; ++j) {
+      const int col = k - 1 - j;
+      theta[j] = hw[col];
+      for (int a = 0; a < m; ++a) {
+        double t = 0.0;
+        for (int c = 0; c < k; ++c) t += Bm[(size_t)a * k + c] * HV[(size_t)c * k + col];
+        C[a * 4 + j] = Dn[a] * t;
+        CP[a * 4 + j] = a >= 4 ? Dn[a] * t : 0.0;
+      }
+    }
+    return true;
+  }
+
+  // Thm. 1 certificate with FP32 Z products by LOBPCG (Knyazev 2001) on Z restricted to
+  // range(Y)^perp: blocks of 4 vectors (one R = 4 sweep per iteration), 3 x 3 block-Jacobi
+  // preconditioner of Z, Rayleigh-Ritz in FP64.  lambda_max and the Rayleigh quotients on
+  // range(Y) come from a 40-step Lanczos run.  Stops when the smallest Ritz pair's residual is
+  // <= 1e-6 |lambda_max| (its Ritz value is then within that of lambda_min); *converged = false
+  // after 300 iterations (the caller falls back to Lanczos).
+  template <int R>
+  xm_status certify_lobpcg(int r, double* lam_def, double* lam_max, double* lam_range, bool* converged) {
+    *converged = false;
+    auto tic = std::chrono::steady_clock::now();
+    const double t_cert_before = info.t_cert_s;
+    double ld_short = 0.0;
+    XM_TRY(certify_t<R, float>(r, XM_FP32_BULK, &ld_short, lam_max, lam_range, 40));
+    if (!q.q64) return XM_OK;   // the preconditioner reads the FP64 diagonal blocks
+    const int nn = n_pad, nd = last_nd;
+    const float* Vd = static_cast<const float*>(V);
+    const size_t blk = (size_t)nn * 4;
+    if (!lob) {
+      XM_CUDA_TRY(cudaMalloc(&lob, sizeof(float) * blk * 12));
+      XM_CUDA_TRY(cudaMemsetAsync(lob, 0, sizeof(float) * blk * 12, st));
+      XM_CUDA_TRY(cudaMalloc(&lob_minv, sizeof(double) * 9 * (size_t)N));
+      lob_nxb = std::max(1, std::min((nn + 255) / 256, ctx->num_sms * 2));
+      XM_CUDA_TRY(cudaMalloc(&lob_part, sizeof(double) * 15 * 16 * (size_t)lob_nxb));
+      XM_CUDA_TRY(cudaMalloc(&lob_small, sizeof(double) * 512));
+    }
+    float *X = lob, *ZX = lob + blk, *W = lob + 2 * blk, *ZW = lob + 3 * blk, *P = lob + 4 * blk,
+          *ZP = lob + 5 * blk, *X2 = lob + 6 * blk, *ZX2 = lob + 7 * blk, *P2 = lob + 8 * blk,
+          *ZP2 = lob + 9 * blk, *Wz = lob + 10 * blk, *Zero = lob + 11 * blk;
+    double* gram = lob_small;          // 15 x 16
+    double* dC = lob_small + 240;      // 48
+    double* dCP = lob_small + 288;     // 48
+    double* dth = lob_small + 336;     // 4
+    double* dnorm = lob_small + 344;   // 4
+    double* dcoef = lob_small + 352;   // 32
+    const int gv = grid_elems((size_t)nn);
+    auto deflate = [&](float* B) {
+      if (nd == 0) return;
+      k_lob_defl_coef<float><<<gv, CAM_THREADS, 0, st>>>(nn, nd, Vd, nn, B, ctx->d_partials, ctx->d_counter, dcoef);
+      k_lob_defl_apply<float><<<gv, CAM_THREADS, 0, st>>>(nn, nd, Vd, nn, dcoef, B);
+      launches += 2;
+    };
+    auto zmul4 = [&](float* B, float* ZB) -> xm_status {
+      XM_TRY(sweep(XM_FP32_BULK, 4, B, Wz, nullptr, false));
+      k_zv4<<<nb_cam, CAM_THREADS, 0, st>>>(N, Wz, B, Lam, ZB);
+      ++launches;
+      return XM_OK;
+    };
+    std::vector<double> hblk(15 * 16 + 8);
+    auto gram_rr = [&](float* S1, float* ZS1, float* S2, float* ZS2, int nb, double* theta, bool* ok) -> xm_status {
+      LobBlocks Bk{{X, S1, S2}, {ZX, ZS1, ZS2}};
+      k_lob_gram<<<dim3(lob_nxb, 15), 256, 0, st>>>(nn, Bk, lob_part);
+      k_lob_gram_finish<<<1, 256, 0, st>>>(lob_nxb, lob_part, gram);
+      launches += 2;
+      XM_CUDA_TRY(cudaMemcpyAsync(hblk.data(), gram, sizeof(double) * 15 * 16, cudaMemcpyDeviceToHost, st));
+      XM_CUDA_TRY(cudaMemcpyAsync(hblk.data() + 240, dnorm, sizeof(double) * 4, cudaMemcpyDeviceToHost, st));
+      XM_CUDA_TRY(cudaStreamSynchronize(st));
+      double C[48], CP[48];
+      *ok = lob_rayleigh_ritz(hblk.data(), nb, C, CP, theta);
+      if (!*ok) return XM_OK;
+      XM_CUDA_TRY(cudaMemcpyAsync(dC, C, sizeof(C), cudaMemcpyHostToDevice, st));
+      XM_CUDA_TRY(cudaMemcpyAsync(dCP, CP, sizeof(CP), cudaMemcpyHostToDevice, st));
+      XM_CUDA_TRY(cudaMemcpyAsync(dth, theta, sizeof(double) * 4, cudaMemcpyHostToDevice, st));
+      k_lob_update<<<gv, CAM_THREADS, 0, st>>>(nn, Bk, dC, dCP, X2, ZX2, P2, ZP2);
+      ++launches;
+      std::swap(X, X2); std::swap(ZX, ZX2); std::swap(P, P2); std::swap(ZP, ZP2);
+      // the host copies above read C and CP before they go out of scope
+      XM_CUDA_TRY(cudaStreamSynchronize(st));
+      return XM_OK;
+    };
+    k_zblock_precond<<<nb_cam, CAM_THREADS, 0, st>>>(N, q.q64, q.nt, Lam, lob_minv);
+    k_lob_random<<<gv, CAM_THREADS, 0, st>>>(nn, n, o.seed ^ 0x5DEECE66Dull, X);
+    launches += 2;
+    deflate(X);
+    XM_TRY(zmul4(X, ZX));
+    double theta[4] = {0, 0, 0, 0};
+    bool ok = false;
+    XM_TRY(gram_rr(Zero, Zero, Zero, Zero, 1, theta, &ok));   // orthonormal Ritz basis of span X
+    if (!ok) return XM_OK;
+    const double tol = 1e-6 * std::max(std::fabs(*lam_max), 1e-300);
+    bool have_p = false;
+    int it = 0;
+    double rn0 = 0.0;
+    for (it = 1; it <= 300; ++it) {
+      k_lob_resid<<<nb_cam, CAM_THREADS, 0, st>>>(N, X, ZX, dth, lob_minv, W, ctx->d_partials, ctx->d_counter, dnorm);
+      ++launches;
+      deflate(W);
+      XM_TRY(zmul4(W, ZW));
+      XM_TRY(gram_rr(W, ZW, have_p ? P : Zero, have_p ? ZP : Zero, have_p ? 3 : 2, theta, &ok));
+      rn0 = std::sqrt(std::max(hblk[240], 0.0));   // residual of the Ritz pair before this update
+      ++info.n_lanczos;
+      if (!ok) return XM_OK;
+      if (rn0 <= tol) { *converged = true; break; }
+      have_p = true;
+      XM_CUDA_TRY(cudaGetLastError());
+    }
+    if (!*converged) return XM_OK;
+    *lam_def = theta[0];
+    // escape direction: the Ritz vector of theta_min (FP64)
+    k_lob_col<<<gv, CAM_THREADS, 0, st>>>(nn, 0, X, lritz);
+    ++launches;
+    XM_CUDA_TRY(cudaStreamSynchronize(st));
+    info.lanczos_converged = 1;
+    info.t_cert_s = t_cert_before + std::chrono::duration<double>(std::chrono::steady_clock::now() - tic).count();
+    if (o.verbose >= 1)
+      fprintf(stderr, "[xm] LOBPCG certificate: %d iterations, theta_min=%.6e residual=%.3e\n", it,
+              theta[0], rn0);
+    return XM_OK;
   }
 
   template <int R, typename VT>
@@ -660,6 +1034,7 @@ struct Solver {
       k_col_from_rows<VT, R><<<gv, CAM_THREADS, 0, st>>>(nn, j, (const double*)bXi, Vb + (size_t)j * nn);
       ++launches;
     }
+    last_nd = nd;
     // Rayleigh quotients of Z on range(Y): Vd^T Z Vd (nd x nd)
     std::vector<double> zr((size_t)nd * nd, 0.0);
     for (int j = 0; j < nd; ++j) {
@@ -1128,6 +1503,7 @@ xm_status check_opts(const DeviceQ& q, const xm_opts& o) {
   if (!(o.scale_reg >= 0.0) || !std::isfinite(o.scale_reg))
     return set_error(XM_EINVAL, "opts: scale_reg must be finite and >= 0 (got %g)", o.scale_reg);
   if (o.precond != 0 && o.precond != 1) return set_error(XM_EINVAL, "opts: precond must be 0 or 1");
+  if (o.cert_lobpcg != 0 && o.cert_lobpcg != 1) return set_error(XM_EINVAL, "opts: cert_lobpcg must be 0 or 1");
   if (o.bulk_stall < 0 || o.bulk_stall > o.max_outer)
     return set_error(XM_EINVAL, "opts: bulk_stall must be in [0, max_outer] (got %d)", o.bulk_stall);
   return XM_OK;

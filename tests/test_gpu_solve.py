@@ -170,3 +170,44 @@ def test_bulk_stall_option():
     assert e.value.status == xm.XM_EINVAL
     q.free()
     ctx.close()
+
+
+@pytest.mark.parametrize("lob", [0, 1])
+def test_fp32_certificate_lobpcg_and_lanczos(C, lob):
+    """The FP32-Z certificate by block-Jacobi LOBPCG (opts.cert_lobpcg = 1, the default) and by
+    Lanczos (0) both match the oracle's deflated minimum to 1e-5 of lambda_max, at the certified
+    optimum and at the rank-3 saddle of the [I..I] start (Thm. 2: not certified)."""
+    from paper_2502_04640_b300 import xm
+    sc = scenes.config1()
+    Qo = O.build_Q_schur(sc.N, sc.M, sc.cam, sc.lmk, sc.ukp, sc.w)
+    q = xm.xm_build_Q(C, sc.N, sc.M, *xm.scene_tensors(sc))
+    opts = xm.xm_default_opts(prec=xm.XM_FP32_BULK, cert_lobpcg=lob)
+    ref = O.solve(Qo, r0=4)
+    good = xm.xm_certify(q, torch.tensor(ref.Y, device="cuda"), opts)
+    cg = O.certify(Qo, ref.Y)
+    assert good["info"]["certified"] == 1 and good["info"]["lanczos_converged"] == 1
+    assert abs(good["info"]["lambda_min_deflated"] - cg.lam_min_deflated) <= 1e-5 * cg.lam_max_Q
+    r3 = O.rtr(Qo, O.initial_point(sc.N, 3))
+    bad = xm.xm_certify(q, torch.tensor(r3.Y, device="cuda"), opts)
+    c3 = O.certify(Qo, r3.Y)
+    assert bad["info"]["certified"] == 0
+    assert abs(bad["info"]["lambda_min_deflated"] - c3.lam_min_deflated) <= 1e-5 * c3.lam_max_Q
+    q.free()
+
+
+def test_lobpcg_certificate_agrees_with_lanczos_mid_size(C):
+    """300 cameras with outliers: the two FP32-Z certificates agree on the decision and on
+    lambda_min to 1e-5 of lambda_max."""
+    from paper_2502_04640_b300 import xm
+    sc = scenes.random_scene(300, 6000, noise=0.02, outlier_frac=0.05, seed=31)
+    q = xm.xm_build_Q(C, sc.N, sc.M, *xm.scene_tensors(sc))
+    out = xm.xm_solve(q, xm.xm_default_opts(prec=xm.XM_FP64))
+    assert out["info"]["certified"] == 1
+    r = out["info"]["rank"]
+    Y = out["Y"][:, :r].contiguous()
+    res = {}
+    for lob in (0, 1):
+        res[lob] = xm.xm_certify(q, Y, xm.xm_default_opts(prec=xm.XM_FP32_BULK, cert_lobpcg=lob))["info"]
+    assert res[0]["certified"] == res[1]["certified"] == 1
+    assert abs(res[0]["lambda_min_deflated"] - res[1]["lambda_min_deflated"]) <= 1e-5 * res[0]["lambda_max"]
+    q.free()
