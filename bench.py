@@ -524,7 +524,7 @@ def run_recover(args):
     cpu = None
     if not args.no_cpu:
         from oracle import xm_oracle as O
-        sub = scenes.sub_scene(sc, min(400, sc.N))
+        sub = scenes.sub_scene(sc, min(60, sc.N))   # the oracle's sparse solve is slow: keep it bounded
         Q = O.build_Q_schur(sub.N, sub.M, sub.cam, sub.lmk, sub.ukp, sub.w)
         res = O.solve(Q, r0=4, mu=wopts.get("scale_reg", 0.0))
         U3 = np.concatenate([res.s[i] * res.R[i] for i in range(sub.N)], axis=1)
