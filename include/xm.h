@@ -268,8 +268,9 @@ typedef struct xm_adj_info {
   double t_resid_s;        /* wall time of the residual pull-back (incl. the Cholesky)         */
   double t_total_s;
   long launches;           /* kernel launches of this call (library calls not counted)        */
-  int dense_precond;       /* 1: CG preconditioned by the dense factor of Z + gamma Pi_Y
-                              (n <= 40000); 0: by Z's 3 x 3 diagonal blocks                   */
+  int dense_precond;       /* 1: CG preconditioned by the explicit FP32 inverse of the dense
+                              Z + gamma Pi_Y (n <= 40000), packed like Q and applied by the
+                              sweep; 0: by Z's 3 x 3 diagonal blocks                          */
   double gamma;            /* curvature given to range(Y) by the dense preconditioner          */
 } xm_adj_info;
 

@@ -303,8 +303,8 @@ k_pcg_update(int N, const T* __restrict__ Y, T* __restrict__ x, T* __restrict__ 
   grid_reduce<R * R>(v, partials, counter, [&](double* t) { omega_from_C<R>(t, defl, Om); });
 }
 
-// v -= Y Om (deflation); optionally also writes v column-major in FP32 (n x R, ld n) for the
-// dense preconditioner's triangular solves
+// v -= Y Om (deflation); optionally also writes v in FP32 (n_pad x R, row-major) as the input
+// of the dense preconditioner's sweep
 template <typename T, int R>
 __global__ void __launch_bounds__(CAM_THREADS)
 k_deflate(int N, const T* __restrict__ Y, T* __restrict__ v, const double* __restrict__ Om,
@@ -328,7 +328,7 @@ k_deflate(int N, const T* __restrict__ Y, T* __restrict__ v, const double* __res
 #pragma unroll
       for (int k = 0; k < R; ++k) t += y[a][k] * O[k][j];
       vv[a][j] -= t;
-      if (col) col[(size_t)j * n + 3 * i + a] = float(vv[a][j]);
+      if (col) col[(size_t)(3 * i + a) * R + j] = float(vv[a][j]);
     }
   store_block<T, double, R>(v, i, vv);
 }
@@ -355,10 +355,11 @@ k_precond_bj(int N, const T* __restrict__ Y, const T* __restrict__ r, T* __restr
   grid_reduce<R * R>(v, partials, counter, [&](double* t) { omega_from_C<R>(t, defl, Om); });
 }
 
-// dense preconditioner, after the two triangular solves: z = P_Y(col / 2), C = Y^T z -> Om
+// dense preconditioner, after the sweep with its inverse: z = P_Y(col / 2), C = Y^T z -> Om;
+// col (the sweep's output, n_pad x R row-major) is zeroed for the next sweep's accumulation
 template <typename T, int R>
 __global__ void __launch_bounds__(CAM_THREADS)
-k_precond_from_col(int N, const T* __restrict__ Y, const float* __restrict__ col, T* __restrict__ z,
+k_precond_from_col(int N, const T* __restrict__ Y, float* __restrict__ col, T* __restrict__ z,
                    const double* __restrict__ defl, double* __restrict__ Om, Scal* sc,
                    double* partials, unsigned* counter) {
   if (sc->done) return;
@@ -369,11 +370,14 @@ k_precond_from_col(int N, const T* __restrict__ Y, const float* __restrict__ col
   if (i < N) {
     double y[3][R], zz[3][R];
     load_block<T, double, R>(Y, i, y);
-    const size_t n = (size_t)3 * N;
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
-      for (int j = 0; j < R; ++j) zz[a][j] = 0.5 * double(col[(size_t)j * n + 3 * i + a]);
+      for (int j = 0; j < R; ++j) {
+        float* c = col + (size_t)(3 * i + a) * R + j;
+        zz[a][j] = 0.5 * double(*c);
+        *c = 0.0f;
+      }
     double S[3][3], al;
     dual_block<double, R>(zz, y, i == 0, S, al);
 #pragma unroll
@@ -598,6 +602,7 @@ namespace {
 struct Buf {
   void* p = nullptr;
   ~Buf() { if (p) cudaFree(p); }
+  void reset() { if (p) cudaFree(p); p = nullptr; }
   template <typename T> T* as() const { return static_cast<T*>(p); }
 };
 
@@ -674,7 +679,8 @@ static xm_status backward_impl(xm_ctx* ctx, const DeviceQ& q, const xm_opts& o, 
 
   // ---- vectors (FP64: Y, G, Lam, g_L, lambda, res, Wd; inner: Y, G, eta, Heta, r, d, Hd, Wd)
   Buf bY, bG, bLam, bMinv, bgL, blam, bres, bWd, bsc, bYi, bGi, beta, bHeta, br, bd, bHd, bWi;
-  Buf bsmall, bZ, bcol, bwork, binfo;
+  Buf bsmall, bZ, bcol, bcol2, bwork, binfo;
+  struct TilesGuard { DeviceQ q; ~TilesGuard() { free_tiles(q); } } Pinv;
   for (Buf* b : {&bY, &bG, &bgL, &blam, &bres, &bWd}) {
     XM_CUDA_TRY(cudaMalloc(&b->p, vec64));
     XM_CUDA_TRY(cudaMemsetAsync(b->p, 0, vec64, st));
@@ -770,7 +776,6 @@ static xm_status backward_impl(xm_ctx* ctx, const DeviceQ& q, const xm_opts& o, 
     inf.dense_precond = 0;
     if (n <= DENSE_PRECOND_MAX_N && gnorm > 0.0) {
       XM_CUDA_TRY(cudaMalloc(&bZ.p, sizeof(float) * (size_t)n * n));
-      XM_CUDA_TRY(cudaMalloc(&bcol.p, sizeof(float) * (size_t)n * R));
       k_dense_Z<R><<<grid_cap((size_t)n * n, 256, ctx->num_sms * 4), 256, 0, st>>>(
           N, q.q64, q.nt, bLam.as<double>(), bY.as<double>(), dsm + SM_GP, gamma, bZ.as<float>());
       ++launches;
@@ -795,18 +800,37 @@ static xm_status backward_impl(xm_ctx* ctx, const DeviceQ& q, const xm_opts& o, 
         XM_CUDA_TRY(cudaStreamSynchronize(st));
       }
       if (ok && hinfo == 0) {
-        inf.dense_precond = 1;
-        if (!ctx->cublas) {
-          cublasHandle_t h;
-          if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS)
-            return set_error(XM_ECUDA, "xm_backward: cublasCreate failed");
-          ctx->cublas = h;
+        // Explicit inverse from the factor (lower triangle, in place), packed into FP32
+        // upper-triangle tiles: applying it is then one Q.Y-style sweep per CG step, which
+        // streams n^2/2 floats at the sweep's HBM rate, where triangular solves with the factor
+        // are long chains of small dependent steps.  A preconditioner needs no more accuracy
+        // than the FP32 inverse gives.
+        int lw2 = 0, hinv = 1;
+        if (cusolverDnSpotri_bufferSize(cs, CUBLAS_FILL_MODE_LOWER, n, bZ.as<float>(), n, &lw2) ==
+            CUSOLVER_STATUS_SUCCESS) {
+          Buf bw2;
+          XM_CUDA_TRY(cudaMalloc(&bw2.p, sizeof(float) * (size_t)std::max(lw2, 1)));
+          if (cusolverDnSpotri(cs, CUBLAS_FILL_MODE_LOWER, n, bZ.as<float>(), n, bw2.as<float>(), lw2,
+                               binfo.as<int>()) == CUSOLVER_STATUS_SUCCESS) {
+            XM_CUDA_TRY(cudaMemcpyAsync(&hinv, binfo.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+            XM_CUDA_TRY(cudaStreamSynchronize(st));
+          }
         }
-        if (cublasSetStream(static_cast<cublasHandle_t>(ctx->cublas), st) != CUBLAS_STATUS_SUCCESS)
-          return set_error(XM_ECUDA, "xm_backward: cublasSetStream failed");
-      } else {
-        cudaFree(bZ.p); bZ.p = nullptr;
+        if (hinv == 0) {
+          XM_TRY(alloc_tiles(ctx, Pinv.q, N, XM_STORE_FP32));
+          XM_TRY(pack_dense_f32(ctx, Pinv.q, bZ.as<float>()));
+          ++launches;
+          const size_t colb = sizeof(float) * rows * R;
+          XM_CUDA_TRY(cudaMalloc(&bcol.p, colb));
+          XM_CUDA_TRY(cudaMalloc(&bcol2.p, colb));
+          XM_CUDA_TRY(cudaMemsetAsync(bcol.p, 0, colb, st));
+          XM_CUDA_TRY(cudaMemsetAsync(bcol2.p, 0, colb, st));
+          inf.dense_precond = 1;
+        }
       }
+      XM_CUDA_TRY(cudaStreamSynchronize(st));   // the packing has read the inverse
+      bwork.reset();
+      bZ.reset();
     }
     if (!inf.dense_precond) {
       k_adj_precond<<<nb_cam, CAM_THREADS, 0, st>>>(N, q.q64, q.nt, bLam.as<double>(), bMinv.as<double>());
@@ -816,17 +840,6 @@ static xm_status backward_impl(xm_ctx* ctx, const DeviceQ& q, const xm_opts& o, 
     inf.gamma = gamma;
   }
   const bool dense = inf.dense_precond != 0;
-  // z = M^-1 r for the dense preconditioner: two triangular solves on the FP32 column copy
-  auto trsm_pair = [&]() -> xm_status {
-    cublasHandle_t cb = static_cast<cublasHandle_t>(ctx->cublas);
-    const float one = 1.0f;
-    if (cublasStrsm(cb, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N, CUBLAS_DIAG_NON_UNIT, n, R,
-                    &one, bZ.as<float>(), n, bcol.as<float>(), n) != CUBLAS_STATUS_SUCCESS ||
-        cublasStrsm(cb, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T, CUBLAS_DIAG_NON_UNIT, n, R,
-                    &one, bZ.as<float>(), n, bcol.as<float>(), n) != CUBLAS_STATUS_SUCCESS)
-      return set_error(XM_ECUDA, "xm_backward: cublasStrsm failed");
-    return XM_OK;
-  };
 
   // ---- 2. Hess[lambda] = g_L: CG, FP64 residual refinement around an FP32 inner solve
   const double target = o.grad_tol_rel * gnorm;
@@ -888,9 +901,10 @@ static xm_status backward_impl(xm_ctx* ctx, const DeviceQ& q, const xm_opts& o, 
         // z = deflated, projected M^-1 r (r already deflated)
         auto precond = [&]() -> xm_status {
           if (dense) {
-            XM_TRY(trsm_pair());
+            XM_TRY(qy_launch(ctx, Pinv.q, XM_FP32_BULK, R, bcol.p, bcol2.p, &sc->done, st));
+            ++launches;
             k_precond_from_col<Ti, R><<<nb_cam, CAM_THREADS, 0, st>>>(
-                N, Yi, bcol.as<float>(), bHeta.as<Ti>(), defl, Om, sc, ctx->d_partials, ctx->d_counter);
+                N, Yi, bcol2.as<float>(), bHeta.as<Ti>(), defl, Om, sc, ctx->d_partials, ctx->d_counter);
           } else {
             k_precond_bj<Ti, R><<<nb_cam, CAM_THREADS, 0, st>>>(
                 N, Yi, br.as<Ti>(), bHeta.as<Ti>(), bMinv.as<double>(), defl, Om, sc, ctx->d_partials,

@@ -184,8 +184,10 @@ __global__ void k_landmark_schur(int M, int n, int N, const int64_t* off, const 
 }
 
 // ------------------------------------------------------------------ tile packing
-// Reads the upper triangle (row <= col) of a row-major n x n FP64 matrix; one block per tile.
-__global__ void k_pack_tiles(const double* __restrict__ Qd, int n, int nt, int64_t ntiles,
+// Reads the upper triangle (row <= col) of a row-major n x n matrix (equivalently the lower
+// triangle of a column-major one); one block per tile.
+template <typename TI>
+__global__ void k_pack_tiles(const TI* __restrict__ Qd, int n, int nt, int64_t ntiles,
                              double* q64, float* q32, __nv_bfloat16* q16) {
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     // tile coordinates from the linear index (row-major upper triangle)
@@ -202,8 +204,8 @@ __global__ void k_pack_tiles(const double* __restrict__ Qd, int n, int nt, int64
       const int row = I * TILE + a, col = J * TILE + b;
       double v = 0.0;
       if (row < n && col < n) {
-        if (I < J || a < b) v = Qd[(size_t)row * n + col];
-        else if (a == b) v = 0.5 * Qd[(size_t)row * n + col];
+        if (I < J || a < b) v = (double)Qd[(size_t)row * n + col];
+        else if (a == b) v = 0.5 * (double)Qd[(size_t)row * n + col];
       }
       if (q64) q64[g0 + e] = v;
       if (q32) q32[g0 + e] = (float)v;
@@ -258,7 +260,14 @@ void free_tiles(DeviceQ& q) {
 
 xm_status pack_dense(xm_ctx* ctx, DeviceQ& q, const double* Qd) {
   const int grid = (int)(q.ntiles < (int64_t)ctx->num_sms * 16 ? q.ntiles : (int64_t)ctx->num_sms * 16);
-  k_pack_tiles<<<grid, 256, 0, ctx->stream>>>(Qd, q.n, q.nt, q.ntiles, q.q64, q.q32, q.q16);
+  k_pack_tiles<double><<<grid, 256, 0, ctx->stream>>>(Qd, q.n, q.nt, q.ntiles, q.q64, q.q32, q.q16);
+  XM_CUDA_TRY(cudaGetLastError());
+  return XM_OK;
+}
+
+xm_status pack_dense_f32(xm_ctx* ctx, DeviceQ& q, const float* A) {
+  const int grid = (int)(q.ntiles < (int64_t)ctx->num_sms * 16 ? q.ntiles : (int64_t)ctx->num_sms * 16);
+  k_pack_tiles<float><<<grid, 256, 0, ctx->stream>>>(A, q.n, q.nt, q.ntiles, q.q64, q.q32, q.q16);
   XM_CUDA_TRY(cudaGetLastError());
   return XM_OK;
 }

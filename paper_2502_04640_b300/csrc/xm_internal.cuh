@@ -100,6 +100,11 @@ xm_status ensure_partials(xm_ctx* ctx, size_t ndoubles);
 // ------------------------------------------------------------------ sweep (xm_qy.cu)
 // W = Q Y (n_pad x R, row-major, zero-initialised by the caller: the kernel accumulates).
 // skip: optional device flag; when non-zero the launch does nothing (early-exit of loops).
+// packed tiles (alloc_tiles/free_tiles in the build); pack_dense_f32 packs the lower triangle of
+// a column-major n x n FP32 symmetric matrix into the copies q's mask holds
+xm_status alloc_tiles(xm_ctx* ctx, DeviceQ& q, int N, unsigned mask);
+void free_tiles(DeviceQ& q);
+xm_status pack_dense_f32(xm_ctx* ctx, DeviceQ& q, const float* A);
 xm_status qy_launch(xm_ctx* ctx, const DeviceQ& q, int prec, int R, const void* Y, void* W,
                     const int* skip, cudaStream_t st);
 

@@ -71,6 +71,7 @@ def test_backward_matches_oracle_adjoint(C, name, prec):
                                              torch.as_tensor(D, device="cuda:0"), bopts,
                                              want_lambda=True)
     assert st == 0 and info["res_rel"] <= 1e-12
+    assert info["dense_precond"] == 1        # the inverse's sweep preconditions every case here
     Y = out["Y"].cpu().numpy()[:, :r]
     ref_u, ref_w, ref_lam = O.adjoint(sc.N, sc.M, sc.cam, sc.lmk, sc.ukp, sc.w, Y, D)
     assert _max_rel(d_u.cpu().numpy(), ref_u) <= 1e-6
