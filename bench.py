@@ -245,11 +245,12 @@ def run_sweep_only(args):
 def update_tensor_flops(N: int) -> float:
     """BF16 tensor FLOPs of the translation elimination on the tensor cores: 36 digit pairs
     (levels 0..7) of (a) the rank-(N-1) product over the n(n+1)/2 entries of the upper
-    triangle, (b) the block updates of the blocked triangular solve and (c) the trailing updates
-    of the blocked Cholesky factor (lower triangle), both with 512-row blocks; n = 3N."""
+    triangle, (b) the blocked triangular solve: per 512-row block the product with the diagonal
+    block's inverse and the block update of the rows below, and (c) the trailing updates of the
+    blocked Cholesky factor (lower triangle), 512-row blocks; n = 3N."""
     n, K = 3 * N, N - 1
     syrk = 36 * 2.0 * K * n * (n + 1) / 2
-    trsm = sum(36 * 2.0 * (K - i0 - min(512, K - i0)) * n * min(512, K - i0) for i0 in range(0, K, 512))
+    trsm = sum(36 * 2.0 * (K - i0) * n * min(512, K - i0) for i0 in range(0, K, 512))
     chol = sum(36 * 2.0 * (K - i0 - min(512, K - i0)) ** 2 / 2 * min(512, K - i0) for i0 in range(0, K, 512))
     return syrk + trsm + chol
 
@@ -275,8 +276,9 @@ def update_report(N: int, path: int, t_update: float) -> dict:
         ach = update_tensor_flops(N) / t_update / 1e12
         rep["roofline"] = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
                            "frac": ach / pk, "traffic": None,
-                           "kernel": "k_oz_mma<SYRK> + k_oz_mma<GEMM> block updates (+ digit splits, "
-                                     "FP64 diagonal blocks and panels, packing)",
+                           "kernel": "k_oz_mma<SYRK> + k_oz_mma<GEMM> (triangular solve, Cholesky updates) "
+                                     "(+ digit splits, FP64 diagonal inverses, Cholesky diagonal "
+                                     "blocks and panels, packing)",
                            "flops": update_tensor_flops(N), "peak_kind": kind + " bf16 burst"}
     return rep
 

@@ -22,9 +22,10 @@
 //   OZ_SYRK  Q = P - C^T C into the packed upper-triangle tiles of the sweep (FP64 accumulator
 //            tile, then P added, diagonal halved, lower triangle and padding zeroed, FP32 and
 //            BF16 copies written);
-//   OZ_GEMM  out -= A B^T into a column-major FP64 matrix: the block updates X_rest -= L_rest,i X_i
-//            of a right-looking blocked triangular solve (the 512 x 512 diagonal blocks solved by
-//            cuBLAS DTRSM in FP64), and the trailing updates S_rest -= L_k L_k^T of a right-looking
+//   OZ_GEMM  out -= A B^T into a column-major FP64 matrix: the steps X_i = 0 - (-L_ii^{-1}) X_i and
+//            the block updates X_rest -= L_rest,i X_i of a right-looking blocked triangular solve
+//            (the 512 x 512 diagonal-block inverses formed in FP64 by cuBLAS), and the trailing
+//            updates S_rest -= L_k L_k^T of a right-looking
 //            blocked Cholesky factorisation (diagonal blocks by cuSOLVER, panels by DTRSM, FP64;
 //            only tiles meeting the lower triangle).
 //
@@ -135,18 +136,50 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
-// 8 digits of x (|x| < 1): d_s = trunc(2^7 r_s), r_{s+1} = 2^7 r_s - d_s (all steps exact)
-__device__ __forceinline__ void digits8(double x, double (&d)[OZ_SLICES]) {
+// 8 digits of x = v 2^{-e} (|v| < 2^e): d_s = trunc(2^7 r_s), r_0 = x, r_{s+1} = 2^7 r_s - d_s.
+// Each step truncates toward zero, so d_s carries the sign of x and |d_s| is digit s (most
+// significant first) of the base-128 expansion of floor(|x| 2^56).  That integer is read off the
+// bits of v: |v| = m 2^{ex} with m the 53-bit significand, floor(|x| 2^56) = floor(m 2^{ex+56-e})
+// (< 2^56 since |x| < 1).  Integer operations only: B300's FP64 pipe is 1/64 of its FP32 rate.
+__device__ __forceinline__ void digits8(double v, int e, int (&d)[OZ_SLICES]) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+  const int E = (int)((bits >> 52) & 0x7FFu);
+  unsigned long long m = bits & 0xFFFFFFFFFFFFFull;
+  int ex = -1074;                                    // subnormal (or zero) v
+  if (E != 0) { m |= 1ull << 52; ex = E - 1075; }
+  const int sh = ex + 56 - e;                        // <= 3 because |v| < 2^e
+  unsigned long long U = 0;
+  if (sh >= 0) U = m << sh;
+  else if (sh > -64) U = m >> (-sh);
+  const bool neg = (bits >> 63) != 0;
 #pragma unroll
   for (int s = 0; s < OZ_SLICES; ++s) {
-    const double t = x * (double)(1 << OZ_BITS);
-    d[s] = trunc(t);
-    x = t - d[s];
+    const int g = (int)((U >> (OZ_BITS * (OZ_SLICES - 1 - s))) & 127u);
+    d[s] = neg ? -g : g;
   }
 }
 
+// the BF16 pair (lo, hi) of two digits (|d| <= 127: exact) as one 32-bit word
+__device__ __forceinline__ uint32_t bf16_pair(int lo, int hi) {
+  const __nv_bfloat162 p = __halves2bfloat162(__float2bfloat16_rn((float)lo), __float2bfloat16_rn((float)hi));
+  return *reinterpret_cast<const uint32_t*>(&p);
+}
+
+// |v| as an ordered integer key (sign cleared: the order of non-negative doubles)
+__device__ __forceinline__ unsigned long long abs_key(double v) {
+  return (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+}
+
+// scale exponent of a vector with largest magnitude mx: mx = f 2^e, f in [0.5, 1); 0 if mx == 0
+__device__ __forceinline__ int scale_exp(double mx) {
+  int e = 0;
+  if (mx > 0.0) (void)frexp(mx, &e);
+  return e;
+}
+
 // ------------------------------------------------------------------ digit split
-// Columns of a column-major matrix: one warp per vector c (K entries at V + c * ldv, c < nv).
+// Columns of a column-major matrix: one warp per vector c (K entries at V + c * ldv, c < nv);
+// lane l takes entries 8l .. 8l+7 of every 256 and writes each digit slice 16 bytes at a time.
 // Writes the digit slices S[s][c][0..K_pad) (BF16, zero beyond K and for nv <= c < rows) and
 // scale[c] = 2^{e_c} with max_k |V[k][c]| < 2^{e_c} (0 for a zero vector).
 __global__ void k_oz_split_cols(const double* __restrict__ V, int ldv, int K, int nv, int rows,
@@ -156,20 +189,31 @@ __global__ void k_oz_split_cols(const double* __restrict__ V, int ldv, int K, in
   const int wpb = blockDim.x >> 5;
   for (int c = blockIdx.x * wpb + (threadIdx.x >> 5); c < rows; c += gridDim.x * wpb) {
     const double* col = V + (size_t)c * ldv;
-    double mx = 0.0;
-    if (c < nv)
-      for (int k = lane; k < K; k += 32) mx = fmax(mx, fabs(col[k]));
+    const bool valid = c < nv;
+    unsigned long long mk = 0;
+    if (valid)
+      for (int k = lane; k < K; k += 32) mk = max(mk, abs_key(col[k]));
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    int e = 0;
-    if (mx > 0.0) (void)frexp(mx, &e);     // mx = f 2^e, f in [0.5, 1)
+    for (int o = 16; o > 0; o >>= 1) mk = max(mk, __shfl_xor_sync(0xffffffffu, mk, o));
+    const double mx = __longlong_as_double((long long)mk);
+    const int e = scale_exp(mx);
     if (lane == 0) scale[c] = mx > 0.0 ? ldexp(1.0, e) : 0.0;
     __nv_bfloat16* dst = S + (size_t)c * K_pad;
-    for (int k = lane; k < K_pad; k += 32) {
-      double d[OZ_SLICES];
-      digits8((c < nv && k < K && mx > 0.0) ? ldexp(col[k], -e) : 0.0, d);
+    for (int k0 = 8 * lane; k0 < K_pad; k0 += 256) {
+      uint32_t w[OZ_SLICES][4];
 #pragma unroll
-      for (int s = 0; s < OZ_SLICES; ++s) dst[(size_t)s * slice_stride + k] = __double2bfloat16(d[s]);
+      for (int j = 0; j < 8; j += 2) {
+        int d0[OZ_SLICES], d1[OZ_SLICES];
+        const int k = k0 + j;
+        digits8((valid && k < K) ? col[k] : 0.0, e, d0);
+        digits8((valid && k + 1 < K) ? col[k + 1] : 0.0, e, d1);
+#pragma unroll
+        for (int s = 0; s < OZ_SLICES; ++s) w[s][j / 2] = bf16_pair(d0[s], d1[s]);
+      }
+#pragma unroll
+      for (int s = 0; s < OZ_SLICES; ++s)
+        *reinterpret_cast<uint4*>(dst + (size_t)s * slice_stride + k0) =
+            make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
     }
   }
 }
@@ -180,25 +224,23 @@ __global__ void k_oz_split_rows(const double* __restrict__ A, int lda, int K, in
                                 int K_pad, __nv_bfloat16* __restrict__ S, size_t slice_stride,
                                 double* __restrict__ scale) {
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x) {
-    double mx = 0.0;
-    if (r < nv)
-      for (int k = 0; k < K; ++k) mx = fmax(mx, fabs(A[r + (size_t)k * lda]));
-    int e = 0;
-    if (mx > 0.0) (void)frexp(mx, &e);
+    const bool valid = r < nv;
+    unsigned long long mk = 0;
+    if (valid)
+      for (int k = 0; k < K; ++k) mk = max(mk, abs_key(A[r + (size_t)k * lda]));
+    const double mx = __longlong_as_double((long long)mk);
+    const int e = scale_exp(mx);
     scale[r] = mx > 0.0 ? ldexp(1.0, e) : 0.0;
     for (int k0 = 0; k0 < K_pad; k0 += 8) {
       uint32_t w[OZ_SLICES][4];
 #pragma unroll
       for (int j = 0; j < 8; j += 2) {
-        double d0[OZ_SLICES], d1[OZ_SLICES];
+        int d0[OZ_SLICES], d1[OZ_SLICES];
         const int k = k0 + j;
-        digits8((r < nv && k < K && mx > 0.0) ? ldexp(A[r + (size_t)k * lda], -e) : 0.0, d0);
-        digits8((r < nv && k + 1 < K && mx > 0.0) ? ldexp(A[r + (size_t)(k + 1) * lda], -e) : 0.0, d1);
+        digits8((valid && k < K) ? A[r + (size_t)k * lda] : 0.0, e, d0);
+        digits8((valid && k + 1 < K) ? A[r + (size_t)(k + 1) * lda] : 0.0, e, d1);
 #pragma unroll
-        for (int s = 0; s < OZ_SLICES; ++s) {
-          const __nv_bfloat162 p = __halves2bfloat162(__double2bfloat16(d0[s]), __double2bfloat16(d1[s]));
-          w[s][j / 2] = *reinterpret_cast<const uint32_t*>(&p);
-        }
+        for (int s = 0; s < OZ_SLICES; ++s) w[s][j / 2] = bf16_pair(d0[s], d1[s]);
       }
 #pragma unroll
       for (int s = 0; s < OZ_SLICES; ++s)
@@ -549,63 +591,130 @@ xm_status split_update_pack(xm_ctx* ctx, const double* C, int ldc, int K, const 
   return check_device_error(ctx, "split-BF16 rank-k update");
 }
 
+// Identity blocks: block j of nb (b x b, column-major, leading dimension b) holds the identity of
+// order min(b, m - j b) in its leading part, zeros elsewhere.
+__global__ void k_oz_eye_blocks(double* __restrict__ B, int b, int nb, int m) {
+  const size_t bb = (size_t)b * b, total = (size_t)nb * bb;
+  for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < total;
+       g += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(g / bb);
+    const int e = (int)(g % bb);
+    const int r = e % b, c = e / b;
+    B[g] = (r == c && r < m - j * b) ? 1.0 : 0.0;
+  }
+}
+
 // X <- L^{-1} X for L lower triangular m x m (column-major, leading dimension ldl) and X m x n
-// (column-major, leading dimension ldx): right-looking blocked forward substitution, the
-// diagonal blocks by cuBLAS DTRSM (FP64), the block updates X_rest -= L_rest,i X_i on the
-// tensor cores.
+// (column-major, leading dimension ldx): right-looking blocked forward substitution in blocks of
+// 512 rows, every product on the tensor cores.  The inverses -L_ii^{-1} of the diagonal blocks
+// are formed first in FP64 (triangular solves against identity blocks: 2.7 GFLOP at m = 10154,
+// where solving the n right-hand sides by substitution costs m 512 n = 160 GFLOP at the FP64
+// rate); each step is then X_i <- L_ii^{-1} X_i as X_i = 0 - (-L_ii^{-1}) X_i (its digits taken
+// before X_i is cleared) and the block update X_rest -= L_rest,i X_i.  Multiplying by a
+// triangular inverse formed by substitution has the componentwise error bound of substitution.
 xm_status split_trsm(xm_ctx* ctx, void* cublas, const double* L, int ldl, double* X, int ldx,
                      int m, int n) {
   cudaStream_t st = ctx->stream;
   cublasHandle_t cb = static_cast<cublasHandle_t>(cublas);
-  const int b = OZ_TRSM_BLOCK;
-  const int K_pad = b;                                       // a multiple of OZ_BK
+  const int b = OZ_TRSM_BLOCK;                               // a multiple of OZ_BM and OZ_BK
+  const int K_pad = b;
+  const int nb = (m + b - 1) / b;
   const int nJ = (n + OZ_BN - 1) / OZ_BN;
   const int rowsB = nJ * OZ_BN;
-  const int rowsA_max = ((std::max(m - b, 1) + OZ_BM - 1) / OZ_BM) * OZ_BM;
-  DevMem SA, SB, scA, scB, tl;
+  const int rowsA_max = ((std::max(m - b, b) + OZ_BM - 1) / OZ_BM) * OZ_BM;
+  DevMem SA, SB, scA, scB, tl, tld, Li, ptrs;
   XM_CUDA_TRY(cudaMalloc(&SA.p, sizeof(__nv_bfloat16) * (size_t)OZ_SLICES * rowsA_max * K_pad));
   XM_CUDA_TRY(cudaMalloc(&SB.p, sizeof(__nv_bfloat16) * (size_t)OZ_SLICES * rowsB * K_pad));
   XM_CUDA_TRY(cudaMalloc(&scA.p, sizeof(double) * (size_t)rowsA_max));
   XM_CUDA_TRY(cudaMalloc(&scB.p, sizeof(double) * (size_t)rowsB));
   const int nI_max = rowsA_max / OZ_BM;
   XM_CUDA_TRY(cudaMalloc(&tl.p, sizeof(int2) * (size_t)nI_max * nJ));
-  const double one = 1.0;
-  for (int i0 = 0; i0 < m; i0 += b) {
-    const int bi = std::min(b, m - i0);
-    if (cublasDtrsm(cb, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N, CUBLAS_DIAG_NON_UNIT,
-                    bi, n, &one, L + i0 + (size_t)i0 * ldl, ldl, X + i0, ldx) != CUBLAS_STATUS_SUCCESS)
-      return set_error(XM_ECUDA, "cublasDtrsm (diagonal block %d) failed", i0 / b);
-    const int rest = m - i0 - bi;
-    if (rest == 0) break;
-    const int KB = (bi + OZ_BK - 1) / OZ_BK;
-    const int rowsA = ((rest + OZ_BM - 1) / OZ_BM) * OZ_BM;
-    const size_t strideA = (size_t)rowsA * K_pad, strideB = (size_t)rowsB * K_pad;
-    k_oz_split_rows<<<split_grid(ctx, rowsA, 128), 128, 0, st>>>(
-        L + (i0 + bi) + (size_t)i0 * ldl, ldl, bi, rest, rowsA, K_pad, SA.as<__nv_bfloat16>(),
-        strideA, scA.as<double>());
-    k_oz_split_cols<<<split_grid(ctx, rowsB, 8), 256, 0, st>>>(
-        X + i0, ldx, bi, n, rowsB, K_pad, SB.as<__nv_bfloat16>(), strideB, scB.as<double>());
-    XM_CUDA_TRY(cudaGetLastError());
-    const int nI = rowsA / OZ_BM;
-    std::vector<int2> order = tile_order(nI, nJ, [](int, int) { return true; });
-    XM_CUDA_TRY(cudaMemcpyAsync(tl.p, order.data(), sizeof(int2) * order.size(),
+  XM_CUDA_TRY(cudaMalloc(&tld.p, sizeof(int2) * (size_t)(b / OZ_BM) * nJ));
+
+  // -L_jj^{-1} for every diagonal block (FP64, column-major b x b each)
+  XM_CUDA_TRY(cudaMalloc(&Li.p, sizeof(double) * (size_t)nb * b * b));
+  k_oz_eye_blocks<<<ctx->num_sms * 4, 256, 0, st>>>(Li.as<double>(), b, nb, m);
+  XM_CUDA_TRY(cudaGetLastError());
+  const double minus_one = -1.0;
+  const int nfull = m / b;
+  std::vector<double*> hptr((size_t)2 * std::max(nfull, 1));   // [A pointers | B pointers]
+  if (nfull > 0) {
+    for (int j = 0; j < nfull; ++j) {
+      hptr[j] = const_cast<double*>(L) + (size_t)j * b + (size_t)j * b * ldl;
+      hptr[nfull + j] = Li.as<double>() + (size_t)j * b * b;
+    }
+    XM_CUDA_TRY(cudaMalloc(&ptrs.p, sizeof(double*) * (size_t)2 * nfull));
+    XM_CUDA_TRY(cudaMemcpyAsync(ptrs.p, hptr.data(), sizeof(double*) * (size_t)2 * nfull,
                                 cudaMemcpyHostToDevice, st));
+    double** dp = ptrs.as<double*>();
+    const double* const* dA = dp;
+    double* const* dB = dp + nfull;
+    if (cublasDtrsmBatched(cb, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N,
+                           CUBLAS_DIAG_NON_UNIT, b, b, &minus_one, dA, ldl, dB, b, nfull) !=
+        CUBLAS_STATUS_SUCCESS)
+      return set_error(XM_ECUDA, "cublasDtrsmBatched (diagonal block inverses) failed");
+  }
+  if (m % b) {
+    const int j = nfull, bj = m - j * b;
+    if (cublasDtrsm(cb, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N, CUBLAS_DIAG_NON_UNIT, bj,
+                    bj, &minus_one, L + (size_t)j * b + (size_t)j * b * ldl, ldl,
+                    Li.as<double>() + (size_t)j * b * b, b) != CUBLAS_STATUS_SUCCESS)
+      return set_error(XM_ECUDA, "cublasDtrsm (last diagonal block inverse) failed");
+  }
+
+  auto gemm = [&](const int2* tiles, const std::vector<int2>& order, int rowsA, int KB,
+                  double* out, int M) -> xm_status {
     CUtensorMap ma, mb;
     XM_TRY(slice_map(&ma, SA.p, K_pad, rowsA, OZ_BM));
     XM_TRY(slice_map(&mb, SB.p, K_pad, rowsB, OZ_BN));
     OzArgs a{};
-    a.tiles = tl.as<int2>();
+    a.tiles = tiles;
     a.ntiles = (int)order.size();
     a.KB = KB;
     a.scaleA = scA.as<double>();
     a.scaleB = scB.as<double>();
-    a.out = X + i0 + bi;
+    a.out = out;
     a.ldo = ldx;
-    a.M = rest;
+    a.M = M;
     a.ncols = n;
     a.err = ctx->d_err;
-    XM_TRY(launch_mma<OZ_GEMM>(ctx, ma, mb, a));
-    // the host order vector is reused next step: the copy above must have been consumed
+    return launch_mma<OZ_GEMM>(ctx, ma, mb, a);
+  };
+  std::vector<int2> order_d, order;
+  for (int i0 = 0, blk = 0; i0 < m; i0 += b, ++blk) {
+    const int bi = std::min(b, m - i0);
+    const int KB = (bi + OZ_BK - 1) / OZ_BK;
+    const size_t strideB = (size_t)rowsB * K_pad;
+    // X_i <- L_ii^{-1} X_i: digits of the rows of -L_ii^{-1} and of the columns of X_i, X_i
+    // cleared, then X_i -= (-L_ii^{-1}) X_i
+    const int rowsD = ((bi + OZ_BM - 1) / OZ_BM) * OZ_BM;
+    k_oz_split_rows<<<split_grid(ctx, rowsD, 128), 128, 0, st>>>(
+        Li.as<double>() + (size_t)blk * b * b, b, bi, bi, rowsD, K_pad, SA.as<__nv_bfloat16>(),
+        (size_t)rowsD * K_pad, scA.as<double>());
+    k_oz_split_cols<<<split_grid(ctx, rowsB, 8), 256, 0, st>>>(
+        X + i0, ldx, bi, n, rowsB, K_pad, SB.as<__nv_bfloat16>(), strideB, scB.as<double>());
+    XM_CUDA_TRY(cudaGetLastError());
+    XM_CUDA_TRY(cudaMemset2DAsync(X + i0, sizeof(double) * (size_t)ldx, 0, sizeof(double) * (size_t)bi,
+                                  (size_t)n, st));
+    order_d = tile_order(rowsD / OZ_BM, nJ, [](int, int) { return true; });
+    XM_CUDA_TRY(cudaMemcpyAsync(tld.p, order_d.data(), sizeof(int2) * order_d.size(),
+                                cudaMemcpyHostToDevice, st));
+    XM_TRY(gemm(tld.as<int2>(), order_d, rowsD, KB, X + i0, bi));
+    const int rest = m - i0 - bi;
+    if (rest == 0) break;
+    // X_rest -= L_rest,i X_i
+    const int rowsA = ((rest + OZ_BM - 1) / OZ_BM) * OZ_BM;
+    k_oz_split_rows<<<split_grid(ctx, rowsA, 128), 128, 0, st>>>(
+        L + (i0 + bi) + (size_t)i0 * ldl, ldl, bi, rest, rowsA, K_pad, SA.as<__nv_bfloat16>(),
+        (size_t)rowsA * K_pad, scA.as<double>());
+    k_oz_split_cols<<<split_grid(ctx, rowsB, 8), 256, 0, st>>>(
+        X + i0, ldx, bi, n, rowsB, K_pad, SB.as<__nv_bfloat16>(), strideB, scB.as<double>());
+    XM_CUDA_TRY(cudaGetLastError());
+    order = tile_order(rowsA / OZ_BM, nJ, [](int, int) { return true; });
+    XM_CUDA_TRY(cudaMemcpyAsync(tl.p, order.data(), sizeof(int2) * order.size(),
+                                cudaMemcpyHostToDevice, st));
+    XM_TRY(gemm(tl.as<int2>(), order, rowsA, KB, X + i0 + bi, rest));
+    // the host order vectors are reused next step: their copies must have been consumed
     XM_CUDA_TRY(cudaStreamSynchronize(st));
   }
   return check_device_error(ctx, "split-BF16 triangular solve");
