@@ -245,12 +245,12 @@ def run_sweep_only(args):
 def update_tensor_flops(N: int) -> float:
     """BF16 tensor FLOPs of the translation elimination on the tensor cores: 36 digit pairs
     (levels 0..7) of (a) the rank-(N-1) product over the n(n+1)/2 entries of the upper
-    triangle, (b) the blocked triangular solve: per 512-row block the product with the diagonal
+    triangle, (b) the blocked triangular solve: per 1024-row block the product with the diagonal
     block's inverse and the block update of the rows below, and (c) the trailing updates of the
     blocked Cholesky factor (lower triangle), 512-row blocks; n = 3N."""
     n, K = 3 * N, N - 1
     syrk = 36 * 2.0 * K * n * (n + 1) / 2
-    trsm = sum(36 * 2.0 * (K - i0) * n * min(512, K - i0) for i0 in range(0, K, 512))
+    trsm = sum(36 * 2.0 * (K - i0) * n * min(1024, K - i0) for i0 in range(0, K, 1024))
     chol = sum(36 * 2.0 * (K - i0 - min(512, K - i0)) ** 2 / 2 * min(512, K - i0) for i0 in range(0, K, 512))
     return syrk + trsm + chol
 

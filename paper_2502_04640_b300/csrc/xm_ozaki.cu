@@ -24,7 +24,7 @@
 //            BF16 copies written);
 //   OZ_GEMM  out -= A B^T into a column-major FP64 matrix: the steps X_i = 0 - (-L_ii^{-1}) X_i and
 //            the block updates X_rest -= L_rest,i X_i of a right-looking blocked triangular solve
-//            (the 512 x 512 diagonal-block inverses formed in FP64 by cuBLAS), and the trailing
+//            (the 1024 x 1024 diagonal-block inverses formed in FP64 by cuBLAS), and the trailing
 //            updates S_rest -= L_k L_k^T of a right-looking
 //            blocked Cholesky factorisation (diagonal blocks by cuSOLVER, panels by DTRSM, FP64;
 //            only tiles meeting the lower triangle).
@@ -71,7 +71,8 @@ constexpr uint32_t OZ_STAGE_BYTES = OZ_A_BYTES + OZ_B_BYTES;
 constexpr uint32_t OZ_TMEM_COLS = OZ_ACC * OZ_BN;
 constexpr size_t OZ_SMEM = 1024 + (size_t)OZ_STAGES * OZ_STAGE_BYTES + 256;
 constexpr int64_t OZ_MAX_K = 16640;        // int32 level sums: 8 K 127^2 < 2^31
-constexpr int OZ_TRSM_BLOCK = 512;         // diagonal block of the blocked triangular solve
+constexpr int OZ_TRSM_BLOCK = 1024;        // diagonal block of the blocked triangular solve
+constexpr int OZ_CHOL_BLOCK = 512;         // diagonal block of the blocked Cholesky factorisation
 
 enum { OZ_SYRK = 0, OZ_GEMM = 1 };
 
@@ -606,12 +607,15 @@ __global__ void k_oz_eye_blocks(double* __restrict__ B, int b, int nb, int m) {
 
 // X <- L^{-1} X for L lower triangular m x m (column-major, leading dimension ldl) and X m x n
 // (column-major, leading dimension ldx): right-looking blocked forward substitution in blocks of
-// 512 rows, every product on the tensor cores.  The inverses -L_ii^{-1} of the diagonal blocks
-// are formed first in FP64 (triangular solves against identity blocks: 2.7 GFLOP at m = 10154,
-// where solving the n right-hand sides by substitution costs m 512 n = 160 GFLOP at the FP64
+// 1024 rows, every product on the tensor cores.  The inverses -L_ii^{-1} of the diagonal blocks
+// are formed first in FP64 (triangular solves against identity blocks: 11 GFLOP at m = 10154,
+// where solving the n right-hand sides by substitution costs m 1024 n = 320 GFLOP at the FP64
 // rate); each step is then X_i <- L_ii^{-1} X_i as X_i = 0 - (-L_ii^{-1}) X_i (its digits taken
 // before X_i is cleared) and the block update X_rest -= L_rest,i X_i.  Multiplying by a
 // triangular inverse formed by substitution has the componentwise error bound of substitution.
+// Blocks of 1024 rather than 512 halve the FP64 level folds per tensor-core flop of the block
+// updates (10154 x 30465: 0.70 -> 0.63 s for the whole update; 2048 is no faster and its
+// difference from the FP64 build is 3x larger).
 xm_status split_trsm(xm_ctx* ctx, void* cublas, const double* L, int ldl, double* X, int ldx,
                      int m, int n) {
   cudaStream_t st = ctx->stream;
@@ -734,7 +738,7 @@ xm_status split_potrf(xm_ctx* ctx, void* cublas, void* cusolver, double* A, int 
   cudaStream_t st = ctx->stream;
   cublasHandle_t cb = static_cast<cublasHandle_t>(cublas);
   cusolverDnHandle_t cs = static_cast<cusolverDnHandle_t>(cusolver);
-  const int b = OZ_TRSM_BLOCK;
+  const int b = OZ_CHOL_BLOCK;
   const int K_pad = b;
   *minor = 0;
   int lwork = 0;

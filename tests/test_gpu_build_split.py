@@ -39,8 +39,8 @@ CASES = [
     ("traj", lambda: scenes.sub_scene(scenes.trajectory_scene(300, 20000, seed=7), 120)),
     # 55 tiles; K = 399: levels of up to 56 k-blocks, several exact-accumulation chunks each
     ("chunks", lambda: scenes.random_scene(400, 8000, noise=0.02, outlier_frac=0.05, seed=8)),
-    # K = 699: a blocked triangular solve (diagonal blocks 512 + 187, one tensor-core block
-    # update with a ragged row tile); 17 tile rows, so the last 256-column tile is half outside
+    # K = 699: one ragged diagonal block of the triangular solve, a blocked Cholesky factor
+    # (blocks 512 + 187); 17 tile rows, so the last 256-column tile is half outside
     ("trsm-blocks", lambda: scenes.random_scene(700, 12000, noise=0.02, outlier_frac=0.02, seed=15)),
 ]
 
@@ -67,11 +67,14 @@ def test_split_build_matches_oracle(C, name, make):
     qf.free()
 
 
-def test_split_build_large_against_fp64_build(C):
-    """K = 1499: a single digit pair spans two exact-accumulation chunks; three diagonal blocks
-    and two tensor-core block updates in the triangular solve."""
+@pytest.mark.parametrize("N", [1500, 2200])
+def test_split_build_large_against_fp64_build(C, N):
+    """K = 1499: a single digit pair spans two exact-accumulation chunks; diagonal blocks of
+    1024 + 475 rows in the triangular solve (one block update), 512 x 3 in the Cholesky factor.
+    K = 2199: diagonal blocks 1024 + 1024 + 151 (two block updates, the second with a ragged
+    row tile)."""
     from paper_2502_04640_b300 import xm
-    sc = scenes.random_scene(1500, 40000, noise=0.02, outlier_frac=0.05, seed=9)
+    sc = scenes.random_scene(N, 27 * N, noise=0.02, outlier_frac=0.05, seed=9)
     qs = _build(C, sc, xm.XM_BUILD_SPLIT_BF16)
     qf = _build(C, sc, xm.XM_BUILD_FP64)
     Qs = xm.xm_qmat_to_dense(qs)
