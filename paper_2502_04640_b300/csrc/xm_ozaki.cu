@@ -182,10 +182,10 @@ __device__ __forceinline__ int scale_exp(double mx) {
 // Columns of a column-major matrix: one warp per vector c (K entries at V + c * ldv, c < nv);
 // lane l takes entries 8l .. 8l+7 of every 256 and writes each digit slice 16 bytes at a time.
 // Writes the digit slices S[s][c][0..K_pad) (BF16, zero beyond K and for nv <= c < rows) and
-// scale[c] = 2^{e_c} with max_k |V[k][c]| < 2^{e_c} (0 for a zero vector).
+// the scale exponent sexp[c] = e_c with max_k |V[k][c]| < 2^{e_c} (0 for a zero vector).
 __global__ void k_oz_split_cols(const double* __restrict__ V, int ldv, int K, int nv, int rows,
                                 int K_pad, __nv_bfloat16* __restrict__ S, size_t slice_stride,
-                                double* __restrict__ scale) {
+                                int* __restrict__ sexp) {
   const int lane = threadIdx.x & 31;
   const int wpb = blockDim.x >> 5;
   for (int c = blockIdx.x * wpb + (threadIdx.x >> 5); c < rows; c += gridDim.x * wpb) {
@@ -198,7 +198,7 @@ __global__ void k_oz_split_cols(const double* __restrict__ V, int ldv, int K, in
     for (int o = 16; o > 0; o >>= 1) mk = max(mk, __shfl_xor_sync(0xffffffffu, mk, o));
     const double mx = __longlong_as_double((long long)mk);
     const int e = scale_exp(mx);
-    if (lane == 0) scale[c] = mx > 0.0 ? ldexp(1.0, e) : 0.0;
+    if (lane == 0) sexp[c] = e;
     __nv_bfloat16* dst = S + (size_t)c * K_pad;
     for (int k0 = 8 * lane; k0 < K_pad; k0 += 256) {
       uint32_t w[OZ_SLICES][4];
@@ -223,7 +223,7 @@ __global__ void k_oz_split_cols(const double* __restrict__ V, int ldv, int K, in
 // same outputs as k_oz_split_cols, written 8 digits (16 bytes) at a time.
 __global__ void k_oz_split_rows(const double* __restrict__ A, int lda, int K, int nv, int rows,
                                 int K_pad, __nv_bfloat16* __restrict__ S, size_t slice_stride,
-                                double* __restrict__ scale) {
+                                int* __restrict__ sexp) {
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x) {
     const bool valid = r < nv;
     unsigned long long mk = 0;
@@ -231,7 +231,7 @@ __global__ void k_oz_split_rows(const double* __restrict__ A, int lda, int K, in
       for (int k = 0; k < K; ++k) mk = max(mk, abs_key(A[r + (size_t)k * lda]));
     const double mx = __longlong_as_double((long long)mk);
     const int e = scale_exp(mx);
-    scale[r] = mx > 0.0 ? ldexp(1.0, e) : 0.0;
+    sexp[r] = e;
     for (int k0 = 0; k0 < K_pad; k0 += 8) {
       uint32_t w[OZ_SLICES][4];
 #pragma unroll
@@ -251,13 +251,31 @@ __global__ void k_oz_split_rows(const double* __restrict__ A, int lda, int K, in
   }
 }
 
+// 2^E a as a double (a an int32), exact whenever it is a normal double: the leading bit, the
+// significand and the exponent field are set with integer operations (no branch, no FP64
+// instruction), so that a level fold costs one FP64 operation (the subtraction) instead of three
+// (conversion, scaling, subtraction) on B300's slow FP64 pipe.  Below the normal range the
+// result is 0 (a level term under 2^-1022, far below the rounding of the FP64 output); above it,
+// +-inf.
+__device__ __forceinline__ double i2d_pow2(int a, int E) {
+  const unsigned u = a < 0 ? 0u - (unsigned)a : (unsigned)a;
+  const int p = 31 - __clz(u | 1u);                  // 2^p <= u < 2^{p+1} (u > 0)
+  const int be = p + E + 1023;
+  const unsigned long long sign = a < 0 ? (1ull << 63) : 0ull;
+  const unsigned long long mant = ((unsigned long long)u << (52 - p)) & 0xFFFFFFFFFFFFFull;
+  unsigned long long bits = sign | ((unsigned long long)(be > 0 ? be : 0) << 52) | mant;
+  bits = be >= 2047 ? (sign | 0x7FF0000000000000ull) : bits;
+  bits = (u == 0u || be <= 0) ? 0ull : bits;
+  return __longlong_as_double((long long)bits);
+}
+
 // ------------------------------------------------------------------ digit-product kernel
 struct OzArgs {
   const int2* tiles;        // (I, J) per work item: rows I*128.., columns J*256..
   int ntiles;
   int KB;                   // k-blocks per digit slice
-  const double* scaleA;     // 2^{e} of the A vectors (rows of the output)
-  const double* scaleB;     // 2^{e} of the B vectors (columns of the output)
+  const int* expA;          // scale exponents e of the A vectors (rows of the output)
+  const int* expB;          // scale exponents e of the B vectors (columns of the output)
   // OZ_SYRK
   int n, nt;                // Q order, 128-tiles per side
   const double* P;          // row-major n x n, upper triangle valid
@@ -385,8 +403,8 @@ k_oz_mma(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUten
       const int2 tj = args.tiles[w];
       const int row = tj.x * OZ_BM + a_loc;
       const int col0 = tj.y * OZ_BN + grp * OZ_EPI_COLS;       // first output column
-      const double rs = args.scaleA[row];
-      const double* cs = args.scaleB + col0;                     // uniform across the warp
+      const int er = args.expA[row];
+      const int* ce = args.expB + col0;                          // uniform across the warp
       // OZ_SYRK: the packed 128 x 128 tile this warp's columns fall in
       const int I = tj.x, J = 2 * tj.y + (grp >> 1);
       const bool live = MODE == OZ_GEMM || (J >= I && J < args.nt);
@@ -421,13 +439,13 @@ k_oz_mma(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUten
         }
         if (!ok || !live) continue;
         // level m: output -= 2^{e_row + e_col - 7(m+2)} L_m (exact scaling, FP64 subtraction)
-        const double f = ldexp(rs, -OZ_BITS * (m + 2));
+        const int Em = er - OZ_BITS * (m + 2);
         if constexpr (MODE == OZ_SYRK) {
 #pragma unroll
           for (int c = 0; c < OZ_EPI_COLS; c += 2) {
             double2 cur = m == 0 ? make_double2(0.0, 0.0) : *reinterpret_cast<const double2*>(dst + c);
-            cur.x -= (double)acc[c] * (f * cs[c]);
-            cur.y -= (double)acc[c + 1] * (f * cs[c + 1]);
+            cur.x -= i2d_pow2(acc[c], Em + ce[c]);
+            cur.y -= i2d_pow2(acc[c + 1], Em + ce[c + 1]);
             *reinterpret_cast<double2*>(dst + c) = cur;
           }
         } else {
@@ -437,7 +455,7 @@ k_oz_mma(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUten
               const int col = col0 + c;
               if (col < args.ncols) {
                 double* o = args.out + (size_t)col * args.ldo + row;   // coalesced along rows
-                *o -= (double)acc[c] * (f * cs[c]);
+                *o -= i2d_pow2(acc[c], Em + ce[c]);
               }
             }
           }
@@ -559,12 +577,12 @@ xm_status split_update_pack(xm_ctx* ctx, const double* C, int ldc, int K, const 
   const int nt2 = (nt + 1) / 2;                   // 256-column tiles
   const int rows = nt2 * OZ_BN;                   // slice rows: a multiple of 128 and 256
   const size_t slice_stride = (size_t)rows * K_pad;
-  DevMem S, scale, tl;
+  DevMem S, sexp, tl;
   XM_CUDA_TRY(cudaMalloc(&S.p, sizeof(__nv_bfloat16) * slice_stride * OZ_SLICES));
-  XM_CUDA_TRY(cudaMalloc(&scale.p, sizeof(double) * (size_t)rows));
+  XM_CUDA_TRY(cudaMalloc(&sexp.p, sizeof(int) * (size_t)rows));
   k_oz_split_cols<<<split_grid(ctx, rows, 8), 256, 0, st>>>(C, ldc, K, q.n, rows, K_pad,
                                                             S.as<__nv_bfloat16>(), slice_stride,
-                                                            scale.as<double>());
+                                                            sexp.as<int>());
   XM_CUDA_TRY(cudaGetLastError());
   // 128 x 256 tiles meeting the upper triangle: packed tile (I, 2J) or (I, 2J+1) with J >= I
   std::vector<int2> order = tile_order(nt, nt2, [](int I, int J) { return 2 * J + 1 >= I; });
@@ -578,8 +596,8 @@ xm_status split_update_pack(xm_ctx* ctx, const double* C, int ldc, int K, const 
   a.tiles = tl.as<int2>();
   a.ntiles = (int)order.size();
   a.KB = KB;
-  a.scaleA = scale.as<double>();
-  a.scaleB = scale.as<double>();
+  a.expA = sexp.as<int>();
+  a.expB = sexp.as<int>();
   a.n = q.n;
   a.nt = nt;
   a.P = P;
@@ -629,8 +647,8 @@ xm_status split_trsm(xm_ctx* ctx, void* cublas, const double* L, int ldl, double
   DevMem SA, SB, scA, scB, tl, tld, Li, ptrs;
   XM_CUDA_TRY(cudaMalloc(&SA.p, sizeof(__nv_bfloat16) * (size_t)OZ_SLICES * rowsA_max * K_pad));
   XM_CUDA_TRY(cudaMalloc(&SB.p, sizeof(__nv_bfloat16) * (size_t)OZ_SLICES * rowsB * K_pad));
-  XM_CUDA_TRY(cudaMalloc(&scA.p, sizeof(double) * (size_t)rowsA_max));
-  XM_CUDA_TRY(cudaMalloc(&scB.p, sizeof(double) * (size_t)rowsB));
+  XM_CUDA_TRY(cudaMalloc(&scA.p, sizeof(int) * (size_t)rowsA_max));
+  XM_CUDA_TRY(cudaMalloc(&scB.p, sizeof(int) * (size_t)rowsB));
   const int nI_max = rowsA_max / OZ_BM;
   XM_CUDA_TRY(cudaMalloc(&tl.p, sizeof(int2) * (size_t)nI_max * nJ));
   XM_CUDA_TRY(cudaMalloc(&tld.p, sizeof(int2) * (size_t)(b / OZ_BM) * nJ));
@@ -675,8 +693,8 @@ xm_status split_trsm(xm_ctx* ctx, void* cublas, const double* L, int ldl, double
     a.tiles = tiles;
     a.ntiles = (int)order.size();
     a.KB = KB;
-    a.scaleA = scA.as<double>();
-    a.scaleB = scB.as<double>();
+    a.expA = scA.as<int>();
+    a.expB = scB.as<int>();
     a.out = out;
     a.ldo = ldx;
     a.M = M;
@@ -694,9 +712,9 @@ xm_status split_trsm(xm_ctx* ctx, void* cublas, const double* L, int ldl, double
     const int rowsD = ((bi + OZ_BM - 1) / OZ_BM) * OZ_BM;
     k_oz_split_rows<<<split_grid(ctx, rowsD, 128), 128, 0, st>>>(
         Li.as<double>() + (size_t)blk * b * b, b, bi, bi, rowsD, K_pad, SA.as<__nv_bfloat16>(),
-        (size_t)rowsD * K_pad, scA.as<double>());
+        (size_t)rowsD * K_pad, scA.as<int>());
     k_oz_split_cols<<<split_grid(ctx, rowsB, 8), 256, 0, st>>>(
-        X + i0, ldx, bi, n, rowsB, K_pad, SB.as<__nv_bfloat16>(), strideB, scB.as<double>());
+        X + i0, ldx, bi, n, rowsB, K_pad, SB.as<__nv_bfloat16>(), strideB, scB.as<int>());
     XM_CUDA_TRY(cudaGetLastError());
     XM_CUDA_TRY(cudaMemset2DAsync(X + i0, sizeof(double) * (size_t)ldx, 0, sizeof(double) * (size_t)bi,
                                   (size_t)n, st));
@@ -710,9 +728,9 @@ xm_status split_trsm(xm_ctx* ctx, void* cublas, const double* L, int ldl, double
     const int rowsA = ((rest + OZ_BM - 1) / OZ_BM) * OZ_BM;
     k_oz_split_rows<<<split_grid(ctx, rowsA, 128), 128, 0, st>>>(
         L + (i0 + bi) + (size_t)i0 * ldl, ldl, bi, rest, rowsA, K_pad, SA.as<__nv_bfloat16>(),
-        (size_t)rowsA * K_pad, scA.as<double>());
+        (size_t)rowsA * K_pad, scA.as<int>());
     k_oz_split_cols<<<split_grid(ctx, rowsB, 8), 256, 0, st>>>(
-        X + i0, ldx, bi, n, rowsB, K_pad, SB.as<__nv_bfloat16>(), strideB, scB.as<double>());
+        X + i0, ldx, bi, n, rowsB, K_pad, SB.as<__nv_bfloat16>(), strideB, scB.as<int>());
     XM_CUDA_TRY(cudaGetLastError());
     order = tile_order(rowsA / OZ_BM, nJ, [](int, int) { return true; });
     XM_CUDA_TRY(cudaMemcpyAsync(tl.p, order.data(), sizeof(int2) * order.size(),
@@ -750,7 +768,7 @@ xm_status split_potrf(xm_ctx* ctx, void* cublas, void* cusolver, double* A, int 
   XM_CUDA_TRY(cudaMalloc(&work.p, sizeof(double) * (size_t)std::max(lwork, 1)));
   XM_CUDA_TRY(cudaMalloc(&info.p, sizeof(int)));
   XM_CUDA_TRY(cudaMalloc(&S.p, sizeof(__nv_bfloat16) * (size_t)OZ_SLICES * rows_max * K_pad));
-  XM_CUDA_TRY(cudaMalloc(&sc.p, sizeof(double) * (size_t)rows_max));
+  XM_CUDA_TRY(cudaMalloc(&sc.p, sizeof(int) * (size_t)rows_max));
   XM_CUDA_TRY(cudaMalloc(&tl.p, sizeof(int2) * (size_t)(rows_max / OZ_BM) * (rows_max / OZ_BN)));
   const double one = 1.0;
   for (int k0 = 0; k0 < m; k0 += b) {
@@ -773,7 +791,7 @@ xm_status split_potrf(xm_ctx* ctx, void* cublas, void* cusolver, double* A, int 
     const size_t stride = (size_t)rows * K_pad;
     k_oz_split_rows<<<split_grid(ctx, rows, 128), 128, 0, st>>>(P, lda, bk, rest, rows, K_pad,
                                                                S.as<__nv_bfloat16>(), stride,
-                                                               sc.as<double>());
+                                                               sc.as<int>());
     XM_CUDA_TRY(cudaGetLastError());
     const int nI = (rest + OZ_BM - 1) / OZ_BM, nJ = (rest + OZ_BN - 1) / OZ_BN;
     // 128 x 256 tiles with some column <= some row (they meet the lower triangle)
@@ -787,8 +805,8 @@ xm_status split_potrf(xm_ctx* ctx, void* cublas, void* cusolver, double* A, int 
     a.tiles = tl.as<int2>();
     a.ntiles = (int)order.size();
     a.KB = (bk + OZ_BK - 1) / OZ_BK;
-    a.scaleA = sc.as<double>();
-    a.scaleB = sc.as<double>();
+    a.expA = sc.as<int>();
+    a.expB = sc.as<int>();
     a.out = A + (k0 + bk) + (size_t)(k0 + bk) * lda;
     a.ldo = lda;
     a.M = rest;
