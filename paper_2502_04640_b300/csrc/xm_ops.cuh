@@ -20,6 +20,7 @@ struct Scal {
   double dot;                // generic reduction result
   double mu;                 // App. D scale-regularisation weight (0: plain Eq. 17 objective)
   double thr_min;            // floor of the residual stop: no tighter than the phase's tolerance
+  double df;                 // f(candidate) - f(current) in difference form (RTR ratio test)
   int done, stop_after, iters, max_iters, reason, pad_;
 };
 

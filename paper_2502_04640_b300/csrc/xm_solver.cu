@@ -191,6 +191,57 @@ k_bnorm(int N, const T* __restrict__ Y, const double* __restrict__ B, Scal* sc, 
   grid_reduce<1>(v, partials, counter, [&](double* t) { sc->dot = t[0]; });
 }
 
+// Gradient epilogue of the RTR iterates: grad_block, plus the raw Q Y of the point saved to QY and,
+// for a candidate Yc with reference Y (Yref, its Q Y in QYref), the change of the objective in
+// difference form, sc->df = <Yc - Y, Q Yc + Q Y> + mu sum_{i>=1} (xc_i - x_i)(xc_i + x_i - 2)
+// (Q symmetric; x_i = ||row 2 of Y_i||^2 as in the App. D term).  Its rounding error scales with
+// |Yc - Y| instead of |Y|: near convergence f is a sum of terms many orders of magnitude above f
+// itself, and the difference of two such sums is rounding noise once the predicted decrease is
+// small (in FP64 too), which turns the trust-region ratio into noise.
+template <typename T, int R>
+__global__ void __launch_bounds__(CAM_THREADS)
+k_grad_epi_rtr(int N, const T* __restrict__ Y, T* __restrict__ W, T* __restrict__ G,
+               double* __restrict__ Lam, Scal* sc, int cand, const T* __restrict__ Yref,
+               const T* __restrict__ QYref, T* __restrict__ QY, double* partials, unsigned* counter,
+               int* err) {
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) {
+    double y[3][R], w[3][R];
+    load_block<T, double, R>(Y, i, y);
+    load_block<T, double, R>(W, i, w);
+    store_block<T, double, R>(QY, i, w);
+    if (cand && Yref) {
+      double yr[3][R], wr[3][R];
+      load_block<T, double, R>(Yref, i, yr);
+      load_block<T, double, R>(QYref, i, wr);
+      double d = 0.0;
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int j = 0; j < R; ++j) d += (y[a][j] - yr[a][j]) * (w[a][j] + wr[a][j]);
+      if (sc->mu != 0.0 && i > 0) {
+        double xc = 0.0, xr = 0.0;
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+          xc += y[2][j] * y[2][j];
+          xr += yr[2][j] * yr[2][j];
+        }
+        d += sc->mu * (xc - xr) * (xc + xr - 2.0);
+      }
+      v[3] = d;
+    }
+    double vg[3] = {0.0, 0.0, 0.0};
+    grad_block<T, R>(i, N, Y, W, G, Lam, sc->mu, vg);
+    v[0] = vg[0]; v[1] = vg[1]; v[2] = vg[2];
+  }
+  grid_reduce<4>(v, partials, counter, [&](double* t) {
+    if (!isfinite(t[0]) || !isfinite(t[1])) atomicOr(err, DEV_NUMERIC);
+    if (cand) { sc->fc = t[0]; sc->gc2 = t[1]; sc->yc2 = t[2]; sc->df = t[3]; }
+    else { sc->f = t[0]; sc->g2 = t[1]; sc->y2 = t[2]; }
+  });
+}
+
 // ------------------------------------------------------------------ LOBPCG certificate kernels
 // Blocks of 4 vectors are n_pad x 4 row-major FP32 arrays (the sweep's layout for R = 4).
 
@@ -392,7 +443,7 @@ struct Solver {
   void *bY = nullptr, *bYc = nullptr, *bW = nullptr, *bWc = nullptr, *bG = nullptr,
        *bGc = nullptr, *bYin = nullptr, *bEta = nullptr, *bHeta = nullptr, *bR = nullptr,
        *bD = nullptr, *bHd = nullptr, *bWd = nullptr, *bY64 = nullptr, *bXi = nullptr,
-       *bYh = nullptr;
+       *bYh = nullptr, *bQY = nullptr, *bQYc = nullptr;   // Q Y of the RTR iterate / candidate
   double *Lam = nullptr, *Lamc = nullptr;
   double *pcMinv = nullptr, *pcB = nullptr;   // tCG preconditioner blocks (N x 9), or null
   void* bZ = nullptr;                         // tCG preconditioned residual
@@ -436,7 +487,7 @@ struct Solver {
   }
   ~Solver() {
     void* bufs[] = {bY, bYc, bW, bWc, bG, bGc, bYin, bEta, bHeta, bR, bD, bHd, bWd, bY64, bXi, bYh,
-                    bZ, Lam, Lamc, pcMinv, pcB, d_sc, d_small, V, lw, lz, lalpha, lbeta, lc, lnrm,
+                    bQY, bQYc, bZ, Lam, Lamc, pcMinv, pcB, d_sc, d_small, V, lw, lz, lalpha, lbeta, lc, lnrm,
                     lritz, lv32, lW32, lwf, lcf, lpart, lob, lob_minv, lob_part, lob_small};
     for (void* p : bufs) if (p) cudaFree(p);
     if (h_sc) cudaFreeHost(h_sc);
@@ -449,7 +500,7 @@ struct Solver {
 
   xm_status alloc() {
     void** vecs[] = {&bY, &bYc, &bW, &bWc, &bG, &bGc, &bYin, &bEta, &bHeta, &bR, &bD, &bHd, &bWd,
-                     &bY64, &bXi, &bYh, &bZ};
+                     &bY64, &bXi, &bYh, &bQY, &bQYc, &bZ};
     for (void** p : vecs) {
       XM_CUDA_TRY(cudaMalloc(p, vec_bytes));
       XM_CUDA_TRY(cudaMemsetAsync(*p, 0, vec_bytes, st));
@@ -543,11 +594,19 @@ struct Solver {
 
   // ---------------- gradient / objective at a point (W zero on entry, zero on exit)
   template <typename To, int R>
-  xm_status grad_at(int prec, void* Yp, void* Wp, void* Gp, double* L, int cand, bool timed) {
+  // QYp: also save Q Y of this point (RTR iterates); Yref, QYref: a candidate's reference point
+  // and its saved Q Y, for the objective change in difference form (sc->df)
+  xm_status grad_at(int prec, void* Yp, void* Wp, void* Gp, double* L, int cand, bool timed,
+                    void* QYp = nullptr, const void* Yref = nullptr, const void* QYref = nullptr) {
     XM_TRY(sweep(prec, R, Yp, Wp, nullptr, timed));
-    k_grad_epi<To, R><<<nb_cam, CAM_THREADS, 0, st>>>(N, (const To*)Yp, (To*)Wp, (To*)Gp, L, d_sc,
-                                                      cand, ctx->d_partials, ctx->d_counter,
-                                                      ctx->d_err);
+    if (QYp)
+      k_grad_epi_rtr<To, R><<<nb_cam, CAM_THREADS, 0, st>>>(
+          N, (const To*)Yp, (To*)Wp, (To*)Gp, L, d_sc, cand, (const To*)Yref, (const To*)QYref,
+          (To*)QYp, ctx->d_partials, ctx->d_counter, ctx->d_err);
+    else
+      k_grad_epi<To, R><<<nb_cam, CAM_THREADS, 0, st>>>(N, (const To*)Yp, (To*)Wp, (To*)Gp, L, d_sc,
+                                                        cand, ctx->d_partials, ctx->d_counter,
+                                                        ctx->d_err);
     ++launches;
     XM_CUDA_TRY(cudaGetLastError());
     return XM_OK;
@@ -557,7 +616,7 @@ struct Solver {
   template <typename To, typename Ti, int R>
   xm_status rtr(int prec_grad, int prec_hvp, double tol_rel, int max_outer, bool bulk) {
     const size_t rows = (size_t)n_pad;
-    XM_TRY(grad_at<To, R>(prec_grad, bY, bW, bG, Lam, 0, true));
+    XM_TRY(grad_at<To, R>(prec_grad, bY, bW, bG, Lam, 0, true, bQY));
     XM_TRY(pull_scalars());
     double f = h_sc->f, g2 = h_sc->g2;
     if (!std::isfinite(f) || !std::isfinite(g2)) return set_error(XM_ENUMERIC, "rtr: non-finite f");
@@ -686,7 +745,7 @@ struct Solver {
                                                            (To*)bYc);
       launches += 2;
       XM_CUDA_TRY(cudaGetLastError());
-      XM_TRY(grad_at<To, R>(prec_grad, bYc, bWc, bGc, Lamc, 1, true));
+      XM_TRY(grad_at<To, R>(prec_grad, bYc, bWc, bGc, Lamc, 1, true, bQYc, bY, bQY));
       XM_TRY(pull_scalars());
       ++info.n_outer;
       info.n_tcg += h_sc->iters;
@@ -695,22 +754,25 @@ struct Solver {
       info.n_sweeps += h_sc->iters;
       if (prec_hvp == XM_FP64) info.n_sweeps_fp64 += h_sc->iters;
       const double fc = h_sc->fc;
+      const double dfc = h_sc->df;   // f(Yc) - f(Y) in difference form
       const double model_dec = -(h_sc->g_eta + 0.5 * h_sc->eta_Heta);
       const double reg = std::max(1.0, std::fabs(f)) * eps_reg;
-      const double rho = (f - fc + reg) / (model_dec + reg);
+      const double rho = (-dfc + reg) / (model_dec + reg);
       const double en = std::sqrt(pcMinv ? h_sc->ee : h_sc->eta2);   // ||eta|| in the tCG's norm
-      if (!std::isfinite(fc) || rho < 0.25) {
+      const bool finite = std::isfinite(fc) && std::isfinite(dfc);
+      if (!finite || rho < 0.25) {
         Delta *= 0.25;
       } else if (rho > 0.75 && en >= Delta * (1.0 - 1e-6)) {
         Delta = std::min(2.0 * Delta, Delta_bar);
       }
-      const bool accept = std::isfinite(fc) && rho > 0.1 && fc <= f + reg;
+      const bool accept = finite && rho > 0.1 && dfc <= reg;
       if (o.verbose >= 2)
         fprintf(stderr, "[xm] %s k=%d f=%.12e |g|=%.3e rho=%.3f Delta=%.3e tcg=%d(%d) %s\n",
                 bulk ? "bulk" : "fp64", k, f, std::sqrt(g2), rho, Delta, h_sc->iters, h_sc->reason,
                 accept ? "acc" : "rej");
       if (accept) {
         std::swap(bY, bYc); std::swap(bW, bWc); std::swap(bG, bGc); std::swap(Lam, Lamc);
+        std::swap(bQY, bQYc);
         f = fc;
         g2 = h_sc->gc2;
         rejects = 0;
