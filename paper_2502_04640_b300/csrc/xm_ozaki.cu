@@ -25,9 +25,9 @@
 //   OZ_GEMM  out -= A B^T into a column-major FP64 matrix: the steps X_i = 0 - (-L_ii^{-1}) X_i and
 //            the block updates X_rest -= L_rest,i X_i of a right-looking blocked triangular solve
 //            (the 1024 x 1024 diagonal-block inverses formed in FP64 by cuBLAS), and the trailing
-//            updates S_rest -= L_k L_k^T of a right-looking
-//            blocked Cholesky factorisation (diagonal blocks by cuSOLVER, panels by DTRSM, FP64;
-//            only tiles meeting the lower triangle).
+//            updates S_rest -= L_k L_k^T of a right-looking blocked Cholesky factorisation
+//            (diagonal blocks by cuSOLVER, panels by DTRSM, FP64; only tiles meeting the lower
+//            triangle).
 //
 // Kernel: persistent, one CTA per SM, 128 x 256 output tiles (MMA M = 128, N = 256) in an order
 // that lets concurrent CTAs share operand k-blocks in L2.  Warp 0 streams the 128 x 64 and
@@ -610,25 +610,87 @@ xm_status split_update_pack(xm_ctx* ctx, const double* C, int ldc, int K, const 
   return check_device_error(ctx, "split-BF16 rank-k update");
 }
 
-// Identity blocks: block j of nb (b x b, column-major, leading dimension b) holds the identity of
-// order min(b, m - j b) in its leading part, zeros elsewhere.
-__global__ void k_oz_eye_blocks(double* __restrict__ B, int b, int nb, int m) {
-  const size_t bb = (size_t)b * b, total = (size_t)nb * bb;
-  for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < total;
-       g += (size_t)gridDim.x * blockDim.x) {
-    const int j = (int)(g / bb);
-    const int e = (int)(g % bb);
-    const int r = e % b, c = e / b;
-    B[g] = (r == c && r < m - j * b) ? 1.0 : 0.0;
+// Inverses of the 128 x 128 diagonal leaves of a lower-triangular m x m matrix L (column-major,
+// leading dimension ldl; leaf g covers rows and columns [128 g, 128 g + h), h = min(128, m - 128 g)),
+// written into the diagonal blocks of Li: block j (b x b, column-major, leading dimension b, b a
+// multiple of 128) holds rows and columns [j b, j b + b).  Thread c forward-substitutes
+// L_leaf x = e_c for column c of the inverse, keeping the column in shared memory; the loop over
+// l is the same for every thread (entries above the diagonal are zero), so all threads read the
+// same entry of L at a time.
+constexpr int OZ_LEAF = 128;
+__global__ void __launch_bounds__(OZ_LEAF) k_oz_trinv_leaf(const double* __restrict__ L, int ldl,
+                                                          double* __restrict__ Li, int b, int m) {
+  extern __shared__ double xs[];                        // [OZ_LEAF rows][OZ_LEAF columns]
+  const int j0 = blockIdx.x * OZ_LEAF, h = min(OZ_LEAF, m - j0);
+  const int c = threadIdx.x;
+  for (int k = 0; k < h; ++k) {
+    const double* Lk = L + (size_t)(j0 + k) + (size_t)j0 * ldl;   // L[j0 + k, j0 + l] = Lk[l ldl]
+    double s = k == c ? 1.0 : 0.0;
+    for (int l = 0; l < k; ++l) s -= Lk[(size_t)l * ldl] * xs[l * OZ_LEAF + c];
+    xs[k * OZ_LEAF + c] = k < c ? 0.0 : s / Lk[(size_t)k * ldl];
   }
+  const int blk = j0 / b, off = j0 - blk * b;
+  double* dst = Li + (size_t)blk * b * b + off + (size_t)off * b;
+  if (c < h)
+    for (int k = 0; k < h; ++k) dst[k + (size_t)c * b] = xs[k * OZ_LEAF + c];
+}
+
+__global__ void k_oz_negate(double* __restrict__ v, size_t count) {
+  for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < count;
+       g += (size_t)gridDim.x * blockDim.x)
+    v[g] = -v[g];
+}
+
+// -L_jj^{-1} of the diagonal blocks of the lower-triangular m x m matrix L (blocks of b rows, b a
+// multiple of 128; the last one m - (nb - 1) b) into Li (nb blocks of b x b, column-major,
+// leading dimension b, zeros above the diagonal).  The 128 x 128 leaves are inverted by
+// k_oz_trinv_leaf; then, leaf row by leaf row, X_ik = -L_ii^{-1} sum_{k <= l < i} L_il X_lk
+// (FP64 cuBLAS products, 7 GFLOP at 10 blocks of 1024).  The batched library triangular solve
+// this replaces cost 0.9-1.5 s at its first call in a process on a fresh B300 machine.
+static xm_status tri_inverse_blocks(xm_ctx* ctx, void* cublas, const double* L, int ldl, int m, int b,
+                                    double* Li) {
+  cudaStream_t st = ctx->stream;
+  cublasHandle_t cb = static_cast<cublasHandle_t>(cublas);
+  const int nb = (m + b - 1) / b;
+  static int configured_dev = -1;
+  if (configured_dev != ctx->device) {
+    XM_CUDA_TRY(cudaFuncSetAttribute(k_oz_trinv_leaf, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(sizeof(double) * OZ_LEAF * OZ_LEAF)));
+    configured_dev = ctx->device;
+  }
+  XM_CUDA_TRY(cudaMemsetAsync(Li, 0, sizeof(double) * (size_t)nb * b * b, st));
+  k_oz_trinv_leaf<<<(m + OZ_LEAF - 1) / OZ_LEAF, OZ_LEAF, sizeof(double) * OZ_LEAF * OZ_LEAF, st>>>(
+      L, ldl, Li, b, m);
+  XM_CUDA_TRY(cudaGetLastError());
+  DevMem T;
+  XM_CUDA_TRY(cudaMalloc(&T.p, sizeof(double) * (size_t)OZ_LEAF * b));
+  const double one = 1.0, zero = 0.0, minus_one = -1.0;
+  for (int j = 0; j < nb; ++j) {
+    const int o = j * b, bj = std::min(b, m - o);
+    const double* Ljj = L + (size_t)o + (size_t)o * ldl;
+    double* X = Li + (size_t)j * b * b;
+    for (int r0 = OZ_LEAF; r0 < bj; r0 += OZ_LEAF) {
+      const int hi = std::min(OZ_LEAF, bj - r0);
+      // T = L[r0:r0+hi, 0:r0] X[0:r0, 0:r0]; X[r0:r0+hi, 0:r0] = -X[r0:, r0:] T
+      if (cublasDgemm(cb, CUBLAS_OP_N, CUBLAS_OP_N, hi, r0, r0, &one, Ljj + r0, ldl, X, b, &zero,
+                      T.as<double>(), OZ_LEAF) != CUBLAS_STATUS_SUCCESS ||
+          cublasDgemm(cb, CUBLAS_OP_N, CUBLAS_OP_N, hi, r0, hi, &minus_one, X + r0 + (size_t)r0 * b, b,
+                      T.as<double>(), OZ_LEAF, &zero, X + r0, b) != CUBLAS_STATUS_SUCCESS)
+        return set_error(XM_ECUDA, "cublasDgemm (diagonal block inverse %d) failed", j);
+    }
+  }
+  k_oz_negate<<<ctx->num_sms * 4, 256, 0, st>>>(Li, (size_t)nb * b * b);
+  XM_CUDA_TRY(cudaGetLastError());
+  // T is freed on return: the products above must have read it
+  XM_CUDA_TRY(cudaStreamSynchronize(st));
+  return XM_OK;
 }
 
 // X <- L^{-1} X for L lower triangular m x m (column-major, leading dimension ldl) and X m x n
 // (column-major, leading dimension ldx): right-looking blocked forward substitution in blocks of
 // 1024 rows, every product on the tensor cores.  The inverses -L_ii^{-1} of the diagonal blocks
-// are formed first in FP64 (triangular solves against identity blocks: 11 GFLOP at m = 10154,
-// where solving the n right-hand sides by substitution costs m 1024 n = 320 GFLOP at the FP64
-// rate); each step is then X_i <- L_ii^{-1} X_i as X_i = 0 - (-L_ii^{-1}) X_i (its digits taken
+// are formed first in FP64 (tri_inverse_blocks: 7 GFLOP at m = 10154, where solving the n
+// right-hand sides by substitution costs m 1024 n = 320 GFLOP at the FP64 rate); each step is then X_i <- L_ii^{-1} X_i as X_i = 0 - (-L_ii^{-1}) X_i (its digits taken
 // before X_i is cleared) and the block update X_rest -= L_rest,i X_i.  Multiplying by a
 // triangular inverse formed by substitution has the componentwise error bound of substitution.
 // Blocks of 1024 rather than 512 halve the FP64 level folds per tensor-core flop of the block
@@ -637,14 +699,13 @@ __global__ void k_oz_eye_blocks(double* __restrict__ B, int b, int nb, int m) {
 xm_status split_trsm(xm_ctx* ctx, void* cublas, const double* L, int ldl, double* X, int ldx,
                      int m, int n) {
   cudaStream_t st = ctx->stream;
-  cublasHandle_t cb = static_cast<cublasHandle_t>(cublas);
   const int b = OZ_TRSM_BLOCK;                               // a multiple of OZ_BM and OZ_BK
   const int K_pad = b;
   const int nb = (m + b - 1) / b;
   const int nJ = (n + OZ_BN - 1) / OZ_BN;
   const int rowsB = nJ * OZ_BN;
   const int rowsA_max = ((std::max(m - b, b) + OZ_BM - 1) / OZ_BM) * OZ_BM;
-  DevMem SA, SB, scA, scB, tl, tld, Li, ptrs;
+  DevMem SA, SB, scA, scB, tl, tld, Li;
   XM_CUDA_TRY(cudaMalloc(&SA.p, sizeof(__nv_bfloat16) * (size_t)OZ_SLICES * rowsA_max * K_pad));
   XM_CUDA_TRY(cudaMalloc(&SB.p, sizeof(__nv_bfloat16) * (size_t)OZ_SLICES * rowsB * K_pad));
   XM_CUDA_TRY(cudaMalloc(&scA.p, sizeof(int) * (size_t)rowsA_max));
@@ -655,34 +716,7 @@ xm_status split_trsm(xm_ctx* ctx, void* cublas, const double* L, int ldl, double
 
   // -L_jj^{-1} for every diagonal block (FP64, column-major b x b each)
   XM_CUDA_TRY(cudaMalloc(&Li.p, sizeof(double) * (size_t)nb * b * b));
-  k_oz_eye_blocks<<<ctx->num_sms * 4, 256, 0, st>>>(Li.as<double>(), b, nb, m);
-  XM_CUDA_TRY(cudaGetLastError());
-  const double minus_one = -1.0;
-  const int nfull = m / b;
-  std::vector<double*> hptr((size_t)2 * std::max(nfull, 1));   // [A pointers | B pointers]
-  if (nfull > 0) {
-    for (int j = 0; j < nfull; ++j) {
-      hptr[j] = const_cast<double*>(L) + (size_t)j * b + (size_t)j * b * ldl;
-      hptr[nfull + j] = Li.as<double>() + (size_t)j * b * b;
-    }
-    XM_CUDA_TRY(cudaMalloc(&ptrs.p, sizeof(double*) * (size_t)2 * nfull));
-    XM_CUDA_TRY(cudaMemcpyAsync(ptrs.p, hptr.data(), sizeof(double*) * (size_t)2 * nfull,
-                                cudaMemcpyHostToDevice, st));
-    double** dp = ptrs.as<double*>();
-    const double* const* dA = dp;
-    double* const* dB = dp + nfull;
-    if (cublasDtrsmBatched(cb, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N,
-                           CUBLAS_DIAG_NON_UNIT, b, b, &minus_one, dA, ldl, dB, b, nfull) !=
-        CUBLAS_STATUS_SUCCESS)
-      return set_error(XM_ECUDA, "cublasDtrsmBatched (diagonal block inverses) failed");
-  }
-  if (m % b) {
-    const int j = nfull, bj = m - j * b;
-    if (cublasDtrsm(cb, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N, CUBLAS_DIAG_NON_UNIT, bj,
-                    bj, &minus_one, L + (size_t)j * b + (size_t)j * b * ldl, ldl,
-                    Li.as<double>() + (size_t)j * b * b, b) != CUBLAS_STATUS_SUCCESS)
-      return set_error(XM_ECUDA, "cublasDtrsm (last diagonal block inverse) failed");
-  }
+  XM_TRY(tri_inverse_blocks(ctx, cublas, L, ldl, m, b, Li.as<double>()));
 
   auto gemm = [&](const int2* tiles, const std::vector<int2>& order, int rowsA, int KB,
                   double* out, int M) -> xm_status {
@@ -749,7 +783,9 @@ namespace xm {
 // In-place Cholesky factor of the m x m SPD matrix A (column-major, leading dimension lda, lower
 // triangle used and overwritten by L): right-looking, blocks of 512; the diagonal blocks by
 // cuSOLVER DPOTRF and the panels by cuBLAS DTRSM (FP64), the trailing updates
-// A_rest -= L_k L_k^T on the tensor cores (only the tiles that meet the lower triangle).
+// A_rest -= L_k L_k^T on the tensor cores (only the tiles that meet the lower triangle).  (Panels
+// as products with explicit inverses of the diagonal blocks doubled the build's difference from
+// the FP64 build at 1500 cameras, to 2.1e-11 of max |Q|.)
 // *minor = 0 on success, else the 1-based order of the first non-positive leading minor.
 xm_status split_potrf(xm_ctx* ctx, void* cublas, void* cusolver, double* A, int lda, int m,
                       int* minor) {
@@ -771,6 +807,7 @@ xm_status split_potrf(xm_ctx* ctx, void* cublas, void* cusolver, double* A, int 
   XM_CUDA_TRY(cudaMalloc(&sc.p, sizeof(int) * (size_t)rows_max));
   XM_CUDA_TRY(cudaMalloc(&tl.p, sizeof(int2) * (size_t)(rows_max / OZ_BM) * (rows_max / OZ_BN)));
   const double one = 1.0;
+  std::vector<int2> order;
   for (int k0 = 0; k0 < m; k0 += b) {
     const int bk = std::min(b, m - k0);
     double* Akk = A + k0 + (size_t)k0 * lda;
@@ -789,13 +826,13 @@ xm_status split_potrf(xm_ctx* ctx, void* cublas, void* cusolver, double* A, int 
       return set_error(XM_ECUDA, "cublasDtrsm (panel %d) failed", k0 / b);
     const int rows = ((rest + OZ_BN - 1) / OZ_BN) * OZ_BN;
     const size_t stride = (size_t)rows * K_pad;
+    const int nI = (rest + OZ_BM - 1) / OZ_BM, nJ = (rest + OZ_BN - 1) / OZ_BN;
     k_oz_split_rows<<<split_grid(ctx, rows, 128), 128, 0, st>>>(P, lda, bk, rest, rows, K_pad,
                                                                S.as<__nv_bfloat16>(), stride,
                                                                sc.as<int>());
     XM_CUDA_TRY(cudaGetLastError());
-    const int nI = (rest + OZ_BM - 1) / OZ_BM, nJ = (rest + OZ_BN - 1) / OZ_BN;
     // 128 x 256 tiles with some column <= some row (they meet the lower triangle)
-    std::vector<int2> order = tile_order(nI, nJ, [](int I, int J) { return J * OZ_BN <= I * OZ_BM + OZ_BM - 1; });
+    order = tile_order(nI, nJ, [](int I, int J) { return J * OZ_BN <= I * OZ_BM + OZ_BM - 1; });
     XM_CUDA_TRY(cudaMemcpyAsync(tl.p, order.data(), sizeof(int2) * order.size(),
                                 cudaMemcpyHostToDevice, st));
     CUtensorMap ma, mb;
@@ -813,7 +850,7 @@ xm_status split_potrf(xm_ctx* ctx, void* cublas, void* cusolver, double* A, int 
     a.ncols = rest;
     a.err = ctx->d_err;
     XM_TRY(launch_mma<OZ_GEMM>(ctx, ma, mb, a));
-    // the host order vector is reused next step
+    // the host order vectors are reused next step
     XM_CUDA_TRY(cudaStreamSynchronize(st));
   }
   return check_device_error(ctx, "split-BF16 Cholesky factor");
