@@ -761,7 +761,11 @@ struct Solver {
       const double en = std::sqrt(pcMinv ? h_sc->ee : h_sc->eta2);   // ||eta|| in the tCG's norm
       const bool finite = std::isfinite(fc) && std::isfinite(dfc);
       if (!finite || rho < 0.25) {
-        Delta *= 0.25;
+        // a quarter of the step actually taken when it stayed inside the region: the tCG's
+        // interior solution is what failed, and shrinking from a radius it never reached only
+        // repeats it (the FP32-HVP polish ran 200 iterations to the same rejected interior step
+        // at every radius from 5e-2 down to 3e-6); for a boundary step en = Delta
+        Delta = 0.25 * ((finite && en > 0.0) ? std::min(Delta, en) : Delta);
       } else if (rho > 0.75 && en >= Delta * (1.0 - 1e-6)) {
         Delta = std::min(2.0 * Delta, Delta_bar);
       }
