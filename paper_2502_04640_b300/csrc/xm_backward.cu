@@ -13,14 +13,14 @@
 //
 // Device path:
 //   1. FP64 gradient at Y (dual blocks Lambda of Sec. 3), dL/dY from dL/dG, tangent projection.
-//   2. Hess[lambda] = g_L by conjugate gradients on the Q sweep, preconditioned by the
-//      per-camera 3 x 3 diagonal blocks of the certificate matrix Z (block Jacobi, projected
-//      onto the tangent space): FP64 operator for prec FP64; otherwise FP32 inner CG with FP64
-//      residual refinement (mixed-precision iterative refinement: each refinement step solves
-//      Hess[delta] = g_L - Hess64[lambda] in FP32).
+//   2. Hess[lambda] = g_L by conjugate gradients on the Q sweep, preconditioned by
+//      (Z + gamma Pi_Y)^-1 (Z the certificate matrix; an explicit FP32 inverse packed like Q and
+//      applied by the same sweep, n <= 40000) or else by Z's per-camera 3 x 3 diagonal blocks,
+//      projected onto the tangent space: FP64 operator for prec FP64; otherwise FP32 inner CG
+//      with FP64 residual refinement (mixed-precision iterative refinement: each refinement
+//      step solves Hess[delta] = g_L - Hess64[lambda] in FP32).
 //   3. The optimal residuals of the 2R columns [Y, lambda]: landmark means, camera sums, the
 //      anchored translation solve with the Cholesky factor of Sbar, then the outputs.
-#include <cublas_v2.h>
 #include <cusolverDn.h>
 
 #include <algorithm>
