@@ -319,7 +319,6 @@ k_deflate(int N, const T* __restrict__ Y, T* __restrict__ v, const double* __res
   for (int a = 0; a < R; ++a)
 #pragma unroll
     for (int b = 0; b < R; ++b) O[a][b] = Om[a * R + b];
-  const size_t n = (size_t)3 * N;
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
