@@ -62,24 +62,28 @@ typedef enum xm_prec { XM_FP64 = 0, XM_FP32_BULK = 1, XM_BF16Q_BULK = 2 } xm_pre
 #define XM_STORE_ALL  7u
 
 typedef struct xm_opts {
-  int r0;                  /* initial BM rank, 1 <= r0 <= XM_MAX_RANK (Alg. 1 uses 3)      */
-  int r_max;               /* staircase cap, r0 <= r_max <= XM_MAX_RANK                    */
-  int prec;                /* xm_prec                                                       */
-  double grad_tol_rel;     /* final stop: ||rgrad|| <= grad_tol_rel * ||rgrad(Y0)||         */
-  double bulk_tol_rel;     /* mixed modes: hand over to the FP64 polish at this tolerance   */
-  double cert_tau_rel;     /* certified iff lambda_min(Z) >= -cert_tau_rel * lambda_max     */
-  int max_outer;           /* RTR iterations per rank (per phase)                          */
-  int max_tcg;             /* tCG iterations per RTR step                                  */
-  int max_polish;          /* FP64 polish RTR iterations (mixed modes)                     */
+  int r0;                  /* initial BM rank, 1 <= r0 <= XM_MAX_RANK (Alg. 1 uses 3);
+                              default 4                                                     */
+  int r_max;               /* staircase cap, r0 <= r_max <= XM_MAX_RANK (default XM_MAX_RANK) */
+  int prec;                /* xm_prec (default XM_FP32_BULK)                                */
+  double grad_tol_rel;     /* final stop: ||rgrad|| <= grad_tol_rel * ||rgrad(Y0)||
+                              (default 1e-11)                                                */
+  double bulk_tol_rel;     /* mixed modes: hand over to the FP64 polish at this tolerance
+                              (default 1e-9)                                                 */
+  double cert_tau_rel;     /* certified iff lambda_min(Z) >= -cert_tau_rel * lambda_max
+                              (default 1e-6)                                                 */
+  int max_outer;           /* RTR iterations per rank (per phase; default 300)             */
+  int max_tcg;             /* tCG iterations per RTR step (default 200)                    */
+  int max_polish;          /* FP64 polish RTR iterations (mixed modes; default 20)         */
   int lanczos_max;         /* Krylov dimension cap of the certificate (default 800)        */
-  double lanczos_tol;      /* Ritz residual / |theta_max| stop for lambda_min              */
-  double time_limit_s;     /* wall-clock cap of xm_solve (<= 0: none)                      */
-  uint64_t seed;           /* Lanczos start vector                                         */
-  int verbose;             /* 0 silent, 1 per rank, 2 per RTR iteration (stderr)           */
+  double lanczos_tol;      /* Ritz residual / |theta_max| stop for lambda_min (default 1e-8) */
+  double time_limit_s;     /* wall-clock cap of xm_solve (<= 0: none; default 0)           */
+  uint64_t seed;           /* Lanczos start vector and init_jitter fill (default 12345)    */
+  int verbose;             /* 0 silent (default), 1 per rank, 2 per RTR iteration (stderr)  */
   double init_jitter;      /* start = Alg. 1's [I_3, ..., I_3] padded to rank r0, plus this
                               amplitude times a seeded uniform(-1, 1) fill of the extra
                               columns (0: the padded start exactly; a zero column confines
-                              rank-r0 RTR to the rank-3 subspace)                           */
+                              rank-r0 RTR to the rank-3 subspace); default 0.1              */
   double scale_reg;        /* App. D scale regularisation: objective tr(QX) + scale_reg *
                               sum_{i>=2} (X_{3i,3i} - 1)^2 (the third diagonal entry of every
                               non-anchor block, paper's 1-based indexing); Z, the dual value
@@ -94,8 +98,8 @@ typedef struct xm_opts {
                               polish once ||rgrad|| <= 1e-6 ||rgrad(Y0)|| and the best objective
                               has not improved by more than the ratio test's FP32 noise allowance
                               over k outer steps (the FP32 objective is noise there); the polish
-                              starts from the bulk's trust radius.  0 runs the bulk to
-                              bulk_tol_rel or max_outer.  0 <= k <= max_outer               */
+                              starts from the bulk's trust radius.  0 (default) runs the bulk
+                              to bulk_tol_rel or max_outer.  0 <= k <= max_outer            */
   int cert_lobpcg;         /* certificates with FP32 Z products (mixed modes): 1 (default)
                               finds lambda_min(Z) on range(Y)^perp by block-Jacobi preconditioned
                               LOBPCG (blocks of 4, stop at a Ritz residual <= 1e-6 lambda_max,
