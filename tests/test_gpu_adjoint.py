@@ -87,6 +87,29 @@ def test_backward_matches_oracle_adjoint(C, name, prec):
     q.free()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_backward_on_a_zero_padded_rank(C, prec):
+    """The certified point with a zero column appended is the same point of the SDP (X = Y Y^T
+    unchanged); at rank 5 the adjoint runs its R = 8 instantiation (the packed-inverse
+    preconditioner's sweep at R = 8 included) and must return the rank-4 gradients: the loss
+    gradient and hence lambda have no component in the zero column."""
+    from paper_2502_04640_b300 import xm
+    sc = _scenes()["random"]
+    q, t, out = _solve(C, sc, xm.xm_default_opts(prec=0, grad_tol_rel=1e-12))
+    assert out["status"] == 0 and out["info"]["certified"] == 1
+    r = out["info"]["rank"]
+    Y = out["Y"][:, :r].contiguous()
+    Yp = torch.cat([Y, torch.zeros((Y.shape[0], 1), dtype=Y.dtype, device=Y.device)], dim=1)
+    D = torch.as_tensor(_dG(sc, 11), device="cuda:0")
+    bopts = xm.xm_default_opts(prec=PRECS[prec], grad_tol_rel=1e-12)
+    u, w, _, info, st = xm.xm_backward(q, Y, r, sc.M, *t, D, bopts)
+    up, wp, _, infop, stp = xm.xm_backward(q, Yp.contiguous(), r + 1, sc.M, *t, D, bopts)
+    assert st == 0 and stp == 0 and infop["dense_precond"] == 1
+    assert _max_rel(up.cpu().numpy(), u.cpu().numpy()) <= 1e-6
+    assert _max_rel(wp.cpu().numpy(), w.cpu().numpy()) <= 1e-6
+    q.free()
+
+
 def test_backward_matches_oracle_solution(C):
     """Both pipelines end to end (own solve, own adjoint) on the same observations."""
     from paper_2502_04640_b300 import xm
