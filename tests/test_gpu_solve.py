@@ -56,6 +56,21 @@ def test_config1_matches_oracle(C, prec, jitter):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_start_above_rank_4_reaches_the_same_optimum(C, prec):
+    """r0 = 5 runs every RTR phase in the 8-column layout (the R = 8 kernels); X = Y Y^T of a
+    certified optimum is unique, so the certified result is the oracle's rank-4 one."""
+    sc = scenes.config1()
+    ref = O.solve(O.build_Q_schur(sc.N, sc.M, sc.cam, sc.lmk, sc.ukp, sc.w), r0=4)
+    q, out = _solve(C, sc, PRECS[prec], r0=5)
+    info = out["info"]
+    assert out["status"] == 0 and info["certified"] == 1 and info["rank"] >= 5
+    assert _rel(info["f"], ref.f) <= 1e-6
+    assert np.abs(out["R"] - ref.R).max() <= 1e-5
+    assert np.abs(out["s"] - ref.s).max() <= 1e-5 * ref.s.max()
+    q.free()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_noise_free_recovery(C, prec):
     sc = scenes.circle_scene(40, 600, 4, 0.0, seed=11)
     q, out = _solve(C, sc, PRECS[prec])
