@@ -160,3 +160,26 @@ def test_deflation_basis_is_an_orthonormal_basis_of_range_Y():
     assert U.shape == (24, 3)
     assert np.abs(U.T @ U - np.eye(3)).max() <= 1e-12
     assert np.abs(U @ (U.T @ Y) - Y).max() <= 1e-12 * np.abs(Y).max()
+
+
+def test_retraction_returns_the_closest_feasible_block():
+    """retract(Y, Xi) is, per non-anchor block, the nearest c U (c > 0, U U^T = I) to
+    Y_i + Xi_i: no feasible point obtained by perturbing its scale and rotating its rows or its
+    row space is closer."""
+    rng = np.random.default_rng(13)
+    N, r = 4, 5
+    Y = O.random_point(N, r, rng)
+    Xi = 0.4 * rng.standard_normal(Y.shape)
+    A = O.blocks(Y + Xi)
+    P = O.blocks(O.retract(Y, Xi))
+    for i in range(1, N):
+        c = math.sqrt(np.trace(P[i] @ P[i].T) / 3.0)
+        U = P[i] / c
+        assert np.abs(U @ U.T - np.eye(3)).max() <= 1e-12
+        best = np.linalg.norm(A[i] - P[i])
+        for _ in range(200):
+            W = 1e-3 * rng.standard_normal((3, 3)); W = W - W.T            # row rotation
+            V = 1e-3 * rng.standard_normal((r, r)); V = V - V.T            # row-space rotation
+            Up = scipy.linalg.expm(W) @ U @ scipy.linalg.expm(V)
+            cp = c * math.exp(1e-3 * rng.standard_normal())
+            assert np.linalg.norm(A[i] - cp * Up) >= best - 1e-12
