@@ -14,7 +14,7 @@ Notation (paper, Sec. 2-3 and App. A):
     f(Y) = tr(Q U^T U) = tr(Y^T Q Y)   (Eq. 5 / Eq. 17).
     Camera 0 is the anchor (the paper's camera 1): alpha_0 = 1.
 
-Readings of the paper taken here (each is also listed in the design notes):
+Readings of the paper taken here:
   * App. A writes Q1 with a stray "p_{i,k}^T"; the sum of w (e_i (x) u)(e_i (x) u)^T is used.
   * App. A's anchored least-squares solve carries a sign slip in two places that cancel;
     ``build_Q_literal`` follows the printed A and Q formulas, ``build_Q_schur`` the

@@ -283,3 +283,87 @@ def test_rounding_projects_reflections_onto_SO3():
     # the mirrored camera's rounded rotation is the SO(3) projection of its O(3) block
     Yb = np.swapaxes(O.blocks(res.Y @ np.linalg.eigh(res.Y.T @ res.Y)[1][:, ::-1][:, :3]), 1, 2)
     assert np.linalg.det(Yb[3]) * np.linalg.det(Yb[0]) < 0
+
+
+# ------------------------------------------------------------------ Eq. 18 and App. E's bound
+
+def _rounded_cost_brute_force(sc, R, s):
+    """rho_hat evaluated independently of the oracle's Q: the SBA cost (Eq. 3) at the rounded
+    rotations and scales, minimised over translations and landmarks by dense least squares."""
+    U = np.concatenate([s[i] * R[i] for i in range(sc.N)], axis=1)
+    c, _, _ = O.min_over_tp(sc.N, sc.M, sc.cam, sc.lmk, sc.ukp, sc.w, U.T)
+    return c
+
+
+def test_eta_against_barrier_sdp_value_and_brute_force_rounding():
+    """A 6-camera scene whose rank-3 SDP optimum holds a reflected block (Prop. 2: O(3) but not
+    SO(3)), so rounding to SO(3) costs something and the chain rho_SDP <= rho_hat of Eq. 17 is
+    strict.  eta must equal Eq. 18 evaluated on independent values: rho_SDP from the primal
+    log-barrier solver and rho_hat from brute-force least squares over t, p at the rounded
+    (R, s).  A swapped numerator sign gives eta < 0; a dropped "1 +" in the denominator moves eta
+    by 0.2 %."""
+    sc = scenes.random_scene(6, 40, noise=0.3, outlier_frac=0.2, seed=7, center_sigma=2.0)
+    Q = _Q(sc)
+    res = O.solve(Q, r0=4)
+    rho_sdp, X = O.sdp_barrier(Q)
+    rho_hat = _rounded_cost_brute_force(sc, res.R, res.s)
+    assert res.certified
+    assert np.all(np.linalg.det(res.R) > 0.999)
+    assert abs(res.rho_hat - rho_hat) <= 1e-9 * (1 + rho_hat)
+    assert abs(res.f - rho_sdp) <= 1e-7 * (1 + rho_sdp)
+    eta = (rho_hat - rho_sdp) / (1.0 + abs(rho_hat) + abs(rho_sdp))
+    assert eta > 1e-2                                                    # rounding is not free here
+    assert abs(res.eta - eta) <= 1e-6 * eta
+    # at a certified optimum lambda_min ~ 0, so App. E's bound gives the same value
+    assert abs(res.eta_robust - eta) <= 1e-6 * eta
+
+
+@pytest.mark.parametrize("N,seed", [(4, 2), (5, 1), (5, 7)])
+def test_app_e_lower_bound_brackets_the_sdp_value(N, seed):
+    """At an uncertified stationary point (the rank-3 saddle reached from [I, ..., I]) the dual
+    value alone exceeds rho_SDP; App. E's bound with the sign kept, tr(Lambda_0) +
+    min(0, lambda_min(Z)) tr(X), is a valid lower bound (weak duality) for the optimal X* of the
+    independent barrier solver, and in these instances also with tr(X) at the computed point.
+    The staircase stopped at rank 3 reports eta_robust >= the true relative gap (Eq. 18 with the
+    barrier's rho_SDP): the bound can only overstate the suboptimality."""
+    sc = scenes.random_scene(N, 40, noise=0.3, outlier_frac=0.2, seed=seed, center_sigma=2.0)
+    Q = _Q(sc)
+    rho_sdp, Xs = O.sdp_barrier(Q)
+    r3 = O.rtr(Q, O.initial_point(N, 3))
+    c3 = O.certify(Q, r3.Y)
+    assert c3.lam_min < -1.0                                             # not certified
+    assert c3.dual > rho_sdp + 1.0 and r3.f >= rho_sdp                   # the dual value alone is no bound
+    lower_star = c3.dual + min(0.0, c3.lam_min) * np.trace(Xs)
+    lower_here = c3.dual + min(0.0, c3.lam_min) * float(np.sum(r3.Y * r3.Y))
+    assert lower_star <= rho_sdp + 1e-8 * (1 + abs(rho_sdp))
+    assert lower_here <= rho_sdp
+    res = O.solve(Q, r0=3, r_max=3)
+    assert not res.certified and res.rank == 3
+    rho_hat = _rounded_cost_brute_force(sc, res.R, res.s)
+    eta_true = (rho_hat - rho_sdp) / (1.0 + abs(rho_hat) + abs(rho_sdp))
+    assert eta_true > 0
+    assert res.eta_robust >= eta_true
+    assert res.eta_robust < 1.0
+
+
+def test_iterative_certificate_branch_matches_dense_branch():
+    """certify's branch for large n (ARPACK on the Z operator, deflated) against its dense eigh
+    branch on the same small instance, at the certified optimum and at the rank-3 saddle."""
+    sc = scenes.config1()
+    Q = _Q(sc)
+    opt = O.solve(Q, r0=4)
+    r3 = O.rtr(Q, O.initial_point(sc.N, 3))
+    for Y in (opt.Y, r3.Y):
+        d = O.certify(Q, Y)
+        it = O.certify(Q, Y, dense_limit=0)
+        scale = d.lam_max_Q
+        assert abs(it.lam_max_Q - d.lam_max_Q) <= 1e-8 * scale
+        assert abs(it.lam_min - d.lam_min) <= 1e-8 * scale
+        assert abs(it.lam_min_deflated - d.lam_min_deflated) <= 1e-8 * scale
+        assert it.dual == d.dual and np.array_equal(it.Lambda, d.Lambda)
+        Z = Q.copy()
+        for i in range(sc.N):
+            Z[3 * i:3 * i + 3, 3 * i:3 * i + 3] -= d.Lambda[i]
+        # the returned vector is an eigenvector of lambda_min in both branches
+        for c in (d, it):
+            assert np.linalg.norm(Z @ c.v - c.lam_min * c.v) <= 1e-6 * scale
