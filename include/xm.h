@@ -138,6 +138,17 @@ void        xm_destroy(xm_ctx* ctx);
 const char* xm_last_error(void);
 xm_status   xm_sync(xm_ctx* ctx);
 
+/* Self-check of the failure path that every pipelined kernel shares (the paper has no
+ * counterpart: its solver has no device-side waits).  Each wait of a CTA on its copy pipeline is
+ * a bounded poll of an mbarrier; when the bound runs out the kernel raises a timeout flag in the
+ * context's device error word, stops waiting and returns, and the calling entry point reports
+ * XM_ETIMEOUT.  This call runs that wait in isolation: one CTA initialises an mbarrier for one
+ * arrival and waits for its first phase with at most `polls` polls (1 <= polls <= 2^24, the
+ * kernels' own bound).  arrive = 1: the CTA arrives first, the wait completes, XM_OK.
+ * arrive = 0: nothing arrives, the wait gives up, XM_ETIMEOUT; no copy is in flight and the
+ * context stays usable.  Synchronous; XM_EINVAL for polls out of range. */
+xm_status   xm_selftest_wait(xm_ctx* ctx, long long polls, int arrive);
+
 /* ---- Q construction (Prop. 1, App. A) ------------------------------------------------
  * Q = P - Bbar Sbar^{-1} Bbar^T with P = Q1 - V2 Q3^{-1} V2^T, B = V1 - V2 Q3^{-1} V3^T,
  * S = Q2 - V3 Q3^{-1} V3^T (landmarks eliminated, then translations with t_0 = 0); equal to
@@ -198,6 +209,8 @@ xm_status xm_qy(xm_ctx* ctx, const xm_qmat* q, int prec, int r, const void* Y, v
  * to a multiple of 128 and R = 1, 4 or 8 the padded width of r (for example every precision and
  * r <= 8 at 10155 cameras).  Larger sizes are rejected with XM_EINVAL (use xm_qy).  The first
  * call on a device looks up the array's device address; make it before any stream capture.
+ * The address is kept for the life of the process: after cudaDeviceReset on a device, do not
+ * call this entry point on that device again.
  * All calls share the array: calls whose work overlaps on the GPU race.  Asynchronous on the
  * context stream. */
 xm_status xm_qy_noalloc(xm_ctx* ctx, const xm_qmat* q, int prec, int r, const void* Y, void* W);

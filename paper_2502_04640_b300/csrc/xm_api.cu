@@ -54,11 +54,39 @@ void free_tiles(DeviceQ& q);
 xm_status pack_dense(xm_ctx* ctx, DeviceQ& q, const double* Qd);
 xm_status unpack_dense(xm_ctx* ctx, const DeviceQ& q, double* Qd);
 
+// Self-check of the bounded waits (xm_selftest_wait): thread 0 initialises an mbarrier for one
+// arrival, optionally arrives on it, and waits for phase 0 with at most `polls` polls.  No copy
+// or transaction count is attached to the barrier, so a wait that gives up leaves nothing in
+// flight; the barrier is invalidated before the CTA exits.
+static __global__ void k_selftest_wait(int* err, long long polls, int arrive) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (arrive) mbar_arrive(&bar);
+    if (!mbar_wait(&bar, 0, polls)) atomicOr(err, DEV_TIMEOUT);
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&bar)) : "memory");
+  }
+}
+
 }  // namespace xm
 
 using namespace xm;
 
 extern "C" {
+
+xm_status xm_selftest_wait(xm_ctx* c, long long polls, int arrive) {
+  if (!c) return set_error(XM_EINVAL, "xm_selftest_wait: NULL context");
+  if (polls < 1 || polls > WAIT_LIMIT)
+    return set_error(XM_EINVAL, "xm_selftest_wait: polls=%lld not in [1, %lld]", polls, WAIT_LIMIT);
+  XM_CUDA_TRY(cudaSetDevice(c->device));
+  k_selftest_wait<<<1, 32, 0, c->stream>>>(c->d_err, polls, arrive ? 1 : 0);
+  XM_CUDA_TRY(cudaGetLastError());
+  return check_device_error(c, "xm_selftest_wait");
+}
 
 int xm_abi_version(void) { return XM_ABI_VERSION; }
 

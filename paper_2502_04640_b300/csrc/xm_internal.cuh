@@ -153,10 +153,12 @@ __device__ __forceinline__ void fence_mbar_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 // Bounded wait for the completion of the phase with the given parity.  Returns false after
-// WAIT_LIMIT polls (the caller records DEV_TIMEOUT and stops waiting).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// `limit` polls (WAIT_LIMIT unless a self-check passes a smaller one); the caller records
+// DEV_TIMEOUT and stops waiting.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
+                                          long long limit = WAIT_LIMIT) {
   const uint32_t a = smem_u32(bar);
-  for (long long it = 0; it < WAIT_LIMIT; ++it) {
+  for (long long it = 0; it < limit; ++it) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"

@@ -11,7 +11,10 @@
 // address is looked up once per device, on the first call made on that device (with that
 // device current); make that first call before any stream capture.  All calls share the array
 // and it keeps the previous call's contents, so the padded W is cleared on every call; two
-// calls whose work overlaps on the GPU (different streams or contexts) race on it.
+// calls whose work overlaps on the GPU (different streams or contexts) race on it.  The
+// looked-up address is kept for the life of the process: after cudaDeviceReset on a device
+// (which also invalidates every context, stream and Q handle made on it) this entry point must
+// not be used on that device again.
 #include <algorithm>
 #include <mutex>
 

@@ -107,6 +107,7 @@ def lib() -> ctypes.CDLL:
         "xm_destroy": (None, [_P]),
         "xm_last_error": (ctypes.c_char_p, []),
         "xm_sync": (ctypes.c_int, [_P]),
+        "xm_selftest_wait": (ctypes.c_int, [_P, ctypes.c_longlong, ctypes.c_int]),
         "xm_build_Q": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int64, _P, _P, _P, _P,
                                       ctypes.c_uint, ctypes.POINTER(_P)]),
         "xm_qmat_from_dense": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_uint, ctypes.POINTER(_P)]),
@@ -289,6 +290,11 @@ def xm_bench_qy(q: QMat, prec: int, r: int, iters: int = 20):
     mean, mn = ctypes.c_double(), ctypes.c_double()
     _check(lib().xm_bench_qy(q.ctx.h, q.h, prec, r, iters, ctypes.byref(mean), ctypes.byref(mn)))
     return mean.value, mn.value
+
+
+def xm_selftest_wait(ctx: Context, polls: int, arrive: bool) -> int:
+    """Bounded-wait self-check: XM_OK when the barrier is arrived on, XM_ETIMEOUT when not."""
+    return _check(lib().xm_selftest_wait(ctx.h, polls, 1 if arrive else 0), (XM_OK, XM_ETIMEOUT))
 
 
 def xm_last_launch_count() -> int:

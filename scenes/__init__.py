@@ -22,7 +22,7 @@ import numpy as np
 __all__ = [
     "Scene", "haar_rotations", "circle_scene", "random_scene", "trajectory_scene",
     "config1", "config2", "config3", "config4", "config5", "sub_scene",
-    "batch_scenes", "shuffled",
+    "batch_scenes", "shuffled", "depth_noise_scenes", "DEPTH_NOISE_EPS",
 ]
 
 
@@ -114,7 +114,7 @@ def _distinct_observers(rng, N: int, L: np.ndarray):
 
 
 def _observe(name, rng, R, s, t, p, obs, noise_sigma, outlier_frac, outlier_half,
-             w_lo, w_hi, mult_noise=0.0, meta=None) -> Scene:
+             w_lo, w_hi, mult_noise=0.0, meta=None, depth_eps=0.0) -> Scene:
     N, M = R.shape[0], p.shape[0]
     cam, lmk = obs
     E = cam.size
@@ -123,6 +123,11 @@ def _observe(name, rng, R, s, t, p, obs, noise_sigma, outlier_frac, outlier_half
     ukp = np.einsum("eba,eb->ea", R[cam], d) / s[cam][:, None]
     if mult_noise > 0:
         ukp *= (1.0 + mult_noise * rng.standard_normal(E))[:, None]
+    if depth_eps > 0:
+        # depth-noise model of the paper's noise analysis: every observation's depth (hence its
+        # lifted keypoint) is scaled by (1 + eps)^x with x ~ U(-1, 1) drawn per observation
+        x = rng.uniform(-1.0, 1.0, size=E)
+        ukp *= np.power(1.0 + depth_eps, x)[:, None]
     if noise_sigma > 0:
         ukp += noise_sigma * rng.standard_normal((E, 3))
     outlier = np.zeros(E, dtype=bool)
@@ -135,9 +140,10 @@ def _observe(name, rng, R, s, t, p, obs, noise_sigma, outlier_frac, outlier_half
 
 def circle_scene(N: int = 20, M: int = 200, obs_per_lmk: int = 4, noise: float = 0.01,
                  seed: int = 0, radius: float = 5.0, s_range=(0.5, 2.0), w_range=(1.0, 1.0),
-                 name: str | None = None) -> Scene:
+                 name: str | None = None, depth_eps: float = 0.0) -> Scene:
     """Cameras on a circle of the given radius, Haar rotations, landmarks in [-1,1]^3,
-    each landmark seen by ``obs_per_lmk`` distinct random cameras (the tiny FP64 workload)."""
+    each landmark seen by ``obs_per_lmk`` distinct random cameras (the tiny FP64 workload).
+    depth_eps > 0 adds the depth-noise factor (1 + depth_eps)^x, x ~ U(-1, 1), per observation."""
     rng = np.random.default_rng(seed)
     R = haar_rotations(rng, N)
     th = 2 * math.pi * np.arange(N) / N
@@ -147,16 +153,19 @@ def circle_scene(N: int = 20, M: int = 200, obs_per_lmk: int = 4, noise: float =
     L = np.full(M, min(obs_per_lmk, N), dtype=np.int64)
     obs = _distinct_observers(rng, N, L)
     return _observe(name or f"circle-N{N}-M{M}", rng, R, s, t, p, obs, noise, 0.0, 0.0,
-                    w_range[0], w_range[1], meta=dict(kind="circle", seed=seed))
+                    w_range[0], w_range[1], meta=dict(kind="circle", seed=seed, depth_eps=depth_eps),
+                    depth_eps=depth_eps)
 
 
 def random_scene(N: int, M: int, noise: float = 0.02, outlier_frac: float = 0.0, seed: int = 1,
                  geom_p: float = 0.25, min_track: int = 2, center_sigma: float = 10.0,
                  s_range=(0.3, 3.0), w_range=(0.5, 1.0), lmk_half: float = 10.0,
-                 outlier_half: float = 5.0, name: str | None = None) -> Scene:
+                 outlier_half: float = 5.0, name: str | None = None,
+                 depth_eps: float = 0.0) -> Scene:
     """Community-photo-shaped scene: Haar rotations, Gaussian-clustered centres, track length
     min_track + Geometric(geom_p) (mean 5 for the defaults) clipped to N, a fraction of
-    observations replaced by outliers uniform in a box of side 2*outlier_half."""
+    observations replaced by outliers uniform in a box of side 2*outlier_half.  depth_eps > 0
+    adds the depth-noise factor (1 + depth_eps)^x, x ~ U(-1, 1), per observation."""
     rng = np.random.default_rng(seed)
     R = haar_rotations(rng, N)
     t = center_sigma * rng.standard_normal((N, 3))
@@ -166,7 +175,8 @@ def random_scene(N: int, M: int, noise: float = 0.02, outlier_frac: float = 0.0,
     obs = _distinct_observers(rng, N, L)
     return _observe(name or f"random-N{N}-M{M}", rng, R, s, t, p, obs, noise, outlier_frac,
                     outlier_half, w_range[0], w_range[1],
-                    meta=dict(kind="random", seed=seed, outlier_frac=outlier_frac))
+                    meta=dict(kind="random", seed=seed, outlier_frac=outlier_frac, depth_eps=depth_eps),
+                    depth_eps=depth_eps)
 
 
 def trajectory_scene(N: int = 2000, M: int = 400000, seed: int = 2, step: float = 0.05,
@@ -275,3 +285,18 @@ def batch_scenes(count: int = 256, seed: int = 3, lo: int = 10, hi: int = 400,
 
 def config5(seed: int = 3, count: int = 256) -> list:
     return batch_scenes(count, seed)
+
+
+# Depth-noise robustness sweep (the paper's noise analysis): noise levels eps of the factor
+# (1 + eps)^x, x ~ U(-1, 1), applied to every observation's depth, from mild to the level where
+# the paper reports the SDP relaxation itself to break (eps = 5).
+DEPTH_NOISE_EPS = (0.0, 0.1, 0.25, 0.5, 1.0, 1.5, 2.0, 3.0, 5.0)
+
+
+def depth_noise_scenes(eps: float, count: int = 8, N: int = 100, M: int = 2000,
+                       seed: int = 4) -> list:
+    """``count`` community-photo-shaped scenes (N cameras, M landmarks, track 2 + Geom(1/4), unit
+    weights) whose only perturbation is the depth-noise factor (1 + eps)^x per observation; scene
+    j uses seed seed * 1000 + j, so every noise level sees the same geometry."""
+    return [random_scene(N, M, noise=0.0, outlier_frac=0.0, seed=seed * 1000 + j, w_range=(1.0, 1.0),
+                         depth_eps=eps, name=f"depthnoise-eps{eps:g}-{j}-N{N}") for j in range(count)]

@@ -1,0 +1,61 @@
+"""Full-size parity on the 1934-camera community-photo workload (about 1.5 M observations, 2 %
+outliers): the CUDA build + solve + certificate in FP64 and in the FP32-bulk mode against the FP64
+oracle's solve of the same scene (Alg. 1 + RTR-tCG + Thm. 1 + rounding, about half a minute on
+the host).  Compared: certificate decision, objective and rounded value (relative 1e-6, 1 + |.|
+denominator), dual value, deflated and raw lambda_min (1e-5 of lambda_max), Eq. 18's eta and
+App. E's eta_robust, and the rounded rotations and scales (anchored gauge)."""
+import numpy as np
+import pytest
+
+import scenes
+from oracle import xm_oracle as O
+from tests.gpu_util import ctx
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def C():
+    c = ctx()
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def c2():
+    sc = scenes.config2()
+    ref = O.solve(O.build_Q_schur(sc.N, sc.M, sc.cam, sc.lmk, sc.ukp, sc.w), r0=4)
+    return sc, ref
+
+
+def _rel(a, b):
+    return abs(a - b) / (1.0 + abs(b))
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_config2_matches_oracle(C, c2, prec):
+    from paper_2502_04640_b300 import xm
+    sc, ref = c2
+    q = xm.xm_build_Q(C, sc.N, sc.M, *xm.scene_tensors(sc))
+    out = xm.xm_solve(q, xm.xm_default_opts(prec=prec))
+    info = out["info"]
+    R, s = out["R"].cpu().numpy(), out["s"].cpu().numpy()
+    lm = ref.cert.lam_max_Q
+    print(f"prec={prec} f={info['f']!r} oracle={ref.f!r} eta={info['eta']:.3e}/{ref.eta:.3e} "
+          f"dR={np.abs(R - ref.R).max():.2e} ds={np.abs(s - ref.s).max() / ref.s.max():.2e} "
+          f"lmin_defl={info['lambda_min_deflated']:.6e}/{ref.cert.lam_min_deflated:.6e}")
+    assert info["certified"] == int(ref.certified) == 1
+    assert _rel(info["f"], ref.f) <= 1e-6
+    assert _rel(info["rho_hat"], ref.rho_hat) <= 1e-6
+    assert abs(info["dual"] - ref.cert.dual) <= 1e-6 * (1 + abs(ref.f))
+    assert abs(info["lambda_min_deflated"] - ref.cert.lam_min_deflated) <= 1e-5 * lm
+    assert abs(info["lambda_min"] - ref.cert.lam_min) <= 1e-5 * lm
+    assert abs(info["eta"] - ref.eta) <= 2e-6
+    assert abs(info["eta_robust"] - ref.eta_robust) <= 2e-6
+    # rotations and scales: cameras with few, down-weighted observations move along directions
+    # that change the cost by less than its rounding, so compare the bulk tightly and bound the rest
+    dR = np.abs(R - ref.R).reshape(sc.N, -1).max(axis=1)
+    ds = np.abs(s - ref.s) / ref.s
+    assert np.median(dR) <= 1e-6 and np.median(ds) <= 1e-6
+    assert dR.max() <= 1e-2 and ds.max() <= 1e-2
+    q.free()

@@ -1,0 +1,43 @@
+"""Depth-noise robustness (the paper's noise analysis, s = (1 + eps)^x per observation): the CUDA
+solver against the FP64 oracle across noise levels, from mild to eps = 5 where the paper reports
+the relaxation to break.  Compared: the certificate decision, the objective and the rounded
+value (relative 1e-6, 1 + |.| denominator), Eq. 18's eta and App. E's eta_robust, the dual value
+and the deflated lambda_min."""
+import numpy as np
+import pytest
+
+import scenes
+from oracle import xm_oracle as O
+from tests.gpu_util import ctx
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def C():
+    c = ctx()
+    yield c
+    c.close()
+
+
+def _rel(a, b):
+    return abs(a - b) / (1.0 + abs(b))
+
+
+@pytest.mark.parametrize("eps", [0.25, 1.5, 5.0])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_depth_noise_solve_matches_oracle(C, eps, prec):
+    from paper_2502_04640_b300 import xm
+    sc = scenes.depth_noise_scenes(eps, count=1, N=30, M=600)[0]
+    ref = O.solve(O.build_Q_schur(sc.N, sc.M, sc.cam, sc.lmk, sc.ukp, sc.w), r0=4)
+    q = xm.xm_build_Q(C, sc.N, sc.M, *xm.scene_tensors(sc))
+    out = xm.xm_solve(q, xm.xm_default_opts(prec=prec))
+    info = out["info"]
+    assert info["certified"] == int(ref.certified) == 1
+    assert _rel(info["f"], ref.f) <= 1e-6
+    assert _rel(info["rho_hat"], ref.rho_hat) <= 1e-6
+    assert abs(info["dual"] - ref.cert.dual) <= 1e-6 * (1 + abs(ref.f))
+    assert abs(info["eta"] - ref.eta) <= 2e-6
+    assert abs(info["eta_robust"] - ref.eta_robust) <= 2e-6
+    assert abs(info["lambda_min_deflated"] - ref.cert.lam_min_deflated) <= 1e-5 * ref.cert.lam_max_Q
+    q.free()

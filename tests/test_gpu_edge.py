@@ -92,3 +92,23 @@ def test_zero_time_limit_returns_not_converged(C):
     assert bo["status"] == xm.XM_ENOCONV and bo["info"][0]["status"] == xm.XM_ENOCONV
     b.free()
     q.free()
+
+
+def test_bounded_wait_gives_up_and_the_context_stays_usable(C):
+    """The pipelined kernels' waits are bounded polls of an mbarrier: a wait that nobody completes
+    gives up after its limit, the kernel raises the timeout flag and the entry point returns
+    XM_ETIMEOUT (no trap, nothing in flight); the same context then runs a sweep correctly."""
+    from paper_2502_04640_b300 import xm
+    assert xm.xm_selftest_wait(C, 1000, arrive=True) == xm.XM_OK
+    assert xm.xm_selftest_wait(C, 1000, arrive=False) == xm.XM_ETIMEOUT
+    assert b"bounded device wait" in xm.lib().xm_last_error()
+    assert xm.xm_selftest_wait(C, 1, arrive=False) == xm.XM_ETIMEOUT
+    assert xm.lib().xm_selftest_wait(C.h, 0, 0) == xm.XM_EINVAL
+    assert xm.xm_selftest_wait(C, 1000, arrive=True) == xm.XM_OK     # the error word was cleared
+    Q = np.random.default_rng(2).standard_normal((30, 30))
+    Q = Q + Q.T
+    q = xm.xm_qmat_from_dense(C, torch.tensor(Q, device="cuda"))
+    Y = np.random.default_rng(3).standard_normal((30, 4))
+    W = xm.xm_qy(q, torch.tensor(Y, device="cuda"), xm.XM_FP64).cpu().numpy()
+    assert np.abs(W - Q @ Y).max() <= 1e-12 * np.abs(Q).sum()
+    q.free()

@@ -37,6 +37,28 @@ def test_sweep_matches_dense_product(C, N, r):
     q.free()
 
 
+@pytest.mark.parametrize("r", [1, 4, 8])
+def test_sweep_several_tiles_per_cta(C, r):
+    """n = 6000 (2000 cameras): 1128 packed tiles over the persistent grid, so every CTA walks a
+    range of about eight tiles across tile-row changes and around its copy ring; the full W is
+    checked element by element in all three storage precisions."""
+    from paper_2502_04640_b300 import xm
+    n = 6000
+    Q = rand_sym(n, 6000 + r)
+    Y = np.random.default_rng(60 + r).standard_normal((n, r))
+    q = xm.xm_qmat_from_dense(C, torch.tensor(Q, device="cuda"))
+    W64 = xm.xm_qy(q, torch.tensor(Y, device="cuda"), xm.XM_FP64).cpu().numpy()
+    assert np.all(np.abs(W64 - Q @ Y) <= gamma(n + 2, EPS64) * (np.abs(Q) @ np.abs(Y)))
+    Y32 = Y.astype(np.float32)
+    ref32 = Q @ Y32.astype(np.float64)
+    b32 = np.abs(Q) @ np.abs(Y32.astype(np.float64))
+    W32 = xm.xm_qy(q, torch.tensor(Y32, device="cuda"), xm.XM_FP32_BULK).cpu().numpy()
+    assert np.all(np.abs(W32 - ref32) <= (EPS32 + gamma(n + 2, EPS32)) * b32)
+    W16 = xm.xm_qy(q, torch.tensor(Y32, device="cuda"), xm.XM_BF16Q_BULK).cpu().numpy()
+    assert np.all(np.abs(W16 - ref32) <= (EPS_BF16 + gamma(n + 2, EPS32)) * b32)
+    q.free()
+
+
 def test_dense_roundtrip_and_symmetry(C):
     from paper_2502_04640_b300 import xm
     for N in (1, 43, 100):

@@ -48,6 +48,11 @@ def test_config1_matches_oracle(C, prec, jitter):
     assert _rel(info["rho_hat"], ref.rho_hat) <= 1e-6
     assert abs(info["dual"] - ref.cert.dual) <= 1e-6 * (1 + abs(ref.f))
     assert abs(info["lambda_min_deflated"] - ref.cert.lam_min_deflated) <= 1e-4 * ref.cert.lam_max_Q
+    # raw lambda_min(Z) (range(Y) is Z-invariant at a stationary point, so it is the smaller of
+    # the deflated minimum and Z's zero block on range(Y)), Eq. 18 and App. E's bound
+    assert abs(info["lambda_min"] - ref.cert.lam_min) <= 1e-5 * ref.cert.lam_max_Q
+    assert abs(info["eta"] - ref.eta) <= 2e-6
+    assert abs(info["eta_robust"] - ref.eta_robust) <= 2e-6
     assert np.abs(out["R"] - ref.R).max() <= 1e-5
     assert np.abs(out["s"] - ref.s).max() <= 1e-5 * ref.s.max()
     if jitter == 0.0:
@@ -136,6 +141,31 @@ def test_certify_entry_point_matches_oracle(C, prec):
     c3 = O.certify(Qo, r3.Y)
     assert bad["info"]["certified"] == 0
     assert abs(bad["info"]["lambda_min_deflated"] - c3.lam_min_deflated) <= 1e-5 * c3.lam_max_Q
+    assert abs(bad["info"]["lambda_min"] - c3.lam_min) <= 1e-5 * c3.lam_max_Q
+    assert abs(bad["info"]["dual"] - c3.dual) <= 1e-8 * (1 + abs(c3.f))
+    q.free()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_uncertified_stop_reports_app_e_bound(C, prec):
+    """The staircase capped at rank 3 from Alg. 1's start stops at config 1's rank-3 saddle
+    (Thm. 1 fails: lambda_min < 0): XM_ENOTCERT with the oracle's objective, dual value, raw
+    lambda_min, Eq. 18's eta and App. E's eta_robust (whose bound now carries
+    min(0, lambda_min) tr(X) < 0)."""
+    from paper_2502_04640_b300 import xm
+    sc = scenes.config1()
+    ref = O.solve(O.build_Q_schur(sc.N, sc.M, sc.cam, sc.lmk, sc.ukp, sc.w), r0=3, r_max=3)
+    assert not ref.certified and ref.cert.lam_min < 0
+    q, out = _solve(C, sc, PRECS[prec], r0=3, r_max=3, init_jitter=0.0)
+    info = out["info"]
+    assert out["status"] == xm.XM_ENOTCERT and info["certified"] == 0 and info["rank"] == 3
+    assert _rel(info["f"], ref.f) <= 1e-6
+    assert abs(info["dual"] - ref.cert.dual) <= 1e-6 * (1 + abs(ref.f))
+    assert abs(info["lambda_min"] - ref.cert.lam_min) <= 1e-5 * ref.cert.lam_max_Q
+    assert _rel(info["rho_hat"], ref.rho_hat) <= 1e-6
+    assert abs(info["eta"] - ref.eta) <= 2e-6
+    assert abs(info["eta_robust"] - ref.eta_robust) <= 1e-5 * ref.eta_robust
+    assert info["eta_robust"] > info["eta"]
     q.free()
 
 

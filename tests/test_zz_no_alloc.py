@@ -9,7 +9,7 @@ import ctypes
 import numpy as np
 import pytest
 
-from tests.gpu_util import EPS32, EPS64, ctx, gamma, rand_sym, torch
+from tests.gpu_util import EPS32, EPS64, EPS_BF16, ctx, gamma, rand_sym, torch
 
 pytestmark = pytest.mark.gpu
 
@@ -21,28 +21,36 @@ def _noalloc(xm, C, q, prec, Y):
 
 
 def test_noalloc_sweep_matches_xm_qy_twice():
+    """Calls in a row on the same shared array, alternating between a 450-row and a 183-row Q (a
+    smaller call after a larger one must not see stale rows), through every padded width
+    (r = 1, the 4-column layout at r = 3 and 4, the 8-column layout at r = 6 and 8, which also
+    moves W's offset in the array) and every storage precision (FP32, BF16, FP64)."""
     from paper_2502_04640_b300 import xm
     C = ctx()
     try:
         Q1 = rand_sym(3 * 150, 11)                    # 450 rows: 4 tiles, ragged tail
-        Q2 = rand_sym(3 * 61, 12)                     # smaller second call: stale rows must not leak
+        Q2 = rand_sym(3 * 61, 12)                     # 183 rows: 2 tiles
         q1 = xm.xm_qmat_from_dense(C, torch.tensor(Q1, device="cuda"))
         q2 = xm.xm_qmat_from_dense(C, torch.tensor(Q2, device="cuda"))
         rng = np.random.default_rng(5)
-        # call 1: FP32, r = 4
-        Y1 = torch.tensor(rng.standard_normal((450, 4)).astype(np.float32), device="cuda")
-        st, W1 = _noalloc(xm, C, q1, xm.XM_FP32_BULK, Y1)
-        assert st == xm.XM_OK
-        ref1 = xm.xm_qy(q1, Y1, xm.XM_FP32_BULK)
-        b1 = np.abs(Q1) @ np.abs(Y1.cpu().numpy().astype(np.float64))
-        assert np.all(np.abs(W1.cpu().numpy() - ref1.cpu().numpy()) <= 2 * (EPS32 + gamma(452, EPS32)) * b1)
-        # call 2: FP64, r = 3, on a smaller Q
-        Y2 = torch.tensor(rng.standard_normal((183, 3)), device="cuda")
-        st, W2 = _noalloc(xm, C, q2, xm.XM_FP64, Y2)
-        assert st == xm.XM_OK
-        ref2 = xm.xm_qy(q2, Y2, xm.XM_FP64)
-        b2 = np.abs(Q2) @ np.abs(Y2.cpu().numpy())
-        assert np.all(np.abs(W2.cpu().numpy() - ref2.cpu().numpy()) <= 2 * gamma(185, EPS64) * b2)
+        calls = [(q1, Q1, xm.XM_FP32_BULK, 4), (q2, Q2, xm.XM_FP64, 3), (q1, Q1, xm.XM_FP32_BULK, 6),
+                 (q2, Q2, xm.XM_FP32_BULK, 1), (q1, Q1, xm.XM_BF16Q_BULK, 4), (q2, Q2, xm.XM_FP64, 8),
+                 (q1, Q1, xm.XM_FP64, 1), (q2, Q2, xm.XM_BF16Q_BULK, 8)]
+        for q, Qd, prec, r in calls:
+            n = Qd.shape[0]
+            if prec == xm.XM_FP64:
+                Y = torch.tensor(rng.standard_normal((n, r)), device="cuda")
+                eps = gamma(n + 2, EPS64)
+            else:
+                Y = torch.tensor(rng.standard_normal((n, r)).astype(np.float32), device="cuda")
+                eps = (EPS_BF16 if prec == xm.XM_BF16Q_BULK else EPS32) + gamma(n + 2, EPS32)
+            st, W = _noalloc(xm, C, q, prec, Y)
+            assert st == xm.XM_OK
+            ref = xm.xm_qy(q, Y, prec)
+            b = np.abs(Qd) @ np.abs(Y.cpu().numpy().astype(np.float64))
+            # both results are within the a-priori bound of the exact product, so of each other
+            # within twice that bound
+            assert np.all(np.abs(W.cpu().numpy() - ref.cpu().numpy()) <= 2 * eps * b), (prec, r)
         torch.cuda.synchronize()
         q1.free(); q2.free()
     finally:
