@@ -623,20 +623,52 @@ def xm2_keep(res2, drop_frac=0.1):
     return keep
 
 
-def solve_xm2(N, M, cam, lmk, ukp, w, drop_frac=0.1, mu=0.0, **kw):
-    """XM^2 (running twice): solve, recover t and p (Eq. 7), drop the drop_frac measurements with
-    the largest residual terms, solve again on the rest.  Returns (first, second, keep, t, p)."""
+@dataclass
+class XM2Result:
+    first: "SolveResult"
+    second: "SolveResult"       # the solve on the kept measurements of the anchor's component
+    keep: np.ndarray            # bool[E]: measurement used by the second solve
+    cams: np.ndarray            # bool[N]: camera in the anchor's component of the kept view graph
+    R: np.ndarray               # N x 3 x 3 (zero for excluded cameras)
+    s: np.ndarray               # N (zero for excluded cameras)
+    t: np.ndarray               # N x 3 (zero for excluded cameras)
+    p: np.ndarray               # M x 3 (zero for landmarks outside the component)
+
+
+def solve_xm2(N, M, cam, lmk, ukp, w, drop_frac=0.1, mu=0.0, **kw) -> XM2Result:
+    """XM^2 (running twice, Sec. 5): solve, recover t and p (Eq. 7), drop the drop_frac
+    measurements with the largest residual terms, solve again on the rest.  Dropping can split
+    the view graph (a camera whose every measurement was dropped: without App. D's regulariser
+    even the anchor, whose unit-scale terms can be the largest); the second solve then runs on
+    the connected component with the most cameras (ties: the one holding the lowest camera
+    index), anchored at its lowest-index camera (R = I, s = 1, t = 0 there), and reports the
+    cameras and landmarks outside it with zero rotation, scale, translation and position."""
     cam, lmk, ukp, w = _validated(N, M, cam, lmk, ukp, w)
     Q = build_Q_schur(N, M, cam, lmk, ukp, w)
     first = solve(Q, mu=mu, **kw)
     U3 = np.concatenate([first.s[i] * first.R[i] for i in range(N)], axis=1)
     t, p = recover_tp(N, M, cam, lmk, ukp, w, U3)
     keep = xm2_keep(observation_residuals(cam, lmk, ukp, w, first.R, first.s, t, p), drop_frac)
-    Q2 = build_Q_schur(N, M, cam[keep], lmk[keep], ukp[keep], w[keep])
-    second = solve(Q2, mu=mu, **kw)
-    U3 = np.concatenate([second.s[i] * second.R[i] for i in range(N)], axis=1)
-    t2, p2 = recover_tp(N, M, cam[keep], lmk[keep], ukp[keep], w[keep], U3)
-    return first, second, keep, t2, p2
+    # components of the camera-landmark graph of the kept measurements (vertices: N cameras, then
+    # M landmarks)
+    A = sp.csr_matrix((np.ones(int(keep.sum())), (cam[keep], N + lmk[keep])), shape=(N + M, N + M))
+    _, lab = sp.csgraph.connected_components(A, directed=False)
+    size = np.bincount(lab[:N])
+    best = lab[:N][np.argmax(size[lab[:N]] == size.max())]   # first camera of a largest component
+    cams = lab[:N] == best
+    use = keep & cams[cam]
+    cidx = np.nonzero(cams)[0]
+    cmap = -np.ones(N, np.int64); cmap[cidx] = np.arange(cidx.size)
+    lidx = np.unique(lmk[use])
+    lmap = -np.ones(M, np.int64); lmap[lidx] = np.arange(lidx.size)
+    N2, M2 = int(cidx.size), int(lidx.size)
+    c2, l2, u2, w2 = cmap[cam[use]], lmap[lmk[use]], ukp[use], w[use]
+    second = solve(build_Q_schur(N2, M2, c2, l2, u2, w2), mu=mu, **kw)
+    U3 = np.concatenate([second.s[i] * second.R[i] for i in range(N2)], axis=1)
+    t2, p2 = recover_tp(N2, M2, c2, l2, u2, w2, U3)
+    R = np.zeros((N, 3, 3)); s = np.zeros(N); tt = np.zeros((N, 3)); pp = np.zeros((M, 3))
+    R[cidx], s[cidx], tt[cidx], pp[lidx] = second.R, second.s, t2, p2
+    return XM2Result(first, second, use, cams, R, s, tt, pp)
 
 
 # ======================================================================================
