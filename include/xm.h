@@ -215,6 +215,33 @@ xm_status xm_qy(xm_ctx* ctx, const xm_qmat* q, int prec, int r, const void* Y, v
  * context stream. */
 xm_status xm_qy_noalloc(xm_ctx* ctx, const xm_qmat* q, int prec, int r, const void* Y, void* W);
 
+/* ---- factored Q operator (App. A's elimination kept in product form; Prop. 1) -------------
+ * Q Y without forming Q: for observation e = (i, k) with a_e = u_e^T Y_i, landmark means
+ * m_k = sum_{e in k} w_e a_e / d_k (d_k = sum_{e in k} w_e), camera sums b_j = sum_{e in j}
+ * w_e (a_e - m_k) (= Bbar^T Y), the optimal translations t = -Sbar^{-1} bbar (t_0 = 0) and
+ * their landmark means tb_k,
+ *   (Q Y)_i = sum_{e in i} w_e u_e (a_e - m_k + t_i - tb_k),
+ * the least-squares residual of Eq. 3 for the columns of Y weighted by the keypoints (the
+ * envelope theorem applied to Prop. 1's minimisation over t and p).  Per product four passes
+ * over the observations and one packed symmetric product with -Sbar^{-1} ((N-1)^2 entries,
+ * against (3N)^2 for Q); FP64 throughout, deterministic.
+ * xm_qfact_create: observations as for xm_build_Q (device pointers, copied); sets up the
+ * landmark- and camera-major copies of (u, w), 1 / d_k and the FP64 tiles of -Sbar^{-1} (Cholesky
+ * factor, triangular inverse and product by the build's FP64-accurate digit-split tensor-core
+ * arithmetic).  XM_EINVAL on bad observations, XM_EDISCONNECTED when Sbar is singular.  The
+ * handle owns its device memory until xm_qfact_free.
+ * xm_qy_factored: W = Q Y for an n x r row-major FP64 Y (1 <= r <= XM_MAX_RANK); W (n x r) is
+ * overwritten.  Asynchronous on the context stream; one product at a time per handle (it keeps
+ * its intermediate vectors).
+ * xm_qfact_info: sizes, resident device bytes and set-up seconds (any pointer may be NULL). */
+typedef struct xm_qfact xm_qfact;
+xm_status xm_qfact_create(xm_ctx* ctx, int N, int M, int64_t E, const int32_t* cam,
+                          const int32_t* lmk, const double* ukp, const double* w, xm_qfact** out);
+xm_status xm_qy_factored(xm_ctx* ctx, const xm_qfact* f, int r, const double* Y, double* W);
+xm_status xm_qfact_info(const xm_qfact* f, int* N, int* M, int64_t* E, size_t* bytes,
+                        double* t_setup_s);
+xm_status xm_qfact_free(xm_ctx* ctx, xm_qfact* f);
+
 /* Device time of one sweep, measured with CUDA events on the context stream after three
  * warm-up sweeps (Y filled with a fixed pattern, W zeroed before each sweep outside the timed
  * interval).  ms_mean / ms_min may be NULL.  Synchronous. */
@@ -307,9 +334,15 @@ xm_status xm_recover_tp(xm_ctx* ctx, int N, int M, int64_t E, const int32_t* cam
                         double* t_out, double* p_out, double* res2_out);
 /* xm_solve_xm2: XM^2 (running twice): build Q, solve, recover (t, p), drop the floor(drop_frac E)
  * measurements with the largest Eq. 3 terms (ties by the lower index), then build and solve
- * again on the rest.  Outputs (device) of the second solve: R_out, s_out, t_out, p_out (may be
- * NULL); keep_out (E bytes, may be NULL): 1 for a kept measurement.  info_first / info_second
- * (host, may be NULL).  Returns the second solve's status. */
+ * again on the rest.  The paper does not say what happens when the cut splits the view graph
+ * (a camera, even the anchor, whose every measurement was dropped): the second solve then runs
+ * on the connected component with the most cameras (ties: the one holding the lowest camera
+ * index), re-indexed and anchored at its lowest-index camera (R = I, s = 1, t = 0 there);
+ * cameras outside it get R = 0 and s = 0 (a solved camera always has s > 0), t = 0, and
+ * landmarks outside it p = 0.  Outputs (device) of the second solve: R_out, s_out, t_out,
+ * p_out (may be NULL); keep_out (E bytes, may be NULL): 1 for a measurement used by the second
+ * solve.  info_first / info_second (host, may be NULL).  Returns the second solve's status;
+ * XM_EDISCONNECTED only if the full view graph is disconnected. */
 xm_status xm_solve_xm2(xm_ctx* ctx, int N, int M, int64_t E, const int32_t* cam, const int32_t* lmk,
                        const double* ukp, const double* w, const xm_opts* opts, double drop_frac,
                        double* R_out, double* s_out, double* t_out, double* p_out,

@@ -301,6 +301,28 @@ struct DevBuf {
 };
 }  // namespace
 
+// XM_EDISCONNECTED unless every camera and every observed landmark lie in one component of the
+// camera-landmark view graph (App. A lemma: Q_tp has rank N + M - 1 exactly then).
+xm_status check_connected(xm_ctx* ctx, int N, int M, int64_t E, const int32_t* cam, const int32_t* lmk) {
+  cudaStream_t st = ctx->stream;
+  const int threads = 256;
+  DevBuf parent, flag;
+  XM_CUDA_TRY(cudaMalloc(&parent.p, sizeof(int) * (size_t)(N + M)));
+  XM_CUDA_TRY(cudaMalloc(&flag.p, sizeof(int)));
+  XM_CUDA_TRY(cudaMemsetAsync(flag.p, 0, sizeof(int), st));
+  k_uf_init<<<grid_for(N + M, threads, ctx->num_sms), threads, 0, st>>>(parent.as<int>(), N + M);
+  if (E > 0)
+    k_uf_union<<<grid_for(E, threads, ctx->num_sms), threads, 0, st>>>(E, N, cam, lmk, parent.as<int>());
+  k_uf_check<<<grid_for(E + N, threads, ctx->num_sms), threads, 0, st>>>(E, N, cam, lmk, parent.as<int>(),
+                                                                         flag.as<int>());
+  XM_CUDA_TRY(cudaGetLastError());
+  int h = 0;
+  XM_CUDA_TRY(cudaMemcpyAsync(&h, flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  XM_CUDA_TRY(cudaStreamSynchronize(st));
+  if (h) return set_error(XM_EDISCONNECTED, "view graph is not connected (N=%d, M=%d)", N, M);
+  return XM_OK;
+}
+
 xm_status build_Q(xm_ctx* ctx, int N, int M, int64_t E, const int32_t* cam, const int32_t* lmk,
                   const double* ukp, const double* w, unsigned mask, DeviceQ& out,
                   double* t_build) {
@@ -317,23 +339,7 @@ xm_status build_Q(xm_ctx* ctx, int N, int M, int64_t E, const int32_t* cam, cons
   XM_TRY(check_device_error(ctx, "observation validation"));
 
   // ---- connectivity (App. A lemma: rank N + M - 1 iff the view graph is connected)
-  {
-    DevBuf parent, flag;
-    XM_CUDA_TRY(cudaMalloc(&parent.p, sizeof(int) * (size_t)(N + M)));
-    XM_CUDA_TRY(cudaMalloc(&flag.p, sizeof(int)));
-    XM_CUDA_TRY(cudaMemsetAsync(flag.p, 0, sizeof(int), st));
-    k_uf_init<<<grid_for(N + M, threads, ctx->num_sms), threads, 0, st>>>(parent.as<int>(), N + M);
-    if (E > 0)
-      k_uf_union<<<grid_for(E, threads, ctx->num_sms), threads, 0, st>>>(E, N, cam, lmk,
-                                                                          parent.as<int>());
-    k_uf_check<<<grid_for(E + N, threads, ctx->num_sms), threads, 0, st>>>(
-        E, N, cam, lmk, parent.as<int>(), flag.as<int>());
-    XM_CUDA_TRY(cudaGetLastError());
-    int h = 0;
-    XM_CUDA_TRY(cudaMemcpyAsync(&h, flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-    XM_CUDA_TRY(cudaStreamSynchronize(st));
-    if (h) return set_error(XM_EDISCONNECTED, "view graph is not connected (N=%d, M=%d)", N, M);
-  }
+  XM_TRY(check_connected(ctx, N, M, E, cam, lmk));
 
   DevBuf P, B, S, d, cnt, off, bsum, cursor, idx;
   XM_CUDA_TRY(cudaMalloc(&P.p, sizeof(double) * (size_t)n * n));

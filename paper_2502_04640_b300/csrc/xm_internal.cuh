@@ -128,6 +128,8 @@ xm_status split_potrf(xm_ctx* ctx, void* cublas, void* cusolver, double* A, int 
 // Index and value checks of the observation arrays (synchronous; XM_EINVAL on a bad entry).
 xm_status validate_obs(xm_ctx* ctx, int N, int M, int64_t E, const int32_t* cam, const int32_t* lmk,
                        const double* ukp, const double* w);
+// XM_EDISCONNECTED unless the camera-landmark view graph is connected (App. A lemma).
+xm_status check_connected(xm_ctx* ctx, int N, int M, int64_t E, const int32_t* cam, const int32_t* lmk);
 // Observations grouped by key (ascending observation index within a group); off (K+1), idx (E)
 // are allocated by the caller.
 xm_status obs_csr(xm_ctx* ctx, int64_t E, const int32_t* key, int K, int64_t* off, int64_t* idx);

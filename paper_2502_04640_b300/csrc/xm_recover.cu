@@ -7,7 +7,10 @@
 // landmark mean of a.  All sums run in observation order (deterministic), in FP64.
 //
 // XM^2 drops the tenth of the measurements whose Eq. 3 terms w_e ||a_e + t_i - p_k||^2 are the
-// largest (ties broken by the lower index) and solves again on the rest.
+// largest (ties broken by the lower index) and solves again on the rest.  When the cut splits the
+// view graph, the second solve runs on the component with the most cameras (ties: the one with
+// the lowest camera index), anchored at its lowest-index camera; cameras and landmarks outside
+// it are reported with zero rotation, scale, translation and position.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -144,6 +147,45 @@ __global__ void k_gather_obs(int64_t Ek, const int64_t* __restrict__ idx, const 
   }
 }
 
+// dst[map[j] * width + c] = src[j * width + c]: results of a re-indexed sub-problem written
+// back to the rows of the full problem (the caller zeroes the rows nothing maps to)
+__global__ void k_scatter_rows(int rows, int width, const int32_t* __restrict__ map,
+                               const double* __restrict__ src, double* __restrict__ dst) {
+  const int64_t total = (int64_t)rows * width;
+  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total;
+       x += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = x / width;
+    dst[(int64_t)map[j] * width + (x - j * width)] = src[x];
+  }
+}
+
+// Connected components of the camera-landmark graph of the kept measurements (vertices: N
+// cameras, then M landmarks), by union-find on the host.  in_comp[i] = 1 for the cameras of the
+// component with the most cameras; ties go to the component of the lowest camera index.
+static void largest_component(int N, int M, int64_t E, const std::vector<int32_t>& cam,
+                              const std::vector<int32_t>& lmk, const std::vector<unsigned char>& keep,
+                              std::vector<unsigned char>& in_comp) {
+  std::vector<int> parent((size_t)N + M);
+  std::iota(parent.begin(), parent.end(), 0);
+  auto find = [&](int v) {
+    while (parent[v] != v) { parent[v] = parent[parent[v]]; v = parent[v]; }
+    return v;
+  };
+  for (int64_t e = 0; e < E; ++e) {
+    if (!keep[e]) continue;
+    const int a = find(cam[e]), b = find(N + lmk[e]);
+    if (a != b) parent[std::max(a, b)] = std::min(a, b);
+  }
+  std::vector<int> count((size_t)N + M, 0);
+  for (int i = 0; i < N; ++i) ++count[find(i)];
+  const int most = *std::max_element(count.begin(), count.end());
+  int best = -1;
+  for (int i = 0; i < N && best < 0; ++i)
+    if (count[find(i)] == most) best = find(i);
+  in_comp.assign(N, 0);
+  for (int i = 0; i < N; ++i) in_comp[i] = find(i) == best;
+}
+
 static xm_status recover_impl(xm_ctx* c, int N, int M, int64_t E, const int32_t* cam, const int32_t* lmk,
                               const double* ukp, const double* w, const double* R, const double* s,
                               double* t_out, double* p_out, double* res2_out) {
@@ -228,12 +270,30 @@ extern "C" xm_status xm_solve_xm2(xm_ctx* c, int N, int M, int64_t E, const int3
     std::nth_element(order.begin(), order.begin() + (k - 1), order.end(), before);
     for (int64_t j = 0; j < k; ++j) keep[order[j]] = 0;
   }
-  if (keep_out) XM_CUDA_TRY(cudaMemcpy(keep_out, keep.data(), (size_t)E, cudaMemcpyHostToDevice));
+  // ---- the kept view graph may have split: solve on its largest component
+  std::vector<int32_t> hc(E), hl(E);
+  XM_CUDA_TRY(cudaMemcpy(hc.data(), cam, sizeof(int32_t) * (size_t)E, cudaMemcpyDeviceToHost));
+  XM_CUDA_TRY(cudaMemcpy(hl.data(), lmk, sizeof(int32_t) * (size_t)E, cudaMemcpyDeviceToHost));
+  std::vector<unsigned char> in_comp;
+  largest_component(N, M, E, hc, hl, keep, in_comp);
+  std::vector<int32_t> cmap(N, -1), cidx, lmap(M, -1), lidx;
+  for (int i = 0; i < N; ++i)
+    if (in_comp[i]) { cmap[i] = (int32_t)cidx.size(); cidx.push_back(i); }
   std::vector<int64_t> kept;
   kept.reserve(E - k);
-  for (int64_t e = 0; e < E; ++e) if (keep[e]) kept.push_back(e);
+  for (int64_t e = 0; e < E; ++e) {
+    keep[e] = keep[e] && in_comp[hc[e]];
+    if (!keep[e]) continue;
+    kept.push_back(e);
+    if (lmap[hl[e]] < 0) lmap[hl[e]] = 0;
+  }
+  for (int j = 0; j < M; ++j)
+    if (lmap[j] >= 0) { lmap[j] = (int32_t)lidx.size(); lidx.push_back(j); }
+  const bool split = (int)cidx.size() < N;
+  const int N2 = (int)cidx.size(), M2 = split ? (int)lidx.size() : M;
+  if (keep_out) XM_CUDA_TRY(cudaMemcpy(keep_out, keep.data(), (size_t)E, cudaMemcpyHostToDevice));
   const int64_t Ek = (int64_t)kept.size();
-  // ---- second solve on the kept measurements
+  // ---- second solve on the kept measurements (re-indexed when the graph split)
   Buf idx, cam2, lmk2, ukp2, w2;
   XM_CUDA_TRY(cudaMalloc(&idx.p, sizeof(int64_t) * (size_t)std::max<int64_t>(Ek, 1)));
   XM_CUDA_TRY(cudaMalloc(&cam2.p, sizeof(int32_t) * (size_t)std::max<int64_t>(Ek, 1)));
@@ -245,19 +305,61 @@ extern "C" xm_status xm_solve_xm2(xm_ctx* c, int N, int M, int64_t E, const int3
       Ek, idx.as<int64_t>(), cam, lmk, ukp, w, cam2.as<int32_t>(), lmk2.as<int32_t>(), ukp2.as<double>(),
       w2.as<double>());
   XM_CUDA_TRY(cudaGetLastError());
+  Buf dcidx, dlidx, R2, s2b, t2, p2;
+  if (split) {
+    std::vector<int32_t> hc2(Ek), hl2(Ek);
+    for (int64_t j = 0; j < Ek; ++j) { hc2[j] = cmap[hc[kept[j]]]; hl2[j] = lmap[hl[kept[j]]]; }
+    XM_CUDA_TRY(cudaMemcpy(cam2.p, hc2.data(), sizeof(int32_t) * (size_t)Ek, cudaMemcpyHostToDevice));
+    XM_CUDA_TRY(cudaMemcpy(lmk2.p, hl2.data(), sizeof(int32_t) * (size_t)Ek, cudaMemcpyHostToDevice));
+    XM_CUDA_TRY(cudaMalloc(&dcidx.p, sizeof(int32_t) * (size_t)N2));
+    XM_CUDA_TRY(cudaMalloc(&dlidx.p, sizeof(int32_t) * (size_t)std::max(M2, 1)));
+    XM_CUDA_TRY(cudaMemcpy(dcidx.p, cidx.data(), sizeof(int32_t) * (size_t)N2, cudaMemcpyHostToDevice));
+    XM_CUDA_TRY(cudaMemcpy(dlidx.p, lidx.data(), sizeof(int32_t) * (size_t)M2, cudaMemcpyHostToDevice));
+    XM_CUDA_TRY(cudaMalloc(&R2.p, sizeof(double) * 9 * (size_t)N2));
+    XM_CUDA_TRY(cudaMalloc(&s2b.p, sizeof(double) * (size_t)N2));
+    XM_CUDA_TRY(cudaMalloc(&t2.p, sizeof(double) * 3 * (size_t)N2));
+    XM_CUDA_TRY(cudaMalloc(&p2.p, sizeof(double) * 3 * (size_t)std::max(M2, 1)));
+  }
+  double* Rs = split ? R2.as<double>() : R_out;
+  double* ss = split ? s2b.as<double>() : s_out;
   xm_status s2;
   {
     DeviceQ q;
-    xm_status sb = build_Q(c, N, M, Ek, cam2.as<int32_t>(), lmk2.as<int32_t>(), ukp2.as<double>(), w2.as<double>(),
-                           mask, q, nullptr);
+    xm_status sb = build_Q(c, N2, M2, Ek, cam2.as<int32_t>(), lmk2.as<int32_t>(), ukp2.as<double>(),
+                           w2.as<double>(), mask, q, nullptr);
     if (sb != XM_OK) { free_tiles(q); return sb; }
-    s2 = solve_impl(c, q, *opts, 0, nullptr, nullptr, R_out, s_out, info_second, false, nullptr, nullptr);
+    s2 = solve_impl(c, q, *opts, 0, nullptr, nullptr, Rs, ss, info_second, false, nullptr, nullptr);
     free_tiles(q);
     if (s2 != XM_OK && s2 != XM_ENOTCERT && s2 != XM_ENOCONV) return s2;
   }
-  if (t_out || p_out)
-    XM_TRY(recover_impl(c, N, M, Ek, cam2.as<int32_t>(), lmk2.as<int32_t>(), ukp2.as<double>(), w2.as<double>(),
-                        R_out, s_out, t_out, p_out, nullptr));
+  if (!split) {
+    if (t_out || p_out)
+      XM_TRY(recover_impl(c, N, M, Ek, cam2.as<int32_t>(), lmk2.as<int32_t>(), ukp2.as<double>(),
+                          w2.as<double>(), R_out, s_out, t_out, p_out, nullptr));
+  } else {
+    const bool want_tp = t_out || p_out;
+    if (want_tp)
+      XM_TRY(recover_impl(c, N2, M2, Ek, cam2.as<int32_t>(), lmk2.as<int32_t>(), ukp2.as<double>(),
+                          w2.as<double>(), Rs, ss, t2.as<double>(), p2.as<double>(), nullptr));
+    // rows outside the solved component: zero rotation, scale, translation and position
+    XM_CUDA_TRY(cudaMemsetAsync(R_out, 0, sizeof(double) * 9 * (size_t)N, st));
+    XM_CUDA_TRY(cudaMemsetAsync(s_out, 0, sizeof(double) * (size_t)N, st));
+    const int gsc = grid_cap((size_t)9 * N2, 256, c->num_sms);
+    k_scatter_rows<<<gsc, 256, 0, st>>>(N2, 9, dcidx.as<int32_t>(), Rs, R_out);
+    k_scatter_rows<<<gsc, 256, 0, st>>>(N2, 1, dcidx.as<int32_t>(), ss, s_out);
+    if (t_out) {
+      XM_CUDA_TRY(cudaMemsetAsync(t_out, 0, sizeof(double) * 3 * (size_t)N, st));
+      k_scatter_rows<<<gsc, 256, 0, st>>>(N2, 3, dcidx.as<int32_t>(), t2.as<double>(), t_out);
+    }
+    if (p_out) {
+      XM_CUDA_TRY(cudaMemsetAsync(p_out, 0, sizeof(double) * 3 * (size_t)M, st));
+      if (M2 > 0)
+        k_scatter_rows<<<grid_cap((size_t)3 * M2, 256, c->num_sms), 256, 0, st>>>(
+            M2, 3, dlidx.as<int32_t>(), p2.as<double>(), p_out);
+    }
+    XM_CUDA_TRY(cudaGetLastError());
+    XM_CUDA_TRY(cudaStreamSynchronize(st));
+  }
   if (s2 != XM_OK) return set_error(s2, "xm_solve_xm2: the second solve ended with status %d", (int)s2);
   return XM_OK;
 }

@@ -53,7 +53,8 @@ def test_noise_free_recovery_of_translations_and_landmarks(C):
 def test_xm2_matches_oracle(C):
     from paper_2502_04640_b300 import xm
     sc = scenes.random_scene(15, 300, noise=0.01, outlier_frac=0.05, seed=82, center_sigma=3.0)
-    first, second, keep_ref, t_ref, p_ref = O.solve_xm2(sc.N, sc.M, sc.cam, sc.lmk, sc.ukp, sc.w)
+    x = O.solve_xm2(sc.N, sc.M, sc.cam, sc.lmk, sc.ukp, sc.w)
+    first, second, keep_ref, t_ref, p_ref = x.first, x.second, x.keep, x.t, x.p
     out = xm.xm_solve_xm2(C, sc.N, sc.M, *xm.scene_tensors(sc), xm.xm_default_opts(), 0.1,
                           allow_notcert=False)
     keep = out["keep"].cpu().numpy()
@@ -70,3 +71,37 @@ def test_xm2_matches_oracle(C):
     scale = max(np.abs(t_ref).max(), np.abs(p_ref).max())
     assert np.abs(out["t"].cpu().numpy() - t_ref).max() <= 1e-4 * scale
     assert np.abs(out["p"].cpu().numpy() - p_ref).max() <= 1e-4 * scale
+
+
+def test_xm2_on_a_split_view_graph_matches_oracle(C):
+    """The cut drops every measurement of a camera with planted outliers and of the anchor (the
+    unregularised optimum shrinks the other scales): both sides solve the largest remaining
+    component, anchored at camera 1, and report cameras 0 and 7 with zero scale and rotation."""
+    from paper_2502_04640_b300 import xm
+    sc = scenes.random_scene(40, 500, noise=0.01, outlier_frac=0.0, seed=83, center_sigma=3.0)
+    rng = np.random.default_rng(83)
+    ukp = sc.ukp.copy()
+    ukp[sc.cam == 7] = rng.uniform(-100.0, 100.0, size=(int((sc.cam == 7).sum()), 3))
+    x = O.solve_xm2(sc.N, sc.M, sc.cam, sc.lmk, ukp, sc.w)
+    assert list(np.nonzero(~x.cams)[0]) == [0, 7]
+    cam, lmk, _, w = xm.scene_tensors(sc)
+    out = xm.xm_solve_xm2(C, sc.N, sc.M, cam, lmk, torch.tensor(ukp, device="cuda"), w,
+                          xm.xm_default_opts(), 0.1, allow_notcert=False)
+    s, R = out["s"].cpu().numpy(), out["R"].cpu().numpy()
+    assert out["status"] == xm.XM_OK and out["info_second"]["certified"] == 1
+    assert np.array_equal(s > 0, x.cams) and not R[[0, 7]].any()
+    keep = out["keep"].cpu().numpy()
+    if not np.array_equal(keep, x.keep):
+        # the two first solves agree to ~1e-6, so the cut may differ at its threshold only
+        U3 = np.concatenate([x.first.s[i] * x.first.R[i] for i in range(sc.N)], axis=1)
+        t1, p1 = O.recover_tp(sc.N, sc.M, sc.cam, sc.lmk, ukp, sc.w, U3)
+        r2 = O.observation_residuals(sc.cam, sc.lmk, ukp, sc.w, x.first.R, x.first.s, t1, p1)
+        thr = np.sort(r2)[::-1][int(0.1 * sc.E) - 1]
+        diff = np.nonzero(keep != x.keep)[0]
+        assert np.all(np.abs(r2[diff] - thr) <= 1e-4 * thr), r2[diff] / thr
+        return
+    assert abs(out["info_second"]["f"] - x.second.f) <= 1e-6 * (1 + abs(x.second.f))
+    assert np.abs(R - x.R).max() <= 1e-5 and np.abs(s - x.s).max() <= 1e-5 * x.s.max()
+    scale = max(np.abs(x.t).max(), np.abs(x.p).max())
+    assert np.abs(out["t"].cpu().numpy() - x.t).max() <= 1e-4 * scale
+    assert np.abs(out["p"].cpu().numpy() - x.p).max() <= 1e-4 * scale
