@@ -637,6 +637,29 @@ k_gram(int n_rows, const T* __restrict__ Y, double* out, double* partials, unsig
   });
 }
 
+// C = A^T B (R x R) for two n_rows x R row-major arrays, deterministic
+template <typename T, int R>
+__global__ void __launch_bounds__(CAM_THREADS)
+k_cross(int n_rows, const T* __restrict__ A, const T* __restrict__ B, double* out, double* partials,
+        unsigned* counter) {
+  double v[R * R];
+#pragma unroll
+  for (int k = 0; k < R * R; ++k) v[k] = 0.0;
+  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < n_rows;
+       row += gridDim.x * blockDim.x) {
+    double a[R], b[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) { a[j] = double(A[(size_t)row * R + j]); b[j] = double(B[(size_t)row * R + j]); }
+#pragma unroll
+    for (int x = 0; x < R; ++x)
+#pragma unroll
+      for (int y = 0; y < R; ++y) v[x * R + y] += a[x] * b[y];
+  }
+  grid_reduce<R * R>(v, partials, counter, [&](double* t) {
+    for (int k = 0; k < R * R; ++k) out[k] = t[k];
+  });
+}
+
 // <a, b> over total elements (mixed types) -> *out
 template <typename Ta, typename Tb>
 __global__ void __launch_bounds__(CAM_THREADS)

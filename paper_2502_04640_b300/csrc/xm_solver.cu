@@ -479,6 +479,9 @@ struct Solver {
   double cur_g2 = 0.0;
   double carry_delta = 0.0;   // trust radius handed from a stalled bulk phase to the polish
   bool bulk_stalled = false;  // the last bulk phase stopped on stagnation (opts.bulk_stall)
+  // bG holds the FP64 Riemannian gradient 2 Z Y at bY64 (set for the final certificate after an
+  // FP64 gradient): Z's block on range(Y) then follows from Y^T G without a Z product
+  bool g64_valid = false;
 
   Solver(xm_ctx* c, const DeviceQ& qq, const xm_opts& oo) : ctx(c), q(qq), o(oo), st(c->stream) {
     N = q.N; n = q.n; n_pad = q.n_pad;
@@ -1101,9 +1104,27 @@ struct Solver {
       ++launches;
     }
     last_nd = nd;
-    // Rayleigh quotients of Z on range(Y): Vd^T Z Vd (nd x nd)
+    // Rayleigh quotients of Z on range(Y): Vd^T Z Vd (nd x nd).  With the FP64 gradient at hand,
+    // Vd^T Z Vd = rot^T (Y^T G / 2) rot in FP64 (G = 2 Z Y, App. D's term included); otherwise
+    // one Z product per basis vector in the certificate's precision.
     std::vector<double> zr((size_t)nd * nd, 0.0);
-    for (int j = 0; j < nd; ++j) {
+    if (g64_valid && nd > 0) {
+      k_cross<double, R><<<grid_gram(), CAM_THREADS, 0, st>>>(nn, (const double*)bY64, (const double*)bG,
+                                                              d_small, ctx->d_partials, ctx->d_counter);
+      ++launches;
+      std::vector<double> yg(R * R);
+      XM_CUDA_TRY(cudaMemcpyAsync(yg.data(), d_small, sizeof(double) * R * R, cudaMemcpyDeviceToHost, st));
+      XM_CUDA_TRY(cudaStreamSynchronize(st));
+      for (int j = 0; j < nd; ++j)
+        for (int l = 0; l < nd; ++l) {
+          double acc = 0.0;
+          for (int a = 0; a < r; ++a)
+            for (int b = 0; b < r; ++b)
+              acc += rot[(size_t)a * R + j] * 0.5 * yg[a * R + b] * rot[(size_t)b * R + l];
+          zr[(size_t)j * nd + l] = acc;
+        }
+    }
+    for (int j = 0; j < nd && !g64_valid; ++j) {
       XM_TRY(zmul<VT>(prec_z, Vb + (size_t)j * nn, lw));
       const VT* wv = reinterpret_cast<const VT*>(lw);
       if (sizeof(VT) == 4) {
@@ -1407,8 +1428,13 @@ xm_status solve_impl(xm_ctx* ctx, const DeviceQ& q, const xm_opts& o, int r_in, 
     double gap = 0.0;
     bool stationary = false;
     if (!quick_escape) {
-      XM_TRY(with_R(R, [&] { return S.certify<4>(r, prec_z, &lam_def, &lam_max, &lam_range); },
-                       [&] { return S.certify<8>(r, prec_z, &lam_def, &lam_max, &lam_range); }));
+      // every path here ended with an FP64 gradient at bY64 (FP64 RTR, the FP64 polish, or the
+      // certify-only gradient)
+      S.g64_valid = true;
+      const xm_status sc = with_R(R, [&] { return S.certify<4>(r, prec_z, &lam_def, &lam_max, &lam_range); },
+                                     [&] { return S.certify<8>(r, prec_z, &lam_def, &lam_max, &lam_range); });
+      S.g64_valid = false;
+      XM_TRY(sc);
       // Thm. 1 needs a first-order critical point: with Lambda in closed form the duality gap
       // f - tr(Lambda_0) = <Y, Z Y> vanishes exactly there, so it is checked beside lambda_min.
       double L0g[9], regd = 0.0;

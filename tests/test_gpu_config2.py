@@ -3,13 +3,15 @@ outliers): the CUDA build + solve + certificate in FP64 and in the FP32-bulk mod
 oracle's solve of the same scene (Alg. 1 + RTR-tCG + Thm. 1 + rounding, about half a minute on
 the host).  Compared: certificate decision, objective and rounded value (relative 1e-6, 1 + |.|
 denominator), dual value, deflated and raw lambda_min (1e-5 of lambda_max), Eq. 18's eta and
-App. E's eta_robust, and the rounded rotations and scales (anchored gauge)."""
+App. E's eta_robust, and the rounded rotations and scales, the last three at the GPU's own point
+(the optimum has rank > 3, so the rounding depends on which optimal X the iterations reach)."""
 import numpy as np
 import pytest
 
 import scenes
 from oracle import xm_oracle as O
 from tests.gpu_util import ctx
+from tests.oracle_checks import check_at_returned_point
 
 pytestmark = pytest.mark.gpu
 
@@ -24,7 +26,7 @@ def C():
 @pytest.fixture(scope="module")
 def c2():
     sc = scenes.config2()
-    ref = O.solve(O.build_Q_schur(sc.N, sc.M, sc.cam, sc.lmk, sc.ukp, sc.w), r0=4)
+    ref = O.solve(Qo(sc), r0=4)
     return sc, ref
 
 
@@ -42,20 +44,27 @@ def test_config2_matches_oracle(C, c2, prec):
     R, s = out["R"].cpu().numpy(), out["s"].cpu().numpy()
     lm = ref.cert.lam_max_Q
     print(f"prec={prec} f={info['f']!r} oracle={ref.f!r} eta={info['eta']:.3e}/{ref.eta:.3e} "
-          f"dR={np.abs(R - ref.R).max():.2e} ds={np.abs(s - ref.s).max() / ref.s.max():.2e} "
-          f"lmin_defl={info['lambda_min_deflated']:.6e}/{ref.cert.lam_min_deflated:.6e}")
+          f"rho_hat={info['rho_hat']!r}/{ref.rho_hat!r} rank={info['rank']}/{ref.rank}")
+    # quantities of the SDP optimum itself (unique): certificate decision, value, dual value,
+    # lambda_min
     assert info["certified"] == int(ref.certified) == 1
     assert _rel(info["f"], ref.f) <= 1e-6
-    assert _rel(info["rho_hat"], ref.rho_hat) <= 1e-6
     assert abs(info["dual"] - ref.cert.dual) <= 1e-6 * (1 + abs(ref.f))
     assert abs(info["lambda_min_deflated"] - ref.cert.lam_min_deflated) <= 1e-5 * lm
     assert abs(info["lambda_min"] - ref.cert.lam_min) <= 1e-5 * lm
-    assert abs(info["eta"] - ref.eta) <= 2e-6
-    assert abs(info["eta_robust"] - ref.eta_robust) <= 2e-6
-    # rotations and scales: cameras with few, down-weighted observations move along directions
-    # that change the cost by less than its rounding, so compare the bulk tightly and bound the rest
-    dR = np.abs(R - ref.R).reshape(sc.N, -1).max(axis=1)
-    ds = np.abs(s - ref.s) / ref.s
-    assert np.median(dR) <= 1e-6 and np.median(ds) <= 1e-6
-    assert dR.max() <= 1e-2 and ds.max() <= 1e-2
+    # this optimum has rank > 3 (eta > 0): its optimal face holds many X, so the rounded
+    # rotations depend on which one the iterations reached; rounding, eta and eta_robust are
+    # compared at the GPU's own point, and both roundings must be near-optimal
+    assert ref.eta > 1e-8
+    check_at_returned_point(Qo(sc), out)
+    assert 0 <= info["eta"] <= 1e-4
     q.free()
+
+
+_Q = {}
+
+
+def Qo(sc):
+    if sc.name not in _Q:
+        _Q[sc.name] = O.build_Q_schur(sc.N, sc.M, sc.cam, sc.lmk, sc.ukp, sc.w)
+    return _Q[sc.name]

@@ -1,14 +1,16 @@
 """Depth-noise robustness (the paper's noise analysis, s = (1 + eps)^x per observation): the CUDA
 solver against the FP64 oracle across noise levels, from mild to eps = 5 where the paper reports
 the relaxation to break.  Compared: the certificate decision, the objective and the rounded
-value (relative 1e-6, 1 + |.| denominator), Eq. 18's eta and App. E's eta_robust, the dual value
-and the deflated lambda_min."""
+value (relative 1e-6, 1 + |.| denominator), the dual value and the deflated lambda_min; where the noise makes the
+optimum's rank exceed 3 (its optimal face is then not a single X), the rounding, eta and
+eta_robust at the GPU's own point."""
 import numpy as np
 import pytest
 
 import scenes
 from oracle import xm_oracle as O
 from tests.gpu_util import ctx
+from tests.oracle_checks import check_at_returned_point
 
 pytestmark = pytest.mark.gpu
 
@@ -29,15 +31,18 @@ def _rel(a, b):
 def test_depth_noise_solve_matches_oracle(C, eps, prec):
     from paper_2502_04640_b300 import xm
     sc = scenes.depth_noise_scenes(eps, count=1, N=30, M=600)[0]
-    ref = O.solve(O.build_Q_schur(sc.N, sc.M, sc.cam, sc.lmk, sc.ukp, sc.w), r0=4)
+    Qo = O.build_Q_schur(sc.N, sc.M, sc.cam, sc.lmk, sc.ukp, sc.w)
+    ref = O.solve(Qo, r0=4)
     q = xm.xm_build_Q(C, sc.N, sc.M, *xm.scene_tensors(sc))
     out = xm.xm_solve(q, xm.xm_default_opts(prec=prec))
     info = out["info"]
     assert info["certified"] == int(ref.certified) == 1
     assert _rel(info["f"], ref.f) <= 1e-6
-    assert _rel(info["rho_hat"], ref.rho_hat) <= 1e-6
     assert abs(info["dual"] - ref.cert.dual) <= 1e-6 * (1 + abs(ref.f))
-    assert abs(info["eta"] - ref.eta) <= 2e-6
-    assert abs(info["eta_robust"] - ref.eta_robust) <= 2e-6
     assert abs(info["lambda_min_deflated"] - ref.cert.lam_min_deflated) <= 1e-5 * ref.cert.lam_max_Q
+    if ref.eta <= 1e-9:
+        # tight: the rounded solution is unique
+        assert _rel(info["rho_hat"], ref.rho_hat) <= 1e-6
+        assert abs(info["eta"] - ref.eta) <= 2e-6
+    check_at_returned_point(Qo, out)
     q.free()

@@ -9,6 +9,7 @@ import pytest
 import scenes
 from oracle import xm_oracle as O
 from tests.gpu_util import ctx, torch
+from tests.oracle_checks import check_at_returned_point
 
 pytestmark = pytest.mark.gpu
 
@@ -57,6 +58,7 @@ def test_config1_matches_oracle(C, prec, jitter):
     assert np.abs(out["s"] - ref.s).max() <= 1e-5 * ref.s.max()
     if jitter == 0.0:
         assert info["n_escapes"] >= 1     # Alg. 1's exact start needs the escape of Thm. 2
+    check_at_returned_point(Qo, out)
     q.free()
 
 
@@ -149,9 +151,9 @@ def test_certify_entry_point_matches_oracle(C, prec):
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_uncertified_stop_reports_app_e_bound(C, prec):
     """The staircase capped at rank 3 from Alg. 1's start stops at config 1's rank-3 saddle
-    (Thm. 1 fails: lambda_min < 0): XM_ENOTCERT with the oracle's objective, dual value, raw
-    lambda_min, Eq. 18's eta and App. E's eta_robust (whose bound now carries
-    min(0, lambda_min) tr(X) < 0)."""
+    (Thm. 1 fails: lambda_min < 0): XM_ENOTCERT with the oracle's objective, dual value and raw
+    lambda_min, and at the returned point the oracle's rounding, Eq. 18's eta and App. E's
+    eta_robust (whose bound now carries min(0, lambda_min) tr(X) < 0)."""
     from paper_2502_04640_b300 import xm
     sc = scenes.config1()
     ref = O.solve(O.build_Q_schur(sc.N, sc.M, sc.cam, sc.lmk, sc.ukp, sc.w), r0=3, r_max=3)
@@ -162,10 +164,10 @@ def test_uncertified_stop_reports_app_e_bound(C, prec):
     assert _rel(info["f"], ref.f) <= 1e-6
     assert abs(info["dual"] - ref.cert.dual) <= 1e-6 * (1 + abs(ref.f))
     assert abs(info["lambda_min"] - ref.cert.lam_min) <= 1e-5 * ref.cert.lam_max_Q
-    assert _rel(info["rho_hat"], ref.rho_hat) <= 1e-6
-    assert abs(info["eta"] - ref.eta) <= 2e-6
-    assert abs(info["eta_robust"] - ref.eta_robust) <= 1e-5 * ref.eta_robust
-    assert info["eta_robust"] > info["eta"]
+    # a saddle is not an isolated point (scale-collapsed cameras move along flat directions), so
+    # the rounding and both bounds are compared at the GPU's own point
+    check_at_returned_point(O.build_Q_schur(sc.N, sc.M, sc.cam, sc.lmk, sc.ukp, sc.w), out)
+    assert info["eta_robust"] > info["eta"] > 0
     q.free()
 
 
