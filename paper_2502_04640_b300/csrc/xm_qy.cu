@@ -547,18 +547,27 @@ static xm_status launch_t(xm_ctx* ctx, const TQ* tiles, const DeviceQ& q, const 
                           const int* skip, cudaStream_t st, const CUtensorMap& ymap) {
   using C = SweepCfg<TQ, R, NW, SW>;
   using A = typename C::A;
-  static int configured_dev = -1;
-  static int nstage_cfg = 0;
-  if (configured_dev != ctx->device) {
-    const size_t fixed = C::smem_bytes(0);
-    int ns = (int)((ctx->smem_optin - fixed) / (SLAB_BYTES + 16));
-    if (ns > 12) ns = 12;
-    if (ns < 2) return set_error(XM_ECUDA, "sweep: not enough shared memory (%zu)", ctx->smem_optin);
-    XM_CUDA_TRY(cudaFuncSetAttribute(qy_packed_kernel<TQ, R, NW, SW>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)C::smem_bytes(ns)));
-    nstage_cfg = ns;
-    configured_dev = ctx->device;
+  // The shared-memory opt-in is an attribute of the kernel on each device: configure it once
+  // per device (contexts on different devices may launch from different host threads).
+  constexpr int MAX_DEVICES = 64;
+  static std::mutex mu;
+  static int nstage_dev[MAX_DEVICES] = {};
+  if (ctx->device < 0 || ctx->device >= MAX_DEVICES)
+    return set_error(XM_EINVAL, "sweep: device %d out of range", ctx->device);
+  int nstage_cfg;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    nstage_cfg = nstage_dev[ctx->device];
+    if (nstage_cfg == 0) {
+      const size_t fixed = C::smem_bytes(0);
+      int ns = (int)((ctx->smem_optin - fixed) / (SLAB_BYTES + 16));
+      if (ns > 12) ns = 12;
+      if (ns < 2) return set_error(XM_ECUDA, "sweep: not enough shared memory (%zu)", ctx->smem_optin);
+      XM_CUDA_TRY(cudaFuncSetAttribute(qy_packed_kernel<TQ, R, NW, SW>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)C::smem_bytes(ns)));
+      nstage_dev[ctx->device] = nstage_cfg = ns;
+    }
   }
   int grid = ctx->num_sms;
   if ((int64_t)grid > q.ntiles) grid = (int)q.ntiles;
