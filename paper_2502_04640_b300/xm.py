@@ -139,6 +139,13 @@ def lib() -> ctypes.CDLL:
         "xm_batch_autotune": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
         "xm_solve_batched": (ctypes.c_int, [_P, _P, ctypes.POINTER(XmOpts), _P, _P,
                                             ctypes.POINTER(XmBatchInfo)]),
+        "xm_qfact_create": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int64, _P, _P, _P, _P,
+                                           ctypes.POINTER(_P)]),
+        "xm_qy_factored": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P]),
+        "xm_qfact_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_size_t),
+                                         ctypes.POINTER(ctypes.c_double)]),
+        "xm_qfact_free": (ctypes.c_int, [_P, _P]),
         "xm_backward": (ctypes.c_int, [_P, _P, ctypes.POINTER(XmOpts), ctypes.c_int, _P, ctypes.c_int,
                                        ctypes.c_int, ctypes.c_int64, _P, _P, _P, _P, _P, _P, _P, _P,
                                        ctypes.POINTER(XmAdjInfo)]),
@@ -283,6 +290,49 @@ def xm_qy(q: QMat, Y, prec: int = XM_FP64):
     Y = Y.contiguous()
     W = torch.empty_like(Y)
     _check(lib().xm_qy(q.ctx.h, q.h, prec, Y.shape[1], _ptr(Y), _ptr(W)))
+    return W
+
+
+class QFact:
+    """Owning handle of an xm_qfact (the factored Q operator)."""
+
+    def __init__(self, ctx: Context, h):
+        self.ctx, self.h = ctx, h
+        N, M, E = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64()
+        nb, ts = ctypes.c_size_t(), ctypes.c_double()
+        _check(lib().xm_qfact_info(h, ctypes.byref(N), ctypes.byref(M), ctypes.byref(E), ctypes.byref(nb),
+                                   ctypes.byref(ts)))
+        self.N, self.M, self.E, self.n = N.value, M.value, E.value, 3 * N.value
+        self.bytes, self.t_setup_s = nb.value, ts.value
+
+    def free(self):
+        if getattr(self, "h", None):
+            lib().xm_qfact_free(self.ctx.h, self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def xm_qfact_create(ctx: Context, N: int, M: int, cam, lmk, ukp, w) -> QFact:
+    """Factored Q operator from observation tensors (as for xm_build_Q)."""
+    h = _P()
+    _check(lib().xm_qfact_create(ctx.h, N, M, int(cam.shape[0]), _ptr(cam), _ptr(lmk), _ptr(ukp), _ptr(w),
+                                 ctypes.byref(h)))
+    return QFact(ctx, h)
+
+
+def xm_qy_factored(f: QFact, Y):
+    """W = Q Y by the factored operator for an n x r float64 CUDA tensor Y."""
+    import torch
+    if Y.dtype != torch.float64 or Y.dim() != 2 or Y.shape[0] != f.n:
+        raise ValueError(f"Y must be float64 of shape (n={f.n}, r)")
+    Y = Y.contiguous()
+    W = torch.empty_like(Y)
+    _check(lib().xm_qy_factored(f.ctx.h, f.h, Y.shape[1], _ptr(Y), _ptr(W)))
     return W
 
 
