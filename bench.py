@@ -52,15 +52,18 @@ BATCH_DESC = ("256 independent scenes, cameras log-uniform in [10, 400] (floor),
 PRECS = {"fp64": 0, "fp32": 1, "bf16": 2}
 DTYPES = {"fp64": "f64", "fp32": "f32", "bf16": "bf16/f32"}
 # Sweeps of one certified FP32-bulk solve of each workload as measured on a B300 by the GPU arm
-# of this benchmark (mean of its 5 or 2 timed solves); the reference arm multiplies the oracle's
-# time per sweep by it.
-REFERENCE_SWEEPS = {"c3": 2050, "c2": 575, "c4": 8737, "c1": 500}
+# of this benchmark (10155 cameras: mean of the 20 timed solves of a 20-step run; the others:
+# mean of 5 or 2); the reference arm multiplies the oracle's time per sweep by it (an
+# extrapolation, labelled as such in its line).
+REFERENCE_SWEEPS = {"c3": 2230, "c2": 575, "c4": 8737, "c1": 500}
+L2_BYTES = 126e6
 # DRAM bytes (read + write) over algorithmic bytes of qy_packed_kernel<float,4,8> from one ncu
 # capture at the 10155-camera size itself (n = 30465: 1.8832 GB read + 0.0040 GB written per
 # launch against 1.8573 GB algorithmic), on the kernel as it stands (swizzled Y_J, paired
-# tile-row order).  The kernel streams every tile once, so other sizes scale the same ratio by
-# the tiles.  Must be re-measured (or set to None) whenever the sweep kernel changes.
+# tile-row order).  Applied only at that size (other sizes get traffic = null); must be
+# re-measured (or set to None) whenever the sweep kernel changes.
 SWEEP_TRAFFIC_RATIO = (1.883209 + 0.003997) / 1.857268
+SWEEP_TRAFFIC_N = 30465
 
 
 def peaks():
@@ -184,26 +187,58 @@ def run_reference(args):
     _, N, desc = WORKLOADS[args.workload]
     n = 3 * N
     S = REFERENCE_SWEEPS[args.workload]
+    from oracle import xm_oracle as O
+    rng = np.random.default_rng(0)
+    Q = rng.standard_normal((n, n))
+    Q += Q.T
+    Y = O.initial_point(N, 4)
     times = []
     for i in range(args.warmup + args.steps):
-        dt = oracle_sweep_seconds(n, 4, reps=1, seed=i)
+        t0 = time.perf_counter()
+        G = Q @ Y
+        L = O.lambdas(Y, G)
+        O.proj_tangent(Y, 2.0 * (G - O.apply_blockdiag(L, Y)))
+        dt = time.perf_counter() - t0
         if i >= args.warmup:
             times.append(dt)
+    del Q
     per = statistics.mean(times)
     value = per * S
+    full = oracle_full_solve_c2()
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": f"{args.workload}: {desc}", "prec": "fp64 (oracle)"},
-        "cpu_baseline": {"value": value, "unit": "s", "cores": host_cores(), "kind": "oracle",
-                         "sample": f"one oracle sweep (dense FP64 Q@Y, n={n}, r=4, plus dual blocks "
-                                   f"and projection) per step, times {S} sweeps of a certified solve"},
+        "cpu_baseline": {"value": value, "unit": "s", "cores": host_cores(),
+                         "kind": "oracle, extrapolated",
+                         "sample": f"one oracle sweep (dense FP64 Q@Y on a seeded random symmetric Q "
+                                   f"of the workload's size n={n}, r=4, plus dual blocks and "
+                                   f"projection; the product's time does not depend on Q's values) "
+                                   f"timed per step, times the {S} sweeps of the GPU arm's mean "
+                                   f"certified solve"},
         "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "oracle_end_to_end_c2": full,
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def oracle_full_solve_c2() -> dict:
+    """One complete oracle run on the 1934-camera workload, measured end to end on the host cores
+    (no extrapolation): Q by the Schur form, then the staircase (Alg. 1 + RTR-tCG), certificate
+    and rounding."""
+    from oracle import xm_oracle as O
+    sc = scenes.config2()
+    t0 = time.perf_counter()
+    Q = O.build_Q_schur(sc.N, sc.M, sc.cam, sc.lmk, sc.ukp, sc.w)
+    t1 = time.perf_counter()
+    res = O.solve(Q, r0=4)
+    t2 = time.perf_counter()
+    return {"workload": "c2: 1934 cameras, 300k landmarks, ~1.5M observations, 2% outliers",
+            "build_s": t1 - t0, "solve_s": t2 - t1, "certified": bool(res.certified),
+            "sweeps": int(res.sweeps), "f": res.f, "cores": host_cores(), "kind": "oracle, measured"}
 
 
 def run_sweep_only(args):
@@ -332,16 +367,15 @@ def _pct(xs, q):
     return float(np.percentile(np.asarray(xs, dtype=np.float64), q)) if len(xs) else float("nan")
 
 
-def run_batched(args):
-    """The serving-style batch: every scene's Q resident, W untimed and K timed batched solves;
-    value = scenes per second.  Per-scene latency from the device clock of each scene's CTA:
-    completion time after the batch's first scene started (p50/p99), and the scene's own
-    solve time."""
+def batched_measure(ctx, scs, warmup: int, steps: int, time_limit: float = 60.0) -> dict:
+    """Builds every scene's Q, packs the batch, autotunes its tiling, then W untimed and K timed
+    batched solves (CUDA events on the context's stream around the K graph replays, and the
+    wall clock; the larger counts); per-scene latency from the device clock of each scene's CTA
+    in the last batch: completion after the batch's first scene started (p50/p99) and the
+    scene's own solve time."""
     import torch
     from paper_2502_04640_b300 import xm
-    scs = scenes.config5()
     S = len(scs)
-    ctx = xm.Context(0)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     qs = [xm.xm_build_Q(ctx, sc.N, sc.M, *xm.scene_tensors(sc)) for sc in scs]
@@ -355,27 +389,26 @@ def run_batched(args):
     t0 = time.perf_counter()
     tiling = xm.xm_batch_autotune(b, reps=8)
     t_tune = time.perf_counter() - t0
-    opts = xm.xm_default_opts(time_limit_s=args.time_limit if args.time_limit > 0 else 60.0)
+    opts = xm.xm_default_opts(time_limit_s=time_limit)
     tot = sum(sc.N for sc in scs)
     R = torch.zeros((tot, 3, 3), dtype=torch.float64, device="cuda:0")
     s = torch.zeros((tot,), dtype=torch.float64, device="cuda:0")
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         xm.xm_solve_batched(b, opts, R=R, s=s)
-    clocks = ClockSampler(0)
     torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(ctx.stream)
     wall0 = time.perf_counter()
     infos = []
-    for _ in range(args.steps):
+    for _ in range(steps):
         infos.append(xm.xm_solve_batched(b, opts, R=R, s=s)["info"])
+    ev1.record(ctx.stream)
     torch.cuda.synchronize()
-    wall = time.perf_counter() - wall0
-    clk = clocks.stop()
-    per_step = wall / args.steps
+    per_step = max(time.perf_counter() - wall0, ev0.elapsed_time(ev1) / 1e3) / steps
     last = infos[-1]
     t_first = min(i["t_begin_ns"] for i in last)
     done_ms = [(i["t_end_ns"] - t_first) / 1e6 for i in last]
     own_ms = [(i["t_end_ns"] - i["t_begin_ns"]) / 1e6 for i in last]
-    certified = sum(i["certified"] for i in last)
     # bytes the dense sweeps read: FP32 sweeps n x ldq x 4, FP64 sweeps n x ldq x 8 (Y in shared memory)
     by = 0.0
     for sc, i in zip(scs, last):
@@ -384,6 +417,41 @@ def run_batched(args):
         by += (i["n_sweeps"] - i["n_sweeps_fp64"]) * n * ldq * 4 + i["n_sweeps_fp64"] * n * ldq * 8
     peak, peak_kind = peaks()
     achieved = by / per_step / 1e9
+    q_bytes = sum(3 * sc.N * ((3 * sc.N + 3) & ~3) for sc in scs) * 4
+    return {
+        "b": b, "opts": opts, "R": R, "s": s, "tot": tot,
+        "scenes_per_s": S / per_step, "s_per_batch": per_step,
+        "latency_ms": {"p50": _pct(done_ms, 50), "p99": _pct(done_ms, 99), "max": max(done_ms),
+                       "scene_solve_p50": _pct(own_ms, 50), "scene_solve_p99": _pct(own_ms, 99)},
+        "certified": sum(i["certified"] for i in last), "scenes": S, "cameras": tot,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "k_batched<4>",
+                     "bytes_per_launch": by, "launch_ms": per_step * 1e3, "peak_kind": peak_kind,
+                     "note": "dense sweep bytes of all scenes / batch time; the FP32 copies total "
+                             f"{q_bytes / 1e6:.0f} MB, so part of every sweep is served by L2"},
+        "l2": f"per-scene Q re-read every sweep; the batch's FP32 copies total {q_bytes / 1e6:.0f} MB",
+        "tiling_rows_chunks": tiling,
+        "sweeps": int(sum(i["n_sweeps"] for i in last)),
+        "sweeps_fp64": int(sum(i["n_sweeps_fp64"] for i in last)),
+        "escapes": int(sum(i["n_escapes"] for i in last)),
+        "ranks": {str(r): sum(1 for i in last if i["rank"] == r) for r in sorted({i["rank"] for i in last})},
+        "build_q_s": t_build, "pack_s": t_pack, "autotune_s": t_tune,
+    }
+
+
+def run_batched(args):
+    """The serving-style batch: every scene's Q resident, W untimed and K timed batched solves;
+    value = scenes per second."""
+    import torch
+    from paper_2502_04640_b300 import xm
+    scs = scenes.config5()
+    S = len(scs)
+    ctx = xm.Context(0)
+    clocks = ClockSampler(0)
+    m = batched_measure(ctx, scs, args.warmup, args.steps,
+                        args.time_limit if args.time_limit > 0 else 60.0)
+    clk = clocks.stop()
+    b, opts, R, s, tot = m.pop("b"), m.pop("opts"), m.pop("R"), m.pop("s"), m.pop("tot")
     # end to end from pinned host arrays: copies, Q builds, batch packing, solve, results back
     e2e = None
     if args.e2e_steps > 0:
@@ -417,34 +485,185 @@ def run_batched(args):
         cpu = oracle_batch_sample(scs, budget_s=20.0)
     line = {
         "metric": "batched certified solves: scenes/s and p50/p99 per-scene latency",
-        "value": S / per_step, "unit": "scenes/s", "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True,
+        "value": m["scenes_per_s"], "unit": "scenes/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": m["s_per_batch"] * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
-        "config": {"workload": f"c5: {BATCH_DESC}", "scenes": S, "cameras": tot,
-                   "l2": "per-scene Q re-read every sweep; the batch's FP32 copies total "
-                         f"{sum(3 * sc.N * ((3 * sc.N + 3) & ~3) for sc in scs) * 4 / 1e6:.0f} MB"},
-        "latency_ms": {"p50": _pct(done_ms, 50), "p99": _pct(done_ms, 99), "max": max(done_ms),
-                       "scene_solve_p50": _pct(own_ms, 50), "scene_solve_p99": _pct(own_ms, 99)},
-        "certified": certified,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "k_batched<4>",
-                     "bytes_per_launch": by, "launch_ms": per_step * 1e3, "peak_kind": peak_kind,
-                     "note": "dense sweep bytes of all scenes / batch time; much of it is served by L2"},
-        "cpu_baseline": cpu,
-        "e2e": e2e,
-        "gpu_launches": 2 * args.steps,
-        "clocks": clk,
-        "tiling_rows_chunks": tiling,
-        "sweeps": int(sum(i["n_sweeps"] for i in last)),
-        "sweeps_fp64": int(sum(i["n_sweeps_fp64"] for i in last)),
-        "escapes": int(sum(i["n_escapes"] for i in last)),
-        "ranks": {str(r): sum(1 for i in last if i["rank"] == r) for r in sorted({i["rank"] for i in last})},
-        "build_q_s": t_build, "pack_s": t_pack, "autotune_s": t_tune,
+        "config": {"workload": f"c5: {BATCH_DESC}", "scenes": S, "cameras": tot, "l2": m.pop("l2")},
+        "latency_ms": m["latency_ms"], "certified": m["certified"], "roofline": m["roofline"],
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps, "clocks": clk,
+        **{k: m[k] for k in ("tiling_rows_chunks", "sweeps", "sweeps_fp64", "escapes", "ranks",
+                             "build_q_s", "pack_s", "autotune_s")},
     }
     print(json.dumps(line), flush=True)
     b.free()
     ctx.close()
     return 0
+
+
+def factored_bytes_flops(N: int, M: int, E: int, r: int) -> tuple:
+    """Algorithmic bytes and FP64 flops of one factored product (App. A's elimination in product
+    form): the landmark-major copy of (u, w, camera) read twice (u once), the camera-major copy
+    (u, w, landmark) twice, per landmark its offsets and 1/d_k twice and the two means written and
+    read (8 doubles a row), the packed -Sbar^{-1} once, Y read and W written (row offsets and the
+    (N-1) x R sweep vectors are negligible).  Flops: a_e three times (2 x 3r each), the means and
+    sums (2r each), the output outer products (2 x 3r) and the symmetric sweep (2 (N-1)^2 r)."""
+    m = N - 1
+    by = (E * (36 + 12 + 36 + 36) + M * (2 * 8 + 2 * 8 + 4 * 8 * 8) + m * (m + 1) / 2 * 8
+          + 2 * 3 * N * r * 8)
+    fl = E * (3 * 6 * r + 3 * 2 * r + 6 * r) + 2.0 * m * m * r
+    return by, fl
+
+
+def factored_measure(ctx, sc, q, reps: int = 20) -> dict:
+    """The factored Q operator next to the dense sweeps on the same scene: set-up time, resident
+    bytes, time per product (CUDA events on the context stream, after 3 warm-up products), its
+    algorithmic bytes and FP64 flops, and the largest difference from the dense FP64 sweep
+    relative to that sweep's largest entry."""
+    import torch
+    from paper_2502_04640_b300 import xm
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    f = xm.xm_qfact_create(ctx, sc.N, sc.M, *xm.scene_tensors(sc))
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    Y = torch.as_tensor(np.random.default_rng(3).standard_normal((3 * sc.N, 4)), device="cuda:0")
+    W = torch.empty_like(Y)
+    for _ in range(3):
+        xm.lib().xm_qy_factored(ctx.h, f.h, 4, Y.data_ptr(), W.data_ptr())
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(ctx.stream)
+    for _ in range(reps):
+        xm.lib().xm_qy_factored(ctx.h, f.h, 4, Y.data_ptr(), W.data_ptr())
+    ev1.record(ctx.stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / reps
+    res = {"setup_s": setup_s, "resident_GB": f.bytes / 1e9, "ms_per_product_r4": ms}
+    by, fl = factored_bytes_flops(sc.N, sc.M, sc.E, 4)
+    res.update({"bytes_per_product": by, "fp64_flops_per_product": fl,
+                "achieved_GBps": by / (ms * 1e-3) / 1e9, "achieved_fp64_tflops": fl / (ms * 1e-3) / 1e12})
+    if q is not None and (q.mask & xm.XM_STORE_FP64):
+        Wd = xm.xm_qy(q, Y, xm.XM_FP64)
+        res["max_diff_vs_dense_fp64_rel"] = float((W - Wd).abs().max() / Wd.abs().max())
+        d_ms, _ = xm.xm_bench_qy(q, xm.XM_FP64, 4, 10)
+        res["dense_fp64_sweep_ms"] = d_ms
+        res["speedup_vs_dense_fp64"] = d_ms / ms
+    if q is not None and (q.mask & xm.XM_STORE_FP32):
+        res["dense_fp32_sweep_ms"] = xm.xm_bench_qy(q, xm.XM_FP32_BULK, 4, 10)[0]
+    f.free()
+    return res
+
+
+def other_workloads(ctx, steps: int = 3) -> dict:
+    """The other workloads of the benchmark, measured in the same run after the main line's timed
+    region (rank 0): the 1934-camera plain-vs-mixed comparison, the 2000-frame trajectory's
+    certified solve (both hand-over settings) and adjoint, and the 256-scene batch.  Each entry
+    records its own error instead of failing the run."""
+    out = {}
+    for name, fn in (("c2", _c2_compare), ("c4", _c4_solve_and_adjoint), ("c5", _c5_batch)):
+        t0 = time.perf_counter()
+        try:
+            out[name] = fn(ctx, steps)
+        except Exception as e:      # noqa: BLE001 - reported in the line, the main number stands
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+        out[name]["wall_s"] = time.perf_counter() - t0
+    return out
+
+
+def _timed_solves(xm, q, opts, warmup: int, steps: int):
+    import torch
+    for _ in range(warmup):
+        xm.xm_solve(q, opts)
+    outs, walls = [], []
+    for _ in range(steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        o = xm.xm_solve(q, opts)
+        walls.append(time.perf_counter() - t0)
+        outs.append(o)
+    return outs, walls
+
+
+def _errs(o, ref):
+    fi = ref["info"]
+    return {"f_rel": abs(o["info"]["f"] - fi["f"]) / (1 + abs(fi["f"])),
+            "rho_hat_rel": abs(o["info"]["rho_hat"] - fi["rho_hat"]) / (1 + abs(fi["rho_hat"])),
+            "eta_abs": abs(o["info"]["eta"] - fi["eta"]),
+            "lambda_min_abs": abs(o["info"]["lambda_min_deflated"] - fi["lambda_min_deflated"]),
+            "R_max_abs": float((o["R"] - ref["R"]).abs().max()),
+            "s_max_rel": float(((o["s"] - ref["s"]).abs() / ref["s"].abs()).max())}
+
+
+def _c2_compare(ctx, steps):
+    """1934 cameras: certified solve in the FP32-bulk, BF16-storage and plain FP64 forms, with
+    per-result errors against the FP64 form."""
+    from paper_2502_04640_b300 import xm
+    sc = scenes.config2()
+    q = xm.xm_build_Q(ctx, sc.N, sc.M, *xm.scene_tensors(sc), xm.XM_STORE_ALL)
+    n = q.n
+    res = {"N": sc.N, "E": sc.E, "l2": f"L2-resident: packed FP32 Q {n * (n + 1) / 2 * 4 / 1e6:.0f} MB "
+                                     f"< 126 MB L2 (no flush between solves)"}
+    ref = None
+    for name, pv in (("fp64", 0), ("fp32", 1), ("bf16", 2)):
+        outs, walls = _timed_solves(xm, q, xm.xm_default_opts(prec=pv), 1, steps)
+        res[f"{name}_solve_s"] = statistics.median(walls)
+        res[f"{name}_certified"] = all(o["info"]["certified"] for o in outs)
+        res[f"{name}_sweeps"] = outs[-1]["info"]["n_sweeps"]
+        if pv == 0:
+            ref = outs[-1]
+        else:
+            res[f"{name}_vs_fp64"] = _errs(outs[-1], ref)
+    res["eta"] = ref["info"]["eta"]
+    res["factored_qy"] = factored_measure(ctx, sc, q)
+    for pname, pv, bq, byy in (("fp32", 1, 4, 4), ("bf16", 2, 2, 4), ("fp64", 0, 8, 8)):
+        ms, _ = xm.xm_bench_qy(q, pv, 4, 20)
+        res[f"qy_{pname}_r4_us"] = ms * 1e3
+        res[f"qy_{pname}_r4_GBps"] = sweep_bytes(n, 4, bq, byy) / (ms * 1e-3) / 1e9
+    q.free()
+    return res
+
+
+def _c4_solve_and_adjoint(ctx, steps):
+    """2000-frame trajectory (App. D weight 10): the certified FP32-bulk solve with the default
+    hand-over and with bulk_stall = 5, and the adjoint (FP32 inner CG in FP64 refinement)."""
+    import torch
+    from paper_2502_04640_b300 import xm
+    sc = scenes.config4()
+    wopts = dict(WORKLOAD_OPTS["c4"])
+    q = xm.xm_build_Q(ctx, sc.N, sc.M, *xm.scene_tensors(sc), xm.XM_STORE_ALL)
+    res = {"N": sc.N, "E": sc.E, "opts": wopts}
+    outs, walls = _timed_solves(xm, q, xm.xm_default_opts(prec=1, **wopts), 0, 1)
+    res["solve_default_s"] = walls[0]
+    res["solve_default_certified"] = outs[0]["info"]["certified"]
+    out = outs[0]      # the adjoint's forward solve: default options (its stationarity sets the floor)
+    stalls, walls = _timed_solves(xm, q, xm.xm_default_opts(prec=1, bulk_stall=5, **wopts), 1, steps)
+    res["solve_bulk_stall5_s"] = statistics.median(walls)
+    res["solve_bulk_stall5_certified"] = all(o["info"]["certified"] for o in stalls)
+    r = out["info"]["rank"]
+    t = xm.scene_tensors(sc)
+    D = torch.as_tensor(np.random.default_rng(5).standard_normal((sc.N, 3, 3)), device="cuda:0")
+    opts = xm.xm_default_opts(prec=1, **wopts)
+    xm.xm_backward(q, out["Y"], r, sc.M, *t, D, opts)
+    walls, infos = [], []
+    for _ in range(steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        infos.append(xm.xm_backward(q, out["Y"], r, sc.M, *t, D, opts)[3])
+        walls.append(time.perf_counter() - t0)
+    res["adjoint_s"] = statistics.median(walls)
+    res["adjoint_grads_per_s"] = sc.E * 4 / res["adjoint_s"]
+    res["adjoint"] = {k: infos[-1][k] for k in ("res_rel", "n_cg", "n_refine", "t_lambda_s", "t_resid_s")}
+    res["factored_qy"] = factored_measure(ctx, sc, q)
+    q.free()
+    return res
+
+
+def _c5_batch(ctx, steps):
+    m = batched_measure(ctx, scenes.config5(), 2, steps)
+    m.pop("b").free()
+    for k in ("opts", "R", "s", "tot"):
+        m.pop(k)
+    return m
 
 
 def oracle_batch_sample(scs, budget_s=20.0):
@@ -624,6 +843,9 @@ def main():
                     help="time xm_recover_tp (Eq. 7) and xm_solve_xm2 (Sec. 5) on --workload")
     ap.add_argument("--adjoint", action="store_true",
                     help="time xm_backward (the adjoint of the certified optimum) on --workload")
+    ap.add_argument("--no-others", action="store_true",
+                    help="skip the other workloads (1934 cameras, trajectory + adjoint, batch) that the "
+                         "default line measures after its timed region")
     args = ap.parse_args()
     if args.adjoint:
         return run_adjoint(args)
@@ -728,11 +950,13 @@ def main():
     alg = sweep_bytes(n, 4, bq, by)
     peak, peak_kind = peaks()
     achieved = alg / (qy_ms * 1e-3) / 1e9
-    traffic = alg * SWEEP_TRAFFIC_RATIO if prec == 1 and SWEEP_TRAFFIC_RATIO else None
+    measured_here = prec == 1 and SWEEP_TRAFFIC_RATIO and n == SWEEP_TRAFFIC_N
+    traffic = alg * SWEEP_TRAFFIC_RATIO if measured_here else None
     roofline = {"bound": "hbm" if prec != 0 else "alu", "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                "traffic_note": "ncu DRAM read+write of one launch at n = 30465 (the same sweep "
-                                "size), as a ratio to the algorithmic bytes" if traffic else None,
+                "traffic_note": "ncu DRAM read+write of one launch at n = 30465 (this sweep "
+                                "size), as a ratio to the algorithmic bytes" if traffic else
+                                "no ncu DRAM capture at this size",
                 "kernel": f"qy_packed_kernel<{'double' if prec == 0 else 'float'},4,8>",
                 "bytes_per_launch": alg, "launch_ms": qy_ms, "peak_kind": peak_kind}
 
@@ -757,6 +981,10 @@ def main():
             extra["bf16q_solve_s"] = b["info"]["t_solve_s"]
             extra["bf16q_certified"] = b["info"]["certified"]
             extra["bf16q_vs_fp64"] = errs(b)
+        try:
+            extra["factored_qy"] = factored_measure(ctx, sc, q)
+        except Exception as e:      # noqa: BLE001 - reported, the main number stands
+            extra["factored_qy"] = {"error": f"{type(e).__name__}: {e}"}
         for pname, pv in (("fp32", 1), ("bf16", 2), ("fp64", 0)):
             mean_ms, _ = xm.xm_bench_qy(q, pv, 4, 10)
             bqq = {1: 4, 2: 2, 0: 8}[pv]
@@ -783,6 +1011,10 @@ def main():
         e2e = {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(sc.E * (4 + 4 + 24 + 8)),
                "d2h_bytes_per_step": int(sc.N * (72 + 8))}
 
+    others = None
+    if rank == 0 and not args.no_others:
+        others = other_workloads(ctx, steps=3)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         dt = oracle_sweep_seconds(n, 4, reps=2)
@@ -791,14 +1023,16 @@ def main():
                "sample": f"two oracle sweeps (dense FP64 Q@Y, n={n}, r=4, dual blocks, projection) "
                          f"timed, times the {S} sweeps of this certified solve"}
 
+    qb = n * (n + 1) / 2 * {0: 8, 1: 4, 2: 2}[prec]
+    l2_label = (f"inputs larger than L2 (packed Q {qb / 1e9:.2f} GB > 126 MB)" if qb > L2_BYTES else
+                f"L2-resident: packed Q {qb / 1e6:.0f} MB < 126 MB L2 (not flushed between solves)")
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": value * 1e3 * world, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[args.prec], "data": "synthetic",
             "config": {"workload": f"{args.workload}: {desc}", "prec": args.prec, "opts": wopts,
-                       "replicas": world, "l2": "inputs larger than L2 (packed FP32 Q "
-                       f"{n * (n + 1) / 2 * 4 / 1e9:.2f} GB > 126 MB)", "N": sc.N, "M": sc.M, "E": sc.E},
+                       "replicas": world, "l2": l2_label, "N": sc.N, "M": sc.M, "E": sc.E},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
@@ -809,6 +1043,8 @@ def main():
                                            "lambda_max", "dual", "rho_hat", "eta", "eta_robust", "rank",
                                            "n_sweeps", "n_sweeps_fp64", "n_outer", "n_tcg",
                                            "n_lanczos", "n_escapes", "t_cert_s")},
+            "step_s": {"mean": statistics.mean(per_step), "median": statistics.median(per_step),
+                       "p90": _pct(per_step, 90), "min": min(per_step), "max": max(per_step)},
             "per_step": [{"s": round(t, 4), "n_tcg": i["n_tcg"], "n_outer": i["n_outer"],
                           "n_sweeps": i["n_sweeps"], "t_cert_s": round(i["t_cert_s"], 4),
                           "certified": i["certified"]} for t, i in zip(per_step, timed)],
@@ -816,6 +1052,8 @@ def main():
             "build_update": update_report(sc.N, build_path, t_update),
             **extra,
         }
+        if others is not None:
+            line["other_workloads"] = others
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
