@@ -554,13 +554,49 @@ def factored_measure(ctx, sc, q, reps: int = 20) -> dict:
     return res
 
 
+def depth_noise_table(ctx, count: int = 8, N: int = 100, M: int = 2000) -> dict:
+    """Robustness to the depth-noise model of the paper's noise analysis (every observation's depth
+    scaled by (1 + eps)^x, x ~ U(-1, 1)): per noise level, `count` community-photo-shaped scenes
+    of N cameras solved in the FP32-bulk mode; certified count, Eq. 18's eta (median, max), the
+    rounded rotations' angular error against the ground truth (median over cameras and scenes,
+    worst camera), the median |log| scale error, and the median solve time."""
+    from paper_2502_04640_b300 import xm
+    table = {}
+    for eps in scenes.DEPTH_NOISE_EPS:
+        cert, etas, angs, worst, lserr, times = 0, [], [], [], [], []
+        for sc in scenes.depth_noise_scenes(eps, count=count, N=N, M=M):
+            q = xm.xm_build_Q(ctx, sc.N, sc.M, *xm.scene_tensors(sc))
+            o = xm.xm_solve(q, xm.xm_default_opts(prec=xm.XM_FP32_BULK))
+            q.free()
+            info = o["info"]
+            R, s, _, _ = sc.anchored_gt()
+            Rg, sg = o["R"].cpu().numpy(), o["s"].cpu().numpy()
+            c = np.clip((np.einsum("iab,iab->i", Rg, R) - 1.0) / 2.0, -1.0, 1.0)
+            a = np.degrees(np.arccos(c))[1:]
+            cert += int(info["certified"])
+            etas.append(info["eta"])
+            angs.append(a)
+            worst.append(a.max())
+            lserr.append(np.median(np.abs(np.log(np.maximum(sg[1:], 1e-300) / s[1:]))))
+            times.append(info["t_solve_s"])
+        table[f"{eps:g}"] = {"certified": cert, "scenes": count, "eta_median": float(np.median(etas)),
+                             "eta_max": float(np.max(etas)),
+                             "rot_err_deg_median": float(np.median(np.concatenate(angs))),
+                             "rot_err_deg_worst": float(np.max(worst)),
+                             "log_scale_err_median": float(np.median(lserr)),
+                             "solve_s_median": float(np.median(times))}
+    return {"model": "depth x (1 + eps)^x, x ~ U(-1, 1) per observation", "N": N, "M": M,
+            "scenes_per_level": count, "table": table}
+
+
 def other_workloads(ctx, steps: int = 3) -> dict:
     """The other workloads of the benchmark, measured in the same run after the main line's timed
     region (rank 0): the 1934-camera plain-vs-mixed comparison, the 2000-frame trajectory's
     certified solve (both hand-over settings) and adjoint, and the 256-scene batch.  Each entry
     records its own error instead of failing the run."""
     out = {}
-    for name, fn in (("c2", _c2_compare), ("c4", _c4_solve_and_adjoint), ("c5", _c5_batch)):
+    for name, fn in (("c2", _c2_compare), ("c4", _c4_solve_and_adjoint), ("c5", _c5_batch),
+                     ("depth_noise", lambda c, k: depth_noise_table(c, count=4))):
         t0 = time.perf_counter()
         try:
             out[name] = fn(ctx, steps)
@@ -843,12 +879,21 @@ def main():
                     help="time xm_recover_tp (Eq. 7) and xm_solve_xm2 (Sec. 5) on --workload")
     ap.add_argument("--adjoint", action="store_true",
                     help="time xm_backward (the adjoint of the certified optimum) on --workload")
+    ap.add_argument("--noise-sweep", action="store_true",
+                    help="depth-noise robustness table (certified rate, eta, rotation and scale errors "
+                         "across the noise levels of the paper's noise analysis)")
     ap.add_argument("--no-others", action="store_true",
                     help="skip the other workloads (1934 cameras, trajectory + adjoint, batch) that the "
                          "default line measures after its timed region")
     args = ap.parse_args()
     if args.adjoint:
         return run_adjoint(args)
+    if args.noise_sweep:
+        from paper_2502_04640_b300 import xm
+        ctx = xm.Context(0)
+        print(json.dumps({"noise_sweep": True, **depth_noise_table(ctx)}), flush=True)
+        ctx.close()
+        return 0
     if args.recover:
         return run_recover(args)
 

@@ -59,7 +59,14 @@ typedef enum xm_prec { XM_FP64 = 0, XM_FP32_BULK = 1, XM_BF16Q_BULK = 2 } xm_pre
 #define XM_STORE_FP64 1u   /* FP64 packed upper-triangle tiles (needed by XM_FP64, polish) */
 #define XM_STORE_FP32 2u   /* FP32 packed tiles */
 #define XM_STORE_BF16 4u   /* BF16 packed tiles */
-#define XM_STORE_ALL  7u
+#define XM_STORE_ALL  7u   /* the three dense copies */
+#define XM_STORE_FACTORED 8u /* the factored operator (App. A in product form, see xm_qfact_create):
+                                every FP64 product of a Q without XM_STORE_FP64 goes through it
+                                (FP64-mode solves, the mixed modes' FP64 polish, certificates,
+                                rounding).  With no dense bit set, Q itself is never formed (10155
+                                cameras: 1.2 GB resident instead of 3.8 GB of FP64 tiles); solves
+                                then run in XM_FP64 and the block-Jacobi preconditioners (precond,
+                                the LOBPCG certificate) read the FP32 tiles when there are any */
 
 typedef struct xm_opts {
   int r0;                  /* initial BM rank, 1 <= r0 <= XM_MAX_RANK (Alg. 1 uses 3);

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libxm.so")
 SOURCES = ["xm_api.cu", "xm_build.cu", "xm_qy.cu", "xm_solver.cu", "xm_noalloc.cu", "xm_backward.cu",
-           "xm_batched.cu", "xm_recover.cu", "xm_ozaki.cu", "xm_factored.cu"]
+           "xm_batched.cu", "xm_recover.cu", "xm_ozaki.cu", "xm_factored.cu", "xm_dense.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",

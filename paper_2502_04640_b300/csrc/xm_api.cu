@@ -171,12 +171,13 @@ xm_status xm_build_Q(xm_ctx* c, int N, int M, int64_t E, const int32_t* cam, con
   if (!c || !out) return set_error(XM_EINVAL, "xm_build_Q: NULL context or output");
   *out = nullptr;
   if (N < 1 || M < 0 || E < 0) return set_error(XM_EINVAL, "xm_build_Q: N=%d M=%d E=%lld", N, M, (long long)E);
-  if ((mask & XM_STORE_ALL) == 0) return set_error(XM_EINVAL, "xm_build_Q: empty store mask");
+  mask &= XM_STORE_ALL | XM_STORE_FACTORED;
+  if (mask == 0) return set_error(XM_EINVAL, "xm_build_Q: empty store mask");
   if (E > 0 && (!cam || !lmk || !ukp || !w)) return set_error(XM_EINVAL, "xm_build_Q: NULL array");
   if ((int64_t)3 * N > (1 << 20)) return set_error(XM_EINVAL, "xm_build_Q: N=%d too large", N);
   XM_CUDA_TRY(cudaSetDevice(c->device));
   xm_qmat* q = new xm_qmat();
-  xm_status st = build_Q(c, N, M, E, cam, lmk, ukp, w, mask & XM_STORE_ALL, q->d, &q->t_build_s);
+  xm_status st = build_Q(c, N, M, E, cam, lmk, ukp, w, mask, q->d, &q->t_build_s);
   if (st != XM_OK) {
     free_tiles(q->d);
     delete q;

@@ -15,8 +15,6 @@
 //      the tensor-core update writes the packed tiles itself.
 // Connectivity of the view graph (rank N+M-1 of the Laplacian Q_tp, App. A lemma) is checked
 // with a union-find over the camera-landmark edges before any elimination.
-#include <cublas_v2.h>
-#include <cusolverDn.h>
 
 #include <algorithm>
 #include <chrono>
@@ -252,6 +250,11 @@ xm_status alloc_tiles(xm_ctx* ctx, DeviceQ& q, int N, unsigned mask) {
 }
 
 void free_tiles(DeviceQ& q) {
+  if (q.fact) {
+    qfact_release(*q.fact);
+    delete q.fact;
+    q.fact = nullptr;
+  }
   if (q.q64) cudaFree(q.q64);
   if (q.q32) cudaFree(q.q32);
   if (q.q16) cudaFree(q.q16);
@@ -279,19 +282,6 @@ xm_status unpack_dense(xm_ctx* ctx, const DeviceQ& q, double* Qd) {
   XM_CUDA_TRY(cudaGetLastError());
   return XM_OK;
 }
-
-#define XM_CUBLAS_TRY(expr)                                                                \
-  do {                                                                                     \
-    cublasStatus_t s_ = (expr);                                                            \
-    if (s_ != CUBLAS_STATUS_SUCCESS)                                                       \
-      return set_error(XM_ECUDA, "%s failed: cublas status %d", #expr, (int)s_);           \
-  } while (0)
-#define XM_CUSOLVER_TRY(expr)                                                              \
-  do {                                                                                     \
-    cusolverStatus_t s_ = (expr);                                                          \
-    if (s_ != CUSOLVER_STATUS_SUCCESS)                                                     \
-      return set_error(XM_ECUDA, "%s failed: cusolver status %d", #expr, (int)s_);         \
-  } while (0)
 
 namespace {
 struct DevBuf {
@@ -341,6 +331,25 @@ xm_status build_Q(xm_ctx* ctx, int N, int M, int64_t E, const int32_t* cam, cons
   // ---- connectivity (App. A lemma: rank N + M - 1 iff the view graph is connected)
   XM_TRY(check_connected(ctx, N, M, E, cam, lmk));
 
+  // ---- the factored operator (XM_STORE_FACTORED), with or without dense copies
+  if (mask & XM_STORE_FACTORED) {
+    out.fact = new QFact();
+    const xm_status sf = qfact_build(ctx, N, M, E, cam, lmk, ukp, w, *out.fact);
+    if (sf != XM_OK) {
+      qfact_release(*out.fact);
+      delete out.fact;
+      out.fact = nullptr;
+      return sf;
+    }
+    if (!(mask & XM_STORE_ALL)) {     // no dense copy: Q itself is never formed
+      XM_TRY(alloc_tiles(ctx, out, N, 0));
+      out.mask = mask;
+      if (t_build)
+        *t_build = std::chrono::duration<double>(std::chrono::steady_clock::now() - tic).count();
+      return XM_OK;
+    }
+  }
+
   DevBuf P, B, S, d, cnt, off, bsum, cursor, idx;
   XM_CUDA_TRY(cudaMalloc(&P.p, sizeof(double) * (size_t)n * n));
   XM_CUDA_TRY(cudaMalloc(&B.p, sizeof(double) * (size_t)n * N));
@@ -378,23 +387,8 @@ xm_status build_Q(xm_ctx* ctx, int N, int M, int64_t E, const int32_t* cam, cons
     XM_CUDA_TRY(cudaGetLastError());
   }
 
-  // ---- translation elimination (dense FP64)
+  // ---- translation elimination (dense FP64, own kernels: no vendor library on this path)
   if (N > 1) {
-    if (!ctx->cublas) {
-      cublasHandle_t h;
-      XM_CUBLAS_TRY(cublasCreate(&h));
-      ctx->cublas = h;
-    }
-    if (!ctx->cusolver) {
-      cusolverDnHandle_t h;
-      XM_CUSOLVER_TRY(cusolverDnCreate(&h));
-      ctx->cusolver = h;
-    }
-    cublasHandle_t cb = static_cast<cublasHandle_t>(ctx->cublas);
-    cusolverDnHandle_t cs = static_cast<cusolverDnHandle_t>(ctx->cusolver);
-    XM_CUBLAS_TRY(cublasSetStream(cb, st));
-    XM_CUSOLVER_TRY(cusolverDnSetStream(cs, st));
-    XM_CUBLAS_TRY(cublasSetMathMode(cb, CUBLAS_DEFAULT_MATH));
     const int m = N - 1;
     // rows/cols 1..N-1 of S, ld N: the row-major upper triangle is the column-major lower one
     double* Sbar = S.as<double>() + N + 1;
@@ -413,30 +407,24 @@ xm_status build_Q(xm_ctx* ctx, int N, int M, int64_t E, const int32_t* cam, cons
     XM_CUDA_TRY(cudaEventCreate(&e1));
     XM_CUDA_TRY(cudaEventRecord(e0, st));
     int hinfo = 0;
+    DevBuf fail;
+    XM_CUDA_TRY(cudaMalloc(&fail.p, sizeof(int)));
+    XM_CUDA_TRY(cudaMemsetAsync(fail.p, 0, sizeof(int), st));
     if (split) {
-      XM_TRY(split_potrf(ctx, cb, cs, Sbar, N, m, &hinfo));
+      XM_TRY(split_potrf(ctx, Sbar, N, m, &hinfo));
     } else {
-      int lwork = 0;
-      XM_CUSOLVER_TRY(cusolverDnDpotrf_bufferSize(cs, CUBLAS_FILL_MODE_LOWER, m, Sbar, N, &lwork));
-      DevBuf work, info;
-      XM_CUDA_TRY(cudaMalloc(&work.p, sizeof(double) * (size_t)(lwork > 0 ? lwork : 1)));
-      XM_CUDA_TRY(cudaMalloc(&info.p, sizeof(int)));
-      XM_CUSOLVER_TRY(cusolverDnDpotrf(cs, CUBLAS_FILL_MODE_LOWER, m, Sbar, N, work.as<double>(),
-                                       lwork, info.as<int>()));
-      XM_CUDA_TRY(cudaMemcpyAsync(&hinfo, info.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-      XM_CUDA_TRY(cudaStreamSynchronize(st));
+      XM_TRY(dense_potrf(ctx, Sbar, N, m, fail.as<int>(), &hinfo));
     }
     if (hinfo != 0) {
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
       return set_error(XM_EDISCONNECTED,
-                       "translation Schur block not positive definite (potrf info %d)", hinfo);
+                       "translation Schur block not positive definite (leading minor %d)", hinfo);
     }
-    const double one = 1.0, minus_one = -1.0;
     xm_status stu = XM_OK;
     if (split) {
       // both on the tensor cores; the rank-k update writes the packed tiles itself
-      stu = split_trsm(ctx, cb, Sbar, N, BbarT, N, m, n);
+      stu = split_trsm(ctx, Sbar, N, BbarT, N, m, n);
       if (stu == XM_OK) stu = alloc_tiles(ctx, out, N, mask);
       DevBuf acc;
       double* acc64 = out.q64;
@@ -450,11 +438,12 @@ xm_status build_Q(xm_ctx* ctx, int N, int M, int64_t E, const int32_t* cam, cons
       if (stu == XM_OK) stu = split_update_pack(ctx, BbarT, N, m, P.as<double>(), out, acc64);
       out.build_path = XM_BUILD_SPLIT_BF16;
     } else {
-      if (cublasDtrsm(cb, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N,
-                      CUBLAS_DIAG_NON_UNIT, m, n, &one, Sbar, N, BbarT, N) != CUBLAS_STATUS_SUCCESS ||
-          cublasDsyrk(cb, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T, n, m, &minus_one, BbarT, N, &one,
-                      P.as<double>(), n) != CUBLAS_STATUS_SUCCESS)
-        stu = set_error(XM_ECUDA, "cublasDtrsm / cublasDsyrk failed");
+      // C = L^{-1} Bbar^T (blocked substitution), then P -= C^T C on the lower triangle of the
+      // column-major P (its row-major upper triangle, which the packing reads)
+      stu = dense_trsm_left_lower(ctx, Sbar, N, BbarT, N, m, n, nullptr);
+      if (stu == XM_OK)
+        stu = dense_gemm(ctx, true, false, true, n, n, m, -1.0, BbarT, N, BbarT, N, 1.0, P.as<double>(), n,
+                         nullptr);
       if (stu == XM_OK) stu = alloc_tiles(ctx, out, N, mask);
       if (stu == XM_OK) stu = pack_dense(ctx, out, P.as<double>());
       out.build_path = XM_BUILD_FP64;
@@ -568,6 +557,11 @@ __global__ void k_landmark_S(int M, int N, const int64_t* off, const int64_t* id
   }
 }
 
+// b (N x c column-major) <- -b
+__global__ void k_negate_cols(int N, int c, double* b) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < N * c; e += gridDim.x * blockDim.x) b[e] = -b[e];
+}
+
 // The camera block S = diag(sum w) - sum_k (w w^T)/d_k that remains after the landmarks are
 // eliminated (App. A), and the Cholesky factor of Sbar (camera 0 anchored, t_0 = 0).  S (N x N)
 // and d (M) are allocated by the caller; on return the column-major lower triangle of rows and
@@ -583,25 +577,19 @@ xm_status schur_S_factor(xm_ctx* ctx, int N, int M, const int32_t* cam, const do
     k_landmark_S<<<grid_for(M, 128, ctx->num_sms), 128, 0, st>>>(M, N, loff, lidx, cam, w, d, S);
   XM_CUDA_TRY(cudaGetLastError());
   if (N > 1) {
-    if (!ctx->cusolver) {
-      cusolverDnHandle_t h;
-      XM_CUSOLVER_TRY(cusolverDnCreate(&h));
-      ctx->cusolver = h;
-    }
-    cusolverDnHandle_t cs = static_cast<cusolverDnHandle_t>(ctx->cusolver);
-    XM_CUSOLVER_TRY(cusolverDnSetStream(cs, st));
+    // Cholesky factor of Sbar: tensor-core trailing updates from 512 rows (the build's own
+    // factorisation), the FP64 blocked factor below
     const int m = N - 1;
     double* Sbar = S + N + 1;
-    int lwork = 0;
-    XM_CUSOLVER_TRY(cusolverDnDpotrf_bufferSize(cs, CUBLAS_FILL_MODE_LOWER, m, Sbar, N, &lwork));
-    DevBuf work, info;
-    XM_CUDA_TRY(cudaMalloc(&work.p, sizeof(double) * (size_t)(lwork > 0 ? lwork : 1)));
-    XM_CUDA_TRY(cudaMalloc(&info.p, sizeof(int)));
-    XM_CUSOLVER_TRY(cusolverDnDpotrf(cs, CUBLAS_FILL_MODE_LOWER, m, Sbar, N, work.as<double>(), lwork,
-                                     info.as<int>()));
     int hinfo = 0;
-    XM_CUDA_TRY(cudaMemcpyAsync(&hinfo, info.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-    XM_CUDA_TRY(cudaStreamSynchronize(st));
+    if (m >= XM_BUILD_SPLIT_MIN_N) {
+      XM_TRY(split_potrf(ctx, Sbar, N, m, &hinfo));
+    } else {
+      DevBuf fail;
+      XM_CUDA_TRY(cudaMalloc(&fail.p, sizeof(int)));
+      XM_CUDA_TRY(cudaMemsetAsync(fail.p, 0, sizeof(int), st));
+      XM_TRY(dense_potrf(ctx, Sbar, N, m, fail.as<int>(), &hinfo));
+    }
     if (hinfo != 0)
       return set_error(XM_EDISCONNECTED, "translation Schur block not positive definite (minor %d)", hinfo);
   }
@@ -613,19 +601,12 @@ xm_status schur_S_factor(xm_ctx* ctx, int N, int M, const int32_t* cam, const do
 xm_status schur_S_solve(xm_ctx* ctx, int N, const double* S, double* b, int c) {
   cudaStream_t st = ctx->stream;
   if (N > 1 && c > 0) {
-    if (!ctx->cublas) {
-      cublasHandle_t h;
-      XM_CUBLAS_TRY(cublasCreate(&h));
-      ctx->cublas = h;
-    }
-    cublasHandle_t cb = static_cast<cublasHandle_t>(ctx->cublas);
-    XM_CUBLAS_TRY(cublasSetStream(cb, st));
-    const double minus_one = -1.0, one = 1.0;
     const double* Sbar = S + N + 1;
-    XM_CUBLAS_TRY(cublasDtrsm(cb, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N,
-                              CUBLAS_DIAG_NON_UNIT, N - 1, c, &minus_one, Sbar, N, b + 1, N));
-    XM_CUBLAS_TRY(cublasDtrsm(cb, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T,
-                              CUBLAS_DIAG_NON_UNIT, N - 1, c, &one, Sbar, N, b + 1, N));
+    // tbar = -Sbar^{-1} bbar = -L^{-T} L^{-1} bbar
+    XM_TRY(dense_trsm_left_lower(ctx, Sbar, N, b + 1, N, N - 1, c, nullptr));
+    XM_TRY(dense_trsm_left_lower_t(ctx, Sbar, N, b + 1, N, N - 1, c, nullptr));
+    k_negate_cols<<<std::max(1, std::min(c * N / 256 + 1, 1024)), 256, 0, st>>>(N, c, b);
+    XM_CUDA_TRY(cudaGetLastError());
   }
   if (c > 0) XM_CUDA_TRY(cudaMemset2DAsync(b, sizeof(double) * N, 0, sizeof(double), c, st));
   return XM_OK;

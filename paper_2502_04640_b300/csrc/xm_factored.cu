@@ -19,8 +19,6 @@
 // Set-up: Sbar's Cholesky factor L (the camera block left after the landmark elimination), the
 // triangular inverse X = L^{-1} and the tiles of 0 - X^T X = -Sbar^{-1}, all by the build's
 // error-free digit-split products on the BF16 tensor cores (FP64-accurate).
-#include <cublas_v2.h>
-
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -45,21 +43,6 @@ int grid_of(size_t work, int threads, int num_sms, int per_sm = 8) {
 }
 }  // namespace
 
-struct QFact {
-  int N = 0, M = 0;
-  int64_t E = 0;
-  int64_t *loff = nullptr, *coff = nullptr;        // landmark / camera CSR offsets (M+1, N+1)
-  double *lu = nullptr, *lw = nullptr;             // landmark-major u (E x 3) and w (E)
-  int32_t* lc = nullptr;                           // camera of each landmark-major observation
-  double *cu = nullptr, *cw = nullptr;             // camera-major u (E x 3) and w (E)
-  int32_t* cl = nullptr;                           // landmark of each camera-major observation
-  double* dinv = nullptr;                          // 1 / d_k (0 for a landmark without observations)
-  DeviceQ sinv;                                    // packed tiles of -Sbar^{-1} (n = N - 1), FP64
-  double *mk = nullptr, *tbk = nullptr;            // landmark means (M x 8)
-  double *bb = nullptr, *tt = nullptr;             // sweep input / output (sinv.n_pad x R)
-  size_t bytes = 0;
-  double t_setup_s = 0.0;
-};
 
 // ------------------------------------------------------------------ kernels
 // Observation pass kernels take the padded width R of Y (1, 4 or 8) and the used columns r.
@@ -95,7 +78,7 @@ __global__ void k_qf_dinv(int M, const int64_t* __restrict__ loff, const double*
 
 // m_k = sum_{e in k} w_e u_e^T Y_{i_e} / d_k (one thread per landmark)
 template <int R>
-__global__ void k_qf_lmk_a(int M, int r, const int64_t* __restrict__ loff, const double* __restrict__ lu,
+__global__ void k_qf_lmk_a(int M, int r, int ld, const int64_t* __restrict__ loff, const double* __restrict__ lu,
                            const double* __restrict__ lw, const int32_t* __restrict__ lc,
                            const double* __restrict__ dinv, const double* __restrict__ Y,
                            double* __restrict__ mk, const int* skip) {
@@ -105,11 +88,11 @@ __global__ void k_qf_lmk_a(int M, int r, const int64_t* __restrict__ loff, const
 #pragma unroll
     for (int j = 0; j < R; ++j) acc[j] = 0.0;
     for (int64_t x = loff[k]; x < loff[k + 1]; ++x) {
-      const double* y = Y + (size_t)3 * lc[x] * r;
+      const double* y = Y + (size_t)3 * lc[x] * ld;
       const double u0 = lu[3 * x], u1 = lu[3 * x + 1], u2 = lu[3 * x + 2], we = lw[x];
 #pragma unroll
       for (int j = 0; j < R; ++j)
-        if (j < r) acc[j] += we * (u0 * y[j] + u1 * y[r + j] + u2 * y[2 * r + j]);
+        if (j < r) acc[j] += we * (u0 * y[j] + u1 * y[ld + j] + u2 * y[2 * ld + j]);
     }
     const double di = dinv[k];
 #pragma unroll
@@ -146,7 +129,7 @@ __global__ void k_qf_lmk_t(int M, const int64_t* __restrict__ loff, const double
 // OUT = true:  (Q Y)_i += sum w_e u_e (a_e - m_k + t_i - tb_k); t's row i - 1 is then cleared
 //              for the next accumulating sweep.
 template <int R, bool OUT>
-__global__ void k_qf_cam(int N, int r, const int64_t* __restrict__ coff, const double* __restrict__ cu,
+__global__ void k_qf_cam(int N, int r, int ld, const int64_t* __restrict__ coff, const double* __restrict__ cu,
                          const double* __restrict__ cw, const int32_t* __restrict__ cl,
                          const double* __restrict__ Y, const double* __restrict__ mk,
                          const double* __restrict__ tbk, double* __restrict__ tt,
@@ -159,9 +142,9 @@ __global__ void k_qf_cam(int N, int r, const int64_t* __restrict__ coff, const d
 #pragma unroll
     for (int j = 0; j < R; ++j) {
       const bool on = j < r;
-      y[0][j] = on ? Y[(size_t)(3 * i) * r + j] : 0.0;
-      y[1][j] = on ? Y[(size_t)(3 * i + 1) * r + j] : 0.0;
-      y[2][j] = on ? Y[(size_t)(3 * i + 2) * r + j] : 0.0;
+      y[0][j] = on ? Y[(size_t)(3 * i) * ld + j] : 0.0;
+      y[1][j] = on ? Y[(size_t)(3 * i + 1) * ld + j] : 0.0;
+      y[2][j] = on ? Y[(size_t)(3 * i + 2) * ld + j] : 0.0;
       ti[j] = (OUT && i > 0) ? tt[(size_t)(i - 1) * R + j] : 0.0;
     }
     double acc[OUT ? 3 : 1][R];
@@ -196,7 +179,7 @@ __global__ void k_qf_cam(int N, int r, const int64_t* __restrict__ coff, const d
         for (int a = 0; a < 3; ++a)
 #pragma unroll
           for (int j = 0; j < R; ++j)
-            if (j < r) W[(size_t)(3 * i + a) * r + j] += acc[a][j];
+            if (j < r) W[(size_t)(3 * i + a) * ld + j] += acc[a][j];
         if (i > 0)
 #pragma unroll
           for (int j = 0; j < R; ++j) tt[(size_t)(i - 1) * R + j] = 0.0;
@@ -266,15 +249,7 @@ xm_status qfact_build(xm_ctx* ctx, int N, int M, int64_t E, const int32_t* cam, 
     XM_CUDA_TRY(cudaMemsetAsync(X.p, 0, sizeof(double) * (size_t)m * m, st));
     k_qf_eye<<<grid_of((size_t)m, 256, ctx->num_sms), 256, 0, st>>>(m, X.as<double>());
     XM_CUDA_TRY(cudaGetLastError());
-    if (!ctx->cublas) {   // the triangular solve forms its diagonal-block inverses with it
-      cublasHandle_t h;
-      if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS)
-        return set_error(XM_ECUDA, "factored operator: cublasCreate failed");
-      ctx->cublas = h;
-    }
-    if (cublasSetStream(static_cast<cublasHandle_t>(ctx->cublas), st) != CUBLAS_STATUS_SUCCESS)
-      return set_error(XM_ECUDA, "factored operator: cublasSetStream failed");
-    XM_TRY(split_trsm(ctx, ctx->cublas, S.as<double>() + N + 1, N, X.as<double>(), m, m, m));
+    XM_TRY(split_trsm(ctx, S.as<double>() + N + 1, N, X.as<double>(), m, m, m));
     // tiles of 0 - X^T X; q.n = m rows
     DeviceQ& q = f.sinv;
     q.N = 0;
@@ -300,14 +275,14 @@ xm_status qfact_build(xm_ctx* ctx, int N, int M, int64_t E, const int32_t* cam, 
 }
 
 template <int R>
-static xm_status qfact_apply_t(xm_ctx* ctx, const QFact& f, int r, const double* Y, double* W,
+static xm_status qfact_apply_t(xm_ctx* ctx, const QFact& f, int r, int ld, const double* Y, double* W,
                                const int* skip, cudaStream_t st) {
   const int gl = grid_of((size_t)std::max(f.M, 1), 128, ctx->num_sms, 16);
   const int gc = grid_of((size_t)f.N * 32, 256, ctx->num_sms, 16);
   if (f.M > 0)
-    k_qf_lmk_a<R><<<gl, 128, 0, st>>>(f.M, r, f.loff, f.lu, f.lw, f.lc, f.dinv, Y, f.mk, skip);
+    k_qf_lmk_a<R><<<gl, 128, 0, st>>>(f.M, r, ld, f.loff, f.lu, f.lw, f.lc, f.dinv, Y, f.mk, skip);
   if (f.N > 1) {
-    k_qf_cam<R, false><<<gc, 256, 0, st>>>(f.N, r, f.coff, f.cu, f.cw, f.cl, Y, f.mk, f.tbk, f.tt,
+    k_qf_cam<R, false><<<gc, 256, 0, st>>>(f.N, r, ld, f.coff, f.cu, f.cw, f.cl, Y, f.mk, f.tbk, f.tt,
                                            f.bb, nullptr, skip);
     XM_CUDA_TRY(cudaGetLastError());
     XM_TRY(qy_launch(ctx, f.sinv, XM_FP64, R, f.bb, f.tt, skip, st));   // t = -Sbar^{-1} bbar
@@ -316,18 +291,19 @@ static xm_status qfact_apply_t(xm_ctx* ctx, const QFact& f, int r, const double*
   } else if (f.M > 0) {
     XM_CUDA_TRY(cudaMemsetAsync(f.tbk, 0, sizeof(double) * 8 * (size_t)f.M, st));
   }
-  k_qf_cam<R, true><<<gc, 256, 0, st>>>(f.N, r, f.coff, f.cu, f.cw, f.cl, Y, f.mk, f.tbk, f.tt, f.bb,
+  k_qf_cam<R, true><<<gc, 256, 0, st>>>(f.N, r, ld, f.coff, f.cu, f.cw, f.cl, Y, f.mk, f.tbk, f.tt, f.bb,
                                         W, skip);
   XM_CUDA_TRY(cudaGetLastError());
   return XM_OK;
 }
 
-// W += Q Y for an n x r row-major FP64 Y (W accumulates, like the dense sweep).
-xm_status qfact_apply(xm_ctx* ctx, const QFact& f, int r, const double* Y, double* W, const int* skip,
-                      cudaStream_t st) {
-  if (r == 1) return qfact_apply_t<1>(ctx, f, r, Y, W, skip, st);
-  if (r <= 4) return qfact_apply_t<4>(ctx, f, r, Y, W, skip, st);
-  return qfact_apply_t<8>(ctx, f, r, Y, W, skip, st);
+// W += Q Y for an FP64 Y whose first r columns are used, rows of ld doubles (W accumulates, like
+// the dense sweep; the padded layout of the solver has ld = R).
+xm_status qfact_apply(xm_ctx* ctx, const QFact& f, int r, int ld, const double* Y, double* W,
+                      const int* skip, cudaStream_t st) {
+  if (r == 1) return qfact_apply_t<1>(ctx, f, r, ld, Y, W, skip, st);
+  if (r <= 4) return qfact_apply_t<4>(ctx, f, r, ld, Y, W, skip, st);
+  return qfact_apply_t<8>(ctx, f, r, ld, Y, W, skip, st);
 }
 
 }  // namespace xm
@@ -365,7 +341,7 @@ xm_status xm_qy_factored(xm_ctx* c, const xm_qfact* f, int r, const double* Y, d
   if (r < 1 || r > XM_MAX_RANK) return set_error(XM_EINVAL, "xm_qy_factored: r=%d not in [1, %d]", r, XM_MAX_RANK);
   XM_CUDA_TRY(cudaSetDevice(c->device));
   XM_CUDA_TRY(cudaMemsetAsync(W, 0, sizeof(double) * (size_t)3 * f->f.N * r, c->stream));
-  return qfact_apply(c, f->f, r, Y, W, nullptr, c->stream);
+  return qfact_apply(c, f->f, r, r, Y, W, nullptr, c->stream);
 }
 
 xm_status xm_qfact_info(const xm_qfact* f, int* N, int* M, int64_t* E, size_t* bytes, double* t_setup_s) {

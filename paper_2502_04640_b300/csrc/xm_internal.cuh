@@ -55,6 +55,8 @@ __host__ __device__ inline int64_t tile_index(int nt, int I, int J) {
   return (int64_t)I * nt - (int64_t)I * (I - 1) / 2 + (J - I);
 }
 
+struct QFact;
+
 struct DeviceQ {
   int N = 0, n = 0, n_pad = 0, nt = 0;
   int64_t ntiles = 0;
@@ -64,7 +66,33 @@ struct DeviceQ {
   __nv_bfloat16* q16 = nullptr;     // packed BF16 tiles
   int build_path = 0;               // XM_BUILD_* of the rank-(N-1) update that built it
   double t_update_s = 0.0;          // device time of that update (digit split + tensor cores)
+  QFact* fact = nullptr;            // factored operator (XM_STORE_FACTORED): FP64 products
+                                    // when there is no FP64 tile copy
 };
+
+// Factored Q operator (xm_factored.cu): observations in landmark- and camera-major order, the
+// landmark weight sums and the packed FP64 tiles of -Sbar^{-1}.
+struct QFact {
+  int N = 0, M = 0;
+  int64_t E = 0;
+  int64_t *loff = nullptr, *coff = nullptr;        // landmark / camera CSR offsets (M+1, N+1)
+  double *lu = nullptr, *lw = nullptr;             // landmark-major u (E x 3) and w (E)
+  int32_t* lc = nullptr;                           // camera of each landmark-major observation
+  double *cu = nullptr, *cw = nullptr;             // camera-major u (E x 3) and w (E)
+  int32_t* cl = nullptr;                           // landmark of each camera-major observation
+  double* dinv = nullptr;                          // 1 / d_k (0 for a landmark without observations)
+  DeviceQ sinv;                                    // packed tiles of -Sbar^{-1} (n = N - 1), FP64
+  double *mk = nullptr, *tbk = nullptr;            // landmark means (M x 8)
+  double *bb = nullptr, *tt = nullptr;             // sweep input / output (sinv.n_pad x 8)
+  size_t bytes = 0;
+  double t_setup_s = 0.0;
+};
+xm_status qfact_build(xm_ctx* ctx, int N, int M, int64_t E, const int32_t* cam, const int32_t* lmk,
+                      const double* ukp, const double* w, QFact& f);
+void qfact_release(QFact& f);
+// W += Q Y (FP64; first r columns of rows of ld doubles; skip as for qy_launch)
+xm_status qfact_apply(xm_ctx* ctx, const QFact& f, int r, int ld, const double* Y, double* W,
+                      const int* skip, cudaStream_t st);
 
 }  // namespace xm
 
@@ -116,13 +144,31 @@ bool split_update_fits(int K, int n);
 xm_status split_update_pack(xm_ctx* ctx, const double* C, int ldc, int K, const double* P,
                             DeviceQ& q, double* acc64);
 // X <- L^{-1} X (L lower triangular m x m, X m x n, both column-major): blocked forward
-// substitution with FP64 diagonal blocks (cuBLAS handle) and tensor-core block updates.
-xm_status split_trsm(xm_ctx* ctx, void* cublas, const double* L, int ldl, double* X, int ldx,
-                     int m, int n);
+// substitution with FP64-formed diagonal-block inverses and tensor-core block updates.
+xm_status split_trsm(xm_ctx* ctx, const double* L, int ldl, double* X, int ldx, int m, int n);
 // In-place Cholesky factor (lower) of the SPD m x m A (column-major): blocked, FP64 diagonal
-// blocks and panels, tensor-core trailing updates; *minor = first failing leading minor or 0.
-xm_status split_potrf(xm_ctx* ctx, void* cublas, void* cusolver, double* A, int lda, int m,
-                      int* minor);
+// blocks and panels (dense_*), tensor-core trailing updates; *minor = first failing leading
+// minor or 0.
+xm_status split_potrf(xm_ctx* ctx, double* A, int lda, int m, int* minor);
+
+// ------------------------------------------------------------------ FP64 dense kernels (xm_dense.cu)
+// All column-major.  fail: optional device flag; when non-zero the launches do nothing.
+// C = alpha op(A) op(B) + beta C (op = transpose when ta / tb; lower: only C's lower triangle;
+// supported: NN, NT, TN and the lower NT / TN forms).
+xm_status dense_gemm(xm_ctx* ctx, bool ta, bool tb, bool lower, int m, int n, int k, double alpha,
+                     const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc,
+                     const int* fail);
+// In-place Cholesky factor (lower) of an SPD m x m A; fail_dev a zeroed device int; *minor =
+// first failing leading minor (0: success).  Synchronous.
+xm_status dense_potrf(xm_ctx* ctx, double* A, int lda, int m, int* fail_dev, int* minor);
+// A <- A L^{-T} (A rows x b, L lower b x b, b <= 512).
+xm_status dense_trsm_right_lower_t(xm_ctx* ctx, const double* L, int ldl, double* A, int lda, int rows,
+                                   int b, const int* fail);
+// X <- L^{-1} X and X <- L^{-T} X (X m x n, L lower m x m).
+xm_status dense_trsm_left_lower(xm_ctx* ctx, const double* L, int ldl, double* X, int ldx, int m, int n,
+                                const int* fail);
+xm_status dense_trsm_left_lower_t(xm_ctx* ctx, const double* L, int ldl, double* X, int ldx, int m, int n,
+                                  const int* fail);
 
 // ------------------------------------------------------------------ adjoint support (xm_build.cu)
 // Index and value checks of the observation arrays (synchronous; XM_EINVAL on a bad entry).
@@ -196,11 +242,12 @@ __device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src_gmem, u
 __device__ __forceinline__ void named_bar_sync(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
-// Entry (r, c) of Q from the packed FP64 tiles (upper-triangle tiles, halved diagonal).
-__device__ __forceinline__ double q_entry(const double* __restrict__ q64, int nt, int r, int c) {
+// Entry (r, c) of Q from the packed tiles (upper-triangle tiles, halved diagonal).
+template <typename TQ>
+__device__ __forceinline__ double q_entry(const TQ* __restrict__ tiles, int nt, int r, int c) {
   if (r > c) { const int t = r; r = c; c = t; }
   const int I = r / TILE, J = c / TILE, a = r % TILE, b = c % TILE;
-  const double v = q64[tile_index(nt, I, J) * TILE * TILE + (int64_t)a * TILE + b];
+  const double v = double(tiles[tile_index(nt, I, J) * TILE * TILE + (int64_t)a * TILE + b]);
   return (I == J && a == b) ? 2.0 * v : v;
 }
 

@@ -36,12 +36,11 @@
 // TMEM accumulators (all 512 columns); warps 2..17 read finished chunks with tcgen05.ld (four
 // warps per TMEM lane quarter, 64 columns each) while the next chunk accumulates.  Every wait is
 // bounded; a stalled pipeline raises DEV_TIMEOUT, drains its copies and frees tensor memory.
-#include <cublas_v2.h>
 #include <cuda.h>
-#include <cusolverDn.h>
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "xm_internal.cuh"
@@ -647,16 +646,21 @@ __global__ void k_oz_negate(double* __restrict__ v, size_t count) {
 // k_oz_trinv_leaf; then, leaf row by leaf row, X_ik = -L_ii^{-1} sum_{k <= l < i} L_il X_lk
 // (FP64 cuBLAS products, 7 GFLOP at 10 blocks of 1024).  The batched library triangular solve
 // this replaces cost 0.9-1.5 s at its first call in a process on a fresh B300 machine.
-static xm_status tri_inverse_blocks(xm_ctx* ctx, void* cublas, const double* L, int ldl, int m, int b,
-                                    double* Li) {
+static xm_status tri_inverse_blocks(xm_ctx* ctx, const double* L, int ldl, int m, int b, double* Li) {
   cudaStream_t st = ctx->stream;
-  cublasHandle_t cb = static_cast<cublasHandle_t>(cublas);
   const int nb = (m + b - 1) / b;
-  static int configured_dev = -1;
-  if (configured_dev != ctx->device) {
-    XM_CUDA_TRY(cudaFuncSetAttribute(k_oz_trinv_leaf, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)(sizeof(double) * OZ_LEAF * OZ_LEAF)));
-    configured_dev = ctx->device;
+  {
+    constexpr int MAX_DEVICES = 64;
+    static std::mutex mu;
+    static bool configured[MAX_DEVICES] = {};
+    if (ctx->device < 0 || ctx->device >= MAX_DEVICES)
+      return set_error(XM_EINVAL, "triangular inverse: device %d out of range", ctx->device);
+    std::lock_guard<std::mutex> lock(mu);
+    if (!configured[ctx->device]) {
+      XM_CUDA_TRY(cudaFuncSetAttribute(k_oz_trinv_leaf, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(sizeof(double) * OZ_LEAF * OZ_LEAF)));
+      configured[ctx->device] = true;
+    }
   }
   XM_CUDA_TRY(cudaMemsetAsync(Li, 0, sizeof(double) * (size_t)nb * b * b, st));
   k_oz_trinv_leaf<<<(m + OZ_LEAF - 1) / OZ_LEAF, OZ_LEAF, sizeof(double) * OZ_LEAF * OZ_LEAF, st>>>(
@@ -664,7 +668,6 @@ static xm_status tri_inverse_blocks(xm_ctx* ctx, void* cublas, const double* L, 
   XM_CUDA_TRY(cudaGetLastError());
   DevMem T;
   XM_CUDA_TRY(cudaMalloc(&T.p, sizeof(double) * (size_t)OZ_LEAF * b));
-  const double one = 1.0, zero = 0.0, minus_one = -1.0;
   for (int j = 0; j < nb; ++j) {
     const int o = j * b, bj = std::min(b, m - o);
     const double* Ljj = L + (size_t)o + (size_t)o * ldl;
@@ -672,11 +675,10 @@ static xm_status tri_inverse_blocks(xm_ctx* ctx, void* cublas, const double* L, 
     for (int r0 = OZ_LEAF; r0 < bj; r0 += OZ_LEAF) {
       const int hi = std::min(OZ_LEAF, bj - r0);
       // T = L[r0:r0+hi, 0:r0] X[0:r0, 0:r0]; X[r0:r0+hi, 0:r0] = -X[r0:, r0:] T
-      if (cublasDgemm(cb, CUBLAS_OP_N, CUBLAS_OP_N, hi, r0, r0, &one, Ljj + r0, ldl, X, b, &zero,
-                      T.as<double>(), OZ_LEAF) != CUBLAS_STATUS_SUCCESS ||
-          cublasDgemm(cb, CUBLAS_OP_N, CUBLAS_OP_N, hi, r0, hi, &minus_one, X + r0 + (size_t)r0 * b, b,
-                      T.as<double>(), OZ_LEAF, &zero, X + r0, b) != CUBLAS_STATUS_SUCCESS)
-        return set_error(XM_ECUDA, "cublasDgemm (diagonal block inverse %d) failed", j);
+      XM_TRY(dense_gemm(ctx, false, false, false, hi, r0, r0, 1.0, Ljj + r0, ldl, X, b, 0.0,
+                        T.as<double>(), OZ_LEAF, nullptr));
+      XM_TRY(dense_gemm(ctx, false, false, false, hi, r0, hi, -1.0, X + r0 + (size_t)r0 * b, b,
+                        T.as<double>(), OZ_LEAF, 0.0, X + r0, b, nullptr));
     }
   }
   k_oz_negate<<<ctx->num_sms * 4, 256, 0, st>>>(Li, (size_t)nb * b * b);
@@ -696,8 +698,7 @@ static xm_status tri_inverse_blocks(xm_ctx* ctx, void* cublas, const double* L, 
 // Blocks of 1024 rather than 512 halve the FP64 level folds per tensor-core flop of the block
 // updates (10154 x 30465: 0.70 -> 0.63 s for the whole update; 2048 is no faster and its
 // difference from the FP64 build is 3x larger).
-xm_status split_trsm(xm_ctx* ctx, void* cublas, const double* L, int ldl, double* X, int ldx,
-                     int m, int n) {
+xm_status split_trsm(xm_ctx* ctx, const double* L, int ldl, double* X, int ldx, int m, int n) {
   cudaStream_t st = ctx->stream;
   const int b = OZ_TRSM_BLOCK;                               // a multiple of OZ_BM and OZ_BK
   const int K_pad = b;
@@ -716,7 +717,7 @@ xm_status split_trsm(xm_ctx* ctx, void* cublas, const double* L, int ldl, double
 
   // -L_jj^{-1} for every diagonal block (FP64, column-major b x b each)
   XM_CUDA_TRY(cudaMalloc(&Li.p, sizeof(double) * (size_t)nb * b * b));
-  XM_TRY(tri_inverse_blocks(ctx, cublas, L, ldl, m, b, Li.as<double>()));
+  XM_TRY(tri_inverse_blocks(ctx, L, ldl, m, b, Li.as<double>()));
 
   auto gemm = [&](const int2* tiles, const std::vector<int2>& order, int rowsA, int KB,
                   double* out, int M) -> xm_status {
@@ -787,43 +788,30 @@ namespace xm {
 // as products with explicit inverses of the diagonal blocks doubled the build's difference from
 // the FP64 build at 1500 cameras, to 2.1e-11 of max |Q|.)
 // *minor = 0 on success, else the 1-based order of the first non-positive leading minor.
-xm_status split_potrf(xm_ctx* ctx, void* cublas, void* cusolver, double* A, int lda, int m,
-                      int* minor) {
+xm_status split_potrf(xm_ctx* ctx, double* A, int lda, int m, int* minor) {
   cudaStream_t st = ctx->stream;
-  cublasHandle_t cb = static_cast<cublasHandle_t>(cublas);
-  cusolverDnHandle_t cs = static_cast<cusolverDnHandle_t>(cusolver);
   const int b = OZ_CHOL_BLOCK;
   const int K_pad = b;
   *minor = 0;
-  int lwork = 0;
-  if (cusolverDnDpotrf_bufferSize(cs, CUBLAS_FILL_MODE_LOWER, std::min(b, m), A, lda, &lwork) !=
-      CUSOLVER_STATUS_SUCCESS)
-    return set_error(XM_ECUDA, "cusolverDnDpotrf_bufferSize failed");
   const int rows_max = ((std::max(m - b, 1) + OZ_BN - 1) / OZ_BN) * OZ_BN;   // boxes of 128 and 256 rows
-  DevMem work, info, S, sc, tl;
-  XM_CUDA_TRY(cudaMalloc(&work.p, sizeof(double) * (size_t)std::max(lwork, 1)));
-  XM_CUDA_TRY(cudaMalloc(&info.p, sizeof(int)));
+  DevMem fail, S, sc, tl;
+  XM_CUDA_TRY(cudaMalloc(&fail.p, sizeof(int)));
+  XM_CUDA_TRY(cudaMemsetAsync(fail.p, 0, sizeof(int), st));
   XM_CUDA_TRY(cudaMalloc(&S.p, sizeof(__nv_bfloat16) * (size_t)OZ_SLICES * rows_max * K_pad));
   XM_CUDA_TRY(cudaMalloc(&sc.p, sizeof(int) * (size_t)rows_max));
   XM_CUDA_TRY(cudaMalloc(&tl.p, sizeof(int2) * (size_t)(rows_max / OZ_BM) * (rows_max / OZ_BN)));
-  const double one = 1.0;
   std::vector<int2> order;
   for (int k0 = 0; k0 < m; k0 += b) {
     const int bk = std::min(b, m - k0);
     double* Akk = A + k0 + (size_t)k0 * lda;
-    if (cusolverDnDpotrf(cs, CUBLAS_FILL_MODE_LOWER, bk, Akk, lda, work.as<double>(), lwork,
-                         info.as<int>()) != CUSOLVER_STATUS_SUCCESS)
-      return set_error(XM_ECUDA, "cusolverDnDpotrf (diagonal block %d) failed", k0 / b);
+    // FP64 diagonal block (own blocked factor) and its panel (own substitution)
     int h = 0;
-    XM_CUDA_TRY(cudaMemcpyAsync(&h, info.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-    XM_CUDA_TRY(cudaStreamSynchronize(st));
-    if (h != 0) { *minor = k0 + h; return XM_OK; }
+    XM_TRY(dense_potrf(ctx, Akk, lda, bk, fail.as<int>(), &h));
+    if (h != 0) { *minor = h + k0; return XM_OK; }
     const int rest = m - k0 - bk;
     if (rest == 0) break;
     double* P = A + (k0 + bk) + (size_t)k0 * lda;              // panel, rest x bk
-    if (cublasDtrsm(cb, CUBLAS_SIDE_RIGHT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T, CUBLAS_DIAG_NON_UNIT,
-                    rest, bk, &one, Akk, lda, P, lda) != CUBLAS_STATUS_SUCCESS)
-      return set_error(XM_ECUDA, "cublasDtrsm (panel %d) failed", k0 / b);
+    XM_TRY(dense_trsm_right_lower_t(ctx, Akk, lda, P, lda, rest, bk, nullptr));
     const int rows = ((rest + OZ_BN - 1) / OZ_BN) * OZ_BN;
     const size_t stride = (size_t)rows * K_pad;
     const int nI = (rest + OZ_BM - 1) / OZ_BM, nJ = (rest + OZ_BN - 1) / OZ_BN;

@@ -601,10 +601,15 @@ static xm_status dispatch_r(xm_ctx* ctx, const TQ* tiles, const DeviceQ& q, int 
 
 xm_status qy_launch(xm_ctx* ctx, const DeviceQ& q, int prec, int R, const void* Y, void* W,
                     const int* skip, cudaStream_t st) {
-  if (q.ntiles == 0) return XM_OK;
+  if (q.ntiles == 0 && !q.fact) return XM_OK;
   switch (prec) {
     case XM_FP64:
-      if (!q.q64) return set_error(XM_EINVAL, "sweep: Q has no FP64 copy");
+      if (!q.q64) {
+        // the factored operator (App. A in product form) stands in for the FP64 tiles
+        if (q.fact) return qfact_apply(ctx, *q.fact, R, R, static_cast<const double*>(Y),
+                                       static_cast<double*>(W), skip, st);
+        return set_error(XM_EINVAL, "sweep: Q has no FP64 copy and no factored operator");
+      }
       return dispatch_r<double, 8>(ctx, q.q64, q, R, Y, W, skip, st);
     case XM_FP32_BULK:
       if (!q.q32) return set_error(XM_EINVAL, "sweep: Q has no FP32 copy");

@@ -149,7 +149,8 @@ static void tri_eigvec(int k, const double* a, const double* b, double th, std::
 // ------------------------------------------------------------------ the solver
 // Block-Jacobi preconditioner of the tCG, per camera: B_i = 2 Q_ii and Minv_i = B_i^-1 with the
 // eigenvalues of Q_ii (positive semidefinite) clamped below at 1e-6 of the largest; N x 9 each.
-__global__ void k_tcg_precond_blocks(int N, const double* __restrict__ q64, int nt, double* __restrict__ Minv,
+template <typename TQ>
+__global__ void k_tcg_precond_blocks(int N, const TQ* __restrict__ q64, int nt, double* __restrict__ Minv,
                                      double* __restrict__ B) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
@@ -247,7 +248,8 @@ k_grad_epi_rtr(int N, const T* __restrict__ Y, T* __restrict__ W, T* __restrict_
 
 // Minv_i = inverse of the 3 x 3 diagonal block Z_ii = Q_ii - Lambda_i + dreg_i e3 e3^T of the
 // certificate matrix, eigenvalues clamped at 1e-6 of the largest (block-Jacobi preconditioner).
-__global__ void k_zblock_precond(int N, const double* __restrict__ q64, int nt,
+template <typename TQ>
+__global__ void k_zblock_precond(int N, const TQ* __restrict__ q64, int nt,
                                  const double* __restrict__ Lam, double* __restrict__ Minv) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
@@ -527,7 +529,9 @@ struct Solver {
     if (o.precond) {
       XM_CUDA_TRY(cudaMalloc(&pcMinv, sizeof(double) * 9 * (size_t)N));
       XM_CUDA_TRY(cudaMalloc(&pcB, sizeof(double) * 9 * (size_t)N));
-      k_tcg_precond_blocks<<<nb_cam, CAM_THREADS, 0, st>>>(N, q.q64, q.nt, pcMinv, pcB);
+      // Q's 3 x 3 diagonal blocks: FP64 tiles, else the FP32 ones (a preconditioner)
+      if (q.q64) k_tcg_precond_blocks<double><<<nb_cam, CAM_THREADS, 0, st>>>(N, q.q64, q.nt, pcMinv, pcB);
+      else k_tcg_precond_blocks<float><<<nb_cam, CAM_THREADS, 0, st>>>(N, q.q32, q.nt, pcMinv, pcB);
       ++launches;
       XM_CUDA_TRY(cudaGetLastError());
     }
@@ -953,7 +957,7 @@ struct Solver {
     const double t_cert_before = info.t_cert_s;
     double ld_short = 0.0;
     XM_TRY(certify_t<R, float>(r, XM_FP32_BULK, &ld_short, lam_max, lam_range, 40));
-    if (!q.q64) return XM_OK;   // the preconditioner reads the FP64 diagonal blocks
+    if (!q.q64 && !q.q32) return XM_OK;   // the preconditioner reads Q's diagonal blocks
     const int nn = n_pad, nd = last_nd;
     const float* Vd = static_cast<const float*>(V);
     const size_t blk = (size_t)nn * 4;
@@ -1009,7 +1013,8 @@ struct Solver {
       XM_CUDA_TRY(cudaStreamSynchronize(st));
       return XM_OK;
     };
-    k_zblock_precond<<<nb_cam, CAM_THREADS, 0, st>>>(N, q.q64, q.nt, Lam, lob_minv);
+    if (q.q64) k_zblock_precond<double><<<nb_cam, CAM_THREADS, 0, st>>>(N, q.q64, q.nt, Lam, lob_minv);
+    else k_zblock_precond<float><<<nb_cam, CAM_THREADS, 0, st>>>(N, q.q32, q.nt, Lam, lob_minv);
     k_lob_random<<<gv, CAM_THREADS, 0, st>>>(nn, n, o.seed ^ 0x5DEECE66Dull, X);
     launches += 2;
     deflate(X);
@@ -1587,7 +1592,10 @@ xm_status check_opts(const DeviceQ& q, const xm_opts& o) {
     return set_error(XM_EINVAL, "opts: need 1 <= r0 <= r_max <= %d (r0=%d, r_max=%d)", XM_MAX_RANK,
                      o.r0, o.r_max);
   if (o.prec < XM_FP64 || o.prec > XM_BF16Q_BULK) return set_error(XM_EINVAL, "opts: bad prec %d", o.prec);
-  if (!q.q64) return set_error(XM_EINVAL, "solve: Q needs its FP64 copy (XM_STORE_FP64)");
+  if (!q.q64 && !q.fact)
+    return set_error(XM_EINVAL, "solve: Q needs its FP64 copy (XM_STORE_FP64) or the factored operator");
+  if (o.precond == 1 && !q.q64 && !q.q32)
+    return set_error(XM_EINVAL, "opts: precond = 1 reads Q's diagonal blocks from its FP64 or FP32 tiles");
   if (o.prec != XM_FP64 && !q.q32) return set_error(XM_EINVAL, "solve: mixed precision needs XM_STORE_FP32");
   if (o.prec == XM_BF16Q_BULK && !q.q16) return set_error(XM_EINVAL, "solve: XM_BF16Q_BULK needs XM_STORE_BF16");
   if (o.max_outer < 1 || o.max_tcg < 1 || o.lanczos_max < 1)

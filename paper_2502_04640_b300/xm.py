@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libxm.so")
 XM_OK, XM_EINVAL, XM_EDISCONNECTED, XM_ECUDA, XM_ENOMEM, XM_ENOCONV, XM_ENUMERIC, \
     XM_ETIMEOUT, XM_ENOTCERT = range(9)
 XM_FP64, XM_FP32_BULK, XM_BF16Q_BULK = 0, 1, 2
-XM_STORE_FP64, XM_STORE_FP32, XM_STORE_BF16, XM_STORE_ALL = 1, 2, 4, 7
+XM_STORE_FP64, XM_STORE_FP32, XM_STORE_BF16, XM_STORE_ALL, XM_STORE_FACTORED = 1, 2, 4, 7, 8
 XM_MAX_RANK = 8
 XM_BUILD_AUTO, XM_BUILD_FP64, XM_BUILD_SPLIT_BF16 = 0, 1, 2
 STATUS_NAMES = {0: "XM_OK", 1: "XM_EINVAL", 2: "XM_EDISCONNECTED", 3: "XM_ECUDA", 4: "XM_ENOMEM",

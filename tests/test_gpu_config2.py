@@ -68,3 +68,20 @@ def Qo(sc):
     if sc.name not in _Q:
         _Q[sc.name] = O.build_Q_schur(sc.N, sc.M, sc.cam, sc.lmk, sc.ukp, sc.w)
     return _Q[sc.name]
+
+
+def test_config2_fp64_solve_without_a_dense_Q(C, c2):
+    """The 1934-camera solve in FP64 on the factored operator alone (XM_STORE_FACTORED: Q is
+    never formed): the oracle's certified value, dual value and lambda_min."""
+    from paper_2502_04640_b300 import xm
+    sc, ref = c2
+    q = xm.xm_build_Q(C, sc.N, sc.M, *xm.scene_tensors(sc), xm.XM_STORE_FACTORED)
+    out = xm.xm_solve(q, xm.xm_default_opts(prec=xm.XM_FP64))
+    info = out["info"]
+    lm = ref.cert.lam_max_Q
+    assert info["certified"] == 1
+    assert _rel(info["f"], ref.f) <= 1e-6
+    assert abs(info["dual"] - ref.cert.dual) <= 1e-6 * (1 + abs(ref.f))
+    assert abs(info["lambda_min_deflated"] - ref.cert.lam_min_deflated) <= 1e-5 * lm
+    check_at_returned_point(Qo(sc), out)
+    q.free()

@@ -144,3 +144,36 @@ def test_factored_operator_errors(C):
     Y = torch.zeros((18, 9), dtype=torch.float64, device="cuda")
     assert xm.lib().xm_qy_factored(C.h, f.h, 9, Y.data_ptr(), Y.data_ptr()) == xm.XM_EINVAL
     f.free()
+
+
+@pytest.mark.parametrize("mask,prec", [("factored", 0), ("fp32+factored", 1)])
+@pytest.mark.parametrize("scene", ["config1", "outliers"])
+def test_solve_on_the_factored_operator(C, mask, prec, scene):
+    """XM_STORE_FACTORED: every FP64 product (the FP64 RTR, the mixed modes' polish, the
+    certificate's Z products, rounding) goes through the factored operator.  Alone, Q is never
+    formed and the solve runs in FP64; with the FP32 tiles, the bulk phase reads them.  Either
+    way the certified optimum is the oracle's."""
+    from paper_2502_04640_b300 import xm
+    from tests.oracle_checks import check_at_returned_point
+    sc = scenes.config1() if scene == "config1" else scenes.random_scene(
+        90, 4000, noise=0.03, outlier_frac=0.05, seed=21)
+    Qo = O.build_Q_schur(sc.N, sc.M, sc.cam, sc.lmk, sc.ukp, sc.w)
+    ref = O.solve(Qo, r0=4)
+    store = xm.XM_STORE_FACTORED | (xm.XM_STORE_FP32 if mask == "fp32+factored" else 0)
+    q = xm.xm_build_Q(C, sc.N, sc.M, *xm.scene_tensors(sc), store)
+    assert q.mask == store
+    out = xm.xm_solve(q, xm.xm_default_opts(prec=prec))
+    info = out["info"]
+    assert info["certified"] == int(ref.certified) == 1
+    assert abs(info["f"] - ref.f) <= 1e-6 * (1 + abs(ref.f))
+    assert abs(info["lambda_min_deflated"] - ref.cert.lam_min_deflated) <= 1e-5 * ref.cert.lam_max_Q
+    if ref.eta <= 1e-9:
+        assert np.abs(out["R"].cpu().numpy() - ref.R).max() <= 1e-5
+    check_at_returned_point(Qo, out)
+    if prec == 0:
+        assert info["n_sweeps_fp64"] == info["n_sweeps"]
+    if mask == "factored":                 # no FP32 tiles for a mixed-mode solve
+        with pytest.raises(xm.XmError) as e:
+            xm.xm_solve(q, xm.xm_default_opts(prec=xm.XM_FP32_BULK))
+        assert e.value.status == xm.XM_EINVAL
+    q.free()
