@@ -1021,6 +1021,16 @@ def main():
                     "R_max_abs": float((o["R"] - ref["R"]).abs().max()),
                     "s_max_rel": float(((o["s"] - ref["s"]).abs() / ref["s"].abs()).max())}
         extra["fp32_vs_fp64"] = errs(out)
+        # the plain FP64 form on the factored operator alone (Q never formed)
+        try:
+            qf = xm.xm_build_Q(ctx, sc.N, sc.M, *xm.scene_tensors(sc, local), xm.XM_STORE_FACTORED)
+            ff = xm.xm_solve(qf, xm.xm_default_opts(prec=0, **wopts))
+            extra["fp64_factored_solve_s"] = ff["info"]["t_solve_s"]
+            extra["fp64_factored_certified"] = ff["info"]["certified"]
+            extra["fp64_factored_vs_fp64"] = errs(ff)
+            qf.free()
+        except Exception as e:      # noqa: BLE001 - reported, the main number stands
+            extra["fp64_factored_error"] = f"{type(e).__name__}: {e}"
         if prec != 2:
             b = xm.xm_solve(q, xm.xm_default_opts(prec=2, **wopts))
             extra["bf16q_solve_s"] = b["info"]["t_solve_s"]
