@@ -29,7 +29,7 @@
 extern "C" {
 #endif
 
-#define XM_ABI_VERSION 1
+#define XM_ABI_VERSION 2
 #define XM_MAX_RANK 8   /* largest BM rank r the kernels handle (Alg. 1 stops there) */
 
 typedef struct xm_ctx xm_ctx;   /* opaque: device, stream, workspaces */
@@ -261,10 +261,12 @@ long xm_last_launch_count(void);
  * Y0: NULL for Alg. 1's [I_3, ..., I_3] start padded with zero columns to rank r0, else an
  * n x r_in row-major start (made feasible by the retraction).  Outputs (device, may be NULL):
  * Y_out n x XM_MAX_RANK (columns >= rank are zero), R_out N x 3 x 3 and s_out N of the
- * rounded solution (Sec. 2.2).  Synchronous.  Returns XM_ENOTCERT if the staircase stops
- * at r_max without a certificate, XM_ENOCONV on the time limit. */
+ * rounded solution (Sec. 2.2), G_out N x 3 x 3 the rounded anchored blocks G_i = s_i R_i (the
+ * scaled rotations of Eq. 4, row-major; what xm_backward differentiates).  Synchronous.  Returns
+ * XM_ENOTCERT if the staircase stops at r_max without a certificate, XM_ENOCONV on the time
+ * limit. */
 xm_status xm_solve(xm_ctx* ctx, const xm_qmat* q, const xm_opts* opts, int r_in,
-                   const double* Y0, double* Y_out, double* R_out, double* s_out,
+                   const double* Y0, double* Y_out, double* R_out, double* s_out, double* G_out,
                    xm_info* info);
 
 /* ---- certificate (Thm. 1) ---------------------------------------------------------------

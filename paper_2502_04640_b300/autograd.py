@@ -19,7 +19,7 @@ class XMSolve(torch.autograd.Function):
         fctx.N, fctx.M, fctx.opts = N, M, backward_opts or opts
         fctx.info = out["info"]
         fctx.save_for_backward(ukp.detach(), w.detach(), cam, lmk)
-        return out["s"][:, None, None] * out["R"]
+        return out["G"]
 
     @staticmethod
     def backward(fctx, dG):

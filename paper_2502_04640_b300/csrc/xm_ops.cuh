@@ -899,6 +899,14 @@ __device__ __forceinline__ void round_block(int i, const double* __restrict__ Yh
   sout[i] = s;
 }
 
+// G_i = s_i R_i (row-major 3 x 3) from the rounded Yhat (n_pad x 4 row-major, Yhat_i = G_i^T)
+static __global__ void k_round_G(int N, const double* __restrict__ Yhat, double* __restrict__ G) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) G[(size_t)9 * i + 3 * a + b] = Yhat[(size_t)(3 * i + b) * 4 + a];
+}
+
 static __global__ void k_round(int N, const double* __restrict__ Yh, const double* __restrict__ O0,
                                double* __restrict__ Rout, double* __restrict__ sout,
                                double* __restrict__ Yhat) {

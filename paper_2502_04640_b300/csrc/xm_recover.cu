@@ -25,7 +25,7 @@ xm_status build_Q(xm_ctx* ctx, int N, int M, int64_t E, const int32_t* cam, cons
                   const double* ukp, const double* w, unsigned mask, DeviceQ& out, double* t_build);
 void free_tiles(DeviceQ& q);
 xm_status solve_impl(xm_ctx* ctx, const DeviceQ& q, const xm_opts& o, int r_in, const double* Y0,
-                     double* Y_out, double* R_out, double* s_out, xm_info* out_info,
+                     double* Y_out, double* R_out, double* s_out, double* G_out, xm_info* out_info,
                      bool certify_only, double* Lambda_out, double* v_out);
 xm_status check_opts(const DeviceQ& q, const xm_opts& o);
 
@@ -253,7 +253,8 @@ extern "C" xm_status xm_solve_xm2(xm_ctx* c, int N, int M, int64_t E, const int3
     if (sb != XM_OK) { free_tiles(q); return sb; }
     xm_status so = check_opts(q, *opts);
     if (so != XM_OK) { free_tiles(q); return so; }
-    xm_status s1 = solve_impl(c, q, *opts, 0, nullptr, nullptr, R_out, s_out, info_first, false, nullptr, nullptr);
+    xm_status s1 = solve_impl(c, q, *opts, 0, nullptr, nullptr, R_out, s_out, nullptr, info_first, false, nullptr,
+                              nullptr);
     free_tiles(q);
     if (s1 != XM_OK && s1 != XM_ENOTCERT && s1 != XM_ENOCONV) return s1;
   }
@@ -328,7 +329,7 @@ extern "C" xm_status xm_solve_xm2(xm_ctx* c, int N, int M, int64_t E, const int3
     xm_status sb = build_Q(c, N2, M2, Ek, cam2.as<int32_t>(), lmk2.as<int32_t>(), ukp2.as<double>(),
                            w2.as<double>(), mask, q, nullptr);
     if (sb != XM_OK) { free_tiles(q); return sb; }
-    s2 = solve_impl(c, q, *opts, 0, nullptr, nullptr, Rs, ss, info_second, false, nullptr, nullptr);
+    s2 = solve_impl(c, q, *opts, 0, nullptr, nullptr, Rs, ss, nullptr, info_second, false, nullptr, nullptr);
     free_tiles(q);
     if (s2 != XM_OK && s2 != XM_ENOTCERT && s2 != XM_ENOCONV) return s2;
   }

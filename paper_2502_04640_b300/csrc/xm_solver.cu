@@ -1228,7 +1228,7 @@ struct Solver {
 
   // ---------------- rounding (Sec. 2.2) and the Eq. 18 / App. E numbers
   template <int R>
-  xm_status round_and_eval(int r, double* R_out, double* s_out) {
+  xm_status round_and_eval(int r, double* R_out, double* s_out, double* G_out) {
     const int nn = n_pad;
     k_gram<double, R><<<grid_gram(), CAM_THREADS, 0, st>>>(nn, (const double*)bY64, d_small,
                                                            ctx->d_partials, ctx->d_counter);
@@ -1276,6 +1276,10 @@ struct Solver {
     k_round<<<nb_cam, CAM_THREADS, 0, st>>>(N, (const double*)bYh, d_small + 128, Rd, sd, (double*)bYc);
     ++launches;
     XM_CUDA_TRY(cudaGetLastError());
+    if (G_out) {   // G_i = s_i R_i: the rounded block of camera i, as Yhat holds it (Yhat_i = G_i^T)
+      k_round_G<<<nb_cam, CAM_THREADS, 0, st>>>(N, (const double*)bYc, G_out);
+      ++launches;
+    }
     if (R_out) XM_CUDA_TRY(cudaMemcpyAsync(R_out, Rd, sizeof(double) * 9 * N, cudaMemcpyDeviceToDevice, st));
     if (s_out) XM_CUDA_TRY(cudaMemcpyAsync(s_out, sd, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
     // rho_hat = f(Yhat) in FP64
@@ -1329,7 +1333,7 @@ static double suboptimality(double rho_hat, double rho) {
 }
 
 xm_status solve_impl(xm_ctx* ctx, const DeviceQ& q, const xm_opts& o, int r_in, const double* Y0,
-                     double* Y_out, double* R_out, double* s_out, xm_info* out_info,
+                     double* Y_out, double* R_out, double* s_out, double* G_out, xm_info* out_info,
                      bool certify_only, double* Lambda_out, double* v_out) {
   Solver S(ctx, q, o);
   S.t_start = std::chrono::steady_clock::now();
@@ -1532,8 +1536,8 @@ xm_status solve_impl(xm_ctx* ctx, const DeviceQ& q, const xm_opts& o, int r_in, 
   }
 
   // ---- rounding, suboptimality
-  XM_TRY(with_R(R, [&] { return S.round_and_eval<4>(r, R_out, s_out); },
-                   [&] { return S.round_and_eval<8>(r, R_out, s_out); }));
+  XM_TRY(with_R(R, [&] { return S.round_and_eval<4>(r, R_out, s_out, G_out); },
+                   [&] { return S.round_and_eval<8>(r, R_out, s_out, G_out); }));
   if (Lambda_out) XM_CUDA_TRY(cudaMemcpyAsync(Lambda_out, S.Lam, sizeof(double) * 9 * N, cudaMemcpyDeviceToDevice, st));
   if (v_out && S.lritz) XM_CUDA_TRY(cudaMemcpyAsync(v_out, S.lritz, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
   if (Y_out) {
@@ -1696,7 +1700,7 @@ xm_status xm_bench_qy(xm_ctx* c, const xm_qmat* q, int prec, int r, int iters, d
 long xm_last_launch_count(void) { return g_last_launches; }
 
 xm_status xm_solve(xm_ctx* c, const xm_qmat* q, const xm_opts* opts, int r_in, const double* Y0,
-                   double* Y_out, double* R_out, double* s_out, xm_info* info) {
+                   double* Y_out, double* R_out, double* s_out, double* G_out, xm_info* info) {
   if (!c || !q) return set_error(XM_EINVAL, "xm_solve: NULL context or Q");
   xm_opts o;
   if (opts) o = *opts; else xm_default_opts(&o);
@@ -1704,7 +1708,7 @@ xm_status xm_solve(xm_ctx* c, const xm_qmat* q, const xm_opts* opts, int r_in, c
   if (Y0 && r_in > o.r_max) o.r_max = r_in;
   XM_TRY(check_opts(q->d, o));
   XM_CUDA_TRY(cudaSetDevice(c->device));
-  return solve_impl(c, q->d, o, r_in, Y0, Y_out, R_out, s_out, info, false, nullptr, nullptr);
+  return solve_impl(c, q->d, o, r_in, Y0, Y_out, R_out, s_out, G_out, info, false, nullptr, nullptr);
 }
 
 xm_status xm_certify(xm_ctx* c, const xm_qmat* q, const xm_opts* opts, int r, const double* Y,
@@ -1717,7 +1721,7 @@ xm_status xm_certify(xm_ctx* c, const xm_qmat* q, const xm_opts* opts, int r, co
   o.r_max = r;
   XM_TRY(check_opts(q->d, o));
   XM_CUDA_TRY(cudaSetDevice(c->device));
-  return solve_impl(c, q->d, o, r, Y, nullptr, nullptr, nullptr, info, true, Lambda_out, v_out);
+  return solve_impl(c, q->d, o, r, Y, nullptr, nullptr, nullptr, nullptr, info, true, Lambda_out, v_out);
 }
 
 xm_status xm_pipeline_host(xm_ctx* c, int N, int M, int64_t E, const int32_t* cam_h,
@@ -1764,7 +1768,7 @@ xm_status xm_pipeline_host(xm_ctx* c, int N, int M, int64_t E, const int32_t* ca
   xm_status stt = xm_build_Q(c, N, M, E, cam, lmk, ukp, w, mask, &q);
   xm_info inf{};
   if (stt == XM_OK) {
-    stt = xm_solve(c, q, &o, 0, nullptr, nullptr, R, s, &inf);
+    stt = xm_solve(c, q, &o, 0, nullptr, nullptr, R, s, nullptr, &inf);
     inf.t_build_s = q->t_build_s;
     if (stt == XM_OK || stt == XM_ENOTCERT) {
       cudaError_t e2 = cudaMemcpyAsync(R_h, R, sizeof(double) * 9 * N, cudaMemcpyDeviceToHost, st);

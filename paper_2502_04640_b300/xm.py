@@ -123,7 +123,7 @@ def lib() -> ctypes.CDLL:
         "xm_bench_qy": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
         "xm_last_launch_count": (ctypes.c_long, []),
-        "xm_solve": (ctypes.c_int, [_P, _P, ctypes.POINTER(XmOpts), ctypes.c_int, _P, _P, _P, _P,
+        "xm_solve": (ctypes.c_int, [_P, _P, ctypes.POINTER(XmOpts), ctypes.c_int, _P, _P, _P, _P, _P,
                                     ctypes.POINTER(XmInfo)]),
         "xm_certify": (ctypes.c_int, [_P, _P, ctypes.POINTER(XmOpts), ctypes.c_int, _P, _P, _P,
                                       ctypes.POINTER(XmInfo)]),
@@ -352,13 +352,15 @@ def xm_last_launch_count() -> int:
 
 
 def xm_solve(q: QMat, opts: XmOpts | None = None, Y0=None, allow_notcert: bool = True):
-    """Returns dict(Y (n x 8 float64), R (N x 3 x 3), s (N), info (dict), status)."""
+    """Returns dict(Y (n x 8 float64), R (N x 3 x 3), s (N), G (N x 3 x 3, G_i = s_i R_i),
+    info (dict), status)."""
     import torch
     dev = f"cuda:{q.ctx.device}"
     opts = opts or xm_default_opts()
     Y = torch.zeros((q.n, XM_MAX_RANK), dtype=torch.float64, device=dev)
     R = torch.zeros((q.N, 3, 3), dtype=torch.float64, device=dev)
     s = torch.zeros((q.N,), dtype=torch.float64, device=dev)
+    G = torch.zeros((q.N, 3, 3), dtype=torch.float64, device=dev)
     info = XmInfo()
     r_in = 0
     if Y0 is not None:
@@ -366,8 +368,8 @@ def xm_solve(q: QMat, opts: XmOpts | None = None, Y0=None, allow_notcert: bool =
         r_in = Y0.shape[1]
     allow = (XM_OK, XM_ENOTCERT, XM_ENOCONV) if allow_notcert else (XM_OK,)
     st = _check(lib().xm_solve(q.ctx.h, q.h, ctypes.byref(opts), r_in, _ptr(Y0), _ptr(Y), _ptr(R),
-                               _ptr(s), ctypes.byref(info)), allow)
-    return dict(Y=Y, R=R, s=s, info=info.as_dict(), status=st)
+                               _ptr(s), _ptr(G), ctypes.byref(info)), allow)
+    return dict(Y=Y, R=R, s=s, G=G, info=info.as_dict(), status=st)
 
 
 def xm_certify(q: QMat, Y, opts: XmOpts | None = None):

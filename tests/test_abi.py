@@ -29,7 +29,7 @@ def test_library_loads_and_exports_every_declared_symbol():
     L = xm.lib()
     missing = [n for n in _declared() if not hasattr(L, n)]
     assert not missing, missing
-    assert L.xm_abi_version() == 1
+    assert L.xm_abi_version() == 2
 
 
 def test_default_opts_and_errors_without_device():
@@ -44,7 +44,7 @@ def test_default_opts_and_errors_without_device():
         assert getattr(o, field) == value, field
     L = xm.lib()
     # NULL arguments are rejected on the host before any device work
-    assert L.xm_solve(None, None, None, 0, None, None, None, None, None) == xm.XM_EINVAL
+    assert L.xm_solve(None, None, None, 0, None, None, None, None, None, None) == xm.XM_EINVAL
     assert b"NULL" in L.xm_last_error()
     h = ctypes.c_void_p()
     st = L.xm_create(ctypes.byref(h), 0, None)

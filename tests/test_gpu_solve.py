@@ -29,6 +29,9 @@ def _solve(C, sc, prec, **kw):
     opts = xm.xm_default_opts(prec=prec, **kw)
     out = xm.xm_solve(q, opts)
     out["R"] = out["R"].cpu().numpy(); out["s"] = out["s"].cpu().numpy(); out["Y"] = out["Y"].cpu().numpy()
+    out["G"] = out["G"].cpu().numpy()
+    # the library's G_i is s_i R_i of the same rounding
+    assert np.abs(out["G"] - out["s"][:, None, None] * out["R"]).max() <= 1e-14 * max(1.0, out["s"].max())
     return q, out
 
 
