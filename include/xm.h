@@ -389,6 +389,15 @@ xm_status xm_batch_free(xm_ctx* ctx, xm_batch* b);
  * <= 900, larger), the fastest; tile_out (8 ints: rows, chunks per class; may be NULL)
  * receives the choice.  Run by xm_solve_batched on first use if not called before. */
 xm_status xm_batch_autotune(xm_ctx* ctx, xm_batch* b, int reps, int* tile_out);
+/* Teams for large scenes.  A scene with n = 3N >= n_min rows runs on a thread-block cluster of
+ * cs CTAs that execute the same solve and split the rows of every Q product between them,
+ * exchanging the results through distributed shared memory (results bit-identical to cs = 1);
+ * the queue is ordered by size, and at the first smaller scene each cluster splits into single
+ * CTAs for the rest of the batch.  cs in {1, 2, 4}, or 0 (the default): 2.  n_min >= 0, or 0
+ * (the default): the smallest n with n^2 >= sum over scenes of n^2 / (SM count), i.e. the scenes
+ * whose products alone outweigh one SM's share; no cluster launch when no scene reaches it.
+ * XM_EINVAL for other values.  Takes effect at the next xm_solve_batched. */
+xm_status xm_batch_cluster(xm_ctx* ctx, xm_batch* b, int cs, int n_min);
 /* Solves every scene.  opts: as xm_solve (r0 <= 4, r_max <= 8; prec is ignored: the FP32-bulk
  * schedule is used; time_limit_s applies per scene).  R_out (sum N x 3 x 3) and s_out (sum N),
  * device pointers, receive the rounded solutions scene after scene in the order of

@@ -64,6 +64,8 @@ struct Params {
   xm_opts o;
   double mu;                       // App. D weight
   unsigned long long time_limit_ns;  // per-scene wall-clock cap (0: none)
+  int team_min_n;                  // scenes with n >= this run on a whole cluster
+  int pf_dist;                     // L2 prefetch distance of the sweeps (rounds; 0: none)
 };
 
 __device__ __forceinline__ unsigned long long gtimer() {
@@ -93,18 +95,97 @@ __device__ __forceinline__ void bsum(double (&v)[K], double* red) {
   __syncthreads();
 }
 
+// ------------------------------------------------------------------ thread-block clusters
+// A large scene may run on a team of CS CTAs, one thread-block cluster (xm_batch_cluster): every
+// CTA of the team executes the same solver on the same data (identical arithmetic, hence
+// identical branches), each computes a contiguous share of the rows of every Q product and
+// stores it into all the team's copies of the product (distributed shared memory), between two
+// cluster barriers.  Only rank 0 claims work, reads the clock for the time limit and writes
+// results.  The queue is ordered by size; at the first scene below the team threshold the
+// cluster splits up for good and its CTAs claim scenes one by one (no cluster barrier or
+// distributed-shared-memory access after that point).
+__device__ __forceinline__ unsigned cl_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned cl_size() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+// CTAs working on the current scene: the cluster size until the cluster splits up, then 1
+__shared__ int s_team;
+__device__ __forceinline__ int team() { return s_team; }
+// this CTA writes the scene's results (alone, or rank 0 of its team)
+__device__ __forceinline__ bool team_lead() { return s_team == 1 || cl_rank() == 0; }
+// all threads of every CTA of the cluster; orders the shared::cluster stores before it
+__device__ __forceinline__ void cl_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t cl_map(const void* p, unsigned rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void cl_st(uint32_t a, float v) {
+  asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
+}
+__device__ __forceinline__ void cl_st(uint32_t a, double v) {
+  asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory");
+}
+__device__ __forceinline__ void cl_st(uint32_t a, int v) {
+  asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+// rows [r0, r1) of this CTA's share of an n-row product (multiples of 8 rows)
+__device__ __forceinline__ void cl_rows(int n, int& r0, int& r1) {
+  const int cs = team(), per = ((n + cs - 1) / cs + 7) & ~7;
+  r0 = min(n, (int)cl_rank() * per);
+  r1 = min(n, r0 + per);
+}
+// copy rows [r0, r1) of ws (R values a row) into the other CTAs' ws, then a cluster barrier
+template <typename T, int R>
+__device__ __forceinline__ void cl_share_rows(T* ws, int r0, int r1) {
+  const unsigned cs = (unsigned)team(), me = cl_rank();
+  __syncthreads();
+  for (unsigned k = 1; k < cs; ++k) {
+    const unsigned peer = (me + k) % cs;
+    const uint32_t base = cl_map(ws, peer);
+    for (int e = r0 * R + threadIdx.x; e < r1 * R; e += NT) cl_st(base + (uint32_t)(e * sizeof(T)), ws[e]);
+  }
+  cl_sync();
+}
+
 // ------------------------------------------------------------------ block-row sweeps
-// ws (n x R) = Q xs with Q dense row-major (ld ldq, rows padded with zeros) and xs (ldq x R)
-// in shared memory, zero beyond row n.  Warp w takes rows [w RPW, w RPW + RPW), then strides
+// L2 prefetch distance of the sweeps, in rounds of NW x RPW rows (set at kernel start)
+__shared__ int s_pfd;
+// bulk prefetch of `bytes` at p into L2 (TMA engine; no completion to wait for).  p 16-byte
+// aligned, bytes a multiple of 16.
+__device__ __forceinline__ void l2_prefetch(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+// lane 0 of each warp: prefetch its row group `pf` rounds ahead (rows rb + pf NW RPW ...)
+template <typename T, int RPW>
+__device__ __forceinline__ void prefetch_rows(const T* Q, int rb, int n, int ldq, int pf) {
+  const int nx = rb + pf * NW * RPW;
+  if (nx < n) l2_prefetch(Q + (size_t)nx * ldq, (uint32_t)(min(RPW, n - nx) * ldq * (int)sizeof(T)));
+}
+// ws (n x R, row-major) = Q xs with Q dense row-major (ld ldq, rows padded with zeros) and xs
+// in shared memory column by column (column j at xs + j ldq, zero beyond row n: a lane's
+// 16-byte loads of consecutive chunks fall in distinct banks).  Warp w takes rows [w RPW, w RPW + RPW), then strides
 // by NW RPW; lane l reads the 16-byte chunks l, l + 32, ... of each row, U chunks per step with
 // all RPW x U loads issued before the FMAs (memory-level parallelism: one CTA streams a whole
 // scene's Q).
 template <int R, int RPW, int U>
-__device__ __forceinline__ void sweep32_t(const float* __restrict__ Q, int n, int ldq,
+__device__ __forceinline__ void sweep32_t(const float* __restrict__ Q, int r0, int n, int ldq,
                                           const float* __restrict__ xs, float* __restrict__ ws) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int nc = ldq >> 2;
-  for (int rb = wid * RPW; rb < n; rb += NW * RPW) {
+  const int pfd = s_pfd;
+  if (lane == 0)
+    for (int d = 1; d < pfd; ++d) prefetch_rows<float, RPW>(Q, r0 + wid * RPW, n, ldq, d);
+  for (int rb = r0 + wid * RPW; rb < n; rb += NW * RPW) {
+    if (lane == 0 && pfd > 0) prefetch_rows<float, RPW>(Q, rb, n, ldq, pfd);
     float acc[RPW][R];
 #pragma unroll
     for (int q = 0; q < RPW; ++q)
@@ -127,9 +208,10 @@ __device__ __forceinline__ void sweep32_t(const float* __restrict__ Q, int n, in
         if (c < nc) {
           float y[4][R];
 #pragma unroll
-          for (int k = 0; k < 4; ++k)
-#pragma unroll
-            for (int j = 0; j < R; ++j) y[k][j] = xs[(4 * c + k) * R + j];
+          for (int j = 0; j < R; ++j) {
+            const float4 t = *reinterpret_cast<const float4*>(xs + (size_t)j * ldq + 4 * c);
+            y[0][j] = t.x; y[1][j] = t.y; y[2][j] = t.z; y[3][j] = t.w;
+          }
 #pragma unroll
           for (int q = 0; q < RPW; ++q)
 #pragma unroll
@@ -165,11 +247,15 @@ __host__ __device__ inline int tile_rpw(int v) { const int t[NTILE] = {2, 4, 4, 
 __host__ __device__ inline int tile_u(int v) { const int t[NTILE] = {4, 1, 2, 4, 1, 2}; return t[v]; }
 
 template <int R, int RPW>
-__device__ __forceinline__ void sweep64_t(const double* __restrict__ Q, int n, int ldq,
+__device__ __forceinline__ void sweep64_t(const double* __restrict__ Q, int r0, int n, int ldq,
                                           const double* __restrict__ xs, double* __restrict__ ws) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int nc = ldq >> 1;
-  for (int rb = wid * RPW; rb < n; rb += NW * RPW) {
+  const int pfd = s_pfd;
+  if (lane == 0)
+    for (int d = 1; d < pfd; ++d) prefetch_rows<double, RPW>(Q, r0 + wid * RPW, n, ldq, d);
+  for (int rb = r0 + wid * RPW; rb < n; rb += NW * RPW) {
+    if (lane == 0 && pfd > 0) prefetch_rows<double, RPW>(Q, rb, n, ldq, pfd);
     double acc[RPW][R];
 #pragma unroll
     for (int q = 0; q < RPW; ++q)
@@ -178,9 +264,10 @@ __device__ __forceinline__ void sweep64_t(const double* __restrict__ Q, int n, i
     for (int c = lane; c < nc; c += 32) {
       double y[2][R];
 #pragma unroll
-      for (int k = 0; k < 2; ++k)
-#pragma unroll
-        for (int j = 0; j < R; ++j) y[k][j] = xs[(2 * c + k) * R + j];
+      for (int j = 0; j < R; ++j) {
+        const double2 t = *reinterpret_cast<const double2*>(xs + (size_t)j * ldq + 2 * c);
+        y[0][j] = t.x; y[1][j] = t.y;
+      }
 #pragma unroll
       for (int q = 0; q < RPW; ++q) {
         if (rb + q < n) {
@@ -206,29 +293,49 @@ __device__ __forceinline__ void sweep64_t(const double* __restrict__ Q, int n, i
 
 // Out of line on purpose: one copy of the tiling variants per R instead of one per call site
 // keeps the solver kernel's instruction footprint small.
+// In a cluster: a barrier first (every CTA has finished reading the previous product from its ws,
+// which the peers are about to write), this CTA's rows, then the exchange.  Each row is still
+// one warp's fixed-order sum, so the product is bit-identical to the one-CTA sweep.
 template <int R>
 __device__ __noinline__ void sweep32(int tile, const float* Q, int n, int ldq, const float* xs, float* ws) {
-  switch (tile) {
-    case 0: sweep32_t<R, 2, 4>(Q, n, ldq, xs, ws); break;
-    case 1: sweep32_t<R, 4, 1>(Q, n, ldq, xs, ws); break;
-    case 2: sweep32_t<R, 4, 2>(Q, n, ldq, xs, ws); break;
-    case 3: sweep32_t<R, 4, 4>(Q, n, ldq, xs, ws); break;
-    case 4: sweep32_t<R, 8, 1>(Q, n, ldq, xs, ws); break;
-    default: sweep32_t<R, 8, 2>(Q, n, ldq, xs, ws); break;
+  int r0 = 0, r1 = n;
+  const bool clu = team() > 1;
+  if (clu) {
+    cl_sync();
+    cl_rows(n, r0, r1);
   }
-  __syncthreads();
+  switch (tile) {
+    case 0: sweep32_t<R, 2, 4>(Q, r0, r1, ldq, xs, ws); break;
+    case 1: sweep32_t<R, 4, 1>(Q, r0, r1, ldq, xs, ws); break;
+    case 2: sweep32_t<R, 4, 2>(Q, r0, r1, ldq, xs, ws); break;
+    case 3: sweep32_t<R, 4, 4>(Q, r0, r1, ldq, xs, ws); break;
+    case 4: sweep32_t<R, 8, 1>(Q, r0, r1, ldq, xs, ws); break;
+    default: sweep32_t<R, 8, 2>(Q, r0, r1, ldq, xs, ws); break;
+  }
+  if (clu) cl_share_rows<float, R>(ws, r0, r1);
+  else __syncthreads();
 }
 
 template <int R>
 __device__ __noinline__ void sweep64(const double* Q, int n, int ldq, const double* xs, double* ws) {
-  sweep64_t<R, 2>(Q, n, ldq, xs, ws);
-  __syncthreads();
+  int r0 = 0, r1 = n;
+  const bool clu = team() > 1;
+  if (clu) {
+    cl_sync();
+    cl_rows(n, r0, r1);
+  }
+  sweep64_t<R, 2>(Q, r0, r1, ldq, xs, ws);
+  if (clu) cl_share_rows<double, R>(ws, r0, r1);
+  else __syncthreads();
 }
 
-// xs (ldq x R, type Td) <- v (n x R, type Ts), zero below row n
+// xs (R columns of ldq, type Td) <- v (n x R row-major, type Ts), zero below row n
 template <typename Ts, typename Td, int R>
 __device__ __forceinline__ void stage(const Ts* __restrict__ v, int n, int ldq, Td* __restrict__ xs) {
-  for (int e = threadIdx.x; e < ldq * R; e += NT) xs[e] = e < n * R ? Td(v[e]) : Td(0);
+  for (int e = threadIdx.x; e < ldq * R; e += NT) {
+    const int j = e / ldq, i = e - j * ldq;
+    xs[e] = i < n ? Td(v[(size_t)i * R + j]) : Td(0);
+  }
   __syncthreads();
 }
 
@@ -516,11 +623,19 @@ struct Cta {
   }
 
   // CTA-uniform: thread 0 reads the clock and broadcasts, so every thread takes the same branch
+  // In a cluster, rank 0's clock decides for every CTA (the branches must stay identical).
   __device__ bool over_time() {
     if (!P->time_limit_ns) return timed_out;
     __shared__ int s_late;
-    if (threadIdx.x == 0) s_late = gtimer() > info.t_begin_ns + P->time_limit_ns ? 1 : 0;
-    __syncthreads();
+    const unsigned cs = (unsigned)team();
+    if (cs > 1) cl_sync();               // every CTA has read the previous decision
+    if (threadIdx.x == 0 && cl_rank() == 0) {
+      const int late = gtimer() > info.t_begin_ns + P->time_limit_ns ? 1 : 0;
+      s_late = late;
+      for (unsigned k = 1; k < cs; ++k) cl_st(cl_map(&s_late, k), late);
+    }
+    if (cs > 1) cl_sync();
+    else __syncthreads();
     if (s_late) timed_out = true;
     __syncthreads();
     return timed_out;
@@ -998,8 +1113,11 @@ struct Cta {
     }
     __syncthreads();
     double* Yhat = xi;   // n x 4
-    for (int i = threadIdx.x; i < N; i += NT)
-      round_block(i, yh, sm.small + 200, P->R_out + 9 * d.cam0, P->s_out + d.cam0, Yhat);
+    // the results go out from the team's lead; the other CTAs write the same values to t0
+    const bool lead = team_lead();
+    double* Rdst = lead ? P->R_out + 9 * d.cam0 : t0;
+    double* sdst = lead ? P->s_out + d.cam0 : t0 + 9 * (size_t)N;
+    for (int i = threadIdx.x; i < N; i += NT) round_block(i, yh, sm.small + 200, Rdst, sdst, Yhat);
     __syncthreads();
     stage<double, double, 4>(Yhat, n, ldq, (double*)sm.xs);
     sweep64<4>(Q64, n, ldq, (const double*)sm.xs, (double*)sm.ws);
@@ -1124,10 +1242,12 @@ struct Cta {
           col = r - 1;
         } else if (r + 1 > R) {
           // hand the scene to the rank-8 kernel
-          if (threadIdx.x == 0) { spill[0] = ref_g; spill[1] = r; }
-          for (int e = threadIdx.x; e < n; e += NT) {
-            for (int j = 0; j < 4; ++j) spill[2 + (size_t)e * 4 + j] = y64[(size_t)e * R + j];
-            spill[2 + (size_t)n * 4 + e] = lritz[e];
+          if (team_lead()) {
+            if (threadIdx.x == 0) { spill[0] = ref_g; spill[1] = r; }
+            for (int e = threadIdx.x; e < n; e += NT) {
+              for (int j = 0; j < 4; ++j) spill[2 + (size_t)e * 4 + j] = y64[(size_t)e * R + j];
+              spill[2 + (size_t)n * 4 + e] = lritz[e];
+            }
           }
           __syncthreads();
           return false;
@@ -1190,13 +1310,32 @@ template <int R>
 __global__ void __launch_bounds__(NT, 1) k_batched(Params p) {
   extern __shared__ __align__(16) char smem_base[];
   __shared__ int s_job;
+  if (threadIdx.x == 0) { s_team = (int)cl_size(); s_pfd = p.pf_dist; }
+  __syncthreads();
   for (;;) {
-    if (threadIdx.x == 0) s_job = (int)atomicAdd(p.queue, 1u);
-    __syncthreads();
+    // a team's rank 0 claims the next scene for the whole team
+    const int tm = team();
+    if (tm > 1) cl_sync();               // every CTA has read the previous claim
+    if (threadIdx.x == 0 && cl_rank() == 0) {
+      const int job = (int)atomicAdd(p.queue, 1u);
+      s_job = job;
+      for (int k = 1; k < tm; ++k) cl_st(cl_map(&s_job, (unsigned)k), job);
+    } else if (threadIdx.x == 0 && tm == 1) {
+      s_job = (int)atomicAdd(p.queue, 1u);
+    }
+    if (tm > 1) cl_sync();
+    else __syncthreads();
     const int job = s_job;
     __syncthreads();
     if (job >= p.S) break;
     const Desc d = p.desc[job];
+    if (tm > 1 && d.n < p.team_min_n) {
+      // below the team threshold: the cluster splits up, rank 0 keeps this scene alone and the
+      // others go back to the queue
+      if (threadIdx.x == 0) s_team = 1;
+      __syncthreads();
+      if (cl_rank() != 0) continue;
+    }
     xm_batch_info* out = p.out + d.scene;
     if (R == 8 && out->status != XM_BATCH_HANDOVER) continue;
     Cta<R> c;
@@ -1212,7 +1351,7 @@ __global__ void __launch_bounds__(NT, 1) k_batched(Params p) {
     __syncthreads();
     const bool finished = c.run(resume);
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && team_lead()) {
       if (!finished) c.info.status = XM_BATCH_HANDOVER;
       c.info.t_end_ns = gtimer();
       *out = c.info;
@@ -1225,17 +1364,19 @@ __global__ void __launch_bounds__(NT, 1) k_batched(Params p) {
 // (r = 4) of their scenes with one tiling variant and record the clock cycles per scene.
 template <int RPW, int U>
 __global__ void __launch_bounds__(NT, 1) k_tune_sweep(const Desc* desc, const float* Q32, int S, int NM, int reps,
-                                                     long long* cycles) {
+                                                     int pfd, long long* cycles) {
   extern __shared__ __align__(16) char smem_base[];
+  if (threadIdx.x == 0) s_pfd = pfd;
+  __syncthreads();
   for (int j = blockIdx.x; j < S; j += gridDim.x) {
     const Desc d = desc[j];
     float* xs = reinterpret_cast<float*>(smem_base);
     float* ws = xs + (size_t)NM * 4;
-    for (int e = threadIdx.x; e < d.ldq * 4; e += NT) xs[e] = e < d.n * 4 ? 1.0f / (1 + (e % 7)) : 0.0f;
+    for (int e = threadIdx.x; e < d.ldq * 4; e += NT) xs[e] = e % d.ldq < d.n ? 1.0f / (1 + (e % 7)) : 0.0f;
     __syncthreads();
     const long long t0 = clock64();
     for (int k = 0; k < reps; ++k) {
-      sweep32_t<4, RPW, U>(Q32 + d.q32, d.n, d.ldq, xs, ws);
+      sweep32_t<4, RPW, U>(Q32 + d.q32, 0, d.n, d.ldq, xs, ws);
       __syncthreads();
     }
     const long long t1 = clock64();
@@ -1287,6 +1428,12 @@ struct xm_batch {
   double* gR = nullptr;
   double* gs = nullptr;
   int gkmax = 0;
+  int cluster = 0;                          // CTAs per large scene (0: automatic)
+  int team_n = 0;                           // rows from which a scene is large (0: automatic)
+  int gcs = 0, gteam = 0;                   // the captured graph's cluster size and threshold
+  int pf = 1, gpf = -1;                     // sweep L2 prefetch distance (and the graph's): one
+                                            // round measured best on the 256-scene batch (2 and 3
+                                            // evict rows still in use)
 };
 
 using namespace xm;
@@ -1384,6 +1531,16 @@ extern "C" xm_status xm_batch_free(xm_ctx* c, xm_batch* b) {
   return XM_OK;
 }
 
+extern "C" xm_status xm_batch_cluster(xm_ctx* c, xm_batch* b, int cs, int n_min) {
+  if (!c || !b) return set_error(XM_EINVAL, "xm_batch_cluster: NULL argument");
+  if (cs != 0 && cs != 1 && cs != 2 && cs != 4)
+    return set_error(XM_EINVAL, "xm_batch_cluster: cs = %d not in {0, 1, 2, 4}", cs);
+  if (n_min < 0) return set_error(XM_EINVAL, "xm_batch_cluster: n_min = %d < 0", n_min);
+  b->cluster = cs;
+  b->team_n = n_min;
+  return XM_OK;
+}
+
 extern "C" xm_status xm_batch_autotune(xm_ctx* c, xm_batch* b, int reps, int* tile_out) {
   if (!c || !b) return set_error(XM_EINVAL, "xm_batch_autotune: NULL argument");
   if (reps < 1) reps = 1;
@@ -1402,7 +1559,7 @@ extern "C" xm_status xm_batch_autotune(xm_ctx* c, xm_batch* b, int reps, int* ti
     cudaError_t e = cudaSuccess;
 #define XB_TUNE(RP, UU)                                                                           \
   e = cudaFuncSetAttribute(bat::k_tune_sweep<RP, UU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-  if (e == cudaSuccess) bat::k_tune_sweep<RP, UU><<<grid, bat::NT, smem, b->stream>>>(b->desc, b->Q32, S, b->NM, reps, dcyc);
+  if (e == cudaSuccess) bat::k_tune_sweep<RP, UU><<<grid, bat::NT, smem, b->stream>>>(b->desc, b->Q32, S, b->NM, reps, b->pf, dcyc);
     switch (v) {
       case 0: XB_TUNE(2, 4) break;
       case 1: XB_TUNE(4, 1) break;
@@ -1460,7 +1617,44 @@ extern "C" xm_status xm_solve_batched(xm_ctx* c, xm_batch* b, const xm_opts* opt
                      "memory, above %zu", b->n_max, smem8 + fa8.sharedSizeBytes, c->smem_optin);
   XM_CUDA_TRY(cudaFuncSetAttribute(bat::k_batched<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem4));
   XM_CUDA_TRY(cudaFuncSetAttribute(bat::k_batched<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem8));
-  const int grid = std::min(c->num_sms, b->S);
+  // Teams: a scene whose solve alone would outlast the average load of a CTA sets the batch's
+  // makespan, so it runs on a cluster of cs CTAs (its solve is mostly Q products, which the
+  // cluster splits by rows).  Cost model: n^2 per scene (the products' bytes), spread over one
+  // CTA per SM.  Without such a scene the launch has no clusters.
+  int cs = b->cluster > 0 ? b->cluster : 2;
+  int team_n = b->team_n;
+  if (cs > 1 && team_n == 0) {
+    double w = 0.0;
+    for (const bat::Desc& d : b->desc_h) w += (double)d.n * d.n;
+    team_n = (int)std::ceil(std::sqrt(w / c->num_sms));
+  }
+  if (b->n_max < team_n) cs = 1;
+  if (cs == 1) team_n = 0;
+  int grid = std::min(c->num_sms, b->S);
+  if (cs > 1) {
+    int ncl = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+      cudaLaunchConfig_t cfg{};
+      cfg.gridDim = dim3(cs * std::max(1, c->num_sms / cs));
+      cfg.blockDim = dim3(bat::NT);
+      cfg.dynamicSmemBytes = pass == 0 ? smem4 : smem8;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = cs;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int k = 0;
+      XM_CUDA_TRY(cudaOccupancyMaxActiveClusters(&k, pass == 0 ? (const void*)bat::k_batched<4>
+                                                                : (const void*)bat::k_batched<8>, &cfg));
+      ncl = pass == 0 ? k : std::min(ncl, k);
+    }
+    if (ncl < 1) return set_error(XM_EINVAL, "xm_solve_batched: no cluster of %d CTAs fits on this device", cs);
+    int big = 0;
+    for (const bat::Desc& d : b->desc_h) big += d.n >= team_n;
+    grid = cs * std::min(ncl, big + (b->S - big + cs - 1) / cs);   // teams, then single CTAs
+  }
   const size_t slot_doubles = ((size_t)bat::NVEC * b->NM * 8 + (size_t)b->NM * (XM_MAX_RANK + kmax + 1) +
                                2 * (size_t)b->NM + 31) & ~size_t(31);
   if (!b->slots || b->slots_doubles < slot_doubles * grid) {
@@ -1475,7 +1669,7 @@ extern "C" xm_status xm_solve_batched(xm_ctx* c, xm_batch* b, const xm_opts* opt
   // order after the caller's work on the context stream
   XM_CUDA_TRY(cudaEventRecord(b->ev, c->stream));
   XM_CUDA_TRY(cudaStreamWaitEvent(b->stream, b->ev, 0));
-  const bool same = b->gexec && b->gR == R_out && b->gs == s_out && b->gkmax == kmax &&
+  const bool same = b->gexec && b->gR == R_out && b->gs == s_out && b->gkmax == kmax && b->gcs == cs && b->gteam == team_n && b->gpf == b->pf &&
                     std::memcmp(&b->gopts, &o, sizeof(xm_opts)) == 0;
   if (!same) {
     if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
@@ -1496,14 +1690,33 @@ extern "C" xm_status xm_solve_batched(xm_ctx* c, xm_batch* b, const xm_opts* opt
     p.o = o;
     p.mu = o.scale_reg;
     p.time_limit_ns = o.time_limit_s > 0 ? (unsigned long long)(o.time_limit_s * 1e9) : 0ull;
+    p.team_min_n = team_n;
+    p.pf_dist = b->pf;
     bat::Params p8 = p;
     p.queue = b->queue;
     p8.queue = b->queue + 1;
     cudaGraph_t graph = nullptr;
     XM_CUDA_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
     cudaMemsetAsync(b->queue, 0, sizeof(unsigned) * 2, b->stream);
-    bat::k_batched<4><<<grid, bat::NT, smem4, b->stream>>>(p);
-    if (o.r_max > 4) bat::k_batched<8><<<grid, bat::NT, smem8, b->stream>>>(p8);
+    {
+      cudaLaunchConfig_t cfg{};
+      cfg.gridDim = dim3(grid);
+      cfg.blockDim = dim3(bat::NT);
+      cfg.stream = b->stream;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = cs;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      cfg.dynamicSmemBytes = smem4;
+      cudaLaunchKernelEx(&cfg, bat::k_batched<4>, p);
+      if (o.r_max > 4) {
+        cfg.dynamicSmemBytes = smem8;
+        cudaLaunchKernelEx(&cfg, bat::k_batched<8>, p8);
+      }
+    }
     const cudaError_t ec = cudaStreamEndCapture(b->stream, &graph);
     if (ec != cudaSuccess) return set_error(XM_ECUDA, "xm_solve_batched: capture failed: %s", cudaGetErrorString(ec));
     const cudaError_t ei = cudaGraphInstantiate(&b->gexec, graph, 0);
@@ -1515,6 +1728,9 @@ extern "C" xm_status xm_solve_batched(xm_ctx* c, xm_batch* b, const xm_opts* opt
     b->gR = R_out;
     b->gs = s_out;
     b->gkmax = kmax;
+    b->gcs = cs;
+    b->gteam = team_n;
+    b->gpf = b->pf;
     b->gopts = o;
   }
   XM_CUDA_TRY(cudaGraphLaunch(b->gexec, b->stream));

@@ -137,6 +137,7 @@ def lib() -> ctypes.CDLL:
         "xm_batch_create": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(_P)]),
         "xm_batch_free": (ctypes.c_int, [_P, _P]),
         "xm_batch_autotune": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+        "xm_batch_cluster": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int]),
         "xm_solve_batched": (ctypes.c_int, [_P, _P, ctypes.POINTER(XmOpts), _P, _P,
                                             ctypes.POINTER(XmBatchInfo)]),
         "xm_qfact_create": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int64, _P, _P, _P, _P,
@@ -479,6 +480,12 @@ def xm_batch_autotune(b: Batch, reps: int = 8):
     out = (ctypes.c_int * 8)()
     _check(lib().xm_batch_autotune(b.ctx.h, b.h, reps, out))
     return [(out[2 * k], out[2 * k + 1]) for k in range(4)]
+
+
+def xm_batch_cluster(b: Batch, cs: int, n_min: int = 0) -> None:
+    """Scenes with 3N >= n_min run on a thread-block cluster of cs CTAs (1, 2, 4); 0 for the
+    automatic choice of either."""
+    _check(lib().xm_batch_cluster(b.ctx.h, b.h, cs, n_min))
 
 
 def xm_solve_batched(b: Batch, opts: XmOpts | None = None, R=None, s=None, allow_notcert: bool = True):

@@ -125,3 +125,59 @@ def test_batched_regularised_and_errors(C):
         xm.xm_solve_batched(b, xm.xm_default_opts(r0=5, r_max=8))
     for q in qs:
         q.free()
+
+
+@pytest.mark.parametrize("init_jitter", [0.1, 0.0])
+def test_batched_clusters_are_bit_identical(C, init_jitter):
+    """Scenes run on teams of 2 and 4 CTAs (thread-block clusters; rows of every Q product split
+    between them, exchanged through distributed shared memory) give exactly the results of one
+    CTA per scene: every row is still one warp's fixed-order sum.  Covers a 400-camera scene,
+    clusters that split into single CTAs part-way through the queue, escapes and the rank-8
+    hand-over (Alg. 1's exact start), and the graph's re-capture per setting."""
+    from paper_2502_04640_b300 import xm
+    scs = _batch([400, 250, 30, 120, 8], seed=1000)
+    if init_jitter == 0.0:
+        scs += [scenes.config1(), scenes.circle_scene(16, 200, 4, 0.05, seed=61, w_range=(0.5, 1.5))]
+    qs, b = _build(C, scs)
+    opts = xm.xm_default_opts(init_jitter=init_jitter, time_limit_s=60.0)
+    outs = {}
+    # (cluster size, team threshold): every scene on a team, teams for the two or three largest
+    # then single CTAs (the split inside the persistent loop), and the automatic choice
+    for cs, n_min in ((1, 0), (2, 1), (4, 1), (2, 600), (4, 300), (0, 0)):
+        xm.xm_batch_cluster(b, cs, n_min)
+        outs[cs, n_min] = xm.xm_solve_batched(b, opts)
+    ref = outs[1, 0]
+    for key, o in outs.items():
+        assert torch.equal(o["R"], ref["R"]) and torch.equal(o["s"], ref["s"]), key
+        for a, c in zip(o["info"], ref["info"]):
+            assert a["f"] == c["f"] and a["n_sweeps"] == c["n_sweeps"] and a["rank"] == c["rank"]
+            assert a["certified"] == c["certified"] and a["lambda_min_deflated"] == c["lambda_min_deflated"]
+    assert all(i["certified"] == 1 for i in ref["info"])
+    for cs, n_min in ((3, 0), (2, -1)):
+        with pytest.raises(xm.XmError):
+            xm.xm_batch_cluster(b, cs, n_min)
+    b.free()
+    for q in qs:
+        q.free()
+
+
+def test_batched_400_camera_scene_matches_oracle(C):
+    """The largest scene size of the serving batch (400 cameras, 3N = 1200: sweep staging and
+    Krylov scratch near the shared-memory ceiling), in the batch's own shape (50 landmarks per
+    camera, 4 observers), next to a mid-size scene, on the automatic cluster setting."""
+    from paper_2502_04640_b300 import xm
+    scs = [scenes.circle_scene(400, 20000, 4, 0.01, seed=1100), scenes.circle_scene(150, 7500, 4, 0.01, seed=1101)]
+    qs, b = _build(C, scs)
+    out = xm.xm_solve_batched(b, xm.xm_default_opts(time_limit_s=60.0), allow_notcert=False)
+    parts = _split(out, scs)
+    for j, sc in enumerate(scs):
+        info = out["info"][j]
+        ref = O.solve(O.build_Q_schur(sc.N, sc.M, sc.cam, sc.lmk, sc.ukp, sc.w), r0=4)
+        assert ref.certified and info["certified"] == 1, (j, info)
+        assert _rel(info["f"], ref.f) <= 1e-6 and _rel(info["rho_hat"], ref.rho_hat) <= 1e-6
+        assert abs(info["dual"] - ref.cert.dual) <= 1e-6 * (1 + abs(ref.f))
+        R, s = parts[j]
+        assert np.abs(R - ref.R).max() <= 1e-5 and np.abs(s - ref.s).max() <= 1e-5 * ref.s.max()
+    b.free()
+    for q in qs:
+        q.free()
