@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libxm.so")
-SOURCES = ["xm_api.cu", "xm_build.cu", "xm_qy.cu", "xm_solver.cu", "xm_noalloc.cu", "xm_backward.cu",
+SOURCES = ["xm_api.cu", "xm_build.cu", "xm_qy.cu", "xm_qy_tc.cu", "xm_solver.cu", "xm_noalloc.cu", "xm_backward.cu",
            "xm_batched.cu", "xm_recover.cu", "xm_ozaki.cu", "xm_factored.cu", "xm_dense.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -207,7 +207,7 @@ __global__ void k_pack_tiles(const TI* __restrict__ Qd, int n, int nt, int64_t n
       }
       if (q64) q64[g0 + e] = v;
       if (q32) q32[g0 + e] = (float)v;
-      if (q16) q16[g0 + e] = __double2bfloat16(v);
+      if (q16) q16[g0 + bf16_tile_off(a, b)] = __double2bfloat16(v);
     }
   }
 }
@@ -245,7 +245,10 @@ xm_status alloc_tiles(xm_ctx* ctx, DeviceQ& q, int N, unsigned mask) {
   const size_t elems = (size_t)q.ntiles * TILE * TILE;
   if (mask & XM_STORE_FP64) XM_CUDA_TRY(cudaMalloc(&q.q64, elems * sizeof(double)));
   if (mask & XM_STORE_FP32) XM_CUDA_TRY(cudaMalloc(&q.q32, elems * sizeof(float)));
-  if (mask & XM_STORE_BF16) XM_CUDA_TRY(cudaMalloc(&q.q16, elems * sizeof(__nv_bfloat16)));
+  if (mask & XM_STORE_BF16) {
+    XM_CUDA_TRY(cudaMalloc(&q.q16, elems * sizeof(__nv_bfloat16)));
+    XM_CUDA_TRY(cudaMalloc(&q.ydig, (size_t)32 * q.n_pad * sizeof(__nv_bfloat16)));
+  }
   return XM_OK;
 }
 
@@ -258,7 +261,8 @@ void free_tiles(DeviceQ& q) {
   if (q.q64) cudaFree(q.q64);
   if (q.q32) cudaFree(q.q32);
   if (q.q16) cudaFree(q.q16);
-  q.q64 = nullptr; q.q32 = nullptr; q.q16 = nullptr;
+  if (q.ydig) cudaFree(q.ydig);
+  q.q64 = nullptr; q.q32 = nullptr; q.q16 = nullptr; q.ydig = nullptr;
 }
 
 xm_status pack_dense(xm_ctx* ctx, DeviceQ& q, const double* Qd) {

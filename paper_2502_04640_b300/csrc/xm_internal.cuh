@@ -51,6 +51,13 @@ constexpr int XM_BUILD_SPLIT_MIN_N = 512;   // XM_BUILD_AUTO: tensor-core update
 constexpr int SLAB_BYTES = 16384;   // unit of one bulk async copy
 
 __host__ __device__ inline int64_t tile_count(int nt) { return (int64_t)nt * (nt + 1) / 2; }
+// Element offset of entry (a, b) of a packed 128 x 128 BF16 tile, stored in the tensor cores'
+// operand layout: two 64-column halves of 16 KB, rows of 128 bytes, the 16-byte chunks of each
+// row permuted by the 128-byte swizzle (chunk c of row a at position c xor (a mod 8)).  One
+// contiguous bulk copy then lands a tile in shared memory ready for tcgen05.mma.
+__host__ __device__ inline int bf16_tile_off(int a, int b) {
+  return (b >> 6) * (128 * 64) + a * 64 + ((((b & 63) >> 3) ^ (a & 7)) << 3) + (b & 7);
+}
 __host__ __device__ inline int64_t tile_index(int nt, int I, int J) {
   return (int64_t)I * nt - (int64_t)I * (I - 1) / 2 + (J - I);
 }
@@ -64,6 +71,8 @@ struct DeviceQ {
   double* q64 = nullptr;            // packed FP64 tiles
   float* q32 = nullptr;             // packed FP32 tiles
   __nv_bfloat16* q16 = nullptr;     // packed BF16 tiles
+  __nv_bfloat16* ydig = nullptr;    // with q16: the tensor-core sweep's BF16 digit rows of Y
+                                    // (32 x n_pad; one sweep of this Q at a time)
   int build_path = 0;               // XM_BUILD_* of the rank-(N-1) update that built it
   double t_update_s = 0.0;          // device time of that update (digit split + tensor cores)
   QFact* fact = nullptr;            // factored operator (XM_STORE_FACTORED): FP64 products
@@ -135,6 +144,10 @@ void free_tiles(DeviceQ& q);
 xm_status pack_dense_f32(xm_ctx* ctx, DeviceQ& q, const float* A);
 xm_status qy_launch(xm_ctx* ctx, const DeviceQ& q, int prec, int R, const void* Y, void* W,
                     const int* skip, cudaStream_t st);
+// the BF16-stored Q's sweep on the tensor cores (xm_qy_tc.cu): FP32 Y (n_pad x R, R in
+// {1, 4, 8}) in three BF16 digits, FP32 W accumulated
+xm_status qy_tc_launch(xm_ctx* ctx, const DeviceQ& q, int R, const float* Y, float* W,
+                       const int* skip, cudaStream_t st);
 
 // ------------------------------------------------------------------ split-BF16 update (xm_ozaki.cu)
 // Whether the tensor-core rank-K update handles K = N - 1 and n = 3N.
@@ -249,6 +262,23 @@ __device__ __forceinline__ double q_entry(const TQ* __restrict__ tiles, int nt, 
   const int I = r / TILE, J = c / TILE, a = r % TILE, b = c % TILE;
   const double v = double(tiles[tile_index(nt, I, J) * TILE * TILE + (int64_t)a * TILE + b]);
   return (I == J && a == b) ? 2.0 * v : v;
+}
+
+// Traversal order of the tiles: tile rows 0, nt-1, 1, nt-2, ... (a long row, then the short row
+// that completes it to nt + 1 tiles), each row from its diagonal tile outwards.  Every CTA takes a
+// contiguous range of this order, so each crosses one to three row boundaries (a row change costs
+// a flush of the row partials and a Y_I reload), where row-major order left the CTA holding the
+// last, shortest rows with a dozen or more.
+__device__ __forceinline__ void pair_order_start(int nt, int64_t v, int& I, int& J) {
+  const int64_t P = (int64_t)nt + 1;
+  const int p = (int)(v / P), rem = (int)(v % P);
+  if (rem < nt - p) { I = p; J = p + rem; }
+  else { I = nt - 1 - p; J = I + (rem - (nt - p)); }
+}
+__device__ __forceinline__ void pair_order_next(int nt, int& I, int& J) {
+  if (++J < nt) return;
+  I = (2 * I < nt - 1) ? nt - 1 - I : nt - I;   // long row p -> short row nt-1-p -> long row p+1
+  J = I;
 }
 
 template <typename T>

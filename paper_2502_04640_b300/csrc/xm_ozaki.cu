@@ -476,7 +476,7 @@ k_oz_mma(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUten
           }
           dst[c] = v;
           if (args.q32) args.q32[g0 + c] = (float)v;
-          if (args.q16) args.q16[g0 + c] = __double2bfloat16(v);
+          if (args.q16) args.q16[(size_t)t * TILE * TILE + bf16_tile_off(a_loc, b_loc)] = __double2bfloat16(v);
         }
       }
     }

@@ -31,10 +31,6 @@ template <> struct QT<float> {
   using A = float;
   static constexpr int ROWS = SLAB_BYTES / (TILE * 4);   // 32 rows per slab
 };
-template <> struct QT<__nv_bfloat16> {
-  using A = float;
-  static constexpr int ROWS = SLAB_BYTES / (TILE * 2);   // 64
-};
 template <> struct QT<double> {
   using A = double;
   static constexpr int ROWS = SLAB_BYTES / (TILE * 8);   // 16
@@ -44,13 +40,6 @@ template <> struct QT<double> {
 __device__ __forceinline__ void load4(const float* p, float (&q)[4]) {
   float4 v = *reinterpret_cast<const float4*>(p);
   q[0] = v.x; q[1] = v.y; q[2] = v.z; q[3] = v.w;
-}
-__device__ __forceinline__ void load4(const __nv_bfloat16* p, float (&q)[4]) {
-  uint2 v = *reinterpret_cast<const uint2*>(p);
-  q[0] = __uint_as_float(v.x << 16);
-  q[1] = __uint_as_float(v.x & 0xffff0000u);
-  q[2] = __uint_as_float(v.y << 16);
-  q[3] = __uint_as_float(v.y & 0xffff0000u);
 }
 __device__ __forceinline__ void load4(const double* p, double (&q)[4]) {
   double2 a = *reinterpret_cast<const double2*>(p);
@@ -113,23 +102,6 @@ __device__ __forceinline__ T transpose_reduce(T (&v)[V], int lane) {
 #pragma unroll
   for (; o >= 1; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
   return x;
-}
-
-// Traversal order of the tiles: tile rows 0, nt-1, 1, nt-2, ... (a long row, then the short row
-// that completes it to nt + 1 tiles), each row from its diagonal tile outwards.  Every CTA takes a
-// contiguous range of this order, so each crosses one to three row boundaries (a row change costs
-// a flush of the row partials and a Y_I reload), where row-major order left the CTA holding the
-// last, shortest rows with a dozen or more.
-__device__ __forceinline__ void pair_order_start(int nt, int64_t v, int& I, int& J) {
-  const int64_t P = (int64_t)nt + 1;
-  const int p = (int)(v / P), rem = (int)(v % P);
-  if (rem < nt - p) { I = p; J = p + rem; }
-  else { I = nt - 1 - p; J = I + (rem - (nt - p)); }
-}
-__device__ __forceinline__ void pair_order_next(int nt, int& I, int& J) {
-  if (++J < nt) return;
-  I = (2 * I < nt - 1) ? nt - 1 - I : nt - I;   // long row p -> short row nt-1-p -> long row p+1
-  J = I;
 }
 
 template <typename TQ, int R, int NW, bool SW>
@@ -615,8 +587,8 @@ xm_status qy_launch(xm_ctx* ctx, const DeviceQ& q, int prec, int R, const void* 
       if (!q.q32) return set_error(XM_EINVAL, "sweep: Q has no FP32 copy");
       return dispatch_r<float, 8>(ctx, q.q32, q, R, Y, W, skip, st);
     case XM_BF16Q_BULK:
-      if (!q.q16) return set_error(XM_EINVAL, "sweep: Q has no BF16 copy");
-      return dispatch_r<__nv_bfloat16, 8>(ctx, q.q16, q, R, Y, W, skip, st);
+      // tensor cores: Y in three BF16 digits against the BF16 tiles (xm_qy_tc.cu)
+      return qy_tc_launch(ctx, q, R, static_cast<const float*>(Y), static_cast<float*>(W), skip, st);
     default:
       return set_error(XM_EINVAL, "sweep: unknown precision %d", prec);
   }
