@@ -29,7 +29,7 @@
 extern "C" {
 #endif
 
-#define XM_ABI_VERSION 2
+#define XM_ABI_VERSION 3
 #define XM_MAX_RANK 8   /* largest BM rank r the kernels handle (Alg. 1 stops there) */
 
 typedef struct xm_ctx xm_ctx;   /* opaque: device, stream, workspaces */
@@ -112,6 +112,12 @@ typedef struct xm_opts {
                               LOBPCG (blocks of 4, stop at a Ritz residual <= 1e-6 lambda_max,
                               lambda_max from 40 Lanczos steps; Lanczos if it does not converge
                               in 300 iterations); 0: Lanczos to lanczos_tol                     */
+  double bf16_hvp_until;   /* XM_FP32_BULK with a BF16 copy of Q (XM_STORE_BF16): the bulk
+                              phase's Hessian products read the BF16 tiles (the tensor-core
+                              sweep, half the bytes) while ||rgrad|| > bf16_hvp_until *
+                              ||rgrad(Y0)||, the FP32 tiles after; gradients, objective and
+                              ratio test stay FP32.  0 (default): FP32 products throughout.
+                              Must be >= 0; > 0 needs the BF16 copy (XM_EINVAL otherwise)    */
 } xm_opts;
 
 typedef struct xm_info {

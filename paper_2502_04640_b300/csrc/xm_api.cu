@@ -114,6 +114,7 @@ void xm_default_opts(xm_opts* o) {
   o->precond = 0;
   o->bulk_stall = 0;
   o->cert_lobpcg = 1;
+  o->bf16_hvp_until = 0.0;
 }
 
 xm_status xm_create(xm_ctx** out, int device, void* stream) {

@@ -646,12 +646,14 @@ struct Solver {
     const double eps_reg = std::is_same<To, float>::value ? 1e2 * 1.1920929e-07
                                                           : 1e3 * 2.220446049250313e-16;
     int rejects = 0;
+    // BF16-tile Hessian products early in the FP32 bulk phase (opts.bf16_hvp_until)
+    const bool bf16_early = bulk && prec_hvp == XM_FP32_BULK && o.bf16_hvp_until > 0.0 && q.q16;
     double best_f = f;   // bulk stagnation test (opts.bulk_stall)
     int stall = 0;
     // captured tCG chunks of this call, keyed by the (iterate, Lambda) buffers they read
-    struct ChunkGraph { const void* yin; const double* lam; cudaGraphExec_t exec; };
+    struct ChunkGraph { const void* yin; const double* lam; int prec; cudaGraphExec_t exec; };
     struct GraphCache {
-      ChunkGraph e[2] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+      ChunkGraph e[2] = {{nullptr, nullptr, 0, nullptr}, {nullptr, nullptr, 0, nullptr}};
       int n = 0;
       cudaStream_t s = nullptr;
       ~GraphCache() {
@@ -665,6 +667,7 @@ struct Solver {
     for (int k = 0; k < max_outer; ++k) {
       if (std::sqrt(g2) <= tol_abs) break;
       if (over_time()) break;
+      const int hvp = (bf16_early && std::sqrt(g2) > o.bf16_hvp_until * ref_g) ? XM_BF16Q_BULK : prec_hvp;
       const Ti* Yin;
       if (!std::is_same<To, Ti>::value) {
         k_cast<To, Ti><<<grid_elems(rows * R), CAM_THREADS, 0, st>>>(rows * R, (const To*)bY, (Ti*)bYin);
@@ -689,7 +692,7 @@ struct Solver {
       bool pending = false;
       auto launch_chunk = [&](cudaStream_t cst) -> xm_status {
         for (int c = 0; c < CH; ++c) {
-          XM_TRY(qy_launch(ctx, q, prec_hvp, R, bD, bWd, &d_sc->done, cst));
+          XM_TRY(qy_launch(ctx, q, hvp, R, bD, bWd, &d_sc->done, cst));
           k_hvp_epi<Ti, R><<<nb_cam, CAM_THREADS, 0, cst>>>(N, Yin, (Ti*)bWd, (const Ti*)bD, (Ti*)bHd,
                                                            Lam, d_sc, ctx->d_partials, ctx->d_counter);
           k_tcg_update<Ti, R><<<nb_cam, CAM_THREADS, 0, cst>>>(N, Yin, (Ti*)bEta, (Ti*)bHeta, (Ti*)bR,
@@ -703,7 +706,7 @@ struct Solver {
       };
       auto chunk_exec = [&]() -> cudaGraphExec_t {
         for (int i = 0; i < ncg; ++i)
-          if (cg[i].yin == Yin && cg[i].lam == Lam) return cg[i].exec;
+          if (cg[i].yin == Yin && cg[i].lam == Lam && cg[i].prec == hvp) return cg[i].exec;
         if (cudaStreamBeginCapture(cap_st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
           (void)cudaGetLastError();
           return nullptr;
@@ -718,7 +721,7 @@ struct Solver {
         (void)cudaGetLastError();
         if (!ex) return nullptr;
         if (ncg == 2) { cudaGraphExecDestroy(cg[0].exec); cg[0] = cg[1]; ncg = 1; }
-        cg[ncg++] = ChunkGraph{Yin, Lam, ex};
+        cg[ncg++] = ChunkGraph{Yin, Lam, hvp, ex};
         return ex;
       };
       xm_status chunk_status = XM_OK;
@@ -1608,6 +1611,9 @@ xm_status check_opts(const DeviceQ& q, const xm_opts& o) {
     return set_error(XM_EINVAL, "opts: scale_reg must be finite and >= 0 (got %g)", o.scale_reg);
   if (o.precond != 0 && o.precond != 1) return set_error(XM_EINVAL, "opts: precond must be 0 or 1");
   if (o.cert_lobpcg != 0 && o.cert_lobpcg != 1) return set_error(XM_EINVAL, "opts: cert_lobpcg must be 0 or 1");
+  if (!(o.bf16_hvp_until >= 0.0)) return set_error(XM_EINVAL, "opts: bf16_hvp_until must be >= 0");
+  if (o.bf16_hvp_until > 0.0 && o.prec == XM_FP32_BULK && !q.q16)
+    return set_error(XM_EINVAL, "solve: bf16_hvp_until > 0 needs XM_STORE_BF16");
   if (o.bulk_stall < 0 || o.bulk_stall > o.max_outer)
     return set_error(XM_EINVAL, "opts: bulk_stall must be in [0, max_outer] (got %d)", o.bulk_stall);
   return XM_OK;
@@ -1735,7 +1741,7 @@ xm_status xm_pipeline_host(xm_ctx* c, int N, int M, int64_t E, const int32_t* ca
   cudaStream_t st = c->stream;
   unsigned mask = XM_STORE_FP64;
   if (o.prec != XM_FP64) mask |= XM_STORE_FP32;
-  if (o.prec == XM_BF16Q_BULK) mask |= XM_STORE_BF16;
+  if (o.prec == XM_BF16Q_BULK || (o.prec == XM_FP32_BULK && o.bf16_hvp_until > 0.0)) mask |= XM_STORE_BF16;
   int32_t *cam = nullptr, *lmk = nullptr;
   double *ukp = nullptr, *w = nullptr, *R = nullptr, *s = nullptr;
   auto cleanup = [&]() {

@@ -33,7 +33,8 @@ class XmOpts(ctypes.Structure):
                 ("time_limit_s", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("verbose", ctypes.c_int), ("init_jitter", ctypes.c_double),
                 ("scale_reg", ctypes.c_double), ("precond", ctypes.c_int),
-                ("bulk_stall", ctypes.c_int), ("cert_lobpcg", ctypes.c_int)]
+                ("bulk_stall", ctypes.c_int), ("cert_lobpcg", ctypes.c_int),
+                ("bf16_hvp_until", ctypes.c_double)]
 
 
 class XmInfo(ctypes.Structure):

@@ -29,7 +29,7 @@ def test_library_loads_and_exports_every_declared_symbol():
     L = xm.lib()
     missing = [n for n in _declared() if not hasattr(L, n)]
     assert not missing, missing
-    assert L.xm_abi_version() == 2
+    assert L.xm_abi_version() == 3
 
 
 def test_default_opts_and_errors_without_device():

@@ -108,6 +108,28 @@ def test_two_views_umeyama(C):
     q.free()
 
 
+@pytest.mark.parametrize("thr", [1e-2, 1e-6])
+def test_bf16_hessian_products_early_in_the_bulk_phase(C, thr):
+    """bf16_hvp_until: the FP32 bulk phase takes its Hessian products from the BF16 tiles (the
+    tensor-core sweep) until ||rgrad|| falls below thr of the start, then from the FP32 tiles;
+    the certified optimum is the oracle's.  Without a BF16 copy the option is refused."""
+    from paper_2502_04640_b300 import xm
+    sc = scenes.random_scene(90, 4000, noise=0.03, outlier_frac=0.05, seed=21)
+    Qo = O.build_Q_schur(sc.N, sc.M, sc.cam, sc.lmk, sc.ukp, sc.w)
+    ref = O.solve(Qo, r0=4)
+    q, out = _solve(C, sc, PRECS["fp32"], bf16_hvp_until=thr)
+    info = out["info"]
+    assert ref.certified and info["certified"] == 1
+    assert _rel(info["f"], ref.f) <= 1e-6 and _rel(info["rho_hat"], ref.rho_hat) <= 1e-6
+    assert abs(info["lambda_min_deflated"] - ref.cert.lam_min_deflated) <= 1e-5 * ref.cert.lam_max_Q
+    q.free()
+    q = xm.xm_build_Q(C, sc.N, sc.M, *xm.scene_tensors(sc), xm.XM_STORE_FP32 | xm.XM_STORE_FP64)
+    with pytest.raises(xm.XmError) as e:
+        xm.xm_solve(q, xm.xm_default_opts(bf16_hvp_until=thr))
+    assert e.value.status == xm.XM_EINVAL
+    q.free()
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_outliers_and_tiles_match_oracle(C, prec):
     sc = scenes.random_scene(90, 4000, noise=0.03, outlier_frac=0.05, seed=21)
