@@ -688,7 +688,8 @@ def _c4_solve_and_adjoint(ctx, steps):
         walls.append(time.perf_counter() - t0)
     res["adjoint_s"] = statistics.median(walls)
     res["adjoint_grads_per_s"] = sc.E * 4 / res["adjoint_s"]
-    res["adjoint"] = {k: infos[-1][k] for k in ("res_rel", "n_cg", "n_refine", "t_lambda_s", "t_resid_s")}
+    res["adjoint"] = {k: infos[-1][k] for k in ("res_rel", "n_cg", "n_refine", "t_lambda_s", "t_resid_s",
+                                                 "t_precond_s")}
     res["factored_qy"] = factored_measure(ctx, sc, q)
     q.free()
     return res
@@ -779,9 +780,15 @@ def run_recover(args):
     try:
         x2 = xm.xm_solve_xm2(ctx, sc.N, sc.M, *t, xm.xm_default_opts(prec=1, **wopts))
         torch.cuda.synchronize()
+        # cameras left in the solved component (an isolated camera comes back with zero scale)
+        kept_cams = int((x2["s"] != 0).sum().item())
         xm2 = {"xm2_s": time.perf_counter() - t0, "xm2_first_certified": x2["info_first"]["certified"],
                "xm2_second_certified": x2["info_second"]["certified"],
-               "xm2_kept": int(x2["keep"].sum().item())}
+               "xm2_kept": int(x2["keep"].sum().item()), "xm2_dropped": int((~x2["keep"]).sum().item()),
+               "xm2_cameras_solved": kept_cams, "xm2_eta_second": x2["info_second"]["eta"],
+               "xm2_solve_first_s": x2["info_first"]["t_solve_s"],
+               "xm2_solve_second_s": x2["info_second"]["t_solve_s"],
+               "xm2_sweeps_second": x2["info_second"]["n_sweeps"]}
     except xm.XmError as e:
         # dropping the largest residuals can leave a camera or landmark unobserved
         xm2 = {"xm2_status": xm.STATUS_NAMES.get(e.status, str(e.status)), "xm2_message": str(e)}
@@ -835,7 +842,8 @@ def run_adjoint(args):
         last = infos[-1]
         res[name] = {"s_per_backward": dt, "grads_per_s": sc.E * 4 / dt,
                      **{k: last[k] for k in ("res_rel", "n_refine", "n_cg", "n_sweeps_fp32",
-                                             "n_sweeps_fp64", "t_lambda_s", "t_resid_s", "launches")}}
+                                             "n_sweeps_fp64", "t_lambda_s", "t_resid_s", "t_precond_s",
+                                             "launches")}}
     cpu = None
     if not args.no_cpu:
         cpu = oracle_adjoint_sample(sc, wopts.get("scale_reg", 0.0))

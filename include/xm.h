@@ -331,6 +331,8 @@ typedef struct xm_adj_info {
                               Z + gamma Pi_Y (n <= 40000), packed like Q and applied by the
                               sweep; 0: by Z's 3 x 3 diagonal blocks                          */
   double gamma;            /* curvature given to range(Y) by the dense preconditioner          */
+  double t_precond_s;      /* wall time of forming the preconditioner (part of t_lambda_s):
+                              dense Z + gamma Pi_Y, its Cholesky factor and inverse, packing  */
 } xm_adj_info;
 
 xm_status xm_backward(xm_ctx* ctx, const xm_qmat* q, const xm_opts* opts, int r, const double* Y,

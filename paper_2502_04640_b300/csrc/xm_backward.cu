@@ -743,6 +743,7 @@ static xm_status backward_impl(xm_ctx* ctx, const DeviceQ& q, const xm_opts& o, 
   inf.grad_norm_Y = std::sqrt(hs.g2);
 
   // ---- preconditioner data: deflation basis of the gauge directions, Pi_Y, gamma, Z's factor
+  const auto tp0 = clk::now();
   {
     std::vector<double> G(R * R), gw, W, host(4 * R * R + R + 1, 0.0);
     XM_CUDA_TRY(cudaMemcpy(G.data(), dsm + SM_G, sizeof(double) * R * R, cudaMemcpyDeviceToHost));
@@ -838,6 +839,8 @@ static xm_status backward_impl(xm_ctx* ctx, const DeviceQ& q, const xm_opts& o, 
     }
     inf.gamma = gamma;
   }
+  XM_CUDA_TRY(cudaStreamSynchronize(st));
+  inf.t_precond_s = std::chrono::duration<double>(clk::now() - tp0).count();
   const bool dense = inf.dense_precond != 0;
 
   // ---- 2. Hess[lambda] = g_L: CG, FP64 residual refinement around an FP32 inner solve

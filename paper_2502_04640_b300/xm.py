@@ -61,7 +61,7 @@ class XmAdjInfo(ctypes.Structure):
                 ("n_sweeps_fp64", ctypes.c_int), ("t_lambda_s", ctypes.c_double),
                 ("t_resid_s", ctypes.c_double), ("t_total_s", ctypes.c_double),
                 ("launches", ctypes.c_long), ("dense_precond", ctypes.c_int),
-                ("gamma", ctypes.c_double)]
+                ("gamma", ctypes.c_double), ("t_precond_s", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
