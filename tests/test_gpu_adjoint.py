@@ -87,6 +87,27 @@ def test_backward_matches_oracle_adjoint(C, name, prec):
     q.free()
 
 
+def test_backward_mid_size_matches_oracle(C):
+    """n = 3N = 2100 (700 cameras, 55 sweep tiles per side): the dense preconditioner's inverse
+    and its packed sweep at a size with several tiles per CTA; same parity with the oracle."""
+    from paper_2502_04640_b300 import xm
+    sc = scenes.random_scene(700, 10000, noise=0.02, seed=45, center_sigma=3.0)
+    opts = xm.xm_default_opts(prec=0, grad_tol_rel=1e-12)
+    q, t, out = _solve(C, sc, opts)
+    assert out["status"] == 0 and out["info"]["certified"] == 1
+    r = out["info"]["rank"]
+    D = _dG(sc, 8)
+    d_u, d_w, lam, info, st = xm.xm_backward(q, out["Y"], r, sc.M, *t,
+                                             torch.as_tensor(D, device="cuda:0"),
+                                             xm.xm_default_opts(prec=1, grad_tol_rel=1e-12), want_lambda=True)
+    assert st == 0 and info["res_rel"] <= 1e-12 and info["dense_precond"] == 1
+    Y = out["Y"].cpu().numpy()[:, :r]
+    ref_u, ref_w, _ = O.adjoint(sc.N, sc.M, sc.cam, sc.lmk, sc.ukp, sc.w, Y, D)
+    assert _max_rel(d_u.cpu().numpy(), ref_u) <= 1e-6
+    assert _max_rel(d_w.cpu().numpy(), ref_w) <= 1e-6
+    q.free()
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_backward_on_a_zero_padded_rank(C, prec):
     """The certified point with a zero column appended is the same point of the SDP (X = Y Y^T
