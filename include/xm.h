@@ -178,14 +178,15 @@ xm_status xm_build_Q(xm_ctx* ctx, int N, int M, int64_t E, const int32_t* cam,
  * L of the anchored translation block (N^3 / 3 flops), C = L^{-1} Bbar^T (3 N^3 flops) and the
  * symmetric rank-(N-1) update Q = P - C^T C (9 N^3 flops; 9.4 TFLOP at N = 10155): the build's
  * dense contractions.
- * XM_BUILD_FP64:       cuSOLVER DPOTRF, cuBLAS DTRSM and DSYRK on the FP64 units.
+ * XM_BUILD_FP64:       the library's own FP64 kernels (blocked Cholesky, substitution, tiled
+ *                      products) on the FP64 units.
  * XM_BUILD_SPLIT_BF16: the dense products on the BF16 tensor cores by error-free digit splitting
  *                      (Ozaki et al. 2012): each operand vector as 8 signed 7-bit digits scaled by
  *                      a power of two, exact FP32 accumulation of the digit products, int32 and
  *                      FP64 recombination; normwise as accurate as FP64 products (error below
  *                      2^-56 sqrt(K) |u| |v| per dot product).  The factorisation and the
- *                      triangular solve are blocked (512-row diagonal blocks and panels by
- *                      cuSOLVER / cuBLAS in FP64, the trailing and block updates on the tensor
+ *                      triangular solve are blocked (512- and 1024-row diagonal blocks, panels by
+ *                      the library's FP64 kernels, the trailing and block updates on the tensor
  *                      cores).  Needs N - 1 <= 16640.
  * XM_BUILD_AUTO:       XM_BUILD_SPLIT_BF16 when 512 <= N <= 16641, else XM_BUILD_FP64 (default).
  * The landmark elimination stays in FP64 either way. */
@@ -332,13 +333,25 @@ typedef struct xm_adj_info {
                               sweep; 0: by Z's 3 x 3 diagonal blocks                          */
   double gamma;            /* curvature given to range(Y) by the dense preconditioner          */
   double t_precond_s;      /* wall time of forming the preconditioner (part of t_lambda_s):
-                              dense Z + gamma Pi_Y, its Cholesky factor and inverse, packing  */
+                              dense Z + gamma Pi_Y, its inverse (xm_spd_inverse), packing     */
 } xm_adj_info;
 
 xm_status xm_backward(xm_ctx* ctx, const xm_qmat* q, const xm_opts* opts, int r, const double* Y,
                       int ldy, int M, int64_t E, const int32_t* cam, const int32_t* lmk,
                       const double* ukp, const double* w, const double* dL_dG, double* dL_dukp,
                       double* dL_dw, double* lam, xm_adj_info* info);
+
+/* In-place inverse of a dense symmetric positive definite FP32 matrix: the adjoint's
+ * preconditioner (Z + gamma Pi_Y)^{-1} above (the paper has no adjoint; Z is the certificate
+ * matrix of Sec. 3).  A: device, n x n column-major with leading dimension lda >= n, both
+ * triangles set; overwritten by A^{-1} (both triangles).  Block inversion by Schur complements
+ * (blocks split near n / 2 at multiples of 128; FP64 Gauss-Jordan below 129 rows); the
+ * products, n^3 / 2 multiply-adds in all, run on the BF16 tensor cores with every FP32 operand
+ * split into three BF16 digits and FP32 accumulation (the accuracy of FP32 products).  Allocates
+ * about 1.1 n^2 floats of scratch, freed before return.  Synchronous.  XM_ENUMERIC when a pivot
+ * is not positive (A not numerically positive definite; A is then undefined), XM_EINVAL on bad
+ * arguments. */
+xm_status xm_spd_inverse(xm_ctx* ctx, int n, float* A, int lda);
 
 /* ---- translations and landmarks (Eq. 7), per-measurement residuals, XM^2 (Sec. 5) --------
  * xm_recover_tp: for rotations R (N x 3 x 3 row-major) and scales s (N), the least-squares

@@ -2,7 +2,7 @@
 
 Run as ``python -m paper_2502_04640_b300.build`` or call ``build()``.  Each translation unit
 is compiled by nvcc into ``_build/`` next to the sources, then linked into
-``paper_2502_04640_b300/libxm.so`` together with cuBLAS / cuSOLVER.  Rebuilds only what is
+``paper_2502_04640_b300/libxm.so`` (CUDA runtime only: no vendor math library).  Rebuilds only what is
 older than its sources or headers.
 """
 from __future__ import annotations
@@ -18,7 +18,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libxm.so")
 SOURCES = ["xm_api.cu", "xm_build.cu", "xm_qy.cu", "xm_qy_tc.cu", "xm_solver.cu", "xm_noalloc.cu", "xm_backward.cu",
-           "xm_batched.cu", "xm_recover.cu", "xm_ozaki.cu", "xm_factored.cu", "xm_dense.cu"]
+           "xm_batched.cu", "xm_recover.cu", "xm_ozaki.cu", "xm_factored.cu", "xm_dense.cu", "xm_spdinv.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
@@ -53,7 +53,7 @@ def build(verbose: bool = False, ptxas_info: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(lambda s: _compile(s, extra, verbose or ptxas_info), SOURCES))
     if not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
-        cmd = [NVCC, *ARCH, "-shared", "-o", LIB, *objs, "-lcublas", "-lcusolver"]
+        cmd = [NVCC, *ARCH, "-shared", "-o", LIB, *objs]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
             raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")

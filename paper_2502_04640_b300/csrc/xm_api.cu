@@ -1,7 +1,4 @@
 // C ABI: context, error reporting and Q handles.
-#include <cublas_v2.h>
-#include <cusolverDn.h>
-
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -156,8 +153,6 @@ void xm_destroy(xm_ctx* c) {
   if (c->h_err) cudaFreeHost(c->h_err);
   if (c->d_counter) cudaFree(c->d_counter);
   if (c->d_partials) cudaFree(c->d_partials);
-  if (c->cublas) cublasDestroy(static_cast<cublasHandle_t>(c->cublas));
-  if (c->cusolver) cusolverDnDestroy(static_cast<cusolverDnHandle_t>(c->cusolver));
   delete c;
 }
 

@@ -21,7 +21,6 @@
 //      step solves Hess[delta] = g_L - Hess64[lambda] in FP32).
 //   3. The optimal residuals of the 2R columns [Y, lambda]: landmark means, camera sums, the
 //      anchored translation solve with the Cholesky factor of Sbar, then the outputs.
-#include <cusolverDn.h>
 
 #include <algorithm>
 #include <chrono>
@@ -678,7 +677,7 @@ static xm_status backward_impl(xm_ctx* ctx, const DeviceQ& q, const xm_opts& o, 
 
   // ---- vectors (FP64: Y, G, Lam, g_L, lambda, res, Wd; inner: Y, G, eta, Heta, r, d, Hd, Wd)
   Buf bY, bG, bLam, bMinv, bgL, blam, bres, bWd, bsc, bYi, bGi, beta, bHeta, br, bd, bHd, bWi;
-  Buf bsmall, bZ, bcol, bcol2, bwork, binfo;
+  Buf bsmall, bZ, bcol, bcol2;
   struct TilesGuard { DeviceQ q; ~TilesGuard() { free_tiles(q); } } Pinv;
   for (Buf* b : {&bY, &bG, &bgL, &blam, &bres, &bWd}) {
     XM_CUDA_TRY(cudaMalloc(&b->p, vec64));
@@ -780,56 +779,27 @@ static xm_status backward_impl(xm_ctx* ctx, const DeviceQ& q, const xm_opts& o, 
           N, q.q64, q.nt, bLam.as<double>(), bY.as<double>(), dsm + SM_GP, gamma, bZ.as<float>());
       ++launches;
       XM_CUDA_TRY(cudaGetLastError());
-      if (!ctx->cusolver) {
-        cusolverDnHandle_t h;
-        if (cusolverDnCreate(&h) != CUSOLVER_STATUS_SUCCESS)
-          return set_error(XM_ECUDA, "xm_backward: cusolverDnCreate failed");
-        ctx->cusolver = h;
-      }
-      cusolverDnHandle_t cs = static_cast<cusolverDnHandle_t>(ctx->cusolver);
-      int lwork = 0, hinfo = 1;
-      bool ok = cusolverDnSetStream(cs, st) == CUSOLVER_STATUS_SUCCESS &&
-                cusolverDnSpotrf_bufferSize(cs, CUBLAS_FILL_MODE_LOWER, n, bZ.as<float>(), n, &lwork) ==
-                    CUSOLVER_STATUS_SUCCESS;
-      if (ok) {
-        XM_CUDA_TRY(cudaMalloc(&bwork.p, sizeof(float) * (size_t)std::max(lwork, 1)));
-        XM_CUDA_TRY(cudaMalloc(&binfo.p, sizeof(int)));
-        ok = cusolverDnSpotrf(cs, CUBLAS_FILL_MODE_LOWER, n, bZ.as<float>(), n, bwork.as<float>(), lwork,
-                              binfo.as<int>()) == CUSOLVER_STATUS_SUCCESS;
-        XM_CUDA_TRY(cudaMemcpyAsync(&hinfo, binfo.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-        XM_CUDA_TRY(cudaStreamSynchronize(st));
-      }
-      if (ok && hinfo == 0) {
-        // Explicit inverse from the factor (lower triangle, in place), packed into FP32
-        // upper-triangle tiles: applying it is then one Q.Y-style sweep per CG step, which
-        // streams n^2/2 floats at the sweep's HBM rate, where triangular solves with the factor
-        // are long chains of small dependent steps.  A preconditioner needs no more accuracy
-        // than the FP32 inverse gives.
-        int lw2 = 0, hinv = 1;
-        if (cusolverDnSpotri_bufferSize(cs, CUBLAS_FILL_MODE_LOWER, n, bZ.as<float>(), n, &lw2) ==
-            CUSOLVER_STATUS_SUCCESS) {
-          Buf bw2;
-          XM_CUDA_TRY(cudaMalloc(&bw2.p, sizeof(float) * (size_t)std::max(lw2, 1)));
-          if (cusolverDnSpotri(cs, CUBLAS_FILL_MODE_LOWER, n, bZ.as<float>(), n, bw2.as<float>(), lw2,
-                               binfo.as<int>()) == CUSOLVER_STATUS_SUCCESS) {
-            XM_CUDA_TRY(cudaMemcpyAsync(&hinv, binfo.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-            XM_CUDA_TRY(cudaStreamSynchronize(st));
-          }
-        }
-        if (hinv == 0) {
-          XM_TRY(alloc_tiles(ctx, Pinv.q, N, XM_STORE_FP32));
-          XM_TRY(pack_dense_f32(ctx, Pinv.q, bZ.as<float>()));
-          ++launches;
-          const size_t colb = sizeof(float) * rows * R;
-          XM_CUDA_TRY(cudaMalloc(&bcol.p, colb));
-          XM_CUDA_TRY(cudaMalloc(&bcol2.p, colb));
-          XM_CUDA_TRY(cudaMemsetAsync(bcol.p, 0, colb, st));
-          XM_CUDA_TRY(cudaMemsetAsync(bcol2.p, 0, colb, st));
-          inf.dense_precond = 1;
-        }
+      // Explicit inverse (this library's tensor-core SPD inverse, FP32 accuracy), packed into
+      // FP32 upper-triangle tiles: applying it is then one Q.Y-style sweep per CG step, which
+      // streams n^2/2 floats at the sweep's HBM rate, where triangular solves with a factor are
+      // long chains of small dependent steps.  A preconditioner needs no more accuracy than
+      // the FP32 inverse gives; a matrix that is not numerically positive definite falls back
+      // to block Jacobi.
+      const xm_status si = spd_inverse_f32(ctx, bZ.as<float>(), n, n, nullptr);
+      if (si != XM_OK && si != XM_ENUMERIC) return si;
+      launches += g_last_launches;
+      if (si == XM_OK) {
+        XM_TRY(alloc_tiles(ctx, Pinv.q, N, XM_STORE_FP32));
+        XM_TRY(pack_dense_f32(ctx, Pinv.q, bZ.as<float>()));
+        ++launches;
+        const size_t colb = sizeof(float) * rows * R;
+        XM_CUDA_TRY(cudaMalloc(&bcol.p, colb));
+        XM_CUDA_TRY(cudaMalloc(&bcol2.p, colb));
+        XM_CUDA_TRY(cudaMemsetAsync(bcol.p, 0, colb, st));
+        XM_CUDA_TRY(cudaMemsetAsync(bcol2.p, 0, colb, st));
+        inf.dense_precond = 1;
       }
       XM_CUDA_TRY(cudaStreamSynchronize(st));   // the packing has read the inverse
-      bwork.reset();
       bZ.reset();
     }
     if (!inf.dense_precond) {

@@ -121,9 +121,6 @@ struct xm_ctx {
   double* d_partials = nullptr;
   size_t partials_cap = 0;        // doubles
   unsigned* d_counter = nullptr;
-  // cuBLAS / cuSOLVER handles for the dense FP64 translation Schur complement (lazy)
-  void* cublas = nullptr;
-  void* cusolver = nullptr;
   int build_mode = 0;             // XM_BUILD_* for xm_build_Q's dense update
 };
 
@@ -164,6 +161,12 @@ xm_status split_trsm(xm_ctx* ctx, const double* L, int ldl, double* X, int ldx, 
 // minor or 0.
 xm_status split_potrf(xm_ctx* ctx, double* A, int lda, int m, int* minor);
 
+// ------------------------------------------------------------------ SPD inverse (xm_spdinv.cu)
+// In-place inverse of the SPD n x n FP32 matrix A (column-major, lda >= n, both triangles set):
+// Schur-complement recursion with BF16-digit tensor-core products.  Synchronous; XM_ENUMERIC
+// if A is not numerically positive definite (A then undefined).  *gflop (optional): the
+// products' FP32-equivalent GFLOP.
+xm_status spd_inverse_f32(xm_ctx* ctx, float* A, int lda, int n, double* gflop);
 // ------------------------------------------------------------------ FP64 dense kernels (xm_dense.cu)
 // All column-major.  fail: optional device flag; when non-zero the launches do nothing.
 // C = alpha op(A) op(B) + beta C (op = transpose when ta / tb; lower: only C's lower triangle;

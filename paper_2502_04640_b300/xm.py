@@ -148,6 +148,7 @@ def lib() -> ctypes.CDLL:
                                          ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_size_t),
                                          ctypes.POINTER(ctypes.c_double)]),
         "xm_qfact_free": (ctypes.c_int, [_P, _P]),
+        "xm_spd_inverse": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int]),
         "xm_backward": (ctypes.c_int, [_P, _P, ctypes.POINTER(XmOpts), ctypes.c_int, _P, ctypes.c_int,
                                        ctypes.c_int, ctypes.c_int64, _P, _P, _P, _P, _P, _P, _P, _P,
                                        ctypes.POINTER(XmAdjInfo)]),
@@ -336,6 +337,18 @@ def xm_qy_factored(f: QFact, Y):
     W = torch.empty_like(Y)
     _check(lib().xm_qy_factored(f.ctx.h, f.h, Y.shape[1], _ptr(Y), _ptr(W)))
     return W
+
+
+def xm_spd_inverse(ctx: Context, A):
+    """In place: A <- A^{-1} for a symmetric positive definite float32 CUDA tensor A (n x n).
+
+    Symmetric, so the row-major tensor is its own column-major layout; returns A."""
+    import torch
+    if A.dtype != torch.float32 or A.dim() != 2 or A.shape[0] != A.shape[1] or not A.is_contiguous():
+        raise ValueError("A must be a contiguous square float32 tensor")
+    n = A.shape[0]
+    _check(lib().xm_spd_inverse(ctx.h, n, _ptr(A), max(n, 1)))
+    return A
 
 
 def xm_bench_qy(q: QMat, prec: int, r: int, iters: int = 20):

@@ -51,3 +51,22 @@ def test_default_opts_and_errors_without_device():
     assert st != xm.XM_OK or h.value    # no GPU here: a status, never a crash
     if st == xm.XM_OK:
         L.xm_destroy(h)
+
+
+def test_library_needs_no_vendor_math_library():
+    """Every kernel on the path is this library's own: libxm.so links the CUDA runtime only
+    (no cuBLAS, cuSOLVER or other vendor math library among its dynamic dependencies)."""
+    import shutil
+    import subprocess
+    if not os.path.exists(xm.LIB_PATH):
+        from paper_2502_04640_b300 import build
+        build.build()
+    readelf = shutil.which("readelf")
+    if readelf is None:
+        import pytest
+        pytest.skip("readelf not available")
+    out = subprocess.run([readelf, "-d", xm.LIB_PATH], capture_output=True, text=True, check=True).stdout
+    needed = re.findall(r"\(NEEDED\)\s+Shared library: \[([^\]]+)\]", out)
+    assert needed, out
+    vendor = [n for n in needed if re.match(r"lib(cublas|cublasLt|cusolver|cusparse|cufft|curand|cudnn)", n)]
+    assert not vendor, needed
