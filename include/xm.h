@@ -345,7 +345,7 @@ xm_status xm_backward(xm_ctx* ctx, const xm_qmat* q, const xm_opts* opts, int r,
  * preconditioner (Z + gamma Pi_Y)^{-1} above (the paper has no adjoint; Z is the certificate
  * matrix of Sec. 3).  A: device, n x n column-major with leading dimension lda >= n, both
  * triangles set; overwritten by A^{-1} (both triangles).  Block inversion by Schur complements
- * (blocks split near n / 2 at multiples of 128; FP64 Gauss-Jordan below 129 rows); the
+ * (blocks split near n / 2 at multiples of 128; Gauss-Jordan below 129 rows); the
  * products, n^3 / 2 multiply-adds in all, run on the BF16 tensor cores with every FP32 operand
  * split into three BF16 digits and FP32 accumulation (the accuracy of FP32 products).  Allocates
  * about 1.1 n^2 floats of scratch, freed before return.  Synchronous.  XM_ENUMERIC when a pivot

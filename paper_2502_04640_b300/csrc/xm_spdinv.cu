@@ -8,8 +8,8 @@
 //   X = A11^{-1} (recursively), T = A21 X, S = A22 - T A21^T, Y = S^{-1} (recursively),
 //   U = -Y T = (A^{-1})_21,  (A^{-1})_11 = X - T^T U,  (A^{-1})_12 = U^T.
 // Every Schur complement of an SPD matrix is SPD, so no pivoting is needed.  The recursion ends
-// at blocks of at most 128 rows, inverted in FP64 in shared memory by Gauss–Jordan elimination
-// (one CTA per block).  Flops: n^3 / 2 multiply-adds with the symmetric products computed on
+// at blocks of at most 128 rows, inverted in shared memory by Gauss–Jordan elimination (one CTA
+// per block).  Flops: n^3 / 2 multiply-adds with the symmetric products computed on
 // their lower triangle only, the same count as a Cholesky factorisation followed by the inverse
 // of its factor.
 //
@@ -60,8 +60,9 @@ constexpr uint32_t SI_B_BYTES = SI_BN * SI_BK * 2;              // one B digit b
 constexpr uint32_t SI_TMEM_COLS = SI_ACC * SI_BN;
 constexpr size_t SI_SMEM = 1024 + (size_t)SI_ASTAGES * SI_AUNIT + (size_t)SI_BSTAGES * SI_B_BYTES + 256;
 constexpr int SI_LEAF = 128;                 // largest block inverted directly
-constexpr int SI_LEAF_LD = SI_LEAF + 1;      // shared-memory row stride of the leaf (doubles)
-constexpr size_t SI_LEAF_SMEM = sizeof(double) * ((size_t)SI_LEAF * SI_LEAF_LD + 2 * SI_LEAF);
+constexpr int SI_LEAF_LD = SI_LEAF + 4;      // shared-memory row stride of the leaf (floats)
+constexpr size_t SI_LEAF_SMEM =              // block, column panel, row panel, D times it, D
+    sizeof(float) * ((size_t)SI_LEAF * SI_LEAF_LD + SI_LEAF * 17 + 2 * 16 * SI_LEAF_LD + 16 * 20);
 constexpr int SI_LEAF_THREADS = 512;
 
 // kind::f16 instruction descriptor: D FP32, A and B BF16, both K-major, N = 256, M = 128
@@ -306,47 +307,136 @@ __global__ void __launch_bounds__(256) k_si_split(const float* __restrict__ src,
 
 // ------------------------------------------------------------------ leaves and transposes
 // In-place inverse of an SPD m x m block (m <= 128; column-major FP32, leading dimension lda,
-// both triangles valid) by Gauss–Jordan elimination in FP64 in shared memory, without pivoting:
-// at step p the pivot is a diagonal entry of a Schur complement of the SPD block, hence
-// positive.  Step p maps row p to a_pj / a_pp, column p to -a_ip / a_pp, the pivot to 1 / a_pp
-// and every other entry to a_ij - a_ip a_pj / a_pp.  A pivot that is not positive and finite
-// sets *fail and leaves the block unfinished.
+// both triangles valid) by blocked Gauss–Jordan elimination in FP32 in shared memory, without
+// pivoting (every pivot block is a diagonal block of a Schur complement of the SPD matrix,
+// hence SPD).  The block is padded to 128 x 128 with the identity.  Eliminating the 16 pivots of
+// block K at once, with D = A_KK^{-1}:
+//   A_KK <- D,  A_KR <- D A_KR,  A_RK <- -A_RK D,  A_RR <- A_RR - A_RK (D A_KR)
+// (R: every index outside K; the single-pivot step is the case |K| = 1).  D comes from
+// single-pivot steps on the 16 x 16 block by one warp; the rank-16 update runs on all threads,
+// thread t owning rows 4 (t / 16) .. + 3 and columns 8 (t % 16) .. + 7 (one 4-row group and one
+// 8-column group lie wholly inside or outside K).  FP32 like the products around it (an FP64
+// version took 2 ms per block on B300's FP64 units, the unblocked FP32 one 0.45 ms).  A pivot
+// of D that is not positive and finite sets *fail and leaves the block unfinished.
+constexpr int SI_LB = 16;                     // pivots eliminated together
+constexpr int SI_DLD = 20;                    // row stride of D (16-byte aligned rows)
+static_assert(SI_LEAF_SMEM == sizeof(float) * ((size_t)SI_LEAF * SI_LEAF_LD + SI_LEAF * (SI_LB + 1) +
+                                               2 * SI_LB * SI_LEAF_LD + SI_LB * SI_DLD),
+              "leaf shared-memory layout");
 __global__ void __launch_bounds__(SI_LEAF_THREADS) k_si_leaf(float* __restrict__ A, int lda, int m,
                                                              int* __restrict__ fail) {
-  extern __shared__ double s[];
-  double* rowp = s + (size_t)SI_LEAF * SI_LEAF_LD;
-  double* colp = rowp + SI_LEAF;
-  const int mm = m * m;
-  for (int e = threadIdx.x; e < mm; e += blockDim.x) {
-    const int i = e % m, j = e / m;                     // coalesced along i
-    s[i * SI_LEAF_LD + j] = (double)A[i + (size_t)j * lda];
+  extern __shared__ float4 sm4[];
+  float* s = reinterpret_cast<float*>(sm4);               // [128][SI_LEAF_LD]
+  float* Cp = s + SI_LEAF * SI_LEAF_LD;                   // [128][SI_LB + 1]: old column panel
+  float* Rp = Cp + SI_LEAF * (SI_LB + 1);                 // [SI_LB][SI_LEAF_LD]: old row panel
+  float* Pp = Rp + SI_LB * SI_LEAF_LD;                    // [SI_LB][SI_LEAF_LD]: D times Rp
+  float* Dm = Pp + SI_LB * SI_LEAF_LD;                    // [SI_LB][SI_DLD]
+  __shared__ int bad;
+  const int t = threadIdx.x;
+  for (int e = t; e < SI_LEAF * SI_LEAF; e += blockDim.x) {
+    const int i = e & (SI_LEAF - 1), j = e >> 7;         // coalesced along i
+    s[i * SI_LEAF_LD + j] = (i < m && j < m) ? A[i + (size_t)j * lda] : (i == j ? 1.f : 0.f);
   }
+  if (t == 0) bad = 0;
   __syncthreads();
-  for (int p = 0; p < m; ++p) {
-    for (int t = threadIdx.x; t < m; t += blockDim.x) {
-      rowp[t] = s[p * SI_LEAF_LD + t];
-      colp[t] = s[t * SI_LEAF_LD + p];
+  const int i0 = 4 * (t >> 4), j0 = 8 * (t & 15);
+  for (int p0 = 0; p0 < SI_LEAF; p0 += SI_LB) {
+    // old panels: columns K of every row, rows K of every column
+    for (int e = t; e < SI_LEAF * SI_LB; e += blockDim.x) {
+      const int i = e >> 4, l = e & (SI_LB - 1);
+      Cp[i * (SI_LB + 1) + l] = s[i * SI_LEAF_LD + p0 + l];
+      const int l2 = e >> 7, j = e & (SI_LEAF - 1);
+      Rp[l2 * SI_LEAF_LD + j] = s[(p0 + l2) * SI_LEAF_LD + j];
     }
     __syncthreads();
-    const double piv = rowp[p];
-    if (!(piv > 0.0 && piv < 1e300)) {                  // the same decision in every thread
-      if (threadIdx.x == 0) atomicOr(fail, 1);
+    if (t < 32) {
+      // D = A_KK^{-1}: lane t owns row t / 2, columns 8 (t % 2) .. + 7
+      const int a = t >> 1, b0 = 8 * (t & 1);
+      for (int k = 0; k < 8; ++k) Dm[a * SI_DLD + b0 + k] = Rp[a * SI_LEAF_LD + p0 + b0 + k];
+      __syncwarp();
+      for (int q = 0; q < SI_LB; ++q) {
+        const float piv = Dm[q * SI_DLD + q];
+        if (!(piv > 0.f && piv < 3.0e38f)) {           // the same decision in every lane
+          if (t == 0) bad = 1;
+          break;
+        }
+        const float inv = 1.f / piv;
+        const float cq = Dm[a * SI_DLD + q];
+        float rq[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) rq[k] = Dm[q * SI_DLD + b0 + k];
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int b = b0 + k;
+          float v;
+          if (a == q) v = b == q ? inv : rq[k] * inv;
+          else if (b == q) v = -cq * inv;
+          else v = fmaf(-cq, rq[k] * inv, Dm[a * SI_DLD + b]);
+          Dm[a * SI_DLD + b] = v;
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    if (bad) {
+      if (t == 0) atomicOr(fail, 1);
       return;
     }
-    const double inv = 1.0 / piv;
-    for (int e = threadIdx.x; e < mm; e += blockDim.x) {
-      const int i = e / m, j = e - i * m;
-      double v;
-      if (i == p) v = j == p ? inv : rowp[j] * inv;
-      else if (j == p) v = -colp[i] * inv;
-      else v = s[i * SI_LEAF_LD + j] - colp[i] * (rowp[j] * inv);
-      s[i * SI_LEAF_LD + j] = v;
+    // P = D Rp (16 x 128)
+    for (int e = t; e < SI_LB * SI_LEAF; e += blockDim.x) {
+      const int a = e >> 7, j = e & (SI_LEAF - 1);
+      float acc = 0.f;
+#pragma unroll
+      for (int l = 0; l < SI_LB; ++l) acc = fmaf(Dm[a * SI_DLD + l], Rp[l * SI_LEAF_LD + j], acc);
+      Pp[a * SI_LEAF_LD + j] = acc;
+    }
+    __syncthreads();
+    // rank-16 update of this thread's 4 x 8 block
+    const bool iK = i0 >= p0 && i0 < p0 + SI_LB, jK = j0 >= p0 && j0 < p0 + SI_LB;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int i = i0 + r;
+      float acc[8];
+      float4* dst = reinterpret_cast<float4*>(s + i * SI_LEAF_LD + j0);
+      if (iK) {
+        const float* src = jK ? Dm + (i - p0) * SI_DLD + (j0 - p0) : Pp + (i - p0) * SI_LEAF_LD + j0;
+        const float4 u0 = *reinterpret_cast<const float4*>(src);
+        const float4 u1 = *reinterpret_cast<const float4*>(src + 4);
+        acc[0] = u0.x; acc[1] = u0.y; acc[2] = u0.z; acc[3] = u0.w;
+        acc[4] = u1.x; acc[5] = u1.y; acc[6] = u1.z; acc[7] = u1.w;
+      } else {
+        if (jK) {
+#pragma unroll
+          for (int k = 0; k < 8; ++k) acc[k] = 0.f;
+        } else {
+          const float4 u0 = dst[0], u1 = dst[1];
+          acc[0] = u0.x; acc[1] = u0.y; acc[2] = u0.z; acc[3] = u0.w;
+          acc[4] = u1.x; acc[5] = u1.y; acc[6] = u1.z; acc[7] = u1.w;
+        }
+        const float* srow = jK ? Dm + (j0 - p0) : Pp + j0;
+        const int sld = jK ? SI_DLD : SI_LEAF_LD;
+#pragma unroll
+        for (int l = 0; l < SI_LB; ++l) {
+          const float c = Cp[i * (SI_LB + 1) + l];
+          const float4 u0 = *reinterpret_cast<const float4*>(srow + l * sld);
+          const float4 u1 = *reinterpret_cast<const float4*>(srow + l * sld + 4);
+          acc[0] = fmaf(-c, u0.x, acc[0]); acc[1] = fmaf(-c, u0.y, acc[1]);
+          acc[2] = fmaf(-c, u0.z, acc[2]); acc[3] = fmaf(-c, u0.w, acc[3]);
+          acc[4] = fmaf(-c, u1.x, acc[4]); acc[5] = fmaf(-c, u1.y, acc[5]);
+          acc[6] = fmaf(-c, u1.z, acc[6]); acc[7] = fmaf(-c, u1.w, acc[7]);
+        }
+      }
+      dst[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+      dst[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
     }
     __syncthreads();
   }
-  for (int e = threadIdx.x; e < mm; e += blockDim.x) {
-    const int i = e % m, j = e / m;
-    A[i + (size_t)j * lda] = (float)s[i * SI_LEAF_LD + j];
+  // both triangles from the computed lower triangle (the elimination's rounding is not
+  // symmetric; the inverse is)
+  for (int e = t; e < m * m; e += blockDim.x) {
+    const int r = e % m, c = e / m;
+    A[r + (size_t)c * lda] = r >= c ? s[r * SI_LEAF_LD + c] : s[c * SI_LEAF_LD + r];
   }
 }
 
