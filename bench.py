@@ -40,12 +40,10 @@ WORKLOADS = {
 # objective options per workload: the trajectory's unregularised optimum collapses the scales of
 # later frames towards zero (App. D), so it is solved with the scale regulariser
 WORKLOAD_OPTS = {"c4": {"scale_reg": 10.0}}
-# solver options of the timed certified solve per workload (not of the adjoint's forward solve,
-# whose residual floor is set by how stationary Y is): the trajectory's FP32 bulk phase
-# stagnates for tens of thousands of tCG iterations above its tolerance, so it hands over to the
-# FP64 polish after 5 outer steps without progress (3.9 -> 0.56 s, certified, f within 1.1e-9);
-# on the 10155-camera scene the same hand-over costs time (0.84 -> 1.55 s) and stays off
-SOLVE_OPTS = {"c4": {"bulk_stall": 5}}
+# solver options of the timed certified solve per workload beyond the objective's: none (the
+# defaults hand the FP32 bulk phase over at its noise floor and precondition the tCG when it
+# keeps stopping at its iteration cap, which the trajectory needs and the other workloads do not)
+SOLVE_OPTS = {}
 BATCH_DESC = ("256 independent scenes, cameras log-uniform in [10, 400] (floor), 50 landmarks per "
               "camera x 4 observers, keypoint noise N(0, 0.01^2), unit weights; FP32 bulk, one "
               "persistent launch per rank class under a CUDA graph, autotuned block-row tiling")
@@ -661,20 +659,21 @@ def _c2_compare(ctx, steps):
 
 def _c4_solve_and_adjoint(ctx, steps):
     """2000-frame trajectory (App. D weight 10): the certified FP32-bulk solve with the default
-    hand-over and with bulk_stall = 5, and the adjoint (FP32 inner CG in FP64 refinement)."""
+    options (automatic hand-over, adaptive tCG preconditioner), once without either (the bulk
+    then runs to its iteration cap), and the adjoint (FP32 inner CG in FP64 refinement)."""
     import torch
     from paper_2502_04640_b300 import xm
     sc = scenes.config4()
     wopts = dict(WORKLOAD_OPTS["c4"])
     q = xm.xm_build_Q(ctx, sc.N, sc.M, *xm.scene_tensors(sc), xm.XM_STORE_ALL)
     res = {"N": sc.N, "E": sc.E, "opts": wopts}
-    outs, walls = _timed_solves(xm, q, xm.xm_default_opts(prec=1, **wopts), 0, 1)
-    res["solve_default_s"] = walls[0]
-    res["solve_default_certified"] = outs[0]["info"]["certified"]
+    outs, walls = _timed_solves(xm, q, xm.xm_default_opts(prec=1, **wopts), 1, steps)
+    res["solve_default_s"] = statistics.median(walls)
+    res["solve_default_certified"] = all(o["info"]["certified"] for o in outs)
     out = outs[0]      # the adjoint's forward solve: default options (its stationarity sets the floor)
-    stalls, walls = _timed_solves(xm, q, xm.xm_default_opts(prec=1, bulk_stall=5, **wopts), 1, steps)
-    res["solve_bulk_stall5_s"] = statistics.median(walls)
-    res["solve_bulk_stall5_certified"] = all(o["info"]["certified"] for o in stalls)
+    plain, walls = _timed_solves(xm, q, xm.xm_default_opts(prec=1, bulk_stall=0, precond=0, **wopts), 0, 1)
+    res["solve_no_handover_s"] = walls[0]
+    res["solve_no_handover_certified"] = plain[0]["info"]["certified"]
     r = out["info"]["rank"]
     t = xm.scene_tensors(sc)
     D = torch.as_tensor(np.random.default_rng(5).standard_normal((sc.N, 3, 3)), device="cuda:0")

@@ -96,17 +96,22 @@ typedef struct xm_opts {
                               non-anchor block, paper's 1-based indexing); Z, the dual value
                               and the suboptimality bounds follow App. D / App. E.  0 (the
                               default): the plain objective of Eq. 17.  Must be >= 0.        */
-  int precond;             /* tCG preconditioner: 0 (default) plain Steihaug-Toint tCG
-                              (Sec. 3.2); 1: block Jacobi z_i = P(B_i^-1 r_i), B_i = 2 Q_ii
-                              (eigenvalues clamped at 1e-6 of the largest), trust region in the
-                              B-norm (halves the sweeps on the 1934-camera workload, slower on
-                              the 10155-camera one)                                            */
-  int bulk_stall;          /* mixed modes: k > 0 hands the FP32 bulk phase over to the FP64
-                              polish once ||rgrad|| <= 1e-6 ||rgrad(Y0)|| and the best objective
-                              has not improved by more than the ratio test's FP32 noise allowance
-                              over k outer steps (the FP32 objective is noise there); the polish
-                              starts from the bulk's trust radius.  0 (default) runs the bulk
-                              to bulk_tol_rel or max_outer.  0 <= k <= max_outer            */
+  int precond;             /* tCG preconditioner: 0 plain Steihaug-Toint tCG (Sec. 3.2);
+                              1: block Jacobi z_i = P(B_i^-1 r_i), B_i = 2 Q_ii (eigenvalues
+                              clamped at 1e-6 of the largest), trust region in the B-norm
+                              (halves the sweeps on the 1934-camera workload, slower on the
+                              10155-camera one); 2 (default): adaptive, plain until three tCG
+                              solves in a row stop at max_tcg, block Jacobi from then on     */
+  int bulk_stall;          /* mixed modes, hand-over from the FP32 bulk phase to the FP64
+                              polish before bulk_tol_rel when FP32 has stopped converging (both
+                              rules only once ||rgrad|| <= 1e-6 ||rgrad(Y0)||; the polish starts
+                              from the bulk's trust radius).  -1 (default): automatic, at the FP32 noise
+                              floor: the running minimum of ||rgrad|| has not halved over 15
+                              outer steps and the last three tCG solves stopped at max_tcg.
+                              k > 0: when the best objective has not improved by
+                              more than the ratio test's FP32 noise allowance over k outer steps.
+                              0: run the bulk to bulk_tol_rel or max_outer.  Default -1.
+                              -1 <= bulk_stall <= max_outer                                   */
   int cert_lobpcg;         /* certificates with FP32 Z products (mixed modes): 1 (default)
                               finds lambda_min(Z) on range(Y)^perp by block-Jacobi preconditioned
                               LOBPCG (blocks of 4, stop at a Ritz residual <= 1e-6 lambda_max,

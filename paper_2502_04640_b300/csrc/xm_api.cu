@@ -108,8 +108,8 @@ void xm_default_opts(xm_opts* o) {
   o->verbose = 0;
   o->init_jitter = 0.1;
   o->scale_reg = 0.0;
-  o->precond = 0;
-  o->bulk_stall = 0;
+  o->precond = 2;
+  o->bulk_stall = -1;
   o->cert_lobpcg = 1;
   o->bf16_hvp_until = 0.0;
 }

@@ -459,6 +459,8 @@ struct Solver {
          *lnrm = nullptr, *lritz = nullptr;
   float *lv32 = nullptr, *lW32 = nullptr, *lwf = nullptr, *lcf = nullptr;
   static constexpr int LPART_MAX = 64;   // column chunks of the reorthogonalisation product
+  static constexpr int BULK_PLATEAU = 15; // outer steps without a halving of min ||rgrad||
+  static constexpr int PRECOND_CAP_RUN = 3; // capped tCG solves in a row that switch on precond = 2
   double* lpart = nullptr;               // LPART_MAX x n_pad partial sums
   int last_nd = 0;                       // deflation columns of the last certificate's basis
   // LOBPCG certificate: 12 blocks of n_pad x 4 floats, preconditioner, Gram partials, scalars
@@ -526,15 +528,20 @@ struct Solver {
     XM_CUDA_TRY(cudaMallocHost(&h_flags, 2 * sizeof(int)));
     XM_CUDA_TRY(cudaStreamCreateWithFlags(&cap_st, cudaStreamNonBlocking));
     XM_TRY(ensure_partials(ctx, (size_t)std::max(nb_cam, 1024) * 64));
-    if (o.precond) {
-      XM_CUDA_TRY(cudaMalloc(&pcMinv, sizeof(double) * 9 * (size_t)N));
-      XM_CUDA_TRY(cudaMalloc(&pcB, sizeof(double) * 9 * (size_t)N));
-      // Q's 3 x 3 diagonal blocks: FP64 tiles, else the FP32 ones (a preconditioner)
-      if (q.q64) k_tcg_precond_blocks<double><<<nb_cam, CAM_THREADS, 0, st>>>(N, q.q64, q.nt, pcMinv, pcB);
-      else k_tcg_precond_blocks<float><<<nb_cam, CAM_THREADS, 0, st>>>(N, q.q32, q.nt, pcMinv, pcB);
-      ++launches;
-      XM_CUDA_TRY(cudaGetLastError());
-    }
+    if (o.precond == 1) XM_TRY(enable_precond());
+    return XM_OK;
+  }
+
+  // the tCG's block-Jacobi preconditioner: Q's 3 x 3 diagonal blocks from the FP64 tiles, else
+  // the FP32 ones (a preconditioner)
+  xm_status enable_precond() {
+    if (pcMinv) return XM_OK;
+    XM_CUDA_TRY(cudaMalloc(&pcMinv, sizeof(double) * 9 * (size_t)N));
+    XM_CUDA_TRY(cudaMalloc(&pcB, sizeof(double) * 9 * (size_t)N));
+    if (q.q64) k_tcg_precond_blocks<double><<<nb_cam, CAM_THREADS, 0, st>>>(N, q.q64, q.nt, pcMinv, pcB);
+    else k_tcg_precond_blocks<float><<<nb_cam, CAM_THREADS, 0, st>>>(N, q.q32, q.nt, pcMinv, pcB);
+    ++launches;
+    XM_CUDA_TRY(cudaGetLastError());
     return XM_OK;
   }
 
@@ -638,7 +645,7 @@ struct Solver {
       XM_TRY(pull_scalars());
       ynorm2 = h_sc->dot;
     }
-    const double Delta_bar = std::sqrt(std::max(ynorm2, 1e-300));
+    double Delta_bar = std::sqrt(std::max(ynorm2, 1e-300));
     double Delta = Delta_bar / 8.0;
     if (!bulk && carry_delta > 0.0) Delta = std::min(carry_delta, Delta_bar);   // polish after a stall
     carry_delta = 0.0;
@@ -648,18 +655,23 @@ struct Solver {
     int rejects = 0;
     // BF16-tile Hessian products early in the FP32 bulk phase (opts.bf16_hvp_until)
     const bool bf16_early = bulk && prec_hvp == XM_FP32_BULK && o.bf16_hvp_until > 0.0 && q.q16;
-    double best_f = f;   // bulk stagnation test (opts.bulk_stall)
+    double best_f = f;   // bulk stagnation test (opts.bulk_stall > 0)
     int stall = 0;
+    double g_halved = std::sqrt(g2);   // automatic hand-over (opts.bulk_stall < 0): the gradient
+    int since_halved = 0;              // norm at its last halving, outer steps since then
+    int cap_run = 0;                   // consecutive tCG solves stopped by the iteration cap
     // captured tCG chunks of this call, keyed by the (iterate, Lambda) buffers they read
     struct ChunkGraph { const void* yin; const double* lam; int prec; cudaGraphExec_t exec; };
     struct GraphCache {
       ChunkGraph e[2] = {{nullptr, nullptr, 0, nullptr}, {nullptr, nullptr, 0, nullptr}};
       int n = 0;
       cudaStream_t s = nullptr;
-      ~GraphCache() {
+      void clear() {
         if (n > 0) cudaStreamSynchronize(s);   // no launch of these graphs still in flight
         for (int i = 0; i < n; ++i) cudaGraphExecDestroy(e[i].exec);
+        n = 0;
       }
+      ~GraphCache() { clear(); }
     } gcache;
     gcache.s = st;
     ChunkGraph* cg = gcache.e;
@@ -759,6 +771,7 @@ struct Solver {
       XM_TRY(pull_scalars());
       ++info.n_outer;
       info.n_tcg += h_sc->iters;
+      cap_run = h_sc->reason == 4 ? cap_run + 1 : 0;
       // one Hessian-vector sweep per tCG iteration (the sweeps of chunks queued after the
       // device stopped returned at once and are not counted)
       info.n_sweeps += h_sc->iters;
@@ -795,7 +808,20 @@ struct Solver {
       }
       if (Delta < 1e-12 * Delta_bar) break;
       if (bulk && (rejects >= 6 || Delta < 1e-7 * Delta_bar)) break;
-      if (bulk && o.bulk_stall) {
+      if (bulk && o.bulk_stall < 0) {
+        // automatic: FP32 has reached its noise floor when the running minimum of the
+        // gradient norm has not halved over BULK_PLATEAU outer steps (below 1e-6 of its start)
+        // while the inner solves no longer reach their tolerance (the last PRECOND_CAP_RUN tCG
+        // solves stopped at max_tcg); the FP64 polish takes over from there.  Where FP32 keeps
+        // converging the minimum halves every few steps down to bulk_tol_rel
+        const double gn = std::sqrt(g2);
+        if (gn <= 0.5 * g_halved) { g_halved = gn; since_halved = 0; } else { ++since_halved; }
+        if (since_halved >= BULK_PLATEAU && cap_run >= PRECOND_CAP_RUN && gn <= 1e-6 * ref_g) {
+          carry_delta = Delta;
+          bulk_stalled = true;
+          break;
+        }
+      } else if (bulk && o.bulk_stall > 0) {
         // the FP32 objective has stopped improving beyond its own noise (the ratio test's
         // allowance reg): further FP32 steps only chase rounding, the FP64 polish takes over
         if (f < best_f - reg) { best_f = f; stall = 0; } else { ++stall; }
@@ -805,6 +831,21 @@ struct Solver {
           bulk_stalled = true;
           break;
         }
+      }
+      if (o.precond == 2 && !pcMinv && cap_run >= PRECOND_CAP_RUN && (q.q64 || q.q32)) {
+        // adaptive: the Hessian is too ill-conditioned for max_tcg plain CG steps; precondition
+        // every later tCG (this and the following RTR calls).  The chunk graphs captured the
+        // unpreconditioned launches; the trust region moves to the B-norm, radius rescaled.
+        gcache.clear();
+        XM_TRY(enable_precond());
+        k_bnorm<To, R><<<nb_cam, CAM_THREADS, 0, st>>>(N, (const To*)bY, pcB, d_sc, ctx->d_partials,
+                                                        ctx->d_counter);
+        ++launches;
+        XM_TRY(pull_scalars());
+        const double bar_b = std::sqrt(std::max(h_sc->dot, 1e-300));
+        Delta *= bar_b / Delta_bar;
+        Delta_bar = bar_b;
+        if (o.verbose >= 1) fprintf(stderr, "[xm] tCG at its cap %d times: block-Jacobi preconditioner on\n", cap_run);
       }
     }
     info.f = f;
@@ -1609,13 +1650,13 @@ xm_status check_opts(const DeviceQ& q, const xm_opts& o) {
     return set_error(XM_EINVAL, "opts: iteration caps must be positive");
   if (!(o.scale_reg >= 0.0) || !std::isfinite(o.scale_reg))
     return set_error(XM_EINVAL, "opts: scale_reg must be finite and >= 0 (got %g)", o.scale_reg);
-  if (o.precond != 0 && o.precond != 1) return set_error(XM_EINVAL, "opts: precond must be 0 or 1");
+  if (o.precond < 0 || o.precond > 2) return set_error(XM_EINVAL, "opts: precond must be 0, 1 or 2");
   if (o.cert_lobpcg != 0 && o.cert_lobpcg != 1) return set_error(XM_EINVAL, "opts: cert_lobpcg must be 0 or 1");
   if (!(o.bf16_hvp_until >= 0.0)) return set_error(XM_EINVAL, "opts: bf16_hvp_until must be >= 0");
   if (o.bf16_hvp_until > 0.0 && o.prec == XM_FP32_BULK && !q.q16)
     return set_error(XM_EINVAL, "solve: bf16_hvp_until > 0 needs XM_STORE_BF16");
-  if (o.bulk_stall < 0 || o.bulk_stall > o.max_outer)
-    return set_error(XM_EINVAL, "opts: bulk_stall must be in [0, max_outer] (got %d)", o.bulk_stall);
+  if (o.bulk_stall < -1 || o.bulk_stall > o.max_outer)
+    return set_error(XM_EINVAL, "opts: bulk_stall must be -1 or in [0, max_outer] (got %d)", o.bulk_stall);
   return XM_OK;
 }
 

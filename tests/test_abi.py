@@ -39,7 +39,7 @@ def test_default_opts_and_errors_without_device():
     documented = dict(prec=xm.XM_FP32_BULK, grad_tol_rel=1e-11, bulk_tol_rel=1e-9, max_outer=300,
                       max_tcg=200, max_polish=20, lanczos_max=800, lanczos_tol=1e-8,
                       time_limit_s=0.0, seed=12345, verbose=0, init_jitter=0.1, scale_reg=0.0,
-                      precond=0, bulk_stall=0, cert_lobpcg=1)
+                      precond=2, bulk_stall=-1, cert_lobpcg=1)
     for field, value in documented.items():
         assert getattr(o, field) == value, field
     L = xm.lib()

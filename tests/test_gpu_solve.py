@@ -224,22 +224,25 @@ def test_block_jacobi_tcg_reaches_the_oracle_optimum(C, name):
         q.free()
 
 
-def test_bulk_stall_option():
-    """opts.bulk_stall = k hands the FP32 bulk phase to the FP64 polish once the FP32 objective
-    has stopped improving beyond its noise for k outer steps: the result is still the certified
-    optimum (k = 5, the earliest hand-over tried)."""
+@pytest.mark.parametrize("stall,precond", [(5, 0), (-1, 2), (0, 0), (0, 1)])
+def test_bulk_stall_option(stall, precond):
+    """The FP32 bulk phase's hand-over rules (opts.bulk_stall: k = 5 after five outer steps
+    without an FP32 objective improvement beyond its noise, -1 automatic at the gradient's
+    noise floor, 0 none) and the tCG preconditioner settings (0 plain, 1 block Jacobi, 2
+    adaptive) all reach the oracle's certified optimum; out-of-range values are rejected."""
     from paper_2502_04640_b300 import xm
     from oracle import xm_oracle as O
     sc = scenes.random_scene(80, 1600, noise=0.02, outlier_frac=0.02, seed=21, center_sigma=3.0)
     ctx = xm.Context(0)
     q = xm.xm_build_Q(ctx, sc.N, sc.M, *xm.scene_tensors(sc))
-    out = xm.xm_solve(q, xm.xm_default_opts(prec=xm.XM_FP32_BULK, bulk_stall=5))
+    out = xm.xm_solve(q, xm.xm_default_opts(prec=xm.XM_FP32_BULK, bulk_stall=stall, precond=precond))
     ref = O.solve(O.build_Q_schur(sc.N, sc.M, sc.cam, sc.lmk, sc.ukp, sc.w), r0=4)
     assert out["info"]["certified"] == 1 and ref.certified
     assert abs(out["info"]["f"] - ref.f) / (1.0 + abs(ref.f)) <= 1e-6
-    with pytest.raises(xm.XmError) as e:
-        xm.xm_solve(q, xm.xm_default_opts(prec=xm.XM_FP32_BULK, bulk_stall=-1))
-    assert e.value.status == xm.XM_EINVAL
+    for bad in (dict(bulk_stall=-2), dict(precond=3), dict(precond=-1)):
+        with pytest.raises(xm.XmError) as e:
+            xm.xm_solve(q, xm.xm_default_opts(prec=xm.XM_FP32_BULK, **bad))
+        assert e.value.status == xm.XM_EINVAL
     q.free()
     ctx.close()
 
