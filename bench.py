@@ -855,6 +855,51 @@ def run_adjoint(args):
     return 0
 
 
+def run_spd_inverse(args):
+    """xm_spd_inverse on A = G G^T / n + 0.05 I (G seeded standard normal, n x n FP32): W untimed
+    and K timed calls (CUDA events on the context stream, a fresh copy of A before each), the
+    residual A X - I in FP64 on 64 seeded columns; flops n^3 (n^3 / 2 multiply-adds), BF16 tensor
+    flops 6 n^3 (six digit products per multiply-add)."""
+    import torch
+    from paper_2502_04640_b300 import xm
+    n = args.spd_inverse
+    ctx = xm.Context(0)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    G = torch.randn(n, n, device="cuda", generator=g, dtype=torch.float32)
+    A = torch.addmm(torch.eye(n, device="cuda"), G, G.T, beta=0.05, alpha=1.0 / n)
+    A = 0.5 * (A + A.T)
+    del G
+    X = torch.empty_like(A)
+    st = torch.cuda.current_stream()
+    times = []
+    for i in range(args.warmup + args.steps):
+        X.copy_(A)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        xm.xm_spd_inverse(ctx, X)
+        e1.record(st)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            times.append(e0.elapsed_time(e1) * 1e-3)
+    idx = torch.randint(0, n, (64,), device="cuda", generator=torch.Generator(device="cuda").manual_seed(1))
+    Rm = A.double() @ X[:, idx].double()
+    Rm[idx, torch.arange(64, device="cuda")] -= 1.0
+    t = statistics.median(times)
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            bf16, kind = float(json.load(fh)["bf16_tflops"]), "measured"
+    except Exception:
+        bf16, kind = 1800.0, "fallback"
+    print(json.dumps({"spd_inverse": True, "n": n, "steps": args.steps, "warmup": args.warmup,
+                      "s_median": t, "s_min": min(times), "launches": xm.xm_last_launch_count(),
+                      "fp32_equiv_tflops": n ** 3 / t / 1e12, "bf16_tensor_tflops": 6 * n ** 3 / t / 1e12,
+                      "bf16_peak_tflops": bf16, "peak_kind": kind,
+                      "frac_of_bf16_peak": (6 * n ** 3 / t / 1e12) / bf16,
+                      "residual_max": Rm.abs().max().item()}), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -889,6 +934,9 @@ def main():
     ap.add_argument("--noise-sweep", action="store_true",
                     help="depth-noise robustness table (certified rate, eta, rotation and scale errors "
                          "across the noise levels of the paper's noise analysis)")
+    ap.add_argument("--spd-inverse", type=int, default=0, metavar="n",
+                    help="time only xm_spd_inverse (the adjoint preconditioner's dense inverse) on a "
+                         "seeded SPD n x n FP32 matrix (n = 30465 is the 10155-camera size)")
     ap.add_argument("--no-others", action="store_true",
                     help="skip the other workloads (1934 cameras, trajectory + adjoint, batch) that the "
                          "default line measures after its timed region")
@@ -903,6 +951,8 @@ def main():
         return 0
     if args.recover:
         return run_recover(args)
+    if args.spd_inverse:
+        return run_spd_inverse(args)
 
     if args.warmup < 3 and not args.profile_solve:
         ap.error("--warmup must be >= 3")
