@@ -53,7 +53,7 @@ DTYPES = {"fp64": "f64", "fp32": "f32", "bf16": "bf16/f32"}
 # of this benchmark (10155 cameras: mean of the 20 timed solves of a 20-step run; the others:
 # mean of 5 or 2); the reference arm multiplies the oracle's time per sweep by it (an
 # extrapolation, labelled as such in its line).
-REFERENCE_SWEEPS = {"c3": 2230, "c2": 575, "c4": 8737, "c1": 500}
+REFERENCE_SWEEPS = {"c3": 2230, "c2": 575, "c4": 11500, "c1": 500}
 L2_BYTES = 126e6
 # DRAM bytes (read + write) over algorithmic bytes of qy_packed_kernel<float,4,8> from one ncu
 # capture at the 10155-camera size itself (n = 30465: 1.8832 GB read + 0.0040 GB written per
