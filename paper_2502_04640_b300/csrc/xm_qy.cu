@@ -114,9 +114,15 @@ struct SweepCfg {
   static constexpr int CHUNK = (RPW * R <= 32) ? RPW : (32 / R);   // rows per butterfly
   static constexpr int NCHUNK = RPW / CHUNK;
   static constexpr int V = CHUNK * R;
-  static constexpr int THREADS = 32 * (NW + 1);
   // FP32 accumulation with R >= 2 uses packed pairs; Y_I is then staged as duplicated pairs
   static constexpr bool PAIR = sizeof(A) == 4 && R >= 2;
+  // CRED: the consumer warps hand their column partials of each tile to a reducer warp through
+  // NPB shared-memory buffers; it adds the NW copies and issues one set of vector reductions
+  // into W_J per tile (NW sets otherwise: the dominant L2 traffic of the FP32 sweep after Q)
+  static constexpr bool CRED = PAIR;
+  static constexpr int NPB = 2;
+  static constexpr size_t PART_BYTES = CRED ? (size_t)NW * TILE * R * sizeof(A) : 0;
+  static constexpr int THREADS = 32 * (NW + 1 + (CRED ? 1 : 0));
   // row partials kept per tile row (reduced across lanes once per tile row) when they fit
   static constexpr bool DEFER = PAIR && SLABS * RPW * R <= 64;
   static constexpr size_t YSM_BYTES = sizeof(A) * TILE * R * (PAIR ? 2 : 1);
@@ -130,7 +136,7 @@ struct SweepCfg {
   static constexpr int YV_ROWS = TILE * R / 32;            // 32-float rows of one Y_J tile
   static size_t smem_bytes(int nstage) {
     return 1024 + (size_t)nstage * SLAB_BYTES + YSM_BYTES + (size_t)YJ_SLOTS * YJ_BYTES +
-           16 * (size_t)(nstage + YJ_SLOTS);
+           (size_t)NPB * PART_BYTES + 16 * (size_t)(nstage + YJ_SLOTS + (CRED ? NPB : 0));
   }
 };
 
@@ -151,11 +157,14 @@ qy_packed_kernel(const TQ* __restrict__ tiles, int nt, int64_t ntiles, int nstag
   unsigned char* stages = base;
   A* ysm = reinterpret_cast<A*>(stages + (size_t)nstage * SLAB_BYTES);
   A* yjs = reinterpret_cast<A*>(reinterpret_cast<unsigned char*>(ysm) + C::YSM_BYTES);
-  uint64_t* full = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(yjs) +
-                                               (size_t)C::YJ_SLOTS * C::YJ_BYTES);
+  A* part = reinterpret_cast<A*>(reinterpret_cast<unsigned char*>(yjs) + (size_t)C::YJ_SLOTS * C::YJ_BYTES);
+  uint64_t* full = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(part) +
+                                               (size_t)C::NPB * C::PART_BYTES);
   uint64_t* empty = full + nstage;
   uint64_t* fully = empty + nstage;
   uint64_t* emptyy = fully + C::YJ_SLOTS;
+  uint64_t* pfull = emptyy + C::YJ_SLOTS;    // [NPB] (CRED): partials of every consumer warp written
+  uint64_t* pempty = pfull + C::NPB;         // [NPB] (CRED): the reducer has read the buffer
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t t0 = ntiles * blockIdx.x / gridDim.x;
@@ -170,6 +179,11 @@ qy_packed_kernel(const TQ* __restrict__ tiles, int nt, int64_t ntiles, int nstag
       mbar_init(&fully[s], 1);
       mbar_init(&emptyy[s], NW);
     }
+    if constexpr (C::CRED)
+      for (int b = 0; b < C::NPB; ++b) {
+        mbar_init(&pfull[b], NW);
+        mbar_init(&pempty[b], 1);
+      }
     fence_mbar_init();
   }
   __syncthreads();
@@ -219,6 +233,41 @@ qy_packed_kernel(const TQ* __restrict__ tiles, int nt, int64_t ntiles, int nstag
       }
     }
     return;
+  }
+
+  if constexpr (C::CRED) {
+    if (warp == NW + 1) {
+      // ---------------- reducer: per tile, the NW warps' column partials (buffer layout
+      // [warp][column 4l + cc as (cc, l)][R]) summed in warp order, one vector reduction per
+      // 4 outputs into W_J
+      constexpr int F4 = TILE * R / 4;          // float4 groups of one warp's partials
+      int I = I0, J = J0;
+      for (int64_t t = t0; t < t1; ++t) {
+        const int64_t k = t - t0;
+        const int b = (int)(k % C::NPB);
+        const uint32_t par = (uint32_t)((k / C::NPB) & 1);
+        if (!mbar_wait(&pfull[b], par)) { atomicOr(err, DEV_TIMEOUT); break; }
+        const float4* pb = reinterpret_cast<const float4*>(part + (size_t)b * (C::PART_BYTES / sizeof(A)));
+#pragma unroll
+        for (int qd = 0; qd < F4 / 32; ++qd) {
+          const int m = qd * 32 + lane;          // float4 index within one warp's partials
+          float4 acc = pb[m];
+#pragma unroll
+          for (int w = 1; w < NW; ++w) {
+            const float4 u = pb[(size_t)w * F4 + m];
+            acc.x += u.x; acc.y += u.y; acc.z += u.z; acc.w += u.w;
+          }
+          // float index 4m = (cc * 32 + l) * R + j0
+          const int g = (4 * m) / R, j0 = (4 * m) % R;
+          const int cc = g >> 5, l = g & 31;
+          red_add4(W + ((size_t)J * TILE + 4 * l + cc) * R + j0, acc.x, acc.y, acc.z, acc.w);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&pempty[b]);
+        pair_order_next(nt, I, J);
+      }
+      return;
+    }
   }
 
   // ---------------- consumers
@@ -452,8 +501,29 @@ qy_packed_kernel(const TQ* __restrict__ tiles, int nt, int64_t ntiles, int nstag
       }
     }
     // column contribution: each warp adds its partials for columns 4l..4l+3 of Y_J directly
-    // (vector reductions in L2; no barrier between warps)
-    {
+    // (vector reductions in L2; no barrier between warps), or (CRED) hands them to the reducer
+    if constexpr (C::CRED) {
+      const int64_t k = t - t0;
+      const int b = (int)(k % C::NPB);
+      const uint32_t par = (uint32_t)(((k / C::NPB) & 1) ^ 1);
+      if (ok && !mbar_wait(&pempty[b], par)) { atomicOr(err, DEV_TIMEOUT); ok = false; }
+      if (ok) {
+        A* pw = part + (size_t)b * (C::PART_BYTES / sizeof(A)) + (size_t)warp * TILE * R;
+#pragma unroll
+        for (int cp = 0; cp < 2; ++cp) {
+          float lo[R], hi[R];
+#pragma unroll
+          for (int j = 0; j < R; ++j) upk(colp[cp][j], lo[j], hi[j]);
+#pragma unroll
+          for (int j = 0; j < R; j += 4) {
+            *reinterpret_cast<float4*>(pw + ((2 * cp) * 32 + lane) * R + j) = make_float4(lo[j], lo[j + 1], lo[j + 2], lo[j + 3]);
+            *reinterpret_cast<float4*>(pw + ((2 * cp + 1) * 32 + lane) * R + j) = make_float4(hi[j], hi[j + 1], hi[j + 2], hi[j + 3]);
+          }
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&pfull[b]);
+    } else {
       A* wj = W + ((size_t)J * TILE + 4 * lane) * R;
       if constexpr (C::PAIR) {
 #pragma unroll
