@@ -56,11 +56,12 @@ DTYPES = {"fp64": "f64", "fp32": "f32", "bf16": "bf16/f32"}
 REFERENCE_SWEEPS = {"c3": 2230, "c2": 575, "c4": 11500, "c1": 500}
 L2_BYTES = 126e6
 # DRAM bytes (read + write) over algorithmic bytes of qy_packed_kernel<float,4,8> from one ncu
-# capture at the 10155-camera size itself (n = 30465: 1.8832 GB read + 0.0040 GB written per
-# launch against 1.8573 GB algorithmic), on the kernel as it stands (swizzled Y_J, paired
-# tile-row order).  Applied only at that size (other sizes get traffic = null); must be
-# re-measured (or set to None) whenever the sweep kernel changes.
-SWEEP_TRAFFIC_RATIO = (1.883209 + 0.003997) / 1.857268
+# capture at the 10155-camera size itself (n = 30465: 1.88 GB read + 0.00412 GB written per
+# launch against 1.8573 GB algorithmic, as ncu prints them), on the kernel as it stands (swizzled
+# Y_J, paired tile-row order, column partials through the reducer warp).  Applied only at that
+# size (other sizes get traffic = null); must be re-measured (or set to None) whenever the
+# sweep kernel changes.
+SWEEP_TRAFFIC_RATIO = (1.88 + 0.00412) / 1.857268
 SWEEP_TRAFFIC_N = 30465
 
 
