@@ -26,10 +26,12 @@ def check_at_returned_point(Qo, out, lam_tol_rel=1e-5, mu=0.0):
     f = O.cost(Qo, Y, mu)
     c = O.certify(Qo, Y, mu=mu)
     lam_tol = lam_tol_rel * c.lam_max_Q
-    assert _rel(info["f"], f) <= 1e-9
-    assert abs(info["dual"] - c.dual) <= 1e-9 * (1 + abs(f))
-    assert abs(info["lambda_min_deflated"] - c.lam_min_deflated) <= lam_tol
-    assert abs(info["lambda_min"] - c.lam_min) <= lam_tol
+    assert _rel(info["f"], f) <= 1e-9, (info["f"], f)
+    assert abs(info["dual"] - c.dual) <= 1e-9 * (1 + abs(f)), (info["dual"], c.dual)
+    assert abs(info["lambda_min_deflated"] - c.lam_min_deflated) <= lam_tol, \
+        (info["lambda_min_deflated"], c.lam_min_deflated, lam_tol)
+    assert abs(info["lambda_min"] - c.lam_min) <= lam_tol, \
+        (info["lambda_min"], c.lam_min, c.lam_min_deflated, lam_tol, info["grad_norm"], c.ZY_norm)
     _check_rounding(Qo, Y, out, mu)
     rho = info["rho_hat"]
     assert abs(info["eta"] - O.suboptimality(rho, f)) <= 1e-9
