@@ -505,8 +505,20 @@ def certify(Q, Y, dense_limit=4000, tol=1e-12, mu=0.0):
             return y
         Zd = spla.LinearOperator((n, n), matvec=lambda x: zdmul(x) + big * (Vd @ (Vd.T @ x)),
                                  dtype=np.float64)
-        lam_def = float(spla.eigsh(Zd, k=1, which="SA", tol=tol, maxiter=20 * n,
-                                   return_eigenvectors=False)[0])
+        ed, vd = spla.eigsh(Zd, k=1, which="SA", tol=tol, maxiter=20 * n)
+        lam_def = float(ed[0])
+        # lambda_min(Z) is the least Rayleigh quotient of Z; the Ritz values on range(Y) (the
+        # r x r block Vd^T Z Vd) and on its complement (lam_def) are Rayleigh quotients too, so
+        # the least of the three is still an upper bound of lambda_min(Z), and does not depend
+        # on one Lanczos run finding the near-null cluster that range(Y) gives Z
+        ZVd = zmul(Vd)
+        zr = 0.5 * (Vd.T @ ZVd + (Vd.T @ ZVd).T)
+        if zr.size:
+            ew, ev = np.linalg.eigh(zr)
+            if ew[0] < lam_min:
+                lam_min, v = float(ew[0]), Vd @ ev[:, 0]
+        if lam_def < lam_min:
+            lam_min, v = lam_def, vd[:, 0]
     return Certificate(L, f, dual, lam_min, lam_def, v, lmQ, float(np.linalg.norm(ZY)))
 
 
