@@ -393,7 +393,7 @@ k_hvp_epi(int N, const T* __restrict__ Y, T* __restrict__ Wd, const T* __restric
   if (sc->done) return;
   double v[1] = {0.0};
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < N) v[0] = hvp_block<T, R>(i, N, Y, Wd, delta, Hd, Lam, sc->mu);
+  if (i < N) v[0] = hvp_block<T, R, T>(i, N, Y, Wd, delta, Hd, Lam, sc->mu);
   grid_reduce<1>(v, partials, counter, [&](double* t) {
     const double kap = t[0];
     sc->kappa = kap;
@@ -418,7 +418,10 @@ k_tcg_update(int N, const T* __restrict__ Y, T* eta, T* Heta, T* r, T* z, const 
              const T* __restrict__ Hd, const double* __restrict__ Minv, Scal* sc, double* partials,
              unsigned* counter) {
   if (sc->done) return;
-  using C = double;   // per-camera arithmetic in FP64 whatever the storage type
+  // per-camera arithmetic in the vectors' precision (B300's FP64 rate is 1/64 of its FP32 rate:
+  // FP64 here had made the tCG epilogues slower than the sweep on the 2000-camera trajectory);
+  // the reductions accumulate in FP64
+  using C = T;
   const C alpha = C(sc->alpha);
   const bool stop = sc->stop_after != 0;
   double v[2] = {0.0, 0.0};
@@ -492,7 +495,8 @@ k_tcg_dir(int N, const T* __restrict__ z, T* delta, const Scal* sc) {
   const double beta = sc->beta;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
-  for (int e = 3 * i * R; e < 3 * (i + 1) * R; ++e) delta[e] = T(-double(z[e]) + beta * double(delta[e]));
+  const T b = T(beta);
+  for (int e = 3 * i * R; e < 3 * (i + 1) * R; ++e) delta[e] = -z[e] + b * delta[e];
 }
 
 // model terms <grad, eta>, <eta, Heta>, ||eta||^2 after tCG
