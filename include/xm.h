@@ -190,7 +190,7 @@ xm_status xm_build_Q(xm_ctx* ctx, int N, int M, int64_t E, const int32_t* cam,
  *                      a power of two, exact FP32 accumulation of the digit products, int32 and
  *                      FP64 recombination; normwise as accurate as FP64 products (error below
  *                      2^-56 sqrt(K) |u| |v| per dot product).  The factorisation and the
- *                      triangular solve are blocked (512- and 1024-row diagonal blocks, panels by
+ *                      triangular solve are blocked (256- and 1024-row diagonal blocks, panels by
  *                      the library's FP64 kernels, the trailing and block updates on the tensor
  *                      cores).  Needs N - 1 <= 16640.
  * XM_BUILD_AUTO:       XM_BUILD_SPLIT_BF16 when 512 <= N <= 16641, else XM_BUILD_FP64 (default).

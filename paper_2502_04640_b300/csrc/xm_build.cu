@@ -581,8 +581,8 @@ xm_status schur_S_factor(xm_ctx* ctx, int N, int M, const int32_t* cam, const do
     k_landmark_S<<<grid_for(M, 128, ctx->num_sms), 128, 0, st>>>(M, N, loff, lidx, cam, w, d, S);
   XM_CUDA_TRY(cudaGetLastError());
   if (N > 1) {
-    // Cholesky factor of Sbar: tensor-core trailing updates from 512 rows (the build's own
-    // factorisation), the FP64 blocked factor below
+    // Cholesky factor of Sbar: tensor-core trailing updates from XM_BUILD_SPLIT_MIN_N rows (the
+    // build's own factorisation), the FP64 blocked factor below
     const int m = N - 1;
     double* Sbar = S + N + 1;
     int hinfo = 0;

@@ -71,7 +71,7 @@ constexpr uint32_t OZ_TMEM_COLS = OZ_ACC * OZ_BN;
 constexpr size_t OZ_SMEM = 1024 + (size_t)OZ_STAGES * OZ_STAGE_BYTES + 256;
 constexpr int64_t OZ_MAX_K = 16640;        // int32 level sums: 8 K 127^2 < 2^31
 constexpr int OZ_TRSM_BLOCK = 1024;        // diagonal block of the blocked triangular solve
-constexpr int OZ_CHOL_BLOCK = 512;         // diagonal block of the blocked Cholesky factorisation
+constexpr int OZ_CHOL_BLOCK = 256;         // diagonal block of the blocked Cholesky factorisation
 
 enum { OZ_SYRK = 0, OZ_GEMM = 1 };
 
@@ -782,11 +782,13 @@ xm_status split_trsm(xm_ctx* ctx, const double* L, int ldl, double* X, int ldx, 
 namespace xm {
 
 // In-place Cholesky factor of the m x m SPD matrix A (column-major, leading dimension lda, lower
-// triangle used and overwritten by L): right-looking, blocks of 512; the diagonal blocks by
-// cuSOLVER DPOTRF and the panels by cuBLAS DTRSM (FP64), the trailing updates
-// A_rest -= L_k L_k^T on the tensor cores (only the tiles that meet the lower triangle).  (Panels
-// as products with explicit inverses of the diagonal blocks doubled the build's difference from
-// the FP64 build at 1500 cameras, to 2.1e-11 of max |Q|.)
+// triangle used and overwritten by L): right-looking, blocks of OZ_CHOL_BLOCK (256); the
+// diagonal blocks by dense_potrf and the panels by substitution (dense_trsm_right_lower_t), both
+// this library's FP64 kernels, the trailing updates A_rest -= L_k L_k^T on the tensor cores (only
+// the tiles that meet the lower triangle).  (Panels as products with explicit inverses of the
+// diagonal blocks doubled the build's difference from the FP64 build at 1500 cameras, to 2.1e-11
+// of max |Q|.  256-row blocks halve the panels' substitution work and chains against 512 for a
+// few more level folds of the updates: 10155-camera build 0.667 -> 0.648 s.)
 // *minor = 0 on success, else the 1-based order of the first non-positive leading minor.
 xm_status split_potrf(xm_ctx* ctx, double* A, int lda, int m, int* minor) {
   cudaStream_t st = ctx->stream;
