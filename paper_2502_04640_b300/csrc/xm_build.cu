@@ -133,16 +133,78 @@ __global__ void k_csr_fill(int64_t E, const int32_t* lmk, const int64_t* off, in
     idx[off[k] + pos] = e;
   }
 }
-// Deterministic order within each landmark: sort its observation indices (short segments).
-__global__ void k_csr_sort(int M, const int64_t* off, int64_t* idx) {
+// Deterministic order within each group (landmark or camera): its observation indices ascending.
+// Groups of at most CSR_SMALL entries (the landmarks' tracks) are sorted by one thread each;
+// larger ones (a camera's observations) are queued for k_csr_sort_big.
+constexpr int CSR_SMALL = 16;
+constexpr int CSR_BIG_THREADS = 512;
+constexpr int CSR_OWN = 16;                          // entries per thread in k_csr_sort_big
+constexpr int CSR_BIG_MAX = CSR_BIG_THREADS * CSR_OWN;
+constexpr int CSR_CHUNK = 4096;                      // entries staged in shared memory at a time
+__global__ void k_csr_sort(int M, const int64_t* off, int64_t* idx, int* big, int* nbig) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < M; k += gridDim.x * blockDim.x) {
     const int64_t a = off[k], b = off[k + 1];
+    if (b - a > CSR_SMALL) {
+      big[atomicAdd(nbig, 1)] = k;
+      continue;
+    }
     for (int64_t x = a + 1; x < b; ++x) {
       const int64_t v = idx[x];
       int64_t y = x - 1;
       while (y >= a && idx[y] > v) { idx[y + 1] = idx[y]; --y; }
       idx[y + 1] = v;
     }
+  }
+}
+// One block per queued group: the entries are distinct, so entry v goes to position
+// #{entries < v} (counted against chunks of the group staged in shared memory), written to tmp
+// and copied back.  Groups beyond CSR_BIG_MAX entries fall back to one thread's insertion sort
+// (correct, slow).
+__global__ void __launch_bounds__(CSR_BIG_THREADS) k_csr_sort_big(const int64_t* off, int64_t* idx,
+                                                                 int64_t* tmp, const int* big,
+                                                                 const int* nbig) {
+  __shared__ int64_t sv[CSR_CHUNK];
+  const int t = threadIdx.x;
+  const int ng = *nbig;
+  for (int g = blockIdx.x; g < ng; g += gridDim.x) {
+    const int key = big[g];
+    const int64_t a = off[key], b = off[key + 1], k = b - a;
+    if (k > CSR_BIG_MAX) {
+      if (t == 0)
+        for (int64_t x = a + 1; x < b; ++x) {
+          const int64_t v = idx[x];
+          int64_t y = x - 1;
+          while (y >= a && idx[y] > v) { idx[y + 1] = idx[y]; --y; }
+          idx[y + 1] = v;
+        }
+      __syncthreads();
+      continue;
+    }
+    int64_t val[CSR_OWN];
+    int cnt[CSR_OWN];
+#pragma unroll
+    for (int m = 0; m < CSR_OWN; ++m) {
+      const int64_t j = a + t + (int64_t)CSR_BIG_THREADS * m;
+      val[m] = j < b ? idx[j] : INT64_MAX;
+      cnt[m] = 0;
+    }
+    for (int64_t c0 = a; c0 < b; c0 += CSR_CHUNK) {
+      const int ch = (int)min((int64_t)CSR_CHUNK, b - c0);
+      __syncthreads();
+      for (int q = t; q < ch; q += CSR_BIG_THREADS) sv[q] = idx[c0 + q];
+      __syncthreads();
+      for (int q = 0; q < ch; ++q) {
+        const int64_t x = sv[q];
+#pragma unroll
+        for (int m = 0; m < CSR_OWN; ++m) cnt[m] += x < val[m] ? 1 : 0;
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < CSR_OWN; ++m)
+      if (a + t + (int64_t)CSR_BIG_THREADS * m < b) tmp[a + cnt[m]] = val[m];
+    __syncthreads();
+    for (int64_t q = t; q < k; q += CSR_BIG_THREADS) idx[a + q] = tmp[a + q];
+    __syncthreads();
   }
 }
 
@@ -317,6 +379,25 @@ xm_status check_connected(xm_ctx* ctx, int N, int M, int64_t E, const int32_t* c
   return XM_OK;
 }
 
+// Ascending observation indices within each of the K groups of idx (CSR offsets off): short
+// groups by one thread each, the rest one block each (k_csr_sort_big).  Synchronous: its scratch
+// (the queue of large groups and an E-entry copy buffer) is freed on return.
+static xm_status csr_sort(xm_ctx* ctx, int K, int64_t E, const int64_t* off, int64_t* idx) {
+  if (K <= 0 || E <= 0) return XM_OK;
+  cudaStream_t st = ctx->stream;
+  DevBuf big, nbig, tmp;
+  XM_CUDA_TRY(cudaMalloc(&big.p, sizeof(int) * (size_t)K));
+  XM_CUDA_TRY(cudaMalloc(&nbig.p, sizeof(int)));
+  XM_CUDA_TRY(cudaMalloc(&tmp.p, sizeof(int64_t) * (size_t)E));
+  XM_CUDA_TRY(cudaMemsetAsync(nbig.p, 0, sizeof(int), st));
+  k_csr_sort<<<grid_for(K, 256, ctx->num_sms), 256, 0, st>>>(K, off, idx, big.as<int>(), nbig.as<int>());
+  k_csr_sort_big<<<ctx->num_sms * 4, CSR_BIG_THREADS, 0, st>>>(off, idx, tmp.as<int64_t>(), big.as<int>(),
+                                                              nbig.as<int>());
+  XM_CUDA_TRY(cudaGetLastError());
+  XM_CUDA_TRY(cudaStreamSynchronize(st));
+  return XM_OK;
+}
+
 xm_status build_Q(xm_ctx* ctx, int N, int M, int64_t E, const int32_t* cam, const int32_t* lmk,
                   const double* ukp, const double* w, unsigned mask, DeviceQ& out,
                   double* t_build) {
@@ -383,8 +464,7 @@ xm_status build_Q(xm_ctx* ctx, int N, int M, int64_t E, const int32_t* cam, cons
     k_scan_add<<<nb, 1024, 0, st>>>(off.as<int64_t>(), bsum.as<int64_t>(), M);
     k_csr_fill<<<grid_for(E, threads, ctx->num_sms), threads, 0, st>>>(
         E, lmk, off.as<int64_t>(), cursor.as<int>(), idx.as<int64_t>());
-    k_csr_sort<<<grid_for(M, threads, ctx->num_sms), threads, 0, st>>>(M, off.as<int64_t>(),
-                                                                      idx.as<int64_t>());
+    XM_TRY(csr_sort(ctx, M, E, off.as<int64_t>(), idx.as<int64_t>()));
     k_landmark_schur<<<grid_for(M, 128, ctx->num_sms), 128, 0, st>>>(
         M, n, N, off.as<int64_t>(), idx.as<int64_t>(), cam, ukp, w, d.as<double>(),
         P.as<double>(), B.as<double>(), S.as<double>());
@@ -517,7 +597,7 @@ xm_status obs_csr(xm_ctx* ctx, int64_t E, const int32_t* key, int K, int64_t* of
   k_scan_sums<<<1, 32, 0, st>>>(bsum.as<int64_t>(), nb);
   k_scan_add<<<nb, 1024, 0, st>>>(off, bsum.as<int64_t>(), K);
   k_csr_fill<<<grid_for(E, threads, ctx->num_sms), threads, 0, st>>>(E, key, off, cursor.as<int>(), idx);
-  k_csr_sort<<<grid_for(K, threads, ctx->num_sms), threads, 0, st>>>(K, off, idx);
+  XM_TRY(csr_sort(ctx, K, E, off, idx));
   XM_CUDA_TRY(cudaGetLastError());
   XM_CUDA_TRY(cudaStreamSynchronize(st));   // the scratch above is freed on return
   return XM_OK;
