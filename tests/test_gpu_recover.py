@@ -38,6 +38,29 @@ def test_recover_tp_matches_oracle(C):
     assert np.abs(r2.cpu().numpy() - r2_ref).max() <= 1e-9 * (1 + np.abs(r2_ref).max())
 
 
+@pytest.mark.parametrize("N,M", [(3, 6000), (2, 9000)])
+def test_recover_tp_with_cameras_of_many_observations(C, N, M):
+    """Cameras with thousands of observations: the per-camera groups of the observation index
+    (ascending within each group, so that every per-camera sum is taken in a fixed order) are
+    ordered by the block-parallel sort, over several shared-memory chunks at 6000 observations
+    per camera and by its one-thread fallback at 9000; the recovery must still equal the
+    oracle's, and repeat bit for bit."""
+    from paper_2502_04640_b300 import xm
+    sc = scenes.circle_scene(N, M, N, 0.02, seed=7 + N)
+    Q = O.build_Q_schur(sc.N, sc.M, sc.cam, sc.lmk, sc.ukp, sc.w)
+    ref = O.solve(Q, r0=4)
+    U3 = np.concatenate([ref.s[i] * ref.R[i] for i in range(sc.N)], axis=1)
+    t_ref, p_ref = O.recover_tp(sc.N, sc.M, sc.cam, sc.lmk, sc.ukp, sc.w, U3)
+    cam, lmk, ukp, w = xm.scene_tensors(sc)
+    Rt, st = torch.tensor(ref.R, device="cuda"), torch.tensor(ref.s, device="cuda")
+    t, p, r2 = xm.xm_recover_tp(C, sc.N, sc.M, cam, lmk, ukp, w, Rt, st)
+    scale = max(np.abs(t_ref).max(), np.abs(p_ref).max())
+    assert np.abs(t.cpu().numpy() - t_ref).max() <= 1e-9 * scale
+    assert np.abs(p.cpu().numpy() - p_ref).max() <= 1e-9 * scale
+    t2, p2, r22 = xm.xm_recover_tp(C, sc.N, sc.M, cam, lmk, ukp, w, Rt, st)
+    assert torch.equal(t, t2) and torch.equal(p, p2) and torch.equal(r2, r22)
+
+
 def test_noise_free_recovery_of_translations_and_landmarks(C):
     from paper_2502_04640_b300 import xm
     sc = scenes.circle_scene(12, 120, 4, 0.0, seed=18)
