@@ -134,6 +134,11 @@ __device__ __forceinline__ void cl_st(uint32_t a, float v) {
 __device__ __forceinline__ void cl_st(uint32_t a, double v) {
   asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory");
 }
+__device__ __forceinline__ void cl_st(uint32_t a, float4 v) {
+  asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v.x), "f"(v.y), "f"(v.z),
+               "f"(v.w)
+               : "memory");
+}
 __device__ __forceinline__ void cl_st(uint32_t a, int v) {
   asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
 }
@@ -469,39 +474,47 @@ __device__ void dev_tri_eigvec(int k, const double* a, const double* b, double t
 
 // Number of eigenvalues of the symmetric tridiagonal (a[0..k), b[0..k-1)) below x: sign
 // changes of the Sturm sequence p_0 = 1, p_i = (a_i - x) p_{i-1} - b_{i-1}^2 p_{i-2}, without
-// divisions (B300's FP64 division is slow); the pair (p_{i-1}, p_i) is rescaled by an exact
-// power of two when it leaves [2^-500, 2^500].  A zero p_i takes the sign opposite to p_{i-1}.
+// divisions (B300's FP64 division is slow).  Three FP64 operations a step (a_i - x, b^2 p_{i-2}
+// and one FMA); the sign and the range tests read the exponent and sign bits with integer
+// operations, off the narrow FP64 pipe.  The pair (p_{i-1}, p_i) is rescaled by an exact power
+// of two (which changes no sign) when |p_i| >= 2^501, or when both are below 2^-500.  A zero
+// p_i takes the sign opposite to p_{i-1}.
 __device__ __forceinline__ int sturm_nodiv(int k, const double* __restrict__ a, const double* __restrict__ b2,
                                            double x) {
   double pm = 1.0, p = a[0] - x;
   int c = 0;
   bool neg_prev = false;                       // sign of p_0 = +1
-  bool neg = p < 0.0 || (p == 0.0 && !neg_prev);
-  if (neg != neg_prev) ++c;
-  neg_prev = neg;
-  for (int i = 1; i < k; ++i) {
-    const double pn = (a[i] - x) * p - b2[i - 1] * pm;
-    pm = p;
-    p = pn;
-    const double ap = fabs(p);
-    if (ap > 0x1p500 || (ap < 0x1p-500 && fabs(pm) < 0x1p-500)) {
-      const double sc = ap > 0x1p500 ? 0x1p-500 : 0x1p500;
+  int ex_prev = 1023;                          // biased exponent of p_0
+  for (int i = 0;;) {
+    const int hi = __double2hiint(p);
+    const bool zero = ((hi & 0x7fffffff) | __double2loint(p)) == 0;
+    const bool neg = zero ? !neg_prev : hi < 0;
+    c += neg != neg_prev;
+    neg_prev = neg;
+    if (++i >= k) break;
+    const int ex = (hi >> 20) & 0x7ff;
+    if (ex > 1023 + 500 || (ex < 1023 - 500 && ex_prev < 1023 - 500)) {
+      const double sc = ex > 1023 + 500 ? 0x1p-500 : 0x1p500;
       p *= sc;
       pm *= sc;
     }
-    neg = p < 0.0 || (p == 0.0 && !neg_prev);
-    if (neg != neg_prev) ++c;
-    neg_prev = neg;
+    ex_prev = (__double2hiint(p) >> 20) & 0x7ff;
+    const double pn = fma(a[i] - x, p, -(b2[i - 1] * pm));
+    pm = p;
+    p = pn;
   }
   return c;
 }
 
-// Smallest and largest eigenvalues of the tridiagonal by multisection: each round the 256
-// threads evaluate Sturm counts at 127 interior points of each bracket (threads 0..127 for
-// the smallest, 128..255 for the largest), shrinking both brackets by 128x; 8 rounds reach
-// FP64 resolution.  a, b2 (= b^2) and the scratch `cnt` (256 ints) in shared memory.
-__device__ void tri_extremes(int k, const double* a, const double* b, double* b2, int* cnt, double* brk,
+// Smallest and largest eigenvalues of the tridiagonal by multisection: each round warps 0-1
+// evaluate Sturm counts at 64 interior points of the bracket of the smallest (65 equal parts),
+// warps 2-3 of the largest, one warp per SM partition; 10 rounds shrink each bracket by
+// 65^10 > 2^60, to FP64 resolution.  (More points a round cost FP64 issue slots, of which B300
+// has few: fewer, longer rounds are cheaper.)  a, b2 (= b^2) and the scratch `cnt` (NT ints)
+// in shared memory.
+__device__ __noinline__ void tri_extremes(int k, const double* a, const double* b, double* b2, int* cnt, double* brk,
                              double& tmin, double& tmax) {
+  constexpr int PTS = 64;
   for (int i = threadIdx.x; i < k - 1; i += NT) b2[i] = b[i] * b[i];
   if (threadIdx.x == 0) {
     double lo = a[0], hi = a[0];
@@ -515,23 +528,27 @@ __device__ void tri_extremes(int k, const double* a, const double* b, double* b2
     brk[2] = lo - pad; brk[3] = hi + pad;   // bracket of the largest
   }
   __syncthreads();
-  const int half = NT / 2;
-  const int t = threadIdx.x % half;
-  const bool upper = threadIdx.x >= half;
-  for (int round = 0; round < 8; ++round) {
-    const double lo = brk[upper ? 2 : 0], hi = brk[upper ? 3 : 1];
-    const double x = lo + (hi - lo) * (double)(t + 1) / (double)half;   // t = half-1 -> hi
-    cnt[threadIdx.x] = sturm_nodiv(k, a, b2, x);
+  const bool active = threadIdx.x < 2 * PTS;
+  const bool upper = threadIdx.x >= PTS;
+  const int t = threadIdx.x % PTS;
+  for (int round = 0; round < 10; ++round) {
+    if (active) {
+      const double lo = brk[upper ? 2 : 0], hi = brk[upper ? 3 : 1];
+      const double x = lo + (hi - lo) * (double)(t + 1) / (double)(PTS + 1);
+      cnt[threadIdx.x] = sturm_nodiv(k, a, b2, x);
+    }
     __syncthreads();
-    if (threadIdx.x == 0 || threadIdx.x == half) {
-      // first point whose count reaches the target: the eigenvalue lies in (x_{t-1}, x_t]
+    if (threadIdx.x == 0 || threadIdx.x == PTS) {
+      // first point whose count reaches the target: the eigenvalue lies in (x_{u-1}, x_u]; none
+      // does: in (x_{PTS-1}, hi]
+      const double lo = brk[upper ? 2 : 0], hi = brk[upper ? 3 : 1];
       const int target = upper ? k : 1;
-      const int base = upper ? half : 0;
-      int first = half - 1;
-      for (int u = 0; u < half; ++u)
+      const int base = upper ? PTS : 0;
+      int first = PTS;
+      for (int u = 0; u < PTS; ++u)
         if (cnt[base + u] >= target) { first = u; break; }
-      const double nlo = first == 0 ? lo : lo + (hi - lo) * (double)first / (double)half;
-      const double nhi = lo + (hi - lo) * (double)(first + 1) / (double)half;
+      const double nlo = first == 0 ? lo : lo + (hi - lo) * (double)first / (double)(PTS + 1);
+      const double nhi = first == PTS ? hi : lo + (hi - lo) * (double)(first + 1) / (double)(PTS + 1);
       brk[upper ? 2 : 0] = nlo;
       brk[upper ? 3 : 1] = nhi;
     }
@@ -692,6 +709,11 @@ struct Cta {
   // Riemannian trust region (Absil et al. 2008, Alg. 10) with Steihaug-Toint tCG (Alg. 11);
   // constants as in xm_solve.  To: iterate / gradient type, Ti: tCG type.  Y, G, Lam and their
   // candidates are the member pointers of that precision (swapped on acceptance).
+  // The per-element loops below give thread t the elements t, t + NT, t + 2 NT, ... (the order
+  // of its partial sums) and take EB of them at a time with every load issued before any store:
+  // the vectors may alias as far as the compiler knows, so a load after a store would wait one
+  // memory round trip per element.  The per-camera loops load a camera's blocks before storing.
+  static constexpr int EB = 4;
   template <typename To, typename Ti>
   __device__ void rtr(double tol_rel, int max_outer, bool bulk) {
     To*& Y = *reinterpret_cast<To**>(sizeof(To) == 4 ? (void*)&yf : (void*)&y64);
@@ -720,15 +742,28 @@ struct Cta {
     for (int k = 0; k < max_outer; ++k) {
       if (!(sqrt(g2) > tol_abs) || over_time()) break;
       if (sizeof(To) != sizeof(Ti)) {
-        for (int e = threadIdx.x; e < nR; e += NT) ((Ti*)yf)[e] = Ti(Y[e]);
+        for (int e0 = threadIdx.x; e0 < nR; e0 += EB * NT) {
+          To v[EB];
+#pragma unroll
+          for (int u = 0; u < EB; ++u) v[u] = e0 + u * NT < nR ? Y[e0 + u * NT] : To(0);
+#pragma unroll
+          for (int u = 0; u < EB; ++u)
+            if (e0 + u * NT < nR) ((Ti*)yf)[e0 + u * NT] = Ti(v[u]);
+        }
         Yin = (const Ti*)yf;
       } else {
         Yin = (const Ti*)Y;
       }
       // ---- tCG
-      for (int e = threadIdx.x; e < nR; e += NT) {
-        const Ti g = Ti(G[e]);
-        eta[e] = Ti(0); Heta[e] = Ti(0); rv[e] = g; dv[e] = -g;
+      for (int e0 = threadIdx.x; e0 < nR; e0 += EB * NT) {
+        Ti g[EB];
+#pragma unroll
+        for (int u = 0; u < EB; ++u) g[u] = e0 + u * NT < nR ? Ti(G[e0 + u * NT]) : Ti(0);
+#pragma unroll
+        for (int u = 0; u < EB; ++u) {
+          const int e = e0 + u * NT;
+          if (e < nR) { eta[e] = Ti(0); Heta[e] = Ti(0); rv[e] = g[u]; dv[e] = -g[u]; }
+        }
       }
       __syncthreads();
       double rr = g2, ee = 0.0, ed = 0.0, dd = g2;
@@ -747,9 +782,23 @@ struct Cta {
         if (!(kap > 0.0) || ee + 2.0 * a * ed + a * a * dd >= D2) {
           const double disc = ed * ed + dd * (D2 - ee);
           const double tau = (-ed + sqrt(disc > 0.0 ? disc : 0.0)) / dd;
-          for (int e = threadIdx.x; e < nR; e += NT) {
-            eta[e] = Ti(double(eta[e]) + tau * double(dv[e]));
-            Heta[e] = Ti(double(Heta[e]) + tau * double(Hd[e]));
+          for (int e0 = threadIdx.x; e0 < nR; e0 += EB * NT) {
+            Ti x[EB], h[EB], d[EB], hd[EB];
+#pragma unroll
+            for (int u = 0; u < EB; ++u) {
+              const int e = e0 + u * NT;
+              const bool ok = e < nR;
+              x[u] = ok ? eta[e] : Ti(0); h[u] = ok ? Heta[e] : Ti(0);
+              d[u] = ok ? dv[e] : Ti(0); hd[u] = ok ? Hd[e] : Ti(0);
+            }
+#pragma unroll
+            for (int u = 0; u < EB; ++u) {
+              const int e = e0 + u * NT;
+              if (e < nR) {
+                eta[e] = Ti(double(x[u]) + tau * double(d[u]));
+                Heta[e] = Ti(double(h[u]) + tau * double(hd[u]));
+              }
+            }
           }
           __syncthreads();
           break;
@@ -760,17 +809,37 @@ struct Cta {
         const Ti at = Ti(a);
         for (int i = threadIdx.x; i < N; i += NT) {
           Ti y[3][R], r3[3][R];
-          load_block<Ti, Ti, R>(Yin, i, y);
+          if constexpr (R <= 4) {
+            Ti hd[3][R], et[3][R], he[3][R], db[3][R];
+            load_block<Ti, Ti, R>(Hd, i, hd);
+            load_block<Ti, Ti, R>(eta, i, et);
+            load_block<Ti, Ti, R>(Heta, i, he);
+            load_block<Ti, Ti, R>(dv, i, db);
+            load_block<Ti, Ti, R>(rv, i, r3);
+            load_block<Ti, Ti, R>(Yin, i, y);
 #pragma unroll
-          for (int aa = 0; aa < 3; ++aa)
+            for (int aa = 0; aa < 3; ++aa)
 #pragma unroll
-            for (int jj = 0; jj < R; ++jj) {
-              const size_t e = (size_t)(3 * i + aa) * R + jj;
-              const Ti hd = Hd[e];
-              eta[e] = eta[e] + at * dv[e];
-              Heta[e] = Heta[e] + at * hd;
-              r3[aa][jj] = rv[e] + at * hd;
-            }
+              for (int jj = 0; jj < R; ++jj) {
+                et[aa][jj] = et[aa][jj] + at * db[aa][jj];
+                he[aa][jj] = he[aa][jj] + at * hd[aa][jj];
+                r3[aa][jj] = r3[aa][jj] + at * hd[aa][jj];
+              }
+            store_block<Ti, Ti, R>(eta, i, et);
+            store_block<Ti, Ti, R>(Heta, i, he);
+          } else {   // rank 8: element by element (the blocks would not fit in registers)
+            load_block<Ti, Ti, R>(Yin, i, y);
+#pragma unroll
+            for (int aa = 0; aa < 3; ++aa)
+#pragma unroll
+              for (int jj = 0; jj < R; ++jj) {
+                const size_t e = (size_t)(3 * i + aa) * R + jj;
+                const Ti hd = Hd[e];
+                eta[e] = eta[e] + at * dv[e];
+                Heta[e] = Heta[e] + at * hd;
+                r3[aa][jj] = rv[e] + at * hd;
+              }
+          }
           Ti S[3][3], al;
           dual_block<Ti, R>(r3, y, i == 0, S, al);
 #pragma unroll
@@ -790,11 +859,24 @@ struct Cta {
         rr = rr_new;
         Ti p3[3] = {Ti(0), Ti(0), Ti(0)};
         const Ti bt = Ti(beta);
-        for (int e = threadIdx.x; e < nR; e += NT) {
-          const Ti de = -rv[e] + bt * dv[e];
-          dv[e] = de;
-          const Ti et = eta[e];
-          p3[0] += et * et; p3[1] += et * de; p3[2] += de * de;
+        for (int e0 = threadIdx.x; e0 < nR; e0 += EB * NT) {
+          Ti rq[EB], dq[EB], tq[EB];
+#pragma unroll
+          for (int u = 0; u < EB; ++u) {
+            const int e = e0 + u * NT;
+            const bool ok = e < nR;
+            rq[u] = ok ? rv[e] : Ti(0); dq[u] = ok ? dv[e] : Ti(0); tq[u] = ok ? eta[e] : Ti(0);
+          }
+#pragma unroll
+          for (int u = 0; u < EB; ++u) {
+            const int e = e0 + u * NT;
+            if (e < nR) {
+              const Ti de = -rq[u] + bt * dq[u];
+              dv[e] = de;
+              const Ti et = tq[u];
+              p3[0] += et * et; p3[1] += et * de; p3[2] += de * de;
+            }
+          }
         }
         double w3[3] = {double(p3[0]), double(p3[1]), double(p3[2])};
         bsum<3>(w3, sm.red);
@@ -803,9 +885,21 @@ struct Cta {
       info.n_tcg += iters;
       // ---- model decrease, candidate, ratio test
       double m3[3] = {0.0, 0.0, 0.0};
-      for (int e = threadIdx.x; e < nR; e += NT) {
-        const double g = double(G[e]), x = double(eta[e]), h = double(Heta[e]);
-        m3[0] += g * x; m3[1] += x * h; m3[2] += x * x;
+      for (int e0 = threadIdx.x; e0 < nR; e0 += EB * NT) {
+        To gq[EB];
+        Ti xq[EB], hq[EB];
+#pragma unroll
+        for (int u = 0; u < EB; ++u) {
+          const int e = e0 + u * NT;
+          const bool ok = e < nR;
+          gq[u] = ok ? G[e] : To(0); xq[u] = ok ? eta[e] : Ti(0); hq[u] = ok ? Heta[e] : Ti(0);
+        }
+#pragma unroll
+        for (int u = 0; u < EB; ++u)
+          if (e0 + u * NT < nR) {
+            const double g = double(gq[u]), x = double(xq[u]), h = double(hq[u]);
+            m3[0] += g * x; m3[1] += x * h; m3[2] += x * x;
+          }
       }
       bsum<3>(m3, sm.red);
       for (int i = threadIdx.x; i < N; i += NT) retract_block<To, Ti, R, To>(i, Y, eta, 1.0, Yc);
@@ -878,32 +972,120 @@ struct Cta {
   // coefficients, the Ritz values and the decision stay FP64.
   __device__ float* Vf() const { return reinterpret_cast<float*>(V); }
 
-  // w -= V c over the first m columns of V (c = V^T w), one pass of classical Gram-Schmidt in
-  // FP32 arithmetic (FP64 w).  w and c are converted once per pass (FP32 copies in shared
-  // memory): float <-> double conversions share B300's narrow FP64 pipe.
+  // w -= V c with c = V^T w over the first m columns of V: one pass of classical Gram-Schmidt in
+  // FP32 arithmetic (FP64 w, converted once per pass: float <-> double conversions share B300's
+  // narrow FP64 pipe).  Each c_j is one warp's sum over the 16-byte chunks of column j (lane l
+  // takes chunks l, l + 32, ...), each (V c)_e one thread's sum over j in order, so neither
+  // depends on which warp or CTA computes it: a team splits the columns of c and the rows of V c
+  // between its CTAs and exchanges them through distributed shared memory, bit-identical to one
+  // CTA.  Every load of V is 16 bytes with several in flight per thread (the basis streams from
+  // L2 at the SM's bandwidth rather than its latency).  Columns of V are zero in rows [n, ldq).
+  static constexpr int RO_COLS = 4;      // columns of c per warp and pass
+  static constexpr int RO_U = 2;         // 16-byte chunks per lane and column in flight
+  static constexpr int RO_J = 8;         // columns of V per thread in flight in V c
   __device__ void reorth(double* w, int m) {
     if (m <= 0) return;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int NMc = P->NM;
-    const float* Vb = Vf();
-    float* wf = (float*)sm.ws;             // free during the certificate between Z products
-    float* cf = (float*)sm.cv;
-    for (int e = threadIdx.x; e < n; e += NT) wf[e] = float(w[e]);
+    const int NM4 = P->NM >> 2, n4 = ldq >> 2;
+    const float4* V4 = reinterpret_cast<const float4*>(Vf());
+    float* wf = (float*)sm.ws;             // FP32 w, ldq entries (free between Z products)
+    float* tf = (float*)sm.xs;             // V c, ldq entries
+    float* cf = (float*)sm.cv;             // c, m entries
+    const int cs = team();
+    const unsigned me = cs > 1 ? cl_rank() : 0u;
+    for (int e = threadIdx.x; e < ldq; e += NT) wf[e] = e < n ? float(w[e]) : 0.f;
     __syncthreads();
-    for (int j = wid; j < m; j += NW) {
-      float sacc = 0.f;
-      const float* col = Vb + (size_t)j * NMc;
-      for (int e = lane; e < n; e += 32) sacc = fmaf(col[e], wf[e], sacc);
+    {  // c_j for j in [j0, j1)
+      const int per = (m + cs - 1) / cs;
+      const int j0 = min(m, (int)me * per), j1 = min(m, j0 + per);
+      const float4* w4 = reinterpret_cast<const float4*>(wf);
+      for (int jb = j0 + RO_COLS * wid; jb < j1; jb += RO_COLS * NW) {
+        float acc[RO_COLS];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
-      if (lane == 0) cf[j] = sacc;
+        for (int q = 0; q < RO_COLS; ++q) acc[q] = 0.f;
+        for (int c0 = lane; c0 < n4; c0 += 32 * RO_U) {
+          float4 a[RO_COLS][RO_U];
+#pragma unroll
+          for (int q = 0; q < RO_COLS; ++q)
+#pragma unroll
+            for (int u = 0; u < RO_U; ++u) {
+              const int c = c0 + 32 * u;
+              a[q][u] = (jb + q < j1 && c < n4) ? V4[(size_t)(jb + q) * NM4 + c] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+          for (int u = 0; u < RO_U; ++u) {
+            const int c = c0 + 32 * u;
+            if (c < n4) {
+              const float4 y = w4[c];
+#pragma unroll
+              for (int q = 0; q < RO_COLS; ++q)
+                acc[q] = fmaf(a[q][u].x, y.x, fmaf(a[q][u].y, y.y, fmaf(a[q][u].z, y.z, fmaf(a[q][u].w, y.w, acc[q]))));
+            }
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < RO_COLS; ++q) {
+          float x = acc[q];
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+          if (lane == q && jb + q < j1) {
+            cf[jb + q] = x;
+            for (int k = 1; k < cs; ++k) cl_st(cl_map(cf + jb + q, (me + k) % cs), x);
+          }
+        }
+      }
     }
-    __syncthreads();
-    for (int e = threadIdx.x; e < n; e += NT) {
-      float t = 0.f;
-      for (int j = 0; j < m; ++j) t = fmaf(Vb[(size_t)j * NMc + e], cf[j], t);
-      w[e] -= double(t);
+    if (cs > 1) cl_sync();
+    else __syncthreads();
+    {  // (V c)_e for the rows [r0, r1), 4 rows (one 16-byte chunk) a thread, two chunks at a time
+      int r0 = 0, r1 = n;
+      if (cs > 1) cl_rows(n, r0, r1);
+      const int cb0 = r0 >> 2, cb1 = r0 < r1 ? (r1 + 3) >> 2 : cb0;
+      float4* t4 = reinterpret_cast<float4*>(tf);
+      for (int c = cb0 + threadIdx.x; c < cb1; c += 2 * NT) {
+        const int c2 = c + NT;
+        const bool two = c2 < cb1;
+        float4 s1 = make_float4(0.f, 0.f, 0.f, 0.f), s2 = s1;
+        int j = 0;
+        for (; j + RO_J <= m; j += RO_J) {
+          float4 a1[RO_J], a2[RO_J];
+#pragma unroll
+          for (int u = 0; u < RO_J; ++u) {
+            a1[u] = V4[(size_t)(j + u) * NM4 + c];
+            a2[u] = two ? V4[(size_t)(j + u) * NM4 + c2] : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+#pragma unroll
+          for (int u = 0; u < RO_J; ++u) {
+            const float cj = cf[j + u];
+            s1.x = fmaf(a1[u].x, cj, s1.x); s1.y = fmaf(a1[u].y, cj, s1.y);
+            s1.z = fmaf(a1[u].z, cj, s1.z); s1.w = fmaf(a1[u].w, cj, s1.w);
+            s2.x = fmaf(a2[u].x, cj, s2.x); s2.y = fmaf(a2[u].y, cj, s2.y);
+            s2.z = fmaf(a2[u].z, cj, s2.z); s2.w = fmaf(a2[u].w, cj, s2.w);
+          }
+        }
+        for (; j < m; ++j) {
+          const float cj = cf[j];
+          const float4 a = V4[(size_t)j * NM4 + c];
+          s1.x = fmaf(a.x, cj, s1.x); s1.y = fmaf(a.y, cj, s1.y);
+          s1.z = fmaf(a.z, cj, s1.z); s1.w = fmaf(a.w, cj, s1.w);
+          if (two) {
+            const float4 b = V4[(size_t)j * NM4 + c2];
+            s2.x = fmaf(b.x, cj, s2.x); s2.y = fmaf(b.y, cj, s2.y);
+            s2.z = fmaf(b.z, cj, s2.z); s2.w = fmaf(b.w, cj, s2.w);
+          }
+        }
+        t4[c] = s1;
+        if (two) t4[c2] = s2;
+        for (int k = 1; k < cs; ++k) {
+          const unsigned peer = (me + k) % cs;
+          cl_st(cl_map(t4 + c, peer), s1);
+          if (two) cl_st(cl_map(t4 + c2, peer), s2);
+        }
+      }
     }
+    if (cs > 1) cl_sync();
+    else __syncthreads();
+    for (int e = threadIdx.x; e < n; e += NT) w[e] -= double(tf[e]);
     __syncthreads();
   }
 
@@ -957,10 +1139,11 @@ struct Cta {
     __syncthreads();
     const int nd = s_nd;
     const double* rot = sm.small + 128;
-    for (int e = threadIdx.x; e < n; e += NT)
+    for (int e = threadIdx.x; e < ldq; e += NT)
       for (int j = 0; j < nd; ++j) {
         double t = 0.0;
-        for (int a = 0; a < R; ++a) t += y64[(size_t)e * R + a] * rot[a * R + j];
+        if (e < n)
+          for (int a = 0; a < R; ++a) t += y64[(size_t)e * R + a] * rot[a * R + j];
         Vb[(size_t)j * NMc + e] = float(t);
       }
     __syncthreads();
@@ -1003,7 +1186,7 @@ struct Cta {
       const double nrm = sqrt(dot(lw, lw, n));
       const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
       float* v0 = Vb + (size_t)nd * NMc;
-      for (int e = threadIdx.x; e < n; e += NT) v0[e] = float(lw[e] * inv);
+      for (int e = threadIdx.x; e < ldq; e += NT) v0[e] = e < n ? float(lw[e] * inv) : 0.f;
       __syncthreads();
     }
     int K = 0;
@@ -1027,7 +1210,7 @@ struct Cta {
       const double bn = sqrt(dot(lw, lw, n));
       const double inv = bn > 0.0 ? 1.0 / bn : 0.0;
       float* vk1 = Vb + (size_t)(nd + k + 1) * NMc;
-      for (int e = threadIdx.x; e < n; e += NT) vk1[e] = float(lw[e] * inv);
+      for (int e = threadIdx.x; e < ldq; e += NT) vk1[e] = e < n ? float(lw[e] * inv) : 0.f;
       if (threadIdx.x == 0) { sm.ha[k] = a; sm.hb[k] = bn; }
       __syncthreads();
       ++info.n_lanczos;
