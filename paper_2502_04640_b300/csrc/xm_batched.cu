@@ -337,9 +337,17 @@ __device__ __noinline__ void sweep64(const double* Q, int n, int ldq, const doub
 // xs (R columns of ldq, type Td) <- v (n x R row-major, type Ts), zero below row n
 template <typename Ts, typename Td, int R>
 __device__ __forceinline__ void stage(const Ts* __restrict__ v, int n, int ldq, Td* __restrict__ xs) {
-  for (int e = threadIdx.x; e < ldq * R; e += NT) {
-    const int j = e / ldq, i = e - j * ldq;
-    xs[e] = i < n ? Td(v[(size_t)i * R + j]) : Td(0);
+  constexpr int B = 4;   // elements a thread loads before it stores
+  for (int e0 = threadIdx.x; e0 < ldq * R; e0 += B * NT) {
+    Ts t[B];
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+      const int e = e0 + u * NT, j = e / ldq, i = e - j * ldq;
+      t[u] = (e < ldq * R && i < n) ? v[(size_t)i * R + j] : Ts(0);
+    }
+#pragma unroll
+    for (int u = 0; u < B; ++u)
+      if (e0 + u * NT < ldq * R) xs[e0 + u * NT] = Td(t[u]);
   }
   __syncthreads();
 }
@@ -701,7 +709,17 @@ struct Cta {
 
   __device__ double dot(const double* a, const double* b, int len) {
     double v[1] = {0.0};
-    for (int e = threadIdx.x; e < len; e += NT) v[0] += a[e] * b[e];
+    for (int e0 = threadIdx.x; e0 < len; e0 += EB * NT) {
+      double x[EB], y[EB];
+#pragma unroll
+      for (int u = 0; u < EB; ++u) {
+        const int e = e0 + u * NT;
+        x[u] = e < len ? a[e] : 0.0; y[u] = e < len ? b[e] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < EB; ++u)
+        if (e0 + u * NT < len) v[0] += x[u] * y[u];
+    }
     bsum<1>(v, sm.red);
     return v[0];
   }
@@ -714,6 +732,7 @@ struct Cta {
   // the vectors may alias as far as the compiler knows, so a load after a store would wait one
   // memory round trip per element.  The per-camera loops load a camera's blocks before storing.
   static constexpr int EB = 4;
+  static constexpr int NMAX_LZ = 4 * NT;   // Lanczos rows a CTA keeps in registers across a step
   template <typename To, typename Ti>
   __device__ void rtr(double tol_rel, int max_outer, bool bulk) {
     To*& Y = *reinterpret_cast<To**>(sizeof(To) == 4 ? (void*)&yf : (void*)&y64);
@@ -925,6 +944,10 @@ struct Cta {
       }
       if (Delta < 1e-12 * Delta_bar) break;
       if (bulk && (rejects >= 6 || Delta < 1e-7 * Delta_bar)) break;
+      // A step rejected at the FP32 floor (||rgrad|| <= 1e-6 of the start): the FP32 objective
+      // can no longer rank the candidates, and every further bulk step (each a tCG run to the
+      // trust-region boundary, then rejected) is lost work; the FP64-gradient polish takes over.
+      if (bulk && !accept && sqrt(g2) <= 1e-6 * ref_g) break;
       if (bulk) {
         // near the FP32 floor (||rgrad|| <= 1e-6 of the start) and f no longer improving beyond
         // its own noise (reg) over STALL_W steps: hand over to the FP64-gradient polish.  This
@@ -993,7 +1016,14 @@ struct Cta {
     float* cf = (float*)sm.cv;             // c, m entries
     const int cs = team();
     const unsigned me = cs > 1 ? cl_rank() : 0u;
-    for (int e = threadIdx.x; e < ldq; e += NT) wf[e] = e < n ? float(w[e]) : 0.f;
+    for (int e0 = threadIdx.x; e0 < ldq; e0 += EB * NT) {
+      double x[EB];
+#pragma unroll
+      for (int u = 0; u < EB; ++u) x[u] = e0 + u * NT < n ? w[e0 + u * NT] : 0.0;
+#pragma unroll
+      for (int u = 0; u < EB; ++u)
+        if (e0 + u * NT < ldq) wf[e0 + u * NT] = float(x[u]);
+    }
     __syncthreads();
     {  // c_j for j in [j0, j1)
       const int per = (m + cs - 1) / cs;
@@ -1085,7 +1115,18 @@ struct Cta {
     }
     if (cs > 1) cl_sync();
     else __syncthreads();
-    for (int e = threadIdx.x; e < n; e += NT) w[e] -= double(tf[e]);
+    for (int e0 = threadIdx.x; e0 < n; e0 += EB * NT) {
+      double x[EB];
+      float t[EB];
+#pragma unroll
+      for (int u = 0; u < EB; ++u) {
+        const int e = e0 + u * NT;
+        x[u] = e < n ? w[e] : 0.0; t[u] = e < n ? tf[e] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < EB; ++u)
+        if (e0 + u * NT < n) w[e0 + u * NT] = x[u] - double(t[u]);
+    }
     __syncthreads();
   }
 
@@ -1198,19 +1239,42 @@ struct Cta {
       const float* vk = Vb + (size_t)(nd + k) * NMc;
       const float* vkm1 = k > 0 ? Vb + (size_t)(nd + k - 1) * NMc : nullptr;
       zmul_f(vk, lw);
+      // a thread's EB elements of v_k, v_{k-1} and w stay in registers between the two loops
+      float vq[(NMAX_LZ + NT - 1) / NT], vmq[(NMAX_LZ + NT - 1) / NT];
+      double wq[(NMAX_LZ + NT - 1) / NT];
       double av[1] = {0.0};
-      for (int e = threadIdx.x; e < n; e += NT) av[0] += double(vk[e]) * lw[e];
+#pragma unroll
+      for (int u = 0; u < (NMAX_LZ + NT - 1) / NT; ++u) {
+        const int e = threadIdx.x + u * NT;
+        const bool ok = e < n;
+        vq[u] = ok ? vk[e] : 0.f; vmq[u] = (ok && vkm1) ? vkm1[e] : 0.f; wq[u] = ok ? lw[e] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < (NMAX_LZ + NT - 1) / NT; ++u)
+        if (threadIdx.x + u * NT < n) av[0] += double(vq[u]) * wq[u];
+      for (int e = threadIdx.x + NMAX_LZ; e < n; e += NT) av[0] += double(vk[e]) * lw[e];
       bsum<1>(av, sm.red);
       const double a = av[0];
       const double b = k > 0 ? sm.hb[k - 1] : 0.0;
-      for (int e = threadIdx.x; e < n; e += NT) lw[e] -= a * double(vk[e]) + (vkm1 ? b * double(vkm1[e]) : 0.0);
+#pragma unroll
+      for (int u = 0; u < (NMAX_LZ + NT - 1) / NT; ++u)
+        if (threadIdx.x + u * NT < n)
+          lw[threadIdx.x + u * NT] = wq[u] - (a * double(vq[u]) + (vkm1 ? b * double(vmq[u]) : 0.0));
+      for (int e = threadIdx.x + NMAX_LZ; e < n; e += NT) lw[e] -= a * double(vk[e]) + (vkm1 ? b * double(vkm1[e]) : 0.0);
       __syncthreads();
       reorth(lw, nd + k + 1);
       reorth(lw, nd + k + 1);
       const double bn = sqrt(dot(lw, lw, n));
       const double inv = bn > 0.0 ? 1.0 / bn : 0.0;
       float* vk1 = Vb + (size_t)(nd + k + 1) * NMc;
-      for (int e = threadIdx.x; e < ldq; e += NT) vk1[e] = e < n ? float(lw[e] * inv) : 0.f;
+      for (int e0 = threadIdx.x; e0 < ldq; e0 += EB * NT) {
+        double x[EB];
+#pragma unroll
+        for (int u = 0; u < EB; ++u) x[u] = e0 + u * NT < n ? lw[e0 + u * NT] : 0.0;
+#pragma unroll
+        for (int u = 0; u < EB; ++u)
+          if (e0 + u * NT < ldq) vk1[e0 + u * NT] = e0 + u * NT < n ? float(x[u] * inv) : 0.f;
+      }
       if (threadIdx.x == 0) { sm.ha[k] = a; sm.hb[k] = bn; }
       __syncthreads();
       ++info.n_lanczos;
