@@ -648,13 +648,14 @@ struct Cta {
   }
 
   // CTA-uniform: thread 0 reads the clock and broadcasts, so every thread takes the same branch
-  // In a cluster, rank 0's clock decides for every CTA (the branches must stay identical).
+  // In a team, rank 0's clock decides for every CTA (the branches must stay identical); a CTA
+  // working alone decides for itself, whatever its rank in the cluster it split from.
   __device__ bool over_time() {
     if (!P->time_limit_ns) return timed_out;
     __shared__ int s_late;
     const unsigned cs = (unsigned)team();
     if (cs > 1) cl_sync();               // every CTA has read the previous decision
-    if (threadIdx.x == 0 && cl_rank() == 0) {
+    if (threadIdx.x == 0 && team_lead()) {
       const int late = gtimer() > info.t_begin_ns + P->time_limit_ns ? 1 : 0;
       s_late = late;
       for (unsigned k = 1; k < cs; ++k) cl_st(cl_map(&s_late, k), late);
@@ -732,6 +733,9 @@ struct Cta {
   // the vectors may alias as far as the compiler knows, so a load after a store would wait one
   // memory round trip per element.  The per-camera loops load a camera's blocks before storing.
   static constexpr int EB = 4;
+  // tCG iterations per step of the FP32 bulk phase (at most max_tcg), as xm_solve: truncated
+  // inner solves far from the optimum; the polish keeps max_tcg
+  static constexpr int BULK_TCG_CAP = 60;
   static constexpr int NMAX_LZ = 4 * NT;   // Lanczos rows a CTA keeps in registers across a step
   template <typename To, typename Ti>
   __device__ void rtr(double tol_rel, int max_outer, bool bulk) {
@@ -793,7 +797,8 @@ struct Cta {
       // converges to the same gradient tolerance, checked by the outer loop in FP64.
       const double floor_rel = (!bulk && sizeof(Ti) < sizeof(To)) ? 1e-4 : 0.0;
       int iters = 0;
-      for (int j = 0; j < P->o.max_tcg; ++j) {
+      const int tcg_cap = bulk ? min(P->o.max_tcg, BULK_TCG_CAP) : P->o.max_tcg;
+      for (int j = 0; j < tcg_cap; ++j) {
         const double kap = hvp<Ti>(Yin, dv, Hd, lam);
         ++iters;
         const double D2 = Delta * Delta;

@@ -461,6 +461,11 @@ struct Solver {
   static constexpr int LPART_MAX = 64;   // column chunks of the reorthogonalisation product
   static constexpr int BULK_PLATEAU = 15; // outer steps without a halving of min ||rgrad||
   static constexpr int PRECOND_CAP_RUN = 3; // capped tCG solves in a row that switch on precond = 2
+  // tCG iterations per step of the FP32 bulk phase (at most max_tcg): far from the optimum a
+  // truncated inner solve is still a descent step and the trust region absorbs it; the long
+  // inner solves of the late bulk (100-200 iterations) bought little.  A solve stopped here
+  // counts as capped (cap_run) like one stopped at max_tcg.  The polish keeps max_tcg.
+  static constexpr int BULK_TCG_CAP = 60;
   double* lpart = nullptr;               // LPART_MAX x n_pad partial sums
   int last_nd = 0;                       // deflation columns of the last certificate's basis
   // LOBPCG certificate: 12 blocks of n_pad x 4 floats, preconditioner, Gram partials, scalars
@@ -688,9 +693,10 @@ struct Solver {
       } else {
         Yin = (const Ti*)bY;
       }
+      const int tcg_cap = bulk ? std::min(o.max_tcg, BULK_TCG_CAP) : o.max_tcg;
       k_tcg_init<To, Ti, R><<<nb_cam, CAM_THREADS, 0, st>>>(
           N, Yin, (const To*)bG, (Ti*)bEta, (Ti*)bHeta, (Ti*)bR, (Ti*)bZ, (Ti*)bD, pcMinv, d_sc, Delta,
-          o.max_tcg, 1.0, 0.1, bulk ? 0.5 * tol_abs : 0.0, ctx->d_partials, ctx->d_counter);
+          tcg_cap, 1.0, 0.1, bulk ? 0.5 * tol_abs : 0.0, ctx->d_partials, ctx->d_counter);
       ++launches;
       XM_CUDA_TRY(cudaGetLastError());
       // Chunks of CH iterations; the host reads the done flag of chunk k-1 while chunk k is
@@ -737,7 +743,7 @@ struct Solver {
         return ex;
       };
       xm_status chunk_status = XM_OK;
-      for (int j = 0; j < o.max_tcg && !done; j += CH) {
+      for (int j = 0; j < tcg_cap && !done; j += CH) {
         cudaGraphExec_t ex = (j > 0 && use_graphs) ? chunk_exec() : nullptr;
         if (j > 0 && use_graphs && !ex) use_graphs = false;
         if (ex) {

@@ -161,6 +161,27 @@ def test_batched_clusters_are_bit_identical(C, init_jitter):
         q.free()
 
 
+def test_batched_time_limit_on_split_clusters(C):
+    """The 256-scene serving batch on the automatic clusters (pairs for the large scenes, then the
+    clusters split and every CTA takes scenes alone), with a per-scene time limit that no scene
+    reaches: every scene certified in every batch, bit-identical to the batch without a limit.
+    A CTA of cluster rank 1 working alone must decide the time limit by its own clock; reading
+    the flag that only a team's rank 0 writes had ended most small scenes at their first step."""
+    from paper_2502_04640_b300 import xm
+    scs = scenes.config5()
+    qs, b = _build(C, scs)
+    for q in qs:
+        q.free()
+    ref = xm.xm_solve_batched(b, xm.xm_default_opts(time_limit_s=0.0))
+    assert all(i["certified"] == 1 for i in ref["info"])
+    for _ in range(3):
+        o = xm.xm_solve_batched(b, xm.xm_default_opts(time_limit_s=60.0))
+        bad = [(i["N"], i["status"], i["n_outer"]) for i in o["info"] if i["certified"] != 1]
+        assert not bad, bad[:8]
+        assert torch.equal(o["R"], ref["R"]) and torch.equal(o["s"], ref["s"])
+    b.free()
+
+
 def test_batched_400_camera_scene_matches_oracle(C):
     """The largest scene size of the serving batch (400 cameras, 3N = 1200: sweep staging and
     Krylov scratch near the shared-memory ceiling), in the batch's own shape (50 landmarks per
