@@ -77,8 +77,13 @@ __device__ __forceinline__ unsigned long long gtimer() {
 // ------------------------------------------------------------------ CTA reductions
 // Deterministic CTA sum of K values: warp butterflies, then the warp partials in warp order;
 // every thread returns the totals.  red: NW * K doubles of shared memory.
+// CTA sum of K values per thread, the same on every thread: warp sums, then thread k adds the
+// NW warp sums of value k in warp order and publishes it (one warp's FP64 adds instead of every
+// thread's: B300's FP64 pipe is narrow).  K <= 64.
+__shared__ double s_bsum[64];
 template <int K>
 __device__ __forceinline__ void bsum(double (&v)[K], double* red) {
+  static_assert(K <= 64, "bsum: K <= 64");
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
@@ -86,13 +91,14 @@ __device__ __forceinline__ void bsum(double (&v)[K], double* red) {
     if (lane == 0) red[wid * K + k] = x;
   }
   __syncthreads();
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
+  if (threadIdx.x < K) {
     double t = 0.0;
-    for (int w = 0; w < NW; ++w) t += red[w * K + k];
-    v[k] = t;
+    for (int w = 0; w < NW; ++w) t += red[w * K + threadIdx.x];
+    s_bsum[threadIdx.x] = t;
   }
   __syncthreads();
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = s_bsum[k];
 }
 
 // ------------------------------------------------------------------ thread-block clusters
