@@ -132,7 +132,7 @@ k_cg_epi(int N, const T* __restrict__ Y, T* __restrict__ Wd, const T* __restrict
   if (sc->done) return;
   double v[1] = {0.0};
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < N) v[0] = hvp_block<T, R>(i, N, Y, Wd, delta, Hd, Lam, sc->mu);
+  if (i < N) v[0] = hvp_block<T, R, T>(i, N, Y, Wd, delta, Hd, Lam, sc->mu);
   grid_reduce<1>(v, partials, counter, [&](double* t) {
     sc->kappa = t[0];
     if (!(t[0] > 0.0)) { sc->done = 1; sc->reason = 1; return; }
@@ -233,13 +233,14 @@ __device__ __forceinline__ void omega_from_C(const double* C, const double* __re
     }
 }
 
-// per-camera share of C = Y^T v
-template <int R>
-__device__ __forceinline__ void yt_v(const double (&y)[3][R], const double (&v)[3][R], double (&c)[R * R]) {
+// per-camera share of C = Y^T v, in the element type C of y and v (FP32 in the FP32 inner solve:
+// B300's FP64 pipe is narrow), handed to the FP64 grid reduction
+template <int R, typename C = double>
+__device__ __forceinline__ void yt_v(const C (&y)[3][R], const C (&v)[3][R], double (&c)[R * R]) {
 #pragma unroll
   for (int a = 0; a < R; ++a)
 #pragma unroll
-    for (int b = 0; b < R; ++b) c[a * R + b] = y[0][a] * v[0][b] + y[1][a] * v[1][b] + y[2][a] * v[2][b];
+    for (int b = 0; b < R; ++b) c[a * R + b] = double(y[0][a] * v[0][b] + y[1][a] * v[1][b] + y[2][a] * v[2][b]);
 }
 
 // x = 0, r = b (tangent), C = Y^T r -> Om; resets the CG scalars
@@ -279,25 +280,27 @@ k_pcg_update(int N, const T* __restrict__ Y, T* __restrict__ x, T* __restrict__ 
   for (int k = 0; k < R * R; ++k) v[k] = 0.0;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < N) {
-    double y[3][R], xx[3][R], rr[3][R], pp[3][R], hp[3][R];
-    load_block<T, double, R>(Y, i, y);
-    load_block<T, double, R>(x, i, xx);
-    load_block<T, double, R>(r, i, rr);
-    load_block<T, double, R>(p, i, pp);
-    load_block<T, double, R>(Hp, i, hp);
+    using C = T;   // per-camera arithmetic in the inner solve's precision
+    const C at = C(alpha);
+    C y[3][R], xx[3][R], rr[3][R], pp[3][R], hp[3][R];
+    load_block<T, C, R>(Y, i, y);
+    load_block<T, C, R>(x, i, xx);
+    load_block<T, C, R>(r, i, rr);
+    load_block<T, C, R>(p, i, pp);
+    load_block<T, C, R>(Hp, i, hp);
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
-      for (int j = 0; j < R; ++j) { xx[a][j] += alpha * pp[a][j]; rr[a][j] -= alpha * hp[a][j]; }
-    double S[3][3], al;
-    dual_block<double, R>(rr, y, i == 0, S, al);
+      for (int j = 0; j < R; ++j) { xx[a][j] += at * pp[a][j]; rr[a][j] -= at * hp[a][j]; }
+    C S[3][3], al;
+    dual_block<C, R>(rr, y, i == 0, S, al);
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
       for (int j = 0; j < R; ++j) rr[a][j] -= S[a][0] * y[0][j] + S[a][1] * y[1][j] + S[a][2] * y[2][j];
-    yt_v<R>(y, rr, v);
-    store_block<T, double, R>(x, i, xx);
-    store_block<T, double, R>(r, i, rr);
+    yt_v<R, C>(y, rr, v);
+    store_block<T, C, R>(x, i, xx);
+    store_block<T, C, R>(r, i, rr);
   }
   grid_reduce<R * R>(v, partials, counter, [&](double* t) { omega_from_C<R>(t, defl, Om); });
 }
@@ -366,24 +369,25 @@ k_precond_from_col(int N, const T* __restrict__ Y, float* __restrict__ col, T* _
   for (int k = 0; k < R * R; ++k) v[k] = 0.0;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < N) {
-    double y[3][R], zz[3][R];
-    load_block<T, double, R>(Y, i, y);
+    using C = T;   // per-camera arithmetic in the inner solve's precision
+    C y[3][R], zz[3][R];
+    load_block<T, C, R>(Y, i, y);
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
       for (int j = 0; j < R; ++j) {
         float* c = col + (size_t)(3 * i + a) * R + j;
-        zz[a][j] = 0.5 * double(*c);
+        zz[a][j] = C(0.5) * C(*c);
         *c = 0.0f;
       }
-    double S[3][3], al;
-    dual_block<double, R>(zz, y, i == 0, S, al);
+    C S[3][3], al;
+    dual_block<C, R>(zz, y, i == 0, S, al);
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
       for (int j = 0; j < R; ++j) zz[a][j] -= S[a][0] * y[0][j] + S[a][1] * y[1][j] + S[a][2] * y[2][j];
-    yt_v<R>(y, zz, v);
-    store_block<T, double, R>(z, i, zz);
+    yt_v<R, C>(y, zz, v);
+    store_block<T, C, R>(z, i, zz);
   }
   grid_reduce<R * R>(v, partials, counter, [&](double* t) { omega_from_C<R>(t, defl, Om); });
 }
@@ -399,27 +403,31 @@ k_pcg_rz(int N, const T* __restrict__ Y, const T* __restrict__ r, T* __restrict_
   double v[2] = {0.0, 0.0};
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < N) {
-    double y[3][R], rr[3][R], zz[3][R], O[R][R];
-    load_block<T, double, R>(Y, i, y);
-    load_block<T, double, R>(r, i, rr);
-    load_block<T, double, R>(z, i, zz);
+    using C = T;   // per-camera arithmetic in the inner solve's precision, sums in FP64
+    C y[3][R], rr[3][R], zz[3][R], O[R][R];
+    load_block<T, C, R>(Y, i, y);
+    load_block<T, C, R>(r, i, rr);
+    load_block<T, C, R>(z, i, zz);
 #pragma unroll
     for (int a = 0; a < R; ++a)
 #pragma unroll
-      for (int b = 0; b < R; ++b) O[a][b] = Om[a * R + b];
+      for (int b = 0; b < R; ++b) O[a][b] = C(Om[a * R + b]);
+    C s0 = C(0), s1 = C(0);
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
       for (int j = 0; j < R; ++j) {
-        double t = 0.0;
+        C t = C(0);
 #pragma unroll
         for (int k = 0; k < R; ++k) t += y[a][k] * O[k][j];
         zz[a][j] -= t;
-        v[0] += rr[a][j] * rr[a][j];
-        v[1] += rr[a][j] * zz[a][j];
+        s0 += rr[a][j] * rr[a][j];
+        s1 += rr[a][j] * zz[a][j];
       }
-    store_block<T, double, R>(z, i, zz);
-    if (init) store_block<T, double, R>(p, i, zz);
+    v[0] = double(s0);
+    v[1] = double(s1);
+    store_block<T, C, R>(z, i, zz);
+    if (init) store_block<T, C, R>(p, i, zz);
   }
   grid_reduce<2>(v, partials, counter, [&](double* t) {
     sc->rr = t[0];
