@@ -80,7 +80,8 @@ typedef struct xm_opts {
   double cert_tau_rel;     /* certified iff lambda_min(Z) >= -cert_tau_rel * lambda_max
                               (default 1e-6)                                                 */
   int max_outer;           /* RTR iterations per rank (per phase; default 300)             */
-  int max_tcg;             /* tCG iterations per RTR step (default 200)                    */
+  int max_tcg;             /* tCG iterations per RTR step (default 200); steps of the FP32
+                              bulk phase stop at min(max_tcg, 60)                          */
   int max_polish;          /* FP64 polish RTR iterations (mixed modes; default 20)         */
   int lanczos_max;         /* Krylov dimension cap of the certificate (default 800)        */
   double lanczos_tol;      /* Ritz residual / |theta_max| stop for lambda_min (default 1e-8) */
