@@ -63,6 +63,12 @@ L2_BYTES = 126e6
 # sweep kernel changes.
 SWEEP_TRAFFIC_RATIO = (1.88 + 0.00412) / 1.857268
 SWEEP_TRAFFIC_N = 30465
+# The same ratio for k_batched<4> on the 256-scene batch: DRAM read + write of one launch (one
+# whole batch, one ncu --set full capture of the kernel as it stands) over the dense sweep bytes
+# of that launch's scenes (the bytes_per_launch the profiled run printed).  Below 1: L2 serves
+# part of the small scenes' re-reads.  Applied to the 256-scene batch only; re-measure (or set
+# to None) whenever the batched kernel changes.
+BATCH_TRAFFIC_RATIO = (78.787872 + 2.726973) / 90.936067344
 
 
 def peaks():
@@ -424,7 +430,11 @@ def batched_measure(ctx, scs, warmup: int, steps: int, time_limit: float = 60.0)
                        "scene_solve_p50": _pct(own_ms, 50), "scene_solve_p99": _pct(own_ms, 99)},
         "certified": sum(i["certified"] for i in last), "scenes": S, "cameras": tot,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "k_batched<4>",
+                     "frac": achieved / peak,
+                     "traffic": by * BATCH_TRAFFIC_RATIO if S == 256 else None,
+                     "traffic_note": "ncu DRAM read+write of one batch launch as a ratio to its dense "
+                                     "sweep bytes (256-scene batch only)",
+                     "kernel": "k_batched<4>",
                      "bytes_per_launch": by, "launch_ms": per_step * 1e3, "peak_kind": peak_kind,
                      "note": "dense sweep bytes of all scenes / batch time; the FP32 copies total "
                              f"{q_bytes / 1e6:.0f} MB, so part of every sweep is served by L2"},
