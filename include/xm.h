@@ -423,6 +423,9 @@ xm_status xm_batch_autotune(xm_ctx* ctx, xm_batch* b, int reps, int* tile_out);
  * CTAs for the rest of the batch.  cs in {1, 2, 4}, or 0 (the default): 2.  n_min >= 0, or 0
  * (the default): the smallest n with n^2 >= sum over scenes of n^2 / (SM count), i.e. the scenes
  * whose products alone outweigh one SM's share; no cluster launch when no scene reaches it.
+ * With both automatic (cs = 0, n_min = 0), when at least two scenes reach 1.8 times that n, those
+ * (at most one per 16 SMs) run on 4-CTA clusters in a launch beside the pairs, which then start at
+ * 1.3 times it; both launches go on with single CTAs from one shared queue (still bit-identical).
  * XM_EINVAL for other values.  Takes effect at the next xm_solve_batched. */
 xm_status xm_batch_cluster(xm_ctx* ctx, xm_batch* b, int cs, int n_min);
 /* Solves every scene.  opts: as xm_solve (r0 <= 4, r_max <= 8; prec is ignored: the FP32-bulk

@@ -35,6 +35,13 @@ constexpr int NW = NT / 32;
 // direction to escape along (lambda_min < -1e-4 |lambda_max|), which Lanczos finds among its
 // first Ritz values; the full certificate after the polish decides (60 steps had cost ~5 % more)
 constexpr int KQUICK = 30;
+// Automatic team sizes (xm_batch_cluster cs = 0, n_min = 0), in units of the smallest n whose
+// n^2 outweighs one SM's share of the batch's sum of n^2: scenes from QUAD_FACTOR times that on
+// 4-CTA clusters when at least two reach it (at most one SM in 16 per quad scene), pairs from
+// PAIR_FACTOR times it beside them.  Chosen by a list-scheduling model on the measured per-scene
+// times of the 256-scene batch for 1, 2 and 4 CTAs (47 ms against 52 ms for pairs alone).
+constexpr double QUAD_FACTOR = 1.8;
+constexpr double PAIR_FACTOR = 1.3;
 constexpr int NVEC = 17;           // per-slot vectors of NM x 8 doubles
 constexpr int NCLASS = 4;          // scene-size classes of the tiling table
 constexpr int XM_BATCH_KMAX = 400;       // Krylov cap of the batched certificate (shared memory)
@@ -69,6 +76,12 @@ struct Params {
   unsigned long long time_limit_ns;  // per-scene wall-clock cap (0: none)
   int team_min_n;                  // scenes with n >= this run on a whole cluster
   int pf_dist;                     // L2 prefetch distance of the sweeps (rounds; 0: none)
+  int slot_base;                   // first per-CTA slot of this launch (launches side by side)
+  // after this launch's own queue (desc[0..S)): its CTAs continue one by one on a second queue
+  // shared with the launch beside it (null: none)
+  unsigned* queue2;
+  const Desc* desc2;
+  int S2;
 };
 
 __device__ __forceinline__ unsigned long long gtimer() {
@@ -643,7 +656,7 @@ struct Cta {
     Q32 = p->Q32 + dd.q32;
     Q64 = p->Q64 + dd.q64;
     sm = carve(smem_base, p->NM, R, p->kmax);
-    slot = p->slots + (size_t)blockIdx.x * p->slot_doubles;
+    slot = p->slots + (size_t)(blockIdx.x + p->slot_base) * p->slot_doubles;
     const size_t VS = (size_t)p->NM * 8;
     double* v[NVEC];
     for (int k = 0; k < NVEC; ++k) v[k] = slot + k * VS;
@@ -1573,23 +1586,40 @@ __global__ void __launch_bounds__(NT, 1) k_batched(Params p) {
   __shared__ int s_job;
   if (threadIdx.x == 0) { s_team = (int)cl_size(); s_pfd = p.pf_dist; }
   __syncthreads();
+  const Desc* descs = p.desc;
+  int S = p.S;
+  unsigned* queue = p.queue;
+  bool second = false;
   for (;;) {
     // a team's rank 0 claims the next scene for the whole team
     const int tm = team();
     if (tm > 1) cl_sync();               // every CTA has read the previous claim
     if (threadIdx.x == 0 && cl_rank() == 0) {
-      const int job = (int)atomicAdd(p.queue, 1u);
+      const int job = (int)atomicAdd(queue, 1u);
       s_job = job;
       for (int k = 1; k < tm; ++k) cl_st(cl_map(&s_job, (unsigned)k), job);
     } else if (threadIdx.x == 0 && tm == 1) {
-      s_job = (int)atomicAdd(p.queue, 1u);
+      s_job = (int)atomicAdd(queue, 1u);
     }
     if (tm > 1) cl_sync();
     else __syncthreads();
     const int job = s_job;
     __syncthreads();
-    if (job >= p.S) break;
-    const Desc d = p.desc[job];
+    if (job >= S) {
+      // this launch's own scenes are all claimed: its CTAs go on one by one with the queue it
+      // shares with the launch beside it (every CTA of a team saw the same claim)
+      if (!second && p.queue2) {
+        second = true;
+        descs = p.desc2;
+        S = p.S2;
+        queue = p.queue2;
+        if (threadIdx.x == 0) s_team = 1;
+        __syncthreads();
+        continue;
+      }
+      break;
+    }
+    const Desc d = descs[job];
     if (tm > 1 && d.n < p.team_min_n) {
       // below the team threshold: the cluster splits up, rank 0 keeps this scene alone and the
       // others go back to the queue
@@ -1681,6 +1711,8 @@ struct xm_batch {
   bool tuned = false;
   cudaStream_t stream = nullptr;
   cudaEvent_t ev = nullptr;
+  cudaStream_t stream2 = nullptr;           // the 4-CTA launch beside the pairs (captured fork)
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   double* slots = nullptr;
   size_t slots_doubles = 0;
   // graph cache
@@ -1692,6 +1724,7 @@ struct xm_batch {
   int cluster = 0;                          // CTAs per large scene (0: automatic)
   int team_n = 0;                           // rows from which a scene is large (0: automatic)
   int gcs = 0, gteam = 0;                   // the captured graph's cluster size and threshold
+  int gquad = -1;                           // and its number of scenes on 4-CTA clusters
   int pf = 1, gpf = -1;                     // sweep L2 prefetch distance (and the graph's): one
                                             // round measured best on the 256-scene batch (2 and 3
                                             // evict rows still in use)
@@ -1707,7 +1740,10 @@ void batch_release(xm_batch* b) {
   void* ps[] = {b->desc, b->Q32, b->Q64, b->spill, b->out, b->queue, b->slots};
   for (void* p : ps) if (p) cudaFree(p);
   if (b->ev) cudaEventDestroy(b->ev);
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  if (b->ev_join) cudaEventDestroy(b->ev_join);
   if (b->stream) cudaStreamDestroy(b->stream);
+  if (b->stream2) cudaStreamDestroy(b->stream2);
   delete b;
 }
 
@@ -1758,12 +1794,15 @@ extern "C" xm_status xm_batch_create(xm_ctx* c, int S, const xm_qmat* const* qs,
   } while (0)
   XB_TRY(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
   XB_TRY(cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming));
+  XB_TRY(cudaStreamCreateWithFlags(&b->stream2, cudaStreamNonBlocking));
+  XB_TRY(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming));
+  XB_TRY(cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming));
   XB_TRY(cudaMalloc(&b->desc, sizeof(bat::Desc) * S));
   XB_TRY(cudaMalloc(&b->Q32, sizeof(float) * (size_t)o64));
   XB_TRY(cudaMalloc(&b->Q64, sizeof(double) * (size_t)o64));
   XB_TRY(cudaMalloc(&b->spill, sizeof(double) * (size_t)osp));
   XB_TRY(cudaMalloc(&b->out, sizeof(xm_batch_info) * S));
-  XB_TRY(cudaMalloc(&b->queue, sizeof(unsigned) * 2));
+  XB_TRY(cudaMalloc(&b->queue, sizeof(unsigned) * 4));
   XB_TRY(cudaMemcpyAsync(b->desc, b->desc_h.data(), sizeof(bat::Desc) * S, cudaMemcpyHostToDevice, c->stream));
   double* tmp = nullptr;
   XB_TRY(cudaMalloc(&tmp, sizeof(double) * (size_t)b->n_max * b->n_max));
@@ -1881,27 +1920,21 @@ extern "C" xm_status xm_solve_batched(xm_ctx* c, xm_batch* b, const xm_opts* opt
   // Teams: a scene whose solve alone would outlast the average load of a CTA sets the batch's
   // makespan, so it runs on a cluster of cs CTAs (its solve is mostly Q products, which the
   // cluster splits by rows).  Cost model: n^2 per scene (the products' bytes), spread over one
-  // CTA per SM.  Without such a scene the launch has no clusters.
-  int cs = b->cluster > 0 ? b->cluster : 2;
-  int team_n = b->team_n;
-  if (cs > 1 && team_n == 0) {
-    double w = 0.0;
-    for (const bat::Desc& d : b->desc_h) w += (double)d.n * d.n;
-    team_n = (int)std::ceil(std::sqrt(w / c->num_sms));
-  }
-  if (b->n_max < team_n) cs = 1;
-  if (cs == 1) team_n = 0;
-  int grid = std::min(c->num_sms, b->S);
-  if (cs > 1) {
+  // CTA per SM.  Without such a scene the launch has no clusters.  The automatic setting also
+  // looks for scenes of QUAD_FACTOR times that size: when at least two exist they run on 4-CTA
+  // clusters in a launch beside the pairs (two branches of the graph, disjoint slots), the
+  // pairs then starting at PAIR_FACTOR times it; both launches go on with single CTAs from one
+  // shared queue once their team scenes are claimed.
+  auto max_clusters = [&](int csz, int* out) -> xm_status {
     int ncl = 0;
     for (int pass = 0; pass < 2; ++pass) {
       cudaLaunchConfig_t cfg{};
-      cfg.gridDim = dim3(cs * std::max(1, c->num_sms / cs));
+      cfg.gridDim = dim3(csz * std::max(1, c->num_sms / csz));
       cfg.blockDim = dim3(bat::NT);
       cfg.dynamicSmemBytes = pass == 0 ? smem4 : smem8;
       cudaLaunchAttribute at[1];
       at[0].id = cudaLaunchAttributeClusterDimension;
-      at[0].val.clusterDim.x = cs;
+      at[0].val.clusterDim.x = csz;
       at[0].val.clusterDim.y = 1;
       at[0].val.clusterDim.z = 1;
       cfg.attrs = at;
@@ -1911,26 +1944,68 @@ extern "C" xm_status xm_solve_batched(xm_ctx* c, xm_batch* b, const xm_opts* opt
                                                                 : (const void*)bat::k_batched<8>, &cfg));
       ncl = pass == 0 ? k : std::min(ncl, k);
     }
+    *out = ncl;
+    return XM_OK;
+  };
+  int cs = b->cluster > 0 ? b->cluster : 2;
+  int team_n = b->team_n;
+  int nquad = 0;
+  if (cs > 1 && team_n == 0) {
+    double w = 0.0;
+    for (const bat::Desc& d : b->desc_h) w += (double)d.n * d.n;
+    const double base = std::sqrt(w / c->num_sms);
+    team_n = (int)std::ceil(base);
+    if (b->cluster == 0) {
+      const int quad_n = (int)std::ceil(bat::QUAD_FACTOR * base);
+      for (const bat::Desc& d : b->desc_h) nquad += d.n >= quad_n;
+      nquad = std::min(nquad, c->num_sms / 16);
+      if (nquad >= 2) team_n = (int)std::ceil(bat::PAIR_FACTOR * base);
+      else nquad = 0;
+    }
+  }
+  if (b->n_max < team_n) { cs = 1; nquad = 0; }
+  if (cs == 1) team_n = 0;
+  int grid = std::min(c->num_sms, b->S);   // the single launch, and the rank-8 launch
+  int gridA = 0, gridB = 0;                 // the 4-CTA launch and the pairs beside it
+  if (cs > 1) {
+    int ncl = 0;
+    XM_TRY(max_clusters(cs, &ncl));
     if (ncl < 1) return set_error(XM_EINVAL, "xm_solve_batched: no cluster of %d CTAs fits on this device", cs);
     int big = 0;
     for (const bat::Desc& d : b->desc_h) big += d.n >= team_n;
     grid = cs * std::min(ncl, big + (b->S - big + cs - 1) / cs);   // teams, then single CTAs
+    if (nquad > 0) {
+      int ncl4 = 0;
+      XM_TRY(max_clusters(4, &ncl4));
+      nquad = std::min(nquad, ncl4);
+      if (nquad >= 2) {
+        gridA = 4 * nquad;
+        const int SB = b->S - nquad;
+        int bigB = 0;
+        for (int j = nquad; j < b->S; ++j) bigB += b->desc_h[j].n >= team_n;
+        const int avail = (c->num_sms - gridA) / 2;
+        gridB = 2 * std::max(1, std::min(std::min(ncl, avail), bigB + (SB - bigB + 1) / 2));
+      } else {
+        nquad = 0;
+      }
+    }
   }
+  const int nslots = std::max(grid, gridA + gridB);
   const size_t slot_doubles = ((size_t)bat::NVEC * b->NM * 8 + (size_t)b->NM * (XM_MAX_RANK + kmax + 1) +
                                2 * (size_t)b->NM + 31) & ~size_t(31);
-  if (!b->slots || b->slots_doubles < slot_doubles * grid) {
+  if (!b->slots || b->slots_doubles < slot_doubles * nslots) {
     if (b->slots) cudaFree(b->slots);
     b->slots = nullptr;
     b->slots_doubles = 0;
-    XM_CUDA_TRY(cudaMalloc(&b->slots, sizeof(double) * slot_doubles * grid));
-    b->slots_doubles = slot_doubles * grid;
+    XM_CUDA_TRY(cudaMalloc(&b->slots, sizeof(double) * slot_doubles * nslots));
+    b->slots_doubles = slot_doubles * nslots;
     if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
   }
   if (!b->tuned) XM_TRY(xm_batch_autotune(c, b, 8, nullptr));
   // order after the caller's work on the context stream
   XM_CUDA_TRY(cudaEventRecord(b->ev, c->stream));
   XM_CUDA_TRY(cudaStreamWaitEvent(b->stream, b->ev, 0));
-  const bool same = b->gexec && b->gR == R_out && b->gs == s_out && b->gkmax == kmax && b->gcs == cs && b->gteam == team_n && b->gpf == b->pf &&
+  const bool same = b->gexec && b->gR == R_out && b->gs == s_out && b->gkmax == kmax && b->gcs == cs && b->gteam == team_n && b->gquad == nquad && b->gpf == b->pf &&
                     std::memcmp(&b->gopts, &o, sizeof(xm_opts)) == 0;
   if (!same) {
     if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
@@ -1953,31 +2028,56 @@ extern "C" xm_status xm_solve_batched(xm_ctx* c, xm_batch* b, const xm_opts* opt
     p.time_limit_ns = o.time_limit_s > 0 ? (unsigned long long)(o.time_limit_s * 1e9) : 0ull;
     p.team_min_n = team_n;
     p.pf_dist = b->pf;
+    p.slot_base = 0;
+    p.queue2 = nullptr;
+    p.desc2 = nullptr;
+    p.S2 = 0;
     bat::Params p8 = p;
     p.queue = b->queue;
     p8.queue = b->queue + 1;
-    cudaGraph_t graph = nullptr;
-    XM_CUDA_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-    cudaMemsetAsync(b->queue, 0, sizeof(unsigned) * 2, b->stream);
-    {
+    // queues: [0] the pairs (or the single launch), [1] the rank-8 launch, [2] the 4-CTA launch
+    bat::Params pA = p, pB = p;
+    if (nquad > 0) {
+      pA.S = nquad;
+      pA.queue = b->queue + 2;
+      pA.team_min_n = 0;
+      pA.queue2 = b->queue;
+      pA.desc2 = b->desc + nquad;
+      pA.S2 = b->S - nquad;
+      pB.desc = b->desc + nquad;
+      pB.S = b->S - nquad;
+      pB.slot_base = gridA;
+    }
+    auto launch = [&](cudaStream_t stv, int g, int csz, size_t smem, bool r8, const bat::Params& pp) {
       cudaLaunchConfig_t cfg{};
-      cfg.gridDim = dim3(grid);
+      cfg.gridDim = dim3(g);
       cfg.blockDim = dim3(bat::NT);
-      cfg.stream = b->stream;
+      cfg.stream = stv;
       cudaLaunchAttribute at[1];
       at[0].id = cudaLaunchAttributeClusterDimension;
-      at[0].val.clusterDim.x = cs;
+      at[0].val.clusterDim.x = csz;
       at[0].val.clusterDim.y = 1;
       at[0].val.clusterDim.z = 1;
       cfg.attrs = at;
       cfg.numAttrs = 1;
-      cfg.dynamicSmemBytes = smem4;
-      cudaLaunchKernelEx(&cfg, bat::k_batched<4>, p);
-      if (o.r_max > 4) {
-        cfg.dynamicSmemBytes = smem8;
-        cudaLaunchKernelEx(&cfg, bat::k_batched<8>, p8);
-      }
+      cfg.dynamicSmemBytes = smem;
+      if (r8) cudaLaunchKernelEx(&cfg, bat::k_batched<8>, pp);
+      else cudaLaunchKernelEx(&cfg, bat::k_batched<4>, pp);
+    };
+    cudaGraph_t graph = nullptr;
+    XM_CUDA_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    cudaMemsetAsync(b->queue, 0, sizeof(unsigned) * 4, b->stream);
+    if (nquad > 0) {
+      cudaEventRecord(b->ev_fork, b->stream);
+      cudaStreamWaitEvent(b->stream2, b->ev_fork, 0);
+      launch(b->stream2, gridA, 4, smem4, false, pA);
+      launch(b->stream, gridB, 2, smem4, false, pB);
+      cudaEventRecord(b->ev_join, b->stream2);
+      cudaStreamWaitEvent(b->stream, b->ev_join, 0);
+    } else {
+      launch(b->stream, grid, cs, smem4, false, p);
     }
+    if (o.r_max > 4) launch(b->stream, grid, cs, smem8, true, p8);
     const cudaError_t ec = cudaStreamEndCapture(b->stream, &graph);
     if (ec != cudaSuccess) return set_error(XM_ECUDA, "xm_solve_batched: capture failed: %s", cudaGetErrorString(ec));
     const cudaError_t ei = cudaGraphInstantiate(&b->gexec, graph, 0);
@@ -1991,6 +2091,7 @@ extern "C" xm_status xm_solve_batched(xm_ctx* c, xm_batch* b, const xm_opts* opt
     b->gkmax = kmax;
     b->gcs = cs;
     b->gteam = team_n;
+    b->gquad = nquad;
     b->gpf = b->pf;
     b->gopts = o;
   }
