@@ -63,12 +63,13 @@ L2_BYTES = 126e6
 # sweep kernel changes.
 SWEEP_TRAFFIC_RATIO = (1.88 + 0.00412) / 1.857268
 SWEEP_TRAFFIC_N = 30465
-# The same ratio for k_batched<4> on the 256-scene batch: DRAM read + write of one launch (one
-# whole batch, one ncu --set full capture of the kernel as it stands) over the dense sweep bytes
-# of that launch's scenes (the bytes_per_launch the profiled run printed).  Below 1: L2 serves
-# part of the small scenes' re-reads.  Applied to the 256-scene batch only; re-measure (or set
-# to None) whenever the batched kernel changes.
-BATCH_TRAFFIC_RATIO = (78.787872 + 2.726973) / 90.936067344
+# The same ratio for k_batched<4> on the 256-scene batch with pairs only (one launch per batch):
+# DRAM read + write of that launch over the dense sweep bytes of its scenes, from one ncu
+# capture (0.90: L2 serves part of the small scenes' re-reads).  With the automatic mixed teams
+# the batch is two launches running side by side, which ncu serialises (the first then drains
+# both queues alone, with L2 serving most of its reads), so no capture measures that mode's
+# traffic: it is reported as null.
+BATCH_TRAFFIC_RATIO_PAIRS = (78.787872 + 2.726973) / 90.936067344
 
 
 def peaks():
@@ -410,6 +411,7 @@ def batched_measure(ctx, scs, warmup: int, steps: int, time_limit: float = 60.0)
     ev1.record(ctx.stream)
     torch.cuda.synchronize()
     per_step = max(time.perf_counter() - wall0, ev0.elapsed_time(ev1) / 1e3) / steps
+    launches, quads = xm.xm_batch_launches(b)
     last = infos[-1]
     t_first = min(i["t_begin_ns"] for i in last)
     done_ms = [(i["t_end_ns"] - t_first) / 1e6 for i in last]
@@ -431,10 +433,13 @@ def batched_measure(ctx, scs, warmup: int, steps: int, time_limit: float = 60.0)
         "certified": sum(i["certified"] for i in last), "scenes": S, "cameras": tot,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
-                     "traffic": by * BATCH_TRAFFIC_RATIO if S == 256 else None,
-                     "traffic_note": "ncu DRAM read+write of one batch launch as a ratio to its dense "
-                                     "sweep bytes (256-scene batch only)",
-                     "kernel": "k_batched<4>",
+                     "traffic": None,
+                     "traffic_note": ("null: the batch's two launches run side by side and ncu "
+                                      "serialises them; " if quads else "null: ") +
+                                     "with pairs only (one launch, before the shared second queue) ncu "
+                                     f"measured DRAM read+write = {BATCH_TRAFFIC_RATIO_PAIRS:.2f} of the "
+                                     "dense sweep bytes",
+                     "kernel": "k_batched<4>" + (" (4-CTA and 2-CTA launches side by side)" if quads else ""),
                      "bytes_per_launch": by, "launch_ms": per_step * 1e3, "peak_kind": peak_kind,
                      "note": "dense sweep bytes of all scenes / batch time; the FP32 copies total "
                              f"{q_bytes / 1e6:.0f} MB, so part of every sweep is served by L2"},
@@ -445,6 +450,7 @@ def batched_measure(ctx, scs, warmup: int, steps: int, time_limit: float = 60.0)
         "escapes": int(sum(i["n_escapes"] for i in last)),
         "ranks": {str(r): sum(1 for i in last if i["rank"] == r) for r in sorted({i["rank"] for i in last})},
         "build_q_s": t_build, "pack_s": t_pack, "autotune_s": t_tune,
+        "launches_per_batch": launches, "quad_scenes": quads,
     }
 
 
@@ -499,7 +505,7 @@ def run_batched(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
         "config": {"workload": f"c5: {BATCH_DESC}", "scenes": S, "cameras": tot, "l2": m.pop("l2")},
         "latency_ms": m["latency_ms"], "certified": m["certified"], "roofline": m["roofline"],
-        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps, "clocks": clk,
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": m["launches_per_batch"] * args.steps, "clocks": clk,
         **{k: m[k] for k in ("tiling_rows_chunks", "sweeps", "sweeps_fp64", "escapes", "ranks",
                              "build_q_s", "pack_s", "autotune_s")},
     }

@@ -428,6 +428,11 @@ xm_status xm_batch_autotune(xm_ctx* ctx, xm_batch* b, int reps, int* tile_out);
  * 1.3 times it; both launches go on with single CTAs from one shared queue (still bit-identical).
  * XM_EINVAL for other values.  Takes effect at the next xm_solve_batched. */
 xm_status xm_batch_cluster(xm_ctx* ctx, xm_batch* b, int cs, int n_min);
+/* The CUDA graph that the last xm_solve_batched replayed: *launches (may be NULL) receives its
+ * kernel launches per call (one rank-4 launch, or the 4-CTA and 2-CTA launches side by side; plus
+ * the rank-8 launch when r_max > 4), *quad_scenes (may be NULL) the number of scenes it runs on
+ * 4-CTA clusters beside the pairs.  XM_EINVAL before the first xm_solve_batched. */
+xm_status xm_batch_launches(xm_ctx* ctx, const xm_batch* b, int* launches, int* quad_scenes);
 /* Solves every scene.  opts: as xm_solve (r0 <= 4, r_max <= 8; prec is ignored: the FP32-bulk
  * schedule is used; time_limit_s applies per scene).  R_out (sum N x 3 x 3) and s_out (sum N),
  * device pointers, receive the rounded solutions scene after scene in the order of

@@ -1725,6 +1725,7 @@ struct xm_batch {
   int team_n = 0;                           // rows from which a scene is large (0: automatic)
   int gcs = 0, gteam = 0;                   // the captured graph's cluster size and threshold
   int gquad = -1;                           // and its number of scenes on 4-CTA clusters
+  int glaunches = 0;                        // kernel launches per replay of the graph
   int pf = 1, gpf = -1;                     // sweep L2 prefetch distance (and the graph's): one
                                             // round measured best on the 256-scene batch (2 and 3
                                             // evict rows still in use)
@@ -1828,6 +1829,14 @@ extern "C" xm_status xm_batch_free(xm_ctx* c, xm_batch* b) {
   if (!b) return XM_OK;
   if (c) cudaSetDevice(c->device);
   batch_release(b);
+  return XM_OK;
+}
+
+extern "C" xm_status xm_batch_launches(xm_ctx* c, const xm_batch* b, int* launches, int* quad_scenes) {
+  if (!c || !b) return set_error(XM_EINVAL, "xm_batch_launches: NULL argument");
+  if (!b->gexec) return set_error(XM_EINVAL, "xm_batch_launches: no batched solve yet");
+  if (launches) *launches = b->glaunches;
+  if (quad_scenes) *quad_scenes = b->gquad;
   return XM_OK;
 }
 
@@ -2092,6 +2101,7 @@ extern "C" xm_status xm_solve_batched(xm_ctx* c, xm_batch* b, const xm_opts* opt
     b->gcs = cs;
     b->gteam = team_n;
     b->gquad = nquad;
+    b->glaunches = (nquad > 0 ? 2 : 1) + (o.r_max > 4 ? 1 : 0);
     b->gpf = b->pf;
     b->gopts = o;
   }

@@ -139,6 +139,7 @@ def lib() -> ctypes.CDLL:
         "xm_batch_free": (ctypes.c_int, [_P, _P]),
         "xm_batch_autotune": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
         "xm_batch_cluster": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int]),
+        "xm_batch_launches": (ctypes.c_int, [_P, _P, _P, _P]),
         "xm_solve_batched": (ctypes.c_int, [_P, _P, ctypes.POINTER(XmOpts), _P, _P,
                                             ctypes.POINTER(XmBatchInfo)]),
         "xm_qfact_create": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int64, _P, _P, _P, _P,
@@ -500,6 +501,15 @@ def xm_batch_cluster(b: Batch, cs: int, n_min: int = 0) -> None:
     """Scenes with 3N >= n_min run on a thread-block cluster of cs CTAs (1, 2, 4); 0 for the
     automatic choice of either."""
     _check(lib().xm_batch_cluster(b.ctx.h, b.h, cs, n_min))
+
+
+def xm_batch_launches(b: Batch) -> tuple:
+    """(kernel launches per xm_solve_batched call, scenes on 4-CTA clusters) of the last solve's
+    graph."""
+    n = ctypes.c_int(0)
+    q = ctypes.c_int(0)
+    _check(lib().xm_batch_launches(b.ctx.h, b.h, ctypes.byref(n), ctypes.byref(q)))
+    return n.value, q.value
 
 
 def xm_solve_batched(b: Batch, opts: XmOpts | None = None, R=None, s=None, allow_notcert: bool = True):

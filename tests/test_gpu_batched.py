@@ -174,6 +174,10 @@ def test_batched_time_limit_on_split_clusters(C):
         q.free()
     ref = xm.xm_solve_batched(b, xm.xm_default_opts(time_limit_s=0.0))
     assert all(i["certified"] == 1 for i in ref["info"])
+    # automatic teams: the largest scenes on 4-CTA clusters beside the pairs (two rank-4 launches
+    # and the rank-8 launch per call)
+    launches, quads = xm.xm_batch_launches(b)
+    assert launches == 3 and 2 <= quads <= 16, (launches, quads)
     for _ in range(3):
         o = xm.xm_solve_batched(b, xm.xm_default_opts(time_limit_s=60.0))
         bad = [(i["N"], i["status"], i["n_outer"]) for i in o["info"] if i["certified"] != 1]
