@@ -50,10 +50,11 @@ BATCH_DESC = ("256 independent scenes, cameras log-uniform in [10, 400] (floor),
 PRECS = {"fp64": 0, "fp32": 1, "bf16": 2}
 DTYPES = {"fp64": "f64", "fp32": "f32", "bf16": "bf16/f32"}
 # Sweeps of one certified FP32-bulk solve of each workload as measured on a B300 by the GPU arm
-# of this benchmark (10155 cameras: mean of the 20 timed solves of a 20-step run; the others:
-# mean of 5 or 2); the reference arm multiplies the oracle's time per sweep by it (an
+# of this benchmark with the default options (bulk-phase tCG solves of at most 60 iterations;
+# 10155 cameras: mean of the 5 timed solves of a default run; 1934 cameras and the trajectory:
+# mean of 3 solves); the reference arm multiplies the oracle's time per sweep by it (an
 # extrapolation, labelled as such in its line).
-REFERENCE_SWEEPS = {"c3": 2230, "c2": 575, "c4": 11500, "c1": 500}
+REFERENCE_SWEEPS = {"c3": 1720, "c2": 570, "c4": 10190, "c1": 500}
 L2_BYTES = 126e6
 # DRAM bytes (read + write) over algorithmic bytes of qy_packed_kernel<float,4,8> from one ncu
 # capture at the 10155-camera size itself (n = 30465: 1.88 GB read + 0.00412 GB written per
